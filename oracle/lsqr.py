@@ -1,0 +1,121 @@
+"""LSQR and the whole of Algorithm 1 (Ski-LLS), step by step.
+
+Test infrastructure: see ``oracle/__init__.py`` for who may import this.
+
+Algorithm 1: (1) draw S, form SA and Sb; (2) factor SA = QR; (3) x_s =
+R^{-1} Q^T Sb, stop if ||A x_s - b|| <= tau_a; (4) LSQR on min ||W y - b|| with
+W = A R^{-1} (Eq. def::W), stopped by the test of Eq. TC-lsqr
+||W^T (W y - b)|| / (||W|| ||W y - b||) <= tau_r; (5) x = R^{-1} y.
+LSQR starts from y_0 = Q^T Sb (Theorem 10 (ii)): it is run on the residual
+problem min ||W delta - (b - W y_0)|| and y = y_0 + delta.
+"""
+import numpy as np
+from scipy.linalg import solve_triangular
+
+from . import qr as _qr
+from . import sketch as _sketch
+from . import wht as _wht
+
+
+def lsqr(Wmul, WTmul, rhs, nvar, tau_r, it_max):
+    """LSQR of Paige & Saunders (ACM TOMS 8, 1982) for min ||W y - rhs||, y_0 = 0.
+
+    Golub-Kahan bidiagonalisation beta_1 u_1 = rhs, alpha_1 v_1 = W^T u_1, then
+    per iteration: beta u <- W v - alpha u; alpha v <- W^T u - beta v; a plane
+    rotation (rho, c, s) eliminates beta; y and w are updated.  The estimates
+    ||r|| = phibar, ||W^T r|| = phibar * alpha * |c| and ||W||_F ~ sqrt(sum of
+    alpha^2 + beta^2) give the stopping test of Eq. TC-lsqr.
+    Returns (y, iterations, list of test values).
+    """
+    u = np.array(rhs, dtype=np.float64, copy=True)
+    beta = np.linalg.norm(u)
+    y = np.zeros(nvar)
+    if beta == 0.0:
+        return y, 0, []
+    u /= beta
+    v = WTmul(u)
+    alpha = np.linalg.norm(v)
+    if alpha == 0.0:
+        return y, 0, []
+    v /= alpha
+    w = v.copy()
+    phibar, rhobar = beta, alpha
+    anorm2 = 0.0
+    trace = []
+    it = 0
+    while it < it_max:
+        it += 1
+        u = Wmul(v) - alpha * u
+        beta = np.linalg.norm(u)
+        if beta > 0.0:
+            u /= beta
+        anorm2 += alpha * alpha + beta * beta
+        v = WTmul(u) - beta * v
+        alpha = np.linalg.norm(v)
+        if alpha > 0.0:
+            v /= alpha
+        rho = np.hypot(rhobar, beta)
+        c, s = rhobar / rho, beta / rho
+        theta = s * alpha
+        rhobar = -c * alpha
+        phi = c * phibar
+        phibar = s * phibar
+        y += (phi / rho) * w
+        w = v - (theta / rho) * w
+        rnorm = phibar
+        arnorm = phibar * alpha * abs(c)
+        test = arnorm / (np.sqrt(anorm2) * rnorm) if rnorm > 0 else 0.0
+        trace.append(test)
+        if test <= tau_r:
+            break
+    return y, it, trace
+
+
+def residual_metric(A, b, x):
+    """||A^T r|| / (||A||_F ||r||) with r = b - A x, all in FP64."""
+    r = b - A @ x
+    fro = np.sqrt((A.multiply(A)).sum()) if hasattr(A, "multiply") else np.linalg.norm(A)
+    rn = np.linalg.norm(r)
+    return float(np.linalg.norm(A.T @ r) / (fro * rn)) if rn > 0 else 0.0
+
+
+def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
+            it_max=10000, rcond=1e-12):
+    """Algorithm 1 with an s-hashing (optionally HRHT) sketch and Householder QR.
+
+    A: dense n x d ndarray or scipy sparse; b: length n.
+    Returns (x, info) with info = {iters, early_exit, x_s, R, qtsb, rank, trace}.
+    """
+    n, d = A.shape
+    if premix:
+        SAb = _wht.hrht_sketch(seed, s, m, np.asarray(A), b, n_pad)
+    else:
+        SAb = _sketch.sketch_rows(seed, s, m, A, b)
+    R, C = _qr.householder_qr(SAb, ncols=d)                       # Step 2
+    qtsb = C[:, 0]
+    p = _qr.numerical_rank(R, rcond)
+    if p < d:
+        raise np.linalg.LinAlgError(f"sketch has numerical rank {p} < {d}")
+    x_s = solve_triangular(R, qtsb)                               # Step 3
+    r0 = b - A @ x_s
+    info = dict(x_s=x_s, R=R, qtsb=qtsb, rank=p, early_exit=False, iters=0, trace=[])
+    if np.linalg.norm(r0) <= tau_a:
+        info["early_exit"] = True
+        return x_s, info
+
+    def Wmul(v):
+        return A @ solve_triangular(R, v)
+
+    def WTmul(u):
+        return solve_triangular(R, A.T @ u, trans="T")
+
+    delta, iters, trace = lsqr(Wmul, WTmul, r0, d, tau_r, it_max)  # Step 4
+    x = x_s + solve_triangular(R, delta)                          # Step 5
+    info.update(iters=iters, trace=trace)
+    return x, info
+
+
+def lstsq_reference(A, b):
+    """The exact least-squares minimiser by LAPACK (gelsd), the result oracle."""
+    A = A.toarray() if hasattr(A, "toarray") else A
+    return np.linalg.lstsq(A, b, rcond=None)[0]

@@ -1,0 +1,56 @@
+"""Unblocked Householder QR of the sketch (Algorithm 1, Step 2).
+
+Test infrastructure: see ``oracle/__init__.py`` for who may import this.
+
+Step 2 factors SA = Q R (plain QR when SA has full rank, Remark (i)); Step 3
+needs Q_1^T Sb.  Factoring the first d columns of the augmented [SA | Sb] while
+applying every reflector to column d as well gives both: R is the leading
+d x d upper triangle and Q_1^T Sb the first d entries of column d.
+"""
+import numpy as np
+
+
+def householder_qr(B, ncols=None):
+    """Householder QR of the first ``ncols`` columns of B (m x c, m >= ncols).
+
+    For column j: x = B[j:, j]; beta = -sign(x_0) ||x||; v = x - beta e_1;
+    B[j:, j:] -= (2 / v^T v) v (v^T B[j:, j:]).  Reflectors are applied to every
+    column to the right, including columns beyond ``ncols``.
+    Returns (R, C): R (ncols x ncols) upper triangular and C = (Q^T B)[:ncols, ncols:].
+    """
+    B = np.array(B, dtype=np.float64, copy=True)
+    m, c = B.shape
+    k = c if ncols is None else ncols
+    if m < k:
+        raise ValueError("need m >= ncols")
+    for j in range(k):
+        x = B[j:, j]
+        normx = np.sqrt(np.dot(x, x))
+        if normx == 0.0:
+            continue
+        beta = -normx if x[0] >= 0 else normx
+        v = x.copy()
+        v[0] -= beta
+        vtv = np.dot(v, v)
+        w = v @ B[j:, j:]
+        B[j:, j:] -= np.outer(v, (2.0 / vtv) * w)
+        B[j + 1:, j] = 0.0
+        B[j, j] = beta
+    return np.triu(B[:k, :k]), B[:k, k:]
+
+
+def numerical_rank(R, rcond):
+    """p = number of leading diagonal entries with |r_qq| >= rcond * |r_11|.
+
+    The paper's rule ("largest q with r_qq >= rcond", Ski-LLS-dense parameters)
+    read relative to |r_11| and on magnitudes, since Householder diagonals carry
+    arbitrary signs.
+    """
+    dg = np.abs(np.diag(R))
+    if dg.size == 0 or dg[0] == 0.0:
+        return 0
+    ok = dg >= rcond * dg[0]
+    p = 0
+    while p < dg.size and ok[p]:
+        p += 1
+    return p

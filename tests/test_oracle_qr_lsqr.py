@@ -1,0 +1,151 @@
+"""Pins for the Householder QR (Step 2), LSQR (Step 4) and Algorithm 1 end to end."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.linalg import solve_triangular
+
+from oracle import adjoint, embedding, lsqr, qr, sketch, wht
+from paper_2105_11815_gb300 import workloads
+
+
+def _signfix(R):
+    return np.sign(np.diag(R))[:, None] * R
+
+
+def test_householder_matches_lapack():
+    g = np.random.default_rng(0)
+    B = g.standard_normal((60, 13))
+    R, C = qr.householder_qr(B, ncols=12)
+    Q, Rl = np.linalg.qr(B[:, :12])
+    assert np.allclose(_signfix(R), _signfix(Rl), atol=1e-12)
+    assert np.allclose(R.T @ R, B[:, :12].T @ B[:, :12], atol=1e-11)
+    # column 12 carries Q^T b (signs follow the rows of R)
+    sgn = np.sign(np.diag(R)) * np.sign(np.diag(Rl))
+    assert np.allclose(C[:, 0], sgn * (Q.T @ B[:, 12]), atol=1e-12)
+
+
+def test_numerical_rank():
+    g = np.random.default_rng(1)
+    B = g.standard_normal((40, 6))
+    B[:, 5] = B[:, 0] + B[:, 1]
+    R, _ = qr.householder_qr(B)
+    assert qr.numerical_rank(R, 1e-12) == 5
+    assert qr.numerical_rank(qr.householder_qr(g.standard_normal((40, 6)))[0], 1e-12) == 6
+
+
+def test_lsqr_matches_lstsq_unpreconditioned():
+    g = np.random.default_rng(2)
+    A, b = g.standard_normal((200, 20)), g.standard_normal(200)
+    y, it, _ = lsqr.lsqr(lambda v: A @ v, lambda u: A.T @ u, b, 20, 1e-14, 500)
+    assert np.allclose(y, np.linalg.lstsq(A, b, rcond=None)[0], rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("premix", [False, True])
+def test_ski_lls_matches_lstsq(premix):
+    A, b, _ = workloads.gaussian_lls(1024, 64, seed=5)
+    x, info = lsqr.ski_lls(A, b, seed=17, s=1, m=128, premix=premix)
+    xr = lsqr.lstsq_reference(A, b)
+    assert np.linalg.norm(x - xr) <= 1e-10 * np.linalg.norm(xr)
+    assert lsqr.residual_metric(A, b, x) <= 1e-10
+    assert info["iters"] > 0
+
+
+def test_ski_lls_sparse():
+    rp, ci, v, b = workloads.csr_heavy_rows(4000, 100, seed=3, nnz_row=8, heavy_frac=0.005, heavy_nnz=60)
+    A = sp.csr_matrix((v, ci, rp), shape=(4000, 100))
+    x, info = lsqr.ski_lls(A, b, seed=1, s=2, m=200)
+    assert lsqr.residual_metric(A, b, x) <= 1e-10
+    xr = lsqr.lstsq_reference(A, b)
+    assert np.linalg.norm(x - xr) <= 1e-9 * np.linalg.norm(xr)
+
+
+def test_preconditioned_spectrum_within_embedding_bound():
+    # Thm 10 proof, Eq. (Low condition number): kappa(W^T W) <= (1+eps)/(1-eps)
+    # for W = A R^{-1} when S is an eps-subspace embedding for A (eps measured
+    # by Lemma 2).  With S A R^{-1} = Q orthonormal the embedding inequality
+    # gives sigma(W) in [1/sqrt(1+eps), 1/sqrt(1-eps)]; the proof's intermediate
+    # [sqrt(1-eps), sqrt(1+eps)] has the two sides exchanged, the ratio is the same.
+    A, b, _ = workloads.gaussian_lls(2000, 40, seed=8)
+    m = 400
+    SAb = sketch.sketch_rows(4, 2, m, A, b)
+    R, _ = qr.householder_qr(SAb, ncols=40)
+    U = embedding.orth(A)
+    eps = embedding.distortion(sketch.sketch_rows(4, 2, m, U))
+    assert 0 < eps < 1
+    sv = np.linalg.svd(A @ np.linalg.inv(R), compute_uv=False)
+    assert sv[0] <= (1 - eps) ** -0.5 * (1 + 1e-12)
+    assert sv[-1] >= (1 + eps) ** -0.5 * (1 - 1e-12)
+    assert (sv[0] / sv[-1]) ** 2 <= (1 + eps) / (1 - eps) * (1 + 1e-12)
+
+
+def test_lemma8_and_theorem10_bounds():
+    A, b, _ = workloads.gaussian_lls(3000, 30, seed=9, noise=1.0)
+    m = 600
+    x, info = lsqr.ski_lls(A, b, seed=6, s=2, m=m, tau_r=1e-6)
+    xr = lsqr.lstsq_reference(A, b)
+    rstar = np.linalg.norm(A @ xr - b)
+    U = embedding.orth(np.column_stack([A, b]))
+    eps = embedding.distortion(sketch.sketch_rows(6, 2, m, U))
+    assert eps < 1
+    # Lemma 8: ||A x_s - b|| <= (1+eps)/(1-eps) ||A x* - b||
+    assert np.linalg.norm(A @ info["x_s"] - b) <= (1 + eps) / (1 - eps) * rstar
+    # Thm 10 (ii) with the energy-norm reduction tau_r reached by LSQR: the final
+    # residual is within (1 + 2 eps tau/(1-eps)) of optimal, tau the achieved reduction.
+    e0 = np.linalg.norm(A @ (info["x_s"] - xr))
+    e1 = np.linalg.norm(A @ (x - xr))
+    tau = e1 / e0
+    assert np.linalg.norm(A @ x - b) <= (1 + 2 * eps * tau / (1 - eps)) * rstar * (1 + 1e-12)
+
+
+def test_theorem10_iteration_count():
+    # Thm 10 (i): energy-norm error reduced by tau_r within
+    # (log 2 + |log tau_r|)/|log eps| iterations.
+    A, b, _ = workloads.gaussian_lls(4000, 40, seed=10, noise=1.0)
+    m, tau_r = 400, 1e-8
+    SAb = sketch.sketch_rows(12, 2, m, A, b)
+    R, C = qr.householder_qr(SAb, ncols=40)
+    eps = embedding.distortion(sketch.sketch_rows(12, 2, m, embedding.orth(A)))
+    xr = lsqr.lstsq_reference(A, b)
+    x_s = solve_triangular(R, C[:, 0])
+    r0 = b - A @ x_s
+    e0 = np.linalg.norm(A @ (x_s - xr))
+    bound = (math.log(2) + abs(math.log(tau_r))) / abs(math.log(eps))
+    k = math.ceil(bound)
+    d, _, _ = lsqr.lsqr(lambda v: A @ solve_triangular(R, v),
+                        lambda u: solve_triangular(R, A.T @ u, trans="T"), r0, 40, 0.0, k)
+    xk = x_s + solve_triangular(R, d)
+    assert np.linalg.norm(A @ (xk - xr)) <= tau_r * e0
+
+
+def test_premix_lowers_coherence_and_distortion():
+    A, _ = workloads.dense_high_coherence(2048, 32, seed=4)
+    Y = wht.premix(1, A, 2048)
+    assert embedding.coherence(Y) < 0.5 * embedding.coherence(A)
+
+
+def test_distortion_decreases_with_gamma():
+    A, _ = workloads.dense_gaussian(8192, 32, seed=2)
+    U = embedding.orth(A)
+    eps = [np.median([embedding.distortion(sketch.sketch_rows(sd, 1, int(g * 32), U))
+                      for sd in range(5)]) for g in (2, 4, 8)]
+    assert eps[0] > eps[1] > eps[2]
+
+
+def test_adjoint_against_finite_differences():
+    g = np.random.default_rng(11)
+    A, b = g.standard_normal((512, 32)), g.standard_normal(512)
+    c = g.standard_normal(32)
+
+    def L(A_, b_):
+        return c @ np.linalg.lstsq(A_, b_, rcond=None)[0]
+
+    x = np.linalg.lstsq(A, b, rcond=None)[0]
+    dA, db = adjoint.lstsq_grad(A, b, x, c)
+    for trial in range(3):
+        EA, eb = g.standard_normal(A.shape), g.standard_normal(b.shape)
+        h = 1e-6
+        fd = (L(A + h * EA, b + h * eb) - L(A - h * EA, b - h * eb)) / (2 * h)
+        an = np.sum(dA * EA) + db @ eb
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
