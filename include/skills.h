@@ -1,0 +1,243 @@
+/*
+ * skills.h -- C ABI of the GB300 (sm_103a) Ski-LLS hot path.
+ *
+ * The library solves the linear least-squares problem min_x ||A x - b||_2
+ * (Eq. LLS-statement; A is n x d, n >= d) by Algorithm 1 of Cartis, Fiala &
+ * Shao, "Hashing embeddings of optimal dimension, with applications to linear
+ * least squares" (arXiv 2105.11815):
+ *   Step 1  sketch: SA = S A and Sb = S b with S an s-hashing matrix (Def. 5),
+ *           optionally after the randomised Walsh-Hadamard premix H D (Def. 8);
+ *   Step 2  factor SA = Q R (Householder QR; plain QR since SA has full rank);
+ *   Step 3  x_s = R^{-1} Q^T Sb, accepted when ||A x_s - b|| <= tau_a;
+ *   Step 4  LSQR on min ||W y - b|| with W = A R^{-1}, stopped by Eq. TC-lsqr;
+ *   Step 5  x = R^{-1} y.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named as device pointers must be device memory of the current
+ *     CUDA device; the caller owns all memory and the library frees nothing.
+ *   - Scratch memory is caller-provided (`ws`, `ws_bytes`); each entry point
+ *     that needs it has a *_workspace_size query.  A too-small workspace
+ *     returns SKI_ENOMEM before any launch.  Workspace base pointers must be
+ *     256-byte aligned (cudaMalloc / the PyTorch allocator give this).
+ *   - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default).
+ *     Entry points documented as synchronous synchronise that stream before
+ *     returning.
+ *   - Argument errors are detected on the host before any launch and return
+ *     SKI_EINVAL.  CUDA launch/runtime errors return SKI_ECUDA.  No exception
+ *     crosses the ABI.
+ *   - Dense matrices are row-major with an explicit leading dimension (row
+ *     stride, in elements).  Element counts are int64.
+ */
+#ifndef SKILLS_H
+#define SKILLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SKI_OK = 0,
+  SKI_EINVAL = 1,      /* bad argument (detected on the host, nothing launched)   */
+  SKI_ENOMEM = 2,      /* caller workspace smaller than the *_workspace_size query */
+  SKI_ECUDA = 3,       /* a CUDA call failed                                       */
+  SKI_ENONFINITE = 4,  /* NaN/Inf met in the sketch, the factor or the residual    */
+  SKI_ESINGULAR = 5,   /* numerical rank of R below d under the rcond rule         */
+  SKI_ENOCONV = 6,     /* it_max LSQR iterations without meeting the tolerance     */
+  SKI_ETIMEOUT = 7     /* a bounded device-side wait gave up                       */
+} ski_status;
+
+typedef enum { SKI_F64 = 0, SKI_F32 = 1, SKI_BF16 = 2 } ski_dtype;
+typedef enum { SKI_DENSE = 0, SKI_CSR = 1 } ski_kind;
+
+/* The data matrix A (n x d).  Values are FP64 in both layouts. */
+typedef struct {
+  int32_t kind;           /* SKI_DENSE or SKI_CSR                                      */
+  int32_t pad_;
+  int64_t n, d;           /* rows, columns; n >= 1, d >= 1                             */
+  int64_t ld;             /* SKI_DENSE: row stride in elements, ld >= d                */
+  const double* val;      /* device. SKI_DENSE: n x d row-major. SKI_CSR: [nnz] values */
+  const int64_t* rowptr;  /* SKI_CSR: device [n+1], rowptr[0] = 0, non-decreasing      */
+  const int32_t* colidx;  /* SKI_CSR: device [nnz], each in [0, d)                     */
+  int64_t nnz;            /* SKI_CSR: number of stored entries                        */
+} ski_matrix;
+
+/* Parameters of Algorithm 1 (names as in the paper's Section 6). */
+typedef struct {
+  uint64_t seed;          /* draws S (Def. 5) and D (Def. 8) through the counter hash  */
+  int32_t s;              /* nonzeros per column of S, 1 <= s <= m                     */
+  int32_t premix;         /* 1: S = S_h H D (Def. 8), dense A only; 0: S = S_h         */
+  int64_t m;              /* sketch rows, d <= m < 2^31                                */
+  int64_t n_pad;          /* premix height, a power of two >= n; 0: next power of two */
+  int32_t sketch_dtype;   /* ski_dtype of the premix, the sketch and its output SA     */
+  int32_t qr_dtype;       /* ski_dtype of the QR of SA and of R^{-1} (R kept in FP64)   */
+  double tau_a;           /* Step 3: accept x_s when ||A x_s - b|| <= tau_a            */
+  double tau_r;           /* Step 4: LSQR tolerance of Eq. TC-lsqr                     */
+  double tol;             /* acceptance: ||A^T r|| / (||A||_F ||r||) <= tol, 0 = off   */
+  double rcond;           /* rank rule: |r_qq| >= rcond |r_11| for all q               */
+  double perturb;         /* > 0: divide by r_ii + perturb when R fails the rank rule  */
+  int64_t it_max;         /* Step 4 iteration cap                                       */
+} ski_opts;
+
+/* Result record of a solve (host memory). */
+typedef struct {
+  int64_t iters;          /* LSQR iterations (Step 4), summed over restarts          */
+  int32_t restarts;       /* LSQR restarts made to meet `tol`                        */
+  int32_t rank;           /* numerical rank p of R under the rcond rule              */
+  int32_t early_exit;     /* 1 when Step 3 accepted x_s                               */
+  int32_t status;         /* ski_status of the solve                                  */
+  double metric;          /* ||A^T r|| / (||A||_F ||r||), r = b - A x, FP64          */
+  double resid_norm;      /* ||b - A x||_2                                            */
+  double anorm_f;         /* ||A||_F                                                  */
+  double lsqr_test;       /* last Eq. TC-lsqr estimate                                */
+  float ms_sketch, ms_qr, ms_trinv, ms_lsqr, ms_total;  /* stage times, CUDA events */
+  float ms_premix, ms_gather;  /* inside ms_sketch: the H D premix and the hash gather */
+} ski_info;
+
+/* Defaults of Ski-LLS-dense (Section 6): m = 0 (caller must set), s = 1,
+ * tau_a = 1e-8, tau_r = 1e-6, it_max = 1e4, rcond = 1e-12; here also
+ * tol = 0, perturb = 0, premix = 0, FP64 sketch and QR. */
+void ski_opts_default(ski_opts* o);
+
+/* Human-readable name of a ski_status.  Never NULL. */
+const char* ski_status_string(int32_t status);
+
+/* ABI version (major * 100 + minor). */
+int32_t ski_version(void);
+
+/* cudaError_t code of the last CUDA call that failed in this host thread
+ * (the cause behind a SKI_ECUDA), 0 when none has failed. */
+int32_t ski_last_cuda_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all threads).  Diagnostic: lets a caller count the kernels of a region. */
+int64_t ski_launch_count(void);
+
+/*
+ * ski_hash_indices -- the nonzeros of the s-hashing matrix S (Def. 5).
+ * Column j < n of S (multiplying row j of A) holds sign[j*s+k] / sqrt(s) in row
+ * idx[j*s+k], k < s; the s rows are distinct (drawn without replacement).
+ * The draw is a counter hash: with sm() the SplitMix64 output function
+ * (Steele, Lea & Flood 2014) and key(tag, j, k, t) =
+ * sm(sm(sm(seed ^ tag << 56) ^ j) ^ (k << 32 | t)) modulo 2^64, nonzero k takes
+ * row floor(key(0xB1, j, k, t) * m / 2^64) for the first retry t = 0, 1, ...
+ * whose row differs from those of nonzeros 0..k-1, and sign -1 exactly when
+ * the top bit of key(0x5A, j, k, 0) is set.  D of Def. 8 uses key(0xD3, j, 0, 0).
+ *   idx  device int32 [n*s], sign device int8 [n*s] (+1 / -1).
+ * Asynchronous.  Errors: SKI_EINVAL unless 1 <= s <= m < 2^31 and n >= 0.
+ */
+ski_status ski_hash_indices(uint64_t seed, int32_t s, int64_t m, int64_t n,
+                            int32_t* idx, int8_t* sign, void* stream);
+
+/*
+ * ski_premix_signs -- the diagonal of D in the HRHT premix (Def. 8), D[j] in
+ * {+1, -1} for j < n.  D: device int8 [n].  Asynchronous.
+ */
+ski_status ski_premix_signs(uint64_t seed, int64_t n, int8_t* D, void* stream);
+
+/*
+ * ski_premix -- Y = H D [A b ; 0] for the n_pad x n_pad normalised
+ * Walsh-Hadamard matrix H_ij = n_pad^{-1/2} (-1)^{<(i-1)_2,(j-1)_2>} (Def. 8).
+ * A dense FP64 n x d; b device FP64 [n] or NULL.  Y: device, n_pad rows of
+ * d (+1 when b != NULL) columns, row stride ld_y, element type o->sketch_dtype
+ * (FP64 or FP32).  Asynchronous.  Uses o->seed and o->n_pad.
+ */
+size_t ski_premix_workspace_size(const ski_matrix* A, int32_t with_b, const ski_opts* o);
+ski_status ski_premix(const ski_matrix* A, const double* b, const ski_opts* o,
+                      void* Y, int64_t ld_y, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * ski_sketch_hash -- Step 1 of Algorithm 1: [SA | Sb] with S the s-hashing
+ * matrix (Def. 5), or S = S_h H D (Def. 8) when o->premix = 1.
+ *   SA  device, m rows, row stride ld_sa, element type o->sketch_dtype;
+ *       columns 0..d-1 receive S A and, when b != NULL, column d receives S b.
+ *       ld_sa >= d + (b != NULL).
+ * Row i of SA is the sum over the rows j hashed to i of sign/sqrt(s) * A[j,:],
+ * formed per output element in a fixed order (deterministic, bit-reproducible
+ * for a given seed).  Asynchronous.
+ */
+size_t ski_sketch_workspace_size(const ski_matrix* A, int32_t with_b, const ski_opts* o);
+ski_status ski_sketch_hash(const ski_matrix* A, const double* b, const ski_opts* o,
+                           void* SA, int64_t ld_sa, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * ski_precondition -- Step 2 of Algorithm 1: Householder QR of SA (m x d,
+ * d <= m), applying every reflector also to column d when with_rhs = 1 so that
+ * column d becomes Q^T Sb.
+ *   SA     device, m x (d + with_rhs), row stride ld_sa, element type sa_dtype
+ *          (FP64 or FP32); overwritten by the reflectors.
+ *   R      device FP64 d x d (row stride ldr): the upper triangle receives R,
+ *          the strict lower triangle is set to zero.
+ *   qtsb   device FP64 [d] or NULL: receives (Q^T Sb)[0..d-1] (with_rhs = 1).
+ *   rank   host int32 or NULL: numerical rank under o->rcond (synchronises).
+ * The factorisation runs in sa_dtype; R is returned in FP64.  Asynchronous
+ * unless rank != NULL.
+ */
+size_t ski_precondition_workspace_size(int64_t m, int64_t d, int32_t with_rhs, int32_t sa_dtype);
+ski_status ski_precondition(int64_t m, int64_t d, int32_t with_rhs, void* SA, int64_t ld_sa,
+                            int32_t sa_dtype, double* R, int64_t ldr, double* qtsb,
+                            int32_t* rank, const ski_opts* o, void* ws, size_t ws_bytes,
+                            void* stream);
+
+/*
+ * ski_trinv -- M = R^{-1} for an upper-triangular d x d R (FP64, row stride
+ * ldr), written to M (FP64, row stride ldm; strict lower triangle zero) and
+ * its transpose to Mt (row stride ldm) when Mt != NULL.  Computed in dtype
+ * (FP64 or FP32) and returned in FP64.  When perturb > 0 every diagonal
+ * r_ii is replaced by r_ii + perturb (the perturbed back-solve of Ski-LLS-sparse).
+ * The library applies R^{-1} as this explicit triangular matrix instead of a
+ * back-substitution (Remark (iii) only asks that no inverse of SA is formed).
+ */
+size_t ski_trinv_workspace_size(int64_t d, int32_t dtype);
+ski_status ski_trinv(int64_t d, const double* R, int64_t ldr, double* M, double* Mt, int64_t ldm,
+                     int32_t dtype, double perturb, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * ski_solve -- Algorithm 1 end to end.  x: device FP64 [d].  info: host, may
+ * be NULL.  R_out: device FP64 d x d (row stride d) or NULL, receives R (for a
+ * later ski_solve_adjoint).  Synchronous.  Returns SKI_ESINGULAR when R fails
+ * the rank rule and o->perturb = 0, SKI_ENOCONV when it_max is reached before
+ * the tolerances (x then holds the last iterate), SKI_ENONFINITE on NaN/Inf.
+ */
+size_t ski_solve_workspace_size(const ski_matrix* A, const ski_opts* o);
+ski_status ski_solve(const ski_matrix* A, const double* b, const ski_opts* o, double* x,
+                     double* R_out, ski_info* info, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * ski_solve_batched -- nprob independent problems (ragged n_i, d_i), each
+ * solved as ski_solve with the same options except m_i = ceil(gamma * d_i)
+ * when o->m <= 0 (gamma = -o->m / 1000, e.g. m = -2000 for gamma = 2) and
+ * seed_i = o->seed + i.  A, b, x, R_out, info are host arrays of nprob
+ * entries (R_out may be NULL, or hold NULL entries); b[i], x[i], R_out[i] are
+ * device pointers.  The workspace is one per problem in flight:
+ * ski_solve_batched_workspace_size gives its size.  Synchronous.  Returns the
+ * first non-SKI_OK status met (every problem is attempted).
+ */
+size_t ski_solve_batched_workspace_size(int32_t nprob, const ski_matrix* A, const ski_opts* o);
+ski_status ski_solve_batched(int32_t nprob, const ski_matrix* A, const double* const* b,
+                             const ski_opts* o, double* const* x, double* const* R_out,
+                             ski_info* info, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * ski_solve_adjoint -- backward pass of x = argmin ||A x - b|| for an upstream
+ * gradient g = dL/dx.  Solves (A^T A) lambda = g by conjugate gradients on the
+ * R-preconditioned normal equations (W^T W z = R^{-T} g, lambda = R^{-1} z,
+ * W = A R^{-1}, R from the forward solve), then forms
+ *   db = A lambda          (device FP64 [n])
+ *   dA = r lambda^T - (A lambda) x^T,  r = b - A x   (device FP64 n x d, row
+ *        stride ld_da; skipped when dA == NULL).
+ * Dense A only.  Stops when ||W^T W z - R^{-T} g|| <= o->tau_r ||R^{-T} g|| or
+ * after o->it_max iterations (SKI_ENOCONV).  Synchronous.
+ */
+size_t ski_solve_adjoint_workspace_size(const ski_matrix* A, const ski_opts* o);
+ski_status ski_solve_adjoint(const ski_matrix* A, const double* b, const double* x,
+                             const double* R, int64_t ldr, const double* g, double* dA,
+                             int64_t ld_da, double* db, const ski_opts* o, ski_info* info,
+                             void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKILLS_H */

@@ -1,0 +1,766 @@
+// C ABI of the library (include/skills.h): argument checks, workspace
+// planning and the stage order of Algorithm 1.  Every arithmetic step runs in
+// the kernels of the other translation units; this file only sequences them.
+#include <math.h>
+#include <string.h>
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "hash.cuh"
+#include "lsqr_impl.cuh"
+#include "sketch_impl.cuh"
+
+#include <atomic>
+
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+static std::atomic<long long> g_launches{0};
+void ski_note_cuda_error(cudaError_t e) { g_last_cuda = e; }
+void ski_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" int64_t ski_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" void ski_opts_default(ski_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->seed = 0;
+  o->s = 1;
+  o->m = 0;
+  o->premix = 0;
+  o->n_pad = 0;
+  o->sketch_dtype = SKI_F64;
+  o->qr_dtype = SKI_F64;
+  o->tau_a = 1e-8;
+  o->tau_r = 1e-6;
+  o->tol = 0.0;
+  o->rcond = 1e-12;
+  o->perturb = 0.0;
+  o->it_max = 10000;
+}
+
+extern "C" const char* ski_status_string(int32_t st) {
+  switch (st) {
+    case SKI_OK: return "SKI_OK";
+    case SKI_EINVAL: return "SKI_EINVAL: invalid argument";
+    case SKI_ENOMEM: return "SKI_ENOMEM: workspace too small";
+    case SKI_ECUDA: return "SKI_ECUDA: CUDA call failed";
+    case SKI_ENONFINITE: return "SKI_ENONFINITE: NaN or Inf encountered";
+    case SKI_ESINGULAR: return "SKI_ESINGULAR: R fails the rank rule";
+    case SKI_ENOCONV: return "SKI_ENOCONV: iteration limit reached";
+    case SKI_ETIMEOUT: return "SKI_ETIMEOUT: bounded device wait expired";
+    default: return "unknown ski_status";
+  }
+}
+
+extern "C" int32_t ski_version(void) { return 100; }
+
+extern "C" int32_t ski_last_cuda_error(void) { return (int32_t)g_last_cuda; }
+
+// ------------------------------------------------------------ validation
+static bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+static int64_t next_pow2(int64_t v) {
+  int64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+static bool dtype_ok(int32_t t) { return t == SKI_F64 || t == SKI_F32 || t == SKI_BF16; }
+static size_t dtype_size(int32_t t) { return t == SKI_F64 ? 8 : (t == SKI_F32 ? 4 : 2); }
+
+static ski_status check_matrix(const ski_matrix* A) {
+  if (!A) return SKI_EINVAL;
+  if (A->n < 1 || A->d < 1) return SKI_EINVAL;
+  if (A->kind == SKI_DENSE) {
+    if (!A->val || A->ld < A->d) return SKI_EINVAL;
+  } else if (A->kind == SKI_CSR) {
+    if (!A->rowptr || !A->colidx || A->nnz < 0 || (A->nnz > 0 && !A->val)) return SKI_EINVAL;
+    if (A->n >= (1ll << 31) || A->d >= (1ll << 31)) return SKI_EINVAL;
+  } else {
+    return SKI_EINVAL;
+  }
+  return SKI_OK;
+}
+
+static ski_status check_sketch_opts(const ski_matrix* A, const ski_opts* o) {
+  if (!o) return SKI_EINVAL;
+  if (o->s < 1 || o->s > 64 || o->m < o->s || o->m >= (1ll << 31)) return SKI_EINVAL;
+  if (!dtype_ok(o->sketch_dtype)) return SKI_EINVAL;
+  if (o->premix) {
+    if (A->kind != SKI_DENSE) return SKI_EINVAL;
+    if (o->n_pad != 0 && (!pow2(o->n_pad) || o->n_pad < A->n)) return SKI_EINVAL;
+    if (o->sketch_dtype == SKI_BF16 && false) return SKI_EINVAL;
+  }
+  const int64_t rows = o->premix ? (o->n_pad ? o->n_pad : next_pow2(A->n)) : A->n;
+  if (rows * (int64_t)o->s >= (1ll << 31) || rows >= (1ll << 31)) return SKI_EINVAL;
+  return SKI_OK;
+}
+
+static int64_t eff_npad(const ski_matrix* A, const ski_opts* o) {
+  return o->premix ? (o->n_pad ? o->n_pad : next_pow2(A->n)) : 0;
+}
+
+// ------------------------------------------------------------ sketch stage
+// Scratch layout: [bucket lists][premix Y][premix intermediates]
+static size_t sketch_scratch_bytes(const ski_matrix* A, int32_t with_b, const ski_opts* o, int64_t* ldy_out) {
+  const int64_t ncols = A->d + (with_b ? 1 : 0);
+  const int64_t rows = o->premix ? eff_npad(A, o) : A->n;
+  SkiArena ar{nullptr, 0, 0, true};
+  ar.take<char>(ski_bucket_ws_bytes(rows, o->s, o->m));
+  int64_t ldy = ski_round_up(ncols, 32);
+  if (o->premix) {
+    const int32_t pdt = o->sketch_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
+    ar.take<char>(dtype_size(pdt) * rows * ldy);
+    ar.take<char>(ski_premix_ws_bytes(A->n, ncols, rows, pdt));
+  }
+  if (ldy_out) *ldy_out = ldy;
+  return ar.off;
+}
+
+static ski_status sketch_run(const ski_matrix* A, const double* b, const ski_opts* o, void* SA, int64_t ld_sa,
+                             char* scratch, size_t scratch_bytes, cudaStream_t st, cudaEvent_t e_bk = nullptr,
+                             cudaEvent_t e_pm = nullptr) {
+  const int64_t ncols = A->d + (b ? 1 : 0);
+  const int64_t rows = o->premix ? eff_npad(A, o) : A->n;
+  SkiArena ar{scratch, scratch_bytes, 0, false};
+  const size_t bkb = ski_bucket_ws_bytes(rows, o->s, o->m);
+  char* bkws = ar.take<char>(bkb);
+  if (!ar.ok() || !bkws) return SKI_ENOMEM;
+  SkiArena bar{bkws, bkb, 0, false};
+  SkiBuckets bk;
+  SKI_TRY(ski_build_buckets(o->seed, o->s, o->m, rows, bar, st, &bk));
+  if (e_bk) SKI_CUDA_TRY(cudaEventRecord(e_bk, st));
+  const double inv_sqrt_s = 1.0 / sqrt((double)o->s);
+  if (!o->premix) {
+    if (e_pm) SKI_CUDA_TRY(cudaEventRecord(e_pm, st));
+    if (A->kind == SKI_DENSE)
+      return ski_gather_dense(A->val, A->ld, A->n, A->d, b, bk, inv_sqrt_s, o->sketch_dtype, SA, ld_sa, st);
+    return ski_gather_csr(A, b, bk, inv_sqrt_s, o->sketch_dtype, SA, ld_sa, st);
+  }
+  const int32_t pdt = o->sketch_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
+  const int64_t ldy = ski_round_up(ncols, 32);
+  void* Y = ar.take<char>(dtype_size(pdt) * rows * ldy);
+  const size_t pwb = ski_premix_ws_bytes(A->n, ncols, rows, pdt);
+  char* pws = ar.take<char>(pwb);
+  if (!ar.ok() || !pws) return SKI_ENOMEM;
+  SkiArena par{pws, pwb, 0, false};
+  double resid = 1.0;
+  SKI_TRY(ski_premix_run(A->val, A->ld, A->n, A->d, b, o->seed, rows, pdt, Y, ldy, par, st, &resid));
+  if (e_pm) SKI_CUDA_TRY(cudaEventRecord(e_pm, st));
+  const double scale = resid * inv_sqrt_s;
+  if (pdt == SKI_F64)
+    return ski_gather_dense((const double*)Y, ldy, rows, ncols, nullptr, bk, scale, SKI_F64, SA, ld_sa, st);
+  return ski_gather_dense_f32in((const float*)Y, ldy, ncols, bk, scale, o->sketch_dtype, SA, ld_sa, st);
+}
+
+extern "C" size_t ski_sketch_workspace_size(const ski_matrix* A, int32_t with_b, const ski_opts* o) {
+  if (check_matrix(A) != SKI_OK || check_sketch_opts(A, o) != SKI_OK) return 0;
+  return sketch_scratch_bytes(A, with_b, o, nullptr);
+}
+
+extern "C" ski_status ski_sketch_hash(const ski_matrix* A, const double* b, const ski_opts* o, void* SA,
+                                      int64_t ld_sa, void* ws, size_t ws_bytes, void* stream) {
+  SKI_TRY(check_matrix(A));
+  SKI_TRY(check_sketch_opts(A, o));
+  if (!SA || ld_sa < A->d + (b ? 1 : 0)) return SKI_EINVAL;
+  const size_t need = sketch_scratch_bytes(A, b != nullptr, o, nullptr);
+  if (ws_bytes < need || (!ws && need)) return SKI_ENOMEM;
+  return sketch_run(A, b, o, SA, ld_sa, (char*)ws, ws_bytes, ski_stream(stream));
+}
+
+extern "C" size_t ski_premix_workspace_size(const ski_matrix* A, int32_t with_b, const ski_opts* o) {
+  if (check_matrix(A) != SKI_OK || !o || A->kind != SKI_DENSE) return 0;
+  const int64_t rows = o->n_pad ? o->n_pad : next_pow2(A->n);
+  const int32_t pdt = o->sketch_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
+  return ski_premix_ws_bytes(A->n, A->d + (with_b ? 1 : 0), rows, pdt);
+}
+
+extern "C" ski_status ski_premix(const ski_matrix* A, const double* b, const ski_opts* o, void* Y, int64_t ld_y,
+                                 void* ws, size_t ws_bytes, void* stream) {
+  SKI_TRY(check_matrix(A));
+  if (!o || A->kind != SKI_DENSE || !Y) return SKI_EINVAL;
+  if (o->sketch_dtype != SKI_F64 && o->sketch_dtype != SKI_F32) return SKI_EINVAL;
+  const int64_t rows = o->n_pad ? o->n_pad : next_pow2(A->n);
+  if (!pow2(rows) || rows < A->n) return SKI_EINVAL;
+  const int64_t ncols = A->d + (b ? 1 : 0);
+  if (ld_y < ncols) return SKI_EINVAL;
+  const size_t need = ski_premix_ws_bytes(A->n, ncols, rows, o->sketch_dtype);
+  if (ws_bytes < need || !ws) return SKI_ENOMEM;
+  SkiArena ar{(char*)ws, ws_bytes, 0, false};
+  double resid;
+  cudaStream_t st = ski_stream(stream);
+  SKI_TRY(ski_premix_run(A->val, A->ld, A->n, A->d, b, o->seed, rows, o->sketch_dtype, Y, ld_y, ar, st, &resid));
+  if (resid != 1.0) {  // odd log2(n_pad): the last factor 2^{-1/2} of n_pad^{-1/2}
+    if (o->sketch_dtype == SKI_F64) return ski_scale_launch(rows, ncols, (double*)Y, ld_y, resid, st);
+    return ski_scale_f32_launch(rows, ncols, (float*)Y, ld_y, (float)resid, st);
+  }
+  return SKI_OK;
+}
+
+// ------------------------------------------------------------ QR stage
+extern "C" size_t ski_precondition_workspace_size(int64_t m, int64_t d, int32_t with_rhs, int32_t sa_dtype) {
+  if (m < d || d < 1) return 0;
+  return ski_qr_ws_bytes(m, d + (with_rhs ? 1 : 0), sa_dtype);
+}
+
+static ski_status rank_from_diag(int64_t d, const double* R, int64_t ldr, double rcond, cudaStream_t st, int32_t* rank,
+                                 bool* nonfinite) {
+  std::vector<double> diag(d);
+  // strided gather of the diagonal: d small copies would be slow; copy rows' diagonal via 2D memcpy
+  SKI_CUDA_TRY(cudaMemcpy2DAsync(diag.data(), sizeof(double), R, (ldr + 1) * sizeof(double), sizeof(double), d,
+                                 cudaMemcpyDeviceToHost, st));
+  SKI_CUDA_TRY(cudaStreamSynchronize(st));
+  *nonfinite = false;
+  int32_t p = 0;
+  const double r11 = fabs(diag[0]);
+  for (int64_t q = 0; q < d; ++q) {
+    if (!isfinite(diag[q])) *nonfinite = true;
+  }
+  if (r11 > 0) {
+    while (p < d && fabs(diag[p]) >= rcond * r11) ++p;
+  }
+  *rank = p;
+  return SKI_OK;
+}
+
+extern "C" ski_status ski_precondition(int64_t m, int64_t d, int32_t with_rhs, void* SA, int64_t ld_sa,
+                                       int32_t sa_dtype, double* R, int64_t ldr, double* qtsb, int32_t* rank,
+                                       const ski_opts* o, void* ws, size_t ws_bytes, void* stream) {
+  if (d < 1 || m < d || !SA || !R || ldr < d || ld_sa < d + (with_rhs ? 1 : 0)) return SKI_EINVAL;
+  if (sa_dtype != SKI_F64 && sa_dtype != SKI_F32) return SKI_EINVAL;
+  const size_t need = ski_qr_ws_bytes(m, d + (with_rhs ? 1 : 0), sa_dtype);
+  if (ws_bytes < need || !ws) return SKI_ENOMEM;
+  cudaStream_t st = ski_stream(stream);
+  SkiArena ar{(char*)ws, ws_bytes, 0, false};
+  SKI_TRY(ski_qr_run(m, d, with_rhs, SA, ld_sa, sa_dtype, R, ldr, with_rhs ? qtsb : nullptr, ar, st));
+  if (rank) {
+    bool nf;
+    SKI_TRY(rank_from_diag(d, R, ldr, o ? o->rcond : 1e-12, st, rank, &nf));
+    if (nf) return SKI_ENONFINITE;
+  }
+  return SKI_OK;
+}
+
+extern "C" size_t ski_trinv_workspace_size(int64_t d, int32_t dtype) {
+  if (d < 1) return 0;
+  return ski_trinv_ws_bytes(d, dtype);
+}
+
+extern "C" ski_status ski_trinv(int64_t d, const double* R, int64_t ldr, double* M, double* Mt, int64_t ldm,
+                                int32_t dtype, double perturb, void* ws, size_t ws_bytes, void* stream) {
+  if (d < 1 || !R || !M || ldr < d || ldm < d) return SKI_EINVAL;
+  if (dtype != SKI_F64 && dtype != SKI_F32) return SKI_EINVAL;
+  const size_t need = ski_trinv_ws_bytes(d, dtype);
+  if (ws_bytes < need || !ws) return SKI_ENOMEM;
+  SkiArena ar{(char*)ws, ws_bytes, 0, false};
+  return ski_trinv_run(d, R, ldr, M, Mt, ldm, dtype, perturb, ar, ski_stream(stream));
+}
+
+// ------------------------------------------------------------ solve
+namespace {
+
+struct SolvePlan {
+  int64_t n, d, m, ncols, ld_sa, ldq_sa;
+  int32_t qr_dt;
+  int nblk;
+  bool csr;
+  // persistent
+  double *R, *qtsb, *M, *Mt, *xs, *t, *v, *w, *y, *z, *p, *q, *part, *part_tt, *part_aa;
+  LsqrScalars* sc;
+  int64_t *colptr;
+  int32_t* rowidx;
+  double* cval;
+  // phase region
+  char* region;
+  size_t region_bytes;
+  void* SA;
+  void* SAq;  // QR input (SA itself, or an FP32 copy of a BF16 sketch)
+  char* stage;
+  size_t stage_bytes;
+  char* csc_tmp;
+  size_t csc_tmp_bytes;
+};
+
+size_t plan_solve(const ski_matrix* A, const ski_opts* o, char* base, size_t cap, SolvePlan* P) {
+  SkiArena ar{base, cap, 0, base == nullptr};
+  const int64_t n = A->n, d = A->d, m = o->m, ncols = d + 1;
+  P->n = n;
+  P->d = d;
+  P->m = m;
+  P->ncols = ncols;
+  P->csr = A->kind == SKI_CSR;
+  P->qr_dt = o->qr_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
+  P->ld_sa = ski_round_up(ncols, 4);
+  P->nblk = ski_fused_ctas(n);
+  P->R = ar.take<double>(d * d);
+  P->qtsb = ar.take<double>(d);
+  P->M = ar.take<double>(d * d);
+  P->Mt = ar.take<double>(d * d);
+  P->xs = ar.take<double>(d);
+  P->t = ar.take<double>(n);
+  P->v = ar.take<double>(d);
+  P->w = ar.take<double>(d);
+  P->y = ar.take<double>(d);
+  P->z = ar.take<double>(d);
+  P->p = ar.take<double>(d);
+  P->q = ar.take<double>(d);
+  P->part = ar.take<double>((int64_t)P->nblk * d);
+  P->part_tt = ar.take<double>(P->nblk);
+  P->part_aa = ar.take<double>(P->nblk);
+  P->sc = ar.take<LsqrScalars>(1);
+  if (P->csr) {
+    P->colptr = ar.take<int64_t>(d + 1);
+    P->rowidx = ar.take<int32_t>(A->nnz);
+    P->cval = ar.take<double>(A->nnz);
+  } else {
+    P->colptr = nullptr;
+    P->rowidx = nullptr;
+    P->cval = nullptr;
+  }
+  // phase region: max(SA [+ QR copy] + max(sketch scratch, QR ws), trinv ws, csc tmp)
+  const size_t sa_bytes = ski_round_up((int64_t)(dtype_size(o->sketch_dtype) * m * P->ld_sa), 256);
+  const bool copy_q = dtype_size(o->sketch_dtype) != dtype_size(P->qr_dt) || o->sketch_dtype == SKI_BF16;
+  const size_t saq_bytes = copy_q ? ski_round_up((int64_t)(dtype_size(P->qr_dt) * m * P->ld_sa), 256) : 0;
+  const size_t sk = sketch_scratch_bytes(A, 1, o, nullptr);
+  const size_t qrw = ski_qr_ws_bytes(m, ncols, P->qr_dt);
+  const size_t stage = std::max(sk, qrw);
+  const size_t ph1 = sa_bytes + saq_bytes + stage;
+  const size_t tiw = ski_trinv_ws_bytes(d, P->qr_dt);
+  const size_t cscw = P->csr ? ski_csc_ws_bytes(n, d, A->nnz) : 0;
+  P->region_bytes = std::max(ph1, std::max(tiw, cscw));
+  P->region = ar.take<char>(P->region_bytes);
+  if (P->region) {
+    P->SA = P->region;
+    P->SAq = copy_q ? (void*)(P->region + sa_bytes) : P->SA;
+    P->stage = P->region + sa_bytes + saq_bytes;
+    P->stage_bytes = stage;
+    P->csc_tmp = P->region;
+    P->csc_tmp_bytes = cscw;
+  }
+  return ar.off;
+}
+
+template <class TI, class TO>
+__global__ void k_convert(int64_t count, const TI* __restrict__ a, TO* __restrict__ b) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < count) b[i] = SkiType<TO>::from(SkiType<TI>::to_f64(a[i]));
+}
+
+struct Events {
+  cudaEvent_t e[8];
+  bool ok;
+  Events() : ok(true) {
+    for (auto& x : e) {
+      if (cudaEventCreate(&x) != cudaSuccess) ok = false;
+    }
+  }
+  ~Events() {
+    for (auto& x : e) cudaEventDestroy(x);
+  }
+  float ms(int a, int b) {
+    float v = 0.f;
+    if (cudaEventElapsedTime(&v, e[a], e[b]) != cudaSuccess) return 0.f;
+    return v;
+  }
+};
+
+// r = b - A x (into P.t), q = A^T r, ||r||^2 (and ||A||_F^2 when want_aa) into scalars.
+ski_status residual_pass(const ski_matrix* A, const double* b, const double* x, SolvePlan& P, bool want_aa,
+                         cudaStream_t st) {
+  FusedArgs f{};
+  f.A = A->kind == SKI_DENSE ? A->val : nullptr;
+  f.lda = A->ld;
+  f.rowptr = A->kind == SKI_CSR ? A->rowptr : nullptr;
+  f.colidx = A->colidx;
+  f.val = A->val;
+  f.n = P.n;
+  f.d = P.d;
+  f.z = x;
+  f.u = nullptr;
+  f.b = b;
+  f.ca = -1.0;
+  f.cu = 0.0;
+  f.cb = 1.0;
+  f.coef_from_scalars = 0;
+  f.t = P.t;
+  f.part = P.part;
+  f.ldp = P.d;
+  f.part_tt = P.part_tt;
+  f.part_aa = P.part_aa;
+  f.want_aa = want_aa ? 1 : 0;
+  f.nblk = P.nblk;
+  f.sc = nullptr;
+  SKI_TRY(ski_fused_launch(f, st));
+  if (P.csr) {
+    SKI_TRY(ski_csc_launch(P.d, P.colptr, P.rowidx, P.cval, P.t, P.q, nullptr, st));
+    SKI_TRY(ski_reduce_launch(P.nblk, P.d, nullptr, P.d, P.part_tt, want_aa ? P.part_aa : nullptr, P.q, P.sc, 2, st));
+  } else {
+    SKI_TRY(ski_reduce_launch(P.nblk, P.d, P.part, P.d, P.part_tt, want_aa ? P.part_aa : nullptr, P.q, P.sc, 2, st));
+  }
+  return SKI_OK;
+}
+
+ski_status lsqr_iteration(const ski_matrix* A, SolvePlan& P, cudaStream_t st) {
+  SKI_TRY(ski_trmv_launch(true, P.d, P.M, P.d, P.v, nullptr, P.z, P.sc, st));
+  FusedArgs f{};
+  f.A = A->kind == SKI_DENSE ? A->val : nullptr;
+  f.lda = A->ld;
+  f.rowptr = A->kind == SKI_CSR ? A->rowptr : nullptr;
+  f.colidx = A->colidx;
+  f.val = A->val;
+  f.n = P.n;
+  f.d = P.d;
+  f.z = P.z;
+  f.u = P.t;
+  f.b = nullptr;
+  f.coef_from_scalars = 1;
+  f.t = P.t;
+  f.part = P.part;
+  f.ldp = P.d;
+  f.part_tt = P.part_tt;
+  f.part_aa = nullptr;
+  f.want_aa = 0;
+  f.nblk = P.nblk;
+  f.sc = P.sc;
+  SKI_TRY(ski_fused_launch(f, st));
+  if (P.csr) {
+    SKI_TRY(ski_csc_launch(P.d, P.colptr, P.rowidx, P.cval, P.t, P.q, P.sc, st));
+    SKI_TRY(ski_reduce_launch(P.nblk, P.d, nullptr, P.d, P.part_tt, nullptr, P.q, P.sc, 0, st));
+  } else {
+    SKI_TRY(ski_reduce_launch(P.nblk, P.d, P.part, P.d, P.part_tt, nullptr, P.q, P.sc, 0, st));
+  }
+  SKI_TRY(ski_trmv_launch(false, P.d, P.Mt, P.d, P.q, nullptr, P.p, P.sc, st));
+  SKI_TRY(ski_update_launch(P.d, P.p, P.v, P.w, P.y, P.sc, 0, st));
+  return SKI_OK;
+}
+
+ski_status read_scalars(const SolvePlan& P, LsqrScalars* h, cudaStream_t st) {
+  SKI_CUDA_TRY(cudaMemcpyAsync(h, P.sc, sizeof(LsqrScalars), cudaMemcpyDeviceToHost, st));
+  SKI_CUDA_TRY(cudaStreamSynchronize(st));
+  return SKI_OK;
+}
+
+}  // namespace
+
+extern "C" size_t ski_solve_workspace_size(const ski_matrix* A, const ski_opts* o) {
+  if (check_matrix(A) != SKI_OK || check_sketch_opts(A, o) != SKI_OK) return 0;
+  SolvePlan P;
+  return plan_solve(A, o, nullptr, 0, &P);
+}
+
+extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_opts* o, double* x, double* R_out,
+                                ski_info* info, void* ws, size_t ws_bytes, void* stream) {
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->status = SKI_EINVAL;
+  }
+  SKI_TRY(check_matrix(A));
+  SKI_TRY(check_sketch_opts(A, o));
+  if (!b || !x) return SKI_EINVAL;
+  if (o->m < A->d || A->n < A->d) return SKI_EINVAL;
+  if (o->qr_dtype != SKI_F64 && o->qr_dtype != SKI_F32) return SKI_EINVAL;
+  if (A->kind == SKI_DENSE && A->d > SKI_DENSE_DMAX) return SKI_EINVAL;
+  if (o->it_max < 0) return SKI_EINVAL;
+  SolvePlan P;
+  const size_t need = plan_solve(A, o, nullptr, 0, &P);
+  if (ws_bytes < need || !ws) {
+    if (info) info->status = SKI_ENOMEM;
+    return SKI_ENOMEM;
+  }
+  plan_solve(A, o, (char*)ws, ws_bytes, &P);
+  cudaStream_t st = ski_stream(stream);
+  Events ev;
+  if (!ev.ok) return SKI_ECUDA;
+  const int64_t d = P.d;
+  ski_status result = SKI_OK;
+  LsqrScalars hs;
+  memset(&hs, 0, sizeof(hs));
+  hs.tau_r = o->tau_r;
+  hs.it_max = o->it_max;
+
+  SKI_CUDA_TRY(cudaEventRecord(ev.e[0], st));
+  // Step 1: sketch [SA | Sb]
+  SKI_TRY(sketch_run(A, b, o, P.SA, P.ld_sa, P.stage, P.stage_bytes, st, ev.e[5], ev.e[6]));
+  SKI_CUDA_TRY(cudaEventRecord(ev.e[1], st));
+  // Step 2: QR of [SA | Sb] in qr_dtype
+  if (P.SAq != P.SA) {
+    const int64_t cnt = P.m * P.ld_sa;
+    const unsigned g = (unsigned)ski_cdiv(cnt, 256);
+    if (o->sketch_dtype == SKI_BF16)
+      k_convert<__nv_bfloat16, float><<<g, 256, 0, st>>>(cnt, (const __nv_bfloat16*)P.SA, (float*)P.SAq);
+    else if (o->sketch_dtype == SKI_F32)
+      k_convert<float, double><<<g, 256, 0, st>>>(cnt, (const float*)P.SA, (double*)P.SAq);
+    else
+      k_convert<double, float><<<g, 256, 0, st>>>(cnt, (const double*)P.SA, (float*)P.SAq);
+    SKI_LAUNCH_CHECK();
+  }
+  {
+    SkiArena qar{P.stage, P.stage_bytes, 0, false};
+    SKI_TRY(ski_qr_run(P.m, d, 1, P.SAq, P.ld_sa, P.qr_dt, P.R, d, P.qtsb, qar, st));
+  }
+  SKI_CUDA_TRY(cudaEventRecord(ev.e[2], st));
+  int32_t rank = 0;
+  bool nonfinite = false;
+  SKI_TRY(rank_from_diag(d, P.R, d, o->rcond, st, &rank, &nonfinite));
+  if (info) info->rank = rank;
+  if (nonfinite) {
+    if (info) info->status = SKI_ENONFINITE;
+    return SKI_ENONFINITE;
+  }
+  if (rank < d && o->perturb <= 0.0) {
+    if (info) info->status = SKI_ESINGULAR;
+    return SKI_ESINGULAR;
+  }
+  if (R_out) SKI_CUDA_TRY(cudaMemcpyAsync(R_out, P.R, d * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // R^{-1} (explicit, and its transpose)
+  {
+    SkiArena tar{P.region, P.region_bytes, 0, false};
+    SKI_TRY(ski_trinv_run(d, P.R, d, P.M, P.Mt, d, P.qr_dt, rank < d ? o->perturb : 0.0, tar, st));
+  }
+  if (P.csr) {
+    SkiArena car{P.csc_tmp, P.region_bytes, 0, false};
+    SKI_TRY(ski_csc_build(A, P.colptr, P.rowidx, P.cval, car, st));
+  }
+  SKI_CUDA_TRY(cudaEventRecord(ev.e[3], st));
+  // Step 3: x_s = R^{-1} Q^T Sb and its residual
+  SKI_TRY(ski_trmv_launch(true, d, P.M, d, P.qtsb, nullptr, P.xs, nullptr, st));
+  SKI_CUDA_TRY(cudaMemcpyAsync(P.sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+  SKI_TRY(residual_pass(A, b, P.xs, P, true, st));
+  SKI_TRY(read_scalars(P, &hs, st));
+  const double anorm_f = sqrt(hs.anorm_f2);
+  if (!isfinite(hs.rnorm2) || !isfinite(hs.anorm_f2)) {
+    if (info) info->status = SKI_ENONFINITE;
+    return SKI_ENONFINITE;
+  }
+  int64_t iters_total = 0;
+  int restarts = 0;
+  double metric = 0.0, lsqr_test = 0.0;
+  bool early = false;
+  if (sqrt(hs.rnorm2) <= o->tau_a) {
+    early = true;
+    SKI_TRY(ski_copy_launch(d, P.xs, x, st));
+    SKI_TRY(ski_norm_launch(d, P.q, P.sc, st));
+    SKI_TRY(read_scalars(P, &hs, st));
+    metric = hs.rnorm2 > 0 ? hs.atr_norm / (anorm_f * sqrt(hs.rnorm2)) : 0.0;
+  } else {
+    // Step 4: LSQR from y_0 = Q^T Sb (x_s), restarted from the current x while
+    // the FP64 acceptance metric is above tol.
+    for (;;) {
+      // start: beta_1 u_1 = r (in P.t), alpha_1 v_1 = M^T A^T u_1
+      LsqrScalars init = hs;
+      init.iters = 0;
+      init.it_max = o->it_max - iters_total;
+      init.done = 0;
+      init.conv = 0;
+      init.tau_r = o->tau_r;
+      SKI_CUDA_TRY(cudaMemcpyAsync(P.sc, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+      SKI_TRY(ski_trmv_launch(false, d, P.Mt, d, P.q, nullptr, P.p, nullptr, st));
+      SKI_TRY(ski_update_launch(d, P.p, P.v, P.w, P.y, P.sc, 1, st));
+      const int CHUNK = 8;
+      int64_t polled = 0;
+      for (;;) {
+        for (int k = 0; k < CHUNK; ++k) SKI_TRY(lsqr_iteration(A, P, st));
+        polled += CHUNK;
+        SKI_TRY(read_scalars(P, &hs, st));
+        if (hs.done) break;
+        if (polled > o->it_max + CHUNK) break;
+      }
+      iters_total += hs.iters;
+      lsqr_test = hs.test;
+      // Step 5: x = x_s + R^{-1} delta
+      SKI_TRY(ski_trmv_launch(true, d, P.M, d, P.y, P.xs, x, nullptr, st));
+      SKI_TRY(residual_pass(A, b, x, P, false, st));
+      SKI_TRY(ski_norm_launch(d, P.q, P.sc, st));
+      SKI_TRY(read_scalars(P, &hs, st));
+      if (!isfinite(hs.rnorm2) || !isfinite(hs.atr_norm)) {
+        result = SKI_ENONFINITE;
+        break;
+      }
+      metric = hs.rnorm2 > 0 ? hs.atr_norm / (anorm_f * sqrt(hs.rnorm2)) : 0.0;
+      const bool lsqr_ok = hs.conv != 0;
+      if (o->tol > 0.0 ? metric <= o->tol : lsqr_ok) break;
+      if (iters_total >= o->it_max || restarts >= 8) {
+        result = SKI_ENOCONV;
+        break;
+      }
+      ++restarts;
+      SKI_TRY(ski_copy_launch(d, x, P.xs, st));  // warm restart from x; P.t = r, P.q = A^T r
+    }
+  }
+  SKI_CUDA_TRY(cudaEventRecord(ev.e[4], st));
+  SKI_CUDA_TRY(cudaEventSynchronize(ev.e[4]));
+  if (info) {
+    info->iters = iters_total;
+    info->restarts = restarts;
+    info->early_exit = early ? 1 : 0;
+    info->metric = metric;
+    info->resid_norm = sqrt(hs.rnorm2);
+    info->anorm_f = anorm_f;
+    info->lsqr_test = lsqr_test;
+    info->ms_sketch = ev.ms(0, 1);
+    info->ms_qr = ev.ms(1, 2);
+    info->ms_trinv = ev.ms(2, 3);
+    info->ms_lsqr = ev.ms(3, 4);
+    info->ms_total = ev.ms(0, 4);
+    info->ms_premix = ev.ms(5, 6);
+    info->ms_gather = ev.ms(6, 1);
+    info->status = result;
+  }
+  return result;
+}
+
+// ------------------------------------------------------------ batched
+static void batched_opts(const ski_opts* o, const ski_matrix* A, int32_t i, ski_opts* oi) {
+  *oi = *o;
+  if (o->m <= 0) {
+    const double gamma = (o->m < 0 ? -(double)o->m : 2000.0) / 1000.0;
+    oi->m = (int64_t)ceil(gamma * (double)A->d);
+    if (oi->m < A->d) oi->m = A->d;
+  }
+  oi->seed = o->seed + (uint64_t)i;
+}
+
+extern "C" size_t ski_solve_batched_workspace_size(int32_t nprob, const ski_matrix* A, const ski_opts* o) {
+  if (nprob < 0 || (nprob > 0 && (!A || !o))) return 0;
+  size_t mx = 0;
+  for (int32_t i = 0; i < nprob; ++i) {
+    ski_opts oi;
+    batched_opts(o, &A[i], i, &oi);
+    mx = std::max(mx, ski_solve_workspace_size(&A[i], &oi));
+  }
+  return mx;
+}
+
+extern "C" ski_status ski_solve_batched(int32_t nprob, const ski_matrix* A, const double* const* b, const ski_opts* o,
+                                        double* const* x, double* const* R_out, ski_info* info, void* ws,
+                                        size_t ws_bytes, void* stream) {
+  if (nprob < 0 || (nprob > 0 && (!A || !b || !x || !o))) return SKI_EINVAL;
+  ski_status first = SKI_OK;
+  for (int32_t i = 0; i < nprob; ++i) {
+    ski_opts oi;
+    batched_opts(o, &A[i], i, &oi);
+    ski_status s = ski_solve(&A[i], b[i], &oi, x[i], R_out ? R_out[i] : nullptr, info ? &info[i] : nullptr, ws,
+                             ws_bytes, stream);
+    if (s != SKI_OK && first == SKI_OK) first = s;
+    if (s == SKI_ECUDA) return s;
+  }
+  return first;
+}
+
+// ------------------------------------------------------------ adjoint
+namespace {
+struct AdjPlan {
+  double *M, *Mt, *t, *al, *h, *r, *p, *z, *zz, *q, *lam, *part, *part_tt;
+  LsqrScalars* sc;
+  char* tw;
+  size_t tw_bytes;
+  int nblk;
+};
+size_t plan_adjoint(const ski_matrix* A, char* base, size_t cap, AdjPlan* P) {
+  SkiArena ar{base, cap, 0, base == nullptr};
+  const int64_t n = A->n, d = A->d;
+  P->nblk = ski_fused_ctas(n);
+  P->M = ar.take<double>(d * d);
+  P->Mt = ar.take<double>(d * d);
+  P->t = ar.take<double>(n);
+  P->al = ar.take<double>(n);
+  P->h = ar.take<double>(d);
+  P->r = ar.take<double>(d);
+  P->p = ar.take<double>(d);
+  P->z = ar.take<double>(d);
+  P->zz = ar.take<double>(d);
+  P->q = ar.take<double>(d);
+  P->lam = ar.take<double>(d);
+  P->part = ar.take<double>((int64_t)P->nblk * d);
+  P->part_tt = ar.take<double>(P->nblk);
+  P->sc = ar.take<LsqrScalars>(1);
+  P->tw_bytes = ski_trinv_ws_bytes(d, SKI_F64);
+  P->tw = ar.take<char>(P->tw_bytes);
+  return ar.off;
+}
+
+FusedArgs dense_pass(const ski_matrix* A, const AdjPlan& P, const double* z, double ca, const double* bvec,
+                     double cb, double* t, const LsqrScalars* sc) {
+  FusedArgs f{};
+  f.A = A->val;
+  f.lda = A->ld;
+  f.n = A->n;
+  f.d = A->d;
+  f.z = z;
+  f.b = bvec;
+  f.ca = ca;
+  f.cb = cb;
+  f.t = t;
+  f.part = P.part;
+  f.ldp = A->d;
+  f.part_tt = P.part_tt;
+  f.nblk = P.nblk;
+  f.sc = sc;
+  return f;
+}
+}  // namespace
+
+extern "C" size_t ski_solve_adjoint_workspace_size(const ski_matrix* A, const ski_opts* o) {
+  (void)o;
+  if (check_matrix(A) != SKI_OK || A->kind != SKI_DENSE) return 0;
+  AdjPlan P;
+  return plan_adjoint(A, nullptr, 0, &P);
+}
+
+extern "C" ski_status ski_solve_adjoint(const ski_matrix* A, const double* b, const double* x, const double* R,
+                                        int64_t ldr, const double* g, double* dA, int64_t ld_da, double* db,
+                                        const ski_opts* o, ski_info* info, void* ws, size_t ws_bytes, void* stream) {
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->status = SKI_EINVAL;
+  }
+  SKI_TRY(check_matrix(A));
+  if (A->kind != SKI_DENSE || A->d > SKI_DENSE_DMAX || !o || !b || !x || !R || !g || !db || ldr < A->d)
+    return SKI_EINVAL;
+  if (dA && ld_da < A->d) return SKI_EINVAL;
+  AdjPlan P;
+  const size_t need = plan_adjoint(A, nullptr, 0, &P);
+  if (ws_bytes < need || !ws) return SKI_ENOMEM;
+  plan_adjoint(A, (char*)ws, ws_bytes, &P);
+  cudaStream_t st = ski_stream(stream);
+  const int64_t d = A->d, n = A->n;
+  {
+    SkiArena tar{P.tw, P.tw_bytes, 0, false};
+    SKI_TRY(ski_trinv_run(d, R, ldr, P.M, P.Mt, d, SKI_F64, 0.0, tar, st));
+  }
+  // h = R^{-T} g; CG on W^T W z = h
+  SKI_TRY(ski_trmv_launch(false, d, P.Mt, d, g, nullptr, P.h, nullptr, st));
+  LsqrScalars hs;
+  memset(&hs, 0, sizeof(hs));
+  hs.it_max = o->it_max > 0 ? o->it_max : 1000;
+  hs.cg_tol2 = o->tau_r * o->tau_r;
+  SKI_CUDA_TRY(cudaMemcpyAsync(P.sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+  SKI_TRY(ski_cg_launch(d, P.h, P.r, P.p, P.z, P.sc, 1, st));
+  int64_t polled = 0;
+  for (;;) {
+    for (int k = 0; k < 8; ++k) {
+      SKI_TRY(ski_trmv_launch(true, d, P.M, d, P.p, nullptr, P.zz, P.sc, st));
+      SKI_TRY(ski_fused_launch(dense_pass(A, P, P.zz, 1.0, nullptr, 0.0, P.t, P.sc), st));
+      SKI_TRY(ski_reduce_launch(P.nblk, d, P.part, d, P.part_tt, nullptr, P.q, P.sc, 0, st));
+      SKI_TRY(ski_trmv_launch(false, d, P.Mt, d, P.q, nullptr, P.zz, P.sc, st));
+      SKI_TRY(ski_cg_launch(d, P.zz, P.r, P.p, P.z, P.sc, 0, st));
+    }
+    SKI_CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    SKI_CUDA_TRY(cudaStreamSynchronize(st));
+    polled += 8;
+    if (hs.done || polled > hs.it_max + 16) break;
+  }
+  // lambda = R^{-1} z; db = A lambda; r = b - A x; dA = r lambda^T - (A lambda) x^T
+  SKI_TRY(ski_trmv_launch(true, d, P.M, d, P.z, nullptr, P.lam, nullptr, st));
+  SKI_TRY(ski_fused_launch(dense_pass(A, P, P.lam, 1.0, nullptr, 0.0, db, nullptr), st));
+  if (dA) {
+    SKI_TRY(ski_fused_launch(dense_pass(A, P, x, -1.0, b, 1.0, P.t, nullptr), st));
+    SKI_TRY(ski_outer_launch(n, d, P.t, P.lam, db, x, dA, ld_da, st));
+  }
+  SKI_CUDA_TRY(cudaStreamSynchronize(st));
+  const ski_status res = hs.conv ? SKI_OK : SKI_ENOCONV;
+  if (info) {
+    info->iters = hs.iters;
+    info->status = res;
+    info->lsqr_test = hs.cg_rr0 > 0 ? sqrt(hs.cg_rr / hs.cg_rr0) : 0.0;
+  }
+  return res;
+}

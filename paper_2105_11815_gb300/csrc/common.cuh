@@ -1,0 +1,152 @@
+// Shared helpers of the Ski-LLS CUDA library: status handling, workspace
+// carving, warp reductions and the exact int64 block-fixed-point arithmetic
+// that replaces FP64 adds on GB300 (whose FP64 pipe runs at 1/64 of FP32).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <algorithm>
+#include "../../include/skills.h"
+
+#define SKI_CUDA_TRY(expr)                                   \
+  do {                                                       \
+    cudaError_t e_ = (expr);                                 \
+    if (e_ != cudaSuccess) { ski_note_cuda_error(e_); return SKI_ECUDA; } \
+  } while (0)
+
+#define SKI_TRY(expr)                                        \
+  do {                                                       \
+    ski_status s_ = (expr);                                  \
+    if (s_ != SKI_OK) return s_;                             \
+  } while (0)
+
+// Every kernel launch of the library is followed by exactly one
+// SKI_LAUNCH_CHECK, which also counts it (ski_launch_count()).
+#define SKI_LAUNCH_CHECK()               \
+  do {                                   \
+    ski_count_launch();                  \
+    SKI_CUDA_TRY(cudaGetLastError());    \
+  } while (0)
+
+void ski_note_cuda_error(cudaError_t e);
+void ski_count_launch();
+
+static inline cudaStream_t ski_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static inline int64_t ski_cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+static inline int64_t ski_round_up(int64_t a, int64_t b) { return ski_cdiv(a, b) * b; }
+
+// Bump allocator over the caller workspace.  Every carve is 256-byte aligned.
+struct SkiArena {
+  char* base;
+  size_t cap;
+  size_t off;
+  bool dry;  // size query only
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = ski_round_up((int64_t)(count * sizeof(T)), 256);
+    size_t o = off;
+    off += bytes;
+    if (dry || off > cap) return nullptr;
+    return reinterpret_cast<T*>(base + o);
+  }
+  bool ok() const { return dry || off <= cap; }
+};
+
+// ----------------------------------------------------------------- device
+__device__ __forceinline__ double ski_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float ski_warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class T> struct SkiType;
+template <> struct SkiType<double> {
+  static constexpr int id = SKI_F64;
+  __device__ __forceinline__ static double from(double v) { return v; }
+  __device__ __forceinline__ static double to_f64(double v) { return v; }
+};
+template <> struct SkiType<float> {
+  static constexpr int id = SKI_F32;
+  __device__ __forceinline__ static float from(double v) { return (float)v; }
+  __device__ __forceinline__ static double to_f64(float v) { return (double)v; }
+};
+template <> struct SkiType<__nv_bfloat16> {
+  static constexpr int id = SKI_BF16;
+  __device__ __forceinline__ static __nv_bfloat16 from(double v) { return __float2bfloat16((float)v); }
+  __device__ __forceinline__ static double to_f64(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+};
+
+// ------------------------------------------- int64 block fixed point (FP64)
+// A double v = (-1)^s * M * 2^(e - 1075) with M the 53-bit significand
+// (implicit bit included; e the biased exponent field, subnormals use e = 1).
+// Values that share a block exponent E are summed exactly as integers
+// q = (M << FX_LIFT) >> (E - e): only bits below 2^(E - 1075 - FX_LIFT) are
+// dropped, i.e. each term is truncated by less than 2^-54 of the largest one,
+// and the integer sum itself is exact and order-independent.  The result is
+// as accurate as FP64 additions, deterministic, and runs on the INT32 pipe
+// (128 lanes/SM) instead of GB300's FP64 pipe (2 DFMA/clk/SM).
+#define FX_LIFT 2
+
+__device__ __forceinline__ int fx_exp(double v) {
+  int e = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+  return e == 0 ? 1 : e;
+}
+
+// q(v) relative to block exponent E >= fx_exp(v); sign applied; neg flips.
+__device__ __forceinline__ long long fx_quant(double v, int E, bool neg) {
+  unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  int e = (int)((bits >> 52) & 0x7FF);
+  unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+  int sh = E - (e ? e : 1);
+  unsigned long long q = sh > 63 ? 0ull : ((M << FX_LIFT) >> sh);
+  bool negative = ((bits >> 63) != 0) != neg;
+  return negative ? -(long long)q : (long long)q;
+}
+
+// The double nearest to S * 2^(E - 1075 - FX_LIFT - extra).
+__device__ __forceinline__ double fx_to_double(long long S, int E, int extra = 0) {
+  if (S == 0) return 0.0;
+  double v = __ll2double_rn(S);  // exact up to one rounding
+  long long bits = __double_as_longlong(v);
+  int e = (int)((bits >> 52) & 0x7FF);
+  int ne = e + (E - 1075 - FX_LIFT - extra);
+  if (ne >= 1 && ne <= 2046) {
+    bits = (bits & ~(0x7FFll << 52)) | ((long long)ne << 52);
+    return __longlong_as_double(bits);
+  }
+  return ldexp(v, E - 1075 - FX_LIFT - extra);  // out of the normal range: rare
+}
+
+// Running exact sum with an adaptive block exponent: a larger addend raises
+// the exponent and truncates the running sum's low bits once.
+// Every addend is below 2^(53 + FX_LIFT) = 2^55 in units of the block; the
+// block is coarsened by 2^6 whenever |S| has reached 2^61 before an add, so
+// |S| < 2^62 for any number of addends.  NaN/Inf make value() NaN.
+struct FxAcc {
+  long long S;
+  int E;
+  bool bad;
+  __device__ __forceinline__ void init() { S = 0; E = 1; bad = false; }
+  __device__ __forceinline__ void add(double v, bool neg) {
+    int e = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+    if (e == 0x7FF) { bad = true; return; }
+    e = e ? e : 1;
+    if (e > E) {
+      int sh = e - E;
+      S = sh > 63 ? (S < 0 ? -1 : 0) : (S >> sh);
+      E = e;
+    }
+    if (S >= (1ll << 61) || S <= -(1ll << 61)) { S >>= 6; E += 6; }
+    S += fx_quant(v, E, neg);
+  }
+  __device__ __forceinline__ double value(int extra = 0) const {
+    return bad ? __longlong_as_double(0x7FF8000000000000ll) : fx_to_double(S, E, extra);
+  }
+};

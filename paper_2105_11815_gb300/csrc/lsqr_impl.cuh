@@ -1,0 +1,65 @@
+// Device-resident LSQR state and launch helpers (lsqr.cu) used by the C ABI.
+#pragma once
+#include "common.cuh"
+
+// Largest d the dense fused pass handles (512 threads x 16 columns each).
+#define SKI_DENSE_DMAX 8192
+
+struct LsqrScalars {
+  double alpha, beta, beta_new, rhobar, phibar, anorm2, test, coef;
+  double tau_r;
+  double rnorm2, anorm_f2, atr_norm;
+  double cg_rr, cg_rr0, cg_tol2;  // conjugate gradients of the adjoint solve
+  long long iters, it_max;
+  int done, conv;
+};
+
+struct FusedArgs {
+  // dense A (row-major) or CSR A
+  const double* A;
+  int64_t lda;
+  const int64_t* rowptr;
+  const int32_t* colidx;
+  const double* val;
+  int64_t n, d;
+  // t = ca * (A z) + cu * u + cb * b ; coefficients from scalars when coef_from_scalars
+  const double* z;
+  const double* u;
+  const double* b;
+  double ca, cu, cb;
+  int coef_from_scalars;
+  double* t;
+  // per-CTA partials: A^T t (dense only), ||t||^2, ||A||_F^2
+  double* part;
+  int64_t ldp;
+  double* part_tt;
+  double* part_aa;
+  int want_aa;
+  int nblk;
+  int64_t rows_per;
+  const LsqrScalars* sc;
+};
+
+int ski_fused_ctas(int64_t n);
+ski_status ski_fused_launch(const FusedArgs& f, cudaStream_t st);
+ski_status ski_trmv_launch(bool upper, int64_t d, const double* M, int64_t ldm, const double* x, const double* add,
+                           double* y, const LsqrScalars* sc, cudaStream_t st);
+ski_status ski_csc_launch(int64_t d, const int64_t* colptr, const int32_t* rowidx, const double* cval,
+                          const double* t, double* q, const LsqrScalars* sc, cudaStream_t st);
+ski_status ski_reduce_launch(int nblk, int64_t d, const double* part, int64_t ldp, const double* part_tt,
+                             const double* part_aa, double* q, LsqrScalars* sc, int mode, cudaStream_t st);
+ski_status ski_update_launch(int64_t d, const double* p, double* v, double* w, double* y, LsqrScalars* sc, int start,
+                             cudaStream_t st);
+ski_status ski_norm_launch(int64_t d, const double* q, LsqrScalars* sc, cudaStream_t st);
+ski_status ski_copy_launch(int64_t n, const double* a, double* b, cudaStream_t st);
+ski_status ski_cg_launch(int64_t d, const double* q, double* r, double* p, double* z, LsqrScalars* sc, int start,
+                         cudaStream_t st);
+ski_status ski_outer_launch(int64_t n, int64_t d, const double* r, const double* lam, const double* al,
+                            const double* x, double* dA, int64_t ld_da, cudaStream_t st);
+ski_status ski_scale_launch(int64_t rows, int64_t cols, double* Y, int64_t ldy, double s, cudaStream_t st);
+ski_status ski_scale_f32_launch(int64_t rows, int64_t cols, float* Y, int64_t ldy, float s, cudaStream_t st);
+
+// csc.cu: deterministic CSR -> CSC transpose (row indices ascending per column).
+size_t ski_csc_ws_bytes(int64_t n, int64_t d, int64_t nnz);
+ski_status ski_csc_build(const ski_matrix* A, int64_t* colptr, int32_t* rowidx, double* cval, SkiArena& ar,
+                         cudaStream_t st);

@@ -1,0 +1,271 @@
+// Step 2 of Algorithm 1: Householder QR of the sketch SA (m x d, m >= d),
+// blocked in panels of NB = 32 columns (compact WY form, Schreiber & Van Loan).
+//
+// Panel: column j of the panel is reduced by one launch that (a) finalises
+// the reflector of column j-1 from the previous launch's partial sums --
+// beta = -sign(x0) ||x||, tau = (beta - x0) / beta, v = [1; x_rest / (x0 - beta)]
+// -- and applies it to the remaining panel columns, then (b) accumulates the
+// partial dot products of column j with the panel for the next launch.  Each
+// CTA owns a slab of rows; one warp handles one row, one lane one panel
+// column, so every access is a coalesced 256 B row segment and the only
+// cross-CTA exchange is the partials buffer between launches (no inter-CTA
+// waits).  Partial sums are combined in a fixed order (deterministic).
+//
+// Trailing update: C <- (I - V T V^T)^T C = C - V (T^T (V^T C)), with V the
+// explicit unit-lower-trapezoidal reflector block and T upper triangular
+// (forward accumulation: T_ii = tau_i, T[0:i, i] = -tau_i T[0:i,0:i] V[:,0:i]^T v_i).
+// V^T C is a split-K GEMM, C -= V (T^T W) a plain GEMM (gemm.cu).
+// Applying the reflectors to column d of [SA | Sb] yields Q^T Sb for Step 3.
+#include "common.cuh"
+#include "sketch_impl.cuh"
+
+namespace {
+
+constexpr int NB = 32;
+constexpr int PW = 2 * NB;  // partial slot: g[32] then the diagonal row[32]
+constexpr int WARPS = 8;
+
+template <class T>
+struct PanelArgs {
+  T* P;           // &B[k0, k0]
+  int64_t ld;
+  int64_t mr;     // rows of the panel (m - k0)
+  int w;          // panel width <= NB
+  int64_t rows_per;
+  int ncta;
+  const T* part_prev;
+  T* part_cur;
+  T* tau;
+  T* V;           // explicit reflectors, mr x NB, written by the last step
+};
+
+template <class T>
+__device__ __forceinline__ T sgn_nrm(T x0, T nrm) { return x0 >= T(0) ? -nrm : nrm; }
+
+template <class T>
+__global__ void __launch_bounds__(32 * WARPS) k_panel_step(PanelArgs<T> a, int s) {
+  __shared__ T red[WARPS][NB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = s - 1;
+  T tau = T(0), beta = T(0), scl = T(0), wc = T(0);
+  if (s > 0) {
+    T g = T(0);
+    for (int b = 0; b < a.ncta; ++b) g += a.part_prev[(int64_t)b * PW + lane];
+    const int owner = (int)(j / a.rows_per);
+    const T dr = a.part_prev[(int64_t)owner * PW + NB + lane];
+    const T x0 = __shfl_sync(0xffffffffu, dr, j);
+    const T gj = __shfl_sync(0xffffffffu, g, j);
+    if (gj == T(0)) {
+      tau = T(0);
+      beta = x0;
+      scl = T(0);
+    } else {
+      const T nrm = sqrt(x0 * x0 + gj);
+      beta = sgn_nrm(x0, nrm);
+      tau = (beta - x0) / beta;
+      scl = T(1) / (x0 - beta);
+    }
+    wc = dr + scl * g;  // v^T p_c for lanes c > j
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.tau[j] = tau;
+  }
+  const int64_t r0 = (int64_t)blockIdx.x * a.rows_per;
+  const int64_t r1 = min(a.mr, r0 + a.rows_per);
+  T acc = T(0);
+  for (int64_t r = r0 + warp; r < r1; r += WARPS) {
+    T val = lane < a.w ? a.P[r * a.ld + lane] : T(0);
+    if (s > 0 && r >= j) {
+      T nv;
+      if (r == j) {
+        nv = lane == j ? beta : (lane > j ? val - tau * wc : val);
+      } else {
+        const T vr = scl * __shfl_sync(0xffffffffu, val, j);
+        nv = lane == j ? vr : (lane > j ? val - (tau * wc) * vr : val);
+      }
+      if (lane < a.w && lane >= j) a.P[r * a.ld + lane] = nv;
+      val = nv;
+    }
+    if (s < a.w) {
+      const T ps = __shfl_sync(0xffffffffu, val, s);
+      if (r == s) {
+        a.part_cur[(int64_t)blockIdx.x * PW + NB + lane] = val;
+      } else if (r > s) {
+        acc = fma(ps, val, acc);
+      }
+    } else {
+      // last step: explicit reflector block
+      T v = (lane >= a.w || r < lane) ? T(0) : (r == lane ? T(1) : val);
+      a.V[r * NB + lane] = v;
+    }
+  }
+  if (s < a.w) {
+    red[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+      T t = T(0);
+#pragma unroll
+      for (int q = 0; q < WARPS; ++q) t += red[q][lane];
+      a.part_cur[(int64_t)blockIdx.x * PW + lane] = t;
+    }
+  }
+}
+
+// Z = sum over splits of the V^T V and V^T C partials.
+template <class T>
+__global__ void k_reduce_z(int w, int64_t nct, const T* __restrict__ pv, int sv, const T* __restrict__ pc, int sc,
+                           int64_t ldz, T* __restrict__ Z) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t cols = w + nct;
+  if (idx >= (int64_t)w * cols) return;
+  int64_t i = idx / cols, c = idx % cols;
+  T acc = T(0);
+  if (c < w) {
+    for (int z = 0; z < sv; ++z) acc += pv[(int64_t)z * NB * NB + i * NB + c];
+  } else {
+    for (int z = 0; z < sc; ++z) acc += pc[(int64_t)z * NB * ldz + i * ldz + (c - w)];
+  }
+  Z[i * (NB + ldz) + c] = acc;
+}
+
+// T (upper triangular, w x w) from V^T V (first w columns of Z) and tau.
+template <class T>
+__global__ void k_tfactor(int w, const T* __restrict__ Z, int64_t ldzz, const T* __restrict__ tau, T* __restrict__ Tm) {
+  __shared__ T Ts[NB][NB + 1];
+  const int lane = threadIdx.x;
+  for (int c = 0; c < NB; ++c) Ts[lane][c] = T(0);
+  __syncwarp();
+  for (int i = 0; i < w; ++i) {
+    // y[r] = sum_{k=r}^{i-1} T[r,k] * (V^T V)[k, i], r < i
+    T y = T(0);
+    if (lane < i)
+      for (int k = lane; k < i; ++k) y += Ts[lane][k] * Z[k * ldzz + i];
+    __syncwarp();
+    if (lane < i) Ts[lane][i] = -tau[i] * y;
+    if (lane == i) Ts[i][i] = tau[i];
+    __syncwarp();
+  }
+  for (int c = 0; c < NB; ++c) Tm[lane * NB + c] = Ts[lane][c];
+}
+
+// B' = T^T W, W = columns [w, w + nct) of Z.
+template <class T>
+__global__ void k_ttw(int w, int64_t nct, const T* __restrict__ Z, int64_t ldzz, const T* __restrict__ Tm,
+                      T* __restrict__ Bp, int64_t ldb) {
+  __shared__ T Ts[NB][NB];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Ts[e / NB][e % NB] = Tm[e];
+  __syncthreads();
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nct) return;
+  T wcol[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) wcol[k] = k < w ? Z[k * ldzz + w + c] : T(0);
+  for (int i = 0; i < w; ++i) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+      if (k <= i) acc += Ts[k][i] * wcol[k];  // (T^T)[i,k] = T[k,i], nonzero for k <= i
+    Bp[i * ldb + c] = acc;
+  }
+}
+
+template <class T>
+__global__ void k_extract_r(int64_t d, const T* __restrict__ B, int64_t ld, int with_rhs, double* __restrict__ R,
+                            int64_t ldr, double* __restrict__ qtsb) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= d * d) return;
+  int64_t i = idx / d, c = idx % d;
+  R[i * ldr + c] = c >= i ? SkiType<T>::to_f64(B[i * ld + c]) : 0.0;
+  if (c == 0 && with_rhs && qtsb) qtsb[i] = SkiType<T>::to_f64(B[i * ld + d]);
+}
+
+struct QrWs {
+  int64_t ncta_max, splits_max, ldz;
+};
+
+QrWs qr_dims(int64_t m, int64_t ncols) {
+  QrWs q;
+  q.ncta_max = std::min<int64_t>(1024, ski_cdiv(m, 64));
+  q.splits_max = 16;
+  q.ldz = ski_round_up(ncols, 4);
+  return q;
+}
+
+template <class T>
+ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, double* R, int64_t ldr, double* qtsb,
+                   SkiArena& ar, cudaStream_t st) {
+  const int64_t ncols = d + (with_rhs ? 1 : 0);
+  QrWs q = qr_dims(m, ncols);
+  T* partA = ar.take<T>(q.ncta_max * PW);
+  T* partB = ar.take<T>(q.ncta_max * PW);
+  T* tau = ar.take<T>(NB);
+  T* V = ar.take<T>(m * NB);
+  T* pv = ar.take<T>(152 * NB * NB);
+  T* pc = ar.take<T>(q.splits_max * NB * q.ldz);
+  T* Z = ar.take<T>(NB * (NB + q.ldz));
+  T* Tm = ar.take<T>(NB * NB);
+  T* Bp = ar.take<T>(NB * q.ldz);
+  if (!ar.ok() || !Bp) return SKI_ENOMEM;
+  for (int64_t k0 = 0; k0 < d; k0 += NB) {
+    const int w = (int)std::min<int64_t>(NB, d - k0);
+    const int64_t mr = m - k0;
+    const int ncta = (int)std::min<int64_t>(q.ncta_max, ski_cdiv(mr, 64));
+    const int64_t rows_per = ski_cdiv(mr, ncta);
+    PanelArgs<T> pa{B + k0 * ld + k0, ld, mr, w, rows_per, ncta, nullptr, nullptr, tau, V};
+    for (int s = 0; s <= w; ++s) {
+      pa.part_prev = (s & 1) ? partA : partB;
+      pa.part_cur = (s & 1) ? partB : partA;
+      k_panel_step<T><<<ncta, 32 * WARPS, 0, st>>>(pa, s);
+      SKI_LAUNCH_CHECK();
+    }
+    const int64_t nct = ncols - (k0 + w);
+    // V^T V (split-K over rows) and V^T C
+    const int sv = (int)std::min<int64_t>(152, ski_cdiv(mr, 64));
+    SKI_TRY(ski_gemm_ex<T>(NB, NB, mr, T(1), V, 1, NB, V, NB, 1, T(0), pv, NB, sv, (int64_t)NB * NB, st));
+    int sc = 1;
+    if (nct > 0) {
+      int64_t tiles = ski_cdiv(nct, 64);
+      sc = (int)std::max<int64_t>(1, std::min<int64_t>(q.splits_max, ski_cdiv(600, tiles)));
+      sc = (int)std::min<int64_t>(sc, ski_cdiv(mr, 64));
+      SKI_TRY(ski_gemm_ex<T>(NB, nct, mr, T(1), V, 1, NB, B + k0 * ld + k0 + w, ld, 1, T(0), pc, q.ldz, sc,
+                             (int64_t)NB * q.ldz, st));
+    }
+    const int64_t zc = w + nct;
+    k_reduce_z<T><<<ski_cdiv(w * zc, 256), 256, 0, st>>>(w, nct, pv, sv, pc, sc, q.ldz, Z);
+    SKI_LAUNCH_CHECK();
+    k_tfactor<T><<<1, 32, 0, st>>>(w, Z, NB + q.ldz, tau, Tm);
+    SKI_LAUNCH_CHECK();
+    if (nct > 0) {
+      k_ttw<T><<<ski_cdiv(nct, 128), 128, 0, st>>>(w, nct, Z, NB + q.ldz, Tm, Bp, q.ldz);
+      SKI_LAUNCH_CHECK();
+      // C -= V B'
+      SKI_TRY(ski_gemm<T>(mr, nct, w, T(-1), V, NB, 1, Bp, q.ldz, 1, T(1), B + k0 * ld + k0 + w, ld, st));
+    }
+  }
+  k_extract_r<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, B, ld, with_rhs, R, ldr, qtsb);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+}  // namespace
+
+size_t ski_qr_ws_bytes(int64_t m, int64_t ncols, int32_t dtype) {
+  QrWs q = qr_dims(m, ncols);
+  size_t es = dtype == SKI_F64 ? 8 : 4;
+  SkiArena ar{nullptr, 0, 0, true};
+  ar.take<char>(es * q.ncta_max * PW);
+  ar.take<char>(es * q.ncta_max * PW);
+  ar.take<char>(es * NB);
+  ar.take<char>(es * m * NB);
+  ar.take<char>(es * 152 * NB * NB);
+  ar.take<char>(es * q.splits_max * NB * q.ldz);
+  ar.take<char>(es * NB * (NB + q.ldz));
+  ar.take<char>(es * NB * NB);
+  ar.take<char>(es * NB * q.ldz);
+  return ar.off;
+}
+
+ski_status ski_qr_run(int64_t m, int64_t d, int32_t with_rhs, void* SA, int64_t ld_sa, int32_t dtype, double* R,
+                      int64_t ldr, double* qtsb, SkiArena& ar, cudaStream_t st) {
+  if (dtype == SKI_F64) return qr_impl<double>(m, d, with_rhs, (double*)SA, ld_sa, R, ldr, qtsb, ar, st);
+  if (dtype == SKI_F32) return qr_impl<float>(m, d, with_rhs, (float*)SA, ld_sa, R, ldr, qtsb, ar, st);
+  return SKI_EINVAL;
+}

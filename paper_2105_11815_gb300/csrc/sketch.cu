@@ -1,0 +1,394 @@
+// Step 1 of Algorithm 1: the s-hashing sketch [S A | S b] (Def. 5).
+//
+// S is never formed.  For every column j of S (row j of A) the s rows it
+// hits are drawn from the counter hash (hash.cuh).  The sketch is computed as
+// a deterministic gather: the (row j, nonzero k) pairs are bucketed by their
+// target row i of SA (count, scan, fill, canonical sort inside each bucket),
+// then row i of SA is formed from the rows of A listed in bucket i.
+//
+// FP64 output: every output element is accumulated in exact int64 block
+// fixed point (FxAcc, common.cuh) -- integer adds on the INT32 pipe instead
+// of FP64 adds, which on GB300 would cost more than the HBM traffic.
+// FP32 / BF16 output: FP32 accumulation of FP64 loads converted to FP32.
+#include "common.cuh"
+#include "hash.cuh"
+#include "sketch_impl.cuh"
+
+// ------------------------------------------------------------ hash tables
+template <int SMAX>
+__global__ void k_hash_table(uint64_t kb, uint64_t ks, int s, uint64_t m, int64_t n, int32_t* idx,
+                             int8_t* sign) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  int32_t rows[SMAX];
+  int neg[SMAX];
+  ski_column<SMAX>(kb, ks, s, m, (uint64_t)j, rows, neg);
+  for (int k = 0; k < s; ++k) {
+    idx[j * s + k] = rows[k];
+    sign[j * s + k] = neg[k] ? (int8_t)-1 : (int8_t)1;
+  }
+}
+
+__global__ void k_premix_signs(uint64_t kd, int64_t n, int8_t* D) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) D[j] = ski_premix_neg(kd, (uint64_t)j) ? (int8_t)-1 : (int8_t)1;
+}
+
+// Count pass: draw the column, store its (row, sign) pairs, count per bucket.
+template <int SMAX>
+__global__ void k_bucket_count(uint64_t kb, uint64_t ks, int s, uint64_t m, int64_t n,
+                               int32_t* __restrict__ pair_row, uint8_t* __restrict__ pair_neg,
+                               int32_t* __restrict__ counts) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  int32_t rows[SMAX];
+  int neg[SMAX];
+  ski_column<SMAX>(kb, ks, s, m, (uint64_t)j, rows, neg);
+  for (int k = 0; k < s; ++k) {
+    pair_row[j * s + k] = rows[k];
+    pair_neg[j * s + k] = (uint8_t)neg[k];
+    atomicAdd(&counts[rows[k]], 1);
+  }
+}
+
+// Exclusive scan of counts[0..m) into offsets[0..m], one CTA of 1024 threads.
+__global__ void k_scan_counts(const int32_t* __restrict__ counts, int64_t m, int64_t* __restrict__ offsets) {
+  __shared__ int64_t warp_tot[32];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t base = 0; base < m; base += blockDim.x) {
+    int64_t i = base + threadIdx.x;
+    int64_t v = i < m ? counts[i] : 0;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int64_t w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      warp_tot[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    int64_t before = carry + (wid ? warp_tot[wid - 1] : 0) + x - v;
+    if (i < m) offsets[i] = before;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = before + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) offsets[m] = carry;
+}
+
+// Fill pass: entry = (j << 1) | neg, placed at offsets[row] + cursor.
+__global__ void k_bucket_fill(int s, int64_t n, const int32_t* __restrict__ pair_row,
+                              const uint8_t* __restrict__ pair_neg, const int64_t* __restrict__ offsets,
+                              int32_t* __restrict__ cursor, uint32_t* __restrict__ list) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n * s) return;
+  int32_t r = pair_row[p];
+  int32_t pos = atomicAdd(&cursor[r], 1);
+  list[offsets[r] + pos] = ((uint32_t)(p / s) << 1) | (uint32_t)pair_neg[p];
+}
+
+// Canonical order inside each bucket (ascending entry), so that the sketch is
+// bit-reproducible whatever order the fill's atomics took.  One warp per
+// bucket: rank sort (entries are distinct), O(K^2 / 32) per bucket.
+__global__ void k_bucket_sort(int64_t m, const int64_t* __restrict__ offsets, const uint32_t* __restrict__ list_in,
+                              uint32_t* __restrict__ list_out) {
+  int64_t bkt = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (bkt >= m) return;
+  int64_t lo = offsets[bkt], hi = offsets[bkt + 1];
+  int64_t K = hi - lo;
+  for (int64_t a = lane; a < K; a += 32) {
+    uint32_t v = list_in[lo + a];
+    int64_t rank = 0;
+    for (int64_t c = 0; c < K; ++c) rank += (list_in[lo + c] < v);
+    list_out[lo + rank] = v;
+  }
+}
+
+// ------------------------------------------------------------ dense gather
+// Row i of SA, columns c in [c0, c0 + 2*blockDim): sum over the bucket's
+// entries (j, neg) of (-1)^neg * X[j, c] (X = [A | b]), times `scale`.
+template <class TOUT>
+__global__ void __launch_bounds__(128) k_sketch_dense_f64acc(
+    const double* __restrict__ A, int64_t lda, int64_t nrows, int64_t d, const double* __restrict__ b,
+    const int64_t* __restrict__ offsets, const uint32_t* __restrict__ list, long long scale_c, int scale_e,
+    TOUT* __restrict__ SA, int64_t ld_sa) {
+  const int64_t i = blockIdx.x;
+  const int64_t ncols = d + (b != nullptr);
+  const int64_t c0 = (int64_t)blockIdx.y * (2 * blockDim.x) + threadIdx.x;
+  const int64_t c1 = c0 + blockDim.x;
+  const int64_t lo = offsets[i], hi = offsets[i + 1];
+  FxAcc a0, a1;
+  a0.init();
+  a1.init();
+  int64_t e = lo;
+  for (; e + 4 <= hi; e += 4) {
+    uint32_t en[4];
+    double v0[4], v1[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) en[u] = __ldg(&list[e + u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int64_t j = en[u] >> 1;
+      v0[u] = c0 < d ? __ldcs(&A[j * lda + c0]) : (c0 == d && b ? __ldg(&b[j]) : 0.0);
+      v1[u] = c1 < d ? __ldcs(&A[j * lda + c1]) : (c1 == d && b ? __ldg(&b[j]) : 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a0.add(v0[u], en[u] & 1);
+      a1.add(v1[u], en[u] & 1);
+    }
+  }
+  for (; e < hi; ++e) {
+    uint32_t en = __ldg(&list[e]);
+    int64_t j = en >> 1;
+    double v0 = c0 < d ? __ldcs(&A[j * lda + c0]) : (c0 == d && b ? __ldg(&b[j]) : 0.0);
+    double v1 = c1 < d ? __ldcs(&A[j * lda + c1]) : (c1 == d && b ? __ldg(&b[j]) : 0.0);
+    a0.add(v0, en & 1);
+    a1.add(v1, en & 1);
+  }
+  (void)nrows;
+  if (c0 < ncols) SA[i * ld_sa + c0] = SkiType<TOUT>::from(fx_scaled(a0, scale_c, scale_e));
+  if (c1 < ncols) SA[i * ld_sa + c1] = SkiType<TOUT>::from(fx_scaled(a1, scale_c, scale_e));
+}
+
+template <class TOUT>
+__global__ void __launch_bounds__(128) k_sketch_dense_f32acc(
+    const double* __restrict__ A, int64_t lda, int64_t d, const double* __restrict__ b,
+    const int64_t* __restrict__ offsets, const uint32_t* __restrict__ list, float scale,
+    TOUT* __restrict__ SA, int64_t ld_sa) {
+  const int64_t i = blockIdx.x;
+  const int64_t ncols = d + (b != nullptr);
+  const int64_t c0 = (int64_t)blockIdx.y * (2 * blockDim.x) + threadIdx.x;
+  const int64_t c1 = c0 + blockDim.x;
+  const int64_t lo = offsets[i], hi = offsets[i + 1];
+  float s0 = 0.f, s1 = 0.f;
+  for (int64_t e = lo; e < hi; ++e) {
+    uint32_t en = __ldg(&list[e]);
+    int64_t j = en >> 1;
+    float v0 = c0 < d ? (float)__ldcs(&A[j * lda + c0]) : (c0 == d && b ? (float)__ldg(&b[j]) : 0.f);
+    float v1 = c1 < d ? (float)__ldcs(&A[j * lda + c1]) : (c1 == d && b ? (float)__ldg(&b[j]) : 0.f);
+    if (en & 1) { v0 = -v0; v1 = -v1; }
+    s0 += v0;
+    s1 += v1;
+  }
+  if (c0 < ncols) SA[i * ld_sa + c0] = SkiType<TOUT>::from((double)(s0 * scale));
+  if (c1 < ncols) SA[i * ld_sa + c1] = SkiType<TOUT>::from((double)(s1 * scale));
+}
+
+// Same gather reading an FP32 matrix Y (the FP32 premix output).
+template <class TOUT>
+__global__ void __launch_bounds__(128) k_sketch_dense_f32in(
+    const float* __restrict__ Y, int64_t ldy, int64_t ncols, const int64_t* __restrict__ offsets,
+    const uint32_t* __restrict__ list, float scale, TOUT* __restrict__ SA, int64_t ld_sa) {
+  const int64_t i = blockIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.y * (2 * blockDim.x) + threadIdx.x;
+  const int64_t c1 = c0 + blockDim.x;
+  const int64_t lo = offsets[i], hi = offsets[i + 1];
+  float s0 = 0.f, s1 = 0.f;
+  for (int64_t e = lo; e < hi; ++e) {
+    uint32_t en = __ldg(&list[e]);
+    int64_t j = en >> 1;
+    float v0 = c0 < ncols ? __ldcs(&Y[j * ldy + c0]) : 0.f;
+    float v1 = c1 < ncols ? __ldcs(&Y[j * ldy + c1]) : 0.f;
+    if (en & 1) { v0 = -v0; v1 = -v1; }
+    s0 += v0;
+    s1 += v1;
+  }
+  if (c0 < ncols) SA[i * ld_sa + c0] = SkiType<TOUT>::from((double)(s0 * scale));
+  if (c1 < ncols) SA[i * ld_sa + c1] = SkiType<TOUT>::from((double)(s1 * scale));
+}
+
+// ------------------------------------------------------------ CSR gather
+// Row i of SA for a CSR A: the bucket's rows are scattered into a
+// shared-memory accumulator over the column chunk [c0, c0 + chunk), then the
+// chunk is written out.  Column indices within one CSR row must be distinct.
+template <class TOUT>
+__global__ void __launch_bounds__(256) k_sketch_csr(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, const double* __restrict__ val,
+    int64_t d, const double* __restrict__ b, const int64_t* __restrict__ offsets,
+    const uint32_t* __restrict__ list, double scale, int64_t chunk, TOUT* __restrict__ SA, int64_t ld_sa) {
+  extern __shared__ double acc[];
+  const int64_t i = blockIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.y * chunk;
+  const int64_t ncols = d + (b != nullptr);
+  const int64_t cw = min(chunk, ncols - c0);
+  for (int64_t c = threadIdx.x; c < cw; c += blockDim.x) acc[c] = 0.0;
+  __syncthreads();
+  const int64_t lo = offsets[i], hi = offsets[i + 1];
+  double bacc = 0.0;
+  for (int64_t e = lo; e < hi; ++e) {
+    uint32_t en = list[e];
+    int64_t j = en >> 1;
+    double sg = (en & 1) ? -1.0 : 1.0;
+    int64_t p0 = rowptr[j], p1 = rowptr[j + 1];
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+      int64_t c = (int64_t)colidx[p] - c0;
+      if (c >= 0 && c < cw) acc[c] += sg * val[p];
+    }
+    if (b && threadIdx.x == 0) bacc += sg * b[j];
+    __syncthreads();
+  }
+  if (b && threadIdx.x == 0 && d >= c0 && d < c0 + cw) acc[d - c0] = bacc;
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < cw; c += blockDim.x)
+    SA[i * ld_sa + c0 + c] = SkiType<TOUT>::from(acc[c] * scale);
+}
+
+// ------------------------------------------------------------ host side
+static void scale_fixed(double scale, long long* c, int* e) {
+  // scale = c * 2^(-62 - e) with c in [2^61, 2^62): the integer multiplier of fx_scaled.
+  int ex;
+  double f = frexp(scale, &ex);  // scale = f * 2^ex, f in [0.5, 1)
+  *c = (long long)ldexp(f, 62);
+  *e = -ex;
+}
+
+size_t ski_bucket_ws_bytes(int64_t nrows, int32_t s, int64_t m) {
+  SkiArena ar{nullptr, 0, 0, true};
+  ar.take<int32_t>(nrows * s);
+  ar.take<uint8_t>(nrows * s);
+  ar.take<int32_t>(m);
+  ar.take<int32_t>(m);
+  ar.take<int64_t>(m + 1);
+  ar.take<uint32_t>(nrows * s);
+  ar.take<uint32_t>(nrows * s);
+  return ar.off;
+}
+
+ski_status ski_build_buckets(uint64_t seed, int32_t s, int64_t m, int64_t nrows, SkiArena& ar,
+                             cudaStream_t st, SkiBuckets* out) {
+  int32_t* pair_row = ar.take<int32_t>(nrows * s);
+  uint8_t* pair_neg = ar.take<uint8_t>(nrows * s);
+  int32_t* counts = ar.take<int32_t>(m);
+  int32_t* cursor = ar.take<int32_t>(m);
+  int64_t* offsets = ar.take<int64_t>(m + 1);
+  uint32_t* tmp = ar.take<uint32_t>(nrows * s);
+  uint32_t* list = ar.take<uint32_t>(nrows * s);
+  if (!ar.ok() || !list) return SKI_ENOMEM;
+  uint64_t kb = ski_tag_base(seed, SKI_TAG_BUCKET), ks = ski_tag_base(seed, SKI_TAG_SIGN);
+  SKI_CUDA_TRY(cudaMemsetAsync(counts, 0, m * sizeof(int32_t), st));
+  SKI_CUDA_TRY(cudaMemsetAsync(cursor, 0, m * sizeof(int32_t), st));
+  const int T = 256;
+  if (nrows > 0) {
+    if (s <= 4)
+      k_bucket_count<4><<<ski_cdiv(nrows, T), T, 0, st>>>(kb, ks, s, m, nrows, pair_row, pair_neg, counts);
+    else
+      k_bucket_count<64><<<ski_cdiv(nrows, T), T, 0, st>>>(kb, ks, s, m, nrows, pair_row, pair_neg, counts);
+    SKI_LAUNCH_CHECK();
+  }
+  k_scan_counts<<<1, 1024, 0, st>>>(counts, m, offsets);
+  SKI_LAUNCH_CHECK();
+  if (nrows > 0) {
+    k_bucket_fill<<<ski_cdiv(nrows * s, T), T, 0, st>>>(s, nrows, pair_row, pair_neg, offsets, cursor, tmp);
+    SKI_LAUNCH_CHECK();
+    k_bucket_sort<<<ski_cdiv(m * 32, T), T, 0, st>>>(m, offsets, tmp, list);
+    SKI_LAUNCH_CHECK();
+  }
+  out->offsets = offsets;
+  out->list = list;
+  out->m = m;
+  return SKI_OK;
+}
+
+ski_status ski_gather_dense(const double* A, int64_t lda, int64_t nrows, int64_t d, const double* b,
+                            const SkiBuckets& bk, double scale, int32_t out_dtype, void* SA, int64_t ld_sa,
+                            cudaStream_t st) {
+  const int T = 128;
+  const int64_t ncols = d + (b != nullptr);
+  dim3 grid((unsigned)bk.m, (unsigned)ski_cdiv(ncols, 2 * T));
+  if (out_dtype == SKI_F64) {
+    long long c;
+    int e;
+    scale_fixed(scale, &c, &e);
+    k_sketch_dense_f64acc<double><<<grid, T, 0, st>>>(A, lda, nrows, d, b, bk.offsets, bk.list, c, e,
+                                                       (double*)SA, ld_sa);
+  } else if (out_dtype == SKI_F32) {
+    k_sketch_dense_f32acc<float><<<grid, T, 0, st>>>(A, lda, d, b, bk.offsets, bk.list, (float)scale,
+                                                     (float*)SA, ld_sa);
+  } else {
+    k_sketch_dense_f32acc<__nv_bfloat16><<<grid, T, 0, st>>>(A, lda, d, b, bk.offsets, bk.list, (float)scale,
+                                                             (__nv_bfloat16*)SA, ld_sa);
+  }
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+ski_status ski_gather_dense_f32in(const float* Y, int64_t ldy, int64_t ncols, const SkiBuckets& bk,
+                                  double scale, int32_t out_dtype, void* SA, int64_t ld_sa, cudaStream_t st) {
+  const int T = 128;
+  dim3 grid((unsigned)bk.m, (unsigned)ski_cdiv(ncols, 2 * T));
+  if (out_dtype == SKI_F32)
+    k_sketch_dense_f32in<float><<<grid, T, 0, st>>>(Y, ldy, ncols, bk.offsets, bk.list, (float)scale,
+                                                    (float*)SA, ld_sa);
+  else
+    k_sketch_dense_f32in<__nv_bfloat16><<<grid, T, 0, st>>>(Y, ldy, ncols, bk.offsets, bk.list, (float)scale,
+                                                            (__nv_bfloat16*)SA, ld_sa);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+ski_status ski_gather_csr(const ski_matrix* A, const double* b, const SkiBuckets& bk, double scale,
+                          int32_t out_dtype, void* SA, int64_t ld_sa, cudaStream_t st) {
+  const int64_t ncols = A->d + (b != nullptr);
+  int64_t chunk = ncols < 8192 ? ncols : 8192;
+  size_t smem = chunk * sizeof(double);
+  dim3 grid((unsigned)bk.m, (unsigned)ski_cdiv(ncols, chunk));
+  const int T = 256;
+  if (out_dtype == SKI_F64) {
+    if (smem > 48 * 1024)
+      SKI_CUDA_TRY(cudaFuncSetAttribute(k_sketch_csr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_sketch_csr<double><<<grid, T, smem, st>>>(A->rowptr, A->colidx, A->val, A->d, b, bk.offsets, bk.list,
+                                                scale, chunk, (double*)SA, ld_sa);
+  } else if (out_dtype == SKI_F32) {
+    if (smem > 48 * 1024)
+      SKI_CUDA_TRY(cudaFuncSetAttribute(k_sketch_csr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_sketch_csr<float><<<grid, T, smem, st>>>(A->rowptr, A->colidx, A->val, A->d, b, bk.offsets, bk.list,
+                                               scale, chunk, (float*)SA, ld_sa);
+  } else {
+    if (smem > 48 * 1024)
+      SKI_CUDA_TRY(cudaFuncSetAttribute(k_sketch_csr<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    k_sketch_csr<__nv_bfloat16><<<grid, T, smem, st>>>(A->rowptr, A->colidx, A->val, A->d, b, bk.offsets,
+                                                       bk.list, scale, chunk, (__nv_bfloat16*)SA, ld_sa);
+  }
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+extern "C" ski_status ski_hash_indices(uint64_t seed, int32_t s, int64_t m, int64_t n, int32_t* idx,
+                                       int8_t* sign, void* stream) {
+  if (s < 1 || m < s || m >= (1ll << 31) || n < 0 || s > 64) return SKI_EINVAL;
+  if (n == 0) return SKI_OK;
+  if (!idx || !sign) return SKI_EINVAL;
+  uint64_t kb = ski_tag_base(seed, SKI_TAG_BUCKET), ks = ski_tag_base(seed, SKI_TAG_SIGN);
+  const int T = 256;
+  if (s <= 4)
+    k_hash_table<4><<<ski_cdiv(n, T), T, 0, ski_stream(stream)>>>(kb, ks, s, (uint64_t)m, n, idx, sign);
+  else
+    k_hash_table<64><<<ski_cdiv(n, T), T, 0, ski_stream(stream)>>>(kb, ks, s, (uint64_t)m, n, idx, sign);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+extern "C" ski_status ski_premix_signs(uint64_t seed, int64_t n, int8_t* D, void* stream) {
+  if (n < 0) return SKI_EINVAL;
+  if (n == 0) return SKI_OK;
+  if (!D) return SKI_EINVAL;
+  const int T = 256;
+  k_premix_signs<<<ski_cdiv(n, T), T, 0, ski_stream(stream)>>>(ski_tag_base(seed, SKI_TAG_PREMIX), n, D);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}

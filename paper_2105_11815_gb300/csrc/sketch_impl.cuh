@@ -1,0 +1,57 @@
+// Internal interfaces between the sketch, premix, QR, LSQR translation units
+// and the C-ABI layer.
+#pragma once
+#include "common.cuh"
+
+struct SkiBuckets {
+  const int64_t* offsets;  // [m+1]
+  const uint32_t* list;    // entries (j << 1) | neg, ascending inside a bucket
+  int64_t m;
+};
+
+// scale * (S * 2^(E - 1075 - FX_LIFT)) with scale = c * 2^(-62 - e), c in [2^61, 2^62).
+__device__ __forceinline__ double fx_scaled(const FxAcc& a, long long c, int e) {
+  if (a.bad) return __longlong_as_double(0x7FF8000000000000ll);
+  long long Sp = (long long)(((__int128)a.S * (__int128)c) >> 62);
+  return fx_to_double(Sp, a.E, e);
+}
+
+// ---- sketch.cu
+size_t ski_bucket_ws_bytes(int64_t nrows, int32_t s, int64_t m);
+ski_status ski_build_buckets(uint64_t seed, int32_t s, int64_t m, int64_t nrows, SkiArena& ar,
+                             cudaStream_t st, SkiBuckets* out);
+ski_status ski_gather_dense(const double* A, int64_t lda, int64_t nrows, int64_t d, const double* b,
+                            const SkiBuckets& bk, double scale, int32_t out_dtype, void* SA, int64_t ld_sa,
+                            cudaStream_t st);
+ski_status ski_gather_dense_f32in(const float* Y, int64_t ldy, int64_t ncols, const SkiBuckets& bk,
+                                  double scale, int32_t out_dtype, void* SA, int64_t ld_sa, cudaStream_t st);
+ski_status ski_gather_csr(const ski_matrix* A, const double* b, const SkiBuckets& bk, double scale,
+                          int32_t out_dtype, void* SA, int64_t ld_sa, cudaStream_t st);
+
+// ---- wht.cu
+// Y = 2^(-floor(L/2)) * Hu D [A b; 0] with Hu the unnormalised Walsh-Hadamard
+// matrix of order n_pad = 2^L; the remaining factor (1 or 2^-1/2) is
+// returned in *residual_scale for the caller to fold into the sketch scale.
+size_t ski_premix_ws_bytes(int64_t n, int64_t ncols, int64_t n_pad, int32_t dtype);
+ski_status ski_premix_run(const double* A, int64_t lda, int64_t n, int64_t d, const double* b, uint64_t seed,
+                          int64_t n_pad, int32_t dtype, void* Y, int64_t ldy, SkiArena& ar, cudaStream_t st,
+                          double* residual_scale);
+
+// ---- qr.cu
+size_t ski_qr_ws_bytes(int64_t m, int64_t ncols, int32_t dtype);
+ski_status ski_qr_run(int64_t m, int64_t d, int32_t with_rhs, void* SA, int64_t ld_sa, int32_t dtype,
+                      double* R, int64_t ldr, double* qtsb, SkiArena& ar, cudaStream_t st);
+
+// ---- trinv.cu
+size_t ski_trinv_ws_bytes(int64_t d, int32_t dtype);
+ski_status ski_trinv_run(int64_t d, const double* R, int64_t ldr, double* M, double* Mt, int64_t ldm,
+                         int32_t dtype, double perturb, SkiArena& ar, cudaStream_t st);
+
+// ---- gemm.cu : C = beta*C + alpha * op(A) op(B), row-major element strides.
+template <class T>
+ski_status ski_gemm(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t sa_m, int64_t sa_k,
+                    const T* B, int64_t sb_k, int64_t sb_n, T beta, T* C, int64_t ldc, cudaStream_t st);
+template <class T>
+ski_status ski_gemm_ex(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t sa_m, int64_t sa_k,
+                       const T* B, int64_t sb_k, int64_t sb_n, T beta, T* C, int64_t ldc, int splits,
+                       int64_t c_zstride, cudaStream_t st);

@@ -1,0 +1,119 @@
+// R^{-1} for the upper-triangular factor of Step 2, formed once so that the
+// two preconditioner applications per LSQR iteration (R^{-1} v, R^{-T} u) are
+// bandwidth-bound triangular matrix-vector products instead of
+// latency-bound back-substitutions.  Recursive 2x2 blocking:
+//   [R11 R12; 0 R22]^{-1} = [X11, -X11 R12 X22; 0, X22],  X11 = R11^{-1}, X22 = R22^{-1},
+// with all 32 x 32 diagonal blocks inverted by back-substitution in one launch
+// and the off-diagonal blocks formed by GEMMs (gemm.cu).  With perturb > 0
+// each diagonal entry r_ii is replaced by r_ii + perturb (the perturbed
+// back-solve of Ski-LLS-sparse).
+#include "common.cuh"
+#include "sketch_impl.cuh"
+
+namespace {
+
+constexpr int LB = 32;
+
+// Invert the LB x LB diagonal blocks of R (in X, same layout): one warp per
+// block, lane = column of the inverse.
+template <class T>
+__global__ void k_diag_inv(int64_t d, const T* __restrict__ R, int64_t ldr, T* __restrict__ X, int64_t ldx,
+                           double perturb) {
+  const int64_t blk = blockIdx.x;
+  const int lane = threadIdx.x;
+  const int64_t o = blk * LB;
+  const int nbk = (int)std::min<int64_t>(LB, d - o);
+  __shared__ T Rs[LB][LB + 1];
+  for (int i = 0; i < nbk; ++i) Rs[i][lane] = lane < nbk ? R[(o + i) * ldr + o + lane] : T(0);
+  __syncwarp();
+  // column `lane` of the inverse: solve R x = e_lane by back-substitution
+  T x[LB];
+#pragma unroll
+  for (int i = 0; i < LB; ++i) x[i] = T(0);
+  if (lane < nbk) {
+#pragma unroll
+    for (int i = LB - 1; i >= 0; --i) {
+      if (i >= nbk || i > lane) continue;
+      T acc = (i == lane) ? T(1) : T(0);
+#pragma unroll
+      for (int k = i + 1; k < LB; ++k)
+        if (k <= lane && k < nbk) acc -= Rs[i][k] * x[k];
+      x[i] = acc / (Rs[i][i] + (T)perturb);
+    }
+  }
+  for (int i = 0; i < nbk; ++i)
+    if (lane < nbk) X[(o + i) * ldx + o + lane] = x[i];
+}
+
+template <class T>
+__global__ void k_cast_upper(int64_t d, const double* __restrict__ R, int64_t ldr, T* __restrict__ Rt, int64_t ldt) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= d * d) return;
+  int64_t i = idx / d, c = idx % d;
+  Rt[i * ldt + c] = c >= i ? (T)R[i * ldr + c] : T(0);
+}
+
+template <class T>
+__global__ void k_emit(int64_t d, const T* __restrict__ X, int64_t ldx, double* __restrict__ M,
+                       double* __restrict__ Mt, int64_t ldm) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= d * d) return;
+  int64_t i = idx / d, c = idx % d;
+  double v = c >= i ? (double)X[i * ldx + c] : 0.0;
+  M[i * ldm + c] = v;
+  if (Mt) Mt[c * ldm + i] = v;
+}
+
+// Off-diagonal blocks, bottom-up over the recursion tree.
+template <class T>
+ski_status rec(int64_t o, int64_t n, const T* R, int64_t ldr, T* X, int64_t ldx, T* tmp, cudaStream_t st) {
+  if (n <= LB) return SKI_OK;
+  int64_t n1 = ski_round_up(n / 2, LB);
+  int64_t n2 = n - n1;
+  SKI_TRY(rec<T>(o, n1, R, ldr, X, ldx, tmp, st));
+  SKI_TRY(rec<T>(o + n1, n2, R, ldr, X, ldx, tmp, st));
+  // tmp = R12 X22 (n1 x n2), X22 upper triangular: K = n2
+  const T* R12 = R + o * ldr + o + n1;
+  const T* X22 = X + (o + n1) * ldx + o + n1;
+  const T* X11 = X + o * ldx + o;
+  T* X12 = X + o * ldx + o + n1;
+  SKI_TRY(ski_gemm<T>(n1, n2, n2, T(1), R12, ldr, 1, X22, ldx, 1, T(0), tmp, n2, st));
+  SKI_TRY(ski_gemm<T>(n1, n2, n1, T(-1), X11, ldx, 1, tmp, n2, 1, T(0), X12, ldx, st));
+  return SKI_OK;
+}
+
+template <class T>
+ski_status trinv_impl(int64_t d, const double* R, int64_t ldr, double* M, double* Mt, int64_t ldm, double perturb,
+                      SkiArena& ar, cudaStream_t st) {
+  T* Rt = ar.take<T>(d * d);
+  T* X = ar.take<T>(d * d);
+  T* tmp = ar.take<T>(ski_cdiv(d, 2) * d + LB * d);
+  if (!ar.ok() || !tmp) return SKI_ENOMEM;
+  SKI_CUDA_TRY(cudaMemsetAsync(X, 0, d * d * sizeof(T), st));
+  k_cast_upper<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, R, ldr, Rt, d);
+  SKI_LAUNCH_CHECK();
+  k_diag_inv<T><<<ski_cdiv(d, LB), 32, 0, st>>>(d, Rt, d, X, d, perturb);
+  SKI_LAUNCH_CHECK();
+  SKI_TRY(rec<T>(0, d, Rt, d, X, d, tmp, st));
+  k_emit<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, X, d, M, Mt, ldm);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+}  // namespace
+
+size_t ski_trinv_ws_bytes(int64_t d, int32_t dtype) {
+  size_t es = dtype == SKI_F64 ? 8 : 4;
+  SkiArena ar{nullptr, 0, 0, true};
+  ar.take<char>(es * d * d);
+  ar.take<char>(es * d * d);
+  ar.take<char>(es * (ski_cdiv(d, 2) * d + LB * d));
+  return ar.off;
+}
+
+ski_status ski_trinv_run(int64_t d, const double* R, int64_t ldr, double* M, double* Mt, int64_t ldm, int32_t dtype,
+                         double perturb, SkiArena& ar, cudaStream_t st) {
+  if (dtype == SKI_F64) return trinv_impl<double>(d, R, ldr, M, Mt, ldm, perturb, ar, st);
+  if (dtype == SKI_F32) return trinv_impl<float>(d, R, ldr, M, Mt, ldm, perturb, ar, st);
+  return SKI_EINVAL;
+}

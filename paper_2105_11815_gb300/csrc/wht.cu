@@ -1,0 +1,405 @@
+// Randomised Walsh-Hadamard premix H D (Def. 8) for dense A.
+//
+// Y = H D [A b; 0]: rows scaled by D_jj, zero-padded to n_pad = 2^L rows and
+// transformed along the row index by the Sylvester-order Walsh-Hadamard
+// matrix.  The transform is L butterfly levels (rows i and i + 2^l replaced
+// by sum and difference); they are split into passes of at most 9 levels.
+// One pass stages a tile of 2^nb rows (row index bits [lo, lo+nb)) by 32
+// columns: each thread holds 2^RB rows of one column in registers and does
+// RB levels there, the tile is exchanged once through shared memory, and the
+// remaining GB = nb - RB levels are again done in registers.  Every global
+// access is a 32-column (256 B) coalesced row segment.
+//
+// FP64: the butterflies run on int64 block-fixed-point values (each tile
+// column shares one power-of-two exponent, stored beside the intermediate),
+// i.e. exact integer adds with headroom for the nb levels of growth -- on
+// GB300 the FP64 pipe (2 adds/clk/SM) could not keep up with HBM here.
+// FP32: plain FP32 butterflies.
+#include "common.cuh"
+#include "hash.cuh"
+#include "sketch_impl.cuh"
+
+namespace {
+
+constexpr int CT = 32;
+
+__device__ __forceinline__ int64_t tile_base(int64_t tile, int lo, int nb) {
+  int64_t low = tile & ((1ll << lo) - 1);
+  int64_t hi = tile >> lo;
+  return (hi << (lo + nb)) | low;
+}
+__device__ __forceinline__ int64_t tile_of_row(int64_t row, int lo, int nb) {
+  return ((row >> (lo + nb)) << lo) | (row & ((1ll << lo) - 1));
+}
+
+struct FxIn {
+  // IN == 0: FP64 source
+  const double* A;
+  int64_t lda, n, d;
+  const double* b;
+  const int8_t* D;
+  // IN == 1: previous pass
+  const long long* Q;
+  const int16_t* X;
+  int64_t ldq, ldx, nvalid;
+  int lo_p, nb_p;
+};
+struct FxOut {
+  long long* Q;
+  int16_t* X;
+  int64_t ldq, ldx;
+  double* Y;
+  int64_t ldy;
+  int yshift;
+  int* nonfinite;
+};
+
+template <int RB, int GB, int IN, int OUT>
+__global__ void __launch_bounds__(CT << GB) k_wht_fx(int lo, int64_t n_pad, int64_t ncols, FxIn in, FxOut out) {
+  constexpr int R = 1 << RB, G = 1 << GB, NB = RB + GB;
+  extern __shared__ long long sq[];            // [R*G][CT]
+  __shared__ int sx[G][CT];
+  const int c = threadIdx.x & (CT - 1), g = threadIdx.x / CT;
+  const int64_t tile = blockIdx.x;
+  const int64_t base = tile_base(tile, lo, NB);
+  if (IN == 0 && OUT == 0 && lo == 0 && base >= in.n) return;  // whole tile in the zero padding
+  const int64_t col = (int64_t)blockIdx.y * CT + c;
+  const bool cok = col < ncols;
+  long long q[R];
+  int xsrc[IN == 1 ? R : 1];
+  int emax = -100000;
+  bool bad = false;
+  if (IN == 0) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int64_t row = base + ((int64_t)(g + (t << GB)) << lo);
+      double v = 0.0;
+      if (cok && row < in.n) {
+        v = col < in.d ? in.A[row * in.lda + col] : in.b[row];
+        if (in.D[row] < 0) v = -v;
+      }
+      long long bits = __double_as_longlong(v);
+      int e = (int)((bits >> 52) & 0x7FF);
+      bad |= (e == 0x7FF);
+      emax = max(emax, e ? e : 1);
+      q[t] = bits;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int64_t row = base + ((int64_t)(g + (t << GB)) << lo);
+      long long v = 0;
+      int xs = -32768;
+      if (cok && row < in.nvalid) {
+        v = in.Q[row * in.ldq + col];
+        xs = in.X[tile_of_row(row, in.lo_p, in.nb_p) * in.ldx + col];
+      }
+      q[t] = v;
+      xsrc[t] = v ? xs : -32768;
+      emax = max(emax, xsrc[t]);
+    }
+  }
+  if (bad && out.nonfinite) atomicOr(out.nonfinite, 1);
+  sx[g][c] = emax;
+  __syncthreads();
+  int E = sx[0][c];
+#pragma unroll
+  for (int gg = 1; gg < G; ++gg) E = max(E, sx[gg][c]);
+  int X;  // value = q * 2^X after quantisation
+  if (IN == 0) {
+    constexpr int LIFT = 9 - NB;  // |q| < 2^(62 - NB) before the NB levels
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      unsigned long long bits = (unsigned long long)q[t];
+      int e = (int)((bits >> 52) & 0x7FF);
+      unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+      int sh = E - (e ? e : 1);
+      unsigned long long mq = sh > 63 ? 0ull : ((M << LIFT) >> sh);
+      q[t] = (bits >> 63) ? -(long long)mq : (long long)mq;
+    }
+    X = E - 1075 - LIFT;
+  } else {
+    if (E == -32768) E = 0;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      int sh = E - xsrc[IN == 1 ? t : 0] + NB;
+      q[t] = (q[t] == 0 || sh > 63) ? 0 : (q[t] >> sh);
+    }
+    X = E + NB;
+  }
+  // RB levels in registers: row bits [GB, GB+RB) of the tile index
+#pragma unroll
+  for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      if (!(t & h)) {
+        long long u = q[t], w = q[t + h];
+        q[t] = u + w;
+        q[t + h] = u - w;
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t) sq[(g + (t << GB)) * CT + c] = q[t];
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < R; ++t) q[t] = sq[((g << RB) + t) * CT + c];
+  // GB levels in registers: row bits [0, GB)
+#pragma unroll
+  for (int h = 1; h < G; h <<= 1) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      if (!(t & h)) {
+        long long u = q[t], w = q[t + h];
+        q[t] = u + w;
+        q[t + h] = u - w;
+      }
+    }
+  }
+  if (!cok) return;
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int64_t row = base + ((int64_t)((g << RB) + t) << lo);
+    if (row >= n_pad) continue;
+    if (OUT == 0) {
+      out.Q[row * out.ldq + col] = q[t];
+    } else {
+      out.Y[row * out.ldy + col] = fx_to_double(q[t], X - out.yshift + 1075 + FX_LIFT, 0);
+    }
+  }
+  if (OUT == 0 && g == 0) out.X[tile * out.ldx + col] = (int16_t)X;
+}
+
+template <class TOUT>
+struct F32Out {
+  float* Q;
+  int64_t ldq;
+  TOUT* Y;
+  int64_t ldy;
+  float yscale;
+};
+
+template <int RB, int GB, int IN, int OUT, class TOUT>
+__global__ void __launch_bounds__(CT << GB) k_wht_f32(int lo, int64_t n_pad, int64_t ncols, FxIn in,
+                                                       const float* Qin, int64_t ldqin, F32Out<TOUT> out) {
+  constexpr int R = 1 << RB, G = 1 << GB, NB = RB + GB;
+  extern __shared__ float sf[];
+  const int c = threadIdx.x & (CT - 1), g = threadIdx.x / CT;
+  const int64_t tile = blockIdx.x;
+  const int64_t base = tile_base(tile, lo, NB);
+  if (IN == 0 && OUT == 0 && lo == 0 && base >= in.n) return;
+  const int64_t col = (int64_t)blockIdx.y * CT + c;
+  const bool cok = col < ncols;
+  float q[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int64_t row = base + ((int64_t)(g + (t << GB)) << lo);
+    float v = 0.f;
+    if (IN == 0) {
+      if (cok && row < in.n) {
+        v = (float)(col < in.d ? in.A[row * in.lda + col] : in.b[row]);
+        if (in.D[row] < 0) v = -v;
+      }
+    } else {
+      if (cok && row < in.nvalid) v = Qin[row * ldqin + col];
+    }
+    q[t] = v;
+  }
+#pragma unroll
+  for (int h = 1; h < R; h <<= 1)
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+      if (!(t & h)) {
+        float u = q[t], w = q[t + h];
+        q[t] = u + w;
+        q[t + h] = u - w;
+      }
+#pragma unroll
+  for (int t = 0; t < R; ++t) sf[(g + (t << GB)) * CT + c] = q[t];
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < R; ++t) q[t] = sf[((g << RB) + t) * CT + c];
+#pragma unroll
+  for (int h = 1; h < G; h <<= 1)
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+      if (!(t & h)) {
+        float u = q[t], w = q[t + h];
+        q[t] = u + w;
+        q[t + h] = u - w;
+      }
+  if (!cok) return;
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int64_t row = base + ((int64_t)((g << RB) + t) << lo);
+    if (row >= n_pad) continue;
+    if (OUT == 0) out.Q[row * out.ldq + col] = q[t];
+    else out.Y[row * out.ldy + col] = SkiType<TOUT>::from((double)(q[t] * out.yscale));
+  }
+}
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((1ll << l) < v) ++l;
+  return l;
+}
+
+void plan_passes(int L, int* nbs, int* np) {
+  if (L == 0) {
+    nbs[0] = 1;
+    *np = 1;
+    return;
+  }
+  int P = (L + 8) / 9;
+  for (int p = 0; p < P; ++p) nbs[p] = L / P + (p < L % P ? 1 : 0);
+  *np = P;
+}
+
+template <int IN, int OUT>
+ski_status launch_fx(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& in, const FxOut& out,
+                     cudaStream_t st) {
+  const int GB = nb / 2, RB = nb - GB;
+  const int64_t ntiles = n_pad >> nb > 0 ? (n_pad >> nb) : 1;
+  dim3 grid((unsigned)ntiles, (unsigned)ski_cdiv(ncols, CT));
+  const size_t smem = (size_t)(1 << nb) * CT * sizeof(long long);
+  const int threads = CT << GB;
+#define SKI_FX_CASE(rb, gb)                                                                      \
+  if (RB == rb && GB == gb) {                                                                    \
+    auto kfn = k_wht_fx<rb, gb, IN, OUT>;                                                        \
+    if (smem > 48 * 1024)                                                                        \
+      SKI_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    kfn<<<grid, threads, smem, st>>>(lo, n_pad, ncols, in, out);                                 \
+    SKI_LAUNCH_CHECK();                                                                          \
+    return SKI_OK;                                                                               \
+  }
+  SKI_FX_CASE(1, 0) SKI_FX_CASE(1, 1) SKI_FX_CASE(2, 1) SKI_FX_CASE(2, 2) SKI_FX_CASE(3, 2)
+  SKI_FX_CASE(3, 3) SKI_FX_CASE(4, 3) SKI_FX_CASE(4, 4) SKI_FX_CASE(5, 4)
+#undef SKI_FX_CASE
+  return SKI_EINVAL;
+}
+
+template <int IN, int OUT, class TOUT>
+ski_status launch_f32(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& in, const float* Qin,
+                      int64_t ldqin, const F32Out<TOUT>& out, cudaStream_t st) {
+  const int GB = nb / 2, RB = nb - GB;
+  const int64_t ntiles = n_pad >> nb > 0 ? (n_pad >> nb) : 1;
+  dim3 grid((unsigned)ntiles, (unsigned)ski_cdiv(ncols, CT));
+  const size_t smem = (size_t)(1 << nb) * CT * sizeof(float);
+  const int threads = CT << GB;
+#define SKI_F32_CASE(rb, gb)                                                                     \
+  if (RB == rb && GB == gb) {                                                                    \
+    auto kfn = k_wht_f32<rb, gb, IN, OUT, TOUT>;                                                 \
+    if (smem > 48 * 1024)                                                                        \
+      SKI_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    kfn<<<grid, threads, smem, st>>>(lo, n_pad, ncols, in, Qin, ldqin, out);                     \
+    SKI_LAUNCH_CHECK();                                                                          \
+    return SKI_OK;                                                                               \
+  }
+  SKI_F32_CASE(1, 0) SKI_F32_CASE(1, 1) SKI_F32_CASE(2, 1) SKI_F32_CASE(2, 2) SKI_F32_CASE(3, 2)
+  SKI_F32_CASE(3, 3) SKI_F32_CASE(4, 3) SKI_F32_CASE(4, 4) SKI_F32_CASE(5, 4)
+#undef SKI_F32_CASE
+  return SKI_EINVAL;
+}
+
+}  // namespace
+
+size_t ski_premix_ws_bytes(int64_t n, int64_t ncols, int64_t n_pad, int32_t dtype) {
+  SkiArena ar{nullptr, 0, 0, true};
+  const int64_t ldq = ski_round_up(ncols, CT);
+  ar.take<int8_t>(n);
+  ar.take<int>(1);
+  if (dtype == SKI_F64) {
+    ar.take<long long>(n_pad * ldq);
+    ar.take<long long>(n_pad * ldq);
+    ar.take<int16_t>(n_pad * ldq);
+    ar.take<int16_t>(n_pad * ldq);
+  } else {
+    ar.take<float>(n_pad * ldq);
+    ar.take<float>(n_pad * ldq);
+  }
+  return ar.off;
+}
+
+ski_status ski_premix_run(const double* A, int64_t lda, int64_t n, int64_t d, const double* b, uint64_t seed,
+                          int64_t n_pad, int32_t dtype, void* Y, int64_t ldy, SkiArena& ar, cudaStream_t st,
+                          double* residual_scale) {
+  const int64_t ncols = d + (b != nullptr);
+  const int64_t ldq = ski_round_up(ncols, CT);
+  int8_t* D = ar.take<int8_t>(n);
+  int* nonfinite = ar.take<int>(1);
+  const int L = ilog2(n_pad);
+  int nbs[8], P;
+  plan_passes(L, nbs, &P);
+  SKI_TRY(ski_premix_signs(seed, n, D, st));
+  *residual_scale = (L & 1) ? 0.70710678118654752440 : 1.0;
+  const int yshift = L / 2;
+  FxIn in{};
+  in.A = A; in.lda = lda; in.n = n; in.d = d; in.b = b; in.D = D;
+  if (dtype == SKI_F64) {
+    long long* Qa = ar.take<long long>(n_pad * ldq);
+    long long* Qb = ar.take<long long>(n_pad * ldq);
+    int16_t* Xa = ar.take<int16_t>(n_pad * ldq);
+    int16_t* Xb = ar.take<int16_t>(n_pad * ldq);
+    if (!ar.ok() || !Xb) return SKI_ENOMEM;
+    SKI_CUDA_TRY(cudaMemsetAsync(nonfinite, 0, sizeof(int), st));
+    int lo = 0;
+    int64_t nvalid = n;
+    long long* Qin = nullptr;
+    int16_t* Xin = nullptr;
+    int lo_p = 0, nb_p = 0;
+    for (int p = 0; p < P; ++p) {
+      const int nb = nbs[p];
+      const bool last = p == P - 1;
+      long long* Qo = (p & 1) ? Qb : Qa;
+      int16_t* Xo = (p & 1) ? Xb : Xa;
+      FxOut out{};
+      out.Q = Qo; out.X = Xo; out.ldq = ldq; out.ldx = ldq; out.Y = (double*)Y; out.ldy = ldy;
+      out.yshift = yshift; out.nonfinite = nonfinite;
+      FxIn cur = in;
+      cur.Q = Qin; cur.X = Xin; cur.ldq = ldq; cur.ldx = ldq; cur.nvalid = nvalid; cur.lo_p = lo_p; cur.nb_p = nb_p;
+      ski_status s;
+      if (p == 0) s = last ? launch_fx<0, 1>(nb, lo, n_pad, ncols, cur, out, st) : launch_fx<0, 0>(nb, lo, n_pad, ncols, cur, out, st);
+      else s = last ? launch_fx<1, 1>(nb, lo, n_pad, ncols, cur, out, st) : launch_fx<1, 0>(nb, lo, n_pad, ncols, cur, out, st);
+      if (s != SKI_OK) return s;
+      nvalid = (p == 0) ? ski_round_up(n, 1ll << nb) : n_pad;
+      if (nvalid > n_pad) nvalid = n_pad;
+      Qin = Qo; Xin = Xo; lo_p = lo; nb_p = nb;
+      lo += nb;
+    }
+  } else {
+    float* Qa = ar.take<float>(n_pad * ldq);
+    float* Qb = ar.take<float>(n_pad * ldq);
+    if (!ar.ok() || !Qb) return SKI_ENOMEM;
+    int lo = 0;
+    int64_t nvalid = n;
+    const float* Qin = nullptr;
+    const float yscale = ldexpf(1.0f, -yshift);
+    for (int p = 0; p < P; ++p) {
+      const int nb = nbs[p];
+      const bool last = p == P - 1;
+      float* Qo = (p & 1) ? Qb : Qa;
+      FxIn cur = in;
+      cur.nvalid = nvalid;
+      ski_status s;
+      if (dtype == SKI_F32) {
+        F32Out<float> out{Qo, ldq, (float*)Y, ldy, yscale};
+        if (p == 0) s = last ? launch_f32<0, 1, float>(nb, lo, n_pad, ncols, cur, Qin, ldq, out, st)
+                             : launch_f32<0, 0, float>(nb, lo, n_pad, ncols, cur, Qin, ldq, out, st);
+        else s = last ? launch_f32<1, 1, float>(nb, lo, n_pad, ncols, cur, Qin, ldq, out, st)
+                      : launch_f32<1, 0, float>(nb, lo, n_pad, ncols, cur, Qin, ldq, out, st);
+      } else {
+        F32Out<__nv_bfloat16> out{Qo, ldq, (__nv_bfloat16*)Y, ldy, yscale};
+        if (p == 0) s = last ? launch_f32<0, 1, __nv_bfloat16>(nb, lo, n_pad, ncols, cur, Qin, ldq, out, st)
+                             : launch_f32<0, 0, __nv_bfloat16>(nb, lo, n_pad, ncols, cur, Qin, ldq, out, st);
+        else s = last ? launch_f32<1, 1, __nv_bfloat16>(nb, lo, n_pad, ncols, cur, Qin, ldq, out, st)
+                      : launch_f32<1, 0, __nv_bfloat16>(nb, lo, n_pad, ncols, cur, Qin, ldq, out, st);
+      }
+      if (s != SKI_OK) return s;
+      nvalid = (p == 0) ? ski_round_up(n, 1ll << nb) : n_pad;
+      if (nvalid > n_pad) nvalid = n_pad;
+      Qin = Qo;
+      lo += nb;
+    }
+  }
+  return SKI_OK;
+}

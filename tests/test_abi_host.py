@@ -1,0 +1,96 @@
+"""C ABI: the library builds for sm_103a, loads, exports every declared entry
+point, and rejects bad arguments on the host (no GPU needed)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "skills.h")
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="nvcc not available")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2105_11815_gb300 import build
+    build.build()
+    import paper_2105_11815_gb300 as pkg
+    return pkg
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ski_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    h = ctypes.CDLL(lib.lib_path)
+    for n in names:
+        assert hasattr(h, n), n
+    assert set(names) == set(lib._SIGS), set(names) ^ set(lib._SIGS)
+
+
+def test_host_only_entry_points(lib):
+    assert lib.ski_version() == 100
+    assert lib.ski_status_string(0) == "SKI_OK"
+    assert "workspace" in lib.ski_status_string(2)
+    assert lib.ski_status_string(99) == "unknown ski_status"
+    o = lib.ski_opts_default(m=10)
+    assert (o.s, o.m, o.tau_a, o.tau_r, o.it_max, o.rcond) == (1, 10, 1e-8, 1e-6, 10000, 1e-12)
+
+
+def _fake_dense(lib, n, d):
+    return lib.ski_matrix(kind=lib.SKI_DENSE, n=n, d=d, ld=d, val=0x1000, rowptr=None, colidx=None, nnz=0)
+
+
+def test_argument_errors_before_launch(lib):
+    L = lib.lib()
+    # s > m, m >= 2^31, n < 0 rejected without touching the device
+    assert L.ski_hash_indices(1, 5, 4, 10, None, None, None) == 1
+    assert L.ski_hash_indices(1, 1, 1 << 31, 10, None, None, None) == 1
+    assert L.ski_hash_indices(1, 1, 4, -1, None, None, None) == 1
+    assert L.ski_hash_indices(1, 1, 4, 0, None, None, None) == 0  # empty: nothing to do
+    A = _fake_dense(lib, 100, 10)
+    bad = lib.ski_opts_default(m=5, s=1)          # m < d
+    x = ctypes.c_void_p(0x2000)
+    info = lib.ski_info()
+    assert L.ski_solve(ctypes.byref(A), x, ctypes.byref(bad), x, None, ctypes.byref(info), None, 0, None) == 1
+    ok = lib.ski_opts_default(m=20, s=2)
+    need = L.ski_solve_workspace_size(ctypes.byref(A), ctypes.byref(ok))
+    assert need > 0
+    assert L.ski_solve(ctypes.byref(A), x, ctypes.byref(ok), x, None, ctypes.byref(info), x, need - 1, None) == 2
+    assert info.status == 2
+    prem = lib.ski_opts_default(m=20, s=1, premix=1, n_pad=96)  # not a power of two
+    assert L.ski_sketch_workspace_size(ctypes.byref(A), 1, ctypes.byref(prem)) == 0
+    csr = lib.ski_matrix(kind=lib.SKI_CSR, n=100, d=10, ld=0, val=0x1000, rowptr=0x1000, colidx=0x1000, nnz=5)
+    prem2 = lib.ski_opts_default(m=20, s=1, premix=1)
+    assert L.ski_sketch_workspace_size(ctypes.byref(csr), 1, ctypes.byref(prem2)) == 0  # premix is dense-only
+    assert L.ski_precondition(10, 20, 1, x, 21, 0, x, 20, None, None, None, x, 1 << 30, None) == 1  # m < d
+
+
+def test_workspace_queries_are_consistent(lib):
+    L = lib.lib()
+    A = _fake_dense(lib, 50000, 4000)
+    o = lib.ski_opts_default(m=8000, s=2, premix=1, n_pad=65536)
+    sk = L.ski_sketch_workspace_size(ctypes.byref(A), 1, ctypes.byref(o))
+    so = L.ski_solve_workspace_size(ctypes.byref(A), ctypes.byref(o))
+    assert 0 < sk < so
+    # premix intermediates: two int64 planes of n_pad x 4032 plus the FP64 output
+    assert sk >= 3 * 65536 * 4001 * 8
+    o32 = lib.ski_opts_default(m=8000, s=2, premix=1, n_pad=65536, sketch_dtype=lib.SKI_F32, qr_dtype=lib.SKI_F32)
+    assert L.ski_sketch_workspace_size(ctypes.byref(A), 1, ctypes.byref(o32)) < sk
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    import paper_2105_11815_gb300 as pkg
+    monkeypatch.setattr(pkg, "_lib", None)
+    monkeypatch.setattr(pkg, "lib_path", "/nonexistent/libskills.so")
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        pkg.lib()

@@ -1,0 +1,183 @@
+"""GPU parity of the sketch, premix, QR and R^{-1} kernels against the oracle.
+
+Tolerances: hash rows/signs bit-exact; FP64 sketch and premix <= 1e-12
+relative Frobenius (the method's FP64 target); FP32 <= 1e-5, BF16 <= 1e-2
+(unit roundoff of the storage type times a small growth factor); R <= 1e-12
+relative to ||R|| after normalising row signs (Householder signs are arbitrary).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import hashing, qr as oqr, sketch as osk, wht as owht
+from paper_2105_11815_gb300 import workloads
+from gpu_util import cuda, rel_fro, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("seed,s,m,n", [(1, 1, 512, 4096), (2, 2, 7, 10001), (3, 3, 5, 777), (4, 8, 9, 3000),
+                                        (5, 2, 40000, 1_000_003), (6, 4, 4, 100)])
+def test_hash_indices_bit_exact(seed, s, m, n):
+    torch, pkg = cuda()
+    idx = torch.empty(n * s, dtype=torch.int32, device="cuda")
+    sg = torch.empty(n * s, dtype=torch.int8, device="cuda")
+    pkg.ski_hash_indices(seed, s, m, n, idx, sg)
+    ri, rs = hashing.hash_table(seed, s, m, n)
+    assert np.array_equal(idx.cpu().numpy().reshape(n, s), ri)
+    assert np.array_equal(sg.cpu().numpy().reshape(n, s), rs)
+
+
+def test_premix_signs_bit_exact():
+    torch, pkg = cuda()
+    D = torch.empty(65537, dtype=torch.int8, device="cuda")
+    pkg.ski_premix_signs(20210525, 65537, D)
+    assert np.array_equal(D.cpu().numpy(), hashing.premix_signs(20210525, 65537))
+
+
+def _sketch(torch, pkg, A, b, **kw):
+    n, d = A.shape
+    At = to_dev(torch, A)
+    bt = to_dev(torch, b) if b is not None else None
+    o = pkg.ski_opts_default(**kw)
+    dt = {0: torch.float64, 1: torch.float32, 2: torch.bfloat16}[o.sketch_dtype]
+    ncols = d + (b is not None)
+    ld = ncols + 3
+    SA = torch.full((o.m, ld), float("nan"), dtype=dt, device="cuda")
+    pkg.ski_sketch_hash(pkg.dense_matrix(At), bt, o, SA, ld)
+    return SA[:, :ncols].double().cpu().numpy()
+
+
+@pytest.mark.parametrize("n,d,m,s", [(4096, 256, 512, 1), (3001, 37, 100, 3), (5000, 300, 310, 2),
+                                     (64, 1, 64, 1), (1, 5, 5, 2)])
+def test_dense_sketch_fp64(n, d, m, s):
+    torch, pkg = cuda()
+    A, b, _ = workloads.gaussian_lls(n, d, seed=n + d)
+    got = _sketch(torch, pkg, A, b, m=m, s=s, seed=11)
+    want = osk.sketch_rows(11, s, m, A, b)
+    assert rel_fro(got, want) <= 1e-12
+
+
+def test_dense_sketch_equals_explicit_S_times_A():
+    torch, pkg = cuda()
+    A, b, _ = workloads.gaussian_lls(300, 9, seed=1)
+    S = osk.s_hashing_matrix(5, 2, 31, 300)
+    got = _sketch(torch, pkg, A, b, m=31, s=2, seed=5)
+    assert rel_fro(got[:, :9], S @ A) <= 1e-12
+    assert rel_fro(got[:, 9], S @ b) <= 1e-12
+
+
+def test_dense_sketch_extreme_scales_and_determinism():
+    torch, pkg = cuda()
+    g = np.random.default_rng(3)
+    A = g.standard_normal((2000, 40)) * np.exp(g.uniform(-60, 60, size=(2000, 1)))  # rows span 1e-26..1e26
+    got1 = _sketch(torch, pkg, A, None, m=100, s=2, seed=9)
+    got2 = _sketch(torch, pkg, A, None, m=100, s=2, seed=9)
+    assert np.array_equal(got1, got2)
+    want = osk.sketch_rows(9, 2, 100, A)
+    # per-entry relative error against the exactly rounded sum magnitude
+    assert np.max(np.abs(got1 - want) / (np.abs(want) + 1e-300)) <= 1e-12
+
+
+@pytest.mark.parametrize("dt,tol", [(1, 1e-5), (2, 1e-2)])
+def test_dense_sketch_low_precision(dt, tol):
+    torch, pkg = cuda()
+    A, b, _ = workloads.gaussian_lls(4096, 100, seed=2)
+    got = _sketch(torch, pkg, A, b, m=256, s=2, seed=3, sketch_dtype=dt)
+    assert rel_fro(got, osk.sketch_rows(3, 2, 256, A, b)) <= tol
+
+
+def test_csr_sketch_fp64():
+    torch, pkg = cuda()
+    rp, ci, v, b = workloads.csr_heavy_rows(20000, 300, seed=4, nnz_row=8, heavy_frac=0.002, heavy_nnz=200)
+    A = sp.csr_matrix((v, ci, rp), shape=(20000, 300))
+    o = pkg.ski_opts_default(m=600, s=2, seed=13)
+    SA = torch.empty(600, 301, dtype=torch.float64, device="cuda")
+    keep = (to_dev(torch, rp), to_dev(torch, ci), to_dev(torch, v))
+    M = pkg.csr_matrix(keep[0], keep[1], keep[2], 20000, 300)
+    pkg.ski_sketch_hash(M, to_dev(torch, b), o, SA, 301)
+    assert rel_fro(SA.cpu().numpy(), osk.sketch_rows(13, 2, 600, A, b)) <= 1e-12
+
+
+@pytest.mark.parametrize("n,d,npad", [(3000, 7, 4096), (20000, 33, 32768), (1, 3, 1), (2, 2, 2), (700, 5, 1024),
+                                      (130000, 3, 262144)])
+def test_premix_fp64(n, d, npad):
+    torch, pkg = cuda()
+    A, b, _ = workloads.gaussian_lls(n, d, seed=n)
+    At, bt = to_dev(torch, A), to_dev(torch, b)
+    o = pkg.ski_opts_default(seed=77, n_pad=npad)
+    Y = torch.empty(npad, d + 1, dtype=torch.float64, device="cuda")
+    pkg.ski_premix(pkg.dense_matrix(At), bt, o, Y, d + 1)
+    want = owht.premix(77, np.column_stack([A, b]), npad)
+    assert rel_fro(Y.cpu().numpy(), want) <= 1e-12
+
+
+def test_premix_fp32():
+    torch, pkg = cuda()
+    A, b, _ = workloads.gaussian_lls(5000, 20, seed=5)
+    o = pkg.ski_opts_default(seed=1, n_pad=8192, sketch_dtype=pkg.SKI_F32)
+    Y = torch.empty(8192, 21, dtype=torch.float32, device="cuda")
+    pkg.ski_premix(pkg.dense_matrix(to_dev(torch, A)), to_dev(torch, b), o, Y, 21)
+    assert rel_fro(Y.double().cpu().numpy(), owht.premix(1, np.column_stack([A, b]), 8192)) <= 1e-5
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_hrht_sketch_fp64(s):
+    torch, pkg = cuda()
+    A, b = workloads.dense_high_coherence(5000, 50, seed=3)
+    got = _sketch(torch, pkg, A, b, m=120, s=s, seed=21, premix=1, n_pad=8192)
+    want = owht.hrht_sketch(21, s, 120, A, b, 8192)
+    assert rel_fro(got, want) <= 1e-12
+
+
+def test_hrht_sketch_full_size_sampled_columns():
+    # The dense test-set shape: n = 50000, d = 4000, n_pad = 65536, s = 2, m = 2d.
+    # Checked on sampled columns: column c of S_h H D A is S_h H D A[:, c].
+    torch, pkg = cuda()
+    n, d, m = 50000, 4000, 8000
+    A, b = workloads.dense_gaussian(n, d, seed=20210527)
+    got = _sketch(torch, pkg, A, b, m=m, s=2, seed=3, premix=1, n_pad=65536)
+    cols = [0, 1, 1234, 2047, 3999, 4000]
+    Ab = np.column_stack([A[:, cols[:-1]], b])
+    want = owht.hrht_sketch(3, 2, m, Ab, None, 65536)
+    assert rel_fro(got[:, cols], want) <= 1e-12
+
+
+def _signfix(R):
+    return np.sign(np.diag(R))[:, None] * R
+
+
+@pytest.mark.parametrize("m,d,dt", [(512, 256, 0), (1000, 100, 0), (64, 64, 0), (300, 1, 0), (777, 45, 0),
+                                    (2000, 300, 1)])
+def test_precondition_qr(m, d, dt):
+    torch, pkg = cuda()
+    g = np.random.default_rng(m + d)
+    B = g.standard_normal((m, d + 1))
+    tdt = torch.float64 if dt == 0 else torch.float32
+    SA = to_dev(torch, B).to(tdt).contiguous()
+    R = torch.empty(d, d, dtype=torch.float64, device="cuda")
+    qtsb = torch.empty(d, dtype=torch.float64, device="cuda")
+    rank = pkg.ski_precondition(m, d, 1, SA, d + 1, dt, R, d, qtsb)
+    Ro, C = oqr.householder_qr(B, ncols=d)
+    Rg = R.cpu().numpy()
+    tol = 1e-12 if dt == 0 else 1e-5
+    assert rank == d
+    assert rel_fro(_signfix(Rg), _signfix(Ro)) <= tol
+    sg = np.sign(np.diag(Rg)) * np.sign(np.diag(Ro))
+    assert rel_fro(sg * qtsb.cpu().numpy(), C[:, 0]) <= tol * 10
+    assert np.allclose(np.tril(Rg, -1), 0)
+
+
+@pytest.mark.parametrize("d,dt", [(1, 0), (31, 0), (64, 0), (257, 0), (1000, 0), (500, 1)])
+def test_trinv(d, dt):
+    torch, pkg = cuda()
+    g = np.random.default_rng(d)
+    R = np.linalg.qr(g.standard_normal((2 * d + 4, d)), mode="r")  # well conditioned
+    Rt = to_dev(torch, R)
+    M = torch.empty(d, d, dtype=torch.float64, device="cuda")
+    Mt = torch.empty(d, d, dtype=torch.float64, device="cuda")
+    pkg.ski_trinv(d, Rt, d, M, Mt, d, dtype=dt)
+    Mn = M.cpu().numpy()
+    tol = 1e-12 if dt == 0 else 1e-5
+    assert np.linalg.norm(Mn @ R - np.eye(d)) / np.sqrt(d) <= tol
+    assert np.array_equal(Mt.cpu().numpy(), Mn.T)
