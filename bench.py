@@ -37,6 +37,8 @@ WORKLOADS = {
     "dense_50000x7000_hrht_s1_g2": (50000, 7000, 65536, 1, 2.0, "gauss"),
     "dense_50000x4000_coherent_hrht_s2_g2": (50000, 4000, 65536, 2, 2.0, "coh"),
     "dense_4096x256_s1_m512": (4096, 256, 0, 1, 2.0, "lls"),
+    # small case for ncu captures: same kernels, A = 205 MB (larger than L2)
+    "dense_50000x512_hrht_s1_g2": (50000, 512, 65536, 1, 2.0, "gauss"),
 }
 DEFAULT = "dense_50000x4000_hrht_s1_g2"
 

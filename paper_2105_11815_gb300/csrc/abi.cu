@@ -265,6 +265,9 @@ struct SolvePlan {
   // persistent
   double *R, *qtsb, *M, *Mt, *xs, *t, *v, *w, *y, *z, *p, *q, *part, *part_tt, *part_aa;
   LsqrScalars* sc;
+  double *vp, *part_vv;
+  float2* A2;  // double-float copy of a dense A for the LSQR passes
+  int sA;
   int64_t *colptr;
   int32_t* rowidx;
   double* cval;
@@ -306,6 +309,9 @@ size_t plan_solve(const ski_matrix* A, const ski_opts* o, char* base, size_t cap
   P->part_tt = ar.take<double>(P->nblk);
   P->part_aa = ar.take<double>(P->nblk);
   P->sc = ar.take<LsqrScalars>(1);
+  P->vp = ar.take<double>(d);
+  P->part_vv = ar.take<double>(ski_vv_blocks(d));
+  P->A2 = P->csr ? nullptr : ar.take<float2>(n * d);
   if (P->csr) {
     P->colptr = ar.take<int64_t>(d + 1);
     P->rowidx = ar.take<int32_t>(A->nnz);
@@ -366,6 +372,7 @@ struct Events {
 ski_status residual_pass(const ski_matrix* A, const double* b, const double* x, SolvePlan& P, bool want_aa,
                          cudaStream_t st) {
   FusedArgs f{};
+  f.maxexp = (want_aa && A->kind == SKI_DENSE) ? &P.sc->amax_exp : nullptr;
   f.A = A->kind == SKI_DENSE ? A->val : nullptr;
   f.lda = A->ld;
   f.rowptr = A->kind == SKI_CSR ? A->rowptr : nullptr;
@@ -398,37 +405,45 @@ ski_status residual_pass(const ski_matrix* A, const double* b, const double* x, 
   return SKI_OK;
 }
 
+// One LSQR iteration (lsqr_df.cu): K2 pass over A, K3 reduction (q, beta),
+// K4 p = M^T q and v', K1 rotation, v / y / w and z = M v.
 ski_status lsqr_iteration(const ski_matrix* A, SolvePlan& P, cudaStream_t st) {
-  SKI_TRY(ski_trmv_launch(true, P.d, P.M, P.d, P.v, nullptr, P.z, P.sc, st));
-  FusedArgs f{};
-  f.A = A->kind == SKI_DENSE ? A->val : nullptr;
-  f.lda = A->ld;
-  f.rowptr = A->kind == SKI_CSR ? A->rowptr : nullptr;
-  f.colidx = A->colidx;
-  f.val = A->val;
-  f.n = P.n;
-  f.d = P.d;
-  f.z = P.z;
-  f.u = P.t;
-  f.b = nullptr;
-  f.coef_from_scalars = 1;
-  f.t = P.t;
-  f.part = P.part;
-  f.ldp = P.d;
-  f.part_tt = P.part_tt;
-  f.part_aa = nullptr;
-  f.want_aa = 0;
-  f.nblk = P.nblk;
-  f.sc = P.sc;
-  SKI_TRY(ski_fused_launch(f, st));
   if (P.csr) {
+    FusedArgs f{};
+    f.rowptr = A->rowptr;
+    f.colidx = A->colidx;
+    f.val = A->val;
+    f.n = P.n;
+    f.d = P.d;
+    f.z = P.z;
+    f.u = P.t;
+    f.coef_from_scalars = 1;
+    f.t = P.t;
+    f.part_tt = P.part_tt;
+    f.nblk = P.nblk;
+    f.sc = P.sc;
+    SKI_TRY(ski_fused_launch(f, st));
     SKI_TRY(ski_csc_launch(P.d, P.colptr, P.rowidx, P.cval, P.t, P.q, P.sc, st));
-    SKI_TRY(ski_reduce_launch(P.nblk, P.d, nullptr, P.d, P.part_tt, nullptr, P.q, P.sc, 0, st));
+    SKI_TRY(ski_reduce_par_launch(P.nblk, P.d, nullptr, P.part_tt, P.q, P.sc, st));
   } else {
-    SKI_TRY(ski_reduce_launch(P.nblk, P.d, P.part, P.d, P.part_tt, nullptr, P.q, P.sc, 0, st));
+    DfArgs f{};
+    f.A2 = P.A2;
+    f.n = P.n;
+    f.d = P.d;
+    f.sA = P.sA;
+    f.z = P.z;
+    f.u = P.t;
+    f.coef_from_scalars = 1;
+    f.t = P.t;
+    f.part = P.part;
+    f.part_tt = P.part_tt;
+    f.nblk = P.nblk;
+    f.sc = P.sc;
+    SKI_TRY(ski_fused_df_launch(f, st));
+    SKI_TRY(ski_reduce_par_launch(P.nblk, P.d, P.part, P.part_tt, P.q, P.sc, st));
   }
-  SKI_TRY(ski_trmv_launch(false, P.d, P.Mt, P.d, P.q, nullptr, P.p, P.sc, st));
-  SKI_TRY(ski_update_launch(P.d, P.p, P.v, P.w, P.y, P.sc, 0, st));
+  SKI_TRY(ski_trmv_lower_vp_launch(P.d, P.Mt, P.q, P.v, P.vp, P.part_vv, P.sc, 0, st));
+  SKI_TRY(ski_trmv_upper_update_launch(P.d, P.M, P.vp, P.part_vv, P.v, P.w, P.y, P.z, P.sc, 0, st));
   return SKI_OK;
 }
 
@@ -475,6 +490,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   memset(&hs, 0, sizeof(hs));
   hs.tau_r = o->tau_r;
   hs.it_max = o->it_max;
+  hs.amax_exp = 0;
 
   SKI_CUDA_TRY(cudaEventRecord(ev.e[0], st));
   // Step 1: sketch [SA | Sb]
@@ -530,6 +546,11 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
     if (info) info->status = SKI_ENONFINITE;
     return SKI_ENONFINITE;
   }
+  if (!P.csr) {
+    // A2 = A * 2^-sA with max|A2| < 1, in (hi, lo) float pairs
+    P.sA = hs.amax_exp > 0 ? hs.amax_exp - 1022 : 0;
+    SKI_TRY(ski_split_a_launch(P.n, d, A->val, A->ld, P.sA, P.A2, st));
+  }
   int64_t iters_total = 0;
   int restarts = 0;
   double metric = 0.0, lsqr_test = 0.0;
@@ -548,19 +569,20 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
       LsqrScalars init = hs;
       init.iters = 0;
       init.it_max = o->it_max - iters_total;
-      init.done = 0;
+      init.flag_a = 0;
+      init.flag_b = 0;
       init.conv = 0;
       init.tau_r = o->tau_r;
       SKI_CUDA_TRY(cudaMemcpyAsync(P.sc, &init, sizeof(init), cudaMemcpyHostToDevice, st));
-      SKI_TRY(ski_trmv_launch(false, d, P.Mt, d, P.q, nullptr, P.p, nullptr, st));
-      SKI_TRY(ski_update_launch(d, P.p, P.v, P.w, P.y, P.sc, 1, st));
+      SKI_TRY(ski_trmv_lower_vp_launch(d, P.Mt, P.q, P.v, P.vp, P.part_vv, P.sc, 1, st));
+      SKI_TRY(ski_trmv_upper_update_launch(d, P.M, P.vp, P.part_vv, P.v, P.w, P.y, P.z, P.sc, 1, st));
       const int CHUNK = 8;
       int64_t polled = 0;
       for (;;) {
         for (int k = 0; k < CHUNK; ++k) SKI_TRY(lsqr_iteration(A, P, st));
         polled += CHUNK;
         SKI_TRY(read_scalars(P, &hs, st));
-        if (hs.done) break;
+        if (hs.flag_a) break;
         if (polled > o->it_max + CHUNK) break;
       }
       iters_total += hs.iters;
@@ -746,7 +768,7 @@ extern "C" ski_status ski_solve_adjoint(const ski_matrix* A, const double* b, co
     SKI_CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, st));
     SKI_CUDA_TRY(cudaStreamSynchronize(st));
     polled += 8;
-    if (hs.done || polled > hs.it_max + 16) break;
+    if (hs.flag_a || polled > hs.it_max + 16) break;
   }
   // lambda = R^{-1} z; db = A lambda; r = b - A x; dA = r lambda^T - (A lambda) x^T
   SKI_TRY(ski_trmv_launch(true, d, P.M, d, P.z, nullptr, P.lam, nullptr, st));

@@ -110,18 +110,31 @@ __device__ __forceinline__ long long fx_quant(double v, int E, bool neg) {
   return negative ? -(long long)q : (long long)q;
 }
 
+// The double nearest to S * 2^X (round to nearest even), using integer
+// operations only: on GB300 the int64 -> FP64 conversion instruction runs on
+// the 1/64-rate FP64 pipe.  |S| < 2^63.
+__device__ __forceinline__ double fx_i64_to_double(long long S, int X) {
+  if (S == 0) return 0.0;
+  const unsigned long long sign = S < 0 ? (1ull << 63) : 0ull;
+  unsigned long long u = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+  const int lz = __clzll(u);
+  u <<= lz;  // leading one at bit 63
+  unsigned long long m = u >> 11;
+  const unsigned long long rem = u & 0x7FFull;
+  m += (rem > 0x400ull || (rem == 0x400ull && (m & 1ull))) ? 1ull : 0ull;
+  int e = 63 - lz + X;  // S * 2^X = m * 2^(e - 52)
+  if (m >> 53) {
+    m >>= 1;
+    e += 1;
+  }
+  const int be = e + 1023;
+  if (be < 1 || be > 2046) return ldexp(__ll2double_rn(S), X);  // subnormal or overflow: rare
+  return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
 // The double nearest to S * 2^(E - 1075 - FX_LIFT - extra).
 __device__ __forceinline__ double fx_to_double(long long S, int E, int extra = 0) {
-  if (S == 0) return 0.0;
-  double v = __ll2double_rn(S);  // exact up to one rounding
-  long long bits = __double_as_longlong(v);
-  int e = (int)((bits >> 52) & 0x7FF);
-  int ne = e + (E - 1075 - FX_LIFT - extra);
-  if (ne >= 1 && ne <= 2046) {
-    bits = (bits & ~(0x7FFll << 52)) | ((long long)ne << 52);
-    return __longlong_as_double(bits);
-  }
-  return ldexp(v, E - 1075 - FX_LIFT - extra);  // out of the normal range: rare
+  return fx_i64_to_double(S, E - 1075 - FX_LIFT - extra);
 }
 
 // Running exact sum with an adaptive block exponent: a larger addend raises

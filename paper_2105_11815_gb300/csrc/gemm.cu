@@ -15,15 +15,19 @@ template <class T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(
     int64_t M, int64_t N, int64_t K, int64_t kchunk, T alpha, const T* __restrict__ A, int64_t sa_m,
     int64_t sa_k, const T* __restrict__ B, int64_t sb_k, int64_t sb_n, T beta, T* __restrict__ C, int64_t ldc,
-    int64_t c_zstride) {
+    int64_t c_zstride, int tri) {
   constexpr int NT = (BM / TM) * (BN / TN);
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
   const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
-  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
-  const int64_t kend = min(K, kbeg + kchunk);
+  int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  int64_t kend = min(K, kbeg + kchunk);
+  // tri bit 0: A upper triangular (A[i,k] = 0 for k < i); bit 1: B upper
+  // triangular (B[k,j] = 0 for k > j).  Skip the k-range that is all zero.
+  if (tri & 1) kbeg = max(kbeg, m0 - (m0 % BK));
+  if (tri & 2) kend = min(kend, n0 + BN);
   C += (int64_t)blockIdx.z * c_zstride;
   T acc[TM][TN];
 #pragma unroll
@@ -82,18 +86,18 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(
 template <class T>
 ski_status ski_gemm_ex(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t sa_m, int64_t sa_k,
                        const T* B, int64_t sb_k, int64_t sb_n, T beta, T* C, int64_t ldc, int splits,
-                       int64_t c_zstride, cudaStream_t st) {
+                       int64_t c_zstride, cudaStream_t st, int tri) {
   if (M <= 0 || N <= 0) return SKI_OK;
   constexpr int BK = sizeof(T) == 8 ? 16 : 16;
   int64_t kchunk = ski_round_up(ski_cdiv(K > 0 ? K : 1, splits), BK);
   if (M <= 32) {
     dim3 grid((unsigned)ski_cdiv(N, 64), (unsigned)ski_cdiv(M, 32), (unsigned)splits);
     k_gemm<T, 32, 64, BK, 2, 4><<<grid, 256, 0, st>>>(M, N, K, kchunk, alpha, A, sa_m, sa_k, B, sb_k, sb_n, beta,
-                                                      C, ldc, c_zstride);
+                                                      C, ldc, c_zstride, tri);
   } else {
     dim3 grid((unsigned)ski_cdiv(N, 64), (unsigned)ski_cdiv(M, 64), (unsigned)splits);
     k_gemm<T, 64, 64, BK, 4, 4><<<grid, 256, 0, st>>>(M, N, K, kchunk, alpha, A, sa_m, sa_k, B, sb_k, sb_n, beta,
-                                                      C, ldc, c_zstride);
+                                                      C, ldc, c_zstride, tri);
   }
   SKI_LAUNCH_CHECK();
   return SKI_OK;
@@ -102,7 +106,13 @@ ski_status ski_gemm_ex(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int
 template <class T>
 ski_status ski_gemm(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t sa_m, int64_t sa_k,
                     const T* B, int64_t sb_k, int64_t sb_n, T beta, T* C, int64_t ldc, cudaStream_t st) {
-  return ski_gemm_ex<T>(M, N, K, alpha, A, sa_m, sa_k, B, sb_k, sb_n, beta, C, ldc, 1, 0, st);
+  return ski_gemm_ex<T>(M, N, K, alpha, A, sa_m, sa_k, B, sb_k, sb_n, beta, C, ldc, 1, 0, st, 0);
+}
+
+template <class T>
+ski_status ski_gemm_tri(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t sa_m, int64_t sa_k,
+                        const T* B, int64_t sb_k, int64_t sb_n, T beta, T* C, int64_t ldc, int tri, cudaStream_t st) {
+  return ski_gemm_ex<T>(M, N, K, alpha, A, sa_m, sa_k, B, sb_k, sb_n, beta, C, ldc, 1, 0, st, tri);
 }
 
 template ski_status ski_gemm<double>(int64_t, int64_t, int64_t, double, const double*, int64_t, int64_t,
@@ -111,7 +121,11 @@ template ski_status ski_gemm<float>(int64_t, int64_t, int64_t, float, const floa
                                     const float*, int64_t, int64_t, float, float*, int64_t, cudaStream_t);
 template ski_status ski_gemm_ex<double>(int64_t, int64_t, int64_t, double, const double*, int64_t, int64_t,
                                         const double*, int64_t, int64_t, double, double*, int64_t, int, int64_t,
-                                        cudaStream_t);
+                                        cudaStream_t, int);
 template ski_status ski_gemm_ex<float>(int64_t, int64_t, int64_t, float, const float*, int64_t, int64_t,
                                        const float*, int64_t, int64_t, float, float*, int64_t, int, int64_t,
-                                       cudaStream_t);
+                                       cudaStream_t, int);
+template ski_status ski_gemm_tri<double>(int64_t, int64_t, int64_t, double, const double*, int64_t, int64_t,
+                                         const double*, int64_t, int64_t, double, double*, int64_t, int, cudaStream_t);
+template ski_status ski_gemm_tri<float>(int64_t, int64_t, int64_t, float, const float*, int64_t, int64_t,
+                                        const float*, int64_t, int64_t, float, float*, int64_t, int, cudaStream_t);

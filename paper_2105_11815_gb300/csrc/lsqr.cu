@@ -35,7 +35,7 @@ template <bool UPPER>
 __global__ void __launch_bounds__(256) k_trmv(int64_t d, const double* __restrict__ M, int64_t ldm,
                                               const double* __restrict__ x, const double* __restrict__ add,
                                               double* __restrict__ y, const LsqrScalars* __restrict__ sc) {
-  if (sc && sc->done) return;
+  if (sc && sc->flag_a) return;
   const int lane = threadIdx.x & 31;
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (row >= d) return;
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(512) k_fused_dense(FusedArgs f) {
   __shared__ double red[RR][NT / 32];
   __shared__ double tsh[RR];
   const LsqrScalars* sc = f.sc;
-  if (sc && sc->done) return;
+  if (sc && sc->flag_a) return;
   double ca = f.ca, cu = f.cu, cb = f.cb;
   if (f.coef_from_scalars) {
     ca = 1.0;
@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(512) k_fused_dense(FusedArgs f) {
   const int64_t r0 = (int64_t)blockIdx.x * f.rows_per;
   const int64_t r1 = min(f.n, r0 + f.rows_per);
   double zr[CPT], acc[CPT], aa = 0.0, tt = 0.0;
+  int emax = 0;
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
     const int64_t c = tid + (int64_t)k * NT;
@@ -81,6 +82,12 @@ __global__ void __launch_bounds__(512) k_fused_dense(FusedArgs f) {
         const int64_t c = tid + (int64_t)k * NT;
         a[r][k] = (j0 + r < r1 && c < f.d) ? __ldcs(&f.A[(j0 + r) * f.lda + c]) : 0.0;
       }
+    if (f.maxexp) {
+#pragma unroll
+      for (int r = 0; r < RR; ++r)
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) emax = max(emax, (int)((__double_as_longlong(a[r][k]) >> 52) & 0x7FF));
+    }
     double p[RR];
 #pragma unroll
     for (int r = 0; r < RR; ++r) {
@@ -131,12 +138,16 @@ __global__ void __launch_bounds__(512) k_fused_dense(FusedArgs f) {
     if (tid == 0) f.part_aa[blockIdx.x] = s;
   }
   if (tid == 0) f.part_tt[blockIdx.x] = tt;
+  if (f.maxexp) {
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if (lane == 0) atomicMax(f.maxexp, emax);
+  }
 }
 
 // CSR pass 1: t_j = ca (A_j z) + cu u_j + cb b_j, warp per row; per-CTA ||t||^2, ||A||_F^2.
 __global__ void __launch_bounds__(256) k_csr_rows(FusedArgs f) {
   const LsqrScalars* sc = f.sc;
-  if (sc && sc->done) return;
+  if (sc && sc->flag_a) return;
   double ca = f.ca, cu = f.cu, cb = f.cb;
   if (f.coef_from_scalars) {
     ca = 1.0;
@@ -184,7 +195,7 @@ __global__ void __launch_bounds__(256) k_csc_cols(int64_t d, const int64_t* __re
                                                   const int32_t* __restrict__ rowidx, const double* __restrict__ cval,
                                                   const double* __restrict__ t, double* __restrict__ q,
                                                   const LsqrScalars* __restrict__ sc) {
-  if (sc && sc->done) return;
+  if (sc && sc->flag_a) return;
   const int lane = threadIdx.x & 31;
   const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (c >= d) return;
@@ -199,7 +210,7 @@ __global__ void __launch_bounds__(256) k_csc_cols(int64_t d, const int64_t* __re
 __global__ void k_reduce_cols(int nblk, int64_t d, const double* __restrict__ part, int64_t ldp,
                               const double* __restrict__ part_tt, const double* __restrict__ part_aa,
                               double* __restrict__ q, LsqrScalars* __restrict__ sc, int mode) {
-  if (sc->done && mode == 0) return;
+  if (sc->flag_a && mode == 0) return;
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (part && c < d) {
     double s = 0.0;
@@ -216,79 +227,6 @@ __global__ void k_reduce_cols(int nblk, int64_t d, const double* __restrict__ pa
       for (int b = 0; b < nblk; ++b) a += part_aa[b];
       sc->anorm_f2 = a;
     }
-  }
-}
-
-// LSQR bookkeeping, one CTA.  start = 1: initialise from beta_1 u_1 = r0 and
-// p = M^T A^T r0; else one iteration's update.
-__global__ void __launch_bounds__(1024) k_lsqr_update(int64_t d, const double* __restrict__ p, double* __restrict__ v,
-                                                      double* __restrict__ w, double* __restrict__ y,
-                                                      LsqrScalars* __restrict__ sc, int start) {
-  __shared__ double sh[32];
-  __shared__ double s_alpha;
-  if (!start && sc->done) return;
-  const double beta = sc->beta_new;
-  const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
-  double ss = 0.0;
-  for (int64_t c = threadIdx.x; c < d; c += blockDim.x) {
-    double vn = p[c] * ib;
-    if (!start) vn = fma(-beta, v[c], vn);
-    v[c] = vn;
-    ss = fma(vn, vn, ss);
-  }
-  ss = block_sum(ss, sh);
-  if (threadIdx.x == 0) s_alpha = sqrt(ss);
-  __syncthreads();
-  const double alpha = s_alpha;
-  const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
-  if (start) {
-    for (int64_t c = threadIdx.x; c < d; c += blockDim.x) {
-      const double vn = v[c] * ia;
-      v[c] = vn;
-      w[c] = vn;
-      y[c] = 0.0;
-    }
-    if (threadIdx.x == 0) {
-      sc->alpha = alpha;
-      sc->beta = beta;
-      sc->phibar = beta;
-      sc->rhobar = alpha;
-      sc->anorm2 = 0.0;
-      sc->test = 1.0;
-      sc->coef = beta > 0.0 ? alpha / beta : 0.0;
-      sc->done = (alpha * beta == 0.0) ? 1 : 0;
-      sc->conv = sc->done;
-    }
-    return;
-  }
-  const double alpha_old = sc->alpha;
-  const double rho = hypot(sc->rhobar, beta);
-  const double cs = sc->rhobar / rho, sn = beta / rho;
-  const double theta = sn * alpha;
-  const double phi = cs * sc->phibar;
-  const double phibar = sn * sc->phibar;
-  const double c1 = phi / rho, c2 = theta / rho;
-  for (int64_t c = threadIdx.x; c < d; c += blockDim.x) {
-    const double vn = v[c] * ia;
-    v[c] = vn;
-    const double wc = w[c];
-    y[c] = fma(c1, wc, y[c]);
-    w[c] = fma(-c2, wc, vn);
-  }
-  if (threadIdx.x == 0) {
-    const double anorm2 = sc->anorm2 + alpha_old * alpha_old + beta * beta;
-    const double test = anorm2 > 0.0 ? alpha * fabs(cs) / sqrt(anorm2) : 0.0;
-    sc->anorm2 = anorm2;
-    sc->rhobar = -cs * alpha;
-    sc->phibar = phibar;
-    sc->alpha = alpha;
-    sc->beta = beta;
-    sc->coef = beta > 0.0 ? alpha / beta : 0.0;
-    sc->test = phibar > 0.0 ? test : 0.0;
-    sc->iters += 1;
-    const bool conv = sc->test <= sc->tau_r || alpha == 0.0 || beta == 0.0;
-    sc->conv = conv ? 1 : 0;
-    if (conv || sc->iters >= sc->it_max) sc->done = 1;
   }
 }
 
@@ -323,12 +261,12 @@ __global__ void __launch_bounds__(1024) k_cg(int64_t d, const double* __restrict
       sc->cg_rr = s;
       sc->cg_rr0 = s;
       sc->iters = 0;
-      sc->done = (s == 0.0) ? 1 : 0;
-      sc->conv = sc->done;
+      sc->flag_a = (s == 0.0) ? 1 : 0;
+      sc->conv = sc->flag_a;
     }
     return;
   }
-  if (sc->done) return;
+  if (sc->flag_a) return;
   double pq = 0.0;
   for (int64_t c = threadIdx.x; c < d; c += blockDim.x) pq = fma(p[c], q[c], pq);
   pq = block_sum(pq, sh);
@@ -351,7 +289,7 @@ __global__ void __launch_bounds__(1024) k_cg(int64_t d, const double* __restrict
     sc->iters += 1;
     const bool conv = rr <= sc->cg_tol2 * sc->cg_rr0 || pq <= 0.0;
     sc->conv = conv ? 1 : 0;
-    if (conv || sc->iters >= sc->it_max) sc->done = 1;
+    if (conv || sc->iters >= sc->it_max) sc->flag_a = 1;
   }
 }
 
@@ -427,13 +365,6 @@ ski_status ski_reduce_launch(int nblk, int64_t d, const double* part, int64_t ld
                              const double* part_aa, double* q, LsqrScalars* sc, int mode, cudaStream_t st) {
   k_reduce_cols<<<(unsigned)std::max<int64_t>(1, ski_cdiv(d, 256)), 256, 0, st>>>(nblk, d, part, ldp, part_tt, part_aa, q,
                                                                             sc, mode);
-  SKI_LAUNCH_CHECK();
-  return SKI_OK;
-}
-
-ski_status ski_update_launch(int64_t d, const double* p, double* v, double* w, double* y, LsqrScalars* sc, int start,
-                             cudaStream_t st) {
-  k_lsqr_update<<<1, 1024, 0, st>>>(d, p, v, w, y, sc, start);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }

@@ -1,0 +1,413 @@
+// The LSQR iteration of Step 4 laid out for GB300, whose FP64 pipe issues 2
+// DFMA per clock per SM (1/64 of FP32).  A plain FP64 pass over A would be
+// bound by those 2 DFMA per element, at 3x the HBM time, so the dense pass
+// runs in double-float arithmetic on the FP32 pipe instead:
+//
+//  * A is copied once per solve into A2 = A * 2^-sA as (hi, lo) float pairs
+//    (hi = the leading 24 significant bits, lo = the next 24), 8 bytes per
+//    element like FP64: 48 significant bits, scaled so that max|A2| < 1.
+//  * products use the error-free transformation p + e = ah * bh (e from an
+//    FMA), sums use TwoSum, so every multiply-add keeps ~2^-47 relative
+//    accuracy -- far below the 1e-10 acceptance tolerance -- and the only
+//    FP64 operations left are per row (t_j) and per column (partials).
+//
+// One iteration is four launches (no host synchronisation):
+//   K2  t = A z - (alpha/beta) t, with per-CTA partials of A^T t and ||t||^2
+//   K3  q = A^T t and beta = ||t|| from the partials (fixed order)
+//   K4  p = M^T q, v' = p / beta - beta v, per-CTA partials of ||v'||^2
+//   K1  alpha = ||v'||, the plane rotation, v = v'/alpha, y and w updates,
+//       and z = M v for the next K2; CTA 0 writes the scalars and the
+//       Eq. TC-lsqr stop flag.
+// Kernels never read a flag written by another CTA of the same launch: K1
+// reads flag_b and writes flag_a; K2, K3, K4 read flag_a; K3 copies it to
+// flag_b for the next K1.
+#include "common.cuh"
+#include "lsqr_impl.cuh"
+
+namespace {
+
+// ------------------------------------------------ error-free FP32 arithmetic
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (Sh, Sl) += (ah + al) * (bh + bl), dropping al * bl (below 2^-48).
+__device__ __forceinline__ void df_mac(float& Sh, float& Sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float e = __fmaf_rn(ah, bh, -p);
+  const float x = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
+  float s, err;
+  two_sum(Sh, p, s, err);
+  Sh = s;
+  Sl = __fadd_rn(Sl, __fadd_rn(err, __fadd_rn(e, x)));
+}
+__device__ __forceinline__ void df_add(float& Sh, float& Sl, float bh, float bl) {
+  float s, e;
+  two_sum(Sh, bh, s, e);
+  Sh = s;
+  Sl = __fadd_rn(Sl, __fadd_rn(e, bl));
+}
+__device__ __forceinline__ void df_warp_sum(float& h, float& l) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+    df_add(h, l, oh, ol);
+  }
+}
+// (hi, lo) float pair of x * 2^-s (x FP64): two conversions and one FP64 add.
+__device__ __forceinline__ float2 df_split(double x, int s) {
+  const double xs = ldexp(x, -s);
+  const float h = __double2float_rn(xs);
+  const float l = __double2float_rn(xs - (double)h);
+  return make_float2(h, l);
+}
+
+__device__ __forceinline__ bool flag_set(const volatile int* f) { return *f != 0; }
+
+// A2[j, c] = split(A[j, c] * 2^-sA) using integer operations only: hi keeps
+// the top 24 significant bits (exact in FP32), lo the remaining 29 bits
+// rounded to 24.  Values below 2^-126 * 2^sA flush to zero.
+__global__ void k_split_a(int64_t n, int64_t d, const double* __restrict__ A, int64_t lda, int sA,
+                          float2* __restrict__ A2) {
+  const int64_t j = blockIdx.y;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < d; c += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(A[j * lda + c]);
+    const int e = (int)((bits >> 52) & 0x7FF);
+    const int es = e - sA;  // biased exponent after scaling by 2^-sA
+    float h = 0.f, l = 0.f;
+    if (e != 0 && es > 0 && es - 1023 + 127 >= 1) {
+      const unsigned long long hb = (bits & 0xFFFFFFFFE0000000ull) - ((unsigned long long)sA << 52);
+      h = __double2float_rn(__longlong_as_double((long long)hb));
+      const unsigned int low = (unsigned int)(bits & 0x1FFFFFFFull);
+      const int le = es - 1075 + 127;  // 2^(es - 1075) as a float exponent field
+      if (low != 0 && le >= 1) {
+        l = __uint2float_rn(low) * __int_as_float(le << 23);
+        if (bits >> 63) l = -l;
+      }
+    }
+    A2[j * d + c] = make_float2(h, l);
+  }
+}
+
+// K2: double-float fused pass.  Thread tid owns columns tid + k*512 (k < CPT).
+template <int CPT, int RR>
+__global__ void __launch_bounds__(512) k_fused_df(DfArgs f) {
+  constexpr int NT = 512, NW = NT / 32;
+  __shared__ float2 red[RR][NW];
+  __shared__ float2 tsh[RR];
+  __shared__ int s_zexp;
+  LsqrScalars* sc = f.sc;
+  if (sc && flag_set(&sc->flag_a)) return;
+  const double cu = f.coef_from_scalars ? -sc->coef : f.cu;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // scale of z: its largest exponent, so that |z * 2^-sz| < 2
+  if (tid == 0) s_zexp = -2000;
+  __syncthreads();
+  int ez = -2000;
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int64_t c = tid + (int64_t)k * NT;
+    if (c < f.d) {
+      const double zc = f.z[c];
+      if (zc != 0.0) ez = max(ez, (int)((__double_as_longlong(zc) >> 52) & 0x7FF) - 1022);
+    }
+  }
+  atomicMax(&s_zexp, ez);
+  __syncthreads();
+  const int sz = s_zexp == -2000 ? 0 : s_zexp;
+  const int st = f.sA + sz;  // t is carried as t * 2^-st
+  float zh[CPT], zl[CPT], ah_acc[CPT], al_acc[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int64_t c = tid + (int64_t)k * NT;
+    const float2 zz = c < f.d ? df_split(f.z[c], sz) : make_float2(0.f, 0.f);
+    zh[k] = zz.x;
+    zl[k] = zz.y;
+    ah_acc[k] = 0.f;
+    al_acc[k] = 0.f;
+  }
+  const int64_t r0 = (int64_t)blockIdx.x * f.rows_per;
+  const int64_t r1 = min(f.n, r0 + f.rows_per);
+  double tt = 0.0;
+  for (int64_t j0 = r0; j0 < r1; j0 += RR) {
+    float2 a[RR][CPT];
+#pragma unroll
+    for (int r = 0; r < RR; ++r)
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        const int64_t c = tid + (int64_t)k * NT;
+        a[r][k] = (j0 + r < r1 && c < f.d) ? __ldcs(&f.A2[(j0 + r) * f.d + c]) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      float h = 0.f, l = 0.f;
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) df_mac(h, l, a[r][k].x, a[r][k].y, zh[k], zl[k]);
+      df_warp_sum(h, l);
+      if (lane == 0) red[r][wid] = make_float2(h, l);
+    }
+    __syncthreads();
+    if (tid < RR) {
+      const int64_t j = j0 + tid;
+      float h = 0.f, l = 0.f;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) df_add(h, l, red[tid][q].x, red[tid][q].y);
+      float2 ts = make_float2(0.f, 0.f);
+      if (j < r1) {
+        double t = ldexp((double)h + (double)l, st);
+        if (f.u) t = fma(cu, f.u[j], t);
+        f.t[j] = t;
+        tt = fma(t, t, tt);
+        ts = df_split(t, st);
+      }
+      tsh[tid] = ts;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      const float2 t = tsh[r];
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) df_mac(ah_acc[k], al_acc[k], a[r][k].x, a[r][k].y, t.x, t.y);
+    }
+  }
+  // partial A^T t of this CTA: (A2 * 2^sA)^T (t2 * 2^st)
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int64_t c = tid + (int64_t)k * NT;
+    if (c < f.d) f.part[(int64_t)blockIdx.x * f.d + c] = ldexp((double)ah_acc[k] + (double)al_acc[k], f.sA + st);
+  }
+  // ||t||^2: threads tid < RR hold pieces
+  __shared__ double tts[32];
+  if (tid < 32) tts[tid] = tid < RR ? tt : 0.0;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int q = 0; q < RR; ++q) s += tts[q];
+    f.part_tt[blockIdx.x] = s;
+  }
+}
+
+// K3: q[c] = sum_b part[b][c] (8 warps share the CTAs, fixed order), beta;
+// CTA 0 also copies flag_a to flag_b for the next K1 (also once stopped).
+__global__ void __launch_bounds__(256) k_reduce_par(int nblk, int64_t d, const double* __restrict__ part,
+                                                    const double* __restrict__ part_tt, double* __restrict__ q,
+                                                    LsqrScalars* __restrict__ sc) {
+  __shared__ double sh[8][33];
+  const bool skip = sc && flag_set(&sc->flag_a);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (!skip) {
+    const int64_t c = (int64_t)blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (part && c < d)
+      for (int b = wid; b < nblk; b += 8) s += part[(int64_t)b * d + c];
+    sh[wid][lane] = s;
+    __syncthreads();
+    if (wid == 0) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += sh[w][lane];
+      if (part && c < d) q[c] = t;
+    }
+  }
+  if (blockIdx.x == 0 && wid == 1 && sc) {
+    double t = 0.0;
+    if (!skip) {
+      for (int b = lane; b < nblk; b += 32) t += part_tt[b];
+      t = ski_warp_sum(t);
+    }
+    if (lane == 0) {
+      if (!skip) {
+        sc->beta_new = sqrt(t);
+        sc->rnorm2 = t;
+      }
+      sc->flag_b = sc->flag_a;
+    }
+  }
+}
+
+// K4: p = M^T q (Mt lower triangular, warp per row), v' = p/beta - beta v
+// (start: v' = p/beta), per-CTA partial ||v'||^2.
+__global__ void __launch_bounds__(256) k_trmv_lower_vp(int64_t d, const double* __restrict__ Mt,
+                                                       const double* __restrict__ q, const double* __restrict__ v,
+                                                       double* __restrict__ vp, double* __restrict__ part_vv,
+                                                       LsqrScalars* __restrict__ sc, int start) {
+  __shared__ double sv[8];
+  if (!start && flag_set(&sc->flag_a)) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t row = (int64_t)blockIdx.x * 8 + wid;
+  const double beta = sc->beta_new;
+  double vv = 0.0;
+  if (row < d) {
+    const double* mr = Mt + row * d;
+    double acc = 0.0;
+    for (int64_t c = lane; c <= row; c += 32) acc = fma(__ldcs(&mr[c]), q[c], acc);
+    acc = ski_warp_sum(acc);
+    const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+    double x = acc * ib;
+    if (!start) x = fma(-beta, v[row], x);
+    if (lane == 0) vp[row] = x;
+    vv = x * x;
+  }
+  if (lane == 0) sv[wid] = vv;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += sv[w];
+    part_vv[blockIdx.x] = s;
+  }
+}
+
+// K1: alpha = ||v'|| from the K4 partials, LSQR rotation, v/y/w updates for
+// this CTA's rows, z = M v for the next pass.  Warp per row.
+__global__ void __launch_bounds__(256) k_trmv_upper_update(int64_t d, const double* __restrict__ M,
+                                                           const double* __restrict__ vp, int nvv,
+                                                           const double* __restrict__ part_vv, double* __restrict__ v,
+                                                           double* __restrict__ w, double* __restrict__ y,
+                                                           double* __restrict__ z, LsqrScalars* __restrict__ sc,
+                                                           int start) {
+  __shared__ double s_par[4];  // 1/alpha, c1, c2, done
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (!start && flag_set(&sc->flag_b)) return;
+  if (wid == 0) {
+    double s = 0.0;
+    for (int b = lane; b < nvv; b += 32) s += part_vv[b];
+    s = ski_warp_sum(s);
+    if (lane == 0) {
+      const double alpha = sqrt(s);
+      const double ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+      const double beta = sc->beta_new;
+      double c1 = 0.0, c2 = 0.0;
+      int done = 0;
+      if (start) {
+        done = (alpha * beta == 0.0) ? 1 : 0;
+        if (blockIdx.x == 0) {
+          sc->alpha = alpha;
+          sc->beta = beta;
+          sc->phibar = beta;
+          sc->rhobar = alpha;
+          sc->anorm2 = 0.0;
+          sc->test = 1.0;
+          sc->coef = beta > 0.0 ? alpha / beta : 0.0;
+          sc->iters = 0;
+          sc->conv = done;
+          sc->flag_a = done;
+          sc->flag_b = done;
+        }
+      } else {
+        const double alpha_old = sc->alpha, rhobar = sc->rhobar, phibar_old = sc->phibar;
+        const double rho = hypot(rhobar, beta);
+        const double cs = rhobar / rho, sn = beta / rho;
+        const double theta = sn * alpha;
+        const double phi = cs * phibar_old;
+        const double phibar = sn * phibar_old;
+        c1 = phi / rho;
+        c2 = theta / rho;
+        const double anorm2 = sc->anorm2 + alpha_old * alpha_old + beta * beta;
+        const double test = (anorm2 > 0.0 && phibar > 0.0) ? alpha * fabs(cs) / sqrt(anorm2) : 0.0;
+        const long long iters = sc->iters + 1;
+        const bool conv = test <= sc->tau_r || alpha == 0.0 || beta == 0.0;
+        done = (conv || iters >= sc->it_max) ? 1 : 0;
+        if (blockIdx.x == 0) {
+          sc->anorm2 = anorm2;
+          sc->rhobar = -cs * alpha;
+          sc->phibar = phibar;
+          sc->alpha = alpha;
+          sc->beta = beta;
+          sc->coef = beta > 0.0 ? alpha / beta : 0.0;
+          sc->test = test;
+          sc->iters = iters;
+          sc->conv = conv ? 1 : 0;
+          sc->flag_a = done;
+        }
+      }
+      s_par[0] = ia;
+      s_par[1] = c1;
+      s_par[2] = c2;
+      s_par[3] = done;
+    }
+  }
+  __syncthreads();
+  const double ia = s_par[0], c1 = s_par[1], c2 = s_par[2];
+  const bool done = s_par[3] != 0.0;
+  const int64_t row = (int64_t)blockIdx.x * 8 + wid;
+  if (row >= d) return;
+  if (lane == 0) {
+    const double vn = vp[row] * ia;
+    v[row] = vn;
+    if (start) {
+      w[row] = vn;
+      y[row] = 0.0;
+    } else {
+      const double wc = w[row];
+      y[row] = fma(c1, wc, y[row]);
+      w[row] = fma(-c2, wc, vn);
+    }
+  }
+  if (done) return;
+  const double* mr = M + row * d;
+  double acc = 0.0;
+  for (int64_t c = row + lane; c < d; c += 32) acc = fma(__ldcs(&mr[c]), vp[c], acc);
+  acc = ski_warp_sum(acc);
+  if (lane == 0) z[row] = acc * ia;
+}
+
+}  // namespace
+
+ski_status ski_split_a_launch(int64_t n, int64_t d, const double* A, int64_t lda, int sA, float2* A2, cudaStream_t st) {
+  for (int64_t j0 = 0; j0 < n; j0 += 65535) {
+    const int64_t nr = std::min<int64_t>(65535, n - j0);
+    dim3 grid((unsigned)std::min<int64_t>(ski_cdiv(d, 256), 16), (unsigned)nr);
+    k_split_a<<<grid, 256, 0, st>>>(nr, d, A + j0 * lda, lda, sA, A2 + j0 * d);
+    SKI_LAUNCH_CHECK();
+  }
+  return SKI_OK;
+}
+
+bool ski_df_supported(int64_t d) { return d <= SKI_DENSE_DMAX; }
+
+ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
+  DfArgs f = f0;
+  f.rows_per = ski_cdiv(f.n, f.nblk);
+  const int64_t cpt = ski_cdiv(f.d, 512);
+#define SKI_DF_CASE(C, R)                          \
+  if (cpt <= C) {                                  \
+    k_fused_df<C, R><<<f.nblk, 512, 0, st>>>(f);   \
+    SKI_LAUNCH_CHECK();                            \
+    return SKI_OK;                                 \
+  }
+  SKI_DF_CASE(1, 8)
+  SKI_DF_CASE(2, 8)
+  SKI_DF_CASE(4, 4)
+  SKI_DF_CASE(8, 2)
+  SKI_DF_CASE(16, 1)
+#undef SKI_DF_CASE
+  return SKI_EINVAL;
+}
+
+ski_status ski_reduce_par_launch(int nblk, int64_t d, const double* part, const double* part_tt, double* q,
+                                 LsqrScalars* sc, cudaStream_t st) {
+  k_reduce_par<<<(unsigned)std::max<int64_t>(1, ski_cdiv(d, 32)), 256, 0, st>>>(nblk, d, part, part_tt, q, sc);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+int ski_vv_blocks(int64_t d) { return (int)ski_cdiv(d, 8); }
+
+ski_status ski_trmv_lower_vp_launch(int64_t d, const double* Mt, const double* q, const double* v, double* vp,
+                                    double* part_vv, LsqrScalars* sc, int start, cudaStream_t st) {
+  k_trmv_lower_vp<<<(unsigned)ski_vv_blocks(d), 256, 0, st>>>(d, Mt, q, v, vp, part_vv, sc, start);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+ski_status ski_trmv_upper_update_launch(int64_t d, const double* M, const double* vp, const double* part_vv,
+                                        double* v, double* w, double* y, double* z, LsqrScalars* sc, int start,
+                                        cudaStream_t st) {
+  k_trmv_upper_update<<<(unsigned)ski_vv_blocks(d), 256, 0, st>>>(d, M, vp, ski_vv_blocks(d), part_vv, v, w, y, z,
+                                                                    sc, start);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}

@@ -11,7 +11,9 @@ struct LsqrScalars {
   double rnorm2, anorm_f2, atr_norm;
   double cg_rr, cg_rr0, cg_tol2;  // conjugate gradients of the adjoint solve
   long long iters, it_max;
-  int done, conv;
+  int flag_a, flag_b;  // stop flags (see lsqr_df.cu for who writes which)
+  int conv;
+  int amax_exp;  // largest biased exponent field of A (from the first residual pass)
 };
 
 struct FusedArgs {
@@ -38,7 +40,39 @@ struct FusedArgs {
   int nblk;
   int64_t rows_per;
   const LsqrScalars* sc;
+  int* maxexp;  // when set: atomicMax of the biased exponent fields of A
 };
+
+// Double-float dense pass (lsqr_df.cu): t = A z + cu u with A held as
+// A2 = A * 2^-sA in (hi, lo) float pairs.
+struct DfArgs {
+  const float2* A2;
+  int64_t n, d;
+  int sA;
+  const double* z;
+  const double* u;
+  double cu;
+  int coef_from_scalars;
+  double* t;
+  double* part;     // [nblk][d] partial A^T t
+  double* part_tt;  // [nblk] partial ||t||^2
+  int nblk;
+  int64_t rows_per;
+  LsqrScalars* sc;
+};
+
+ski_status ski_split_a_launch(int64_t n, int64_t d, const double* A, int64_t lda, int sA, float2* A2,
+                              cudaStream_t st);
+bool ski_df_supported(int64_t d);
+ski_status ski_fused_df_launch(const DfArgs& f, cudaStream_t st);
+ski_status ski_reduce_par_launch(int nblk, int64_t d, const double* part, const double* part_tt, double* q,
+                                 LsqrScalars* sc, cudaStream_t st);
+int ski_vv_blocks(int64_t d);
+ski_status ski_trmv_lower_vp_launch(int64_t d, const double* Mt, const double* q, const double* v, double* vp,
+                                    double* part_vv, LsqrScalars* sc, int start, cudaStream_t st);
+ski_status ski_trmv_upper_update_launch(int64_t d, const double* M, const double* vp, const double* part_vv,
+                                        double* v, double* w, double* y, double* z, LsqrScalars* sc, int start,
+                                        cudaStream_t st);
 
 int ski_fused_ctas(int64_t n);
 ski_status ski_fused_launch(const FusedArgs& f, cudaStream_t st);
@@ -48,8 +82,7 @@ ski_status ski_csc_launch(int64_t d, const int64_t* colptr, const int32_t* rowid
                           const double* t, double* q, const LsqrScalars* sc, cudaStream_t st);
 ski_status ski_reduce_launch(int nblk, int64_t d, const double* part, int64_t ldp, const double* part_tt,
                              const double* part_aa, double* q, LsqrScalars* sc, int mode, cudaStream_t st);
-ski_status ski_update_launch(int64_t d, const double* p, double* v, double* w, double* y, LsqrScalars* sc, int start,
-                             cudaStream_t st);
+
 ski_status ski_norm_launch(int64_t d, const double* q, LsqrScalars* sc, cudaStream_t st);
 ski_status ski_copy_launch(int64_t n, const double* a, double* b, cudaStream_t st);
 ski_status ski_cg_launch(int64_t d, const double* q, double* r, double* p, double* z, LsqrScalars* sc, int start,

@@ -45,28 +45,49 @@ __device__ __forceinline__ T sgn_nrm(T x0, T nrm) { return x0 >= T(0) ? -nrm : n
 template <class T>
 __global__ void __launch_bounds__(32 * WARPS) k_panel_step(PanelArgs<T> a, int s) {
   __shared__ T red[WARPS][NB];
+  __shared__ T s_par[4];  // tau, beta, scl
+  __shared__ T s_wc[NB];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = s - 1;
   T tau = T(0), beta = T(0), scl = T(0), wc = T(0);
   if (s > 0) {
+    // partial sums of the previous launch, split over the warps (fixed order)
     T g = T(0);
-    for (int b = 0; b < a.ncta; ++b) g += a.part_prev[(int64_t)b * PW + lane];
-    const int owner = (int)(j / a.rows_per);
-    const T dr = a.part_prev[(int64_t)owner * PW + NB + lane];
-    const T x0 = __shfl_sync(0xffffffffu, dr, j);
-    const T gj = __shfl_sync(0xffffffffu, g, j);
-    if (gj == T(0)) {
-      tau = T(0);
-      beta = x0;
-      scl = T(0);
-    } else {
-      const T nrm = sqrt(x0 * x0 + gj);
-      beta = sgn_nrm(x0, nrm);
-      tau = (beta - x0) / beta;
-      scl = T(1) / (x0 - beta);
+    for (int b = warp; b < a.ncta; b += WARPS) g += a.part_prev[(int64_t)b * PW + lane];
+    red[warp][lane] = g;
+    __syncthreads();
+    if (warp == 0) {
+      g = T(0);
+#pragma unroll
+      for (int q = 0; q < WARPS; ++q) g += red[q][lane];
+      const int owner = (int)(j / a.rows_per);
+      const T dr = a.part_prev[(int64_t)owner * PW + NB + lane];
+      const T x0 = __shfl_sync(0xffffffffu, dr, j);
+      const T gj = __shfl_sync(0xffffffffu, g, j);
+      T tau_, beta_, scl_;
+      if (gj == T(0)) {
+        tau_ = T(0);
+        beta_ = x0;
+        scl_ = T(0);
+      } else {
+        const T nrm = sqrt(x0 * x0 + gj);
+        beta_ = sgn_nrm(x0, nrm);
+        tau_ = (beta_ - x0) / beta_;
+        scl_ = T(1) / (x0 - beta_);
+      }
+      s_wc[lane] = dr + scl_ * g;  // v^T p_c for lanes c > j
+      if (lane == 0) {
+        s_par[0] = tau_;
+        s_par[1] = beta_;
+        s_par[2] = scl_;
+        if (blockIdx.x == 0) a.tau[j] = tau_;
+      }
     }
-    wc = dr + scl * g;  // v^T p_c for lanes c > j
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.tau[j] = tau;
+    __syncthreads();
+    tau = s_par[0];
+    beta = s_par[1];
+    scl = s_par[2];
+    wc = s_wc[lane];
   }
   const int64_t r0 = (int64_t)blockIdx.x * a.rows_per;
   const int64_t r1 = min(a.mr, r0 + a.rows_per);
@@ -98,6 +119,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_panel_step(PanelArgs<T> a, int s
     }
   }
   if (s < a.w) {
+    __syncthreads();  // red[] may still be read by warp 0 of the finalisation above
     red[warp][lane] = acc;
     __syncthreads();
     if (warp == 0) {
@@ -130,14 +152,18 @@ __global__ void k_reduce_z(int w, int64_t nct, const T* __restrict__ pv, int sv,
 template <class T>
 __global__ void k_tfactor(int w, const T* __restrict__ Z, int64_t ldzz, const T* __restrict__ tau, T* __restrict__ Tm) {
   __shared__ T Ts[NB][NB + 1];
+  __shared__ T G[NB][NB + 1];
   const int lane = threadIdx.x;
-  for (int c = 0; c < NB; ++c) Ts[lane][c] = T(0);
+  for (int c = 0; c < NB; ++c) {
+    Ts[lane][c] = T(0);
+    G[lane][c] = (lane < w && c < w) ? Z[lane * ldzz + c] : T(0);
+  }
   __syncwarp();
   for (int i = 0; i < w; ++i) {
     // y[r] = sum_{k=r}^{i-1} T[r,k] * (V^T V)[k, i], r < i
     T y = T(0);
     if (lane < i)
-      for (int k = lane; k < i; ++k) y += Ts[lane][k] * Z[k * ldzz + i];
+      for (int k = lane; k < i; ++k) y += Ts[lane][k] * G[k][i];
     __syncwarp();
     if (lane < i) Ts[lane][i] = -tau[i] * y;
     if (lane == i) Ts[i][i] = tau[i];

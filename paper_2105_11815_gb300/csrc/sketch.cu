@@ -118,50 +118,97 @@ __global__ void k_bucket_sort(int64_t m, const int64_t* __restrict__ offsets, co
 }
 
 // ------------------------------------------------------------ dense gather
-// Row i of SA, columns c in [c0, c0 + 2*blockDim): sum over the bucket's
-// entries (j, neg) of (-1)^neg * X[j, c] (X = [A | b]), times `scale`.
+// Lean exact accumulator for the gather: block exponent E only ever rises
+// (a rare branch), every addend costs ~20 integer instructions.  The
+// caller bounds |S| by calling renorm() every 4 addends (each < 2^55).
+struct FxGather {
+  long long S;
+  int E;  // biased exponent field of the largest addend so far (>= 1)
+  bool bad;
+  __device__ __forceinline__ void init() { S = 0; E = 1; bad = false; }
+  __device__ __forceinline__ void add(double v, unsigned neg) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(b >> 32);
+    int e = (int)((hi >> 20) & 0x7FF);
+    if (e > E) {
+      if (e == 0x7FF) bad = true;
+      const int sh = e - E;
+      S = sh > 62 ? (S < 0 ? -1 : 0) : (S >> sh);
+      E = e;
+    }
+    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+    const int sh = E - (e ? e : 1);
+    const long long q = sh > 63 ? 0ll : (long long)((M << FX_LIFT) >> sh);
+    const long long mask = -(long long)((hi >> 31) ^ neg);
+    S += (q ^ mask) - mask;
+  }
+  __device__ __forceinline__ void renorm() {
+    if (S >= (1ll << 60) || S <= -(1ll << 60)) {
+      S >>= 4;
+      E += 4;
+    }
+  }
+};
+
+__device__ __forceinline__ double fxg_scaled(const FxGather& a, long long c, int e) {
+  if (a.bad) return __longlong_as_double(0x7FF8000000000000ll);
+  const long long Sp = (long long)(((__int128)a.S * (__int128)c) >> 62);
+  return fx_to_double(Sp, a.E, e);
+}
+
+// Row i of SA, columns c0 + k*128 (k < 4): sum over the bucket's entries
+// (j, neg) of (-1)^neg * X[j, c] (X = [A | b]), times `scale`.
 template <class TOUT>
 __global__ void __launch_bounds__(128) k_sketch_dense_f64acc(
     const double* __restrict__ A, int64_t lda, int64_t nrows, int64_t d, const double* __restrict__ b,
     const int64_t* __restrict__ offsets, const uint32_t* __restrict__ list, long long scale_c, int scale_e,
     TOUT* __restrict__ SA, int64_t ld_sa) {
+  constexpr int CPT = 4;
   const int64_t i = blockIdx.x;
   const int64_t ncols = d + (b != nullptr);
-  const int64_t c0 = (int64_t)blockIdx.y * (2 * blockDim.x) + threadIdx.x;
-  const int64_t c1 = c0 + blockDim.x;
+  const int64_t cb = (int64_t)blockIdx.y * (CPT * 128) + threadIdx.x;
   const int64_t lo = offsets[i], hi = offsets[i + 1];
-  FxAcc a0, a1;
-  a0.init();
-  a1.init();
+  FxGather acc[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) acc[k].init();
   int64_t e = lo;
   for (; e + 4 <= hi; e += 4) {
     uint32_t en[4];
-    double v0[4], v1[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) en[u] = __ldg(&list[e + u]);
+    double v[4][CPT];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      int64_t j = en[u] >> 1;
-      v0[u] = c0 < d ? __ldcs(&A[j * lda + c0]) : (c0 == d && b ? __ldg(&b[j]) : 0.0);
-      v1[u] = c1 < d ? __ldcs(&A[j * lda + c1]) : (c1 == d && b ? __ldg(&b[j]) : 0.0);
+      const int64_t j = en[u] >> 1;
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        const int64_t c = cb + k * 128;
+        v[u][k] = c < d ? __ldcs(&A[j * lda + c]) : (c == d && b ? __ldg(&b[j]) : 0.0);
+      }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      a0.add(v0[u], en[u] & 1);
-      a1.add(v1[u], en[u] & 1);
-    }
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) acc[k].add(v[u][k], en[u] & 1u);
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) acc[k].renorm();
   }
   for (; e < hi; ++e) {
-    uint32_t en = __ldg(&list[e]);
-    int64_t j = en >> 1;
-    double v0 = c0 < d ? __ldcs(&A[j * lda + c0]) : (c0 == d && b ? __ldg(&b[j]) : 0.0);
-    double v1 = c1 < d ? __ldcs(&A[j * lda + c1]) : (c1 == d && b ? __ldg(&b[j]) : 0.0);
-    a0.add(v0, en & 1);
-    a1.add(v1, en & 1);
+    const uint32_t en = __ldg(&list[e]);
+    const int64_t j = en >> 1;
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      const int64_t c = cb + k * 128;
+      const double v = c < d ? __ldcs(&A[j * lda + c]) : (c == d && b ? __ldg(&b[j]) : 0.0);
+      acc[k].add(v, en & 1u);
+    }
   }
   (void)nrows;
-  if (c0 < ncols) SA[i * ld_sa + c0] = SkiType<TOUT>::from(fx_scaled(a0, scale_c, scale_e));
-  if (c1 < ncols) SA[i * ld_sa + c1] = SkiType<TOUT>::from(fx_scaled(a1, scale_c, scale_e));
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int64_t c = cb + k * 128;
+    if (c < ncols) SA[i * ld_sa + c] = SkiType<TOUT>::from(fxg_scaled(acc[k], scale_c, scale_e));
+  }
 }
 
 template <class TOUT>
@@ -313,7 +360,8 @@ ski_status ski_gather_dense(const double* A, int64_t lda, int64_t nrows, int64_t
     long long c;
     int e;
     scale_fixed(scale, &c, &e);
-    k_sketch_dense_f64acc<double><<<grid, T, 0, st>>>(A, lda, nrows, d, b, bk.offsets, bk.list, c, e,
+    dim3 grid64((unsigned)bk.m, (unsigned)ski_cdiv(ncols, 4 * T));
+    k_sketch_dense_f64acc<double><<<grid64, T, 0, st>>>(A, lda, nrows, d, b, bk.offsets, bk.list, c, e,
                                                        (double*)SA, ld_sa);
   } else if (out_dtype == SKI_F32) {
     k_sketch_dense_f32acc<float><<<grid, T, 0, st>>>(A, lda, d, b, bk.offsets, bk.list, (float)scale,

@@ -77,8 +77,8 @@ ski_status rec(int64_t o, int64_t n, const T* R, int64_t ldr, T* X, int64_t ldx,
   const T* X22 = X + (o + n1) * ldx + o + n1;
   const T* X11 = X + o * ldx + o;
   T* X12 = X + o * ldx + o + n1;
-  SKI_TRY(ski_gemm<T>(n1, n2, n2, T(1), R12, ldr, 1, X22, ldx, 1, T(0), tmp, n2, st));
-  SKI_TRY(ski_gemm<T>(n1, n2, n1, T(-1), X11, ldx, 1, tmp, n2, 1, T(0), X12, ldx, st));
+  SKI_TRY(ski_gemm_tri<T>(n1, n2, n2, T(1), R12, ldr, 1, X22, ldx, 1, T(0), tmp, n2, 2, st));
+  SKI_TRY(ski_gemm_tri<T>(n1, n2, n1, T(-1), X11, ldx, 1, tmp, n2, 1, T(0), X12, ldx, 1, st));
   return SKI_OK;
 }
 

@@ -55,7 +55,7 @@ struct FxOut {
 };
 
 template <int RB, int GB, int IN, int OUT>
-__global__ void __launch_bounds__(CT << GB) k_wht_fx(int lo, int64_t n_pad, int64_t ncols, FxIn in, FxOut out) {
+__global__ void __launch_bounds__(CT << GB, (GB >= 4 && RB <= 4) ? 2 : 1) k_wht_fx(int lo, int64_t n_pad, int64_t ncols, FxIn in, FxOut out) {
   constexpr int R = 1 << RB, G = 1 << GB, NB = RB + GB;
   extern __shared__ long long sq[];            // [R*G][CT]
   __shared__ int sx[G][CT];
@@ -73,12 +73,11 @@ __global__ void __launch_bounds__(CT << GB) k_wht_fx(int lo, int64_t n_pad, int6
 #pragma unroll
     for (int t = 0; t < R; ++t) {
       const int64_t row = base + ((int64_t)(g + (t << GB)) << lo);
-      double v = 0.0;
+      long long bits = 0;
       if (cok && row < in.n) {
-        v = col < in.d ? in.A[row * in.lda + col] : in.b[row];
-        if (in.D[row] < 0) v = -v;
+        bits = __double_as_longlong(col < in.d ? in.A[row * in.lda + col] : in.b[row]);
+        if (in.D[row] < 0) bits ^= (1ll << 63);  // D_jj = -1: flip the sign bit (no FP64 op)
       }
-      long long bits = __double_as_longlong(v);
       int e = (int)((bits >> 52) & 0x7FF);
       bad |= (e == 0x7FF);
       emax = max(emax, e ? e : 1);
