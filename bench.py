@@ -39,6 +39,8 @@ WORKLOADS = {
     "dense_4096x256_s1_m512": (4096, 256, 0, 1, 2.0, "lls"),
     # small case for ncu captures: same kernels, A = 205 MB (larger than L2)
     "dense_50000x512_hrht_s1_g2": (50000, 512, 65536, 1, 2.0, "gauss"),
+    # mid case for full ncu captures of the d = 4000 kernel variants (~4.5 GB on the device)
+    "dense_32768x3000_hrht_s1_g2": (32768, 3000, 32768, 1, 2.0, "gauss"),
 }
 DEFAULT = "dense_50000x4000_hrht_s1_g2"
 

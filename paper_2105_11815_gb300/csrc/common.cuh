@@ -9,6 +9,9 @@
 #include <algorithm>
 #include "../../include/skills.h"
 
+// Size of the library-owned scratch behind ski_sketch_hash_noalloc.
+#define SKI_NOALLOC_SCRATCH_BYTES (4u << 20)
+
 #define SKI_CUDA_TRY(expr)                                   \
   do {                                                       \
     cudaError_t e_ = (expr);                                 \
@@ -110,6 +113,10 @@ __device__ __forceinline__ long long fx_quant(double v, int E, bool neg) {
   return negative ? -(long long)q : (long long)q;
 }
 
+// Out-of-range tail of fx_i64_to_double (kept out of line so that the FP64
+// instructions it needs are never issued, predicated, on the fast path).
+static __device__ __noinline__ double fx_i64_to_double_slow(long long S, int X) { return ldexp(__ll2double_rn(S), X); }
+
 // The double nearest to S * 2^X (round to nearest even), using integer
 // operations only: on GB300 the int64 -> FP64 conversion instruction runs on
 // the 1/64-rate FP64 pipe.  |S| < 2^63.
@@ -128,7 +135,7 @@ __device__ __forceinline__ double fx_i64_to_double(long long S, int X) {
     e += 1;
   }
   const int be = e + 1023;
-  if (be < 1 || be > 2046) return ldexp(__ll2double_rn(S), X);  // subnormal or overflow: rare
+  if (be < 1 || be > 2046) return fx_i64_to_double_slow(S, X);  // subnormal or overflow: rare
   return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 

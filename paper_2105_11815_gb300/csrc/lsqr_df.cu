@@ -130,6 +130,11 @@ __global__ void __launch_bounds__(512) k_fused_df(DfArgs f) {
   }
   const int64_t r0 = (int64_t)blockIdx.x * f.rows_per;
   const int64_t r1 = min(f.n, r0 + f.rows_per);
+  // u for this CTA's rows, staged once (off the per-row critical path)
+  extern __shared__ double s_u[];
+  if (f.u)
+    for (int64_t j = r0 + tid; j < r1; j += NT) s_u[j - r0] = f.u[j];
+  __syncthreads();
   double tt = 0.0;
   for (int64_t j0 = r0; j0 < r1; j0 += RR) {
     float2 a[RR][CPT];
@@ -149,20 +154,28 @@ __global__ void __launch_bounds__(512) k_fused_df(DfArgs f) {
       if (lane == 0) red[r][wid] = make_float2(h, l);
     }
     __syncthreads();
-    if (tid < RR) {
-      const int64_t j = j0 + tid;
-      float h = 0.f, l = 0.f;
+    // warp r < RR finishes row j0 + r: tree sum of the 16 warp partials,
+    // then t_j in FP64 (one row per warp, all rows in parallel)
+    if (wid < RR) {
+      const int64_t j = j0 + wid;
+      float h = lane < NW ? red[wid][lane].x : 0.f, l = lane < NW ? red[wid][lane].y : 0.f;
 #pragma unroll
-      for (int q = 0; q < NW; ++q) df_add(h, l, red[tid][q].x, red[tid][q].y);
-      float2 ts = make_float2(0.f, 0.f);
-      if (j < r1) {
-        double t = ldexp((double)h + (double)l, st);
-        if (f.u) t = fma(cu, f.u[j], t);
-        f.t[j] = t;
-        tt = fma(t, t, tt);
-        ts = df_split(t, st);
+      for (int o = NW / 2; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+        df_add(h, l, oh, ol);
       }
-      tsh[tid] = ts;
+      if (lane == 0) {
+        float2 ts = make_float2(0.f, 0.f);
+        if (j < r1) {
+          double t = ldexp((double)h + (double)l, st);
+          if (f.u) t = fma(cu, s_u[j - r0], t);
+          f.t[j] = t;
+          tt = fma(t, t, tt);
+          ts = df_split(t, st);
+        }
+        tsh[wid] = ts;
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -178,9 +191,9 @@ __global__ void __launch_bounds__(512) k_fused_df(DfArgs f) {
     const int64_t c = tid + (int64_t)k * NT;
     if (c < f.d) f.part[(int64_t)blockIdx.x * f.d + c] = ldexp((double)ah_acc[k] + (double)al_acc[k], f.sA + st);
   }
-  // ||t||^2: threads tid < RR hold pieces
-  __shared__ double tts[32];
-  if (tid < 32) tts[tid] = tid < RR ? tt : 0.0;
+  // ||t||^2: lane 0 of warps < RR hold pieces
+  __shared__ double tts[NW];
+  if (lane == 0) tts[wid] = tt;
   __syncthreads();
   if (tid == 0) {
     double s = 0.0;
@@ -372,11 +385,16 @@ ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
   DfArgs f = f0;
   f.rows_per = ski_cdiv(f.n, f.nblk);
   const int64_t cpt = ski_cdiv(f.d, 512);
-#define SKI_DF_CASE(C, R)                          \
-  if (cpt <= C) {                                  \
-    k_fused_df<C, R><<<f.nblk, 512, 0, st>>>(f);   \
-    SKI_LAUNCH_CHECK();                            \
-    return SKI_OK;                                 \
+  const size_t smem = (size_t)f.rows_per * sizeof(double);
+  if (smem > 200 * 1024) return SKI_EINVAL;
+#define SKI_DF_CASE(C, R)                                                                        \
+  if (cpt <= C) {                                                                                \
+    if (smem > 48 * 1024)                                                                        \
+      SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                        (int)smem));                                             \
+    k_fused_df<C, R><<<f.nblk, 512, smem, st>>>(f);                                              \
+    SKI_LAUNCH_CHECK();                                                                          \
+    return SKI_OK;                                                                               \
   }
   SKI_DF_CASE(1, 8)
   SKI_DF_CASE(2, 8)
