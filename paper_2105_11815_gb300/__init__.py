@@ -17,7 +17,7 @@ __all__ = [
     "ski_opts", "ski_info", "ski_matrix", "lib", "lib_path",
     "ski_opts_default", "ski_status_string", "ski_version", "ski_last_cuda_error", "ski_launch_count",
     "ski_hash_indices", "ski_premix_signs", "ski_premix_workspace_size", "ski_premix",
-    "ski_sketch_workspace_size", "ski_sketch_hash",
+    "ski_sketch_workspace_size", "ski_sketch_hash", "ski_sketch_hash_noalloc",
     "ski_precondition_workspace_size", "ski_precondition",
     "ski_trinv_workspace_size", "ski_trinv",
     "ski_solve_workspace_size", "ski_solve",
@@ -87,6 +87,7 @@ _SIGS = {
     "ski_premix": (_I32, [_MP, _P, _OP, _P, _I64, _P, _SZ, _P]),
     "ski_sketch_workspace_size": (_SZ, [_MP, _I32, _OP]),
     "ski_sketch_hash": (_I32, [_MP, _P, _OP, _P, _I64, _P, _SZ, _P]),
+    "ski_sketch_hash_noalloc": (_I32, [_MP, _P, _OP, _P, _I64, _P]),
     "ski_precondition_workspace_size": (_SZ, [_I64, _I64, _I32, _I32]),
     "ski_precondition": (_I32, [_I64, _I64, _I32, _P, _I64, _I32, _P, _I64, _P, _P, _OP, _P, _SZ, _P]),
     "ski_trinv_workspace_size": (_SZ, [_I64, _I32]),
@@ -221,6 +222,12 @@ def ski_sketch_hash(A, b, opts, SA, ld_sa, ws=None, stream=None):
     w = _ws(nb, SA.device, ws)
     return _check(lib().ski_sketch_hash(ctypes.byref(A), _ptr(b), ctypes.byref(opts), _ptr(SA), ld_sa, _ptr(w), nb,
                                         _stream(stream)), "ski_sketch_hash")
+
+
+def ski_sketch_hash_noalloc(A, b, opts, SA, ld_sa, stream=None):
+    """ski_sketch_hash with the library's own fixed scratch (no workspace)."""
+    return _check(lib().ski_sketch_hash_noalloc(ctypes.byref(A), _ptr(b), ctypes.byref(opts), _ptr(SA), ld_sa,
+                                                _stream(stream)), "ski_sketch_hash_noalloc")
 
 
 def ski_precondition_workspace_size(m, d, with_rhs, sa_dtype):

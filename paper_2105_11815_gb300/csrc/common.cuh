@@ -9,9 +9,6 @@
 #include <algorithm>
 #include "../../include/skills.h"
 
-// Size of the library-owned scratch behind ski_sketch_hash_noalloc.
-#define SKI_NOALLOC_SCRATCH_BYTES (4u << 20)
-
 #define SKI_CUDA_TRY(expr)                                   \
   do {                                                       \
     cudaError_t e_ = (expr);                                 \
