@@ -116,6 +116,17 @@ int32_t ski_last_cuda_error(void);
 int64_t ski_launch_count(void);
 
 /*
+ * ski_selftest_wait_timeout -- checks the library's bounded device-side wait
+ * (the grid barrier of the persistent QR panel kernel) on the GPU without a
+ * fault: 4 co-resident CTAs wait for a fifth that never arrives, each poll
+ * loop gives up after spin_limit polls (~64 ns each) and sets an error flag.
+ * Returns SKI_ETIMEOUT when the wait timed out as designed (the expected
+ * result), SKI_OK if it did not.  ws: device scratch of >= 16 bytes.
+ * Synchronous.
+ */
+ski_status ski_selftest_wait_timeout(int64_t spin_limit, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * ski_hash_indices -- the nonzeros of the s-hashing matrix S (Def. 5).
  * Column j < n of S (multiplying row j of A) holds sign[j*s+k] / sqrt(s) in row
  * idx[j*s+k], k < s; the s rows are distinct (drawn without replacement).

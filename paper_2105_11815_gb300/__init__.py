@@ -16,6 +16,7 @@ __all__ = [
     "SKI_F64", "SKI_F32", "SKI_BF16", "SKI_DENSE", "SKI_CSR", "SkiError",
     "ski_opts", "ski_info", "ski_matrix", "lib", "lib_path",
     "ski_opts_default", "ski_status_string", "ski_version", "ski_last_cuda_error", "ski_launch_count",
+    "ski_selftest_wait_timeout",
     "ski_hash_indices", "ski_premix_signs", "ski_premix_workspace_size", "ski_premix",
     "ski_sketch_workspace_size", "ski_sketch_hash", "ski_sketch_hash_noalloc",
     "ski_precondition_workspace_size", "ski_precondition",
@@ -81,6 +82,7 @@ _SIGS = {
     "ski_version": (_I32, []),
     "ski_last_cuda_error": (_I32, []),
     "ski_launch_count": (_I64, []),
+    "ski_selftest_wait_timeout": (_I32, [_I64, _P, _SZ, _P]),
     "ski_hash_indices": (_I32, [_U64, _I32, _I64, _I64, _P, _P, _P]),
     "ski_premix_signs": (_I32, [_U64, _I64, _P, _P]),
     "ski_premix_workspace_size": (_SZ, [_MP, _I32, _OP]),
@@ -191,6 +193,13 @@ def ski_last_cuda_error():
 
 def ski_launch_count():
     return lib().ski_launch_count()
+
+
+def ski_selftest_wait_timeout(spin_limit, ws=None, stream=None):
+    """Returns the status of the bounded-wait self-test (SKI_ETIMEOUT = 7 expected)."""
+    import torch
+    w = ws if ws is not None else torch.zeros(16, dtype=torch.uint8, device="cuda")
+    return lib().ski_selftest_wait_timeout(int(spin_limit), _ptr(w), 16, _stream(stream))
 
 
 # ---------------------------------------------------------------- entry points

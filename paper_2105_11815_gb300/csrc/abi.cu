@@ -311,7 +311,7 @@ size_t plan_solve(const ski_matrix* A, const ski_opts* o, char* base, size_t cap
   P->sc = ar.take<LsqrScalars>(1);
   P->vp = ar.take<double>(d);
   P->part_vv = ar.take<double>(ski_vv_blocks(d));
-  P->A2 = P->csr ? nullptr : ar.take<float2>(n * d);
+  P->A2 = P->csr ? nullptr : ar.take<float2>(n * ski_a2_ld(d));
   if (P->csr) {
     P->colptr = ar.take<int64_t>(d + 1);
     P->rowidx = ar.take<int32_t>(A->nnz);
@@ -785,4 +785,9 @@ extern "C" ski_status ski_solve_adjoint(const ski_matrix* A, const double* b, co
     info->lsqr_test = hs.cg_rr0 > 0 ? sqrt(hs.cg_rr / hs.cg_rr0) : 0.0;
   }
   return res;
+}
+
+extern "C" ski_status ski_selftest_wait_timeout(int64_t spin_limit, void* ws, size_t ws_bytes, void* stream) {
+  if (spin_limit < 1 || !ws || ws_bytes < 16) return SKI_EINVAL;
+  return ski_barrier_selftest(spin_limit, ws, ski_stream(stream));
 }

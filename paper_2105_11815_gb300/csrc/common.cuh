@@ -66,6 +66,24 @@ __device__ __forceinline__ float ski_warp_sumf(float v) {
   return v;
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (TMA unit, no registers or shared
+// memory involved).  p and bytes must be multiples of 16; callers pass only
+// ranges inside their buffers.
+__device__ __forceinline__ void ski_l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Prefetch the 16-byte-aligned interior of [p, p + bytes) in chunks of 4 KB,
+// chunk i issued by the calling thread when i % nthreads == tid.
+__device__ __forceinline__ void ski_l2_prefetch_range(const void* p, size_t bytes, int tid, int nthreads) {
+  uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+  uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  for (uintptr_t c = a + (uintptr_t)tid * 4096; c < e; c += (uintptr_t)nthreads * 4096) {
+    const uintptr_t n = (e - c) < 4096 ? (e - c) : 4096;
+    ski_l2_prefetch((const void*)c, (unsigned)n);
+  }
+}
+
 template <class T> struct SkiType;
 template <> struct SkiType<double> {
   static constexpr int id = SKI_F64;

@@ -317,10 +317,10 @@ __global__ void k_copy(int64_t n, const double* __restrict__ a, double* __restri
 
 }  // namespace
 
-// CTAs of a pass over A: about two per SM, and enough that one CTA's rows
+// CTAs of a pass over A: one per SM (one wave), and enough that one CTA's rows
 // (staged in shared memory by the double-float pass) stay below 16384.
 int ski_fused_ctas(int64_t n) {
-  const int64_t base = std::min<int64_t>(2 * 152, std::max<int64_t>(1, ski_cdiv(n, 16)));
+  const int64_t base = std::min<int64_t>(152, std::max<int64_t>(1, ski_cdiv(n, 16)));
   return (int)std::max<int64_t>(base, ski_cdiv(n, 16384));
 }
 

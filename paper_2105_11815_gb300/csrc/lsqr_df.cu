@@ -70,7 +70,7 @@ __device__ __forceinline__ bool flag_set(const volatile int* f) { return *f != 0
 // the top 24 significant bits (exact in FP32), lo the remaining 29 bits
 // rounded to 24.  Values below 2^-126 * 2^sA flush to zero.
 __global__ void k_split_a(int64_t n, int64_t d, const double* __restrict__ A, int64_t lda, int sA,
-                          float2* __restrict__ A2) {
+                          float2* __restrict__ A2, int64_t ld2) {
   const int64_t j = blockIdx.y;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < d; c += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(A[j * lda + c]);
@@ -87,7 +87,7 @@ __global__ void k_split_a(int64_t n, int64_t d, const double* __restrict__ A, in
         if (bits >> 63) l = -l;
       }
     }
-    A2[j * d + c] = make_float2(h, l);
+    A2[j * ld2 + c] = make_float2(h, l);
   }
 }
 
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(512) k_fused_df(DfArgs f) {
 #pragma unroll
       for (int k = 0; k < CPT; ++k) {
         const int64_t c = tid + (int64_t)k * NT;
-        a[r][k] = (j0 + r < r1 && c < f.d) ? __ldcs(&f.A2[(j0 + r) * f.d + c]) : make_float2(0.f, 0.f);
+        a[r][k] = (j0 + r < r1 && c < f.d) ? __ldcs(&f.A2[(j0 + r) * f.ld2 + c]) : make_float2(0.f, 0.f);
       }
 #pragma unroll
     for (int r = 0; r < RR; ++r) {
@@ -370,10 +370,11 @@ __global__ void __launch_bounds__(256) k_trmv_upper_update(int64_t d, const doub
 }  // namespace
 
 ski_status ski_split_a_launch(int64_t n, int64_t d, const double* A, int64_t lda, int sA, float2* A2, cudaStream_t st) {
+  const int64_t ld2 = ski_a2_ld(d);
   for (int64_t j0 = 0; j0 < n; j0 += 65535) {
     const int64_t nr = std::min<int64_t>(65535, n - j0);
     dim3 grid((unsigned)std::min<int64_t>(ski_cdiv(d, 256), 16), (unsigned)nr);
-    k_split_a<<<grid, 256, 0, st>>>(nr, d, A + j0 * lda, lda, sA, A2 + j0 * d);
+    k_split_a<<<grid, 256, 0, st>>>(nr, d, A + j0 * lda, lda, sA, A2 + j0 * ld2, ld2);
     SKI_LAUNCH_CHECK();
   }
   return SKI_OK;
@@ -381,8 +382,11 @@ ski_status ski_split_a_launch(int64_t n, int64_t d, const double* A, int64_t lda
 
 bool ski_df_supported(int64_t d) { return d <= SKI_DENSE_DMAX; }
 
+int64_t ski_a2_ld(int64_t d) { return ski_round_up(d, 2); }  // rows 16-byte aligned
+
 ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
   DfArgs f = f0;
+  f.ld2 = ski_a2_ld(f.d);
   f.rows_per = ski_cdiv(f.n, f.nblk);
   const int64_t cpt = ski_cdiv(f.d, 512);
   const size_t smem = (size_t)f.rows_per * sizeof(double);

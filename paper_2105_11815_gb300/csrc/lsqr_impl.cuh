@@ -47,7 +47,7 @@ struct FusedArgs {
 // A2 = A * 2^-sA in (hi, lo) float pairs.
 struct DfArgs {
   const float2* A2;
-  int64_t n, d;
+  int64_t n, d, ld2;  // ld2: row stride of A2 (even, so rows are 16-byte aligned)
   int sA;
   const double* z;
   const double* u;
@@ -64,6 +64,7 @@ struct DfArgs {
 ski_status ski_split_a_launch(int64_t n, int64_t d, const double* A, int64_t lda, int sA, float2* A2,
                               cudaStream_t st);
 bool ski_df_supported(int64_t d);
+int64_t ski_a2_ld(int64_t d);
 ski_status ski_fused_df_launch(const DfArgs& f, cudaStream_t st);
 ski_status ski_reduce_par_launch(int nblk, int64_t d, const double* part, const double* part_tt, double* q,
                                  LsqrScalars* sc, cudaStream_t st);

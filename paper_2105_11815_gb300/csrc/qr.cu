@@ -24,6 +24,7 @@ namespace {
 constexpr int NB = 32;
 constexpr int PW = 2 * NB;  // partial slot: g[32] then the diagonal row[32]
 constexpr int WARPS = 8;
+constexpr long long kSpinLimit = 1ll << 24;  // ~1 s of polling at ~64 ns per poll
 
 template <class T>
 struct PanelArgs {
@@ -42,8 +43,12 @@ struct PanelArgs {
 template <class T>
 __device__ __forceinline__ T sgn_nrm(T x0, T nrm) { return x0 >= T(0) ? -nrm : nrm; }
 
+// One column step s of the panel (see the file comment): finalise column
+// s-1 from the partials of step s-1 and accumulate those of column s.
+// Partials are read with L1-bypassing loads: in the persistent kernel they
+// were written by other SMs during this launch.
 template <class T>
-__global__ void __launch_bounds__(32 * WARPS) k_panel_step(PanelArgs<T> a, int s) {
+__device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s) {
   __shared__ T red[WARPS][NB];
   __shared__ T s_par[4];  // tau, beta, scl
   __shared__ T s_wc[NB];
@@ -53,7 +58,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_panel_step(PanelArgs<T> a, int s
   if (s > 0) {
     // partial sums of the previous launch, split over the warps (fixed order)
     T g = T(0);
-    for (int b = warp; b < a.ncta; b += WARPS) g += a.part_prev[(int64_t)b * PW + lane];
+    for (int b = warp; b < a.ncta; b += WARPS) g += __ldcg(&a.part_prev[(int64_t)b * PW + lane]);
     red[warp][lane] = g;
     __syncthreads();
     if (warp == 0) {
@@ -61,7 +66,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_panel_step(PanelArgs<T> a, int s
 #pragma unroll
       for (int q = 0; q < WARPS; ++q) g += red[q][lane];
       const int owner = (int)(j / a.rows_per);
-      const T dr = a.part_prev[(int64_t)owner * PW + NB + lane];
+      const T dr = __ldcg(&a.part_prev[(int64_t)owner * PW + NB + lane]);
       const T x0 = __shfl_sync(0xffffffffu, dr, j);
       const T gj = __shfl_sync(0xffffffffu, g, j);
       T tau_, beta_, scl_;
@@ -130,6 +135,70 @@ __global__ void __launch_bounds__(32 * WARPS) k_panel_step(PanelArgs<T> a, int s
     }
   }
 }
+
+template <class T>
+__global__ void __launch_bounds__(32 * WARPS) k_panel_step(PanelArgs<T> a, int s) {
+  panel_step_body(a, s);
+}
+
+// Grid-wide barrier of the persistent panel kernel (all CTAs co-resident by
+// the cooperative launch).  Every wait is bounded: after `spin_limit` polls
+// the CTA sets gb->err and all CTAs leave at their next barrier.
+struct GridBar {
+  unsigned count, gen;
+  int err, pad;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned nblocks, unsigned& my_gen, long long spin_limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = my_gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&gb->count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*(volatile unsigned*)&gb->gen == g) {
+        if (++spins > spin_limit || *(volatile int*)&gb->err) {
+          atomicExch(&gb->err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = *(volatile int*)&gb->err == 0;
+  }
+  ++my_gen;
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The whole panel in one cooperative launch: the w + 1 column steps are
+// separated by grid barriers instead of kernel boundaries.
+template <class T>
+__global__ void __launch_bounds__(32 * WARPS) k_panel_coop(PanelArgs<T> a, T* partA, T* partB, GridBar* gb,
+                                                          long long spin_limit) {
+  unsigned my_gen = 0;
+  for (int s = 0; s <= a.w; ++s) {
+    a.part_prev = (s & 1) ? partA : partB;
+    a.part_cur = (s & 1) ? partB : partA;
+    panel_step_body(a, s);
+    if (s < a.w && !grid_sync(gb, gridDim.x, my_gen, spin_limit)) return;
+  }
+}
+
+// Self-test of the bounded barrier: `nblocks` is one more than the CTAs
+// launched, so the barrier never completes and every wait must time out.
+__global__ void k_barrier_timeout_probe(GridBar* gb, unsigned nblocks, long long spin_limit) {
+  unsigned my_gen = 0;
+  grid_sync(gb, nblocks, my_gen, spin_limit);
+}
+
 
 // Z = sum over splits of the V^T V and V^T C partials.
 template <class T>
@@ -229,18 +298,39 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
   T* Z = ar.take<T>(NB * (NB + q.ldz));
   T* Tm = ar.take<T>(NB * NB);
   T* Bp = ar.take<T>(NB * q.ldz);
-  if (!ar.ok() || !Bp) return SKI_ENOMEM;
+  GridBar* gb = ar.take<GridBar>(1);
+  if (!ar.ok() || !gb) return SKI_ENOMEM;
+  // cooperative persistent panels when every panel CTA can be co-resident
+  bool coop = false;
+  {
+    int dev = 0, can = 0, per_sm = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&can, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_coop<T>, 32 * WARPS, 0) == cudaSuccess)
+      coop = can && (int64_t)per_sm * sms >= q.ncta_max;
+    cudaGetLastError();
+  }
   for (int64_t k0 = 0; k0 < d; k0 += NB) {
     const int w = (int)std::min<int64_t>(NB, d - k0);
     const int64_t mr = m - k0;
     const int ncta = (int)std::min<int64_t>(q.ncta_max, ski_cdiv(mr, 64));
     const int64_t rows_per = ski_cdiv(mr, ncta);
     PanelArgs<T> pa{B + k0 * ld + k0, ld, mr, w, rows_per, ncta, nullptr, nullptr, tau, V};
-    for (int s = 0; s <= w; ++s) {
-      pa.part_prev = (s & 1) ? partA : partB;
-      pa.part_cur = (s & 1) ? partB : partA;
-      k_panel_step<T><<<ncta, 32 * WARPS, 0, st>>>(pa, s);
+    if (coop) {
+      SKI_CUDA_TRY(cudaMemsetAsync(gb, 0, sizeof(GridBar), st));
+      long long lim = kSpinLimit;
+      void* args[] = {&pa, &partA, &partB, &gb, &lim};
+      SKI_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop<T>, dim3(ncta), dim3(32 * WARPS), args, 0,
+                                               st));
       SKI_LAUNCH_CHECK();
+    } else {
+      for (int s = 0; s <= w; ++s) {
+        pa.part_prev = (s & 1) ? partA : partB;
+        pa.part_cur = (s & 1) ? partB : partA;
+        k_panel_step<T><<<ncta, 32 * WARPS, 0, st>>>(pa, s);
+        SKI_LAUNCH_CHECK();
+      }
     }
     const int64_t nct = ncols - (k0 + w);
     // V^T V (split-K over rows) and V^T C
@@ -268,6 +358,12 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
   }
   k_extract_r<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, B, ld, with_rhs, R, ldr, qtsb);
   SKI_LAUNCH_CHECK();
+  if (coop) {
+    GridBar h;
+    SKI_CUDA_TRY(cudaMemcpyAsync(&h, gb, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SKI_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h.err) return SKI_ETIMEOUT;
+  }
   return SKI_OK;
 }
 
@@ -286,6 +382,7 @@ size_t ski_qr_ws_bytes(int64_t m, int64_t ncols, int32_t dtype) {
   ar.take<char>(es * NB * (NB + q.ldz));
   ar.take<char>(es * NB * NB);
   ar.take<char>(es * NB * q.ldz);
+  ar.take<GridBar>(1);
   return ar.off;
 }
 
@@ -294,4 +391,20 @@ ski_status ski_qr_run(int64_t m, int64_t d, int32_t with_rhs, void* SA, int64_t 
   if (dtype == SKI_F64) return qr_impl<double>(m, d, with_rhs, (double*)SA, ld_sa, R, ldr, qtsb, ar, st);
   if (dtype == SKI_F32) return qr_impl<float>(m, d, with_rhs, (float*)SA, ld_sa, R, ldr, qtsb, ar, st);
   return SKI_EINVAL;
+}
+
+// Self-test of the bounded grid barrier used by the persistent panel kernel:
+// 4 co-resident CTAs wait for a fifth that never arrives; each wait gives up
+// after `spin_limit` polls and the error flag must come back set.
+ski_status ski_barrier_selftest(long long spin_limit, void* ws, cudaStream_t st) {
+  GridBar* gb = (GridBar*)ws;
+  SKI_CUDA_TRY(cudaMemsetAsync(gb, 0, sizeof(GridBar), st));
+  unsigned nb = 5;
+  void* args[] = {&gb, &nb, &spin_limit};
+  SKI_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_barrier_timeout_probe, dim3(4), dim3(32), args, 0, st));
+  SKI_LAUNCH_CHECK();
+  GridBar h;
+  SKI_CUDA_TRY(cudaMemcpyAsync(&h, gb, sizeof(h), cudaMemcpyDeviceToHost, st));
+  SKI_CUDA_TRY(cudaStreamSynchronize(st));
+  return h.err ? SKI_ETIMEOUT : SKI_OK;
 }

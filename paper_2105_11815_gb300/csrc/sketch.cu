@@ -162,53 +162,70 @@ template <class TOUT>
 __global__ void __launch_bounds__(128) k_sketch_dense_f64acc(
     const double* __restrict__ A, int64_t lda, int64_t nrows, int64_t d, const double* __restrict__ b,
     const int64_t* __restrict__ offsets, const uint32_t* __restrict__ list, long long scale_c, int scale_e,
-    TOUT* __restrict__ SA, int64_t ld_sa) {
-  constexpr int CPT = 4;
-  const int64_t i = blockIdx.x;
+    TOUT* __restrict__ SA, int64_t ld_sa, int64_t m) {
+  constexpr int CPT = 4, BPC = 4;  // columns per thread, buckets per CTA
   const int64_t ncols = d + (b != nullptr);
   const int64_t cb = (int64_t)blockIdx.y * (CPT * 128) + threadIdx.x;
-  const int64_t lo = offsets[i], hi = offsets[i + 1];
-  FxGather acc[CPT];
+  const int64_t cfirst = (int64_t)blockIdx.y * (CPT * 128);
+  const int64_t ccount = max((int64_t)0, min((int64_t)(CPT * 128), d - cfirst));
+  const int64_t i0 = (int64_t)blockIdx.x * BPC;
+  // bulk L2 prefetch of this CTA's column chunk of every row of bucket i
+  auto prefetch = [&](int64_t i) {
+    if (i >= m || ccount == 0) return;
+    const int64_t lo = offsets[i], hi = offsets[i + 1];
+    for (int64_t e = lo + threadIdx.x / 8; e < hi; e += 16) {
+      const int64_t j = list[e] >> 1;
+      ski_l2_prefetch_range(A + j * lda + cfirst, (size_t)ccount * sizeof(double), threadIdx.x & 7, 8);
+    }
+  };
+  prefetch(i0);
+  for (int bi = 0; bi < BPC; ++bi) {
+    const int64_t i = i0 + bi;
+    if (i >= m) break;
+    prefetch(i + 1);
+    const int64_t lo = offsets[i], hi = offsets[i + 1];
+    FxGather acc[CPT];
 #pragma unroll
-  for (int k = 0; k < CPT; ++k) acc[k].init();
-  int64_t e = lo;
-  for (; e + 4 <= hi; e += 4) {
-    uint32_t en[4];
+    for (int k = 0; k < CPT; ++k) acc[k].init();
+    int64_t e = lo;
+    for (; e + 4 <= hi; e += 4) {
+      uint32_t en[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) en[u] = __ldg(&list[e + u]);
-    double v[4][CPT];
+      for (int u = 0; u < 4; ++u) en[u] = __ldg(&list[e + u]);
+      double v[4][CPT];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t j = en[u] >> 1;
+      for (int u = 0; u < 4; ++u) {
+        const int64_t j = en[u] >> 1;
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+          const int64_t c = cb + k * 128;
+          v[u][k] = c < d ? __ldcs(&A[j * lda + c]) : (c == d && b ? __ldg(&b[j]) : 0.0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) acc[k].add(v[u][k], en[u] & 1u);
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) acc[k].renorm();
+    }
+    for (; e < hi; ++e) {
+      const uint32_t en = __ldg(&list[e]);
+      const int64_t j = en >> 1;
 #pragma unroll
       for (int k = 0; k < CPT; ++k) {
         const int64_t c = cb + k * 128;
-        v[u][k] = c < d ? __ldcs(&A[j * lda + c]) : (c == d && b ? __ldg(&b[j]) : 0.0);
+        const double v = c < d ? __ldcs(&A[j * lda + c]) : (c == d && b ? __ldg(&b[j]) : 0.0);
+        acc[k].add(v, en & 1u);
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int k = 0; k < CPT; ++k) acc[k].add(v[u][k], en[u] & 1u);
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) acc[k].renorm();
-  }
-  for (; e < hi; ++e) {
-    const uint32_t en = __ldg(&list[e]);
-    const int64_t j = en >> 1;
-#pragma unroll
     for (int k = 0; k < CPT; ++k) {
       const int64_t c = cb + k * 128;
-      const double v = c < d ? __ldcs(&A[j * lda + c]) : (c == d && b ? __ldg(&b[j]) : 0.0);
-      acc[k].add(v, en & 1u);
+      if (c < ncols) SA[i * ld_sa + c] = SkiType<TOUT>::from(fxg_scaled(acc[k], scale_c, scale_e));
     }
   }
   (void)nrows;
-#pragma unroll
-  for (int k = 0; k < CPT; ++k) {
-    const int64_t c = cb + k * 128;
-    if (c < ncols) SA[i * ld_sa + c] = SkiType<TOUT>::from(fxg_scaled(acc[k], scale_c, scale_e));
-  }
 }
 
 template <class TOUT>
@@ -360,9 +377,9 @@ ski_status ski_gather_dense(const double* A, int64_t lda, int64_t nrows, int64_t
     long long c;
     int e;
     scale_fixed(scale, &c, &e);
-    dim3 grid64((unsigned)bk.m, (unsigned)ski_cdiv(ncols, 4 * T));
+    dim3 grid64((unsigned)ski_cdiv(bk.m, 4), (unsigned)ski_cdiv(ncols, 4 * T));
     k_sketch_dense_f64acc<double><<<grid64, T, 0, st>>>(A, lda, nrows, d, b, bk.offsets, bk.list, c, e,
-                                                       (double*)SA, ld_sa);
+                                                       (double*)SA, ld_sa, bk.m);
   } else if (out_dtype == SKI_F32) {
     k_sketch_dense_f32acc<float><<<grid, T, 0, st>>>(A, lda, d, b, bk.offsets, bk.list, (float)scale,
                                                      (float*)SA, ld_sa);

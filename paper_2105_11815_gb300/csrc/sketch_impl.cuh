@@ -42,6 +42,8 @@ size_t ski_qr_ws_bytes(int64_t m, int64_t ncols, int32_t dtype);
 ski_status ski_qr_run(int64_t m, int64_t d, int32_t with_rhs, void* SA, int64_t ld_sa, int32_t dtype,
                       double* R, int64_t ldr, double* qtsb, SkiArena& ar, cudaStream_t st);
 
+ski_status ski_barrier_selftest(long long spin_limit, void* ws, cudaStream_t st);
+
 // ---- trinv.cu
 size_t ski_trinv_ws_bytes(int64_t d, int32_t dtype);
 ski_status ski_trinv_run(int64_t d, const double* R, int64_t ldr, double* M, double* Mt, int64_t ldm,
