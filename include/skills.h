@@ -211,6 +211,19 @@ ski_status ski_precondition(int64_t m, int64_t d, int32_t with_rhs, void* SA, in
                             void* stream);
 
 /*
+ * ski_gemm_tc_f32 -- C = A B^T (subtract = 0) or C -= A B^T (subtract = 1)
+ * on the TF32 tensor cores with FP32 accumulation: the kernel of the FP32
+ * trailing update of Step 2, exposed for testing and reuse.  A: M x K,
+ * B: N x K, C: M x N, all device FP32 row-major; lda and ldb multiples of 4
+ * with 16-byte aligned bases (SKI_EINVAL otherwise).  Products use the top
+ * 10 mantissa bits of each operand (TF32).  ws: device scratch >= 4 bytes
+ * (an error flag).  Synchronous; SKI_ETIMEOUT if a bounded wait gave up.
+ */
+ski_status ski_gemm_tc_f32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+                           int64_t ldb, float* C, int64_t ldc, int32_t subtract, void* ws, size_t ws_bytes,
+                           void* stream);
+
+/*
  * ski_trinv -- M = R^{-1} for an upper-triangular d x d R (FP64, row stride
  * ldr), written to M (FP64, row stride ldm; strict lower triangle zero) and
  * its transpose to Mt (row stride ldm) when Mt != NULL.  Computed in dtype

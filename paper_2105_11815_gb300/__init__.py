@@ -20,7 +20,7 @@ __all__ = [
     "ski_hash_indices", "ski_premix_signs", "ski_premix_workspace_size", "ski_premix",
     "ski_sketch_workspace_size", "ski_sketch_hash", "ski_sketch_hash_noalloc",
     "ski_precondition_workspace_size", "ski_precondition",
-    "ski_trinv_workspace_size", "ski_trinv",
+    "ski_gemm_tc_f32", "ski_trinv_workspace_size", "ski_trinv",
     "ski_solve_workspace_size", "ski_solve",
     "ski_solve_batched_workspace_size", "ski_solve_batched",
     "ski_solve_adjoint_workspace_size", "ski_solve_adjoint",
@@ -92,6 +92,7 @@ _SIGS = {
     "ski_sketch_hash_noalloc": (_I32, [_MP, _P, _OP, _P, _I64, _P]),
     "ski_precondition_workspace_size": (_SZ, [_I64, _I64, _I32, _I32]),
     "ski_precondition": (_I32, [_I64, _I64, _I32, _P, _I64, _I32, _P, _I64, _P, _P, _OP, _P, _SZ, _P]),
+    "ski_gemm_tc_f32": (_I32, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _P, _SZ, _P]),
     "ski_trinv_workspace_size": (_SZ, [_I64, _I32]),
     "ski_trinv": (_I32, [_I64, _P, _I64, _P, _P, _I64, _I32, _D, _P, _SZ, _P]),
     "ski_solve_workspace_size": (_SZ, [_MP, _OP]),
@@ -254,6 +255,14 @@ def ski_precondition(m, d, with_rhs, SA, ld_sa, sa_dtype, R, ldr, qtsb=None, wan
                                   ctypes.byref(rank) if want_rank else None, ctypes.byref(o), _ptr(w), nb,
                                   _stream(stream)), "ski_precondition")
     return rank.value if want_rank else None
+
+
+def ski_gemm_tc_f32(M, N, K, A, lda, B, ldb, C, ldc, subtract=False, ws=None, stream=None):
+    """C = A B^T (or C -= A B^T) on the TF32 tensor cores."""
+    import torch
+    w = ws if ws is not None else torch.zeros(16, dtype=torch.uint8, device=C.device)
+    return _check(lib().ski_gemm_tc_f32(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, int(subtract), _ptr(w),
+                                        16, _stream(stream)), "ski_gemm_tc_f32")
 
 
 def ski_trinv_workspace_size(d, dtype):

@@ -1,0 +1,294 @@
+// Tensor-core GEMM for the FP32 QR trailing update (Algorithm 1, Step 2):
+// D[M x N] = A[M x K] * B[N x K]^T with A and B K-major FP32 in global
+// memory, multiplied as TF32 by tcgen05.mma with the FP32 accumulator in
+// tensor memory, and stored (or subtracted) to a row-major C.
+//
+// One CTA computes one BM x BN tile (BM = 128 rows = 128 TMEM lanes, BN up to
+// 256 TMEM columns), K in steps of BK = 32 FP32 (128 bytes, one 128-byte
+// swizzle row).  Four warps:
+//   warp 0, lane 0   TMA producer: 2-D tensor-map copies of the A and B
+//                    tiles into a STAGES-deep shared-memory ring (128B swizzle)
+//   warp 1           allocates TMEM; lane 0 issues 4 tcgen05.mma per stage
+//                    (K = 8 each) and commits each stage back to the producer
+//   warps 0..3       epilogue: tcgen05.ld of their 32 TMEM lanes, store to C
+// Every mbarrier wait is bounded: after kSpinLimit polls the CTA raises the
+// error flag, drains its outstanding copies (again bounded), frees its TMEM
+// and returns.
+#include <cuda.h>
+
+#include "common.cuh"
+#include "sketch_impl.cuh"
+
+namespace {
+
+constexpr int BM = 128, BK = 32, STAGES = 4, NTHR = 128;
+constexpr long long kSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false (and the error flag set) when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 1023) == 1023 && *(volatile int*)err) return false;
+  }
+  atomicExch(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major operand in the 128-byte swizzle
+// canonical layout: 8-row groups 1024 bytes apart (stride byte offset),
+// descriptor version 1, layout type 2 (128B swizzle).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major.
+__host__ __device__ constexpr uint32_t tf32_idesc(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+template <int BN>
+struct TcSmem {
+  float A[STAGES][BM * BK];  // 16 KB per stage
+  float B[STAGES][BN * BK];  // BN * 128 bytes per stage
+  uint64_t full[STAGES], empty[STAGES], done;
+  uint32_t tmem;
+};
+
+// mode 0: C[m * ldc + n] = D; mode 1: C[m * ldc + n] -= D; mode 2: C[n * ldc + m] = D.
+template <int BN>
+__global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
+                                                      const __grid_constant__ CUtensorMap tb, int M, int N, int K,
+                                                      int kchunk, float* __restrict__ C, int64_t ldc,
+                                                      int64_t c_zstride, int mode, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TcSmem<BN>& sm = *reinterpret_cast<TcSmem<BN>*>(
+      (void*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+  C += (int64_t)blockIdx.z * c_zstride;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&sm.full[s]), 1);
+      mbar_init(smem_u32(&sm.empty[s]), 1);
+    }
+    mbar_init(smem_u32(&sm.done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
+                 "r"(BN < 32 ? 32 : BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sm.tmem;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    const uint32_t bytes = (uint32_t)(BM + BN) * BK * sizeof(float);
+    int issued = 0;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (!mbar_wait(smem_u32(&sm.empty[s]), ph ^ 1u, err)) break;
+      mbar_expect_tx(smem_u32(&sm.full[s]), bytes);
+      const int kx = kbeg + kt * BK;
+      tma_load_2d(smem_u32(sm.A[s]), &ta, kx, m0, smem_u32(&sm.full[s]));
+      tma_load_2d(smem_u32(sm.B[s]), &tb, kx, n0, smem_u32(&sm.full[s]));
+      ++issued;
+    }
+    if (issued < nk) {
+      // error: drain the copies already in flight before leaving (bounded)
+      for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt) {
+        const uint32_t bar = smem_u32(&sm.full[kt % STAGES]);
+        const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+        for (long long i = 0; i < kSpinLimit && !mbar_try(bar, ph); ++i) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = tf32_idesc(BM, BN);
+    bool ok = true;
+    for (int kt = 0; kt < nk && ok; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (!mbar_wait(smem_u32(&sm.full[s]), ph, err)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t abase = smem_u32(sm.A[s]), bbase = smem_u32(sm.B[s]);
+#pragma unroll
+      for (int kk = 0; kk < BK / 8; ++kk) {
+        const uint64_t ad = sw128_desc(abase + kk * 32);
+        const uint64_t bd = sw128_desc(bbase + kk * 32);
+        const uint32_t acc = (kt | kk) ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&sm.empty[s]))
+                   : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&sm.done))
+                 : "memory");
+  }
+  __syncwarp();
+  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31
+  bool have = nk > 0 && mbar_wait(smem_u32(&sm.done), 0u, err);
+  have = __all_sync(0xffffffffu, have && !*(volatile int*)err);  // warp-uniform for tcgen05.ld
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = m0 + warp * 32 + lane;
+  if (have) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < N) {
+            const float d = __uint_as_float(v[j]);
+            if (mode == 0) C[(int64_t)row * ldc + col] = d;
+            else if (mode == 1) C[(int64_t)row * ldc + col] -= d;
+            else C[(int64_t)col * ldc + row] = d;
+          }
+        }
+      }
+    }
+  } else if (nk == 0 && row < M) {
+    for (int j = 0; j < BN; ++j) {
+      const int col = n0 + j;
+      if (col < N) {
+        if (mode == 0) C[(int64_t)row * ldc + col] = 0.f;
+        else if (mode == 2) C[(int64_t)col * ldc + row] = 0.f;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN < 32 ? 32 : BN));
+  }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiled)p;
+  }
+  return fn;
+}
+
+// 2-D FP32 tensor map over a row-major (rows x cols) matrix with row stride
+// ld elements; box = box_rows x 32 columns, 128-byte swizzle.
+bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  EncodeTiled fn = encoder();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * sizeof(float))};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+ski_status launch(const float* A, int64_t lda, const float* B, int64_t ldb, int M, int N, int K, float* C,
+                  int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st) {
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, A, M, K, lda, BM) || !make_map(&tb, B, N, K, ldb, BN)) return SKI_ECUDA;
+  const size_t smem = sizeof(TcSmem<BN>) + 1024;
+  SKI_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int kchunk = (int)ski_round_up(ski_cdiv(K, splits), BK);
+  dim3 grid((unsigned)ski_cdiv(M, BM), (unsigned)ski_cdiv(N, BN), (unsigned)splits);
+  k_gemm_tc<BN><<<grid, NTHR, smem, st>>>(ta, tb, M, N, K, kchunk, C, ldc, c_zstride, mode, err);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+}  // namespace
+
+// D = A B^T (TF32 tensor cores, FP32 accumulate).  A: M x K, B: N x K, both
+// row-major (K contiguous) with row strides lda, ldb that are multiples of 4
+// and 16-byte aligned bases.  mode 0 stores C = D, 1 subtracts C -= D, 2
+// stores the transpose.  splits > 1 splits K, writing partials at
+// C + z * c_zstride (modes 0 and 2 only).
+ski_status ski_gemm_tf32(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
+                         float* C, int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return SKI_OK;
+  if ((lda & 3) || (ldb & 3) || ((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return SKI_EINVAL;
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return SKI_EINVAL;
+  if (N <= 32) return launch<32>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
+  if (N <= 64) return launch<64>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
+  return launch<256>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
+}
+
+extern "C" ski_status ski_gemm_tc_f32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+                                      int64_t ldb, float* C, int64_t ldc, int32_t subtract, void* ws,
+                                      size_t ws_bytes, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || !A || !B || !C || !ws || ws_bytes < sizeof(int)) return SKI_EINVAL;
+  if (lda < K || ldb < K || ldc < N) return SKI_EINVAL;
+  cudaStream_t st = ski_stream(stream);
+  int* err = (int*)ws;
+  SKI_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  SKI_TRY(ski_gemm_tf32(A, lda, B, ldb, M, N, K, C, ldc, subtract ? 1 : 0, 1, 0, err, st));
+  int h = 0;
+  SKI_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SKI_CUDA_TRY(cudaStreamSynchronize(st));
+  return h ? SKI_ETIMEOUT : SKI_OK;
+}

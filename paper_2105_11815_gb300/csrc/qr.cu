@@ -1,6 +1,12 @@
 // Step 2 of Algorithm 1: Householder QR of the sketch SA (m x d, m >= d),
 // blocked in panels of NB = 32 columns (compact WY form, Schreiber & Van Loan).
 //
+// The factorisation works on the transpose Ct = [SA | Sb]^T (column j of SA
+// contiguous), so that both trailing-update GEMMs read K-major operands:
+//   W^T = C^T V   (K = rows of the panel)   and   C^T -= B'^T V^T (K = 32),
+// which is the layout the TF32 tensor-core GEMM (gemm_tc.cu) consumes.  Each
+// panel is copied to a row-major scratch, factored there, and copied back.
+//
 // Panel: column j of the panel is reduced by one launch that (a) finalises
 // the reflector of column j-1 from the previous launch's partial sums --
 // beta = -sign(x0) ||x||, tau = (beta - x0) / beta, v = [1; x_rest / (x0 - beta)]
@@ -37,7 +43,11 @@ struct PanelArgs {
   const T* part_prev;
   T* part_cur;
   T* tau;
-  T* V;           // explicit reflectors, mr x NB, written by the last step
+  T* V;           // explicit reflectors, mr x NB (row-major), written by the last step
+  T* Vt;          // the same, transposed: NB x ldvt
+  int64_t ldvt;
+  T* Ct;          // &Ct[k0][k0]: panel column c, row r at Ct[c * ldt + r]
+  int64_t ldt;
 };
 
 template <class T>
@@ -58,6 +68,7 @@ __device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s) {
   if (s > 0) {
     // partial sums of the previous launch, split over the warps (fixed order)
     T g = T(0);
+#pragma unroll 8
     for (int b = warp; b < a.ncta; b += WARPS) g += __ldcg(&a.part_prev[(int64_t)b * PW + lane]);
     red[warp][lane] = g;
     __syncthreads();
@@ -121,6 +132,7 @@ __device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s) {
       // last step: explicit reflector block
       T v = (lane >= a.w || r < lane) ? T(0) : (r == lane ? T(1) : val);
       a.V[r * NB + lane] = v;
+      a.Vt[(int64_t)lane * a.ldvt + r] = v;
     }
   }
   if (s < a.w) {
@@ -134,6 +146,25 @@ __device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s) {
       a.part_cur[(int64_t)blockIdx.x * PW + lane] = t;
     }
   }
+}
+
+// Rows [r0, r1) of the panel between the column-major Ct and the row-major
+// scratch P (ld = NB); columns >= w of P are zero.
+template <class T>
+__device__ __forceinline__ void panel_copy(const PanelArgs<T>& a, bool in) {
+  const int64_t r0 = (int64_t)blockIdx.x * a.rows_per;
+  const int64_t r1 = min(a.mr, r0 + a.rows_per);
+  for (int c = 0; c < NB; ++c)
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+      if (in) a.P[r * NB + c] = c < a.w ? a.Ct[(int64_t)c * a.ldt + r] : T(0);
+      else if (c < a.w) a.Ct[(int64_t)c * a.ldt + r] = a.P[r * NB + c];
+    }
+  __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(32 * WARPS) k_panel_copy(PanelArgs<T> a, int in) {
+  panel_copy(a, in != 0);
 }
 
 template <class T>
@@ -184,12 +215,15 @@ template <class T>
 __global__ void __launch_bounds__(32 * WARPS) k_panel_coop(PanelArgs<T> a, T* partA, T* partB, GridBar* gb,
                                                           long long spin_limit) {
   unsigned my_gen = 0;
+  panel_copy(a, true);  // own rows only: no barrier needed
   for (int s = 0; s <= a.w; ++s) {
     a.part_prev = (s & 1) ? partA : partB;
     a.part_cur = (s & 1) ? partB : partA;
     panel_step_body(a, s);
     if (s < a.w && !grid_sync(gb, gridDim.x, my_gen, spin_limit)) return;
   }
+  __syncthreads();
+  panel_copy(a, false);
 }
 
 // Self-test of the bounded barrier: `nblocks` is one more than the CTAs
@@ -241,10 +275,11 @@ __global__ void k_tfactor(int w, const T* __restrict__ Z, int64_t ldzz, const T*
   for (int c = 0; c < NB; ++c) Tm[lane * NB + c] = Ts[lane][c];
 }
 
-// B' = T^T W, W = columns [w, w + nct) of Z.
+// B'^T[c][i] = (T^T W)[i][c] for i < w, 0 for w <= i < NB; W = columns
+// [w, w + nct) of Z.  Row-major nct x NB: the K-major operand of the update.
 template <class T>
 __global__ void k_ttw(int w, int64_t nct, const T* __restrict__ Z, int64_t ldzz, const T* __restrict__ Tm,
-                      T* __restrict__ Bp, int64_t ldb) {
+                      T* __restrict__ Bpt) {
   __shared__ T Ts[NB][NB];
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Ts[e / NB][e % NB] = Tm[e];
   __syncthreads();
@@ -253,27 +288,44 @@ __global__ void k_ttw(int w, int64_t nct, const T* __restrict__ Z, int64_t ldzz,
   T wcol[NB];
 #pragma unroll
   for (int k = 0; k < NB; ++k) wcol[k] = k < w ? Z[k * ldzz + w + c] : T(0);
-  for (int i = 0; i < w; ++i) {
+  for (int i = 0; i < NB; ++i) {
     T acc = T(0);
 #pragma unroll
     for (int k = 0; k < NB; ++k)
       if (k <= i) acc += Ts[k][i] * wcol[k];  // (T^T)[i,k] = T[k,i], nonzero for k <= i
-    Bp[i * ldb + c] = acc;
+    Bpt[c * NB + i] = i < w ? acc : T(0);
   }
 }
 
 template <class T>
-__global__ void k_extract_r(int64_t d, const T* __restrict__ B, int64_t ld, int with_rhs, double* __restrict__ R,
+__global__ void k_extract_r(int64_t d, const T* __restrict__ Ct, int64_t ldt, int with_rhs, double* __restrict__ R,
                             int64_t ldr, double* __restrict__ qtsb) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= d * d) return;
   int64_t i = idx / d, c = idx % d;
-  R[i * ldr + c] = c >= i ? SkiType<T>::to_f64(B[i * ld + c]) : 0.0;
-  if (c == 0 && with_rhs && qtsb) qtsb[i] = SkiType<T>::to_f64(B[i * ld + d]);
+  R[i * ldr + c] = c >= i ? SkiType<T>::to_f64(Ct[c * ldt + i]) : 0.0;
+  if (c == 0 && with_rhs && qtsb) qtsb[i] = SkiType<T>::to_f64(Ct[d * ldt + i]);
+}
+
+// Ct[c][r] = SA[r][c] through a 32 x 32 shared-memory tile.
+template <class T>
+__global__ void k_transpose(int64_t m, int64_t ncols, const T* __restrict__ SA, int64_t ld_sa, T* __restrict__ Ct,
+                            int64_t ldt) {
+  __shared__ T tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + k, c = c0 + threadIdx.x;
+    tile[k][threadIdx.x] = (r < m && c < ncols) ? SA[r * ld_sa + c] : T(0);
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c = c0 + k, r = r0 + threadIdx.x;
+    if (c < ncols && r < m) Ct[c * ldt + r] = tile[threadIdx.x][k];
+  }
 }
 
 struct QrWs {
-  int64_t ncta_max, splits_max, ldz;
+  int64_t ncta_max, splits_max, ldz, ldt;
 };
 
 QrWs qr_dims(int64_t m, int64_t ncols) {
@@ -281,25 +333,79 @@ QrWs qr_dims(int64_t m, int64_t ncols) {
   q.ncta_max = std::min<int64_t>(1024, ski_cdiv(m, 64));
   q.splits_max = 16;
   q.ldz = ski_round_up(ncols, 4);
+  q.ldt = ski_round_up(m, 32);  // 128-byte rows: TMA strides and K offsets stay aligned
   return q;
+}
+
+template <class T>
+struct QrBufs {
+  T *Ct, *P, *V, *Vt, *partA, *partB, *tau, *pv, *pc, *Z, *Tm, *Bpt;
+  GridBar* gb;
+  int* err;
+};
+
+// One carving sequence for the size query and the run.
+template <class T>
+QrBufs<T> qr_carve(SkiArena& ar, int64_t m, int64_t ncols) {
+  const QrWs q = qr_dims(m, ncols);
+  QrBufs<T> b;
+  b.Ct = ar.take<T>(ncols * q.ldt);
+  b.P = ar.take<T>(m * NB);
+  b.V = ar.take<T>(m * NB);
+  b.Vt = ar.take<T>(NB * q.ldt);
+  b.partA = ar.take<T>(q.ncta_max * PW);
+  b.partB = ar.take<T>(q.ncta_max * PW);
+  b.tau = ar.take<T>(NB);
+  b.pv = ar.take<T>(152 * NB * NB);
+  b.pc = ar.take<T>(q.splits_max * NB * q.ldz);
+  b.Z = ar.take<T>(NB * (NB + q.ldz));
+  b.Tm = ar.take<T>(NB * NB);
+  b.Bpt = ar.take<T>(q.ldz * NB);
+  b.gb = ar.take<GridBar>(1);
+  b.err = ar.take<int>(1);
+  return b;
+}
+
+template <class T>
+ski_status gemm_w(int64_t nct, int64_t mr, const T* Ctr, int64_t ldt, const T* Vt, T* pc, int64_t ldz, int sc,
+                  int* err, cudaStream_t st);
+template <>
+ski_status gemm_w<float>(int64_t nct, int64_t mr, const float* Ctr, int64_t ldt, const float* Vt, float* pc,
+                         int64_t ldz, int sc, int* err, cudaStream_t st) {
+  // W^T(c, i) = sum_r Ct[c][r] Vt[i][r] on the tensor cores, stored as W[i][c]
+  return ski_gemm_tf32(Ctr, ldt, Vt, ldt, nct, NB, mr, pc, ldz, 2, sc, (int64_t)NB * ldz, err, st);
+}
+template <>
+ski_status gemm_w<double>(int64_t nct, int64_t mr, const double* Ctr, int64_t ldt, const double* Vt, double* pc,
+                          int64_t ldz, int sc, int* err, cudaStream_t st) {
+  (void)err;
+  return ski_gemm_ex<double>(NB, nct, mr, 1.0, Vt, ldt, 1, Ctr, 1, ldt, 0.0, pc, ldz, sc, (int64_t)NB * ldz, st);
+}
+
+template <class T>
+ski_status gemm_update(int64_t nct, int64_t mr, const T* Bpt, const T* V, T* Ctr, int64_t ldt, int* err,
+                       cudaStream_t st);
+template <>
+ski_status gemm_update<float>(int64_t nct, int64_t mr, const float* Bpt, const float* V, float* Ctr, int64_t ldt,
+                              int* err, cudaStream_t st) {
+  // Ct[c][r] -= sum_i B'^T[c][i] V[r][i] on the tensor cores (K = 32)
+  return ski_gemm_tf32(Bpt, NB, V, NB, nct, mr, NB, Ctr, ldt, 1, 1, 0, err, st);
+}
+template <>
+ski_status gemm_update<double>(int64_t nct, int64_t mr, const double* Bpt, const double* V, double* Ctr, int64_t ldt,
+                               int* err, cudaStream_t st) {
+  (void)err;
+  return ski_gemm<double>(nct, mr, NB, -1.0, Bpt, NB, 1, V, 1, NB, 1.0, Ctr, ldt, st);
 }
 
 template <class T>
 ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, double* R, int64_t ldr, double* qtsb,
                    SkiArena& ar, cudaStream_t st) {
   const int64_t ncols = d + (with_rhs ? 1 : 0);
-  QrWs q = qr_dims(m, ncols);
-  T* partA = ar.take<T>(q.ncta_max * PW);
-  T* partB = ar.take<T>(q.ncta_max * PW);
-  T* tau = ar.take<T>(NB);
-  T* V = ar.take<T>(m * NB);
-  T* pv = ar.take<T>(152 * NB * NB);
-  T* pc = ar.take<T>(q.splits_max * NB * q.ldz);
-  T* Z = ar.take<T>(NB * (NB + q.ldz));
-  T* Tm = ar.take<T>(NB * NB);
-  T* Bp = ar.take<T>(NB * q.ldz);
-  GridBar* gb = ar.take<GridBar>(1);
-  if (!ar.ok() || !gb) return SKI_ENOMEM;
+  const QrWs q = qr_dims(m, ncols);
+  QrBufs<T> bf = qr_carve<T>(ar, m, ncols);
+  if (!ar.ok() || !bf.err) return SKI_ENOMEM;
+  const int64_t ldt = q.ldt;
   // cooperative persistent panels when every panel CTA can be co-resident
   bool coop = false;
   {
@@ -308,81 +414,87 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
         cudaDeviceGetAttribute(&can, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_coop<T>, 32 * WARPS, 0) == cudaSuccess)
-      coop = can && (int64_t)per_sm * sms >= q.ncta_max;
+      coop = can && (int64_t)per_sm * sms >= 64;
     cudaGetLastError();
   }
+  SKI_CUDA_TRY(cudaMemsetAsync(bf.err, 0, sizeof(int), st));
+  SKI_CUDA_TRY(cudaMemsetAsync(bf.gb, 0, sizeof(GridBar), st));
+  {
+    dim3 grid((unsigned)ski_cdiv(m, 32), (unsigned)ski_cdiv(ncols, 32));
+    k_transpose<T><<<grid, dim3(32, 8), 0, st>>>(m, ncols, B, ld, bf.Ct, ldt);
+    SKI_LAUNCH_CHECK();
+  }
+  int timed_out = 0;
   for (int64_t k0 = 0; k0 < d; k0 += NB) {
     const int w = (int)std::min<int64_t>(NB, d - k0);
     const int64_t mr = m - k0;
-    const int ncta = (int)std::min<int64_t>(q.ncta_max, ski_cdiv(mr, 64));
+    // few, fat CTAs: each column step reads every CTA's partials and meets
+    // at a grid barrier, so both costs grow with the CTA count
+    const int ncta = (int)std::min<int64_t>(std::min<int64_t>(q.ncta_max, 64), ski_cdiv(mr, 128));
     const int64_t rows_per = ski_cdiv(mr, ncta);
-    PanelArgs<T> pa{B + k0 * ld + k0, ld, mr, w, rows_per, ncta, nullptr, nullptr, tau, V};
+    T* Ctp = bf.Ct + k0 * ldt + k0;
+    PanelArgs<T> pa{bf.P, NB, mr, w, rows_per, ncta, nullptr, nullptr, bf.tau, bf.V, bf.Vt, ldt, Ctp, ldt};
     if (coop) {
-      SKI_CUDA_TRY(cudaMemsetAsync(gb, 0, sizeof(GridBar), st));
+      SKI_CUDA_TRY(cudaMemsetAsync(bf.gb, 0, 2 * sizeof(unsigned), st));  // count, gen (keep err)
       long long lim = kSpinLimit;
-      void* args[] = {&pa, &partA, &partB, &gb, &lim};
+      void* args[] = {&pa, &bf.partA, &bf.partB, &bf.gb, &lim};
       SKI_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop<T>, dim3(ncta), dim3(32 * WARPS), args, 0,
                                                st));
       SKI_LAUNCH_CHECK();
     } else {
+      k_panel_copy<T><<<ncta, 32 * WARPS, 0, st>>>(pa, 1);
+      SKI_LAUNCH_CHECK();
       for (int s = 0; s <= w; ++s) {
-        pa.part_prev = (s & 1) ? partA : partB;
-        pa.part_cur = (s & 1) ? partB : partA;
+        pa.part_prev = (s & 1) ? bf.partA : bf.partB;
+        pa.part_cur = (s & 1) ? bf.partB : bf.partA;
         k_panel_step<T><<<ncta, 32 * WARPS, 0, st>>>(pa, s);
         SKI_LAUNCH_CHECK();
       }
+      k_panel_copy<T><<<ncta, 32 * WARPS, 0, st>>>(pa, 0);
+      SKI_LAUNCH_CHECK();
     }
     const int64_t nct = ncols - (k0 + w);
-    // V^T V (split-K over rows) and V^T C
+    T* Ctr = bf.Ct + (k0 + w) * ldt + k0;  // trailing columns, rows k0..m-1
+    // V^T V (split-K over rows) and W = V^T C
     const int sv = (int)std::min<int64_t>(152, ski_cdiv(mr, 64));
-    SKI_TRY(ski_gemm_ex<T>(NB, NB, mr, T(1), V, 1, NB, V, NB, 1, T(0), pv, NB, sv, (int64_t)NB * NB, st));
+    SKI_TRY(ski_gemm_ex<T>(NB, NB, mr, T(1), bf.Vt, ldt, 1, bf.Vt, 1, ldt, T(0), bf.pv, NB, sv, (int64_t)NB * NB, st));
     int sc = 1;
     if (nct > 0) {
-      int64_t tiles = ski_cdiv(nct, 64);
-      sc = (int)std::max<int64_t>(1, std::min<int64_t>(q.splits_max, ski_cdiv(600, tiles)));
-      sc = (int)std::min<int64_t>(sc, ski_cdiv(mr, 64));
-      SKI_TRY(ski_gemm_ex<T>(NB, nct, mr, T(1), V, 1, NB, B + k0 * ld + k0 + w, ld, 1, T(0), pc, q.ldz, sc,
-                             (int64_t)NB * q.ldz, st));
+      const int64_t tiles = ski_cdiv(nct, 128);
+      sc = (int)std::max<int64_t>(1, std::min<int64_t>(q.splits_max, ski_cdiv(300, tiles)));
+      sc = (int)std::min<int64_t>(sc, ski_cdiv(mr, 128));
+      SKI_TRY(gemm_w<T>(nct, mr, Ctr, ldt, bf.Vt, bf.pc, q.ldz, sc, bf.err, st));
     }
     const int64_t zc = w + nct;
-    k_reduce_z<T><<<ski_cdiv(w * zc, 256), 256, 0, st>>>(w, nct, pv, sv, pc, sc, q.ldz, Z);
+    k_reduce_z<T><<<ski_cdiv(w * zc, 256), 256, 0, st>>>(w, nct, bf.pv, sv, bf.pc, sc, q.ldz, bf.Z);
     SKI_LAUNCH_CHECK();
-    k_tfactor<T><<<1, 32, 0, st>>>(w, Z, NB + q.ldz, tau, Tm);
+    k_tfactor<T><<<1, 32, 0, st>>>(w, bf.Z, NB + q.ldz, bf.tau, bf.Tm);
     SKI_LAUNCH_CHECK();
     if (nct > 0) {
-      k_ttw<T><<<ski_cdiv(nct, 128), 128, 0, st>>>(w, nct, Z, NB + q.ldz, Tm, Bp, q.ldz);
+      k_ttw<T><<<ski_cdiv(nct, 128), 128, 0, st>>>(w, nct, bf.Z, NB + q.ldz, bf.Tm, bf.Bpt);
       SKI_LAUNCH_CHECK();
-      // C -= V B'
-      SKI_TRY(ski_gemm<T>(mr, nct, w, T(-1), V, NB, 1, Bp, q.ldz, 1, T(1), B + k0 * ld + k0 + w, ld, st));
+      SKI_TRY(gemm_update<T>(nct, mr, bf.Bpt, bf.V, Ctr, ldt, bf.err, st));
     }
   }
-  k_extract_r<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, B, ld, with_rhs, R, ldr, qtsb);
+  k_extract_r<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, bf.Ct, ldt, with_rhs, R, ldr, qtsb);
   SKI_LAUNCH_CHECK();
-  if (coop) {
+  {
     GridBar h;
-    SKI_CUDA_TRY(cudaMemcpyAsync(&h, gb, sizeof(h), cudaMemcpyDeviceToHost, st));
+    int e = 0;
+    SKI_CUDA_TRY(cudaMemcpyAsync(&h, bf.gb, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SKI_CUDA_TRY(cudaMemcpyAsync(&e, bf.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     SKI_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h.err) return SKI_ETIMEOUT;
+    timed_out = h.err || e;
   }
-  return SKI_OK;
+  return timed_out ? SKI_ETIMEOUT : SKI_OK;
 }
 
 }  // namespace
 
 size_t ski_qr_ws_bytes(int64_t m, int64_t ncols, int32_t dtype) {
-  QrWs q = qr_dims(m, ncols);
-  size_t es = dtype == SKI_F64 ? 8 : 4;
   SkiArena ar{nullptr, 0, 0, true};
-  ar.take<char>(es * q.ncta_max * PW);
-  ar.take<char>(es * q.ncta_max * PW);
-  ar.take<char>(es * NB);
-  ar.take<char>(es * m * NB);
-  ar.take<char>(es * 152 * NB * NB);
-  ar.take<char>(es * q.splits_max * NB * q.ldz);
-  ar.take<char>(es * NB * (NB + q.ldz));
-  ar.take<char>(es * NB * NB);
-  ar.take<char>(es * NB * q.ldz);
-  ar.take<GridBar>(1);
+  if (dtype == SKI_F64) qr_carve<double>(ar, m, ncols);
+  else qr_carve<float>(ar, m, ncols);
   return ar.off;
 }
 

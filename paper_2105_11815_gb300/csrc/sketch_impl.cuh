@@ -44,6 +44,10 @@ ski_status ski_qr_run(int64_t m, int64_t d, int32_t with_rhs, void* SA, int64_t 
 
 ski_status ski_barrier_selftest(long long spin_limit, void* ws, cudaStream_t st);
 
+// ---- gemm_tc.cu: D = A B^T on the TF32 tensor cores (see there for modes)
+ski_status ski_gemm_tf32(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
+                         float* C, int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st);
+
 // ---- trinv.cu
 size_t ski_trinv_ws_bytes(int64_t d, int32_t dtype);
 ski_status ski_trinv_run(int64_t d, const double* R, int64_t ldr, double* M, double* Mt, int64_t ldm,
