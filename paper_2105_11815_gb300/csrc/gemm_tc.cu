@@ -78,6 +78,7 @@ template <int BN>
 struct TcSmem {
   float A[STAGES][BM * BK];  // 16 KB per stage
   float B[STAGES][BN * BK];  // BN * 128 bytes per stage
+  float stage[4][32][33];     // epilogue staging, one 32 x 32 block per warp
   uint64_t full[STAGES], empty[STAGES], done;
   uint32_t tmem;
 };
@@ -178,27 +179,43 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
   const int row = m0 + warp * 32 + lane;
   if (have) {
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      uint32_t v[16];
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
       asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-          "%14, %15}, [%16];"
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+          "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
           : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
+      if (mode == 2) {
+        // transposed store: consecutive lanes (rows) are consecutive addresses
+        if (row < M)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c0 + j;
-          if (col < N) {
-            const float d = __uint_as_float(v[j]);
-            if (mode == 0) C[(int64_t)row * ldc + col] = d;
-            else if (mode == 1) C[(int64_t)row * ldc + col] -= d;
-            else C[(int64_t)col * ldc + row] = d;
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + c0 + j;
+            if (col < N) C[(int64_t)col * ldc + row] = __uint_as_float(v[j]);
+          }
+      } else {
+        // row-major C: stage the warp's 32 x 32 block in shared memory so that
+        // each store instruction covers 32 consecutive columns of one row
+        float(*st)[33] = sm.stage[warp];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) st[lane][j] = __uint_as_float(v[j]);
+        __syncwarp();
+        const int col = n0 + c0 + lane;
+        for (int rr = 0; rr < 32; ++rr) {
+          const int r = m0 + warp * 32 + rr;
+          if (r < M && col < N) {
+            float* cp = &C[(int64_t)r * ldc + col];
+            if (mode == 0) *cp = st[rr][lane];
+            else *cp -= st[rr][lane];
           }
         }
+        __syncwarp();
       }
     }
   } else if (nk == 0 && row < M) {

@@ -149,17 +149,34 @@ __device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s) {
 }
 
 // Rows [r0, r1) of the panel between the column-major Ct and the row-major
-// scratch P (ld = NB); columns >= w of P are zero.
+// scratch P (ld = NB); columns >= w of P are zero.  Moved in 32 x 32 tiles
+// through shared memory so that both sides are accessed in 128-byte rows.
 template <class T>
 __device__ __forceinline__ void panel_copy(const PanelArgs<T>& a, bool in) {
+  __shared__ T tile[NB][NB + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * a.rows_per;
   const int64_t r1 = min(a.mr, r0 + a.rows_per);
-  for (int c = 0; c < NB; ++c)
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-      if (in) a.P[r * NB + c] = c < a.w ? a.Ct[(int64_t)c * a.ldt + r] : T(0);
-      else if (c < a.w) a.Ct[(int64_t)c * a.ldt + r] = a.P[r * NB + c];
+  for (int64_t rb = r0; rb < r1; rb += NB) {
+    if (in) {
+      for (int c = warp; c < NB; c += WARPS) {
+        const int64_t r = rb + lane;
+        tile[c][lane] = (c < a.w && r < r1) ? a.Ct[(int64_t)c * a.ldt + r] : T(0);
+      }
+      __syncthreads();
+      for (int i = warp; i < NB; i += WARPS)
+        if (rb + i < r1) a.P[(rb + i) * NB + lane] = tile[lane][i];
+    } else {
+      for (int i = warp; i < NB; i += WARPS)
+        if (rb + i < r1) tile[lane][i] = a.P[(rb + i) * NB + lane];
+      __syncthreads();
+      for (int c = warp; c < a.w; c += WARPS) {
+        const int64_t r = rb + lane;
+        if (r < r1) a.Ct[(int64_t)c * a.ldt + r] = tile[c][lane];
+      }
     }
-  __syncthreads();
+    __syncthreads();
+  }
 }
 
 template <class T>
@@ -210,20 +227,35 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned nblocks, unsigne
 }
 
 // The whole panel in one cooperative launch: the w + 1 column steps are
-// separated by grid barriers instead of kernel boundaries.
+// separated by grid barriers instead of kernel boundaries, and each CTA keeps
+// its slab of panel rows in shared memory for all of them (row stride
+// NB + 1 against bank conflicts), so a step's row sweep never leaves the SM.
 template <class T>
 __global__ void __launch_bounds__(32 * WARPS) k_panel_coop(PanelArgs<T> a, T* partA, T* partB, GridBar* gb,
                                                           long long spin_limit) {
+  extern __shared__ __align__(16) unsigned char slab_raw[];
+  T* slab = reinterpret_cast<T*>(slab_raw);
   unsigned my_gen = 0;
-  panel_copy(a, true);  // own rows only: no barrier needed
+  const int64_t r0 = (int64_t)blockIdx.x * a.rows_per;
+  const int64_t r1 = min(a.mr, r0 + a.rows_per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // copy-in: column c of the panel (contiguous in Ct) -> slab row-major
+  for (int c = warp; c < NB; c += WARPS)
+    for (int64_t r = r0 + lane; r < r1; r += 32)
+      slab[(r - r0) * (NB + 1) + c] = c < a.w ? a.Ct[(int64_t)c * a.ldt + r] : T(0);
+  __syncthreads();
+  PanelArgs<T> b = a;
+  b.P = slab - r0 * (NB + 1);  // indexed with global panel rows r in [r0, r1)
+  b.ld = NB + 1;
   for (int s = 0; s <= a.w; ++s) {
-    a.part_prev = (s & 1) ? partA : partB;
-    a.part_cur = (s & 1) ? partB : partA;
-    panel_step_body(a, s);
+    b.part_prev = (s & 1) ? partA : partB;
+    b.part_cur = (s & 1) ? partB : partA;
+    panel_step_body(b, s);
     if (s < a.w && !grid_sync(gb, gridDim.x, my_gen, spin_limit)) return;
   }
   __syncthreads();
-  panel_copy(a, false);
+  for (int c = warp; c < a.w; c += WARPS)
+    for (int64_t r = r0 + lane; r < r1; r += 32) a.Ct[(int64_t)c * a.ldt + r] = slab[(r - r0) * (NB + 1) + c];
 }
 
 // Self-test of the bounded barrier: `nblocks` is one more than the CTAs
@@ -409,14 +441,14 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
   // cooperative persistent panels when every panel CTA can be co-resident
   bool coop = false;
   {
-    int dev = 0, can = 0, per_sm = 0, sms = 0;
+    int dev = 0, can = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&can, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_coop<T>, 32 * WARPS, 0) == cudaSuccess)
-      coop = can && (int64_t)per_sm * sms >= 64;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      coop = can != 0;
     cudaGetLastError();
   }
+  const int64_t max_slab_rows = (200 * 1024) / ((NB + 1) * (int64_t)sizeof(T));
   SKI_CUDA_TRY(cudaMemsetAsync(bf.err, 0, sizeof(int), st));
   SKI_CUDA_TRY(cudaMemsetAsync(bf.gb, 0, sizeof(GridBar), st));
   {
@@ -430,16 +462,24 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     const int64_t mr = m - k0;
     // few, fat CTAs: each column step reads every CTA's partials and meets
     // at a grid barrier, so both costs grow with the CTA count
-    const int ncta = (int)std::min<int64_t>(std::min<int64_t>(q.ncta_max, 64), ski_cdiv(mr, 128));
+    int ncta = (int)std::min<int64_t>(std::min<int64_t>(q.ncta_max, 64), ski_cdiv(mr, 128));
+    // the persistent kernel keeps each CTA's rows in shared memory: one CTA per
+    // SM at most, so the slab must fit and the CTAs must fit on the SMs
+    const int ncta_coop = (int)std::max<int64_t>(ncta, ski_cdiv(mr, max_slab_rows));
+    const bool use_coop = coop && ncta_coop <= 148;
+    if (use_coop) ncta = ncta_coop;
     const int64_t rows_per = ski_cdiv(mr, ncta);
     T* Ctp = bf.Ct + k0 * ldt + k0;
     PanelArgs<T> pa{bf.P, NB, mr, w, rows_per, ncta, nullptr, nullptr, bf.tau, bf.V, bf.Vt, ldt, Ctp, ldt};
-    if (coop) {
+    if (use_coop) {
       SKI_CUDA_TRY(cudaMemsetAsync(bf.gb, 0, 2 * sizeof(unsigned), st));  // count, gen (keep err)
       long long lim = kSpinLimit;
       void* args[] = {&pa, &bf.partA, &bf.partB, &bf.gb, &lim};
-      SKI_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop<T>, dim3(ncta), dim3(32 * WARPS), args, 0,
-                                               st));
+      const size_t smem = (size_t)rows_per * (NB + 1) * sizeof(T);
+      if (smem > 48 * 1024)
+        SKI_CUDA_TRY(cudaFuncSetAttribute(k_panel_coop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      SKI_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop<T>, dim3(ncta), dim3(32 * WARPS), args,
+                                               smem, st));
       SKI_LAUNCH_CHECK();
     } else {
       k_panel_copy<T><<<ncta, 32 * WARPS, 0, st>>>(pa, 1);
