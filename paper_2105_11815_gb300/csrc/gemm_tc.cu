@@ -21,7 +21,7 @@
 
 namespace {
 
-constexpr int BM = 128, BK = 32, STAGES = 4, NTHR = 128;
+constexpr int BM = 128, BK = 32, NTHR = 128;
 constexpr long long kSpinLimit = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -74,7 +74,7 @@ __host__ __device__ constexpr uint32_t tf32_idesc(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-template <int BN>
+template <int BN, int STAGES>
 struct TcSmem {
   float A[STAGES][BM * BK];  // 16 KB per stage
   float B[STAGES][BN * BK];  // BN * 128 bytes per stage
@@ -84,13 +84,13 @@ struct TcSmem {
 };
 
 // mode 0: C[m * ldc + n] = D; mode 1: C[m * ldc + n] -= D; mode 2: C[n * ldc + m] = D.
-template <int BN>
+template <int BN, int STAGES>
 __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
                                                       const __grid_constant__ CUtensorMap tb, int M, int N, int K,
                                                       int kchunk, float* __restrict__ C, int64_t ldc,
                                                       int64_t c_zstride, int mode, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  TcSmem<BN>& sm = *reinterpret_cast<TcSmem<BN>*>(
+  TcSmem<BN, STAGES>& sm = *reinterpret_cast<TcSmem<BN, STAGES>*>(
       (void*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
@@ -207,12 +207,25 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
         for (int j = 0; j < 32; ++j) st[lane][j] = __uint_as_float(v[j]);
         __syncwarp();
         const int col = n0 + c0 + lane;
-        for (int rr = 0; rr < 32; ++rr) {
-          const int r = m0 + warp * 32 + rr;
-          if (r < M && col < N) {
-            float* cp = &C[(int64_t)r * ldc + col];
-            if (mode == 0) *cp = st[rr][lane];
-            else *cp -= st[rr][lane];
+        const bool cok = col < N;
+        if (mode == 1) {
+          // all 32 rows' loads in flight before the first use
+          float cv[32];
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) {
+            const int r = m0 + warp * 32 + rr;
+            cv[rr] = (r < M && cok) ? C[(int64_t)r * ldc + col] : 0.f;
+          }
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) {
+            const int r = m0 + warp * 32 + rr;
+            if (r < M && cok) C[(int64_t)r * ldc + col] = cv[rr] - st[rr][lane];
+          }
+        } else {
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) {
+            const int r = m0 + warp * 32 + rr;
+            if (r < M && cok) C[(int64_t)r * ldc + col] = st[rr][lane];
           }
         }
         __syncwarp();
@@ -264,16 +277,17 @@ bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, i
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int STAGES>
 ski_status launch(const float* A, int64_t lda, const float* B, int64_t ldb, int M, int N, int K, float* C,
                   int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st) {
   CUtensorMap ta, tb;
   if (!make_map(&ta, A, M, K, lda, BM) || !make_map(&tb, B, N, K, ldb, BN)) return SKI_ECUDA;
-  const size_t smem = sizeof(TcSmem<BN>) + 1024;
-  SKI_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = sizeof(TcSmem<BN, STAGES>) + 1024;
+  SKI_CUDA_TRY(
+      cudaFuncSetAttribute(k_gemm_tc<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int kchunk = (int)ski_round_up(ski_cdiv(K, splits), BK);
   dim3 grid((unsigned)ski_cdiv(M, BM), (unsigned)ski_cdiv(N, BN), (unsigned)splits);
-  k_gemm_tc<BN><<<grid, NTHR, smem, st>>>(ta, tb, M, N, K, kchunk, C, ldc, c_zstride, mode, err);
+  k_gemm_tc<BN, STAGES><<<grid, NTHR, smem, st>>>(ta, tb, M, N, K, kchunk, C, ldc, c_zstride, mode, err);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }
@@ -290,9 +304,16 @@ ski_status ski_gemm_tf32(const float* A, int64_t lda, const float* B, int64_t ld
   if (M <= 0 || N <= 0) return SKI_OK;
   if ((lda & 3) || (ldb & 3) || ((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return SKI_EINVAL;
   if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return SKI_EINVAL;
-  if (N <= 32) return launch<32>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
-  if (N <= 64) return launch<64>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
-  return launch<256>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
+  // deep K (the V^T C products): 4-stage ring; K <= 64 (the rank-32 update):
+  // 2 stages, leaving room for two CTAs (and their TMEM) per SM
+  const bool shallow = ski_cdiv(K, splits) <= 2 * BK;
+  if (N <= 32)
+    return shallow ? launch<32, 2>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st)
+                   : launch<32, 4>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
+  if (N <= 64)
+    return launch<64, 4>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
+  return shallow ? launch<256, 2>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st)
+                 : launch<256, 4>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
 }
 
 extern "C" ski_status ski_gemm_tc_f32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,

@@ -22,6 +22,8 @@
 // (forward accumulation: T_ii = tau_i, T[0:i, i] = -tau_i T[0:i,0:i] V[:,0:i]^T v_i).
 // V^T C is a split-K GEMM, C -= V (T^T W) a plain GEMM (gemm.cu).
 // Applying the reflectors to column d of [SA | Sb] yields Q^T Sb for Step 3.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "sketch_impl.cuh"
 
@@ -57,19 +59,33 @@ __device__ __forceinline__ T sgn_nrm(T x0, T nrm) { return x0 >= T(0) ? -nrm : n
 // s-1 from the partials of step s-1 and accumulate those of column s.
 // Partials are read with L1-bypassing loads: in the persistent kernel they
 // were written by other SMs during this launch.
+// Where a step reads the previous step's per-CTA partials and writes its own:
+// global memory (launch-per-step and grid-barrier kernels) or distributed
+// shared memory (cluster kernel).
 template <class T>
-__device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s) {
-  __shared__ T red[WARPS][NB];
+struct GlobalParts {
+  const T* prev;
+  T* cur;
+  __device__ __forceinline__ int rank() const { return blockIdx.x; }
+  __device__ __forceinline__ T get(int b, int idx) const { return __ldcg(&prev[(int64_t)b * PW + idx]); }
+  __device__ __forceinline__ void put(int idx, T v) const { cur[(int64_t)blockIdx.x * PW + idx] = v; }
+};
+
+template <class T, int NW = WARPS, class Parts = GlobalParts<T>>
+__device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s, const Parts& parts) {
+  constexpr int WARPS = NW;
+  __shared__ T red[NW][NB];
   __shared__ T s_par[4];  // tau, beta, scl
   __shared__ T s_wc[NB];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rank = parts.rank();
   const int j = s - 1;
   T tau = T(0), beta = T(0), scl = T(0), wc = T(0);
   if (s > 0) {
     // partial sums of the previous launch, split over the warps (fixed order)
     T g = T(0);
 #pragma unroll 8
-    for (int b = warp; b < a.ncta; b += WARPS) g += __ldcg(&a.part_prev[(int64_t)b * PW + lane]);
+    for (int b = warp; b < a.ncta; b += WARPS) g += parts.get(b, lane);
     red[warp][lane] = g;
     __syncthreads();
     if (warp == 0) {
@@ -77,7 +93,7 @@ __device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s) {
 #pragma unroll
       for (int q = 0; q < WARPS; ++q) g += red[q][lane];
       const int owner = (int)(j / a.rows_per);
-      const T dr = __ldcg(&a.part_prev[(int64_t)owner * PW + NB + lane]);
+      const T dr = parts.get(owner, NB + lane);
       const T x0 = __shfl_sync(0xffffffffu, dr, j);
       const T gj = __shfl_sync(0xffffffffu, g, j);
       T tau_, beta_, scl_;
@@ -96,7 +112,7 @@ __device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s) {
         s_par[0] = tau_;
         s_par[1] = beta_;
         s_par[2] = scl_;
-        if (blockIdx.x == 0) a.tau[j] = tau_;
+        if (rank == 0) a.tau[j] = tau_;
       }
     }
     __syncthreads();
@@ -105,7 +121,7 @@ __device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s) {
     scl = s_par[2];
     wc = s_wc[lane];
   }
-  const int64_t r0 = (int64_t)blockIdx.x * a.rows_per;
+  const int64_t r0 = (int64_t)rank * a.rows_per;
   const int64_t r1 = min(a.mr, r0 + a.rows_per);
   T acc = T(0);
   for (int64_t r = r0 + warp; r < r1; r += WARPS) {
@@ -124,7 +140,7 @@ __device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s) {
     if (s < a.w) {
       const T ps = __shfl_sync(0xffffffffu, val, s);
       if (r == s) {
-        a.part_cur[(int64_t)blockIdx.x * PW + NB + lane] = val;
+        parts.put(NB + lane, val);
       } else if (r > s) {
         acc = fma(ps, val, acc);
       }
@@ -143,7 +159,7 @@ __device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s) {
       T t = T(0);
 #pragma unroll
       for (int q = 0; q < WARPS; ++q) t += red[q][lane];
-      a.part_cur[(int64_t)blockIdx.x * PW + lane] = t;
+      parts.put(lane, t);
     }
   }
 }
@@ -186,7 +202,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_panel_copy(PanelArgs<T> a, int i
 
 template <class T>
 __global__ void __launch_bounds__(32 * WARPS) k_panel_step(PanelArgs<T> a, int s) {
-  panel_step_body(a, s);
+  panel_step_body<T>(a, s, GlobalParts<T>{a.part_prev, a.part_cur});
 }
 
 // Grid-wide barrier of the persistent panel kernel (all CTAs co-resident by
@@ -250,11 +266,55 @@ __global__ void __launch_bounds__(32 * WARPS) k_panel_coop(PanelArgs<T> a, T* pa
   for (int s = 0; s <= a.w; ++s) {
     b.part_prev = (s & 1) ? partA : partB;
     b.part_cur = (s & 1) ? partB : partA;
-    panel_step_body(b, s);
+    panel_step_body<T>(b, s, GlobalParts<T>{b.part_prev, b.part_cur});
     if (s < a.w && !grid_sync(gb, gridDim.x, my_gen, spin_limit)) return;
   }
   __syncthreads();
   for (int c = warp; c < a.w; c += WARPS)
+    for (int64_t r = r0 + lane; r < r1; r += 32) a.Ct[(int64_t)c * a.ldt + r] = slab[(r - r0) * (NB + 1) + c];
+}
+
+// Distributed-shared-memory partials of the cluster kernel: step s writes
+// slot s & 1 of its own CTA, step s + 1 reads slot s & 1 of every CTA.
+template <class T>
+struct ClusterParts {
+  T* mine_prev;
+  T* mine_cur;
+  __device__ __forceinline__ int rank() const { return (int)cooperative_groups::this_cluster().block_rank(); }
+  __device__ __forceinline__ T get(int b, int idx) const {
+    return *cooperative_groups::this_cluster().map_shared_rank(mine_prev + idx, (unsigned)b);
+  }
+  __device__ __forceinline__ void put(int idx, T v) const { mine_cur[idx] = v; }
+};
+
+// The whole panel in one thread-block cluster (one cluster, up to 16 CTAs):
+// slabs in shared memory, partials exchanged through distributed shared
+// memory, one hardware cluster barrier per column step.
+template <class T, int NW>
+__global__ void __launch_bounds__(32 * NW) k_panel_cluster(PanelArgs<T> a) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char cl_raw[];
+  T* slots = reinterpret_cast<T*>(cl_raw);  // [2][PW]
+  T* slab = slots + 2 * PW;
+  const int rank = (int)cl.block_rank();
+  const int64_t r0 = (int64_t)rank * a.rows_per;
+  const int64_t r1 = min(a.mr, r0 + a.rows_per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < NB; c += NW)
+    for (int64_t r = r0 + lane; r < r1; r += 32)
+      slab[(r - r0) * (NB + 1) + c] = c < a.w ? a.Ct[(int64_t)c * a.ldt + r] : T(0);
+  __syncthreads();
+  PanelArgs<T> b = a;
+  b.P = slab - r0 * (NB + 1);
+  b.ld = NB + 1;
+  for (int s = 0; s <= a.w; ++s) {
+    ClusterParts<T> parts{slots + ((s + 1) & 1) * PW, slots + (s & 1) * PW};
+    panel_step_body<T, NW>(b, s, parts);
+    if (s < a.w) cl.sync();
+  }
+  __syncthreads();
+  for (int c = warp; c < a.w; c += NW)
     for (int64_t r = r0 + lane; r < r1; r += 32) a.Ct[(int64_t)c * a.ldt + r] = slab[(r - r0) * (NB + 1) + c];
 }
 
@@ -449,6 +509,39 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     cudaGetLastError();
   }
   const int64_t max_slab_rows = (200 * 1024) / ((NB + 1) * (int64_t)sizeof(T));
+  // cluster panels: 16 CTAs (non-portable size) when the device runs such a
+  // cluster with the largest slab, else 8
+  constexpr int CNW = 16;
+  int CL = 0;
+  bool cluster_ok = false;
+  {
+    const size_t big = (size_t)(200 * 1024 + 2 * PW * sizeof(T));
+    if (cudaFuncSetAttribute(k_panel_cluster<T, CNW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_panel_cluster<T, CNW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big) ==
+            cudaSuccess) {
+      for (int cand : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cand;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(cand);
+        cfg.blockDim = dim3(32 * CNW);
+        cfg.dynamicSmemBytes = big;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclus = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclus, k_panel_cluster<T, CNW>, &cfg) == cudaSuccess && nclus >= 1) {
+          CL = cand;
+          cluster_ok = true;
+          break;
+        }
+      }
+    }
+    cudaGetLastError();
+  }
   SKI_CUDA_TRY(cudaMemsetAsync(bf.err, 0, sizeof(int), st));
   SKI_CUDA_TRY(cudaMemsetAsync(bf.gb, 0, sizeof(GridBar), st));
   {
@@ -471,7 +564,36 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     const int64_t rows_per = ski_cdiv(mr, ncta);
     T* Ctp = bf.Ct + k0 * ldt + k0;
     PanelArgs<T> pa{bf.P, NB, mr, w, rows_per, ncta, nullptr, nullptr, bf.tau, bf.V, bf.Vt, ldt, Ctp, ldt};
-    if (use_coop) {
+    bool done_panel = false;
+    if (cluster_ok) {
+      // one cluster of CL CTAs: the slab of each must fit in shared memory
+      const int64_t rp = ski_cdiv(mr, CL);
+      const size_t csm = (size_t)(2 * PW + rp * (NB + 1)) * sizeof(T);
+      if (csm <= 200 * 1024) {
+        PanelArgs<T> pc = pa;
+        pc.rows_per = rp;
+        pc.ncta = CL;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(CL);
+        cfg.blockDim = dim3(32 * CNW);
+        cfg.dynamicSmemBytes = csm;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        SKI_CUDA_TRY(cudaFuncSetAttribute(k_panel_cluster<T, CNW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(200 * 1024 + 2 * PW * sizeof(T))));
+        SKI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_cluster<T, CNW>, pc));
+        SKI_LAUNCH_CHECK();
+        done_panel = true;
+      }
+    }
+    if (done_panel) {
+    } else if (use_coop) {
       SKI_CUDA_TRY(cudaMemsetAsync(bf.gb, 0, 2 * sizeof(unsigned), st));  // count, gen (keep err)
       long long lim = kSpinLimit;
       void* args[] = {&pa, &bf.partA, &bf.partB, &bf.gb, &lim};
