@@ -587,6 +587,10 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
       }
       iters_total += hs.iters;
       lsqr_test = hs.test;
+      if (hs.df_err) {
+        result = SKI_ETIMEOUT;
+        break;
+      }
       // Step 5: x = x_s + R^{-1} delta
       SKI_TRY(ski_trmv_launch(true, d, P.M, d, P.y, P.xs, x, nullptr, st));
       SKI_TRY(residual_pass(A, b, x, P, false, st));

@@ -21,6 +21,8 @@
 // Kernels never read a flag written by another CTA of the same launch: K1
 // reads flag_b and writes flag_a; K2, K3, K4 read flag_a; K3 copies it to
 // flag_b for the next K1.
+#include <stdlib.h>
+
 #include "common.cuh"
 #include "lsqr_impl.cuh"
 
@@ -199,6 +201,296 @@ __global__ void __launch_bounds__(512) k_fused_df(DfArgs f) {
     double s = 0.0;
     for (int q = 0; q < RR; ++q) s += tts[q];
     f.part_tt[blockIdx.x] = s;
+  }
+}
+
+// K2, TMA-staged: rows of A2 stream into a shared-memory ring by 1-D bulk
+// copies (cp.async.bulk, completion on an mbarrier), one producer thread
+// issuing ahead while the 16 warps compute from shared memory -- the loads
+// never stall the arithmetic.  Same arithmetic and same result as k_fused_df.
+__device__ __forceinline__ uint32_t s_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <int CPT, int RR>
+__global__ void __launch_bounds__(512, 1) k_fused_df_tma(DfArgs f, int nstage) {
+  constexpr int NT = 512, NW = NT / 32;
+  constexpr long long kSpin = 1ll << 22;
+  __shared__ float2 red[RR][NW];
+  __shared__ float2 tsh[RR];
+  __shared__ int s_zexp;
+  __shared__ double tts[NW];
+  __shared__ __align__(8) uint64_t full[4];
+  extern __shared__ __align__(128) unsigned char dyn[];
+  LsqrScalars* sc = f.sc;
+  if (sc && flag_set(&sc->flag_a)) return;
+  const double cu = f.coef_from_scalars ? -sc->coef : f.cu;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * f.rows_per;
+  const int64_t r1 = min(f.n, r0 + f.rows_per);
+  const int64_t rowb = f.ld2 * (int64_t)sizeof(float2);           // bytes per row (multiple of 16)
+  float2* ring = reinterpret_cast<float2*>(dyn);                   // [nstage][RR][ld2]
+  double* s_u = reinterpret_cast<double*>(dyn + (size_t)nstage * RR * rowb);
+  const int64_t ngroups = r1 > r0 ? (r1 - r0 + RR - 1) / RR : 0;
+  auto issue = [&](int64_t g) {  // thread 0: bulk copies of group g into stage g % nstage
+    const int s = (int)(g % nstage);
+    const int64_t j0 = r0 + g * RR;
+    const int nr = (int)min((int64_t)RR, r1 - j0);
+    const uint32_t bar = s_u32(&full[s]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"((uint32_t)(nr * rowb))
+                 : "memory");
+    for (int r = 0; r < nr; ++r) {
+      const uint32_t dst = s_u32(ring + ((size_t)s * RR + r) * f.ld2);
+      const float2* src = f.A2 + (j0 + r) * f.ld2;
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       dst),
+                   "l"(src), "r"((uint32_t)rowb), "r"(bar)
+                   : "memory");
+    }
+  };
+  if (tid == 0) {
+    s_zexp = -2000;
+    for (int s = 0; s < nstage; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_u32(&full[s])), "r"(1u));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int64_t issued = 0;  // groups whose copies thread 0 has issued
+  if (tid == 0)
+    for (; issued < min((int64_t)nstage, ngroups); ++issued) issue(issued);
+  if (f.u)
+    for (int64_t j = r0 + tid; j < r1; j += NT) s_u[j - r0] = f.u[j];
+  int ez = -2000;
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int64_t c = tid + (int64_t)k * NT;
+    if (c < f.d) {
+      const double zc = f.z[c];
+      if (zc != 0.0) ez = max(ez, (int)((__double_as_longlong(zc) >> 52) & 0x7FF) - 1022);
+    }
+  }
+  atomicMax(&s_zexp, ez);
+  __syncthreads();
+  const int sz = s_zexp == -2000 ? 0 : s_zexp;
+  const int st = f.sA + sz;
+  float zh[CPT], zl[CPT], ah_acc[CPT], al_acc[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int64_t c = tid + (int64_t)k * NT;
+    const float2 zz = c < f.d ? df_split(f.z[c], sz) : make_float2(0.f, 0.f);
+    zh[k] = zz.x;
+    zl[k] = zz.y;
+    ah_acc[k] = 0.f;
+    al_acc[k] = 0.f;
+  }
+  double tt = 0.0;
+  bool ok = true;
+  for (int64_t g = 0; g < ngroups && ok; ++g) {
+    const int s = (int)(g % nstage);
+    const uint32_t par = (uint32_t)((g / nstage) & 1);
+    const int64_t j0 = r0 + g * RR;
+    // wait for the group's rows (bounded; the outcome is made CTA-uniform)
+    bool got = false;
+    for (long long i = 0; i < kSpin; ++i) {
+      uint32_t done;
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(s_u32(&full[s])), "r"(par)
+          : "memory");
+      if (done) {
+        got = true;
+        break;
+      }
+    }
+    ok = __syncthreads_and(got) != 0;
+    if (!ok) break;
+    const float2* rows = ring + (size_t)s * RR * f.ld2;
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      float h = 0.f, l = 0.f;
+      if (j0 + r < r1) {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+          const int64_t c = tid + (int64_t)k * NT;
+          if (c < f.d) {
+            const float2 a = rows[(size_t)r * f.ld2 + c];
+            df_mac(h, l, a.x, a.y, zh[k], zl[k]);
+          }
+        }
+      }
+      df_warp_sum(h, l);
+      if (lane == 0) red[r][wid] = make_float2(h, l);
+    }
+    __syncthreads();
+    if (wid < RR) {
+      const int64_t j = j0 + wid;
+      float h = lane < NW ? red[wid][lane].x : 0.f, l = lane < NW ? red[wid][lane].y : 0.f;
+#pragma unroll
+      for (int o = NW / 2; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+        df_add(h, l, oh, ol);
+      }
+      if (lane == 0) {
+        float2 ts = make_float2(0.f, 0.f);
+        if (j < r1) {
+          double t = ldexp((double)h + (double)l, st);
+          if (f.u) t = fma(cu, s_u[j - r0], t);
+          f.t[j] = t;
+          tt = fma(t, t, tt);
+          ts = df_split(t, st);
+        }
+        tsh[wid] = ts;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      const float2 tv = tsh[r];
+      if (j0 + r < r1) {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+          const int64_t c = tid + (int64_t)k * NT;
+          if (c < f.d) {
+            const float2 a = rows[(size_t)r * f.ld2 + c];
+            df_mac(ah_acc[k], al_acc[k], a.x, a.y, tv.x, tv.y);
+          }
+        }
+      }
+    }
+    __syncthreads();  // stage s fully consumed before it is refilled
+    if (tid == 0 && g + nstage < ngroups) issue(issued++);
+  }
+  if (!ok) {
+    // a bulk copy did not land in time: record it and leave once the copies
+    // already issued have completed (bounded wait on each stage's last phase)
+    if (tid == 0) {
+      atomicExch(&sc->df_err, 1);
+      for (int s = 0; s < nstage; ++s) {
+        int64_t last = -1;  // last group issued into stage s
+        for (int64_t g = s; g < issued; g += nstage) last = g;
+        if (last < 0) continue;
+        const uint32_t par = (uint32_t)((last / nstage) & 1);
+        for (long long i = 0; i < kSpin; ++i) {
+          uint32_t done;
+          asm volatile(
+              "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+              : "=r"(done)
+              : "r"(s_u32(&full[s])), "r"(par)
+              : "memory");
+          if (done) break;
+        }
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int64_t c = tid + (int64_t)k * NT;
+    if (c < f.d) f.part[(int64_t)blockIdx.x * f.d + c] = ldexp((double)ah_acc[k] + (double)al_acc[k], f.sA + st);
+  }
+  if (lane == 0) tts[wid] = tt;
+  __syncthreads();
+  if (tid == 0) {
+    double s2 = 0.0;
+    for (int q = 0; q < RR; ++q) s2 += tts[q];
+    f.part_tt[blockIdx.x] = s2;
+  }
+}
+
+// K2, row-per-warp variant: in each group of 16 rows, warp w computes the
+// whole dot product of row j0 + w (lanes stride the columns, z staged in
+// shared memory), so no CTA barrier sits inside a row; after ONE barrier all
+// 512 threads apply the A^T t update of the 16 rows to their own columns,
+// re-reading the rows from L1/L2 where the dot phase just brought them.
+template <int CPT>
+__global__ void __launch_bounds__(512, 1) k_fused_df_rows(DfArgs f) {
+  constexpr int NT = 512, NW = NT / 32;
+  __shared__ float2 tsh[2][NW];
+  __shared__ int s_zexp;
+  __shared__ double tts[NW];
+  extern __shared__ __align__(128) unsigned char dyn[];
+  float2* zs = reinterpret_cast<float2*>(dyn);                            // [ld2]
+  double* s_u = reinterpret_cast<double*>(dyn + (size_t)f.ld2 * sizeof(float2));
+  LsqrScalars* sc = f.sc;
+  if (sc && flag_set(&sc->flag_a)) return;
+  const double cu = f.coef_from_scalars ? -sc->coef : f.cu;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * f.rows_per;
+  const int64_t r1 = min(f.n, r0 + f.rows_per);
+  if (tid == 0) s_zexp = -2000;
+  if (f.u)
+    for (int64_t j = r0 + tid; j < r1; j += NT) s_u[j - r0] = f.u[j];
+  __syncthreads();
+  int ez = -2000;
+  for (int64_t c = tid; c < f.d; c += NT) {
+    const double zc = f.z[c];
+    if (zc != 0.0) ez = max(ez, (int)((__double_as_longlong(zc) >> 52) & 0x7FF) - 1022);
+  }
+  atomicMax(&s_zexp, ez);
+  __syncthreads();
+  const int sz = s_zexp == -2000 ? 0 : s_zexp;
+  const int st = f.sA + sz;
+  for (int64_t c = tid; c < f.d; c += NT) zs[c] = df_split(f.z[c], sz);
+  float ah_acc[CPT], al_acc[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    ah_acc[k] = 0.f;
+    al_acc[k] = 0.f;
+  }
+  __syncthreads();
+  double tt = 0.0;
+  int buf = 0;
+  for (int64_t j0 = r0; j0 < r1; j0 += NW, buf ^= 1) {
+    // dot phase: one row per warp
+    const int64_t j = j0 + wid;
+    if (j < r1) {
+      const float2* row = f.A2 + j * f.ld2;
+      float h = 0.f, l = 0.f;
+#pragma unroll 4
+      for (int64_t c = lane; c < f.d; c += 32) {
+        const float2 a = __ldcg(&row[c]);
+        const float2 z = zs[c];
+        df_mac(h, l, a.x, a.y, z.x, z.y);
+      }
+      df_warp_sum(h, l);
+      if (lane == 0) {
+        double t = ldexp((double)h + (double)l, st);
+        if (f.u) t = fma(cu, s_u[j - r0], t);
+        f.t[j] = t;
+        tt = fma(t, t, tt);
+        tsh[buf][wid] = df_split(t, st);
+      }
+    } else if (lane == 0) {
+      tsh[buf][wid] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    // update phase: every thread, its columns, the group's rows
+    const int nr = (int)min((int64_t)NW, r1 - j0);
+    for (int r = 0; r < nr; ++r) {
+      const float2 tv = tsh[buf][r];
+      const float2* row = f.A2 + (j0 + r) * f.ld2;
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        const int64_t c = tid + (int64_t)k * NT;
+        if (c < f.d) {
+          const float2 a = row[c];
+          df_mac(ah_acc[k], al_acc[k], a.x, a.y, tv.x, tv.y);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int64_t c = tid + (int64_t)k * NT;
+    if (c < f.d) f.part[(int64_t)blockIdx.x * f.d + c] = ldexp((double)ah_acc[k] + (double)al_acc[k], f.sA + st);
+  }
+  if (lane == 0) tts[wid] = tt;
+  __syncthreads();
+  if (tid == 0) {
+    double s2 = 0.0;
+    for (int q = 0; q < NW; ++q) s2 += tts[q];
+    f.part_tt[blockIdx.x] = s2;
   }
 }
 
@@ -384,11 +676,68 @@ bool ski_df_supported(int64_t d) { return d <= SKI_DENSE_DMAX; }
 
 int64_t ski_a2_ld(int64_t d) { return ski_round_up(d, 2); }  // rows 16-byte aligned
 
+// Variant selection of the LSQR pass.  The default is the register-blocked
+// kernel (k_fused_df), measured fastest at 50000 x 4000 (0.55 ms per
+// iteration against 0.68 for the TMA-staged and 0.75 for the row-per-warp
+// variants); SKI_LSQR_PASS = "rows" | "tma" selects another for measurements.
+static int lsqr_pass_choice() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("SKI_LSQR_PASS");
+    v = (e && e[0] == 't') ? 1 : (e && e[0] == 'r' && e[1] == 'o') ? 0 : 2;
+  }
+  return v;
+}
+static bool getenv_flag_df_rows() { return lsqr_pass_choice() == 0; }
+static bool getenv_flag_df_tma() { return lsqr_pass_choice() == 1; }
+
 ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
   DfArgs f = f0;
   f.ld2 = ski_a2_ld(f.d);
   f.rows_per = ski_cdiv(f.n, f.nblk);
   const int64_t cpt = ski_cdiv(f.d, 512);
+  // row-per-warp variant (z and u staged in shared memory)
+  {
+    const size_t sm = (size_t)f.ld2 * sizeof(float2) + (size_t)f.rows_per * sizeof(double);
+    if (sm <= 200 * 1024 && getenv_flag_df_rows()) {
+#define SKI_DFR_CASE(C)                                                                                  \
+      if (cpt <= C) {                                                                                    \
+        SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df_rows<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+        k_fused_df_rows<C><<<f.nblk, 512, sm, st>>>(f);                                                  \
+        SKI_LAUNCH_CHECK();                                                                              \
+        return SKI_OK;                                                                                   \
+      }
+      SKI_DFR_CASE(1)
+      SKI_DFR_CASE(2)
+      SKI_DFR_CASE(4)
+      SKI_DFR_CASE(8)
+#undef SKI_DFR_CASE
+    }
+  }
+  // TMA-staged variant: nstage x RR rows of A2 in shared memory
+  if (getenv_flag_df_tma()) {
+    const size_t rowb = (size_t)f.ld2 * sizeof(float2);
+    const size_t ub = (size_t)f.rows_per * sizeof(double);
+    const size_t budget = 200 * 1024;
+#define SKI_DFT_CASE(C, R)                                                                            \
+    if (cpt <= C) {                                                                                   \
+      for (int ns = 3; ns >= 2; --ns) {                                                               \
+        const size_t sm = (size_t)ns * R * rowb + ub;                                                 \
+        if (sm <= budget) {                                                                           \
+          SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df_tma<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                            (int)sm));                                                \
+          k_fused_df_tma<C, R><<<f.nblk, 512, sm, st>>>(f, ns);                                       \
+          SKI_LAUNCH_CHECK();                                                                         \
+          return SKI_OK;                                                                              \
+        }                                                                                             \
+      }                                                                                               \
+    }
+    SKI_DFT_CASE(1, 8)
+    SKI_DFT_CASE(2, 4)
+    SKI_DFT_CASE(4, 4)
+    SKI_DFT_CASE(8, 2)
+#undef SKI_DFT_CASE
+  }
   const size_t smem = (size_t)f.rows_per * sizeof(double);
   if (smem > 200 * 1024) return SKI_EINVAL;
 #define SKI_DF_CASE(C, R)                                                                        \

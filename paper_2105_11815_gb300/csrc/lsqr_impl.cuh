@@ -14,6 +14,7 @@ struct LsqrScalars {
   int flag_a, flag_b;  // stop flags (see lsqr_df.cu for who writes which)
   int conv;
   int amax_exp;  // largest biased exponent field of A (from the first residual pass)
+  int df_err;    // a staged copy of the LSQR pass timed out
 };
 
 struct FusedArgs {

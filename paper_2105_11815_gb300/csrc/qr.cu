@@ -514,7 +514,9 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
   constexpr int CNW = 16;
   int CL = 0;
   bool cluster_ok = false;
-  {
+  // FP32 only: an FP64 panel does its rank-1 updates on the 1/64-rate FP64
+  // pipe, which 64 SMs (grid-barrier kernel) finish sooner than 16.
+  if (sizeof(T) == 4) {
     const size_t big = (size_t)(200 * 1024 + 2 * PW * sizeof(T));
     if (cudaFuncSetAttribute(k_panel_cluster<T, CNW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
             cudaSuccess &&
