@@ -54,10 +54,13 @@ def peaks():
     return 6800.0, "fallback", {}
 
 
-# FP64 DFMA throughput of this GB300 pool, measured with a dependent-chain
-# DFMA loop (152 SMs x 2 DFMA/clk): 1.00 TFLOP/s at ~2 GHz.
-FP64_PEAK_TFLOPS = 1.0
+# FP64 peak from the unit count and clock: 152 SMs x 2 DFMA/clk x 2 flop x
+# 2.07 GHz = 1.26 TFLOP/s (a DFMA loop measured 1.00 on this machine).
+FP64_PEAK_TFLOPS = 1.26
 FP32_PEAK_TFLOPS = 72.0
+# DRAM bytes (read + write) of one launch of the hash gather, from ncu
+# (profiles/hash_gather_dense_50000x4000.md); None where not captured.
+GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2512025088 + 236451840}
 
 
 class ClockSampler:
@@ -264,10 +267,29 @@ def run_ours(args, name):
     qr_flops = 2.0 * m * (d + 1) ** 2 - 2.0 / 3.0 * d ** 3
     qr64 = statistics.mean(i.ms_qr for i, _ in infos)
     qrmx = statistics.mean(j.ms_qr for _, j in infos)
-    roofline = {"kernel": "k_sketch_dense_f64acc (hash gather)", "bound": "hbm",
-                "achieved": gather_bytes / (g_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": gather_bytes / (g_ms * 1e-3) / 1e9 / hbm, "traffic": None,
-                "peak_source": peak_kind, "bytes_per_launch": gather_bytes, "ms_per_launch": g_ms}
+    # dominant kernel of the step (ncu launch list): the FP64 QR trailing-update
+    # GEMM k_gemm<double>, bound by the FP64 pipe.  Its flops, summed over the
+    # 32-column panels: W = V^T C and C -= V B' each cost 2 w nct mr.
+    gemm_flops = 0.0
+    for k0 in range(0, d, 32):
+        w = min(32, d - k0)
+        gemm_flops += 4.0 * w * ((d + 1) - k0 - w) * (m - k0)
+    g64 = statistics.mean(i.ms_qr_gemm for i, _ in infos)
+    g32 = statistics.mean(j.ms_qr_gemm for _, j in infos)
+    roofline = {"kernel": "k_gemm<double> (FP64 QR trailing update)", "bound": "alu",
+                "achieved": gemm_flops / (g64 * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": gemm_flops / (g64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (DFMA loop measured 1.00)",
+                "flops_per_step": gemm_flops, "ms_per_step": g64}
+    sketch_roofline = {"kernel": "k_sketch_dense_f64acc (hash gather)", "bound": "hbm",
+                       "achieved": gather_bytes / (g_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                       "frac": gather_bytes / (g_ms * 1e-3) / 1e9 / hbm, "traffic": GATHER_TRAFFIC.get(name),
+                       "peak_source": peak_kind, "bytes_per_launch": gather_bytes, "ms_per_launch": g_ms}
+    tf32_peak = 0.5 * pj.get("bf16_tflops", 1900.0)
+    tc_roofline = {"kernel": "k_gemm_tc (TF32 QR trailing update, mixed path)", "bound": "tensor",
+                   "achieved": gemm_flops / (g32 * 1e-3) / 1e12, "unit": "TFLOP/s",
+                   "peak": tf32_peak, "frac": gemm_flops / (g32 * 1e-3) / 1e12 / tf32_peak,
+                   "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 0.5", "ms_per_step": g32}
     stages = {
         "premix_fp64": {"ms": pm_ms, "bound": "hbm", "algorithmic_bytes": premix_bytes,
                         "achieved_gbs": premix_bytes / (pm_ms * 1e-3) / 1e9 if pm_ms > 0 else None},
@@ -331,7 +353,8 @@ def run_ours(args, name):
                        "A": cfg["kind"], "b": "ones" if cfg["kind"] != "lls" else "A x + 1e-3 N(0,1)",
                        "l2": "inputs larger than L2 (A = %.2f GB)" % (8e-9 * n * d),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "hbm_frac": value / world / hbm, "roofline": roofline, "stages": stages, "lls": lls,
+            "hbm_frac": value / world / hbm, "roofline": roofline, "sketch_roofline": sketch_roofline,
+            "tc_roofline": tc_roofline, "stages": stages, "lls": lls,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line), flush=True)

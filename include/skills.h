@@ -94,6 +94,7 @@ typedef struct {
   double lsqr_test;       /* last Eq. TC-lsqr estimate                                */
   float ms_sketch, ms_qr, ms_trinv, ms_lsqr, ms_total;  /* stage times, CUDA events */
   float ms_premix, ms_gather;  /* inside ms_sketch: the H D premix and the hash gather */
+  float ms_qr_gemm;            /* inside ms_qr: the trailing-update GEMMs, summed     */
 } ski_info;
 
 /* Defaults of Ski-LLS-dense (Section 6): m = 0 (caller must set), s = 1,

@@ -65,7 +65,7 @@ class ski_info(ctypes.Structure):
                 ("anorm_f", ctypes.c_double), ("lsqr_test", ctypes.c_double),
                 ("ms_sketch", ctypes.c_float), ("ms_qr", ctypes.c_float), ("ms_trinv", ctypes.c_float),
                 ("ms_lsqr", ctypes.c_float), ("ms_total", ctypes.c_float),
-                ("ms_premix", ctypes.c_float), ("ms_gather", ctypes.c_float)]
+                ("ms_premix", ctypes.c_float), ("ms_gather", ctypes.c_float), ("ms_qr_gemm", ctypes.c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -492,6 +492,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   hs.it_max = o->it_max;
   hs.amax_exp = 0;
 
+  double qr_gemm_ms = 0.0;
   SKI_CUDA_TRY(cudaEventRecord(ev.e[0], st));
   // Step 1: sketch [SA | Sb]
   SKI_TRY(sketch_run(A, b, o, P.SA, P.ld_sa, P.stage, P.stage_bytes, st, ev.e[5], ev.e[6]));
@@ -510,7 +511,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   }
   {
     SkiArena qar{P.stage, P.stage_bytes, 0, false};
-    SKI_TRY(ski_qr_run(P.m, d, 1, P.SAq, P.ld_sa, P.qr_dt, P.R, d, P.qtsb, qar, st));
+    SKI_TRY(ski_qr_run(P.m, d, 1, P.SAq, P.ld_sa, P.qr_dt, P.R, d, P.qtsb, qar, st, info ? &qr_gemm_ms : nullptr));
   }
   SKI_CUDA_TRY(cudaEventRecord(ev.e[2], st));
   int32_t rank = 0;
@@ -628,6 +629,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
     info->ms_total = ev.ms(0, 4);
     info->ms_premix = ev.ms(5, 6);
     info->ms_gather = ev.ms(6, 1);
+    info->ms_qr_gemm = (float)qr_gemm_ms;
     info->status = result;
   }
   return result;

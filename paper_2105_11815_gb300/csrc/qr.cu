@@ -24,6 +24,8 @@
 // Applying the reflectors to column d of [SA | Sb] yields Q^T Sb for Step 3.
 #include <cooperative_groups.h>
 
+#include <vector>
+
 #include "common.cuh"
 #include "sketch_impl.cuh"
 
@@ -490,9 +492,40 @@ ski_status gemm_update<double>(int64_t nct, int64_t mr, const double* Bpt, const
   return ski_gemm<double>(nct, mr, NB, -1.0, Bpt, NB, 1, V, 1, NB, 1.0, Ctr, ldt, st);
 }
 
+// Optional CUDA-event timing of the trailing-update GEMMs (W = V^T C and
+// C -= V B'), summed over the panels: the live roofline of the QR's dominant
+// kernels.  Events are recorded on the launching stream only.
+struct GemmTimer {
+  std::vector<cudaEvent_t> ev;
+  bool on;
+  explicit GemmTimer(bool enable) : on(enable) {}
+  ~GemmTimer() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+  void mark(cudaStream_t st) {
+    if (!on) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      on = false;
+      return;
+    }
+    cudaEventRecord(e, st);
+    ev.push_back(e);
+  }
+  double total_ms() {  // pairs (start, stop); the stream must be synchronised
+    double s = 0.0;
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) s += ms;
+    }
+    return s;
+  }
+};
+
 template <class T>
 ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, double* R, int64_t ldr, double* qtsb,
-                   SkiArena& ar, cudaStream_t st) {
+                   SkiArena& ar, cudaStream_t st, double* gemm_ms) {
+  GemmTimer timer(gemm_ms != nullptr);
   const int64_t ncols = d + (with_rhs ? 1 : 0);
   const QrWs q = qr_dims(m, ncols);
   QrBufs<T> bf = qr_carve<T>(ar, m, ncols);
@@ -627,7 +660,9 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
       const int64_t tiles = ski_cdiv(nct, 128);
       sc = (int)std::max<int64_t>(1, std::min<int64_t>(q.splits_max, ski_cdiv(300, tiles)));
       sc = (int)std::min<int64_t>(sc, ski_cdiv(mr, 128));
+      timer.mark(st);
       SKI_TRY(gemm_w<T>(nct, mr, Ctr, ldt, bf.Vt, bf.pc, q.ldz, sc, bf.err, st));
+      timer.mark(st);
     }
     const int64_t zc = w + nct;
     k_reduce_z<T><<<ski_cdiv(w * zc, 256), 256, 0, st>>>(w, nct, bf.pv, sv, bf.pc, sc, q.ldz, bf.Z);
@@ -637,7 +672,9 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     if (nct > 0) {
       k_ttw<T><<<ski_cdiv(nct, 128), 128, 0, st>>>(w, nct, bf.Z, NB + q.ldz, bf.Tm, bf.Bpt);
       SKI_LAUNCH_CHECK();
+      timer.mark(st);
       SKI_TRY(gemm_update<T>(nct, mr, bf.Bpt, bf.V, Ctr, ldt, bf.err, st));
+      timer.mark(st);
     }
   }
   k_extract_r<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, bf.Ct, ldt, with_rhs, R, ldr, qtsb);
@@ -650,6 +687,7 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     SKI_CUDA_TRY(cudaStreamSynchronize(st));
     timed_out = h.err || e;
   }
+  if (gemm_ms) *gemm_ms = timer.total_ms();
   return timed_out ? SKI_ETIMEOUT : SKI_OK;
 }
 
@@ -663,9 +701,9 @@ size_t ski_qr_ws_bytes(int64_t m, int64_t ncols, int32_t dtype) {
 }
 
 ski_status ski_qr_run(int64_t m, int64_t d, int32_t with_rhs, void* SA, int64_t ld_sa, int32_t dtype, double* R,
-                      int64_t ldr, double* qtsb, SkiArena& ar, cudaStream_t st) {
-  if (dtype == SKI_F64) return qr_impl<double>(m, d, with_rhs, (double*)SA, ld_sa, R, ldr, qtsb, ar, st);
-  if (dtype == SKI_F32) return qr_impl<float>(m, d, with_rhs, (float*)SA, ld_sa, R, ldr, qtsb, ar, st);
+                      int64_t ldr, double* qtsb, SkiArena& ar, cudaStream_t st, double* gemm_ms) {
+  if (dtype == SKI_F64) return qr_impl<double>(m, d, with_rhs, (double*)SA, ld_sa, R, ldr, qtsb, ar, st, gemm_ms);
+  if (dtype == SKI_F32) return qr_impl<float>(m, d, with_rhs, (float*)SA, ld_sa, R, ldr, qtsb, ar, st, gemm_ms);
   return SKI_EINVAL;
 }
 

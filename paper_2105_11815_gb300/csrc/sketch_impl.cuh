@@ -40,7 +40,8 @@ ski_status ski_premix_run(const double* A, int64_t lda, int64_t n, int64_t d, co
 // ---- qr.cu
 size_t ski_qr_ws_bytes(int64_t m, int64_t ncols, int32_t dtype);
 ski_status ski_qr_run(int64_t m, int64_t d, int32_t with_rhs, void* SA, int64_t ld_sa, int32_t dtype,
-                      double* R, int64_t ldr, double* qtsb, SkiArena& ar, cudaStream_t st);
+                      double* R, int64_t ldr, double* qtsb, SkiArena& ar, cudaStream_t st,
+                      double* gemm_ms = nullptr);
 
 ski_status ski_barrier_selftest(long long spin_limit, void* ws, cudaStream_t st);
 
