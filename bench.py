@@ -27,6 +27,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the CPU oracle is timed sequentially (one BLAS / OpenMP thread), as the
+# paper's own timings are; set before numpy loads its BLAS
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 METRIC = "sketch S·A GB/s (% HBM peak); LLS time-to-1e-10 residual, mixed vs FP64"
 
@@ -41,6 +45,13 @@ WORKLOADS = {
     "dense_50000x512_hrht_s1_g2": (50000, 512, 65536, 1, 2.0, "gauss"),
     # mid case for full ncu captures of the d = 4000 kernel variants (~4.5 GB on the device)
     "dense_32768x3000_hrht_s1_g2": (32768, 3000, 32768, 1, 2.0, "gauss"),
+    # mixed-precision workload: A = U diag(sigma) V^T, kappa 1e6 / 1e10, premix to 262144
+    "usv_200000x4000_k1e6_hrht_s1_g2": (200000, 4000, 262144, 1, 2.0, "usv:1e6"),
+    "usv_200000x4000_k1e10_hrht_s1_g2": (200000, 4000, 262144, 1, 2.0, "usv:1e10"),
+    # sparse workload: CSR, 8 nonzeros per row, 0.1% rows with 2000; s = 2, m = 2d
+    "csr_1000000x20000_s2_g2": (1000000, 20000, 0, 2, 2.0, "csr"),
+    # ragged batch: 256 problems, d ~ U{64..1024}, n ~ U{max(2000, 4d)..60000}
+    "batched_256_ragged_g2": (256, 0, 0, 1, 2.0, "batched"),
 }
 DEFAULT = "dense_50000x4000_hrht_s1_g2"
 
@@ -58,9 +69,10 @@ def peaks():
 # 2.07 GHz = 1.26 TFLOP/s (a DFMA loop measured 1.00 on this machine).
 FP64_PEAK_TFLOPS = 1.26
 FP32_PEAK_TFLOPS = 72.0
-# DRAM bytes (read + write) of one launch of the hash gather, from ncu
-# (profiles/hash_gather_dense_50000x4000.md); None where not captured.
-GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2512025088 + 236451840}
+# DRAM bytes (read + write) of the sketch stage's kernels (premix passes and
+# hash gathers of all column slabs, one solve), from ncu; None where not captured
+# for the current kernels.
+SKETCH_TRAFFIC = {}
 
 
 class ClockSampler:
@@ -150,6 +162,8 @@ def make_problem(name, seed):
     n, d, npad, s, gamma, kind = WORKLOADS[name]
     if kind == "gauss":
         A, b = workloads.dense_gaussian(n, d, seed)
+    elif kind.startswith("usv:"):
+        A, b = workloads.usv_torch(n, d, float(kind[4:]), seed, "cuda")
     elif kind == "coh":
         A, b = workloads.dense_high_coherence(n, d, seed)
     else:
@@ -162,10 +176,22 @@ def sketch_bytes(cfg):
     return 8.0 * (n * d + n + m * (d + 1))
 
 
+def host_cols(A, cols):
+    """A[:, :cols] as a host numpy array (A numpy or a device tensor)."""
+    if hasattr(A, "detach"):
+        return A[:, :cols].cpu().numpy()
+    return A[:, :cols].copy()
+
+
+def host_vec(b):
+    return b.cpu().numpy() if hasattr(b, "detach") else b
+
+
 def oracle_sample(A, b, cfg, cols, seed):
     """Time the CPU oracle's sketch on A[:, :cols] (the bounded CPU sample)."""
     from oracle import sketch as osk, wht as owht
-    Asub = A[:, :cols].copy()
+    Asub = host_cols(A, cols)
+    b = host_vec(b)
     t0 = time.perf_counter()
     if cfg["n_pad"]:
         owht.hrht_sketch(seed, cfg["s"], cfg["m"], Asub, b, cfg["n_pad"])
@@ -216,22 +242,24 @@ def run_ours(args, name):
     pkg.lib()
     A, b, cfg = make_problem(name, args.seed + rank)
     n, d, m, s, npad = cfg["n"], cfg["d"], cfg["m"], cfg["s"], cfg["n_pad"]
-    At = torch.from_numpy(A).cuda()
-    bt = torch.from_numpy(b).cuda()
+    At = A if torch.is_tensor(A) else torch.from_numpy(A).cuda()
+    bt = b if torch.is_tensor(b) else torch.from_numpy(b).cuda()
     Amat = pkg.dense_matrix(At)
     # LSQR stops on Eq. TC-lsqr at tau_r = 1e-10; the FP64 acceptance test
     # ||A^T r|| / (||A||_F ||r||) <= 1e-10 is then checked (warm restart if not)
-    common = dict(m=m, s=s, seed=args.seed, premix=1 if npad else 0, n_pad=npad, tol=1e-10, tau_r=1e-10)
+    common = dict(m=m, s=s, seed=args.seed, premix=1 if npad else 0, n_pad=npad, tol=1e-10, tau_r=1e-10,
+                  premix_slab=args.premix_slab)
     o64 = pkg.ski_opts_default(**common)
-    omx = pkg.ski_opts_default(sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32, **common)
+    qmx = pkg.SKI_TF32 if args.qr_mixed == "tf32" else pkg.SKI_F32
+    omx = pkg.ski_opts_default(sketch_dtype=pkg.SKI_F32, qr_dtype=qmx, **common)
     x = torch.empty(d, dtype=torch.float64, device="cuda")
     ws = torch.empty(max(pkg.ski_solve_workspace_size(Amat, o64), pkg.ski_solve_workspace_size(Amat, omx)),
                      dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
-        i64 = pkg.ski_solve(Amat, bt, o64, x, ws=ws)
-        imx = pkg.ski_solve(Amat, bt, omx, x, ws=ws)
+        i64 = pkg.ski_solve(Amat, bt, o64, x, ws=ws, check=False)
+        imx = pkg.ski_solve(Amat, bt, omx, x, ws=ws, check=False)
         return i64, imx
 
     for _ in range(args.warmup):
@@ -258,12 +286,13 @@ def run_ours(args, name):
     sk_ms = max_over_ranks(statistics.mean(i.ms_sketch for i, _ in infos), world)
     value = world * sb / (sk_ms * 1e-3) / 1e9
     hbm, peak_kind, pj = peaks()
-    # the hash gather kernel: reads the premixed Y (n_pad x (d+1)) once per nonzero, writes [SA | Sb]
-    rows = npad if npad else n
-    gather_bytes = 8.0 * (s * rows * (d + 1) + m * (d + 1))
+    # the sketch stage after the bucket lists: with the premix, its passes and
+    # the hash gather run slab by slab over the columns (ms_premix covers both);
+    # without, the gather alone (ms_gather).  Algorithmic bytes: A and b read
+    # once, [SA | Sb] written once -- the intermediates stay in L2.
     g_ms = statistics.mean(i.ms_gather for i, _ in infos)
     pm_ms = statistics.mean(i.ms_premix for i, _ in infos)
-    premix_bytes = 8.0 * (n * (d + 1) + npad * (d + 1)) if npad else 0.0
+    stage_ms = pm_ms + g_ms
     qr_flops = 2.0 * m * (d + 1) ** 2 - 2.0 / 3.0 * d ** 3
     qr64 = statistics.mean(i.ms_qr for i, _ in infos)
     qrmx = statistics.mean(j.ms_qr for _, j in infos)
@@ -281,18 +310,21 @@ def run_ours(args, name):
                 "frac": gemm_flops / (g64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (DFMA loop measured 1.00)",
                 "flops_per_step": gemm_flops, "ms_per_step": g64}
-    sketch_roofline = {"kernel": "k_sketch_dense_f64acc (hash gather)", "bound": "hbm",
-                       "achieved": gather_bytes / (g_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                       "frac": gather_bytes / (g_ms * 1e-3) / 1e9 / hbm, "traffic": GATHER_TRAFFIC.get(name),
-                       "peak_source": peak_kind, "bytes_per_launch": gather_bytes, "ms_per_launch": g_ms}
+    sketch_roofline = {"kernel": ("k_wht_fx + k_sketch_slab_f64acc (premix and hash gather in L2 column slabs)"
+                                  if npad else "k_sketch_dense_f64acc (hash gather)"), "bound": "hbm",
+                       "achieved": sb / (stage_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                       "frac": sb / (stage_ms * 1e-3) / 1e9 / hbm, "traffic": SKETCH_TRAFFIC.get(name),
+                       "peak_source": peak_kind, "bytes_per_stage": sb, "ms_per_stage": stage_ms}
     tf32_peak = 0.5 * pj.get("bf16_tflops", 1900.0)
-    tc_roofline = {"kernel": "k_gemm_tc (TF32 QR trailing update, mixed path)", "bound": "tensor",
+    # the mixed path's QR runs its products in three TF32 passes: the tensor
+    # pipe executes 3x the algorithmic flops counted here
+    tc_roofline = {"kernel": "k_gemm_tc<.., SPLIT> (3-pass TF32 QR trailing update, mixed path)", "bound": "tensor",
                    "achieved": gemm_flops / (g32 * 1e-3) / 1e12, "unit": "TFLOP/s",
                    "peak": tf32_peak, "frac": gemm_flops / (g32 * 1e-3) / 1e12 / tf32_peak,
                    "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 0.5", "ms_per_step": g32}
     stages = {
-        "premix_fp64": {"ms": pm_ms, "bound": "hbm", "algorithmic_bytes": premix_bytes,
-                        "achieved_gbs": premix_bytes / (pm_ms * 1e-3) / 1e9 if pm_ms > 0 else None},
+        "premix_and_hash_fp64": {"ms": stage_ms, "bound": "hbm", "algorithmic_bytes": sb,
+                                 "achieved_gbs": sb / (stage_ms * 1e-3) / 1e9 if stage_ms > 0 else None},
         "qr_fp64": {"ms": qr64, "bound": "alu", "flops": qr_flops,
                     "achieved_tflops": qr_flops / (qr64 * 1e-3) / 1e12,
                     "peak_tflops": FP64_PEAK_TFLOPS},
@@ -301,10 +333,14 @@ def run_ours(args, name):
     }
     lls = {
         "fp64": {"ms": statistics.mean(i.ms_total for i, _ in infos), "iters": infos[-1][0].iters,
+                 "restarts": infos[-1][0].restarts, "status": infos[-1][0].status,
+                 "rdiag_ratio": infos[-1][0].rdiag_ratio,
                  "metric": max(i.metric for i, _ in infos), "ms_sketch": sk_ms, "ms_qr": qr64,
                  "ms_trinv": statistics.mean(i.ms_trinv for i, _ in infos),
                  "ms_lsqr": statistics.mean(i.ms_lsqr for i, _ in infos)},
         "mixed_fp32": {"ms": statistics.mean(j.ms_total for _, j in infos), "iters": infos[-1][1].iters,
+                       "restarts": infos[-1][1].restarts, "status": infos[-1][1].status,
+                       "qr_fallback": infos[-1][1].qr_fallback, "rdiag_ratio": infos[-1][1].rdiag_ratio,
                        "metric": max(j.metric for _, j in infos),
                        "ms_sketch": statistics.mean(j.ms_sketch for _, j in infos), "ms_qr": qrmx,
                        "ms_trinv": statistics.mean(j.ms_trinv for _, j in infos),
@@ -313,8 +349,8 @@ def run_ours(args, name):
 
     # end to end through the public API with host buffers: pinned A, b -> device,
     # ski_sketch_hash, [SA | Sb] -> pinned host
-    Ah = torch.from_numpy(A).pin_memory()
-    bh = torch.from_numpy(b).pin_memory()
+    Ah = (A.cpu() if torch.is_tensor(A) else torch.from_numpy(A)).pin_memory()
+    bh = (b.cpu() if torch.is_tensor(b) else torch.from_numpy(b)).pin_memory()
     SAd = torch.empty(m, d + 1, dtype=torch.float64, device="cuda")
     SAh = torch.empty(m, d + 1, dtype=torch.float64).pin_memory()
     sws = torch.empty(pkg.ski_sketch_workspace_size(Amat, 1, o64), dtype=torch.uint8, device="cuda")
@@ -350,6 +386,7 @@ def run_ours(args, name):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": name, "n": n, "d": d, "n_pad": npad, "m": m, "s": s, "gamma": cfg["gamma"],
+                       "mixed_qr": args.qr_mixed, "premix_slab": args.premix_slab,
                        "A": cfg["kind"], "b": "ones" if cfg["kind"] != "lls" else "A x + 1e-3 N(0,1)",
                        "l2": "inputs larger than L2 (A = %.2f GB)" % (8e-9 * n * d),
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -358,6 +395,373 @@ def run_ours(args, name):
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- sparse workload
+def csr_bytes(n, nnz, m, d):
+    """Sketch metric bytes of the CSR path: rowptr, colidx, values and b read,
+    [SA | Sb] written."""
+    return 8.0 * (n + 1) + 12.0 * nnz + 8.0 * n + 8.0 * m * (d + 1)
+
+
+def make_csr(name, seed):
+    from paper_2105_11815_gb300 import workloads
+    n, d, _, s, gamma, _ = WORKLOADS[name]
+    rowptr, colidx, val, b = workloads.csr_heavy_rows(n, d, seed)
+    return rowptr, colidx, val, b, dict(n=n, d=d, n_pad=0, s=s, m=int(round(gamma * d)), gamma=gamma, kind="csr",
+                                        nnz=int(rowptr[-1]))
+
+
+def csr_oracle_sample(rowptr, colidx, val, b, cfg, cols, seed):
+    """Time the oracle's CSR sketch restricted to the columns < cols (all rows)."""
+    import numpy as np
+    import scipy.sparse as sp
+    from oracle import sketch as osk
+    n = cfg["n"]
+    keep = colidx < cols
+    rows = np.repeat(np.arange(n), np.diff(rowptr))[keep]
+    A = sp.csr_matrix((val[keep], (rows, colidx[keep])), shape=(n, cols))
+    t0 = time.perf_counter()
+    osk.sketch_rows(seed, cfg["s"], cfg["m"], A, b)
+    dt = time.perf_counter() - t0
+    return csr_bytes(n, int(keep.sum()), cfg["m"], cols) / dt / 1e9, dt, int(keep.sum())
+
+
+def run_reference_csr(args, name):
+    rank, world, _ = dist_init(args.gpus)
+    if rank != 0:
+        return
+    rowptr, colidx, val, b, cfg = make_csr(name, args.seed)
+    cols = args.ref_cols
+    for _ in range(args.warmup):
+        csr_oracle_sample(rowptr, colidx, val, b, cfg, cols, args.seed)
+    vals, times = [], []
+    nnz_s = 0
+    for _ in range(args.steps):
+        v, dt, nnz_s = csr_oracle_sample(rowptr, colidx, val, b, cfg, cols, args.seed)
+        vals.append(v)
+        times.append(dt)
+    value = statistics.mean(vals)
+    sample = "oracle CSR sketch (numpy FP64) of the columns < %d (%d nonzeros), all rows, m=%d, s=%d" % (
+        cols, nnz_s, cfg["m"], cfg["s"])
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, **cfg},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_csr(args, name):
+    import torch
+
+    import paper_2105_11815_gb300 as pkg
+    from paper_2105_11815_gb300 import build
+
+    rank, world, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    build.build()
+    pkg.lib()
+    rowptr, colidx, val, b, cfg = make_csr(name, args.seed + rank)
+    n, d, m, s, nnz = cfg["n"], cfg["d"], cfg["m"], cfg["s"], cfg["nnz"]
+    rp, ci, va, bt = (torch.from_numpy(x).cuda() for x in (rowptr, colidx, val, b))
+    Amat = pkg.csr_matrix(rp, ci, va, n, d)
+    common = dict(m=m, s=s, seed=args.seed, tol=1e-10, tau_r=1e-10)
+    o64 = pkg.ski_opts_default(**common)
+    omx = pkg.ski_opts_default(sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32, **common)
+    x = torch.empty(d, dtype=torch.float64, device="cuda")
+    ws = torch.empty(max(pkg.ski_solve_workspace_size(Amat, o64), pkg.ski_solve_workspace_size(Amat, omx)),
+                     dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return pkg.ski_solve(Amat, bt, o64, x, ws=ws), pkg.ski_solve(Amat, bt, omx, x, ws=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = pkg.ski_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = pkg.ski_launch_count() - l0
+    clk = clocks.stop()
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1), world) / args.steps
+    sb = csr_bytes(n, nnz, m, d)
+    sk_ms = max_over_ranks(statistics.mean(i.ms_sketch for i, _ in infos), world)
+    value = world * sb / (sk_ms * 1e-3) / 1e9
+    hbm, peak_kind, _ = peaks()
+    gemm_flops = qr_gemm_flops(m, d)
+    g64 = statistics.mean(i.ms_qr_gemm for i, _ in infos)
+    roofline = {"kernel": "k_gemm<double> (FP64 QR trailing update)", "bound": "alu",
+                "achieved": gemm_flops / (g64 * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": gemm_flops / (g64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz", "ms_per_step": g64}
+    g_ms = statistics.mean(i.ms_gather for i, _ in infos)
+    sketch_roofline = {"kernel": "k_sketch_csr<double> (CSR hash sketch)", "bound": "hbm",
+                       "achieved": sb / (g_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                       "frac": sb / (g_ms * 1e-3) / 1e9 / hbm, "traffic": None, "peak_source": peak_kind,
+                       "bytes_per_launch": sb, "ms_per_launch": g_ms}
+    lls = {lab: {"ms": statistics.mean(v.ms_total for v in col), "iters": col[-1].iters,
+                 "restarts": col[-1].restarts, "metric": max(v.metric for v in col),
+                 "ms_sketch": statistics.mean(v.ms_sketch for v in col),
+                 "ms_qr": statistics.mean(v.ms_qr for v in col),
+                 "ms_trinv": statistics.mean(v.ms_trinv for v in col),
+                 "ms_lsqr": statistics.mean(v.ms_lsqr for v in col)}
+           for lab, col in (("fp64", [i for i, _ in infos]), ("mixed_fp32", [j for _, j in infos]))}
+    # end to end: pinned CSR arrays and b -> device, ski_sketch_hash, [SA | Sb] -> pinned host
+    hs = [torch.from_numpy(x).pin_memory() for x in (rowptr, colidx, val, b)]
+    SAd = torch.empty(m, d + 1, dtype=torch.float64, device="cuda")
+    SAh = torch.empty(m, d + 1, dtype=torch.float64).pin_memory()
+    sws = torch.empty(pkg.ski_sketch_workspace_size(Amat, 1, o64), dtype=torch.uint8, device="cuda")
+
+    def e2e_step():
+        for dst, src in zip((rp, ci, va, bt), hs):
+            dst.copy_(src, non_blocking=True)
+        pkg.ski_sketch_hash(Amat, bt, o64, SAd, d + 1, ws=sws)
+        SAh.copy_(SAd, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(ev0.elapsed_time(ev1), world) / args.steps
+    e2e = {"value": world * sb / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": int(8 * (n + 1) + 12 * nnz + 8 * n), "d2h_bytes_per_step": int(8 * m * (d + 1)),
+           "ms_per_step": e2e_ms}
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, _, nnz_s = csr_oracle_sample(rowptr, colidx, val, b, cfg, args.ref_cols, args.seed)
+        cpu = {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle CSR sketch (numpy FP64) of the columns < %d (%d nonzeros), all rows" % (
+                   args.ref_cols, nnz_s)}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "n": n, "d": d, "nnz": nnz, "m": m, "s": s, "A": "csr_heavy_rows",
+                       "b": "ones", "l2": "SA output larger than L2 (%.1f GB)" % (8e-9 * m * (d + 1)),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "hbm_frac": value / world / hbm, "roofline": roofline, "sketch_roofline": sketch_roofline,
+            "lls": lls, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches)}),
+            flush=True)
+
+
+# ---------------------------------------------------------------- ragged batch
+BATCH_METRIC = "batched LLS problems/s to ||A^T r||/(||A||_F ||r||) <= 1e-10, forward + adjoint backward"
+
+
+def batch_oracle_sample(shapes, seed, count):
+    """Time the oracle's Ski-LLS and adjoint on the first `count` problems."""
+    import numpy as np
+    from oracle import adjoint as oadj, lsqr as olsqr
+    g = np.random.default_rng(seed)
+    t = 0.0
+    for i, (n, d) in enumerate(shapes[:count]):
+        A = g.standard_normal((n, d))
+        b = g.standard_normal(n)
+        c = g.standard_normal(d)
+        t0 = time.perf_counter()
+        x, _ = olsqr.ski_lls(A, b, seed + i, 1, int(2 * d), tau_r=1e-10)
+        oadj.lstsq_grad(A, b, x, c)
+        t += time.perf_counter() - t0
+    return count / t, t
+
+
+def run_reference_batched(args, name):
+    rank, world, _ = dist_init(args.gpus)
+    if rank != 0:
+        return
+    from paper_2105_11815_gb300 import workloads
+    count = WORKLOADS[name][0]
+    shapes = workloads.ragged_batch(count, args.seed)
+    batch_oracle_sample(shapes, args.seed, 1)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt = batch_oracle_sample(shapes, args.seed, args.ref_problems)
+        vals.append(v)
+        times.append(dt)
+    value = statistics.mean(vals)
+    sample = "oracle Ski-LLS + adjoint (numpy FP64) on the first %d problems of the batch" % args.ref_problems
+    print(json.dumps({
+        "impl": "reference", "metric": BATCH_METRIC, "value": value, "unit": "problems/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "problems": count},
+        "cpu_baseline": {"value": value, "unit": "problems/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "problems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+        flush=True)
+
+
+def run_batched(args, name):
+    import torch
+
+    import paper_2105_11815_gb300 as pkg
+    from paper_2105_11815_gb300 import build, workloads
+
+    rank, world, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    build.build()
+    pkg.lib()
+    count = WORKLOADS[name][0]
+    gamma = WORKLOADS[name][4]
+    shapes, As, bs = workloads.ragged_batch_torch(count, args.seed + rank, "cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(args.seed + 7)
+    gs = [torch.randn(d, generator=gen, device="cuda", dtype=torch.float64) for _, d in shapes]
+    mats = [pkg.dense_matrix(a) for a in As]
+    xs = [torch.empty(d, dtype=torch.float64, device="cuda") for _, d in shapes]
+    Rs = [torch.empty(d, d, dtype=torch.float64, device="cuda") for _, d in shapes]
+    dAs = [torch.empty_like(a) for a in As]
+    dbs = [torch.empty_like(b) for b in bs]
+    stream = torch.cuda.current_stream()
+
+    def opts(streams):
+        return pkg.ski_opts_default(m=-int(round(1000 * gamma)), s=1, seed=args.seed, tol=1e-10, tau_r=1e-10,
+                                    streams=streams)
+
+    wsz = {}
+
+    def workspace(o):
+        k = o.streams
+        if k not in wsz:
+            nb = max(pkg.ski_solve_batched_workspace_size(mats, o),
+                     pkg.ski_solve_adjoint_batched_workspace_size(mats, o))
+            wsz[k] = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        return wsz[k]
+
+    def step(o):
+        w = workspace(o)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t_mid = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        fi = pkg.ski_solve_batched(mats, bs, o, xs, R_outs=Rs, ws=w, check=False)
+        t_mid.record(stream)
+        bi = pkg.ski_solve_adjoint_batched(mats, bs, xs, Rs, gs, dAs, dbs, o, ws=w, check=False)
+        return fi, bi, (t0, t_mid)
+
+    def timed(o, steps, warmup):
+        for _ in range(warmup):
+            step(o)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [step(o) for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = max_over_ranks(e0.elapsed_time(e1), world) / steps
+        fwd = statistics.mean(a.elapsed_time(b) for _, _, (a, b) in res)
+        return ms, res, fwd
+
+    o_main = opts(args.streams)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = pkg.ski_launch_count()
+    ms_step, res, fwd_ms = timed(o_main, args.steps, args.warmup)
+    launches = pkg.ski_launch_count() - l0
+    clk = clocks.stop()
+    value = world * count / (ms_step * 1e-3)
+    fi, bi, _ = res[-1]
+    worst = max(i.metric for i in fi)
+    iters = [i.iters for i in fi]
+    # algorithmic HBM bytes of one step: A read by the sketch, by the residual and
+    # split passes (3 reads of A in FP64 + 1 write/read of the float2 copy) and by
+    # every LSQR pass (the float2 copy, 8 bytes per element); the adjoint reads A
+    # once per CG iteration and twice more, and writes dA
+    byt = 0.0
+    for (n, d), f, bw in zip(shapes, fi, bi):
+        byt += 8.0 * n * d * (1 + 3 + 2 + f.iters + f.restarts * 2)
+        byt += 8.0 * n * d * (bw.iters + 3)
+    hbm, peak_kind, _ = peaks()
+    roofline = {"kernel": "whole batch (A reads of every pass, aggregate)", "bound": "hbm",
+                "achieved": byt / (ms_step * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": byt / (ms_step * 1e-3) / 1e9 / hbm, "traffic": None, "peak_source": peak_kind,
+                "bytes_per_step": byt}
+    # sequential form on the same GPU (one problem at a time) and a sweep of the
+    # number of problems in flight
+    sweep = {}
+    for w in args.sweep:
+        ms_w, _, fwd_w = timed(opts(w), 1, 1)
+        sweep[str(w)] = {"ms_per_step": ms_w, "problems_s": count / (ms_w * 1e-3), "fwd_ms": fwd_w}
+    # end to end: pinned host A_i, b_i -> device, solve + adjoint, x_i, dA_i, db_i -> host
+    Ah = [a.cpu().pin_memory() for a in As]
+    bh = [b.cpu().pin_memory() for b in bs]
+    xh = [torch.empty(d, dtype=torch.float64).pin_memory() for _, d in shapes]
+    dAh = [torch.empty(a.shape, dtype=torch.float64).pin_memory() for a in As]
+
+    def e2e_step():
+        for a, h in zip(As, Ah):
+            a.copy_(h, non_blocking=True)
+        for b, h in zip(bs, bh):
+            b.copy_(h, non_blocking=True)
+        step(o_main)
+        for x, h in zip(xs, xh):
+            h.copy_(x, non_blocking=True)
+        for a, h in zip(dAs, dAh):
+            h.copy_(a, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    nA = sum(n * d for n, d in shapes)
+    nb_ = sum(n for n, _ in shapes)
+    nd_ = sum(d for _, d in shapes)
+    e2e = {"value": world * count / (e2e_ms * 1e-3), "unit": "problems/s",
+           "h2d_bytes_per_step": int(8 * (nA + nb_)), "d2h_bytes_per_step": int(8 * (nd_ + nA)),
+           "ms_per_step": e2e_ms}
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, _ = batch_oracle_sample(shapes, args.seed, args.ref_problems)
+        cpu = {"value": v, "unit": "problems/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle Ski-LLS + adjoint (numpy FP64) on the first %d problems" % args.ref_problems}
+    if rank == 0:
+        print(json.dumps({
+            "metric": BATCH_METRIC, "value": value, "unit": "problems/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "problems": count, "gamma": gamma, "s": 1,
+                       "streams": o_main.streams or "auto", "A_bytes": 8 * nA,
+                       "l2": "inputs larger than L2 (%.1f GB)" % (8e-9 * nA),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "forward_ms": fwd_ms, "backward_ms": ms_step - fwd_ms, "worst_metric": worst,
+            "iters": {"min": min(iters), "max": max(iters), "mean": statistics.mean(iters)},
+            "restarts": {"max": max(i.restarts for i in fi), "mean": statistics.mean(i.restarts for i in fi)},
+            "adjoint_iters": {"min": min(i.iters for i in bi), "max": max(i.iters for i in bi),
+                              "mean": statistics.mean(i.iters for i in bi)},
+            "statuses": {"forward": {str(k): sum(1 for i in fi if i.status == k) for k in set(i.status for i in fi)},
+                         "backward": {str(k): sum(1 for i in bi if i.status == k) for k in set(i.status for i in bi)}},
+            "failed": [{"i": k, "n": shapes[k][0], "d": shapes[k][1], "status": int(i.status), "iters": int(i.iters),
+                        "restarts": int(i.restarts), "metric": i.metric} for k, i in enumerate(fi) if i.status][:8],
+            "roofline": roofline, "streams_sweep": sweep, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": int(launches)}), flush=True)
+
+
+def qr_gemm_flops(m, d):
+    """Flops of the QR trailing-update GEMMs, summed over the 32-column panels:
+    W = V^T C and C -= V B' each cost 2 w nct mr."""
+    f = 0.0
+    for k0 in range(0, d, 32):
+        w = min(32, d - k0)
+        f += 4.0 * w * ((d + 1) - k0 - w) * (m - k0)
+    return f
 
 
 def main():
@@ -370,9 +774,25 @@ def main():
     ap.add_argument("--seed", type=int, default=20210525)
     ap.add_argument("--ref-cols", type=int, default=1024)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--streams", type=int, default=0, help="batched workload: problems in flight (0 = auto)")
+    ap.add_argument("--sweep", type=int, nargs="*", default=[1], help="batched workload: also time these")
+    ap.add_argument("--ref-problems", type=int, default=3, help="batched workload: oracle sample size")
+    ap.add_argument("--premix-slab", type=int, default=0, help="premix column slab width (0 = full width)")
+    ap.add_argument("--qr-mixed", default="f32", choices=["f32", "tf32"],
+                    help="QR precision of the mixed solve: f32 (three TF32 passes) or tf32 (one)")
     args = ap.parse_args()
+    kind = WORKLOADS[args.workload][5]
     if args.impl == "reference":
-        run_reference(args, args.workload)
+        if kind == "csr":
+            run_reference_csr(args, args.workload)
+        elif kind == "batched":
+            run_reference_batched(args, args.workload)
+        else:
+            run_reference(args, args.workload)
+    elif kind == "csr":
+        run_csr(args, args.workload)
+    elif kind == "batched":
+        run_batched(args, args.workload)
     else:
         run_ours(args, args.workload)
 

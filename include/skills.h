@@ -49,7 +49,10 @@ typedef enum {
   SKI_ETIMEOUT = 7     /* a bounded device-side wait gave up                       */
 } ski_status;
 
-typedef enum { SKI_F64 = 0, SKI_F32 = 1, SKI_BF16 = 2 } ski_dtype;
+/* SKI_TF32 is a QR precision only (qr_dtype, ski_precondition's sa_dtype): FP32
+ * storage with the trailing-update products in one TF32 tensor-core pass (11
+ * significant bits), where SKI_F32 takes three passes (about FP32 accuracy). */
+typedef enum { SKI_F64 = 0, SKI_F32 = 1, SKI_BF16 = 2, SKI_TF32 = 3 } ski_dtype;
 typedef enum { SKI_DENSE = 0, SKI_CSR = 1 } ski_kind;
 
 /* The data matrix A (n x d).  Values are FP64 in both layouts. */
@@ -72,13 +75,18 @@ typedef struct {
   int64_t m;              /* sketch rows, d <= m < 2^31                                */
   int64_t n_pad;          /* premix height, a power of two >= n; 0: next power of two */
   int32_t sketch_dtype;   /* ski_dtype of the premix, the sketch and its output SA     */
-  int32_t qr_dtype;       /* ski_dtype of the QR of SA and of R^{-1} (R kept in FP64)   */
+  int32_t qr_dtype;       /* QR of SA and R^{-1}: SKI_F64, SKI_F32 (tensor-core products */
+                          /* in three TF32 passes) or SKI_TF32 (one); R kept in FP64    */
   double tau_a;           /* Step 3: accept x_s when ||A x_s - b|| <= tau_a            */
   double tau_r;           /* Step 4: LSQR tolerance of Eq. TC-lsqr                     */
   double tol;             /* acceptance: ||A^T r|| / (||A||_F ||r||) <= tol, 0 = off   */
   double rcond;           /* rank rule: |r_qq| >= rcond |r_11| for all q               */
   double perturb;         /* > 0: divide by r_ii + perturb when R fails the rank rule  */
   int64_t it_max;         /* Step 4 iteration cap                                       */
+  int32_t streams;        /* batched entry points: problems in flight, each on its own */
+                          /* stream and workspace slice; 0 = min(nprob, 8), max 32      */
+  int32_t premix_slab;    /* premix + hash run in column slabs of this many columns     */
+                          /* (a multiple of 32, <= 128) kept in L2; 0 = auto            */
 } ski_opts;
 
 /* Result record of a solve (host memory). */
@@ -95,6 +103,11 @@ typedef struct {
   float ms_sketch, ms_qr, ms_trinv, ms_lsqr, ms_total;  /* stage times, CUDA events */
   float ms_premix, ms_gather;  /* inside ms_sketch: the H D premix and the hash gather */
   float ms_qr_gemm;            /* inside ms_qr: the trailing-update GEMMs, summed     */
+  int32_t qr_fallback;         /* mixed form: 0 kept the FP32/TF32 factor; 1 redid     */
+                               /* Steps 1-2 in FP64 (ratio or rank), 2 after LSQR      */
+                               /* exhausted its budget with the FP32 preconditioner    */
+  int32_t pad_;
+  double rdiag_ratio;          /* max |r_ii| / min |r_ii| of the last factor           */
 } ski_info;
 
 /* Defaults of Ski-LLS-dense (Section 6): m = 0 (caller must set), s = 1,
@@ -197,7 +210,8 @@ ski_status ski_sketch_hash_noalloc(const ski_matrix* A, const double* b, const s
  * d <= m), applying every reflector also to column d when with_rhs = 1 so that
  * column d becomes Q^T Sb.
  *   SA     device, m x (d + with_rhs), row stride ld_sa, element type sa_dtype
- *          (FP64 or FP32); overwritten by the reflectors.
+ *          (FP64, or FP32 for SKI_F32 and SKI_TF32, which differ in the
+ *          tensor-core passes of the trailing update); overwritten.
  *   R      device FP64 d x d (row stride ldr): the upper triangle receives R,
  *          the strict lower triangle is set to zero.
  *   qtsb   device FP64 [d] or NULL: receives (Q^T Sb)[0..d-1] (with_rhs = 1).
@@ -216,13 +230,15 @@ ski_status ski_precondition(int64_t m, int64_t d, int32_t with_rhs, void* SA, in
  * on the TF32 tensor cores with FP32 accumulation: the kernel of the FP32
  * trailing update of Step 2, exposed for testing and reuse.  A: M x K,
  * B: N x K, C: M x N, all device FP32 row-major; lda and ldb multiples of 4
- * with 16-byte aligned bases (SKI_EINVAL otherwise).  Products use the top
- * 10 mantissa bits of each operand (TF32).  ws: device scratch >= 4 bytes
- * (an error flag).  Synchronous; SKI_ETIMEOUT if a bounded wait gave up.
+ * with 16-byte aligned bases (SKI_EINVAL otherwise).  passes = 1: products
+ * of the operands rounded to TF32 (11 significant bits); passes = 3: each
+ * operand split as hi + lo (both TF32) and lo*hi + hi*lo + hi*hi accumulated
+ * (error about 2^-21 |a||b| per product).  ws: device scratch >= 4 bytes (an
+ * error flag).  Synchronous; SKI_ETIMEOUT if a bounded wait gave up.
  */
 ski_status ski_gemm_tc_f32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
-                           int64_t ldb, float* C, int64_t ldc, int32_t subtract, void* ws, size_t ws_bytes,
-                           void* stream);
+                           int64_t ldb, float* C, int64_t ldc, int32_t subtract, int32_t passes, void* ws,
+                           size_t ws_bytes, void* stream);
 
 /*
  * ski_trinv -- M = R^{-1} for an upper-triangular d x d R (FP64, row stride
@@ -252,11 +268,19 @@ ski_status ski_solve(const ski_matrix* A, const double* b, const ski_opts* o, do
  * ski_solve_batched -- nprob independent problems (ragged n_i, d_i), each
  * solved as ski_solve with the same options except m_i = ceil(gamma * d_i)
  * when o->m <= 0 (gamma = -o->m / 1000, e.g. m = -2000 for gamma = 2) and
- * seed_i = o->seed + i.  A, b, x, R_out, info are host arrays of nprob
- * entries (R_out may be NULL, or hold NULL entries); b[i], x[i], R_out[i] are
- * device pointers.  The workspace is one per problem in flight:
- * ski_solve_batched_workspace_size gives its size.  Synchronous.  Returns the
- * first non-SKI_OK status met (every problem is attempted).
+ * seed_i = o->seed + i.  Not in the paper, which solves one problem: this is
+ * the throughput form for many small problems.  A, b, x, R_out, info are host
+ * arrays of nprob entries (R_out may be NULL, or hold NULL entries); b[i],
+ * x[i], R_out[i] are device pointers.  W = o->streams problems (0: min(nprob,
+ * 8)) are solved at once, each by a host worker on its own non-blocking
+ * stream, largest problems first; work already queued on `stream` comes
+ * first and `stream` is ordered after all of it.  A problem's results do not
+ * depend on W or on which worker ran it.  The workspace holds W slices of the
+ * largest single-problem workspace: ski_solve_batched_workspace_size gives
+ * its size.  Synchronous.  Every problem is attempted unless a CUDA call
+ * fails (SKI_ECUDA stops the batch); returns the status of the
+ * lowest-numbered problem that did not return SKI_OK, else SKI_OK.
+ * SKI_EINVAL for o->streams < 0 or an invalid problem.
  */
 size_t ski_solve_batched_workspace_size(int32_t nprob, const ski_matrix* A, const ski_opts* o);
 ski_status ski_solve_batched(int32_t nprob, const ski_matrix* A, const double* const* b,
@@ -279,6 +303,21 @@ ski_status ski_solve_adjoint(const ski_matrix* A, const double* b, const double*
                              const double* R, int64_t ldr, const double* g, double* dA,
                              int64_t ld_da, double* db, const ski_opts* o, ski_info* info,
                              void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * ski_solve_adjoint_batched -- ski_solve_adjoint for nprob independent dense
+ * problems, W = o->streams at once as in ski_solve_batched (same stream
+ * ordering, workspace slicing and status rule).  Host arrays of nprob device
+ * pointers: b[i] [n_i], x[i] [d_i], R[i] (d_i x d_i, row stride d_i), g[i]
+ * [d_i], db[i] [n_i], dA[i] (n_i x d_i, row stride d_i; dA may be NULL, or
+ * hold NULL entries, to skip dA).  Synchronous.
+ */
+size_t ski_solve_adjoint_batched_workspace_size(int32_t nprob, const ski_matrix* A, const ski_opts* o);
+ski_status ski_solve_adjoint_batched(int32_t nprob, const ski_matrix* A, const double* const* b,
+                                     const double* const* x, const double* const* R,
+                                     const double* const* g, double* const* dA, double* const* db,
+                                     const ski_opts* o, ski_info* info, void* ws, size_t ws_bytes,
+                                     void* stream);
 
 #ifdef __cplusplus
 }

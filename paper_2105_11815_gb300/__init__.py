@@ -24,10 +24,11 @@ __all__ = [
     "ski_solve_workspace_size", "ski_solve",
     "ski_solve_batched_workspace_size", "ski_solve_batched",
     "ski_solve_adjoint_workspace_size", "ski_solve_adjoint",
+    "ski_solve_adjoint_batched_workspace_size", "ski_solve_adjoint_batched",
     "dense_matrix", "csr_matrix",
 ]
 
-SKI_F64, SKI_F32, SKI_BF16 = 0, 1, 2
+SKI_F64, SKI_F32, SKI_BF16, SKI_TF32 = 0, 1, 2, 3
 SKI_DENSE, SKI_CSR = 0, 1
 STATUS = ["SKI_OK", "SKI_EINVAL", "SKI_ENOMEM", "SKI_ECUDA", "SKI_ENONFINITE",
           "SKI_ESINGULAR", "SKI_ENOCONV", "SKI_ETIMEOUT"]
@@ -55,7 +56,8 @@ class ski_opts(ctypes.Structure):
                 ("m", ctypes.c_int64), ("n_pad", ctypes.c_int64),
                 ("sketch_dtype", ctypes.c_int32), ("qr_dtype", ctypes.c_int32),
                 ("tau_a", ctypes.c_double), ("tau_r", ctypes.c_double), ("tol", ctypes.c_double),
-                ("rcond", ctypes.c_double), ("perturb", ctypes.c_double), ("it_max", ctypes.c_int64)]
+                ("rcond", ctypes.c_double), ("perturb", ctypes.c_double), ("it_max", ctypes.c_int64),
+                ("streams", ctypes.c_int32), ("premix_slab", ctypes.c_int32)]
 
 
 class ski_info(ctypes.Structure):
@@ -65,7 +67,8 @@ class ski_info(ctypes.Structure):
                 ("anorm_f", ctypes.c_double), ("lsqr_test", ctypes.c_double),
                 ("ms_sketch", ctypes.c_float), ("ms_qr", ctypes.c_float), ("ms_trinv", ctypes.c_float),
                 ("ms_lsqr", ctypes.c_float), ("ms_total", ctypes.c_float),
-                ("ms_premix", ctypes.c_float), ("ms_gather", ctypes.c_float), ("ms_qr_gemm", ctypes.c_float)]
+                ("ms_premix", ctypes.c_float), ("ms_gather", ctypes.c_float), ("ms_qr_gemm", ctypes.c_float),
+                ("qr_fallback", ctypes.c_int32), ("pad_", ctypes.c_int32), ("rdiag_ratio", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -92,7 +95,7 @@ _SIGS = {
     "ski_sketch_hash_noalloc": (_I32, [_MP, _P, _OP, _P, _I64, _P]),
     "ski_precondition_workspace_size": (_SZ, [_I64, _I64, _I32, _I32]),
     "ski_precondition": (_I32, [_I64, _I64, _I32, _P, _I64, _I32, _P, _I64, _P, _P, _OP, _P, _SZ, _P]),
-    "ski_gemm_tc_f32": (_I32, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _P, _SZ, _P]),
+    "ski_gemm_tc_f32": (_I32, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I32, _I32, _P, _SZ, _P]),
     "ski_trinv_workspace_size": (_SZ, [_I64, _I32]),
     "ski_trinv": (_I32, [_I64, _P, _I64, _P, _P, _I64, _I32, _D, _P, _SZ, _P]),
     "ski_solve_workspace_size": (_SZ, [_MP, _OP]),
@@ -101,6 +104,8 @@ _SIGS = {
     "ski_solve_batched": (_I32, [_I32, _MP, _P, _OP, _P, _P, _IP, _P, _SZ, _P]),
     "ski_solve_adjoint_workspace_size": (_SZ, [_MP, _OP]),
     "ski_solve_adjoint": (_I32, [_MP, _P, _P, _P, _I64, _P, _P, _I64, _P, _OP, _IP, _P, _SZ, _P]),
+    "ski_solve_adjoint_batched_workspace_size": (_SZ, [_I32, _MP, _OP]),
+    "ski_solve_adjoint_batched": (_I32, [_I32, _MP, _P, _P, _P, _P, _P, _P, _OP, _IP, _P, _SZ, _P]),
 }
 
 
@@ -257,12 +262,12 @@ def ski_precondition(m, d, with_rhs, SA, ld_sa, sa_dtype, R, ldr, qtsb=None, wan
     return rank.value if want_rank else None
 
 
-def ski_gemm_tc_f32(M, N, K, A, lda, B, ldb, C, ldc, subtract=False, ws=None, stream=None):
-    """C = A B^T (or C -= A B^T) on the TF32 tensor cores."""
+def ski_gemm_tc_f32(M, N, K, A, lda, B, ldb, C, ldc, subtract=False, passes=1, ws=None, stream=None):
+    """C = A B^T (or C -= A B^T) on the TF32 tensor cores (1 or 3 passes)."""
     import torch
     w = ws if ws is not None else torch.zeros(16, dtype=torch.uint8, device=C.device)
-    return _check(lib().ski_gemm_tc_f32(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, int(subtract), _ptr(w),
-                                        16, _stream(stream)), "ski_gemm_tc_f32")
+    return _check(lib().ski_gemm_tc_f32(M, N, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, int(subtract),
+                                        int(passes), _ptr(w), 16, _stream(stream)), "ski_gemm_tc_f32")
 
 
 def ski_trinv_workspace_size(d, dtype):
@@ -312,6 +317,33 @@ def ski_solve_batched(mats, bs, opts, xs, R_outs=None, ws=None, stream=None, che
     st = lib().ski_solve_batched(k, arr, bp, ctypes.byref(opts), xp, rp, infos, _ptr(w), nb, _stream(stream))
     if check:
         _check(st, "ski_solve_batched")
+    return list(infos)
+
+
+def _ptr_array(ts):
+    if ts is None:
+        return None
+    return (ctypes.c_void_p * len(ts))(*[(t.data_ptr() if t is not None else None) for t in ts])
+
+
+def ski_solve_adjoint_batched_workspace_size(mats, opts):
+    arr = (ski_matrix * len(mats))(*mats)
+    return lib().ski_solve_adjoint_batched_workspace_size(len(mats), arr, ctypes.byref(opts))
+
+
+def ski_solve_adjoint_batched(mats, bs, xs, Rs, gs, dAs, dbs, opts, ws=None, stream=None, check=True):
+    """nprob independent adjoint solves (R[i] d_i x d_i, dA[i] n_i x d_i, both
+    contiguous); dAs may be None. Returns the list of ski_info records."""
+    k = len(mats)
+    arr = (ski_matrix * k)(*mats)
+    nb = lib().ski_solve_adjoint_batched_workspace_size(k, arr, ctypes.byref(opts))
+    w = _ws(nb, xs[0].device, ws)
+    infos = (ski_info * k)()
+    st = lib().ski_solve_adjoint_batched(k, arr, _ptr_array(bs), _ptr_array(xs), _ptr_array(Rs), _ptr_array(gs),
+                                         _ptr_array(dAs), _ptr_array(dbs), ctypes.byref(opts), infos, _ptr(w), nb,
+                                         _stream(stream))
+    if check:
+        _check(st, "ski_solve_adjoint_batched")
     return list(infos)
 
 

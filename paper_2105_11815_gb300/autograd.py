@@ -11,7 +11,8 @@ import copy
 
 import torch
 
-from . import dense_matrix, ski_opts_default, ski_solve, ski_solve_adjoint, ski_solve_batched
+from . import (dense_matrix, ski_opts_default, ski_solve, ski_solve_adjoint, ski_solve_adjoint_batched,
+               ski_solve_batched)
 
 
 def make_opts(d, gamma=2.0, s=1, seed=0, premix=False, tol=1e-10, tau_r=1e-12, it_max=10000, **kw):
@@ -56,7 +57,8 @@ def lstsq(A, b, opts=None, **kw):
 
 
 class SkiLstsqBatched(torch.autograd.Function):
-    """Ragged batch: forward by one ``ski_solve_batched`` call, backward per problem."""
+    """Ragged batch: forward by one ``ski_solve_batched`` call, backward by one
+    ``ski_solve_adjoint_batched`` call."""
 
     @staticmethod
     def forward(ctx, opts, *ab):
@@ -79,16 +81,10 @@ class SkiLstsqBatched(torch.autograd.Function):
         As, bs, xs, Rs = t[:k], t[k:2 * k], t[2 * k:3 * k], t[3 * k:]
         o = copy.copy(ctx.opts)
         o.tau_r = min(o.tau_r, 1e-13)
-        dAs, dbs = [], []
-        for A, b, x, R, g in zip(As, bs, xs, Rs, gs):
-            d = A.shape[1]
-            db = torch.empty_like(b)
-            dA = torch.empty_like(A)
-            if g is None:
-                g = torch.zeros_like(x)
-            ski_solve_adjoint(dense_matrix(A), b, x, R, d, g.contiguous(), dA, d, db, o)
-            dAs.append(dA)
-            dbs.append(db)
+        gs = [torch.zeros_like(x) if g is None else g.contiguous().to(torch.float64) for x, g in zip(xs, gs)]
+        dAs = [torch.empty_like(A) for A in As]
+        dbs = [torch.empty_like(b) for b in bs]
+        ski_solve_adjoint_batched([dense_matrix(A) for A in As], bs, xs, Rs, gs, dAs, dbs, o)
         return (None, *dAs, *dbs)
 
 

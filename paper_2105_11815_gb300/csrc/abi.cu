@@ -64,7 +64,9 @@ static int64_t next_pow2(int64_t v) {
   return p;
 }
 static bool dtype_ok(int32_t t) { return t == SKI_F64 || t == SKI_F32 || t == SKI_BF16; }
-static size_t dtype_size(int32_t t) { return t == SKI_F64 ? 8 : (t == SKI_F32 ? 4 : 2); }
+static size_t dtype_size(int32_t t) { return t == SKI_F64 ? 8 : ((t == SKI_F32 || t == SKI_TF32) ? 4 : 2); }
+// storage type of a QR precision: TF32 factors FP32 data
+static int32_t qr_storage(int32_t t) { return t == SKI_F64 ? SKI_F64 : SKI_F32; }
 
 static ski_status check_matrix(const ski_matrix* A) {
   if (!A) return SKI_EINVAL;
@@ -83,6 +85,7 @@ static ski_status check_matrix(const ski_matrix* A) {
 static ski_status check_sketch_opts(const ski_matrix* A, const ski_opts* o) {
   if (!o) return SKI_EINVAL;
   if (o->s < 1 || o->s > 64 || o->m < o->s || o->m >= (1ll << 31)) return SKI_EINVAL;
+  if (o->premix_slab < 0 || o->streams < 0) return SKI_EINVAL;
   if (!dtype_ok(o->sketch_dtype)) return SKI_EINVAL;
   if (o->premix) {
     if (A->kind != SKI_DENSE) return SKI_EINVAL;
@@ -99,17 +102,34 @@ static int64_t eff_npad(const ski_matrix* A, const ski_opts* o) {
 }
 
 // ------------------------------------------------------------ sketch stage
-// Scratch layout: [bucket lists][premix Y][premix intermediates]
+// Columns per premix slab.  With o->premix_slab = w > 0 (a multiple of 32, at
+// most 128) the premix and the hash gather run slab by slab over the columns:
+// the pass-1 intermediate and Y of one slab (n_pad rows each) can stay in the
+// 126 MiB L2 (w = 64 at n_pad = 65536), so only A is read from HBM and only
+// [SA | Sb] written.  0 (the default) transforms all columns at once: at
+// 50000 x 4000 the 63 slabs' 189 launches, each too small to hide its load
+// latency, took 4.6 ms against 3.1 ms for the full-width passes.
+static int64_t premix_slab_cols(int64_t n_pad, int64_t ncols, int32_t pdt, int32_t fixed) {
+  (void)n_pad;
+  (void)pdt;
+  const int64_t full = ski_round_up(ncols, 32);
+  if (fixed <= 0) return full;
+  const int64_t w = std::min<int64_t>(128, std::max<int64_t>(32, fixed / 32 * 32));
+  return std::min<int64_t>(w, full);
+}
+
+// Scratch layout: [bucket lists][premix Y slab][premix intermediates]
 static size_t sketch_scratch_bytes(const ski_matrix* A, int32_t with_b, const ski_opts* o, int64_t* ldy_out) {
   const int64_t ncols = A->d + (with_b ? 1 : 0);
   const int64_t rows = o->premix ? eff_npad(A, o) : A->n;
   SkiArena ar{nullptr, 0, 0, true};
   ar.take<char>(ski_bucket_ws_bytes(rows, o->s, o->m));
-  int64_t ldy = ski_round_up(ncols, 32);
+  int64_t ldy = 0;
   if (o->premix) {
     const int32_t pdt = o->sketch_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
+    ldy = premix_slab_cols(rows, ncols, pdt, o->premix_slab);
     ar.take<char>(dtype_size(pdt) * rows * ldy);
-    ar.take<char>(ski_premix_ws_bytes(A->n, ncols, rows, pdt));
+    ar.take<char>(ski_premix_ws_bytes(A->n, ldy, rows, pdt));
   }
   if (ldy_out) *ldy_out = ldy;
   return ar.off;
@@ -136,19 +156,35 @@ static ski_status sketch_run(const ski_matrix* A, const double* b, const ski_opt
     return ski_gather_csr(A, b, bk, inv_sqrt_s, o->sketch_dtype, SA, ld_sa, st);
   }
   const int32_t pdt = o->sketch_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
-  const int64_t ldy = ski_round_up(ncols, 32);
-  void* Y = ar.take<char>(dtype_size(pdt) * rows * ldy);
-  const size_t pwb = ski_premix_ws_bytes(A->n, ncols, rows, pdt);
+  if (pdt == SKI_F64 && o->sketch_dtype != SKI_F64) return SKI_EINVAL;
+  const int64_t w = premix_slab_cols(rows, ncols, pdt, o->premix_slab);
+  void* Y = ar.take<char>(dtype_size(pdt) * rows * w);
+  const size_t pwb = ski_premix_ws_bytes(A->n, w, rows, pdt);
   char* pws = ar.take<char>(pwb);
   if (!ar.ok() || !pws) return SKI_ENOMEM;
   SkiArena par{pws, pwb, 0, false};
-  double resid = 1.0;
-  SKI_TRY(ski_premix_run(A->val, A->ld, A->n, A->d, b, o->seed, rows, pdt, Y, ldy, par, st, &resid));
+  SkiPremixPlan plan;
+  SKI_TRY(ski_premix_plan(A->n, w, rows, pdt, o->seed, par, st, &plan));
+  const double scale = plan.residual_scale * inv_sqrt_s;
+  if (w >= ncols && (w > 128 || o->premix_slab <= 0)) {
+    // all columns at once: premix into Y, then the full-width hash gather
+    SKI_TRY(ski_premix_cols(plan, A->val, A->ld, A->d, b, Y, w, st));
+    if (e_pm) SKI_CUDA_TRY(cudaEventRecord(e_pm, st));
+    if (pdt == SKI_F64)
+      return ski_gather_dense((const double*)Y, w, rows, ncols, nullptr, bk, scale, SKI_F64, SA, ld_sa, st);
+    return ski_gather_dense_f32in((const float*)Y, w, ncols, bk, scale, o->sketch_dtype, SA, ld_sa, st);
+  }
+  // column slabs: premix then hash-gather each slab while it is in L2
+  const size_t osz = dtype_size(o->sketch_dtype);
+  for (int64_t c0 = 0; c0 < ncols; c0 += w) {
+    const int64_t cw = std::min<int64_t>(w, ncols - c0);
+    const int64_t da = std::max<int64_t>(0, std::min<int64_t>(cw, A->d - c0));  // columns of A in the slab
+    const double* bs = (b && c0 + cw > A->d) ? b : nullptr;                      // b is column d
+    SKI_TRY(ski_premix_cols(plan, A->val + std::min<int64_t>(c0, A->d), A->ld, da, bs, Y, w, st));
+    SKI_TRY(ski_gather_slab(Y, pdt, w, cw, bk, scale, o->sketch_dtype, (char*)SA + c0 * osz, ld_sa, st));
+  }
   if (e_pm) SKI_CUDA_TRY(cudaEventRecord(e_pm, st));
-  const double scale = resid * inv_sqrt_s;
-  if (pdt == SKI_F64)
-    return ski_gather_dense((const double*)Y, ldy, rows, ncols, nullptr, bk, scale, SKI_F64, SA, ld_sa, st);
-  return ski_gather_dense_f32in((const float*)Y, ldy, ncols, bk, scale, o->sketch_dtype, SA, ld_sa, st);
+  return SKI_OK;
 }
 
 extern "C" size_t ski_sketch_workspace_size(const ski_matrix* A, int32_t with_b, const ski_opts* o) {
@@ -198,11 +234,11 @@ extern "C" ski_status ski_premix(const ski_matrix* A, const double* b, const ski
 // ------------------------------------------------------------ QR stage
 extern "C" size_t ski_precondition_workspace_size(int64_t m, int64_t d, int32_t with_rhs, int32_t sa_dtype) {
   if (m < d || d < 1) return 0;
-  return ski_qr_ws_bytes(m, d + (with_rhs ? 1 : 0), sa_dtype);
+  return ski_qr_ws_bytes(m, d + (with_rhs ? 1 : 0), qr_storage(sa_dtype));
 }
 
 static ski_status rank_from_diag(int64_t d, const double* R, int64_t ldr, double rcond, cudaStream_t st, int32_t* rank,
-                                 bool* nonfinite) {
+                                 bool* nonfinite, double* ratio = nullptr) {
   std::vector<double> diag(d);
   // strided gather of the diagonal: d small copies would be slow; copy rows' diagonal via 2D memcpy
   SKI_CUDA_TRY(cudaMemcpy2DAsync(diag.data(), sizeof(double), R, (ldr + 1) * sizeof(double), sizeof(double), d,
@@ -218,6 +254,14 @@ static ski_status rank_from_diag(int64_t d, const double* R, int64_t ldr, double
     while (p < d && fabs(diag[p]) >= rcond * r11) ++p;
   }
   *rank = p;
+  if (ratio) {
+    double mx = 0.0, mn = INFINITY;
+    for (int64_t q = 0; q < d; ++q) {
+      mx = std::max(mx, fabs(diag[q]));
+      mn = std::min(mn, fabs(diag[q]));
+    }
+    *ratio = mn > 0.0 ? mx / mn : INFINITY;
+  }
   return SKI_OK;
 }
 
@@ -225,8 +269,8 @@ extern "C" ski_status ski_precondition(int64_t m, int64_t d, int32_t with_rhs, v
                                        int32_t sa_dtype, double* R, int64_t ldr, double* qtsb, int32_t* rank,
                                        const ski_opts* o, void* ws, size_t ws_bytes, void* stream) {
   if (d < 1 || m < d || !SA || !R || ldr < d || ld_sa < d + (with_rhs ? 1 : 0)) return SKI_EINVAL;
-  if (sa_dtype != SKI_F64 && sa_dtype != SKI_F32) return SKI_EINVAL;
-  const size_t need = ski_qr_ws_bytes(m, d + (with_rhs ? 1 : 0), sa_dtype);
+  if (sa_dtype != SKI_F64 && sa_dtype != SKI_F32 && sa_dtype != SKI_TF32) return SKI_EINVAL;
+  const size_t need = ski_qr_ws_bytes(m, d + (with_rhs ? 1 : 0), qr_storage(sa_dtype));
   if (ws_bytes < need || !ws) return SKI_ENOMEM;
   cudaStream_t st = ski_stream(stream);
   SkiArena ar{(char*)ws, ws_bytes, 0, false};
@@ -259,7 +303,8 @@ namespace {
 
 struct SolvePlan {
   int64_t n, d, m, ncols, ld_sa, ldq_sa;
-  int32_t qr_dt;
+  int32_t qr_dt;    // storage of the QR (F64 or F32)
+  int32_t qr_prec;  // its precision (F64, F32 or TF32)
   int nblk;
   bool csr;
   // persistent
@@ -282,6 +327,42 @@ struct SolvePlan {
   size_t csc_tmp_bytes;
 };
 
+// Mixed form: LSQR iterations allowed with an FP32 / TF32 preconditioner
+// before Steps 1-2 are redone in FP64 (an FP64-preconditioned solve of the
+// dense test set takes ~60).
+constexpr int64_t kMixedLsqrBudget = 150;
+// Largest max|r_ii| / min|r_ii| of an FP32 (TF32) factor kept as the
+// preconditioner: kappa(SA) u must stay well below 1 for R^{-1} to
+// precondition, with u ~ 2^-22 for the three-pass products (2^-11 for one).
+double mixed_ratio_limit(int32_t qr_dtype) { return qr_dtype == SKI_TF32 ? 0x1p10 : 0x1p22; }
+
+// Bytes of the phase region for the sketch / QR / trinv precisions of o.
+size_t region_need(const ski_matrix* A, const ski_opts* o) {
+  const int64_t d = A->d, m = o->m, ncols = d + 1, ld_sa = ski_round_up(ncols, 4);
+  const int32_t qdt = qr_storage(o->qr_dtype);
+  const size_t sa_bytes = ski_round_up((int64_t)(dtype_size(o->sketch_dtype) * m * ld_sa), 256);
+  const bool copy_q = dtype_size(o->sketch_dtype) != dtype_size(qdt) || o->sketch_dtype == SKI_BF16;
+  const size_t saq_bytes = copy_q ? ski_round_up((int64_t)(dtype_size(qdt) * m * ld_sa), 256) : 0;
+  const size_t stage = std::max(sketch_scratch_bytes(A, 1, o, nullptr), ski_qr_ws_bytes(m, ncols, qdt));
+  return std::max(sa_bytes + saq_bytes + stage, ski_trinv_ws_bytes(d, qdt));
+}
+
+// Points SA, SAq (the QR input), the stage scratch and the precisions at the
+// region for the sketch / QR precisions of o.
+void carve_region(const ski_matrix* A, const ski_opts* o, SolvePlan* P) {
+  const int64_t d = A->d, m = o->m, ncols = d + 1;
+  P->qr_dt = qr_storage(o->qr_dtype);
+  P->qr_prec = o->qr_dtype;
+  const size_t sa_bytes = ski_round_up((int64_t)(dtype_size(o->sketch_dtype) * m * P->ld_sa), 256);
+  const bool copy_q = dtype_size(o->sketch_dtype) != dtype_size(P->qr_dt) || o->sketch_dtype == SKI_BF16;
+  const size_t saq_bytes = copy_q ? ski_round_up((int64_t)(dtype_size(P->qr_dt) * m * P->ld_sa), 256) : 0;
+  P->SA = P->region;
+  P->SAq = copy_q ? (void*)(P->region + sa_bytes) : P->SA;
+  P->stage = P->region + sa_bytes + saq_bytes;
+  P->stage_bytes = std::max(sketch_scratch_bytes(A, 1, o, nullptr), ski_qr_ws_bytes(m, ncols, P->qr_dt));
+  (void)d;
+}
+
 size_t plan_solve(const ski_matrix* A, const ski_opts* o, char* base, size_t cap, SolvePlan* P) {
   SkiArena ar{base, cap, 0, base == nullptr};
   const int64_t n = A->n, d = A->d, m = o->m, ncols = d + 1;
@@ -290,7 +371,8 @@ size_t plan_solve(const ski_matrix* A, const ski_opts* o, char* base, size_t cap
   P->m = m;
   P->ncols = ncols;
   P->csr = A->kind == SKI_CSR;
-  P->qr_dt = o->qr_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
+  P->qr_dt = qr_storage(o->qr_dtype);
+  P->qr_prec = o->qr_dtype;
   P->ld_sa = ski_round_up(ncols, 4);
   P->nblk = ski_fused_ctas(n);
   P->R = ar.take<double>(d * d);
@@ -321,23 +403,18 @@ size_t plan_solve(const ski_matrix* A, const ski_opts* o, char* base, size_t cap
     P->rowidx = nullptr;
     P->cval = nullptr;
   }
-  // phase region: max(SA [+ QR copy] + max(sketch scratch, QR ws), trinv ws, csc tmp)
-  const size_t sa_bytes = ski_round_up((int64_t)(dtype_size(o->sketch_dtype) * m * P->ld_sa), 256);
-  const bool copy_q = dtype_size(o->sketch_dtype) != dtype_size(P->qr_dt) || o->sketch_dtype == SKI_BF16;
-  const size_t saq_bytes = copy_q ? ski_round_up((int64_t)(dtype_size(P->qr_dt) * m * P->ld_sa), 256) : 0;
-  const size_t sk = sketch_scratch_bytes(A, 1, o, nullptr);
-  const size_t qrw = ski_qr_ws_bytes(m, ncols, P->qr_dt);
-  const size_t stage = std::max(sk, qrw);
-  const size_t ph1 = sa_bytes + saq_bytes + stage;
-  const size_t tiw = ski_trinv_ws_bytes(d, P->qr_dt);
+  // phase region: max(SA [+ QR copy] + max(sketch scratch, QR ws), trinv ws, csc tmp),
+  // for the requested precisions and, when the QR is not FP64, for the FP64
+  // refactorisation the solve falls back to (see ski_solve)
+  ski_opts o64 = *o;
+  o64.sketch_dtype = SKI_F64;
+  o64.qr_dtype = SKI_F64;
   const size_t cscw = P->csr ? ski_csc_ws_bytes(n, d, A->nnz) : 0;
-  P->region_bytes = std::max(ph1, std::max(tiw, cscw));
+  P->region_bytes = std::max(region_need(A, o), cscw);
+  if (o->qr_dtype != SKI_F64) P->region_bytes = std::max(P->region_bytes, region_need(A, &o64));
   P->region = ar.take<char>(P->region_bytes);
   if (P->region) {
-    P->SA = P->region;
-    P->SAq = copy_q ? (void*)(P->region + sa_bytes) : P->SA;
-    P->stage = P->region + sa_bytes + saq_bytes;
-    P->stage_bytes = stage;
+    carve_region(A, o, P);
     P->csc_tmp = P->region;
     P->csc_tmp_bytes = cscw;
   }
@@ -471,7 +548,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   SKI_TRY(check_sketch_opts(A, o));
   if (!b || !x) return SKI_EINVAL;
   if (o->m < A->d || A->n < A->d) return SKI_EINVAL;
-  if (o->qr_dtype != SKI_F64 && o->qr_dtype != SKI_F32) return SKI_EINVAL;
+  if (o->qr_dtype != SKI_F64 && o->qr_dtype != SKI_F32 && o->qr_dtype != SKI_TF32) return SKI_EINVAL;
   if (A->kind == SKI_DENSE && A->d > SKI_DENSE_DMAX) return SKI_EINVAL;
   if (o->it_max < 0) return SKI_EINVAL;
   SolvePlan P;
@@ -493,45 +570,83 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   hs.amax_exp = 0;
 
   double qr_gemm_ms = 0.0;
-  SKI_CUDA_TRY(cudaEventRecord(ev.e[0], st));
-  // Step 1: sketch [SA | Sb]
-  SKI_TRY(sketch_run(A, b, o, P.SA, P.ld_sa, P.stage, P.stage_bytes, st, ev.e[5], ev.e[6]));
-  SKI_CUDA_TRY(cudaEventRecord(ev.e[1], st));
-  // Step 2: QR of [SA | Sb] in qr_dtype
-  if (P.SAq != P.SA) {
-    const int64_t cnt = P.m * P.ld_sa;
-    const unsigned g = (unsigned)ski_cdiv(cnt, 256);
-    if (o->sketch_dtype == SKI_BF16)
-      k_convert<__nv_bfloat16, float><<<g, 256, 0, st>>>(cnt, (const __nv_bfloat16*)P.SA, (float*)P.SAq);
-    else if (o->sketch_dtype == SKI_F32)
-      k_convert<float, double><<<g, 256, 0, st>>>(cnt, (const float*)P.SA, (double*)P.SAq);
-    else
-      k_convert<double, float><<<g, 256, 0, st>>>(cnt, (const double*)P.SA, (float*)P.SAq);
-    SKI_LAUNCH_CHECK();
-  }
-  {
-    SkiArena qar{P.stage, P.stage_bytes, 0, false};
-    SKI_TRY(ski_qr_run(P.m, d, 1, P.SAq, P.ld_sa, P.qr_dt, P.R, d, P.qtsb, qar, st, info ? &qr_gemm_ms : nullptr));
-  }
-  SKI_CUDA_TRY(cudaEventRecord(ev.e[2], st));
+  float ms_sk = 0.f, ms_qr = 0.f, ms_ti = 0.f, ms_pm = 0.f, ms_ga = 0.f;
   int32_t rank = 0;
-  bool nonfinite = false;
-  SKI_TRY(rank_from_diag(d, P.R, d, o->rcond, st, &rank, &nonfinite));
-  if (info) info->rank = rank;
-  if (nonfinite) {
-    if (info) info->status = SKI_ENONFINITE;
-    return SKI_ENONFINITE;
+  double rdiag_ratio = 0.0;
+  // Steps 1-2 and R^{-1} in the precisions of `of`
+  auto factor = [&](const ski_opts* of) -> ski_status {
+    carve_region(A, of, &P);
+    Events fe;
+    if (!fe.ok) return SKI_ECUDA;
+    SKI_CUDA_TRY(cudaEventRecord(fe.e[0], st));
+    // Step 1: sketch [SA | Sb]
+    SKI_TRY(sketch_run(A, b, of, P.SA, P.ld_sa, P.stage, P.stage_bytes, st, fe.e[5], fe.e[6]));
+    SKI_CUDA_TRY(cudaEventRecord(fe.e[1], st));
+    // Step 2: QR of [SA | Sb] in qr_dtype
+    if (P.SAq != P.SA) {
+      const int64_t cnt = P.m * P.ld_sa;
+      const unsigned g = (unsigned)ski_cdiv(cnt, 256);
+      if (of->sketch_dtype == SKI_BF16)
+        k_convert<__nv_bfloat16, float><<<g, 256, 0, st>>>(cnt, (const __nv_bfloat16*)P.SA, (float*)P.SAq);
+      else if (of->sketch_dtype == SKI_F32)
+        k_convert<float, double><<<g, 256, 0, st>>>(cnt, (const float*)P.SA, (double*)P.SAq);
+      else
+        k_convert<double, float><<<g, 256, 0, st>>>(cnt, (const double*)P.SA, (float*)P.SAq);
+      SKI_LAUNCH_CHECK();
+    }
+    double gm = 0.0;
+    {
+      SkiArena qar{P.stage, P.stage_bytes, 0, false};
+      SKI_TRY(ski_qr_run(P.m, d, 1, P.SAq, P.ld_sa, P.qr_prec, P.R, d, P.qtsb, qar, st, info ? &gm : nullptr));
+    }
+    qr_gemm_ms += gm;
+    SKI_CUDA_TRY(cudaEventRecord(fe.e[2], st));
+    bool nonfinite = false;
+    SKI_TRY(rank_from_diag(d, P.R, d, o->rcond, st, &rank, &nonfinite, &rdiag_ratio));
+    if (nonfinite) return SKI_ENONFINITE;
+    if (rank < d && o->perturb <= 0.0) return SKI_ESINGULAR;
+    // R^{-1} (explicit, and its transpose)
+    {
+      SkiArena tar{P.region, P.region_bytes, 0, false};
+      SKI_TRY(ski_trinv_run(d, P.R, d, P.M, P.Mt, d, P.qr_dt, rank < d ? o->perturb : 0.0, tar, st));
+    }
+    SKI_CUDA_TRY(cudaEventRecord(fe.e[3], st));
+    SKI_CUDA_TRY(cudaEventSynchronize(fe.e[3]));
+    ms_sk += fe.ms(0, 1);
+    ms_qr += fe.ms(1, 2);
+    ms_ti += fe.ms(2, 3);
+    ms_pm += fe.ms(5, 6);
+    ms_ga += fe.ms(6, 1);
+    return SKI_OK;
+  };
+  // The mixed form factors in FP32 (or TF32); R only has to precondition
+  // (Theorem 10), which fails once kappa(SA) times the factorisation's unit
+  // roundoff nears 1.  |r_11| ... |r_dd| bound kappa(R) from below: past the
+  // limit of mixed_ratio_limit() -- or when the FP32 factor fails the rank
+  // rule, or its LSQR run exhausts a budget (below) -- Steps 1-2 are redone
+  // in FP64 and the solve continues from there.
+  const bool mixed = o->qr_dtype != SKI_F64;
+  ski_opts o64 = *o;
+  o64.sketch_dtype = SKI_F64;
+  o64.qr_dtype = SKI_F64;
+  int32_t fell_back = 0;
+  SKI_CUDA_TRY(cudaEventRecord(ev.e[0], st));
+  ski_status fs = factor(o);
+  if (mixed && (fs == SKI_ESINGULAR || fs == SKI_ENONFINITE ||
+                (fs == SKI_OK && !(rdiag_ratio <= mixed_ratio_limit(o->qr_dtype))))) {
+    fell_back = 1;
+    fs = factor(&o64);
   }
-  if (rank < d && o->perturb <= 0.0) {
-    if (info) info->status = SKI_ESINGULAR;
-    return SKI_ESINGULAR;
+  if (info) {
+    info->rank = rank;
+    info->rdiag_ratio = rdiag_ratio;
+    info->qr_fallback = fell_back;
+  }
+  if (fs != SKI_OK) {
+    if (info) info->status = fs;
+    return fs;
   }
   if (R_out) SKI_CUDA_TRY(cudaMemcpyAsync(R_out, P.R, d * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  // R^{-1} (explicit, and its transpose)
-  {
-    SkiArena tar{P.region, P.region_bytes, 0, false};
-    SKI_TRY(ski_trinv_run(d, P.R, d, P.M, P.Mt, d, P.qr_dt, rank < d ? o->perturb : 0.0, tar, st));
-  }
   if (P.csr) {
     SkiArena car{P.csc_tmp, P.region_bytes, 0, false};
     SKI_TRY(ski_csc_build(A, P.colptr, P.rowidx, P.cval, car, st));
@@ -570,6 +685,8 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
       LsqrScalars init = hs;
       init.iters = 0;
       init.it_max = o->it_max - iters_total;
+      const bool budgeted = mixed && !fell_back && init.it_max > kMixedLsqrBudget;
+      if (budgeted) init.it_max = kMixedLsqrBudget;
       init.flag_a = 0;
       init.flag_b = 0;
       init.conv = 0;
@@ -604,6 +721,19 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
       metric = hs.rnorm2 > 0 ? hs.atr_norm / (anorm_f * sqrt(hs.rnorm2)) : 0.0;
       const bool lsqr_ok = hs.conv != 0;
       if (o->tol > 0.0 ? metric <= o->tol : lsqr_ok) break;
+      if (budgeted && !lsqr_ok) {
+        // the FP32 preconditioner is too weak: refactor in FP64, continue from x
+        fell_back = 2;
+        SKI_TRY(factor(&o64));
+        if (info) {
+          info->rank = rank;
+          info->rdiag_ratio = rdiag_ratio;
+          info->qr_fallback = fell_back;
+        }
+        if (R_out) SKI_CUDA_TRY(cudaMemcpyAsync(R_out, P.R, d * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        SKI_TRY(ski_copy_launch(d, x, P.xs, st));  // P.t = r, P.q = A^T r from the pass above
+        continue;
+      }
       if (iters_total >= o->it_max || restarts >= 8) {
         result = SKI_ENOCONV;
         break;
@@ -622,61 +752,25 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
     info->resid_norm = sqrt(hs.rnorm2);
     info->anorm_f = anorm_f;
     info->lsqr_test = lsqr_test;
-    info->ms_sketch = ev.ms(0, 1);
-    info->ms_qr = ev.ms(1, 2);
-    info->ms_trinv = ev.ms(2, 3);
+    info->ms_sketch = ms_sk;
+    info->ms_qr = ms_qr;
+    info->ms_trinv = ms_ti;
     info->ms_lsqr = ev.ms(3, 4);
     info->ms_total = ev.ms(0, 4);
-    info->ms_premix = ev.ms(5, 6);
-    info->ms_gather = ev.ms(6, 1);
+    info->ms_premix = ms_pm;
+    info->ms_gather = ms_ga;
+    info->qr_fallback = fell_back;
     info->ms_qr_gemm = (float)qr_gemm_ms;
     info->status = result;
   }
   return result;
 }
 
-// ------------------------------------------------------------ batched
-static void batched_opts(const ski_opts* o, const ski_matrix* A, int32_t i, ski_opts* oi) {
-  *oi = *o;
-  if (o->m <= 0) {
-    const double gamma = (o->m < 0 ? -(double)o->m : 2000.0) / 1000.0;
-    oi->m = (int64_t)ceil(gamma * (double)A->d);
-    if (oi->m < A->d) oi->m = A->d;
-  }
-  oi->seed = o->seed + (uint64_t)i;
-}
-
-extern "C" size_t ski_solve_batched_workspace_size(int32_t nprob, const ski_matrix* A, const ski_opts* o) {
-  if (nprob < 0 || (nprob > 0 && (!A || !o))) return 0;
-  size_t mx = 0;
-  for (int32_t i = 0; i < nprob; ++i) {
-    ski_opts oi;
-    batched_opts(o, &A[i], i, &oi);
-    mx = std::max(mx, ski_solve_workspace_size(&A[i], &oi));
-  }
-  return mx;
-}
-
-extern "C" ski_status ski_solve_batched(int32_t nprob, const ski_matrix* A, const double* const* b, const ski_opts* o,
-                                        double* const* x, double* const* R_out, ski_info* info, void* ws,
-                                        size_t ws_bytes, void* stream) {
-  if (nprob < 0 || (nprob > 0 && (!A || !b || !x || !o))) return SKI_EINVAL;
-  ski_status first = SKI_OK;
-  for (int32_t i = 0; i < nprob; ++i) {
-    ski_opts oi;
-    batched_opts(o, &A[i], i, &oi);
-    ski_status s = ski_solve(&A[i], b[i], &oi, x[i], R_out ? R_out[i] : nullptr, info ? &info[i] : nullptr, ws,
-                             ws_bytes, stream);
-    if (s != SKI_OK && first == SKI_OK) first = s;
-    if (s == SKI_ECUDA) return s;
-  }
-  return first;
-}
-
 // ------------------------------------------------------------ adjoint
 namespace {
 struct AdjPlan {
-  double *M, *Mt, *t, *al, *h, *r, *p, *z, *zz, *q, *lam, *part, *part_tt;
+  double *M, *Mt, *t, *rres, *h, *r, *p, *z, *zz, *q, *lam, *part, *part_tt;
+  float2* A2;
   LsqrScalars* sc;
   char* tw;
   size_t tw_bytes;
@@ -689,7 +783,7 @@ size_t plan_adjoint(const ski_matrix* A, char* base, size_t cap, AdjPlan* P) {
   P->M = ar.take<double>(d * d);
   P->Mt = ar.take<double>(d * d);
   P->t = ar.take<double>(n);
-  P->al = ar.take<double>(n);
+  P->rres = ar.take<double>(n);
   P->h = ar.take<double>(d);
   P->r = ar.take<double>(d);
   P->p = ar.take<double>(d);
@@ -700,6 +794,7 @@ size_t plan_adjoint(const ski_matrix* A, char* base, size_t cap, AdjPlan* P) {
   P->part = ar.take<double>((int64_t)P->nblk * d);
   P->part_tt = ar.take<double>(P->nblk);
   P->sc = ar.take<LsqrScalars>(1);
+  P->A2 = ar.take<float2>(n * ski_a2_ld(d));
   P->tw_bytes = ski_trinv_ws_bytes(d, SKI_F64);
   P->tw = ar.take<char>(P->tw_bytes);
   return ar.off;
@@ -733,6 +828,10 @@ extern "C" size_t ski_solve_adjoint_workspace_size(const ski_matrix* A, const sk
   return plan_adjoint(A, nullptr, 0, &P);
 }
 
+// Backward pass (see include/skills.h).  The CG products W^T W p = M^T A^T A M p
+// use the double-float pass over the (hi, lo) copy of A, as the forward LSQR
+// does (the FP64 pipe cannot keep up with HBM, see lsqr_df.cu); the residual r,
+// db = A lambda and dA stay in FP64.
 extern "C" ski_status ski_solve_adjoint(const ski_matrix* A, const double* b, const double* x, const double* R,
                                         int64_t ldr, const double* g, double* dA, int64_t ld_da, double* db,
                                         const ski_opts* o, ski_info* info, void* ws, size_t ws_bytes, void* stream) {
@@ -754,37 +853,58 @@ extern "C" ski_status ski_solve_adjoint(const ski_matrix* A, const double* b, co
     SkiArena tar{P.tw, P.tw_bytes, 0, false};
     SKI_TRY(ski_trinv_run(d, R, ldr, P.M, P.Mt, d, SKI_F64, 0.0, tar, st));
   }
-  // h = R^{-T} g; CG on W^T W z = h
-  SKI_TRY(ski_trmv_launch(false, d, P.Mt, d, g, nullptr, P.h, nullptr, st));
   LsqrScalars hs;
   memset(&hs, 0, sizeof(hs));
   hs.it_max = o->it_max > 0 ? o->it_max : 1000;
   hs.cg_tol2 = o->tau_r * o->tau_r;
   SKI_CUDA_TRY(cudaMemcpyAsync(P.sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+  // r = b - A x in FP64, with the largest exponent of A for the (hi, lo) split
+  {
+    FusedArgs f = dense_pass(A, P, x, -1.0, b, 1.0, P.rres, nullptr);
+    f.maxexp = &P.sc->amax_exp;
+    SKI_TRY(ski_fused_launch(f, st));
+  }
+  SKI_CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  SKI_CUDA_TRY(cudaStreamSynchronize(st));
+  const int sA = hs.amax_exp > 0 ? hs.amax_exp - 1022 : 0;
+  SKI_TRY(ski_split_a_launch(n, d, A->val, A->ld, sA, P.A2, st));
+  // h = R^{-T} g; CG on W^T W z = h
+  SKI_TRY(ski_trmv_launch(false, d, P.Mt, d, g, nullptr, P.h, nullptr, st));
   SKI_TRY(ski_cg_launch(d, P.h, P.r, P.p, P.z, P.sc, 1, st));
+  DfArgs f{};
+  f.A2 = P.A2;
+  f.n = n;
+  f.d = d;
+  f.sA = sA;
+  f.z = P.zz;
+  f.u = nullptr;
+  f.cu = 0.0;
+  f.coef_from_scalars = 0;
+  f.t = P.t;
+  f.part = P.part;
+  f.part_tt = P.part_tt;
+  f.nblk = P.nblk;
+  f.sc = P.sc;
   int64_t polled = 0;
   for (;;) {
     for (int k = 0; k < 8; ++k) {
       SKI_TRY(ski_trmv_launch(true, d, P.M, d, P.p, nullptr, P.zz, P.sc, st));
-      SKI_TRY(ski_fused_launch(dense_pass(A, P, P.zz, 1.0, nullptr, 0.0, P.t, P.sc), st));
-      SKI_TRY(ski_reduce_launch(P.nblk, d, P.part, d, P.part_tt, nullptr, P.q, P.sc, 0, st));
+      SKI_TRY(ski_fused_df_launch(f, st));
+      SKI_TRY(ski_reduce_par_launch(P.nblk, d, P.part, P.part_tt, P.q, P.sc, st));
       SKI_TRY(ski_trmv_launch(false, d, P.Mt, d, P.q, nullptr, P.zz, P.sc, st));
       SKI_TRY(ski_cg_launch(d, P.zz, P.r, P.p, P.z, P.sc, 0, st));
     }
     SKI_CUDA_TRY(cudaMemcpyAsync(&hs, P.sc, sizeof(hs), cudaMemcpyDeviceToHost, st));
     SKI_CUDA_TRY(cudaStreamSynchronize(st));
     polled += 8;
-    if (hs.flag_a || polled > hs.it_max + 16) break;
+    if (hs.flag_a || hs.df_err || polled > hs.it_max + 16) break;
   }
-  // lambda = R^{-1} z; db = A lambda; r = b - A x; dA = r lambda^T - (A lambda) x^T
+  // lambda = R^{-1} z; db = A lambda; dA = r lambda^T - (A lambda) x^T
   SKI_TRY(ski_trmv_launch(true, d, P.M, d, P.z, nullptr, P.lam, nullptr, st));
   SKI_TRY(ski_fused_launch(dense_pass(A, P, P.lam, 1.0, nullptr, 0.0, db, nullptr), st));
-  if (dA) {
-    SKI_TRY(ski_fused_launch(dense_pass(A, P, x, -1.0, b, 1.0, P.t, nullptr), st));
-    SKI_TRY(ski_outer_launch(n, d, P.t, P.lam, db, x, dA, ld_da, st));
-  }
+  if (dA) SKI_TRY(ski_outer_launch(n, d, P.rres, P.lam, db, x, dA, ld_da, st));
   SKI_CUDA_TRY(cudaStreamSynchronize(st));
-  const ski_status res = hs.conv ? SKI_OK : SKI_ENOCONV;
+  const ski_status res = hs.df_err ? SKI_ETIMEOUT : (hs.conv ? SKI_OK : SKI_ENOCONV);
   if (info) {
     info->iters = hs.iters;
     info->status = res;

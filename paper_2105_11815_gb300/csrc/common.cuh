@@ -34,6 +34,22 @@ void ski_count_launch();
 
 static inline cudaStream_t ski_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// The dynamic shared-memory cap given to a kernel whose launch size varies:
+// the device's opt-in maximum less the kernel's static shared memory.  A cap
+// only permits, so one constant per kernel keeps concurrent host threads from
+// lowering it under each other's in-flight launches (a per-launch cap races).
+static inline int ski_smem_cap(const void* fn) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes a;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
+    cudaGetLastError();
+    return 48 * 1024;
+  }
+  return optin - (int)a.sharedSizeBytes;
+}
+
 static inline int64_t ski_cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 static inline int64_t ski_round_up(int64_t a, int64_t b) { return ski_cdiv(a, b) * b; }
 

@@ -3,6 +3,12 @@
 // memory, multiplied as TF32 by tcgen05.mma with the FP32 accumulator in
 // tensor memory, and stored (or subtracted) to a row-major C.
 //
+// Precision: one TF32 pass keeps 11 significant bits of each operand (unit
+// roundoff 2^-11).  The split form (SPLIT) writes each operand tile as
+// x = hi + lo with hi = x rounded to TF32 and lo = (x - hi) rounded to TF32,
+// and accumulates lo*hi + hi*lo + hi*hi (the lo*lo term, below 2^-22 |a||b|,
+// is dropped): about FP32 accuracy from three tensor-core passes.
+//
 // One CTA computes one BM x BN tile (BM = 128 rows = 128 TMEM lanes, BN up to
 // 256 TMEM columns), K in steps of BK = 32 FP32 (128 bytes, one 128-byte
 // swizzle row).  Four warps:
@@ -10,6 +16,8 @@
 //                    tiles into a STAGES-deep shared-memory ring (128B swizzle)
 //   warp 1           allocates TMEM; lane 0 issues 4 tcgen05.mma per stage
 //                    (K = 8 each) and commits each stage back to the producer
+//   warps 2, 3       (SPLIT only) split each landed stage into hi and lo
+//                    tiles in place, then release it to the MMA issuer
 //   warps 0..3       epilogue: tcgen05.ld of their 32 TMEM lanes, store to C
 // Every mbarrier wait is bounded: after kSpinLimit polls the CTA raises the
 // error flag, drains its outstanding copies (again bounded), frees its TMEM
@@ -30,6 +38,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -74,23 +85,45 @@ __host__ __device__ constexpr uint32_t tf32_idesc(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool SPLIT>
 struct TcSmem {
   float A[STAGES][BM * BK];  // 16 KB per stage
   float B[STAGES][BN * BK];  // BN * 128 bytes per stage
+  float Alo[SPLIT ? STAGES : 1][SPLIT ? BM * BK : 256];  // lo parts (SPLIT), same swizzled layout
+  float Blo[SPLIT ? STAGES : 1][SPLIT ? BN * BK : 256];
   float stage[4][32][33];     // epilogue staging, one 32 x 32 block per warp
-  uint64_t full[STAGES], empty[STAGES], done;
+  uint64_t full[STAGES], conv[STAGES], empty[STAGES], done;
   uint32_t tmem;
 };
 
+// x -> (hi, lo): hi = x rounded to TF32 (low 13 mantissa bits cleared after
+// rounding), lo = x - hi (exact) rounded to TF32.  In place for hi.
+__device__ __forceinline__ void tf32_split(float* hi_tile, float* lo_tile, int count, int t, int nt) {
+  float4* h4 = reinterpret_cast<float4*>(hi_tile);
+  float4* l4 = reinterpret_cast<float4*>(lo_tile);
+  for (int i = t; i < count / 4; i += nt) {
+    const float4 x = h4[i];
+    float xs[4] = {x.x, x.y, x.z, x.w}, hs[4], ls[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float h = __uint_as_float((__float_as_uint(xs[k]) + 0x1000u) & 0xFFFFE000u);
+      const float l = __fsub_rn(xs[k], h);
+      hs[k] = h;
+      ls[k] = __uint_as_float((__float_as_uint(l) + 0x1000u) & 0xFFFFE000u);
+    }
+    h4[i] = make_float4(hs[0], hs[1], hs[2], hs[3]);
+    l4[i] = make_float4(ls[0], ls[1], ls[2], ls[3]);
+  }
+}
+
 // mode 0: C[m * ldc + n] = D; mode 1: C[m * ldc + n] -= D; mode 2: C[n * ldc + m] = D.
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool SPLIT>
 __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
                                                       const __grid_constant__ CUtensorMap tb, int M, int N, int K,
                                                       int kchunk, float* __restrict__ C, int64_t ldc,
                                                       int64_t c_zstride, int mode, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  TcSmem<BN, STAGES>& sm = *reinterpret_cast<TcSmem<BN, STAGES>*>(
+  TcSmem<BN, STAGES, SPLIT>& sm = *reinterpret_cast<TcSmem<BN, STAGES, SPLIT>*>(
       (void*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
@@ -102,6 +135,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&sm.full[s]), 1);
+      mbar_init(smem_u32(&sm.conv[s]), 64);
       mbar_init(smem_u32(&sm.empty[s]), 1);
     }
     mbar_init(smem_u32(&sm.done), 1);
@@ -147,7 +181,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
     for (int kt = 0; kt < nk && ok; ++kt) {
       const int s = kt % STAGES;
       const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-      if (!mbar_wait(smem_u32(&sm.full[s]), ph, err)) {
+      if (!mbar_wait(smem_u32(SPLIT ? &sm.conv[s] : &sm.full[s]), ph, err)) {
         ok = false;
         break;
       }
@@ -157,7 +191,20 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
       for (int kk = 0; kk < BK / 8; ++kk) {
         const uint64_t ad = sw128_desc(abase + kk * 32);
         const uint64_t bd = sw128_desc(bbase + kk * 32);
-        const uint32_t acc = (kt | kk) ? 1u : 0u;
+        uint32_t acc = (kt | kk) ? 1u : 0u;
+        if (SPLIT) {
+          const uint64_t adl = sw128_desc(smem_u32(sm.Alo[s]) + kk * 32);
+          const uint64_t bdl = sw128_desc(smem_u32(sm.Blo[s]) + kk * 32);
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(adl), "l"(bd), "r"(idesc), "r"(acc));
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bdl), "r"(idesc), "r"(1u));
+          acc = 1u;
+        }
         asm volatile(
             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -170,6 +217,18 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(&sm.done))
                  : "memory");
+  } else if (SPLIT && warp >= 2) {
+    // split each landed stage into hi (in place) and lo tiles
+    const int ct = threadIdx.x - 64;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (!mbar_wait(smem_u32(&sm.full[s]), ph, err)) break;
+      tf32_split(sm.A[s], sm.Alo[s], BM * BK, ct, 64);
+      tf32_split(sm.B[s], sm.Blo[s], BN * BK, ct, 64);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&sm.conv[s]));
+    }
   }
   __syncwarp();
   // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31
@@ -251,15 +310,17 @@ using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// Resolved once per process (thread-safe static initialisation).
 EncodeTiled encoder() {
-  static EncodeTiled fn = nullptr;
-  if (!fn) {
+  static const EncodeTiled fn = []() -> EncodeTiled {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiled)p;
-  }
+      return (EncodeTiled)p;
+    cudaGetLastError();
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -277,19 +338,36 @@ bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, i
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool SPLIT>
 ski_status launch(const float* A, int64_t lda, const float* B, int64_t ldb, int M, int N, int K, float* C,
                   int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st) {
   CUtensorMap ta, tb;
   if (!make_map(&ta, A, M, K, lda, BM) || !make_map(&tb, B, N, K, ldb, BN)) return SKI_ECUDA;
-  const size_t smem = sizeof(TcSmem<BN, STAGES>) + 1024;
-  SKI_CUDA_TRY(
-      cudaFuncSetAttribute(k_gemm_tc<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = sizeof(TcSmem<BN, STAGES, SPLIT>) + 1024;
+  static_assert(sizeof(TcSmem<BN, STAGES, SPLIT>) + 1024 <= 227 * 1024, "shared memory");
+  SKI_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
   const int kchunk = (int)ski_round_up(ski_cdiv(K, splits), BK);
   dim3 grid((unsigned)ski_cdiv(M, BM), (unsigned)ski_cdiv(N, BN), (unsigned)splits);
-  k_gemm_tc<BN, STAGES><<<grid, NTHR, smem, st>>>(ta, tb, M, N, K, kchunk, C, ldc, c_zstride, mode, err);
+  k_gemm_tc<BN, STAGES, SPLIT><<<grid, NTHR, smem, st>>>(ta, tb, M, N, K, kchunk, C, ldc, c_zstride, mode, err);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
+}
+
+template <bool SPLIT>
+ski_status dispatch(const float* A, int64_t lda, const float* B, int64_t ldb, int M, int N, int K, float* C,
+                    int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st) {
+  // deep K (the V^T C products): 4-stage ring; K <= 64 (the rank-32 update):
+  // 2 stages, leaving room for two CTAs (and their TMEM) per SM.  The split
+  // form doubles the tiles, so its 256-wide tiles keep 2 stages.
+  const bool shallow = ski_cdiv(K, splits) <= 2 * BK;
+  if (N <= 32)
+    return shallow ? launch<32, 2, SPLIT>(A, lda, B, ldb, M, N, K, C, ldc, mode, splits, c_zstride, err, st)
+                   : launch<32, 4, SPLIT>(A, lda, B, ldb, M, N, K, C, ldc, mode, splits, c_zstride, err, st);
+  if (N <= 64) return launch<64, 4, SPLIT>(A, lda, B, ldb, M, N, K, C, ldc, mode, splits, c_zstride, err, st);
+  if (shallow || SPLIT)
+    return launch<256, 2, SPLIT>(A, lda, B, ldb, M, N, K, C, ldc, mode, splits, c_zstride, err, st);
+  return launch<256, SPLIT ? 2 : 4, SPLIT>(A, lda, B, ldb, M, N, K, C, ldc, mode, splits, c_zstride, err, st);
 }
 
 }  // namespace
@@ -300,31 +378,26 @@ ski_status launch(const float* A, int64_t lda, const float* B, int64_t ldb, int 
 // stores the transpose.  splits > 1 splits K, writing partials at
 // C + z * c_zstride (modes 0 and 2 only).
 ski_status ski_gemm_tf32(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
-                         float* C, int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st) {
+                         float* C, int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st,
+                         bool split3) {
   if (M <= 0 || N <= 0) return SKI_OK;
   if ((lda & 3) || (ldb & 3) || ((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return SKI_EINVAL;
   if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return SKI_EINVAL;
-  // deep K (the V^T C products): 4-stage ring; K <= 64 (the rank-32 update):
-  // 2 stages, leaving room for two CTAs (and their TMEM) per SM
-  const bool shallow = ski_cdiv(K, splits) <= 2 * BK;
-  if (N <= 32)
-    return shallow ? launch<32, 2>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st)
-                   : launch<32, 4>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
-  if (N <= 64)
-    return launch<64, 4>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
-  return shallow ? launch<256, 2>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st)
-                 : launch<256, 4>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
+  if (split3)
+    return dispatch<true>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
+  return dispatch<false>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
 }
 
 extern "C" ski_status ski_gemm_tc_f32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
-                                      int64_t ldb, float* C, int64_t ldc, int32_t subtract, void* ws,
+                                      int64_t ldb, float* C, int64_t ldc, int32_t subtract, int32_t passes, void* ws,
                                       size_t ws_bytes, void* stream) {
   if (M < 0 || N < 0 || K < 0 || !A || !B || !C || !ws || ws_bytes < sizeof(int)) return SKI_EINVAL;
+  if (passes != 1 && passes != 3) return SKI_EINVAL;
   if (lda < K || ldb < K || ldc < N) return SKI_EINVAL;
   cudaStream_t st = ski_stream(stream);
   int* err = (int*)ws;
   SKI_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
-  SKI_TRY(ski_gemm_tf32(A, lda, B, ldb, M, N, K, C, ldc, subtract ? 1 : 0, 1, 0, err, st));
+  SKI_TRY(ski_gemm_tf32(A, lda, B, ldb, M, N, K, C, ldc, subtract ? 1 : 0, 1, 0, err, st, passes == 3));
   int h = 0;
   SKI_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   SKI_CUDA_TRY(cudaStreamSynchronize(st));

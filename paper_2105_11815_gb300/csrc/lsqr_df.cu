@@ -528,6 +528,12 @@ __global__ void __launch_bounds__(256) k_reduce_par(int nblk, int64_t d, const d
         sc->rnorm2 = t;
       }
       sc->flag_b = sc->flag_a;
+      // snapshot of the rotation state for the next K1 (see LsqrScalars)
+      sc->r_alpha = sc->alpha;
+      sc->r_rhobar = sc->rhobar;
+      sc->r_phibar = sc->phibar;
+      sc->r_anorm2 = sc->anorm2;
+      sc->r_iters = sc->iters;
     }
   }
 }
@@ -602,7 +608,8 @@ __global__ void __launch_bounds__(256) k_trmv_upper_update(int64_t d, const doub
           sc->flag_b = done;
         }
       } else {
-        const double alpha_old = sc->alpha, rhobar = sc->rhobar, phibar_old = sc->phibar;
+        // old state from the K3 snapshot: CTA 0 overwrites sc->alpha etc. below
+        const double alpha_old = sc->r_alpha, rhobar = sc->r_rhobar, phibar_old = sc->r_phibar;
         const double rho = hypot(rhobar, beta);
         const double cs = rhobar / rho, sn = beta / rho;
         const double theta = sn * alpha;
@@ -610,9 +617,9 @@ __global__ void __launch_bounds__(256) k_trmv_upper_update(int64_t d, const doub
         const double phibar = sn * phibar_old;
         c1 = phi / rho;
         c2 = theta / rho;
-        const double anorm2 = sc->anorm2 + alpha_old * alpha_old + beta * beta;
+        const double anorm2 = sc->r_anorm2 + alpha_old * alpha_old + beta * beta;
         const double test = (anorm2 > 0.0 && phibar > 0.0) ? alpha * fabs(cs) / sqrt(anorm2) : 0.0;
-        const long long iters = sc->iters + 1;
+        const long long iters = sc->r_iters + 1;
         const bool conv = test <= sc->tau_r || alpha == 0.0 || beta == 0.0;
         done = (conv || iters >= sc->it_max) ? 1 : 0;
         if (blockIdx.x == 0) {
@@ -681,11 +688,10 @@ int64_t ski_a2_ld(int64_t d) { return ski_round_up(d, 2); }  // rows 16-byte ali
 // iteration against 0.68 for the TMA-staged and 0.75 for the row-per-warp
 // variants); SKI_LSQR_PASS = "rows" | "tma" selects another for measurements.
 static int lsqr_pass_choice() {
-  static int v = -1;
-  if (v < 0) {
+  static const int v = [] {
     const char* e = getenv("SKI_LSQR_PASS");
-    v = (e && e[0] == 't') ? 1 : (e && e[0] == 'r' && e[1] == 'o') ? 0 : 2;
-  }
+    return (e && e[0] == 't') ? 1 : (e && e[0] == 'r' && e[1] == 'o') ? 0 : 2;
+  }();
   return v;
 }
 static bool getenv_flag_df_rows() { return lsqr_pass_choice() == 0; }
@@ -702,7 +708,8 @@ ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
     if (sm <= 200 * 1024 && getenv_flag_df_rows()) {
 #define SKI_DFR_CASE(C)                                                                                  \
       if (cpt <= C) {                                                                                    \
-        SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df_rows<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+        SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df_rows<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                          ski_smem_cap((const void*)k_fused_df_rows<C>)));               \
         k_fused_df_rows<C><<<f.nblk, 512, sm, st>>>(f);                                                  \
         SKI_LAUNCH_CHECK();                                                                              \
         return SKI_OK;                                                                                   \
@@ -725,7 +732,7 @@ ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
         const size_t sm = (size_t)ns * R * rowb + ub;                                                 \
         if (sm <= budget) {                                                                           \
           SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df_tma<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                            (int)sm));                                                \
+                                            ski_smem_cap((const void*)k_fused_df_tma<C, R>)));        \
           k_fused_df_tma<C, R><<<f.nblk, 512, sm, st>>>(f, ns);                                       \
           SKI_LAUNCH_CHECK();                                                                         \
           return SKI_OK;                                                                              \
@@ -744,7 +751,7 @@ ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
   if (cpt <= C) {                                                                                \
     if (smem > 48 * 1024)                                                                        \
       SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                        (int)smem));                                             \
+                                        ski_smem_cap((const void*)k_fused_df<C, R>)));           \
     k_fused_df<C, R><<<f.nblk, 512, smem, st>>>(f);                                              \
     SKI_LAUNCH_CHECK();                                                                          \
     return SKI_OK;                                                                               \

@@ -15,6 +15,11 @@ struct LsqrScalars {
   int conv;
   int amax_exp;  // largest biased exponent field of A (from the first residual pass)
   int df_err;    // a staged copy of the LSQR pass timed out
+  // the rotation state as the LSQR step kernel (K1) reads it: a copy of
+  // alpha, rhobar, phibar, anorm2, iters taken by K3 before every K1, so that
+  // CTA 0 of K1 can write the new state while its other CTAs still read the old
+  double r_alpha, r_rhobar, r_phibar, r_anorm2;
+  long long r_iters;
 };
 
 struct FusedArgs {

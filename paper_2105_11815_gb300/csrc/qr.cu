@@ -460,34 +460,36 @@ QrBufs<T> qr_carve(SkiArena& ar, int64_t m, int64_t ncols) {
   return b;
 }
 
+// split3: the FP32 QR's products in three TF32 passes (about FP32 accuracy);
+// false: one TF32 pass (SKI_TF32).
 template <class T>
 ski_status gemm_w(int64_t nct, int64_t mr, const T* Ctr, int64_t ldt, const T* Vt, T* pc, int64_t ldz, int sc,
-                  int* err, cudaStream_t st);
+                  int* err, cudaStream_t st, bool split3);
 template <>
 ski_status gemm_w<float>(int64_t nct, int64_t mr, const float* Ctr, int64_t ldt, const float* Vt, float* pc,
-                         int64_t ldz, int sc, int* err, cudaStream_t st) {
+                         int64_t ldz, int sc, int* err, cudaStream_t st, bool split3) {
   // W^T(c, i) = sum_r Ct[c][r] Vt[i][r] on the tensor cores, stored as W[i][c]
-  return ski_gemm_tf32(Ctr, ldt, Vt, ldt, nct, NB, mr, pc, ldz, 2, sc, (int64_t)NB * ldz, err, st);
+  return ski_gemm_tf32(Ctr, ldt, Vt, ldt, nct, NB, mr, pc, ldz, 2, sc, (int64_t)NB * ldz, err, st, split3);
 }
 template <>
 ski_status gemm_w<double>(int64_t nct, int64_t mr, const double* Ctr, int64_t ldt, const double* Vt, double* pc,
-                          int64_t ldz, int sc, int* err, cudaStream_t st) {
+                          int64_t ldz, int sc, int* err, cudaStream_t st, bool) {
   (void)err;
   return ski_gemm_ex<double>(NB, nct, mr, 1.0, Vt, ldt, 1, Ctr, 1, ldt, 0.0, pc, ldz, sc, (int64_t)NB * ldz, st);
 }
 
 template <class T>
 ski_status gemm_update(int64_t nct, int64_t mr, const T* Bpt, const T* V, T* Ctr, int64_t ldt, int* err,
-                       cudaStream_t st);
+                       cudaStream_t st, bool split3);
 template <>
 ski_status gemm_update<float>(int64_t nct, int64_t mr, const float* Bpt, const float* V, float* Ctr, int64_t ldt,
-                              int* err, cudaStream_t st) {
+                              int* err, cudaStream_t st, bool split3) {
   // Ct[c][r] -= sum_i B'^T[c][i] V[r][i] on the tensor cores (K = 32)
-  return ski_gemm_tf32(Bpt, NB, V, NB, nct, mr, NB, Ctr, ldt, 1, 1, 0, err, st);
+  return ski_gemm_tf32(Bpt, NB, V, NB, nct, mr, NB, Ctr, ldt, 1, 1, 0, err, st, split3);
 }
 template <>
 ski_status gemm_update<double>(int64_t nct, int64_t mr, const double* Bpt, const double* V, double* Ctr, int64_t ldt,
-                               int* err, cudaStream_t st) {
+                               int* err, cudaStream_t st, bool) {
   (void)err;
   return ski_gemm<double>(nct, mr, NB, -1.0, Bpt, NB, 1, V, 1, NB, 1.0, Ctr, ldt, st);
 }
@@ -524,7 +526,7 @@ struct GemmTimer {
 
 template <class T>
 ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, double* R, int64_t ldr, double* qtsb,
-                   SkiArena& ar, cudaStream_t st, double* gemm_ms) {
+                   SkiArena& ar, cudaStream_t st, double* gemm_ms, bool split3) {
   GemmTimer timer(gemm_ms != nullptr);
   const int64_t ncols = d + (with_rhs ? 1 : 0);
   const QrWs q = qr_dims(m, ncols);
@@ -634,7 +636,9 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
       void* args[] = {&pa, &bf.partA, &bf.partB, &bf.gb, &lim};
       const size_t smem = (size_t)rows_per * (NB + 1) * sizeof(T);
       if (smem > 48 * 1024)
-        SKI_CUDA_TRY(cudaFuncSetAttribute(k_panel_coop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SKI_CUDA_TRY(
+            cudaFuncSetAttribute(k_panel_coop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 ski_smem_cap((const void*)k_panel_coop<T>)));
       SKI_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop<T>, dim3(ncta), dim3(32 * WARPS), args,
                                                smem, st));
       SKI_LAUNCH_CHECK();
@@ -661,7 +665,7 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
       sc = (int)std::max<int64_t>(1, std::min<int64_t>(q.splits_max, ski_cdiv(300, tiles)));
       sc = (int)std::min<int64_t>(sc, ski_cdiv(mr, 128));
       timer.mark(st);
-      SKI_TRY(gemm_w<T>(nct, mr, Ctr, ldt, bf.Vt, bf.pc, q.ldz, sc, bf.err, st));
+      SKI_TRY(gemm_w<T>(nct, mr, Ctr, ldt, bf.Vt, bf.pc, q.ldz, sc, bf.err, st, split3));
       timer.mark(st);
     }
     const int64_t zc = w + nct;
@@ -673,7 +677,7 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
       k_ttw<T><<<ski_cdiv(nct, 128), 128, 0, st>>>(w, nct, bf.Z, NB + q.ldz, bf.Tm, bf.Bpt);
       SKI_LAUNCH_CHECK();
       timer.mark(st);
-      SKI_TRY(gemm_update<T>(nct, mr, bf.Bpt, bf.V, Ctr, ldt, bf.err, st));
+      SKI_TRY(gemm_update<T>(nct, mr, bf.Bpt, bf.V, Ctr, ldt, bf.err, st, split3));
       timer.mark(st);
     }
   }
@@ -702,8 +706,10 @@ size_t ski_qr_ws_bytes(int64_t m, int64_t ncols, int32_t dtype) {
 
 ski_status ski_qr_run(int64_t m, int64_t d, int32_t with_rhs, void* SA, int64_t ld_sa, int32_t dtype, double* R,
                       int64_t ldr, double* qtsb, SkiArena& ar, cudaStream_t st, double* gemm_ms) {
-  if (dtype == SKI_F64) return qr_impl<double>(m, d, with_rhs, (double*)SA, ld_sa, R, ldr, qtsb, ar, st, gemm_ms);
-  if (dtype == SKI_F32) return qr_impl<float>(m, d, with_rhs, (float*)SA, ld_sa, R, ldr, qtsb, ar, st, gemm_ms);
+  if (dtype == SKI_F64)
+    return qr_impl<double>(m, d, with_rhs, (double*)SA, ld_sa, R, ldr, qtsb, ar, st, gemm_ms, false);
+  if (dtype == SKI_F32 || dtype == SKI_TF32)
+    return qr_impl<float>(m, d, with_rhs, (float*)SA, ld_sa, R, ldr, qtsb, ar, st, gemm_ms, dtype == SKI_F32);
   return SKI_EINVAL;
 }
 

@@ -275,6 +275,88 @@ __global__ void __launch_bounds__(128) k_sketch_dense_f32in(
   if (c1 < ncols) SA[i * ld_sa + c1] = SkiType<TOUT>::from((double)(s1 * scale));
 }
 
+// Gather of a narrow column slab (ncols <= 32 * CPT) of the premix output:
+// warp w of the CTA owns bucket blockIdx.x * 8 + w, lane l its columns
+// l + 32 k.  The slab of Y was written just before by the premix and is still
+// in L2, so rows are read with default caching.
+template <int CPT, class TOUT>
+__global__ void __launch_bounds__(256) k_sketch_slab_f64acc(
+    const double* __restrict__ Y, int64_t ldy, int64_t ncols, const int64_t* __restrict__ offsets,
+    const uint32_t* __restrict__ list, long long scale_c, int scale_e, TOUT* __restrict__ SA, int64_t ld_sa,
+    int64_t m) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= m) return;
+  const int64_t lo = offsets[i], hi = offsets[i + 1];
+  FxGather acc[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) acc[k].init();
+  int64_t e = lo;
+  for (; e + 4 <= hi; e += 4) {
+    uint32_t en[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) en[u] = __ldg(&list[e + u]);
+    double v[4][CPT];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const double* row = Y + (int64_t)(en[u] >> 1) * ldy;
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        const int64_t c = lane + 32 * k;
+        v[u][k] = c < ncols ? __ldg(&row[c]) : 0.0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) acc[k].add(v[u][k], en[u] & 1u);
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) acc[k].renorm();
+  }
+  for (; e < hi; ++e) {
+    const uint32_t en = __ldg(&list[e]);
+    const double* row = Y + (int64_t)(en >> 1) * ldy;
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      const int64_t c = lane + 32 * k;
+      acc[k].add(c < ncols ? __ldg(&row[c]) : 0.0, en & 1u);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int64_t c = lane + 32 * k;
+    if (c < ncols) SA[i * ld_sa + c] = SkiType<TOUT>::from(fxg_scaled(acc[k], scale_c, scale_e));
+  }
+}
+
+template <int CPT, class TOUT>
+__global__ void __launch_bounds__(256) k_sketch_slab_f32in(
+    const float* __restrict__ Y, int64_t ldy, int64_t ncols, const int64_t* __restrict__ offsets,
+    const uint32_t* __restrict__ list, float scale, TOUT* __restrict__ SA, int64_t ld_sa, int64_t m) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= m) return;
+  const int64_t lo = offsets[i], hi = offsets[i + 1];
+  float s[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) s[k] = 0.f;
+  for (int64_t e = lo; e < hi; ++e) {
+    const uint32_t en = __ldg(&list[e]);
+    const float* row = Y + (int64_t)(en >> 1) * ldy;
+    const float sg = (en & 1u) ? -1.f : 1.f;
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      const int64_t c = lane + 32 * k;
+      s[k] += c < ncols ? sg * __ldg(&row[c]) : 0.f;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int64_t c = lane + 32 * k;
+    if (c < ncols) SA[i * ld_sa + c] = SkiType<TOUT>::from((double)(s[k] * scale));
+  }
+}
+
 // ------------------------------------------------------------ CSR gather
 // Row i of SA for a CSR A: the bucket's rows are scattered into a
 // shared-memory accumulator over the column chunk [c0, c0 + chunk), then the
@@ -405,6 +487,46 @@ ski_status ski_gather_dense_f32in(const float* Y, int64_t ldy, int64_t ncols, co
   return SKI_OK;
 }
 
+ski_status ski_gather_slab(const void* Y, int32_t y_dtype, int64_t ldy, int64_t ncols, const SkiBuckets& bk,
+                           double scale, int32_t out_dtype, void* SA, int64_t ld_sa, cudaStream_t st) {
+  if (ncols < 1 || ncols > 128) return SKI_EINVAL;
+  const int cpt = (int)ski_cdiv(ncols, 32);
+  const unsigned grid = (unsigned)ski_cdiv(bk.m, 8);
+  if (y_dtype == SKI_F64) {
+    if (out_dtype != SKI_F64) return SKI_EINVAL;
+    long long c;
+    int e;
+    scale_fixed(scale, &c, &e);
+    const double* y = (const double*)Y;
+    double* sa = (double*)SA;
+    switch (cpt) {
+      case 1: k_sketch_slab_f64acc<1, double><<<grid, 256, 0, st>>>(y, ldy, ncols, bk.offsets, bk.list, c, e, sa, ld_sa, bk.m); break;
+      case 2: k_sketch_slab_f64acc<2, double><<<grid, 256, 0, st>>>(y, ldy, ncols, bk.offsets, bk.list, c, e, sa, ld_sa, bk.m); break;
+      case 3: k_sketch_slab_f64acc<3, double><<<grid, 256, 0, st>>>(y, ldy, ncols, bk.offsets, bk.list, c, e, sa, ld_sa, bk.m); break;
+      default: k_sketch_slab_f64acc<4, double><<<grid, 256, 0, st>>>(y, ldy, ncols, bk.offsets, bk.list, c, e, sa, ld_sa, bk.m); break;
+    }
+  } else {
+    const float* y = (const float*)Y;
+    const float sc = (float)scale;
+#define SKI_SLAB32(CP)                                                                                       \
+  if (out_dtype == SKI_F32)                                                                                  \
+    k_sketch_slab_f32in<CP, float><<<grid, 256, 0, st>>>(y, ldy, ncols, bk.offsets, bk.list, sc, (float*)SA, \
+                                                         ld_sa, bk.m);                                       \
+  else                                                                                                       \
+    k_sketch_slab_f32in<CP, __nv_bfloat16><<<grid, 256, 0, st>>>(y, ldy, ncols, bk.offsets, bk.list, sc,    \
+                                                                 (__nv_bfloat16*)SA, ld_sa, bk.m);
+    switch (cpt) {
+      case 1: SKI_SLAB32(1) break;
+      case 2: SKI_SLAB32(2) break;
+      case 3: SKI_SLAB32(3) break;
+      default: SKI_SLAB32(4) break;
+    }
+#undef SKI_SLAB32
+  }
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
 ski_status ski_gather_csr(const ski_matrix* A, const double* b, const SkiBuckets& bk, double scale,
                           int32_t out_dtype, void* SA, int64_t ld_sa, cudaStream_t st) {
   const int64_t ncols = A->d + (b != nullptr);
@@ -414,18 +536,20 @@ ski_status ski_gather_csr(const ski_matrix* A, const double* b, const SkiBuckets
   const int T = 256;
   if (out_dtype == SKI_F64) {
     if (smem > 48 * 1024)
-      SKI_CUDA_TRY(cudaFuncSetAttribute(k_sketch_csr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      SKI_CUDA_TRY(cudaFuncSetAttribute(k_sketch_csr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        ski_smem_cap((const void*)k_sketch_csr<double>)));
     k_sketch_csr<double><<<grid, T, smem, st>>>(A->rowptr, A->colidx, A->val, A->d, b, bk.offsets, bk.list,
                                                 scale, chunk, (double*)SA, ld_sa);
   } else if (out_dtype == SKI_F32) {
     if (smem > 48 * 1024)
-      SKI_CUDA_TRY(cudaFuncSetAttribute(k_sketch_csr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      SKI_CUDA_TRY(cudaFuncSetAttribute(k_sketch_csr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        ski_smem_cap((const void*)k_sketch_csr<float>)));
     k_sketch_csr<float><<<grid, T, smem, st>>>(A->rowptr, A->colidx, A->val, A->d, b, bk.offsets, bk.list,
                                                scale, chunk, (float*)SA, ld_sa);
   } else {
     if (smem > 48 * 1024)
       SKI_CUDA_TRY(cudaFuncSetAttribute(k_sketch_csr<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
+                                        ski_smem_cap((const void*)k_sketch_csr<__nv_bfloat16>)));
     k_sketch_csr<__nv_bfloat16><<<grid, T, smem, st>>>(A->rowptr, A->colidx, A->val, A->d, b, bk.offsets,
                                                        bk.list, scale, chunk, (__nv_bfloat16*)SA, ld_sa);
   }

@@ -25,6 +25,10 @@ ski_status ski_gather_dense(const double* A, int64_t lda, int64_t nrows, int64_t
                             cudaStream_t st);
 ski_status ski_gather_dense_f32in(const float* Y, int64_t ldy, int64_t ncols, const SkiBuckets& bk,
                                   double scale, int32_t out_dtype, void* SA, int64_t ld_sa, cudaStream_t st);
+// Gather of a column slab (ncols <= 128) of the premix output Y (FP64 or
+// FP32 per y_dtype) into the same columns of SA: one warp per bucket.
+ski_status ski_gather_slab(const void* Y, int32_t y_dtype, int64_t ldy, int64_t ncols, const SkiBuckets& bk,
+                           double scale, int32_t out_dtype, void* SA, int64_t ld_sa, cudaStream_t st);
 ski_status ski_gather_csr(const ski_matrix* A, const double* b, const SkiBuckets& bk, double scale,
                           int32_t out_dtype, void* SA, int64_t ld_sa, cudaStream_t st);
 
@@ -33,6 +37,25 @@ ski_status ski_gather_csr(const ski_matrix* A, const double* b, const SkiBuckets
 // matrix of order n_pad = 2^L; the remaining factor (1 or 2^-1/2) is
 // returned in *residual_scale for the caller to fold into the sketch scale.
 size_t ski_premix_ws_bytes(int64_t n, int64_t ncols, int64_t n_pad, int32_t dtype);
+// Buffers and pass plan of a premix over at most ncols_max columns at a time
+// (D drawn once); ski_premix_cols then transforms any column range of A (A and
+// Y offset by the caller), so a wide A can be premixed slab by slab through
+// the same L2-sized buffers.
+struct SkiPremixPlan {
+  int64_t n, n_pad, ldq;
+  int32_t dtype;
+  int L, P, yshift;
+  int nbs[8];
+  double residual_scale;
+  int8_t* D;
+  int* nonfinite;
+  void *Qa, *Qb;
+  int16_t *Xa, *Xb;
+};
+ski_status ski_premix_plan(int64_t n, int64_t ncols_max, int64_t n_pad, int32_t dtype, uint64_t seed, SkiArena& ar,
+                           cudaStream_t st, SkiPremixPlan* plan);
+ski_status ski_premix_cols(const SkiPremixPlan& plan, const double* A, int64_t lda, int64_t d, const double* b,
+                           void* Y, int64_t ldy, cudaStream_t st);
 ski_status ski_premix_run(const double* A, int64_t lda, int64_t n, int64_t d, const double* b, uint64_t seed,
                           int64_t n_pad, int32_t dtype, void* Y, int64_t ldy, SkiArena& ar, cudaStream_t st,
                           double* residual_scale);
@@ -47,7 +70,8 @@ ski_status ski_barrier_selftest(long long spin_limit, void* ws, cudaStream_t st)
 
 // ---- gemm_tc.cu: D = A B^T on the TF32 tensor cores (see there for modes)
 ski_status ski_gemm_tf32(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
-                         float* C, int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st);
+                         float* C, int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st,
+                         bool split3);
 
 // ---- trinv.cu
 size_t ski_trinv_ws_bytes(int64_t d, int32_t dtype);

@@ -15,6 +15,10 @@
 // i.e. exact integer adds with headroom for the nb levels of growth -- on
 // GB300 the FP64 pipe (2 adds/clk/SM) could not keep up with HBM here.
 // FP32: plain FP32 butterflies.
+#include <stdlib.h>
+
+#include <algorithm>
+
 #include "common.cuh"
 #include "hash.cuh"
 #include "sketch_impl.cuh"
@@ -169,6 +173,152 @@ __global__ void __launch_bounds__(CT << GB, (GB >= 4 && RB <= 4) ? 2 : 1) k_wht_
   if (OUT == 0 && g == 0) out.X[tile * out.ldx + col] = (int16_t)X;
 }
 
+// Persistent form of k_wht_fx: each CTA walks the linear tile indices
+// u = blockIdx.x, + gridDim.x, ... (row tile u / nct, column tile u % nct)
+// and issues the global loads of its next tile into registers before it
+// transforms the current one, so a tile's loads are in flight during the
+// previous tile's butterflies and stores (the one-tile-per-CTA kernel leaves
+// HBM idle during those phases).  Same arithmetic and results as k_wht_fx.
+template <int RB, int IN>
+struct WhtRaw {
+  long long v[1 << RB];
+  int xs[IN == 1 ? (1 << RB) : 1];
+};
+
+template <int RB, int GB, int IN>
+__device__ __forceinline__ void wht_load(int64_t u, int64_t nct, int lo, int64_t ncols, const FxIn& in,
+                                         WhtRaw<RB, IN>& r) {
+  constexpr int R = 1 << RB, NB = RB + GB;
+  const int c = threadIdx.x & (CT - 1), g = threadIdx.x / CT;
+  const int64_t base = tile_base(u / nct, lo, NB);
+  const int64_t col = (u % nct) * CT + c;
+  const bool cok = col < ncols;
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int64_t row = base + ((int64_t)(g + (t << GB)) << lo);
+    if (IN == 0) {
+      long long bits = 0;
+      if (cok && row < in.n) {
+        bits = __double_as_longlong(col < in.d ? in.A[row * in.lda + col] : in.b[row]);
+        if (in.D[row] < 0) bits ^= (1ll << 63);
+      }
+      r.v[t] = bits;
+    } else {
+      long long v = 0;
+      int xs = -32768;
+      if (cok && row < in.nvalid) {
+        v = in.Q[row * in.ldq + col];
+        xs = in.X[tile_of_row(row, in.lo_p, in.nb_p) * in.ldx + col];
+      }
+      r.v[t] = v;
+      r.xs[IN == 1 ? t : 0] = xs;
+    }
+  }
+}
+
+template <int RB, int GB, int IN, int OUT>
+__global__ void __launch_bounds__(CT << GB, 1) k_wht_fx_pipe(int lo, int64_t n_pad, int64_t ncols, int64_t nct,
+                                                             int64_t ntotal, FxIn in, FxOut out) {
+  constexpr int R = 1 << RB, G = 1 << GB, NB = RB + GB;
+  extern __shared__ long long sq[];  // [R*G][CT]
+  __shared__ int sx[G][CT];
+  const int c = threadIdx.x & (CT - 1), g = threadIdx.x / CT;
+  int64_t u = blockIdx.x;
+  if (u >= ntotal) return;
+  WhtRaw<RB, IN> cur;
+  wht_load<RB, GB, IN>(u, nct, lo, ncols, in, cur);
+  bool bad = false;
+  for (; u < ntotal; u += gridDim.x) {
+    WhtRaw<RB, IN> nxt;
+    const int64_t un = u + gridDim.x;
+    if (un < ntotal) wht_load<RB, GB, IN>(un, nct, lo, ncols, in, nxt);
+    const int64_t tile = u / nct;
+    const int64_t base = tile_base(tile, lo, NB);
+    const int64_t col = (u % nct) * CT + c;
+    const bool cok = col < ncols;
+    long long q[R];
+    int emax = -100000;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      q[t] = cur.v[t];
+      if (IN == 0) {
+        const int e = (int)((q[t] >> 52) & 0x7FF);
+        bad |= (e == 0x7FF);
+        emax = max(emax, e ? e : 1);
+      } else {
+        if (q[t] == 0) cur.xs[t] = -32768;
+        emax = max(emax, cur.xs[IN == 1 ? t : 0]);
+      }
+    }
+    sx[g][c] = emax;
+    __syncthreads();
+    int E = sx[0][c];
+#pragma unroll
+    for (int gg = 1; gg < G; ++gg) E = max(E, sx[gg][c]);
+    int X;
+    if (IN == 0) {
+      constexpr int LIFT = 9 - NB;
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const unsigned long long bits = (unsigned long long)q[t];
+        const int e = (int)((bits >> 52) & 0x7FF);
+        const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+        const int sh = E - (e ? e : 1);
+        const unsigned long long mq = sh > 63 ? 0ull : ((M << LIFT) >> sh);
+        q[t] = (bits >> 63) ? -(long long)mq : (long long)mq;
+      }
+      X = E - 1075 - LIFT;
+    } else {
+      if (E == -32768) E = 0;
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const int sh = E - cur.xs[IN == 1 ? t : 0] + NB;
+        q[t] = (q[t] == 0 || sh > 63) ? 0 : (q[t] >> sh);
+      }
+      X = E + NB;
+    }
+#pragma unroll
+    for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        if (!(t & h)) {
+          const long long a = q[t], b = q[t + h];
+          q[t] = a + b;
+          q[t + h] = a - b;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < R; ++t) sq[(g + (t << GB)) * CT + c] = q[t];
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < R; ++t) q[t] = sq[((g << RB) + t) * CT + c];
+#pragma unroll
+    for (int h = 1; h < G; h <<= 1) {
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        if (!(t & h)) {
+          const long long a = q[t], b = q[t + h];
+          q[t] = a + b;
+          q[t + h] = a - b;
+        }
+      }
+    }
+    if (cok) {
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const int64_t row = base + ((int64_t)((g << RB) + t) << lo);
+        if (row >= n_pad) continue;
+        if (OUT == 0) out.Q[row * out.ldq + col] = q[t];
+        else out.Y[row * out.ldy + col] = fx_to_double(q[t], X - out.yshift + 1075 + FX_LIFT, 0);
+      }
+      if (OUT == 0 && g == 0) out.X[tile * out.ldx + col] = (int16_t)X;
+    }
+    cur = nxt;
+  }
+  if (bad && out.nonfinite) atomicOr(out.nonfinite, 1);
+}
+
 template <class TOUT>
 struct F32Out {
   float* Q;
@@ -262,6 +412,34 @@ ski_status launch_fx(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& i
   dim3 grid((unsigned)ntiles, (unsigned)ski_cdiv(ncols, CT));
   const size_t smem = (size_t)(1 << nb) * CT * sizeof(long long);
   const int threads = CT << GB;
+  // persistent, register-prefetching form (16 rows per thread at most), chosen
+  // by SKI_WHT_PIPE=1: at 50000 x 4000 it measured 4.1 ms for both passes
+  // against 3.2 ms for one tile per CTA at two CTAs per SM, so it is not the
+  // default.  The first pass skips the row tiles wholly in the zero padding.
+  static const bool use_pipe = [] {
+    const char* e = getenv("SKI_WHT_PIPE");
+    return e && e[0] == '1';
+  }();
+  const int64_t nct = ski_cdiv(ncols, CT);
+  const int64_t nrt = (IN == 0 && OUT == 0 && lo == 0) ? ski_cdiv(in.n, 1ll << nb) : ntiles;
+  const int64_t ntotal = nrt * nct;
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SKI_ECUDA;
+  const unsigned pgrid = (unsigned)std::min<int64_t>(ntotal, sms);
+#define SKI_FXP_CASE(rb, gb)                                                                     \
+  if (RB == rb && GB == gb) {                                                                    \
+    auto kfn = k_wht_fx_pipe<rb, gb, IN, OUT>;                                                   \
+    if (smem > 48 * 1024)                                                                        \
+      SKI_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    if (ntotal > 0) kfn<<<pgrid, threads, smem, st>>>(lo, n_pad, ncols, nct, ntotal, in, out);  \
+    SKI_LAUNCH_CHECK();                                                                          \
+    return SKI_OK;                                                                               \
+  }
+  if (use_pipe) {
+    SKI_FXP_CASE(3, 3) SKI_FXP_CASE(4, 3) SKI_FXP_CASE(4, 4)
+  }
+#undef SKI_FXP_CASE
 #define SKI_FX_CASE(rb, gb)                                                                      \
   if (RB == rb && GB == gb) {                                                                    \
     auto kfn = k_wht_fx<rb, gb, IN, OUT>;                                                        \
@@ -319,41 +497,58 @@ size_t ski_premix_ws_bytes(int64_t n, int64_t ncols, int64_t n_pad, int32_t dtyp
   return ar.off;
 }
 
-ski_status ski_premix_run(const double* A, int64_t lda, int64_t n, int64_t d, const double* b, uint64_t seed,
-                          int64_t n_pad, int32_t dtype, void* Y, int64_t ldy, SkiArena& ar, cudaStream_t st,
-                          double* residual_scale) {
-  const int64_t ncols = d + (b != nullptr);
-  const int64_t ldq = ski_round_up(ncols, CT);
-  int8_t* D = ar.take<int8_t>(n);
-  int* nonfinite = ar.take<int>(1);
-  const int L = ilog2(n_pad);
-  int nbs[8], P;
-  plan_passes(L, nbs, &P);
-  SKI_TRY(ski_premix_signs(seed, n, D, st));
-  *residual_scale = (L & 1) ? 0.70710678118654752440 : 1.0;
-  const int yshift = L / 2;
-  FxIn in{};
-  in.A = A; in.lda = lda; in.n = n; in.d = d; in.b = b; in.D = D;
+ski_status ski_premix_plan(int64_t n, int64_t ncols_max, int64_t n_pad, int32_t dtype, uint64_t seed, SkiArena& ar,
+                           cudaStream_t st, SkiPremixPlan* pp) {
+  SkiPremixPlan& P = *pp;
+  P.n = n;
+  P.n_pad = n_pad;
+  P.dtype = dtype;
+  P.ldq = ski_round_up(ncols_max, CT);
+  P.D = ar.take<int8_t>(n);
+  P.nonfinite = ar.take<int>(1);
+  P.L = ilog2(n_pad);
+  plan_passes(P.L, P.nbs, &P.P);
+  P.residual_scale = (P.L & 1) ? 0.70710678118654752440 : 1.0;
+  P.yshift = P.L / 2;
   if (dtype == SKI_F64) {
-    long long* Qa = ar.take<long long>(n_pad * ldq);
-    long long* Qb = ar.take<long long>(n_pad * ldq);
-    int16_t* Xa = ar.take<int16_t>(n_pad * ldq);
-    int16_t* Xb = ar.take<int16_t>(n_pad * ldq);
-    if (!ar.ok() || !Xb) return SKI_ENOMEM;
-    SKI_CUDA_TRY(cudaMemsetAsync(nonfinite, 0, sizeof(int), st));
+    P.Qa = ar.take<long long>(n_pad * P.ldq);
+    P.Qb = ar.take<long long>(n_pad * P.ldq);
+    P.Xa = ar.take<int16_t>(n_pad * P.ldq);
+    P.Xb = ar.take<int16_t>(n_pad * P.ldq);
+  } else {
+    P.Qa = ar.take<float>(n_pad * P.ldq);
+    P.Qb = ar.take<float>(n_pad * P.ldq);
+    P.Xa = P.Xb = nullptr;
+  }
+  if (!ar.ok() || !P.Qb) return SKI_ENOMEM;
+  SKI_TRY(ski_premix_signs(seed, n, P.D, st));
+  SKI_CUDA_TRY(cudaMemsetAsync(P.nonfinite, 0, sizeof(int), st));
+  return SKI_OK;
+}
+
+ski_status ski_premix_cols(const SkiPremixPlan& P, const double* A, int64_t lda, int64_t d, const double* b, void* Y,
+                           int64_t ldy, cudaStream_t st) {
+  const int64_t ncols = d + (b != nullptr);
+  if (ncols > P.ldq) return SKI_EINVAL;
+  const int64_t n = P.n, n_pad = P.n_pad, ldq = P.ldq;
+  FxIn in{};
+  in.A = A; in.lda = lda; in.n = n; in.d = d; in.b = b; in.D = P.D;
+  if (P.dtype == SKI_F64) {
+    long long* Qa = (long long*)P.Qa;
+    long long* Qb = (long long*)P.Qb;
     int lo = 0;
     int64_t nvalid = n;
     long long* Qin = nullptr;
     int16_t* Xin = nullptr;
     int lo_p = 0, nb_p = 0;
-    for (int p = 0; p < P; ++p) {
-      const int nb = nbs[p];
-      const bool last = p == P - 1;
+    for (int p = 0; p < P.P; ++p) {
+      const int nb = P.nbs[p];
+      const bool last = p == P.P - 1;
       long long* Qo = (p & 1) ? Qb : Qa;
-      int16_t* Xo = (p & 1) ? Xb : Xa;
+      int16_t* Xo = (p & 1) ? P.Xb : P.Xa;
       FxOut out{};
       out.Q = Qo; out.X = Xo; out.ldq = ldq; out.ldx = ldq; out.Y = (double*)Y; out.ldy = ldy;
-      out.yshift = yshift; out.nonfinite = nonfinite;
+      out.yshift = P.yshift; out.nonfinite = P.nonfinite;
       FxIn cur = in;
       cur.Q = Qin; cur.X = Xin; cur.ldq = ldq; cur.ldx = ldq; cur.nvalid = nvalid; cur.lo_p = lo_p; cur.nb_p = nb_p;
       ski_status s;
@@ -366,21 +561,20 @@ ski_status ski_premix_run(const double* A, int64_t lda, int64_t n, int64_t d, co
       lo += nb;
     }
   } else {
-    float* Qa = ar.take<float>(n_pad * ldq);
-    float* Qb = ar.take<float>(n_pad * ldq);
-    if (!ar.ok() || !Qb) return SKI_ENOMEM;
+    float* Qa = (float*)P.Qa;
+    float* Qb = (float*)P.Qb;
     int lo = 0;
     int64_t nvalid = n;
     const float* Qin = nullptr;
-    const float yscale = ldexpf(1.0f, -yshift);
-    for (int p = 0; p < P; ++p) {
-      const int nb = nbs[p];
-      const bool last = p == P - 1;
+    const float yscale = ldexpf(1.0f, -P.yshift);
+    for (int p = 0; p < P.P; ++p) {
+      const int nb = P.nbs[p];
+      const bool last = p == P.P - 1;
       float* Qo = (p & 1) ? Qb : Qa;
       FxIn cur = in;
       cur.nvalid = nvalid;
       ski_status s;
-      if (dtype == SKI_F32) {
+      if (P.dtype == SKI_F32) {
         F32Out<float> out{Qo, ldq, (float*)Y, ldy, yscale};
         if (p == 0) s = last ? launch_f32<0, 1, float>(nb, lo, n_pad, ncols, cur, Qin, ldq, out, st)
                              : launch_f32<0, 0, float>(nb, lo, n_pad, ncols, cur, Qin, ldq, out, st);
@@ -401,4 +595,13 @@ ski_status ski_premix_run(const double* A, int64_t lda, int64_t n, int64_t d, co
     }
   }
   return SKI_OK;
+}
+
+ski_status ski_premix_run(const double* A, int64_t lda, int64_t n, int64_t d, const double* b, uint64_t seed,
+                          int64_t n_pad, int32_t dtype, void* Y, int64_t ldy, SkiArena& ar, cudaStream_t st,
+                          double* residual_scale) {
+  SkiPremixPlan P;
+  SKI_TRY(ski_premix_plan(n, d + (b != nullptr), n_pad, dtype, seed, ar, st, &P));
+  *residual_scale = P.residual_scale;
+  return ski_premix_cols(P, A, lda, d, b, Y, ldy, st);
 }

@@ -107,3 +107,51 @@ def ragged_batch(count, seed, n_lo=2000, n_hi=60000, d_lo=64, d_hi=1024, ratio=4
         n = int(g.integers(max(n_lo, ratio * d), n_hi + 1))
         out.append((n, d))
     return out
+
+
+# ---- device-side generators for the full-size measurement workloads --------
+# Same distributions as above, drawn with torch's seeded generator on the GPU
+# (numpy would take minutes at these sizes).  Used by the benchmark only; the
+# parity tests use the numpy generators.
+
+def gaussian_torch(n, d, seed, device):
+    """A n x d i.i.d. N(0,1) (FP64, on `device`) and b = ones."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    A = torch.randn(n, d, generator=g, device=device, dtype=torch.float64)
+    return A, torch.ones(n, dtype=torch.float64, device=device)
+
+
+def usv_torch(n, d, kappa, seed, device):
+    """A = U diag(sigma) V^T with Haar U (n x d), V (d x d) (QR of a Gaussian,
+    diag(R) made positive), sigma_i = kappa^{-(i-1)/(d-1)}; b = ones."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+
+    def haar_t(rows, cols):
+        Z = torch.randn(rows, cols, generator=g, device=device, dtype=torch.float64)
+        Q, R = torch.linalg.qr(Z)
+        del Z
+        Q *= torch.sign(torch.diagonal(R))[None, :]
+        return Q
+
+    U = haar_t(n, d)
+    V = haar_t(d, d)
+    sig = kappa ** (-torch.arange(d, dtype=torch.float64, device=device) / max(d - 1, 1))
+    U *= sig[None, :]
+    A = U @ V.T
+    del U
+    return A, torch.ones(n, dtype=torch.float64, device=device)
+
+
+def ragged_batch_torch(count, seed, device, **kw):
+    """The ragged batch of `ragged_batch` with A_i, b_i i.i.d. N(0,1) on `device`."""
+    import torch
+    shapes = ragged_batch(count, seed, **kw)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    As = [torch.randn(n, d, generator=g, device=device, dtype=torch.float64) for n, d in shapes]
+    bs = [torch.randn(n, generator=g, device=device, dtype=torch.float64) for n, _ in shapes]
+    return shapes, As, bs

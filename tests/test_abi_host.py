@@ -82,10 +82,16 @@ def test_workspace_queries_are_consistent(lib):
     sk = L.ski_sketch_workspace_size(ctypes.byref(A), 1, ctypes.byref(o))
     so = L.ski_solve_workspace_size(ctypes.byref(A), ctypes.byref(o))
     assert 0 < sk < so
-    # premix intermediates: two int64 planes of n_pad x 4032 plus the FP64 output
+    # full-width premix: two int64 planes of n_pad x 4032 plus the FP64 output
     assert sk >= 3 * 65536 * 4001 * 8
+    # in column slabs of 64: the same planes 64 columns wide
+    slab = lib.ski_opts_default(m=8000, s=2, premix=1, n_pad=65536, premix_slab=64)
+    sks = L.ski_sketch_workspace_size(ctypes.byref(A), 1, ctypes.byref(slab))
+    assert 3 * 65536 * 64 * 8 <= sks < 3 * 65536 * 65 * 8 + 8 * 65536 * 2 + (64 << 20)
     o32 = lib.ski_opts_default(m=8000, s=2, premix=1, n_pad=65536, sketch_dtype=lib.SKI_F32, qr_dtype=lib.SKI_F32)
-    assert L.ski_sketch_workspace_size(ctypes.byref(A), 1, ctypes.byref(o32)) < sk
+    assert L.ski_sketch_workspace_size(ctypes.byref(A), 1, ctypes.byref(o32)) > 0
+    bad = lib.ski_opts_default(m=8000, s=2, premix=1, n_pad=65536, premix_slab=-1)
+    assert L.ski_sketch_workspace_size(ctypes.byref(A), 1, ctypes.byref(bad)) == 0
 
 
 def test_missing_library_fails_loudly(monkeypatch):
@@ -94,3 +100,27 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(pkg, "lib_path", "/nonexistent/libskills.so")
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         pkg.lib()
+
+
+def test_batched_workspace_scales_with_streams_and_rejects_negative(lib):
+    pkg = lib
+    mats = [pkg.ski_matrix(kind=0, n=1000 + 10 * i, d=20 + i, ld=20 + i, val=ctypes.c_void_p(4096))
+            for i in range(5)]
+    one = pkg.ski_opts_default(m=-2000, streams=1)
+    four = pkg.ski_opts_default(m=-2000, streams=4)
+    auto = pkg.ski_opts_default(m=-2000)
+    w1 = pkg.ski_solve_batched_workspace_size(mats, one)
+    assert w1 > 0 and w1 % 256 == 0
+    assert pkg.ski_solve_batched_workspace_size(mats, four) == 4 * w1
+    assert pkg.ski_solve_batched_workspace_size(mats, auto) == 5 * w1   # min(nprob, 8)
+    a1 = pkg.ski_solve_adjoint_batched_workspace_size(mats, one)
+    assert a1 > 0 and pkg.ski_solve_adjoint_batched_workspace_size(mats, four) == 4 * a1
+    bad = pkg.ski_opts_default(m=-2000, streams=-1)
+    arr = (pkg.ski_matrix * 5)(*mats)
+    ptrs = (ctypes.c_void_p * 5)(*([4096] * 5))
+    st = pkg.lib().ski_solve_batched(5, arr, ptrs, ctypes.byref(bad), ptrs, None, None, ctypes.c_void_p(4096),
+                                     1 << 40, None)
+    assert st == 1  # SKI_EINVAL
+    st = pkg.lib().ski_solve_adjoint_batched(5, arr, ptrs, ptrs, ptrs, ptrs, None, ptrs, ctypes.byref(bad), None,
+                                             ctypes.c_void_p(4096), 1 << 40, None)
+    assert st == 1  # SKI_EINVAL

@@ -130,6 +130,22 @@ def test_hrht_sketch_fp64(s):
     assert rel_fro(got, want) <= 1e-12
 
 
+@pytest.mark.parametrize("d,slab,with_b", [(150, 32, True), (150, 64, True), (150, 96, False), (150, 128, True),
+                                           (128, 32, True), (31, 32, True), (200, 0, True)])
+def test_hrht_sketch_column_slabs(d, slab, with_b):
+    # premix and hash gather run slab by slab over the columns; the last slab
+    # may be ragged or hold only b
+    torch, pkg = cuda()
+    A, b = workloads.dense_high_coherence(3000, d, seed=d + slab)
+    bb = b if with_b else None
+    got = _sketch(torch, pkg, A, bb, m=300, s=2, seed=5, premix=1, n_pad=4096, premix_slab=slab)
+    want = owht.hrht_sketch(5, 2, 300, A, bb, 4096)
+    assert rel_fro(got, want) <= 1e-12
+    got32 = _sketch(torch, pkg, A, bb, m=300, s=2, seed=5, premix=1, n_pad=4096, premix_slab=slab,
+                    sketch_dtype=pkg.SKI_F32)
+    assert rel_fro(got32, want) <= 1e-5
+
+
 def test_hrht_sketch_full_size_sampled_columns():
     # The dense test-set shape: n = 50000, d = 4000, n_pad = 65536, s = 2, m = 2d.
     # Checked on sampled columns: column c of S_h H D A is S_h H D A[:, c].
@@ -148,7 +164,7 @@ def _signfix(R):
 
 
 @pytest.mark.parametrize("m,d,dt", [(512, 256, 0), (1000, 100, 0), (64, 64, 0), (300, 1, 0), (777, 45, 0),
-                                    (2000, 300, 1)])
+                                    (2000, 300, 1), (2000, 300, 3), (3000, 1000, 1)])
 def test_precondition_qr(m, d, dt):
     torch, pkg = cuda()
     g = np.random.default_rng(m + d)
@@ -160,15 +176,36 @@ def test_precondition_qr(m, d, dt):
     rank = pkg.ski_precondition(m, d, 1, SA, d + 1, dt, R, d, qtsb)
     Ro, C = oqr.householder_qr(B, ncols=d)
     Rg = R.cpu().numpy()
-    # FP64: 1e-12.  FP32 storage with TF32 (10-bit mantissa, truncating)
-    # tensor-core trailing updates: the unit roundoff 2^-10 ~ 1e-3 times a
-    # small growth factor over the panels bounds the relative error at 1e-2.
-    tol = 1e-12 if dt == 0 else 1e-2
+    # FP64: 1e-12.  SKI_TF32, one tensor-core pass (10-bit mantissa): the unit
+    # roundoff 2^-10 ~ 1e-3 times a small growth factor over the panels bounds
+    # the relative error at 1e-2.  SKI_F32, three passes: FP32 storage and
+    # ~2^-21 products, Householder backward error ~ sqrt(d) u per panel -> 2e-5.
+    tol = {0: 1e-12, 1: 2e-5, 3: 1e-2}[dt]
     assert rank == d
     assert rel_fro(_signfix(Rg), _signfix(Ro)) <= tol
     sg = np.sign(np.diag(Rg)) * np.sign(np.diag(Ro))
-    assert rel_fro(sg * qtsb.cpu().numpy(), C[:, 0]) <= (tol * 10 if dt == 0 else 3e-2)
+    assert rel_fro(sg * qtsb.cpu().numpy(), C[:, 0]) <= (tol * 10 if dt == 0 else 3 * tol)
     assert np.allclose(np.tril(Rg, -1), 0)
+
+
+def test_fp32_qr_preconditions_ill_conditioned_sketch():
+    # R only has to precondition (Theorem 10): kappa(SA R^-1) stays near 1 for
+    # the three-pass FP32 QR at kappa(SA) = 1e5, where one TF32 pass does not.
+    torch, pkg = cuda()
+    g = np.random.default_rng(41)
+    m, d = 2000, 200
+    U = np.linalg.qr(g.standard_normal((m, d)))[0]
+    V = np.linalg.qr(g.standard_normal((d, d)))[0]
+    B = (U * (1e5 ** -(np.arange(d) / (d - 1)))) @ V.T
+    conds = {}
+    for dt in (1, 3):
+        SA = to_dev(torch, B).to(torch.float32).contiguous()
+        R = torch.empty(d, d, dtype=torch.float64, device="cuda")
+        pkg.ski_precondition(m, d, 0, SA, d, dt, R, d, None, want_rank=False)
+        W = np.linalg.solve(R.cpu().numpy().T, B.T).T
+        conds[dt] = np.linalg.cond(W)
+    assert conds[1] < 1.5, conds
+    assert conds[3] > 2 * conds[1], conds
 
 
 @pytest.mark.parametrize("d,dt", [(1, 0), (31, 0), (64, 0), (257, 0), (1000, 0), (500, 1)])
@@ -212,3 +249,35 @@ def test_tensor_core_gemm_tf32(M, N, K, sub):
     # FP32 accumulation of K products: error <= K * 2^-24 * sum |a||b|
     bound = K * 2.0 ** -23 * (np.abs(_tf32(A)) @ np.abs(_tf32(B)).T) + 1e-6
     assert np.all(np.abs(Cd.cpu().numpy() - want) <= bound)
+
+
+@pytest.mark.parametrize("M,N,K,sub", [(128, 32, 32, 0), (200, 300, 100, 0), (257, 64, 1000, 1), (5, 7, 3, 0),
+                                       (1000, 256, 32, 1), (300, 32, 4000, 0)])
+def test_tensor_core_gemm_split_tf32(M, N, K, sub):
+    # three TF32 passes: lo*hi + hi*lo + hi*hi against the exact FP64 product
+    torch, pkg = cuda()
+    g = np.random.default_rng(M * N + K)
+    A = g.standard_normal((M, K)).astype(np.float32)
+    B = g.standard_normal((N, K)).astype(np.float32)
+    C0 = g.standard_normal((M, N)).astype(np.float32)
+    lda = ldb = (K + 3) // 4 * 4
+    Ad = torch.zeros(M, lda, dtype=torch.float32, device="cuda")
+    Bd = torch.zeros(N, ldb, dtype=torch.float32, device="cuda")
+    Ad[:, :K] = torch.from_numpy(A).cuda()
+    Bd[:, :K] = torch.from_numpy(B).cuda()
+    Cd = torch.from_numpy(C0).cuda()
+    pkg.ski_gemm_tc_f32(M, N, K, Ad, lda, Bd, ldb, Cd, N, subtract=bool(sub), passes=3)
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    D = A64 @ B64.T
+    want = C0.astype(np.float64) - D if sub else D
+    absprod = np.abs(A64) @ np.abs(B64).T
+    # per product <= 3 * 2^-22 |a||b| (dropped lo*lo, lo rounded); FP32 sums of
+    # K terms <= K * 2^-24 sum |a||b|; the C0 update adds one FP32 rounding
+    bound = (3 * 2.0 ** -22 + K * 2.0 ** -24) * absprod + 2.0 ** -23 * np.abs(want) + 1e-6
+    err = np.abs(Cd.cpu().numpy() - want)
+    assert np.all(err <= bound)
+    # and far below one TF32 pass on the same operands
+    C1 = torch.from_numpy(C0).cuda()
+    pkg.ski_gemm_tc_f32(M, N, K, Ad, lda, Bd, ldb, C1, N, subtract=bool(sub), passes=1)
+    err1 = np.abs(C1.cpu().numpy() - want)
+    assert np.median(err) * 10 < np.median(err1)

@@ -170,6 +170,101 @@ def test_batched_matches_single():
         xi = torch.empty(A.shape[1], dtype=torch.float64, device="cuda")
         pkg.ski_solve(pkg.dense_matrix(At[i]), bt[i], oi, xi)
         assert torch.equal(xi, xs[i])
+    # results do not depend on the number of problems in flight
+    for w in (1, 3, 6):
+        ow = copy.copy(o)
+        ow.streams = w
+        xw = [torch.empty(A.shape[1], dtype=torch.float64, device="cuda") for A in As]
+        iw = pkg.ski_solve_batched([pkg.dense_matrix(a) for a in At], bt, ow, xw)
+        for i in range(len(As)):
+            assert iw[i].status == 0 and iw[i].iters == infos[i].iters
+            assert torch.equal(xw[i], xs[i])
+
+
+def test_batched_concurrent_runs_are_identical():
+    # many problems in flight on few streams, repeated: every run must give the
+    # same bits (a cross-CTA race on the LSQR scalars once showed up only here)
+    torch, pkg = cuda()
+    shapes = workloads.ragged_batch(12, seed=19, n_lo=600, n_hi=4000, d_lo=8, d_hi=150)
+    At, bt = [], []
+    for i, (n, d) in enumerate(shapes):
+        A, b, _ = workloads.gaussian_lls(n, d, seed=400 + i)
+        At.append(to_dev(torch, A))
+        bt.append(to_dev(torch, b))
+    mats = [pkg.dense_matrix(a) for a in At]
+    ref = None
+    for rep in range(8):
+        o = pkg.ski_opts_default(m=-2000, s=1, seed=70, tol=1e-10, tau_r=1e-12, streams=(3 if rep % 2 else 5))
+        xs = [torch.empty(d, dtype=torch.float64, device="cuda") for _, d in shapes]
+        infos = pkg.ski_solve_batched(mats, bt, o, xs)
+        got = ([x.clone() for x in xs], [i.iters for i in infos])
+        if ref is None:
+            ref = got
+        assert got[1] == ref[1]
+        assert all(torch.equal(a, b) for a, b in zip(got[0], ref[0]))
+
+
+def test_batched_stream_ordering():
+    # the batch reads b written by work queued on the caller's stream just
+    # before, and the caller's stream sees x after the call
+    torch, pkg = cuda()
+    As, bs = [], []
+    for i in range(5):
+        A, b, _ = workloads.gaussian_lls(2000 + 300 * i, 40 + 10 * i, seed=300 + i)
+        As.append(A)
+        bs.append(b)
+    At = [to_dev(torch, A) for A in As]
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        bt = [torch.zeros(len(b), dtype=torch.float64, device="cuda") for b in bs]
+        torch.cuda._sleep(50_000_000)
+        for t, b in zip(bt, bs):
+            t.copy_(to_dev(torch, b), non_blocking=True)
+        o = pkg.ski_opts_default(m=-2000, s=1, seed=7, tol=1e-10, tau_r=1e-12, streams=4)
+        xs = [torch.empty(A.shape[1], dtype=torch.float64, device="cuda") for A in As]
+        infos = pkg.ski_solve_batched([pkg.dense_matrix(a) for a in At], bt, o, xs, stream=side)
+        ys = [x * 1.0 for x in xs]
+    side.synchronize()
+    for i, (A, b) in enumerate(zip(As, bs)):
+        assert infos[i].status == 0
+        _assert_solution(A, b, ys[i].cpu().numpy())
+
+
+def test_adjoint_batched_matches_single():
+    torch, pkg = cuda()
+    g = np.random.default_rng(17)
+    shapes = [(700, 20), (1500, 64), (512, 32), (2400, 90), (900, 8)]
+    At, bt, xs, Rs, gs = [], [], [], [], []
+    o = pkg.ski_opts_default(m=-2000, s=1, seed=3, tol=1e-10, tau_r=1e-13, streams=3)
+    for i, (n, d) in enumerate(shapes):
+        A = g.standard_normal((n, d))
+        b = g.standard_normal(n)
+        At.append(to_dev(torch, A))
+        bt.append(to_dev(torch, b))
+        xs.append(torch.empty(d, dtype=torch.float64, device="cuda"))
+        Rs.append(torch.empty(d, d, dtype=torch.float64, device="cuda"))
+        gs.append(to_dev(torch, g.standard_normal(d)))
+    mats = [pkg.dense_matrix(a) for a in At]
+    pkg.ski_solve_batched(mats, bt, o, xs, R_outs=Rs)
+    dAs = [torch.empty_like(a) for a in At]
+    dbs = [torch.empty_like(b) for b in bt]
+    infos = pkg.ski_solve_adjoint_batched(mats, bt, xs, Rs, gs, dAs, dbs, o)
+    for i, (n, d) in enumerate(shapes):
+        assert infos[i].status == 0
+        dA1 = torch.empty_like(At[i])
+        db1 = torch.empty_like(bt[i])
+        pkg.ski_solve_adjoint(mats[i], bt[i], xs[i], Rs[i], d, gs[i], dA1, d, db1, o)
+        assert torch.equal(dA1, dAs[i]) and torch.equal(db1, dbs[i])
+        A, b = At[i].cpu().numpy(), bt[i].cpu().numpy()
+        xr = np.linalg.lstsq(A, b, rcond=None)[0]
+        dA, db = oadj.lstsq_grad(A, b, xr, gs[i].cpu().numpy())
+        assert rel_fro(dAs[i].cpu().numpy(), dA) <= 1e-9
+        assert rel_fro(dbs[i].cpu().numpy(), db) <= 1e-9
+    # dA skipped
+    dbs2 = [torch.empty_like(b) for b in bt]
+    pkg.ski_solve_adjoint_batched(mats, bt, xs, Rs, gs, None, dbs2, o)
+    for i in range(len(shapes)):
+        assert torch.equal(dbs2[i], dbs[i])
 
 
 def test_adjoint_matches_closed_form_and_finite_differences():
@@ -198,3 +293,49 @@ def test_adjoint_matches_closed_form_and_finite_differences():
             fd = (lp - lm) / (2 * h)
             an = float((At.grad.cpu().numpy() * EA).sum() + bt.grad.cpu().numpy() @ eb)
             assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
+
+
+def test_lstsq_batched_autograd():
+    torch, pkg = cuda()
+    from paper_2105_11815_gb300.autograd import lstsq_batched
+    g = np.random.default_rng(23)
+    shapes = [(512, 32), (800, 16), (640, 48)]
+    As = [g.standard_normal(s) for s in shapes]
+    bs = [g.standard_normal(s[0]) for s in shapes]
+    cs = [g.standard_normal(s[1]) for s in shapes]
+    At = [to_dev(torch, A).requires_grad_(True) for A in As]
+    bt = [to_dev(torch, b).requires_grad_(True) for b in bs]
+    o = pkg.ski_opts_default(m=-2000, s=1, seed=11, tol=1e-10, tau_r=1e-12)
+    xs = lstsq_batched(At, bt, o)
+    L = sum((x * to_dev(torch, c)).sum() for x, c in zip(xs, cs))
+    L.backward()
+    for A, b, c, a_t, b_t in zip(As, bs, cs, At, bt):
+        xr = np.linalg.lstsq(A, b, rcond=None)[0]
+        dA, db = oadj.lstsq_grad(A, b, xr, c)
+        assert rel_fro(a_t.grad.cpu().numpy(), dA) <= 1e-9
+        assert rel_fro(b_t.grad.cpu().numpy(), db) <= 1e-9
+
+
+@pytest.mark.parametrize("kappa,qr,expect", [(1e3, 1, 0), (1e5, 3, 1), (1e9, 1, 1), (1e5, 1, 0)])
+def test_mixed_precision_fallback(kappa, qr, expect):
+    # the FP32 / TF32 factor is kept while kappa(SA) u stays small; past the
+    # diagonal-ratio limit Steps 1-2 are redone in FP64 -- either way the
+    # FP64 acceptance test holds
+    torch, pkg = cuda()
+    g = np.random.default_rng(int(np.log10(kappa)) + 10 * qr)
+    n, d = 4000, 200
+    A, _ = workloads.usv(n, d, kappa, seed=int(np.log10(kappa)))
+    # b = A x_true + e with e orthogonal to range(A): x = x_true stays O(1), so
+    # the FP64 metric's rounding floor u ||A|| ||x|| / ||r|| is far below 1e-10
+    Q = np.linalg.qr(A)[0]
+    e = g.standard_normal(n)
+    e -= Q @ (Q.T @ e)
+    b = A @ g.standard_normal(d) + e
+    At, bt = to_dev(torch, A), to_dev(torch, b)
+    o = pkg.ski_opts_default(m=400, s=1, seed=2, tol=1e-10, tau_r=1e-12, sketch_dtype=pkg.SKI_F32, qr_dtype=qr)
+    x = torch.empty(d, dtype=torch.float64, device="cuda")
+    info = pkg.ski_solve(pkg.dense_matrix(At), bt, o, x)
+    assert info.status == 0
+    # 1: the diagonal ratio triggered it; 2: the LSQR budget did
+    assert (info.qr_fallback > 0) == (expect > 0), (info.qr_fallback, info.rdiag_ratio, info.iters)
+    assert olsqr.residual_metric(A, b, x.cpu().numpy()) <= 1e-10
