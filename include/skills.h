@@ -104,10 +104,11 @@ typedef struct {
   float ms_premix, ms_gather;  /* inside ms_sketch: the H D premix and the hash gather */
   float ms_qr_gemm;            /* inside ms_qr: the trailing-update GEMMs, summed     */
   int32_t qr_fallback;         /* mixed form: 0 kept the FP32/TF32 factor; 1 redid     */
-                               /* Steps 1-2 in FP64 (ratio or rank), 2 after LSQR      */
-                               /* exhausted its budget with the FP32 preconditioner    */
+                               /* Steps 1-2 in FP64 (ratio or rank), 2 after its LSQR  */
+                               /* run exhausted, or was predicted to exceed, a budget  */
   int32_t pad_;
-  double rdiag_ratio;          /* max |r_ii| / min |r_ii| of the last factor           */
+  double rdiag_ratio;          /* max |r_ii| / min |r_ii| of the first factor (the     */
+                               /* requested precision; it decides the fallback)        */
 } ski_info;
 
 /* Defaults of Ski-LLS-dense (Section 6): m = 0 (caller must set), s = 1,

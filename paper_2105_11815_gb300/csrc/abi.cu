@@ -118,6 +118,12 @@ static int64_t premix_slab_cols(int64_t n_pad, int64_t ncols, int32_t pdt, int32
   return std::min<int64_t>(w, full);
 }
 
+// The FP64 premix over all columns at once leaves its output as int64 planes
+// with per-tile exponents, which the FP64 hash gather reads directly.
+static bool premix_q_path(int32_t pdt, int64_t ncols, int64_t w, const ski_opts* o) {
+  return pdt == SKI_F64 && o->sketch_dtype == SKI_F64 && w >= ncols && (w > 128 || o->premix_slab <= 0);
+}
+
 // Scratch layout: [bucket lists][premix Y slab][premix intermediates]
 static size_t sketch_scratch_bytes(const ski_matrix* A, int32_t with_b, const ski_opts* o, int64_t* ldy_out) {
   const int64_t ncols = A->d + (with_b ? 1 : 0);
@@ -128,7 +134,8 @@ static size_t sketch_scratch_bytes(const ski_matrix* A, int32_t with_b, const sk
   if (o->premix) {
     const int32_t pdt = o->sketch_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
     ldy = premix_slab_cols(rows, ncols, pdt, o->premix_slab);
-    ar.take<char>(dtype_size(pdt) * rows * ldy);
+    // the full-width FP64 premix hands its int64 planes to the gather: no Y
+    if (!premix_q_path(pdt, ncols, ldy, o)) ar.take<char>(dtype_size(pdt) * rows * ldy);
     ar.take<char>(ski_premix_ws_bytes(A->n, ldy, rows, pdt));
   }
   if (ldy_out) *ldy_out = ldy;
@@ -158,7 +165,8 @@ static ski_status sketch_run(const ski_matrix* A, const double* b, const ski_opt
   const int32_t pdt = o->sketch_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
   if (pdt == SKI_F64 && o->sketch_dtype != SKI_F64) return SKI_EINVAL;
   const int64_t w = premix_slab_cols(rows, ncols, pdt, o->premix_slab);
-  void* Y = ar.take<char>(dtype_size(pdt) * rows * w);
+  const bool qpath = premix_q_path(pdt, ncols, w, o);
+  void* Y = qpath ? nullptr : ar.take<char>(dtype_size(pdt) * rows * w);
   const size_t pwb = ski_premix_ws_bytes(A->n, w, rows, pdt);
   char* pws = ar.take<char>(pwb);
   if (!ar.ok() || !pws) return SKI_ENOMEM;
@@ -166,6 +174,14 @@ static ski_status sketch_run(const ski_matrix* A, const double* b, const ski_opt
   SkiPremixPlan plan;
   SKI_TRY(ski_premix_plan(A->n, w, rows, pdt, o->seed, par, st, &plan));
   const double scale = plan.residual_scale * inv_sqrt_s;
+  if (qpath) {
+    // all columns at once, FP64: premix into block-fixed-point planes, then
+    // the hash gather straight from them
+    SkiPremixQ yq;
+    SKI_TRY(ski_premix_cols_q(plan, A->val, A->ld, A->d, b, &yq, st));
+    if (e_pm) SKI_CUDA_TRY(cudaEventRecord(e_pm, st));
+    return ski_gather_q(yq, ncols, bk, scale, (double*)SA, ld_sa, st);
+  }
   if (w >= ncols && (w > 128 || o->premix_slab <= 0)) {
     // all columns at once: premix into Y, then the full-width hash gather
     SKI_TRY(ski_premix_cols(plan, A->val, A->ld, A->d, b, Y, w, st));
@@ -334,7 +350,19 @@ constexpr int64_t kMixedLsqrBudget = 150;
 // Largest max|r_ii| / min|r_ii| of an FP32 (TF32) factor kept as the
 // preconditioner: kappa(SA) u must stay well below 1 for R^{-1} to
 // precondition, with u ~ 2^-22 for the three-pass products (2^-11 for one).
-double mixed_ratio_limit(int32_t qr_dtype) { return qr_dtype == SKI_TF32 ? 0x1p10 : 0x1p22; }
+// The ratio underestimates kappa: at 200000 x 4000, kappa = 1e6 it was 5.9e4
+// (FP32 factor kept, 60 LSQR iterations), at kappa = 1e10 the FP32 factor's
+// ratio saturated at 3.2e6 (FP64: 3.7e8).
+double mixed_ratio_limit(int32_t qr_dtype) { return qr_dtype == SKI_TF32 ? 0x1p7 : 0x1p19; }
+// After >= 24 iterations, the Eq. TC-lsqr estimate extrapolated geometrically
+// (test_k ~ rho^k from test_0 = 1) predicts more than the budget: the FP32
+// preconditioner is too weak, so stop early instead of spending the budget.
+bool weak_preconditioner(double test, long long iters, double tau_r) {
+  if (iters < 24 || !(tau_r > 0.0) || !(tau_r < 1.0)) return false;
+  if (!(test < 1.0)) return true;
+  if (test <= tau_r) return false;
+  return (double)iters * log(tau_r) / log(test) > (double)kMixedLsqrBudget;
+}
 
 // Bytes of the phase region for the sketch / QR / trinv precisions of o.
 size_t region_need(const ski_matrix* A, const ski_opts* o) {
@@ -632,6 +660,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   int32_t fell_back = 0;
   SKI_CUDA_TRY(cudaEventRecord(ev.e[0], st));
   ski_status fs = factor(o);
+  const double ratio_first = rdiag_ratio;
   if (mixed && (fs == SKI_ESINGULAR || fs == SKI_ENONFINITE ||
                 (fs == SKI_OK && !(rdiag_ratio <= mixed_ratio_limit(o->qr_dtype))))) {
     fell_back = 1;
@@ -639,7 +668,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   }
   if (info) {
     info->rank = rank;
-    info->rdiag_ratio = rdiag_ratio;
+    info->rdiag_ratio = ratio_first;
     info->qr_fallback = fell_back;
   }
   if (fs != SKI_OK) {
@@ -702,6 +731,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
         SKI_TRY(read_scalars(P, &hs, st));
         if (hs.flag_a) break;
         if (polled > o->it_max + CHUNK) break;
+        if (budgeted && weak_preconditioner(hs.test, hs.iters, o->tau_r)) break;
       }
       iters_total += hs.iters;
       lsqr_test = hs.test;
@@ -727,7 +757,6 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
         SKI_TRY(factor(&o64));
         if (info) {
           info->rank = rank;
-          info->rdiag_ratio = rdiag_ratio;
           info->qr_fallback = fell_back;
         }
         if (R_out) SKI_CUDA_TRY(cudaMemcpyAsync(R_out, P.R, d * d * sizeof(double), cudaMemcpyDeviceToDevice, st));

@@ -275,6 +275,119 @@ __global__ void __launch_bounds__(128) k_sketch_dense_f32in(
   if (c1 < ncols) SA[i * ld_sa + c1] = SkiType<TOUT>::from((double)(s1 * scale));
 }
 
+// Exact sum of block-fixed-point addends q * 2^x (|q| < 2^62, x per addend)
+// with an adaptive block exponent, as FxGather but without an FP64 decode:
+// each addend gives up its 4 low bits for headroom, a larger x shifts the
+// running sum down once, and |S| >= 2^61 coarsens the block by 2^4.
+struct FxQ {
+  long long S;
+  int E;
+  __device__ __forceinline__ void init() { S = 0; E = -(1 << 30); }
+  __device__ __forceinline__ void add(long long q, int x, unsigned neg) {
+    if (q == 0) return;
+    q >>= 4;
+    x += 4;
+    if (x > E) {
+      const int sh = x - E;
+      S = sh > 62 ? (S < 0 ? -1 : 0) : (S >> sh);
+      E = x;
+    }
+    const int sh = E - x;
+    const long long v = sh > 62 ? (q < 0 ? -1 : 0) : (q >> sh);
+    S += neg ? -v : v;
+  }
+  __device__ __forceinline__ void renorm() {
+    if (S >= (1ll << 61) || S <= -(1ll << 61)) {
+      S >>= 4;
+      E += 4;
+    }
+  }
+};
+
+// scale * S * 2^(E - yshift) with scale = c * 2^(-62 - e)
+__device__ __forceinline__ double fxq_scaled(const FxQ& a, long long c, int e, int yshift) {
+  if (a.S == 0) return 0.0;
+  const long long Sp = (long long)(((__int128)a.S * (__int128)c) >> 62);
+  return fx_i64_to_double(Sp, a.E - yshift - e);
+}
+
+// Hash gather over the premix output in block-fixed-point form (SkiPremixQ):
+// the layout and work split of k_sketch_dense_f64acc (4 buckets per CTA, 4
+// columns per thread, bulk L2 prefetch of the next bucket's rows).
+__global__ void __launch_bounds__(128) k_sketch_q_f64acc(
+    const long long* __restrict__ Q, int64_t ldq, const int16_t* __restrict__ X, int64_t ldx, int lo, int nb,
+    int yshift, int64_t ncols, const int64_t* __restrict__ offsets, const uint32_t* __restrict__ list,
+    long long scale_c, int scale_e, double* __restrict__ SA, int64_t ld_sa, int64_t m) {
+  constexpr int CPT = 4, BPC = 4;
+  const int64_t cb = (int64_t)blockIdx.y * (CPT * 128) + threadIdx.x;
+  const int64_t cfirst = (int64_t)blockIdx.y * (CPT * 128);
+  const int64_t ccount = max((int64_t)0, min((int64_t)(CPT * 128), ncols - cfirst));
+  const int64_t i0 = (int64_t)blockIdx.x * BPC;
+  const int64_t lomask = (1ll << lo) - 1;
+  auto tile_of = [&](int64_t j) { return ((j >> (lo + nb)) << lo) | (j & lomask); };
+  auto prefetch = [&](int64_t i) {
+    if (i >= m || ccount == 0) return;
+    const int64_t lo_e = offsets[i], hi_e = offsets[i + 1];
+    for (int64_t e = lo_e + threadIdx.x / 8; e < hi_e; e += 16) {
+      const int64_t j = list[e] >> 1;
+      ski_l2_prefetch_range(Q + j * ldq + cfirst, (size_t)ccount * sizeof(long long), threadIdx.x & 7, 8);
+    }
+  };
+  prefetch(i0);
+  for (int bi = 0; bi < BPC; ++bi) {
+    const int64_t i = i0 + bi;
+    if (i >= m) break;
+    prefetch(i + 1);
+    const int64_t lo_e = offsets[i], hi_e = offsets[i + 1];
+    FxQ acc[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) acc[k].init();
+    int64_t e = lo_e;
+    for (; e + 4 <= hi_e; e += 4) {
+      uint32_t en[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) en[u] = __ldg(&list[e + u]);
+      long long v[4][CPT];
+      int x[4][CPT];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t j = en[u] >> 1;
+        const int64_t tj = tile_of(j);
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+          const int64_t c = cb + k * 128;
+          const bool ok = c < ncols;
+          v[u][k] = ok ? __ldcs(&Q[j * ldq + c]) : 0ll;
+          x[u][k] = ok ? (int)__ldg(&X[tj * ldx + c]) : 0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) acc[k].add(v[u][k], x[u][k], en[u] & 1u);
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) acc[k].renorm();
+    }
+    for (; e < hi_e; ++e) {
+      const uint32_t en = __ldg(&list[e]);
+      const int64_t j = en >> 1;
+      const int64_t tj = tile_of(j);
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        const int64_t c = cb + k * 128;
+        if (c < ncols) acc[k].add(__ldcs(&Q[j * ldq + c]), (int)__ldg(&X[tj * ldx + c]), en & 1u);
+      }
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) acc[k].renorm();
+    }
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      const int64_t c = cb + k * 128;
+      if (c < ncols) SA[i * ld_sa + c] = fxq_scaled(acc[k], scale_c, scale_e, yshift);
+    }
+  }
+}
+
 // Gather of a narrow column slab (ncols <= 32 * CPT) of the premix output:
 // warp w of the CTA owns bucket blockIdx.x * 8 + w, lane l its columns
 // l + 32 k.  The slab of Y was written just before by the premix and is still
@@ -483,6 +596,18 @@ ski_status ski_gather_dense_f32in(const float* Y, int64_t ldy, int64_t ncols, co
   else
     k_sketch_dense_f32in<__nv_bfloat16><<<grid, T, 0, st>>>(Y, ldy, ncols, bk.offsets, bk.list, (float)scale,
                                                             (__nv_bfloat16*)SA, ld_sa);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+ski_status ski_gather_q(const SkiPremixQ& y, int64_t ncols, const SkiBuckets& bk, double scale, double* SA,
+                        int64_t ld_sa, cudaStream_t st) {
+  long long c;
+  int e;
+  scale_fixed(scale, &c, &e);
+  dim3 grid((unsigned)ski_cdiv(bk.m, 4), (unsigned)ski_cdiv(ncols, 4 * 128));
+  k_sketch_q_f64acc<<<grid, 128, 0, st>>>(y.Q, y.ldq, y.X, y.ldx, y.lo, y.nb, y.yshift, ncols, bk.offsets, bk.list, c,
+                                           e, SA, ld_sa, bk.m);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }

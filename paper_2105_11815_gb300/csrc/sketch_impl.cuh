@@ -56,6 +56,20 @@ ski_status ski_premix_plan(int64_t n, int64_t ncols_max, int64_t n_pad, int32_t 
                            cudaStream_t st, SkiPremixPlan* plan);
 ski_status ski_premix_cols(const SkiPremixPlan& plan, const double* A, int64_t lda, int64_t d, const double* b,
                            void* Y, int64_t ldy, cudaStream_t st);
+// The FP64 premix output left in block-fixed-point form: row j, column c is
+// Q[j * ldq + c] * 2^(X[tile(j) * ldx + c] - yshift), with tile(j) the tile of
+// row j in the last pass (row bits [lo, lo + nb)).  Saves the last pass its
+// FP64 conversion and the hash gather its FP64 decode.
+struct SkiPremixQ {
+  const long long* Q;
+  const int16_t* X;
+  int64_t ldq, ldx;
+  int lo, nb, yshift;
+};
+ski_status ski_premix_cols_q(const SkiPremixPlan& plan, const double* A, int64_t lda, int64_t d, const double* b,
+                             SkiPremixQ* out, cudaStream_t st);
+ski_status ski_gather_q(const SkiPremixQ& y, int64_t ncols, const SkiBuckets& bk, double scale, double* SA,
+                        int64_t ld_sa, cudaStream_t st);
 ski_status ski_premix_run(const double* A, int64_t lda, int64_t n, int64_t d, const double* b, uint64_t seed,
                           int64_t n_pad, int32_t dtype, void* Y, int64_t ldy, SkiArena& ar, cudaStream_t st,
                           double* residual_scale);

@@ -58,16 +58,20 @@ struct FxOut {
   int* nonfinite;
 };
 
-template <int RB, int GB, int IN, int OUT>
-__global__ void __launch_bounds__(CT << GB, (GB >= 4 && RB <= 4) ? 2 : 1) k_wht_fx(int lo, int64_t n_pad, int64_t ncols, FxIn in, FxOut out) {
+// CW: columns per tile (32, or 16 for twice the CTAs per SM where the pass is
+// latency-bound).
+template <int RB, int GB, int IN, int OUT, int CW = CT>
+__global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4 : 2) : 1) k_wht_fx(int lo, int64_t n_pad, int64_t ncols, FxIn in, FxOut out, int colx) {
   constexpr int R = 1 << RB, G = 1 << GB, NB = RB + GB;
-  extern __shared__ long long sq[];            // [R*G][CT]
-  __shared__ int sx[G][CT];
-  const int c = threadIdx.x & (CT - 1), g = threadIdx.x / CT;
-  const int64_t tile = blockIdx.x;
+  extern __shared__ long long sq[];            // [R*G][CW]
+  __shared__ int sx[G][CW];
+  const int c = threadIdx.x & (CW - 1), g = threadIdx.x / CW;
+  // colx: column tiles along x, so that the CTAs resident together read
+  // neighbouring segments of the same rows (DRAM page locality)
+  const int64_t tile = colx ? blockIdx.y : blockIdx.x;
   const int64_t base = tile_base(tile, lo, NB);
   if (IN == 0 && OUT == 0 && lo == 0 && base >= in.n) return;  // whole tile in the zero padding
-  const int64_t col = (int64_t)blockIdx.y * CT + c;
+  const int64_t col = (int64_t)(colx ? blockIdx.x : blockIdx.y) * CW + c;
   const bool cok = col < ncols;
   long long q[R];
   int xsrc[IN == 1 ? R : 1];
@@ -143,10 +147,10 @@ __global__ void __launch_bounds__(CT << GB, (GB >= 4 && RB <= 4) ? 2 : 1) k_wht_
     }
   }
 #pragma unroll
-  for (int t = 0; t < R; ++t) sq[(g + (t << GB)) * CT + c] = q[t];
+  for (int t = 0; t < R; ++t) sq[(g + (t << GB)) * CW + c] = q[t];
   __syncthreads();
 #pragma unroll
-  for (int t = 0; t < R; ++t) q[t] = sq[((g << RB) + t) * CT + c];
+  for (int t = 0; t < R; ++t) q[t] = sq[((g << RB) + t) * CW + c];
   // GB levels in registers: row bits [0, GB)
 #pragma unroll
   for (int h = 1; h < G; h <<= 1) {
@@ -330,14 +334,14 @@ struct F32Out {
 
 template <int RB, int GB, int IN, int OUT, class TOUT>
 __global__ void __launch_bounds__(CT << GB) k_wht_f32(int lo, int64_t n_pad, int64_t ncols, FxIn in,
-                                                       const float* Qin, int64_t ldqin, F32Out<TOUT> out) {
+                                                       const float* Qin, int64_t ldqin, F32Out<TOUT> out, int colx) {
   constexpr int R = 1 << RB, G = 1 << GB, NB = RB + GB;
   extern __shared__ float sf[];
   const int c = threadIdx.x & (CT - 1), g = threadIdx.x / CT;
-  const int64_t tile = blockIdx.x;
+  const int64_t tile = colx ? blockIdx.y : blockIdx.x;
   const int64_t base = tile_base(tile, lo, NB);
   if (IN == 0 && OUT == 0 && lo == 0 && base >= in.n) return;
-  const int64_t col = (int64_t)blockIdx.y * CT + c;
+  const int64_t col = (int64_t)(colx ? blockIdx.x : blockIdx.y) * CT + c;
   const bool cok = col < ncols;
   float q[R];
 #pragma unroll
@@ -409,7 +413,9 @@ ski_status launch_fx(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& i
                      cudaStream_t st) {
   const int GB = nb / 2, RB = nb - GB;
   const int64_t ntiles = n_pad >> nb > 0 ? (n_pad >> nb) : 1;
-  dim3 grid((unsigned)ntiles, (unsigned)ski_cdiv(ncols, CT));
+  const int colx = ntiles <= 65535 ? 1 : 0;
+  dim3 grid = colx ? dim3((unsigned)ski_cdiv(ncols, CT), (unsigned)ntiles)
+                   : dim3((unsigned)ntiles, (unsigned)ski_cdiv(ncols, CT));
   const size_t smem = (size_t)(1 << nb) * CT * sizeof(long long);
   const int threads = CT << GB;
   // persistent, register-prefetching form (16 rows per thread at most), chosen
@@ -440,12 +446,25 @@ ski_status launch_fx(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& i
     SKI_FXP_CASE(3, 3) SKI_FXP_CASE(4, 3) SKI_FXP_CASE(4, 4)
   }
 #undef SKI_FXP_CASE
+  // the first pass (FP64 in) is latency-bound: 16-column tiles, four CTAs per SM
+  if (IN == 0 && RB == 4 && GB == 4 && lo == 0) {
+    constexpr int CW = 16;
+    auto kfn = k_wht_fx<4, 4, IN, OUT, CW>;
+    const size_t sm16 = (size_t)(1 << nb) * CW * sizeof(long long);
+    dim3 g16 = colx ? dim3((unsigned)ski_cdiv(ncols, CW), (unsigned)ntiles)
+                    : dim3((unsigned)ntiles, (unsigned)ski_cdiv(ncols, CW));
+    if (sm16 > 48 * 1024)
+      SKI_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm16));
+    kfn<<<g16, CW << 4, sm16, st>>>(lo, n_pad, ncols, in, out, colx);
+    SKI_LAUNCH_CHECK();
+    return SKI_OK;
+  }
 #define SKI_FX_CASE(rb, gb)                                                                      \
   if (RB == rb && GB == gb) {                                                                    \
     auto kfn = k_wht_fx<rb, gb, IN, OUT>;                                                        \
     if (smem > 48 * 1024)                                                                        \
       SKI_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    kfn<<<grid, threads, smem, st>>>(lo, n_pad, ncols, in, out);                                 \
+    kfn<<<grid, threads, smem, st>>>(lo, n_pad, ncols, in, out, colx);                           \
     SKI_LAUNCH_CHECK();                                                                          \
     return SKI_OK;                                                                               \
   }
@@ -460,7 +479,9 @@ ski_status launch_f32(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& 
                       int64_t ldqin, const F32Out<TOUT>& out, cudaStream_t st) {
   const int GB = nb / 2, RB = nb - GB;
   const int64_t ntiles = n_pad >> nb > 0 ? (n_pad >> nb) : 1;
-  dim3 grid((unsigned)ntiles, (unsigned)ski_cdiv(ncols, CT));
+  const int colx = ntiles <= 65535 ? 1 : 0;
+  dim3 grid = colx ? dim3((unsigned)ski_cdiv(ncols, CT), (unsigned)ntiles)
+                   : dim3((unsigned)ntiles, (unsigned)ski_cdiv(ncols, CT));
   const size_t smem = (size_t)(1 << nb) * CT * sizeof(float);
   const int threads = CT << GB;
 #define SKI_F32_CASE(rb, gb)                                                                     \
@@ -468,7 +489,7 @@ ski_status launch_f32(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& 
     auto kfn = k_wht_f32<rb, gb, IN, OUT, TOUT>;                                                 \
     if (smem > 48 * 1024)                                                                        \
       SKI_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    kfn<<<grid, threads, smem, st>>>(lo, n_pad, ncols, in, Qin, ldqin, out);                     \
+    kfn<<<grid, threads, smem, st>>>(lo, n_pad, ncols, in, Qin, ldqin, out, colx);               \
     SKI_LAUNCH_CHECK();                                                                          \
     return SKI_OK;                                                                               \
   }
@@ -526,6 +547,61 @@ ski_status ski_premix_plan(int64_t n, int64_t ncols_max, int64_t n_pad, int32_t 
   return SKI_OK;
 }
 
+namespace {
+// FP64 passes; qfinal: the last pass also writes block-fixed-point int64
+// values and per-(tile, column) exponents instead of FP64 Y, described in *qo.
+ski_status premix_fx_passes(const SkiPremixPlan& P, const FxIn& in, int64_t ncols, void* Y, int64_t ldy, bool qfinal,
+                            SkiPremixQ* qo, cudaStream_t st) {
+  const int64_t n = P.n, n_pad = P.n_pad, ldq = P.ldq;
+  long long* Qa = (long long*)P.Qa;
+  long long* Qb = (long long*)P.Qb;
+  int lo = 0;
+  int64_t nvalid = n;
+  long long* Qin = nullptr;
+  int16_t* Xin = nullptr;
+  int lo_p = 0, nb_p = 0;
+  for (int p = 0; p < P.P; ++p) {
+    const int nb = P.nbs[p];
+    const bool last = p == P.P - 1;
+    const bool to_y = last && !qfinal;
+    long long* Qo = (p & 1) ? Qb : Qa;
+    int16_t* Xo = (p & 1) ? P.Xb : P.Xa;
+    FxOut out{};
+    out.Q = Qo; out.X = Xo; out.ldq = ldq; out.ldx = ldq; out.Y = (double*)Y; out.ldy = ldy;
+    out.yshift = P.yshift; out.nonfinite = P.nonfinite;
+    FxIn cur = in;
+    cur.Q = Qin; cur.X = Xin; cur.ldq = ldq; cur.ldx = ldq; cur.nvalid = nvalid; cur.lo_p = lo_p; cur.nb_p = nb_p;
+    ski_status s;
+    if (p == 0) s = to_y ? launch_fx<0, 1>(nb, lo, n_pad, ncols, cur, out, st) : launch_fx<0, 0>(nb, lo, n_pad, ncols, cur, out, st);
+    else s = to_y ? launch_fx<1, 1>(nb, lo, n_pad, ncols, cur, out, st) : launch_fx<1, 0>(nb, lo, n_pad, ncols, cur, out, st);
+    if (s != SKI_OK) return s;
+    if (last && qfinal) {
+      qo->Q = Qo;
+      qo->X = Xo;
+      qo->ldq = ldq;
+      qo->ldx = ldq;
+      qo->lo = lo;
+      qo->nb = nb;
+      qo->yshift = P.yshift;
+    }
+    nvalid = (p == 0) ? ski_round_up(n, 1ll << nb) : n_pad;
+    if (nvalid > n_pad) nvalid = n_pad;
+    Qin = Qo; Xin = Xo; lo_p = lo; nb_p = nb;
+    lo += nb;
+  }
+  return SKI_OK;
+}
+}  // namespace
+
+ski_status ski_premix_cols_q(const SkiPremixPlan& P, const double* A, int64_t lda, int64_t d, const double* b,
+                             SkiPremixQ* qo, cudaStream_t st) {
+  const int64_t ncols = d + (b != nullptr);
+  if (ncols > P.ldq || P.dtype != SKI_F64) return SKI_EINVAL;
+  FxIn in{};
+  in.A = A; in.lda = lda; in.n = P.n; in.d = d; in.b = b; in.D = P.D;
+  return premix_fx_passes(P, in, ncols, nullptr, 0, true, qo, st);
+}
+
 ski_status ski_premix_cols(const SkiPremixPlan& P, const double* A, int64_t lda, int64_t d, const double* b, void* Y,
                            int64_t ldy, cudaStream_t st) {
   const int64_t ncols = d + (b != nullptr);
@@ -534,32 +610,7 @@ ski_status ski_premix_cols(const SkiPremixPlan& P, const double* A, int64_t lda,
   FxIn in{};
   in.A = A; in.lda = lda; in.n = n; in.d = d; in.b = b; in.D = P.D;
   if (P.dtype == SKI_F64) {
-    long long* Qa = (long long*)P.Qa;
-    long long* Qb = (long long*)P.Qb;
-    int lo = 0;
-    int64_t nvalid = n;
-    long long* Qin = nullptr;
-    int16_t* Xin = nullptr;
-    int lo_p = 0, nb_p = 0;
-    for (int p = 0; p < P.P; ++p) {
-      const int nb = P.nbs[p];
-      const bool last = p == P.P - 1;
-      long long* Qo = (p & 1) ? Qb : Qa;
-      int16_t* Xo = (p & 1) ? P.Xb : P.Xa;
-      FxOut out{};
-      out.Q = Qo; out.X = Xo; out.ldq = ldq; out.ldx = ldq; out.Y = (double*)Y; out.ldy = ldy;
-      out.yshift = P.yshift; out.nonfinite = P.nonfinite;
-      FxIn cur = in;
-      cur.Q = Qin; cur.X = Xin; cur.ldq = ldq; cur.ldx = ldq; cur.nvalid = nvalid; cur.lo_p = lo_p; cur.nb_p = nb_p;
-      ski_status s;
-      if (p == 0) s = last ? launch_fx<0, 1>(nb, lo, n_pad, ncols, cur, out, st) : launch_fx<0, 0>(nb, lo, n_pad, ncols, cur, out, st);
-      else s = last ? launch_fx<1, 1>(nb, lo, n_pad, ncols, cur, out, st) : launch_fx<1, 0>(nb, lo, n_pad, ncols, cur, out, st);
-      if (s != SKI_OK) return s;
-      nvalid = (p == 0) ? ski_round_up(n, 1ll << nb) : n_pad;
-      if (nvalid > n_pad) nvalid = n_pad;
-      Qin = Qo; Xin = Xo; lo_p = lo; nb_p = nb;
-      lo += nb;
-    }
+    SKI_TRY(premix_fx_passes(P, in, ncols, Y, ldy, false, nullptr, st));
   } else {
     float* Qa = (float*)P.Qa;
     float* Qb = (float*)P.Qb;

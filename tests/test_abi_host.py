@@ -82,8 +82,9 @@ def test_workspace_queries_are_consistent(lib):
     sk = L.ski_sketch_workspace_size(ctypes.byref(A), 1, ctypes.byref(o))
     so = L.ski_solve_workspace_size(ctypes.byref(A), ctypes.byref(o))
     assert 0 < sk < so
-    # full-width premix: two int64 planes of n_pad x 4032 plus the FP64 output
-    assert sk >= 3 * 65536 * 4001 * 8
+    # full-width FP64 premix: two int64 planes of n_pad x 4032, handed to the
+    # gather as they are (no FP64 copy of the premixed matrix)
+    assert 2 * 65536 * 4001 * 8 <= sk < 3 * 65536 * 4001 * 8
     # in column slabs of 64: the same planes 64 columns wide
     slab = lib.ski_opts_default(m=8000, s=2, premix=1, n_pad=65536, premix_slab=64)
     sks = L.ski_sketch_workspace_size(ctypes.byref(A), 1, ctypes.byref(slab))
