@@ -63,7 +63,7 @@ typedef struct {
   int64_t ld;             /* SKI_DENSE: row stride in elements, ld >= d                */
   const double* val;      /* device. SKI_DENSE: n x d row-major. SKI_CSR: [nnz] values */
   const int64_t* rowptr;  /* SKI_CSR: device [n+1], rowptr[0] = 0, non-decreasing      */
-  const int32_t* colidx;  /* SKI_CSR: device [nnz], each in [0, d)                     */
+  const int32_t* colidx;  /* SKI_CSR: device [nnz], each in [0, d), distinct in a row  */
   int64_t nnz;            /* SKI_CSR: number of stored entries                        */
 } ski_matrix;
 

@@ -388,6 +388,106 @@ __global__ void __launch_bounds__(128) k_sketch_q_f64acc(
   }
 }
 
+// Exact sum of column-aligned addends (|q| < 2^55, one exponent per column):
+// plain int64 adds; |S| >= 2^61 coarsens the sum by 2^4 (later addends are
+// shifted to match), so any number of addends is safe.
+struct FxA {
+  long long S;
+  int E;
+  __device__ __forceinline__ void init() { S = 0; E = 0; }
+  __device__ __forceinline__ void add(long long q, unsigned neg) {
+    const long long v = q >> E;
+    S += neg ? -v : v;
+  }
+  __device__ __forceinline__ void renorm() {
+    if (S >= (1ll << 61) || S <= -(1ll << 61)) {
+      S >>= 4;
+      E += 4;
+    }
+  }
+};
+
+// Hash gather over the column-aligned premix output (SkiPremixQ with ecol):
+// the layout and work split of k_sketch_dense_f64acc, with 8 addends per
+// renormalisation check and no per-addend exponent.
+__global__ void __launch_bounds__(128) k_sketch_qa_f64acc(
+    const long long* __restrict__ Q, int64_t ldq, const int* __restrict__ ecol, int headroom, int yshift,
+    int64_t ncols, const int64_t* __restrict__ offsets, const uint32_t* __restrict__ list, long long scale_c,
+    int scale_e, double* __restrict__ SA, int64_t ld_sa, int64_t m) {
+  constexpr int CPT = 4, BPC = 4, U = 8;
+  const int64_t cb = (int64_t)blockIdx.y * (CPT * 128) + threadIdx.x;
+  const int64_t cfirst = (int64_t)blockIdx.y * (CPT * 128);
+  const int64_t ccount = max((int64_t)0, min((int64_t)(CPT * 128), ncols - cfirst));
+  const int64_t i0 = (int64_t)blockIdx.x * BPC;
+  auto prefetch = [&](int64_t i) {
+    if (i >= m || ccount == 0) return;
+    const int64_t lo_e = offsets[i], hi_e = offsets[i + 1];
+    for (int64_t e = lo_e + threadIdx.x / 8; e < hi_e; e += 16) {
+      const int64_t j = list[e] >> 1;
+      ski_l2_prefetch_range(Q + j * ldq + cfirst, (size_t)ccount * sizeof(long long), threadIdx.x & 7, 8);
+    }
+  };
+  int ec[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int64_t c = cb + k * 128;
+    ec[k] = c < ncols ? __ldg(&ecol[c]) : 0;
+  }
+  prefetch(i0);
+  for (int bi = 0; bi < BPC; ++bi) {
+    const int64_t i = i0 + bi;
+    if (i >= m) break;
+    prefetch(i + 1);
+    const int64_t lo_e = offsets[i], hi_e = offsets[i + 1];
+    FxA acc[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) acc[k].init();
+    int64_t e = lo_e;
+    for (; e + U <= hi_e; e += U) {
+      uint32_t en[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) en[u] = __ldg(&list[e + u]);
+      long long v[U][CPT];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t j = en[u] >> 1;
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+          const int64_t c = cb + k * 128;
+          v[u][k] = c < ncols ? __ldcs(&Q[j * ldq + c]) : 0ll;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) acc[k].add(v[u][k], en[u] & 1u);
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) acc[k].renorm();
+    }
+    for (; e < hi_e; ++e) {
+      const uint32_t en = __ldg(&list[e]);
+      const int64_t j = en >> 1;
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        const int64_t c = cb + k * 128;
+        if (c < ncols) acc[k].add(__ldcs(&Q[j * ldq + c]), en & 1u);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      const int64_t c = cb + k * 128;
+      if (c < ncols) {
+        double r = 0.0;
+        if (acc[k].S != 0) {
+          const long long Sp = (long long)(((__int128)acc[k].S * (__int128)scale_c) >> 62);
+          r = fx_i64_to_double(Sp, acc[k].E + ec[k] + headroom - yshift - scale_e);
+        }
+        SA[i * ld_sa + c] = r;
+      }
+    }
+  }
+}
+
 // Gather of a narrow column slab (ncols <= 32 * CPT) of the premix output:
 // warp w of the CTA owns bucket blockIdx.x * 8 + w, lane l its columns
 // l + 32 k.  The slab of Y was written just before by the premix and is still
@@ -471,39 +571,38 @@ __global__ void __launch_bounds__(256) k_sketch_slab_f32in(
 }
 
 // ------------------------------------------------------------ CSR gather
-// Row i of SA for a CSR A: the bucket's rows are scattered into a
-// shared-memory accumulator over the column chunk [c0, c0 + chunk), then the
-// chunk is written out.  Column indices within one CSR row must be distinct.
+// Row i of SA for a CSR A: SA is zeroed first (a bandwidth-bound memset of the
+// dense m x (d+1) output, the dominant traffic), then warp i scatters the
+// nonzeros of bucket i's rows into row i of SA, one source row after another
+// (__syncwarp between rows orders the read-modify-writes), so the summation
+// order is fixed and no atomics are needed.  Column indices within one CSR
+// row must be distinct.  Each SA entry receives few addends (about
+// s * nnz / (m d) on average), so FP32 / BF16 outputs are accumulated in place.
 template <class TOUT>
 __global__ void __launch_bounds__(256) k_sketch_csr(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, const double* __restrict__ val,
     int64_t d, const double* __restrict__ b, const int64_t* __restrict__ offsets,
-    const uint32_t* __restrict__ list, double scale, int64_t chunk, TOUT* __restrict__ SA, int64_t ld_sa) {
-  extern __shared__ double acc[];
-  const int64_t i = blockIdx.x;
-  const int64_t c0 = (int64_t)blockIdx.y * chunk;
-  const int64_t ncols = d + (b != nullptr);
-  const int64_t cw = min(chunk, ncols - c0);
-  for (int64_t c = threadIdx.x; c < cw; c += blockDim.x) acc[c] = 0.0;
-  __syncthreads();
+    const uint32_t* __restrict__ list, double scale, TOUT* __restrict__ SA, int64_t ld_sa, int64_t m) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= m) return;
+  TOUT* out = SA + i * ld_sa;
   const int64_t lo = offsets[i], hi = offsets[i + 1];
   double bacc = 0.0;
   for (int64_t e = lo; e < hi; ++e) {
-    uint32_t en = list[e];
-    int64_t j = en >> 1;
-    double sg = (en & 1) ? -1.0 : 1.0;
-    int64_t p0 = rowptr[j], p1 = rowptr[j + 1];
-    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-      int64_t c = (int64_t)colidx[p] - c0;
-      if (c >= 0 && c < cw) acc[c] += sg * val[p];
+    const uint32_t en = __ldg(&list[e]);
+    const int64_t j = en >> 1;
+    const double sg = (en & 1u) ? -scale : scale;
+    const int64_t p0 = __ldg(&rowptr[j]), p1 = __ldg(&rowptr[j + 1]);
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      const int32_t c = __ldg(&colidx[p]);
+      const double v = sg * __ldg(&val[p]);
+      out[c] = SkiType<TOUT>::from(SkiType<TOUT>::to_f64(out[c]) + v);
     }
-    if (b && threadIdx.x == 0) bacc += sg * b[j];
-    __syncthreads();
+    if (b && lane == 0) bacc += sg * __ldg(&b[j]);
+    __syncwarp();
   }
-  if (b && threadIdx.x == 0 && d >= c0 && d < c0 + cw) acc[d - c0] = bacc;
-  __syncthreads();
-  for (int64_t c = threadIdx.x; c < cw; c += blockDim.x)
-    SA[i * ld_sa + c0 + c] = SkiType<TOUT>::from(acc[c] * scale);
+  if (b && lane == 0) out[d] = SkiType<TOUT>::from(bacc);
 }
 
 // ------------------------------------------------------------ host side
@@ -606,8 +705,12 @@ ski_status ski_gather_q(const SkiPremixQ& y, int64_t ncols, const SkiBuckets& bk
   int e;
   scale_fixed(scale, &c, &e);
   dim3 grid((unsigned)ski_cdiv(bk.m, 4), (unsigned)ski_cdiv(ncols, 4 * 128));
-  k_sketch_q_f64acc<<<grid, 128, 0, st>>>(y.Q, y.ldq, y.X, y.ldx, y.lo, y.nb, y.yshift, ncols, bk.offsets, bk.list, c,
-                                           e, SA, ld_sa, bk.m);
+  if (!y.X)
+    k_sketch_qa_f64acc<<<grid, 128, 0, st>>>(y.Q, y.ldq, y.ecol, y.headroom, y.yshift, ncols, bk.offsets, bk.list, c,
+                                              e, SA, ld_sa, bk.m);
+  else
+    k_sketch_q_f64acc<<<grid, 128, 0, st>>>(y.Q, y.ldq, y.X, y.ldx, y.lo, y.nb, y.yshift, ncols, bk.offsets, bk.list,
+                                             c, e, SA, ld_sa, bk.m);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }
@@ -654,30 +757,18 @@ ski_status ski_gather_slab(const void* Y, int32_t y_dtype, int64_t ldy, int64_t 
 
 ski_status ski_gather_csr(const ski_matrix* A, const double* b, const SkiBuckets& bk, double scale,
                           int32_t out_dtype, void* SA, int64_t ld_sa, cudaStream_t st) {
-  const int64_t ncols = A->d + (b != nullptr);
-  int64_t chunk = ncols < 8192 ? ncols : 8192;
-  size_t smem = chunk * sizeof(double);
-  dim3 grid((unsigned)bk.m, (unsigned)ski_cdiv(ncols, chunk));
-  const int T = 256;
-  if (out_dtype == SKI_F64) {
-    if (smem > 48 * 1024)
-      SKI_CUDA_TRY(cudaFuncSetAttribute(k_sketch_csr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        ski_smem_cap((const void*)k_sketch_csr<double>)));
-    k_sketch_csr<double><<<grid, T, smem, st>>>(A->rowptr, A->colidx, A->val, A->d, b, bk.offsets, bk.list,
-                                                scale, chunk, (double*)SA, ld_sa);
-  } else if (out_dtype == SKI_F32) {
-    if (smem > 48 * 1024)
-      SKI_CUDA_TRY(cudaFuncSetAttribute(k_sketch_csr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        ski_smem_cap((const void*)k_sketch_csr<float>)));
-    k_sketch_csr<float><<<grid, T, smem, st>>>(A->rowptr, A->colidx, A->val, A->d, b, bk.offsets, bk.list,
-                                               scale, chunk, (float*)SA, ld_sa);
-  } else {
-    if (smem > 48 * 1024)
-      SKI_CUDA_TRY(cudaFuncSetAttribute(k_sketch_csr<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        ski_smem_cap((const void*)k_sketch_csr<__nv_bfloat16>)));
-    k_sketch_csr<__nv_bfloat16><<<grid, T, smem, st>>>(A->rowptr, A->colidx, A->val, A->d, b, bk.offsets,
-                                                       bk.list, scale, chunk, (__nv_bfloat16*)SA, ld_sa);
-  }
+  const size_t esz = out_dtype == SKI_F64 ? 8 : (out_dtype == SKI_F32 ? 4 : 2);
+  SKI_CUDA_TRY(cudaMemsetAsync(SA, 0, (size_t)bk.m * (size_t)ld_sa * esz, st));
+  const unsigned grid = (unsigned)ski_cdiv(bk.m, 8);
+  if (out_dtype == SKI_F64)
+    k_sketch_csr<double><<<grid, 256, 0, st>>>(A->rowptr, A->colidx, A->val, A->d, b, bk.offsets, bk.list, scale,
+                                               (double*)SA, ld_sa, bk.m);
+  else if (out_dtype == SKI_F32)
+    k_sketch_csr<float><<<grid, 256, 0, st>>>(A->rowptr, A->colidx, A->val, A->d, b, bk.offsets, bk.list, scale,
+                                              (float*)SA, ld_sa, bk.m);
+  else
+    k_sketch_csr<__nv_bfloat16><<<grid, 256, 0, st>>>(A->rowptr, A->colidx, A->val, A->d, b, bk.offsets, bk.list,
+                                                      scale, (__nv_bfloat16*)SA, ld_sa, bk.m);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }

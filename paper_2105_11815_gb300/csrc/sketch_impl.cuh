@@ -51,18 +51,24 @@ struct SkiPremixPlan {
   int* nonfinite;
   void *Qa, *Qb;
   int16_t *Xa, *Xb;
+  int* ecol;
 };
 ski_status ski_premix_plan(int64_t n, int64_t ncols_max, int64_t n_pad, int32_t dtype, uint64_t seed, SkiArena& ar,
                            cudaStream_t st, SkiPremixPlan* plan);
 ski_status ski_premix_cols(const SkiPremixPlan& plan, const double* A, int64_t lda, int64_t d, const double* b,
                            void* Y, int64_t ldy, cudaStream_t st);
-// The FP64 premix output left in block-fixed-point form: row j, column c is
-// Q[j * ldq + c] * 2^(X[tile(j) * ldx + c] - yshift), with tile(j) the tile of
-// row j in the last pass (row bits [lo, lo + nb)).  Saves the last pass its
-// FP64 conversion and the hash gather its FP64 decode.
+// The FP64 premix output left in block-fixed-point form (one pass): row j,
+// column c is Q[j * ldq + c] * 2^(X[tile(j) * ldx + c] - yshift), with tile(j)
+// the tile of row j in the last pass (row bits [lo, lo + nb)).  Saves the
+// last pass its FP64 conversion and the hash gather its FP64 decode.
+// With two or more passes the last one aligns each column to a common
+// exponent instead (X == nullptr): row j, column c is Q[j * ldq + c] *
+// 2^(ecol[c] + headroom - yshift).
 struct SkiPremixQ {
   const long long* Q;
   const int16_t* X;
+  const int* ecol;
+  int headroom;
   int64_t ldq, ldx;
   int lo, nb, yshift;
 };

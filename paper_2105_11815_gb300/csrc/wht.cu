@@ -56,7 +56,14 @@ struct FxOut {
   int64_t ldy;
   int yshift;
   int* nonfinite;
+  const int* ecol;  // OUT == 2: per-column exponent all tiles are aligned to
 };
+
+// OUT == 2 (last pass feeding the hash gather): values are stored as
+// q >> (ecol[c] - X + kAlignHeadroom), i.e. in units of 2^(ecol[c] + headroom)
+// shared by the whole column, so the gather sums them with plain int64 adds;
+// |q| < 2^62 becomes < 2^55, leaving room for 2^6 addends between renorms.
+constexpr int kAlignHeadroom = 7;
 
 // CW: columns per tile (32, or 16 for twice the CTAs per SM where the pass is
 // latency-bound).
@@ -164,12 +171,16 @@ __global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4
     }
   }
   if (!cok) return;
+  int ash = 0;
+  if (OUT == 2) ash = max(0, min(63, out.ecol[col] - X + kAlignHeadroom));
 #pragma unroll
   for (int t = 0; t < R; ++t) {
     const int64_t row = base + ((int64_t)((g << RB) + t) << lo);
     if (row >= n_pad) continue;
     if (OUT == 0) {
       out.Q[row * out.ldq + col] = q[t];
+    } else if (OUT == 2) {
+      out.Q[row * out.ldq + col] = q[t] >> ash;
     } else {
       out.Y[row * out.ldy + col] = fx_to_double(q[t], X - out.yshift + 1075 + FX_LIFT, 0);
     }
@@ -177,150 +188,15 @@ __global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4
   if (OUT == 0 && g == 0) out.X[tile * out.ldx + col] = (int16_t)X;
 }
 
-// Persistent form of k_wht_fx: each CTA walks the linear tile indices
-// u = blockIdx.x, + gridDim.x, ... (row tile u / nct, column tile u % nct)
-// and issues the global loads of its next tile into registers before it
-// transforms the current one, so a tile's loads are in flight during the
-// previous tile's butterflies and stores (the one-tile-per-CTA kernel leaves
-// HBM idle during those phases).  Same arithmetic and results as k_wht_fx.
-template <int RB, int IN>
-struct WhtRaw {
-  long long v[1 << RB];
-  int xs[IN == 1 ? (1 << RB) : 1];
-};
-
-template <int RB, int GB, int IN>
-__device__ __forceinline__ void wht_load(int64_t u, int64_t nct, int lo, int64_t ncols, const FxIn& in,
-                                         WhtRaw<RB, IN>& r) {
-  constexpr int R = 1 << RB, NB = RB + GB;
-  const int c = threadIdx.x & (CT - 1), g = threadIdx.x / CT;
-  const int64_t base = tile_base(u / nct, lo, NB);
-  const int64_t col = (u % nct) * CT + c;
-  const bool cok = col < ncols;
-#pragma unroll
-  for (int t = 0; t < R; ++t) {
-    const int64_t row = base + ((int64_t)(g + (t << GB)) << lo);
-    if (IN == 0) {
-      long long bits = 0;
-      if (cok && row < in.n) {
-        bits = __double_as_longlong(col < in.d ? in.A[row * in.lda + col] : in.b[row]);
-        if (in.D[row] < 0) bits ^= (1ll << 63);
-      }
-      r.v[t] = bits;
-    } else {
-      long long v = 0;
-      int xs = -32768;
-      if (cok && row < in.nvalid) {
-        v = in.Q[row * in.ldq + col];
-        xs = in.X[tile_of_row(row, in.lo_p, in.nb_p) * in.ldx + col];
-      }
-      r.v[t] = v;
-      r.xs[IN == 1 ? t : 0] = xs;
-    }
-  }
-}
-
-template <int RB, int GB, int IN, int OUT>
-__global__ void __launch_bounds__(CT << GB, 1) k_wht_fx_pipe(int lo, int64_t n_pad, int64_t ncols, int64_t nct,
-                                                             int64_t ntotal, FxIn in, FxOut out) {
-  constexpr int R = 1 << RB, G = 1 << GB, NB = RB + GB;
-  extern __shared__ long long sq[];  // [R*G][CT]
-  __shared__ int sx[G][CT];
-  const int c = threadIdx.x & (CT - 1), g = threadIdx.x / CT;
-  int64_t u = blockIdx.x;
-  if (u >= ntotal) return;
-  WhtRaw<RB, IN> cur;
-  wht_load<RB, GB, IN>(u, nct, lo, ncols, in, cur);
-  bool bad = false;
-  for (; u < ntotal; u += gridDim.x) {
-    WhtRaw<RB, IN> nxt;
-    const int64_t un = u + gridDim.x;
-    if (un < ntotal) wht_load<RB, GB, IN>(un, nct, lo, ncols, in, nxt);
-    const int64_t tile = u / nct;
-    const int64_t base = tile_base(tile, lo, NB);
-    const int64_t col = (u % nct) * CT + c;
-    const bool cok = col < ncols;
-    long long q[R];
-    int emax = -100000;
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-      q[t] = cur.v[t];
-      if (IN == 0) {
-        const int e = (int)((q[t] >> 52) & 0x7FF);
-        bad |= (e == 0x7FF);
-        emax = max(emax, e ? e : 1);
-      } else {
-        if (q[t] == 0) cur.xs[t] = -32768;
-        emax = max(emax, cur.xs[IN == 1 ? t : 0]);
-      }
-    }
-    sx[g][c] = emax;
-    __syncthreads();
-    int E = sx[0][c];
-#pragma unroll
-    for (int gg = 1; gg < G; ++gg) E = max(E, sx[gg][c]);
-    int X;
-    if (IN == 0) {
-      constexpr int LIFT = 9 - NB;
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        const unsigned long long bits = (unsigned long long)q[t];
-        const int e = (int)((bits >> 52) & 0x7FF);
-        const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
-        const int sh = E - (e ? e : 1);
-        const unsigned long long mq = sh > 63 ? 0ull : ((M << LIFT) >> sh);
-        q[t] = (bits >> 63) ? -(long long)mq : (long long)mq;
-      }
-      X = E - 1075 - LIFT;
-    } else {
-      if (E == -32768) E = 0;
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        const int sh = E - cur.xs[IN == 1 ? t : 0] + NB;
-        q[t] = (q[t] == 0 || sh > 63) ? 0 : (q[t] >> sh);
-      }
-      X = E + NB;
-    }
-#pragma unroll
-    for (int h = 1; h < R; h <<= 1) {
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        if (!(t & h)) {
-          const long long a = q[t], b = q[t + h];
-          q[t] = a + b;
-          q[t + h] = a - b;
-        }
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < R; ++t) sq[(g + (t << GB)) * CT + c] = q[t];
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < R; ++t) q[t] = sq[((g << RB) + t) * CT + c];
-#pragma unroll
-    for (int h = 1; h < G; h <<= 1) {
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        if (!(t & h)) {
-          const long long a = q[t], b = q[t + h];
-          q[t] = a + b;
-          q[t + h] = a - b;
-        }
-      }
-    }
-    if (cok) {
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        const int64_t row = base + ((int64_t)((g << RB) + t) << lo);
-        if (row >= n_pad) continue;
-        if (OUT == 0) out.Q[row * out.ldq + col] = q[t];
-        else out.Y[row * out.ldy + col] = fx_to_double(q[t], X - out.yshift + 1075 + FX_LIFT, 0);
-      }
-      if (OUT == 0 && g == 0) out.X[tile * out.ldx + col] = (int16_t)X;
-    }
-    cur = nxt;
-  }
-  if (bad && out.nonfinite) atomicOr(out.nonfinite, 1);
+// ecol[c] = max over the first ntiles tiles of X[t][c], plus nb: an upper bound
+// of the exponent X that the next pass (nb levels) gives any tile of column c.
+__global__ void k_colmax_exp(int64_t ncols, const int16_t* __restrict__ X, int64_t ldx, int64_t ntiles, int nb,
+                             int* __restrict__ ecol) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  int e = -32768;
+  for (int64_t tt = 0; tt < ntiles; ++tt) e = max(e, (int)X[tt * ldx + c]);
+  ecol[c] = (e == -32768 ? 0 : e) + nb;
 }
 
 template <class TOUT>
@@ -418,34 +294,6 @@ ski_status launch_fx(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& i
                    : dim3((unsigned)ntiles, (unsigned)ski_cdiv(ncols, CT));
   const size_t smem = (size_t)(1 << nb) * CT * sizeof(long long);
   const int threads = CT << GB;
-  // persistent, register-prefetching form (16 rows per thread at most), chosen
-  // by SKI_WHT_PIPE=1: at 50000 x 4000 it measured 4.1 ms for both passes
-  // against 3.2 ms for one tile per CTA at two CTAs per SM, so it is not the
-  // default.  The first pass skips the row tiles wholly in the zero padding.
-  static const bool use_pipe = [] {
-    const char* e = getenv("SKI_WHT_PIPE");
-    return e && e[0] == '1';
-  }();
-  const int64_t nct = ski_cdiv(ncols, CT);
-  const int64_t nrt = (IN == 0 && OUT == 0 && lo == 0) ? ski_cdiv(in.n, 1ll << nb) : ntiles;
-  const int64_t ntotal = nrt * nct;
-  int sms = 0, dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return SKI_ECUDA;
-  const unsigned pgrid = (unsigned)std::min<int64_t>(ntotal, sms);
-#define SKI_FXP_CASE(rb, gb)                                                                     \
-  if (RB == rb && GB == gb) {                                                                    \
-    auto kfn = k_wht_fx_pipe<rb, gb, IN, OUT>;                                                   \
-    if (smem > 48 * 1024)                                                                        \
-      SKI_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    if (ntotal > 0) kfn<<<pgrid, threads, smem, st>>>(lo, n_pad, ncols, nct, ntotal, in, out);  \
-    SKI_LAUNCH_CHECK();                                                                          \
-    return SKI_OK;                                                                               \
-  }
-  if (use_pipe) {
-    SKI_FXP_CASE(3, 3) SKI_FXP_CASE(4, 3) SKI_FXP_CASE(4, 4)
-  }
-#undef SKI_FXP_CASE
   // the first pass (FP64 in) is latency-bound: 16-column tiles, four CTAs per SM
   if (IN == 0 && RB == 4 && GB == 4 && lo == 0) {
     constexpr int CW = 16;
@@ -511,6 +359,7 @@ size_t ski_premix_ws_bytes(int64_t n, int64_t ncols, int64_t n_pad, int32_t dtyp
     ar.take<long long>(n_pad * ldq);
     ar.take<int16_t>(n_pad * ldq);
     ar.take<int16_t>(n_pad * ldq);
+    ar.take<int>(ldq);
   } else {
     ar.take<float>(n_pad * ldq);
     ar.take<float>(n_pad * ldq);
@@ -536,10 +385,12 @@ ski_status ski_premix_plan(int64_t n, int64_t ncols_max, int64_t n_pad, int32_t 
     P.Qb = ar.take<long long>(n_pad * P.ldq);
     P.Xa = ar.take<int16_t>(n_pad * P.ldq);
     P.Xb = ar.take<int16_t>(n_pad * P.ldq);
+    P.ecol = ar.take<int>(P.ldq);
   } else {
     P.Qa = ar.take<float>(n_pad * P.ldq);
     P.Qb = ar.take<float>(n_pad * P.ldq);
     P.Xa = P.Xb = nullptr;
+    P.ecol = nullptr;
   }
   if (!ar.ok() || !P.Qb) return SKI_ENOMEM;
   SKI_TRY(ski_premix_signs(seed, n, P.D, st));
@@ -564,20 +415,32 @@ ski_status premix_fx_passes(const SkiPremixPlan& P, const FxIn& in, int64_t ncol
     const int nb = P.nbs[p];
     const bool last = p == P.P - 1;
     const bool to_y = last && !qfinal;
+    const bool aligned = last && qfinal && p > 0;  // column-aligned int64 for the gather
     long long* Qo = (p & 1) ? Qb : Qa;
     int16_t* Xo = (p & 1) ? P.Xb : P.Xa;
     FxOut out{};
     out.Q = Qo; out.X = Xo; out.ldq = ldq; out.ldx = ldq; out.Y = (double*)Y; out.ldy = ldy;
-    out.yshift = P.yshift; out.nonfinite = P.nonfinite;
+    out.yshift = P.yshift; out.nonfinite = P.nonfinite; out.ecol = P.ecol;
     FxIn cur = in;
     cur.Q = Qin; cur.X = Xin; cur.ldq = ldq; cur.ldx = ldq; cur.nvalid = nvalid; cur.lo_p = lo_p; cur.nb_p = nb_p;
+    if (aligned) {
+      // exponent bound of every tile of the last pass, per column, from the
+      // previous pass's exponents (its tiles that hold rows below nvalid)
+      const int64_t ntp = ski_cdiv(nvalid, 1ll << nb_p) << lo_p;
+      k_colmax_exp<<<(unsigned)ski_cdiv(ncols, 256), 256, 0, st>>>(ncols, Xin, ldq, std::min<int64_t>(ntp, n_pad >> nb_p),
+                                                                   nb, P.ecol);
+      SKI_LAUNCH_CHECK();
+    }
     ski_status s;
     if (p == 0) s = to_y ? launch_fx<0, 1>(nb, lo, n_pad, ncols, cur, out, st) : launch_fx<0, 0>(nb, lo, n_pad, ncols, cur, out, st);
+    else if (aligned) s = launch_fx<1, 2>(nb, lo, n_pad, ncols, cur, out, st);
     else s = to_y ? launch_fx<1, 1>(nb, lo, n_pad, ncols, cur, out, st) : launch_fx<1, 0>(nb, lo, n_pad, ncols, cur, out, st);
     if (s != SKI_OK) return s;
     if (last && qfinal) {
       qo->Q = Qo;
-      qo->X = Xo;
+      qo->X = aligned ? nullptr : Xo;
+      qo->ecol = aligned ? P.ecol : nullptr;
+      qo->headroom = kAlignHeadroom;
       qo->ldq = ldq;
       qo->ldx = ldq;
       qo->lo = lo;

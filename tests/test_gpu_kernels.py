@@ -96,7 +96,21 @@ def test_csr_sketch_fp64():
     keep = (to_dev(torch, rp), to_dev(torch, ci), to_dev(torch, v))
     M = pkg.csr_matrix(keep[0], keep[1], keep[2], 20000, 300)
     pkg.ski_sketch_hash(M, to_dev(torch, b), o, SA, 301)
-    assert rel_fro(SA.cpu().numpy(), osk.sketch_rows(13, 2, 600, A, b)) <= 1e-12
+    want = osk.sketch_rows(13, 2, 600, A, b)
+    assert rel_fro(SA.cpu().numpy(), want) <= 1e-12
+    # FP32 output with a padded row stride, and empty rows (5000..5099 dropped)
+    keep_rows = np.ones(20000, bool)
+    keep_rows[5000:5100] = False
+    A2 = sp.csr_matrix(sp.diags(keep_rows.astype(np.float64)) @ A)
+    A2.eliminate_zeros()
+    A2.sort_indices()
+    rp2, ci2, v2 = A2.indptr.astype(np.int64), A2.indices.astype(np.int32), A2.data
+    M2 = pkg.csr_matrix(to_dev(torch, rp2), to_dev(torch, ci2), to_dev(torch, v2), 20000, 300)
+    o32 = pkg.ski_opts_default(m=600, s=2, seed=13, sketch_dtype=pkg.SKI_F32)
+    SA32 = torch.full((600, 305), float("nan"), dtype=torch.float32, device="cuda")
+    pkg.ski_sketch_hash(M2, to_dev(torch, b), o32, SA32, 305)
+    want2 = osk.sketch_rows(13, 2, 600, A2, b)
+    assert rel_fro(SA32[:, :301].double().cpu().numpy(), want2) <= 1e-6
 
 
 @pytest.mark.parametrize("n,d,npad", [(3000, 7, 4096), (20000, 33, 32768), (1, 3, 1), (2, 2, 2), (700, 5, 1024),
