@@ -69,10 +69,13 @@ def peaks():
 # 2.07 GHz = 1.26 TFLOP/s (a DFMA loop measured 1.00 on this machine).
 FP64_PEAK_TFLOPS = 1.26
 FP32_PEAK_TFLOPS = 72.0
-# DRAM bytes (read + write) of the sketch stage's kernels (premix passes and
-# hash gathers of all column slabs, one solve), from ncu; None where not captured
-# for the current kernels.
-SKETCH_TRAFFIC = {}
+# DRAM bytes (read + write) per launch from ncu for the current kernels
+# (profiles/hash_gather_and_premix_dense_50000x4000.md): the whole sketch stage
+# (both premix passes, the column-exponent bound, the bucket lists and the
+# hash gather) and the hash gather alone; None where not captured.
+SKETCH_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 1602613760 + 1554212096 + 1587456 + 1618959872 + 2044096768 +
+                  2424035328 + 236445696 + 805632}
+GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2424035328 + 236445696}
 
 
 class ClockSampler:
@@ -310,11 +313,19 @@ def run_ours(args, name):
                 "frac": gemm_flops / (g64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (DFMA loop measured 1.00)",
                 "flops_per_step": gemm_flops, "ms_per_step": g64}
-    sketch_roofline = {"kernel": ("k_wht_fx + k_sketch_slab_f64acc (premix and hash gather in L2 column slabs)"
+    sketch_roofline = {"kernel": ("premix + hash stage (k_wht_fx x2, k_sketch_qa_f64acc)"
                                   if npad else "k_sketch_dense_f64acc (hash gather)"), "bound": "hbm",
                        "achieved": sb / (stage_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                        "frac": sb / (stage_ms * 1e-3) / 1e9 / hbm, "traffic": SKETCH_TRAFFIC.get(name),
                        "peak_source": peak_kind, "bytes_per_stage": sb, "ms_per_stage": stage_ms}
+    # the hash gather alone (S applied to the premixed rows): reads s * rows *
+    # (d + 1) int64 values, writes [SA | Sb]
+    rows = npad if npad else n
+    gather_bytes = 8.0 * (s * rows * (d + 1) + m * (d + 1))
+    hash_roofline = {"kernel": "k_sketch_qa_f64acc (hash gather)" if npad else "k_sketch_dense_f64acc (hash gather)",
+                     "bound": "hbm", "achieved": gather_bytes / (g_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": gather_bytes / (g_ms * 1e-3) / 1e9 / hbm, "traffic": GATHER_TRAFFIC.get(name),
+                     "peak_source": peak_kind, "bytes_per_launch": gather_bytes, "ms_per_launch": g_ms}
     tf32_peak = 0.5 * pj.get("bf16_tflops", 1900.0)
     # the mixed path's QR runs its products in three TF32 passes: the tensor
     # pipe executes 3x the algorithmic flops counted here
@@ -391,7 +402,7 @@ def run_ours(args, name):
                        "l2": "inputs larger than L2 (A = %.2f GB)" % (8e-9 * n * d),
                        "parallelism": "replicas" if world > 1 else "single"},
             "hbm_frac": value / world / hbm, "roofline": roofline, "sketch_roofline": sketch_roofline,
-            "tc_roofline": tc_roofline, "stages": stages, "lls": lls,
+            "hash_roofline": hash_roofline, "tc_roofline": tc_roofline, "stages": stages, "lls": lls,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line), flush=True)
