@@ -73,9 +73,9 @@ FP32_PEAK_TFLOPS = 72.0
 # (profiles/hash_gather_and_premix_dense_50000x4000.md): the whole sketch stage
 # (both premix passes, the column-exponent bound, the bucket lists and the
 # hash gather) and the hash gather alone; None where not captured.
-SKETCH_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 1602613760 + 1554212096 + 1587456 + 1618959872 + 2044096768 +
-                  2424035328 + 236445696 + 805632}
-GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2424035328 + 236445696}
+SKETCH_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 1651373056 + 1558533120 + 1587456 + 1619061760 + 2044707840 +
+                  2425030400 + 236545536 + 805632}
+GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2425030400 + 236545536}
 
 
 class ClockSampler:
@@ -313,7 +313,7 @@ def run_ours(args, name):
                 "frac": gemm_flops / (g64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (DFMA loop measured 1.00)",
                 "flops_per_step": gemm_flops, "ms_per_step": g64}
-    sketch_roofline = {"kernel": ("premix + hash stage (k_wht_fx x2, k_sketch_qa_f64acc)"
+    sketch_roofline = {"kernel": ("premix + hash stage (k_wht_p1_tma, k_wht_fx, k_sketch_qa_f64acc)"
                                   if npad else "k_sketch_dense_f64acc (hash gather)"), "bound": "hbm",
                        "achieved": sb / (stage_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                        "frac": sb / (stage_ms * 1e-3) / 1e9 / hbm, "traffic": SKETCH_TRAFFIC.get(name),

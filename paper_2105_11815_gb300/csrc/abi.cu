@@ -150,7 +150,7 @@ static size_t sketch_scratch_bytes(const ski_matrix* A, int32_t with_b, const sk
 
 static ski_status sketch_run(const ski_matrix* A, const double* b, const ski_opts* o, void* SA, int64_t ld_sa,
                              char* scratch, size_t scratch_bytes, cudaStream_t st, cudaEvent_t e_bk = nullptr,
-                             cudaEvent_t e_pm = nullptr) {
+                             cudaEvent_t e_pm = nullptr, int* err_flag = nullptr) {
   const int64_t ncols = A->d + (b ? 1 : 0);
   const int64_t rows = o->premix ? eff_npad(A, o) : A->n;
   SkiArena ar{scratch, scratch_bytes, 0, false};
@@ -178,7 +178,7 @@ static ski_status sketch_run(const ski_matrix* A, const double* b, const ski_opt
   if (!ar.ok() || !pws) return SKI_ENOMEM;
   SkiArena par{pws, pwb, 0, false};
   SkiPremixPlan plan;
-  SKI_TRY(ski_premix_plan(A->n, w, rows, pdt, o->seed, par, st, &plan));
+  SKI_TRY(ski_premix_plan(A->n, w, rows, pdt, o->seed, par, st, &plan, err_flag));
   const double scale = plan.residual_scale * inv_sqrt_s;
   if (qpath) {
     // all columns at once, FP64: premix into block-fixed-point planes, then
@@ -332,6 +332,7 @@ struct SolvePlan {
   // persistent
   double *R, *qtsb, *M, *Mt, *xs, *t, *v, *w, *y, *z, *p, *q, *part, *part_tt, *part_aa;
   LsqrScalars* sc;
+  int* perr;  // bounded-wait flag of the premix (read after Step 2)
   double *vp, *part_vv;
   float2* A2;  // double-float copy of a dense A for the LSQR passes
   int sA;
@@ -425,6 +426,7 @@ size_t plan_solve(const ski_matrix* A, const ski_opts* o, char* base, size_t cap
   P->part_tt = ar.take<double>(P->nblk);
   P->part_aa = ar.take<double>(P->nblk);
   P->sc = ar.take<LsqrScalars>(1);
+  P->perr = ar.take<int>(1);
   P->vp = ar.take<double>(d);
   P->part_vv = ar.take<double>(ski_vv_blocks(d));
   P->A2 = P->csr ? nullptr : ar.take<float2>(n * ski_a2_ld(d));
@@ -670,9 +672,10 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
     carve_region(A, of, &P);
     Events fe;
     if (!fe.ok) return SKI_ECUDA;
+    SKI_CUDA_TRY(cudaMemsetAsync(P.perr, 0, sizeof(int), st));
     SKI_CUDA_TRY(cudaEventRecord(fe.e[0], st));
     // Step 1: sketch [SA | Sb]
-    SKI_TRY(sketch_run(A, b, of, P.SA, P.ld_sa, P.stage, P.stage_bytes, st, fe.e[5], fe.e[6]));
+    SKI_TRY(sketch_run(A, b, of, P.SA, P.ld_sa, P.stage, P.stage_bytes, st, fe.e[5], fe.e[6], P.perr));
     SKI_CUDA_TRY(cudaEventRecord(fe.e[1], st));
     // Step 2: QR of [SA | Sb] in qr_dtype
     if (P.SAq != P.SA) {
@@ -695,6 +698,10 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
     SKI_CUDA_TRY(cudaEventRecord(fe.e[2], st));
     bool nonfinite = false;
     SKI_TRY(rank_from_diag(d, P.R, d, o->rcond, st, &rank, &nonfinite, &rdiag_ratio));
+    int perr = 0;
+    SKI_CUDA_TRY(cudaMemcpyAsync(&perr, P.perr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SKI_CUDA_TRY(cudaStreamSynchronize(st));
+    if (perr) return SKI_ETIMEOUT;
     if (nonfinite) return SKI_ENONFINITE;
     if (rank < d && o->perturb <= 0.0) return SKI_ESINGULAR;
     // R^{-1} (explicit, and its transpose)

@@ -338,6 +338,29 @@ bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, i
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+}  // namespace
+
+// 2-D FP64 tensor map over a row-major rows x cols matrix (row stride ld
+// elements, a multiple of 2), box = box_rows x box_cols, no swizzle, zero
+// fill outside the matrix.  False when the driver entry point is missing or
+// the encoding is refused.
+bool ski_tmap_f64_2d(CUtensorMap* map, const double* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                     int box_cols) {
+  EncodeTiled fn = encoder();
+  if (!fn || (ld & 1) || ((uintptr_t)base & 15)) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * sizeof(double))};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  const bool ok = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  cudaGetLastError();
+  return ok;
+}
+
+namespace {
+
 template <int BN, int STAGES, bool SPLIT>
 ski_status launch(const float* A, int64_t lda, const float* B, int64_t ldb, int M, int N, int K, float* C,
                   int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st) {

@@ -1,6 +1,8 @@
 // Internal interfaces between the sketch, premix, QR, LSQR translation units
 // and the C-ABI layer.
 #pragma once
+#include <cuda.h>
+
 #include "common.cuh"
 
 struct SkiBuckets {
@@ -49,12 +51,15 @@ struct SkiPremixPlan {
   double residual_scale;
   int8_t* D;
   int* nonfinite;
+  int* err;  // set when a bounded wait of the TMA-fed pass gave up
   void *Qa, *Qb;
   int16_t *Xa, *Xb;
   int* ecol;
 };
+// err_flag: a device int the caller zeroes and reads (nullptr: one in the
+// plan's scratch).
 ski_status ski_premix_plan(int64_t n, int64_t ncols_max, int64_t n_pad, int32_t dtype, uint64_t seed, SkiArena& ar,
-                           cudaStream_t st, SkiPremixPlan* plan);
+                           cudaStream_t st, SkiPremixPlan* plan, int* err_flag = nullptr);
 ski_status ski_premix_cols(const SkiPremixPlan& plan, const double* A, int64_t lda, int64_t d, const double* b,
                            void* Y, int64_t ldy, cudaStream_t st);
 // The FP64 premix output left in block-fixed-point form (one pass): row j,
@@ -89,6 +94,8 @@ ski_status ski_qr_run(int64_t m, int64_t d, int32_t with_rhs, void* SA, int64_t 
 ski_status ski_barrier_selftest(long long spin_limit, void* ws, cudaStream_t st);
 
 // ---- gemm_tc.cu: D = A B^T on the TF32 tensor cores (see there for modes)
+bool ski_tmap_f64_2d(CUtensorMap* map, const double* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                     int box_cols);
 ski_status ski_gemm_tf32(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
                          float* C, int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st,
                          bool split3);

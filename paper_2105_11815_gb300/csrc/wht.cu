@@ -42,6 +42,7 @@ struct FxIn {
   int64_t lda, n, d;
   const double* b;
   const int8_t* D;
+  int* err;  // bounded-wait error flag of the TMA-fed first pass (nullptr: not used)
   // IN == 1: previous pass
   const long long* Q;
   const int16_t* X;
@@ -199,6 +200,172 @@ __global__ void k_colmax_exp(int64_t ncols, const int16_t* __restrict__ X, int64
   ecol[c] = (e == -32768 ? 0 : e) + nb;
 }
 
+// ---- first pass fed by the tensor memory accelerator
+// Row bits 0..7, FP64 A in, int64 tile out: the arithmetic and output of
+// k_wht_fx<4, 4, 0, 0, 16>.  A persistent CTA walks its tiles u = blockIdx.x,
+// + gridDim.x, ... (column tile fastest) through a 3-stage ring of 256-row x
+// 16-column boxes of A (and the tile's 256 signs of D) that TMA fills ahead,
+// so the loads of the next two tiles are in flight while the current one is
+// transformed; each stage also serves as its tile's exchange buffer.  The
+// one-tile-per-CTA kernel idles HBM while it transforms and stores.
+constexpr int P1_CW = 16, P1_ROWS = 256, P1_STAGES = 3;
+constexpr long long kP1Spin = 1ll << 24;
+struct P1Smem {
+  long long tile[P1_STAGES][P1_ROWS * P1_CW];  // 32 KB per stage
+  int8_t dseg[P1_STAGES][P1_ROWS];
+  int sx[16][P1_CW];
+  uint64_t full[P1_STAGES];
+  int ok;
+};
+
+__device__ __forceinline__ uint32_t p1_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool p1_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(256, 2) k_wht_p1_tma(const __grid_constant__ CUtensorMap ta, FxIn in, FxOut out,
+                                                       int64_t n_pad, int64_t ncols, int64_t nct, int64_t ntotal,
+                                                       int* err) {
+  constexpr int RB = 4, GB = 4, R = 1 << RB, G = 1 << GB, NB = RB + GB, CW = P1_CW, S = P1_STAGES;
+  extern __shared__ unsigned char p1_raw[];
+  P1Smem& sm = *reinterpret_cast<P1Smem*>(((uintptr_t)p1_raw + 127) & ~(uintptr_t)127);
+  const int c = threadIdx.x & (CW - 1), g = threadIdx.x / CW;
+  const int64_t gstride = gridDim.x;
+  const int64_t u0 = blockIdx.x;
+  const int64_t mine = u0 < ntotal ? (ntotal - u0 + gstride - 1) / gstride : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(p1_u32(&sm.full[s])), "r"(1u));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // thread 0: the k-th tile of this CTA into stage k % S
+  auto issue = [&](int64_t k) {
+    const int64_t u = u0 + k * gstride;
+    const int s = (int)(k % S);
+    const int64_t base = (u / nct) * P1_ROWS;
+    const uint32_t bar = p1_u32(&sm.full[s]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"((uint32_t)(P1_ROWS * CW * sizeof(long long) + P1_ROWS))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            p1_u32(sm.tile[s])),
+        "l"((uint64_t)&ta), "r"((int)((u % nct) * CW)), "r"((int)base), "r"(bar)
+        : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     p1_u32(sm.dseg[s])),
+                 "l"(in.D + base), "r"((uint32_t)P1_ROWS), "r"(bar)
+                 : "memory");
+  };
+  int64_t issued = 0;
+  if (threadIdx.x == 0)
+    for (; issued < mine && issued < S; ++issued) issue(issued);
+  bool bad = false;
+  int64_t k = 0;
+  for (; k < mine; ++k) {
+    const int s = (int)(k % S);
+    const uint32_t ph = (uint32_t)(k / S) & 1u;
+    const int64_t u = u0 + k * gstride;
+    const int64_t tile = u / nct;
+    const int64_t base = tile * P1_ROWS;
+    const int64_t col = (u % nct) * CW + c;
+    const bool cok = col < ncols;
+    if (threadIdx.x == 0) {
+      bool got = false;
+      for (long long i = 0; i < kP1Spin; ++i)
+        if (p1_try(p1_u32(&sm.full[s]), ph)) {
+          got = true;
+          break;
+        }
+      if (!got) atomicExch(err, 1);
+      sm.ok = got ? 1 : 0;
+    }
+    __syncthreads();
+    if (!sm.ok) break;
+    long long q[R];
+    int emax = -100000;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int rl = g + (t << GB);
+      const int64_t row = base + rl;
+      long long bits = 0;
+      if (col < in.d) bits = sm.tile[s][rl * CW + c];  // zero outside A (TMA fill)
+      else if (col == in.d && in.b && row < in.n) bits = __double_as_longlong(in.b[row]);
+      if (sm.dseg[s][rl] < 0) bits ^= (1ll << 63);
+      const int e = (int)((bits >> 52) & 0x7FF);
+      bad |= (e == 0x7FF);
+      emax = max(emax, e ? e : 1);
+      q[t] = bits;
+    }
+    sm.sx[g][c] = emax;
+    __syncthreads();
+    int E = sm.sx[0][c];
+#pragma unroll
+    for (int gg = 1; gg < G; ++gg) E = max(E, sm.sx[gg][c]);
+    constexpr int LIFT = 9 - NB;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const unsigned long long bits = (unsigned long long)q[t];
+      const int e = (int)((bits >> 52) & 0x7FF);
+      const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+      const int sh = E - (e ? e : 1);
+      const unsigned long long mq = sh > 63 ? 0ull : ((M << LIFT) >> sh);
+      q[t] = (bits >> 63) ? -(long long)mq : (long long)mq;
+    }
+    const int X = E - 1075 - LIFT;
+#pragma unroll
+    for (int h = 1; h < R; h <<= 1)
+#pragma unroll
+      for (int t = 0; t < R; ++t)
+        if (!(t & h)) {
+          const long long a = q[t], b = q[t + h];
+          q[t] = a + b;
+          q[t + h] = a - b;
+        }
+#pragma unroll
+    for (int t = 0; t < R; ++t) sm.tile[s][(g + (t << GB)) * CW + c] = q[t];
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < R; ++t) q[t] = sm.tile[s][((g << RB) + t) * CW + c];
+#pragma unroll
+    for (int h = 1; h < G; h <<= 1)
+#pragma unroll
+      for (int t = 0; t < R; ++t)
+        if (!(t & h)) {
+          const long long a = q[t], b = q[t + h];
+          q[t] = a + b;
+          q[t + h] = a - b;
+        }
+    __syncthreads();  // stage s is free again
+    if (threadIdx.x == 0 && issued < mine) issue(issued++);
+    if (cok) {
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const int64_t row = base + ((g << RB) + t);
+        if (row < n_pad) out.Q[row * out.ldq + col] = q[t];
+      }
+      if (g == 0) out.X[tile * out.ldx + col] = (int16_t)X;
+    }
+  }
+  if (threadIdx.x == 0) {
+    // after a timeout: let the copies still in flight land before leaving
+    for (int64_t kk = k; kk < issued; ++kk) {
+      const uint32_t bar = p1_u32(&sm.full[kk % S]);
+      const uint32_t ph = (uint32_t)(kk / S) & 1u;
+      for (long long i = 0; i < kP1Spin && !p1_try(bar, ph); ++i) {
+      }
+    }
+  }
+  if (bad && out.nonfinite) atomicOr(out.nonfinite, 1);
+}
+
 template <class TOUT>
 struct F32Out {
   float* Q;
@@ -294,7 +461,25 @@ ski_status launch_fx(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& i
                    : dim3((unsigned)ntiles, (unsigned)ski_cdiv(ncols, CT));
   const size_t smem = (size_t)(1 << nb) * CT * sizeof(long long);
   const int threads = CT << GB;
-  // the first pass (FP64 in) is latency-bound: 16-column tiles, four CTAs per SM
+  // the first pass (FP64 in) is latency-bound: fed by TMA when A's layout
+  // allows a tensor map (row stride a multiple of 16 bytes), else 16-column
+  // tiles at four CTAs per SM
+  if (IN == 0 && OUT == 0 && RB == 4 && GB == 4 && lo == 0 && in.err) {
+    CUtensorMap ta;
+    if (ski_tmap_f64_2d(&ta, in.A, in.n, in.d, in.lda, P1_ROWS, P1_CW)) {
+      const int64_t nct = ski_cdiv(ncols, P1_CW);
+      const int64_t ntotal = ski_cdiv(in.n, (int64_t)P1_ROWS) * nct;
+      int sms = 0, dev = 0;
+      SKI_CUDA_TRY(cudaGetDevice(&dev));
+      SKI_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      const size_t sm1 = sizeof(P1Smem) + 128;
+      SKI_CUDA_TRY(cudaFuncSetAttribute(k_wht_p1_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+      const unsigned grid1 = (unsigned)std::min<int64_t>(ntotal, 2ll * sms);
+      if (ntotal > 0) k_wht_p1_tma<<<grid1, 256, sm1, st>>>(ta, in, out, n_pad, ncols, nct, ntotal, in.err);
+      SKI_LAUNCH_CHECK();
+      return SKI_OK;
+    }
+  }
   if (IN == 0 && RB == 4 && GB == 4 && lo == 0) {
     constexpr int CW = 16;
     auto kfn = k_wht_fx<4, 4, IN, OUT, CW>;
@@ -352,7 +537,8 @@ ski_status launch_f32(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& 
 size_t ski_premix_ws_bytes(int64_t n, int64_t ncols, int64_t n_pad, int32_t dtype) {
   SkiArena ar{nullptr, 0, 0, true};
   const int64_t ldq = ski_round_up(ncols, CT);
-  ar.take<int8_t>(n);
+  ar.take<int8_t>(ski_round_up(n, 256));
+  ar.take<int>(1);
   ar.take<int>(1);
   if (dtype == SKI_F64) {
     ar.take<long long>(n_pad * ldq);
@@ -368,14 +554,16 @@ size_t ski_premix_ws_bytes(int64_t n, int64_t ncols, int64_t n_pad, int32_t dtyp
 }
 
 ski_status ski_premix_plan(int64_t n, int64_t ncols_max, int64_t n_pad, int32_t dtype, uint64_t seed, SkiArena& ar,
-                           cudaStream_t st, SkiPremixPlan* pp) {
+                           cudaStream_t st, SkiPremixPlan* pp, int* err_flag) {
   SkiPremixPlan& P = *pp;
   P.n = n;
   P.n_pad = n_pad;
   P.dtype = dtype;
   P.ldq = ski_round_up(ncols_max, CT);
-  P.D = ar.take<int8_t>(n);
+  P.D = ar.take<int8_t>(ski_round_up(n, 256));  // padded: the TMA pass copies 256 signs per tile
   P.nonfinite = ar.take<int>(1);
+  int* own_err = ar.take<int>(1);
+  P.err = err_flag ? err_flag : own_err;
   P.L = ilog2(n_pad);
   plan_passes(P.L, P.nbs, &P.P);
   P.residual_scale = (P.L & 1) ? 0.70710678118654752440 : 1.0;
@@ -394,7 +582,9 @@ ski_status ski_premix_plan(int64_t n, int64_t ncols_max, int64_t n_pad, int32_t 
   }
   if (!ar.ok() || !P.Qb) return SKI_ENOMEM;
   SKI_TRY(ski_premix_signs(seed, n, P.D, st));
+  if (ski_round_up(n, 256) > n) SKI_CUDA_TRY(cudaMemsetAsync(P.D + n, 0, ski_round_up(n, 256) - n, st));
   SKI_CUDA_TRY(cudaMemsetAsync(P.nonfinite, 0, sizeof(int), st));
+  if (!err_flag) SKI_CUDA_TRY(cudaMemsetAsync(P.err, 0, sizeof(int), st));
   return SKI_OK;
 }
 
@@ -461,7 +651,7 @@ ski_status ski_premix_cols_q(const SkiPremixPlan& P, const double* A, int64_t ld
   const int64_t ncols = d + (b != nullptr);
   if (ncols > P.ldq || P.dtype != SKI_F64) return SKI_EINVAL;
   FxIn in{};
-  in.A = A; in.lda = lda; in.n = P.n; in.d = d; in.b = b; in.D = P.D;
+  in.A = A; in.lda = lda; in.n = P.n; in.d = d; in.b = b; in.D = P.D; in.err = P.err;
   return premix_fx_passes(P, in, ncols, nullptr, 0, true, qo, st);
 }
 
@@ -471,7 +661,7 @@ ski_status ski_premix_cols(const SkiPremixPlan& P, const double* A, int64_t lda,
   if (ncols > P.ldq) return SKI_EINVAL;
   const int64_t n = P.n, n_pad = P.n_pad, ldq = P.ldq;
   FxIn in{};
-  in.A = A; in.lda = lda; in.n = n; in.d = d; in.b = b; in.D = P.D;
+  in.A = A; in.lda = lda; in.n = n; in.d = d; in.b = b; in.D = P.D; in.err = P.err;
   if (P.dtype == SKI_F64) {
     SKI_TRY(premix_fx_passes(P, in, ncols, Y, ldy, false, nullptr, st));
   } else {
