@@ -638,9 +638,11 @@ def run_batched(args, name):
     dbs = [torch.empty_like(b) for b in bs]
     stream = torch.cuda.current_stream()
 
+    prec = {} if args.batch_precision == "f64" else dict(sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32)
+
     def opts(streams):
         return pkg.ski_opts_default(m=-int(round(1000 * gamma)), s=1, seed=args.seed, tol=1e-10, tau_r=1e-10,
-                                    streams=streams)
+                                    streams=streams, **prec)
 
     wsz = {}
 
@@ -749,6 +751,7 @@ def run_batched(args, name):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": name, "problems": count, "gamma": gamma, "s": 1,
+                       "sketch_qr": args.batch_precision,
                        "streams": o_main.streams or "auto", "A_bytes": 8 * nA,
                        "l2": "inputs larger than L2 (%.1f GB)" % (8e-9 * nA),
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -791,6 +794,9 @@ def main():
     ap.add_argument("--premix-slab", type=int, default=0, help="premix column slab width (0 = full width)")
     ap.add_argument("--qr-mixed", default="f32", choices=["f32", "tf32"],
                     help="QR precision of the mixed solve: f32 (three TF32 passes) or tf32 (one)")
+    ap.add_argument("--batch-precision", default="f64", choices=["f64", "mixed"],
+                    help="batched workload: sketch and QR in FP64, or FP32 with three TF32 passes "
+                         "(LSQR, residuals and the acceptance test stay FP64 either way)")
     args = ap.parse_args()
     kind = WORKLOADS[args.workload][5]
     if args.impl == "reference":

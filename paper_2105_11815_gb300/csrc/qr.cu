@@ -313,7 +313,9 @@ __global__ void __launch_bounds__(32 * NW) k_panel_cluster(PanelArgs<T> a) {
   for (int s = 0; s <= a.w; ++s) {
     ClusterParts<T> parts{slots + ((s + 1) & 1) * PW, slots + (s & 1) * PW};
     panel_step_body<T, NW>(b, s, parts);
-    if (s < a.w) cl.sync();
+    // also after the last step, which still reads the other CTAs' partials:
+    // no CTA may leave (and release its shared memory) while a peer reads it
+    cl.sync();
   }
   __syncthreads();
   for (int c = warp; c < a.w; c += NW)
@@ -433,7 +435,7 @@ QrWs qr_dims(int64_t m, int64_t ncols) {
 
 template <class T>
 struct QrBufs {
-  T *Ct, *P, *V, *Vt, *partA, *partB, *tau, *pv, *pc, *Z, *Tm, *Bpt;
+  T *Ct, *P, *V, *V2, *Vt, *partA, *partB, *tau, *pv, *pc, *Z, *Tm, *Bpt;
   GridBar* gb;
   int* err;
 };
@@ -446,6 +448,7 @@ QrBufs<T> qr_carve(SkiArena& ar, int64_t m, int64_t ncols) {
   b.Ct = ar.take<T>(ncols * q.ldt);
   b.P = ar.take<T>(m * NB);
   b.V = ar.take<T>(m * NB);
+  b.V2 = ar.take<T>(m * NB);  // panels alternate: V of panel k is still read by its update
   b.Vt = ar.take<T>(NB * q.ldt);
   b.partA = ar.take<T>(q.ncta_max * PW);
   b.partB = ar.take<T>(q.ncta_max * PW);
@@ -524,10 +527,66 @@ struct GemmTimer {
   }
 };
 
+// Look-ahead (two streams): panel k's trailing update is split into the next
+// panel's 32 columns (on the high-priority stream, right before that panel)
+// and the rest (on the low-priority stream), so panel k + 1 -- latency-bound,
+// one barrier per column -- runs while the bulk of update k is in flight, and
+// freed SMs go to the panel's CTAs first.  The two streams belong to the host
+// thread (created once per thread and device) and join the caller's stream
+// at both ends of the factorisation.
+struct QrStreams {
+  cudaStream_t hi = nullptr, lo = nullptr;
+  cudaEvent_t e_start = nullptr, e_upd = nullptr, e_lo = nullptr, e_done = nullptr;
+  int dev = -1;
+  bool ok = false;
+  ~QrStreams() {
+    if (e_start) cudaEventDestroy(e_start);
+    if (e_upd) cudaEventDestroy(e_upd);
+    if (e_lo) cudaEventDestroy(e_lo);
+    if (e_done) cudaEventDestroy(e_done);
+    if (hi) cudaStreamDestroy(hi);
+    if (lo) cudaStreamDestroy(lo);
+  }
+};
+
+QrStreams* qr_streams() {
+  static thread_local QrStreams s[8];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 8) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  QrStreams& q = s[dev];
+  if (!q.ok && q.dev != dev) {
+    q.dev = dev;
+    int least = 0, greatest = 0;
+    q.ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+           cudaStreamCreateWithPriority(&q.hi, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+           cudaStreamCreateWithPriority(&q.lo, cudaStreamNonBlocking, least) == cudaSuccess &&
+           cudaEventCreateWithFlags(&q.e_start, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&q.e_upd, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&q.e_lo, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&q.e_done, cudaEventDisableTiming) == cudaSuccess;
+    if (!q.ok) cudaGetLastError();
+  }
+  return q.ok ? &q : nullptr;
+}
+
 template <class T>
 ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, double* R, int64_t ldr, double* qtsb,
-                   SkiArena& ar, cudaStream_t st, double* gemm_ms, bool split3) {
+                   SkiArena& ar, cudaStream_t caller, double* gemm_ms, bool split3) {
   GemmTimer timer(gemm_ms != nullptr);
+  // main sequence on the high-priority stream (or the caller's if the
+  // auxiliary streams are unavailable), the bulk of each update on the low one
+  QrStreams* qs = qr_streams();
+  cudaStream_t st = caller, st_lo = caller;
+  if (qs) {
+    SKI_CUDA_TRY(cudaEventRecord(qs->e_start, caller));
+    SKI_CUDA_TRY(cudaStreamWaitEvent(qs->hi, qs->e_start, 0));
+    st = qs->hi;
+    st_lo = qs->lo;
+  }
+  bool pending_lo = false;  // an update still running on st_lo
   const int64_t ncols = d + (with_rhs ? 1 : 0);
   const QrWs q = qr_dims(m, ncols);
   QrBufs<T> bf = qr_carve<T>(ar, m, ncols);
@@ -600,7 +659,8 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     if (use_coop) ncta = ncta_coop;
     const int64_t rows_per = ski_cdiv(mr, ncta);
     T* Ctp = bf.Ct + k0 * ldt + k0;
-    PanelArgs<T> pa{bf.P, NB, mr, w, rows_per, ncta, nullptr, nullptr, bf.tau, bf.V, bf.Vt, ldt, Ctp, ldt};
+    T* Vk = ((k0 / NB) & 1) ? bf.V2 : bf.V;
+    PanelArgs<T> pa{bf.P, NB, mr, w, rows_per, ncta, nullptr, nullptr, bf.tau, Vk, bf.Vt, ldt, Ctp, ldt};
     bool done_panel = false;
     if (cluster_ok) {
       // one cluster of CL CTAs: the slab of each must fit in shared memory
@@ -659,6 +719,10 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     // V^T V (split-K over rows) and W = V^T C
     const int sv = (int)std::min<int64_t>(152, ski_cdiv(mr, 64));
     SKI_TRY(ski_gemm_ex<T>(NB, NB, mr, T(1), bf.Vt, ldt, 1, bf.Vt, 1, ldt, T(0), bf.pv, NB, sv, (int64_t)NB * NB, st));
+    if (pending_lo) {  // W reads every trailing column: the previous update must be done
+      SKI_CUDA_TRY(cudaStreamWaitEvent(st, qs->e_lo, 0));
+      pending_lo = false;
+    }
     int sc = 1;
     if (nct > 0) {
       const int64_t tiles = ski_cdiv(nct, 128);
@@ -676,13 +740,31 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     if (nct > 0) {
       k_ttw<T><<<ski_cdiv(nct, 128), 128, 0, st>>>(w, nct, bf.Z, NB + q.ldz, bf.Tm, bf.Bpt);
       SKI_LAUNCH_CHECK();
+      // the next panel's columns first (high priority), the rest alongside it;
+      // below ~4M updated elements the split costs more than it overlaps
+      const int64_t na = (qs && nct > NB && mr * (nct - NB) >= (1ll << 22)) ? NB : nct;
+      if (na < nct) {
+        SKI_CUDA_TRY(cudaEventRecord(qs->e_upd, st));
+        SKI_CUDA_TRY(cudaStreamWaitEvent(st_lo, qs->e_upd, 0));
+        timer.mark(st_lo);
+        SKI_TRY(gemm_update<T>(nct - na, mr, bf.Bpt + na * NB, Vk, Ctr + na * ldt, ldt, bf.err, st_lo, split3));
+        timer.mark(st_lo);
+        SKI_CUDA_TRY(cudaEventRecord(qs->e_lo, st_lo));
+        pending_lo = true;
+      }
       timer.mark(st);
-      SKI_TRY(gemm_update<T>(nct, mr, bf.Bpt, bf.V, Ctr, ldt, bf.err, st, split3));
+      SKI_TRY(gemm_update<T>(na, mr, bf.Bpt, Vk, Ctr, ldt, bf.err, st, split3));
       timer.mark(st);
     }
   }
+  if (pending_lo) SKI_CUDA_TRY(cudaStreamWaitEvent(st, qs->e_lo, 0));
   k_extract_r<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, bf.Ct, ldt, with_rhs, R, ldr, qtsb);
   SKI_LAUNCH_CHECK();
+  if (qs) {
+    SKI_CUDA_TRY(cudaEventRecord(qs->e_done, st));
+    SKI_CUDA_TRY(cudaStreamWaitEvent(caller, qs->e_done, 0));
+    st = caller;
+  }
   {
     GridBar h;
     int e = 0;

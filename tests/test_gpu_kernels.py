@@ -113,8 +113,11 @@ def test_csr_sketch_fp64():
     assert rel_fro(SA32[:, :301].double().cpu().numpy(), want2) <= 1e-6
 
 
+# (40000, 34) and (20000, 34): the TMA-fed first pass (even row stride); odd
+# strides take the one-tile-per-CTA kernel
 @pytest.mark.parametrize("n,d,npad", [(3000, 7, 4096), (20000, 33, 32768), (1, 3, 1), (2, 2, 2), (700, 5, 1024),
-                                      (130000, 3, 262144)])
+                                      (130000, 3, 262144), (20000, 34, 32768), (40000, 34, 65536),
+                                      (40000, 35, 65536)])
 def test_premix_fp64(n, d, npad):
     torch, pkg = cuda()
     A, b, _ = workloads.gaussian_lls(n, d, seed=n)

@@ -181,10 +181,14 @@ def test_batched_matches_single():
             assert torch.equal(xw[i], xs[i])
 
 
-def test_batched_concurrent_runs_are_identical():
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batched_concurrent_runs_are_identical(mixed):
     # many problems in flight on few streams, repeated: every run must give the
-    # same bits (a cross-CTA race on the LSQR scalars once showed up only here)
+    # same bits (a cross-CTA race on the LSQR scalars once showed up only here;
+    # the mixed form runs the FP32 cluster panels and tensor-core GEMMs of
+    # several problems at once)
     torch, pkg = cuda()
+    prec = dict(sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32) if mixed else {}
     shapes = workloads.ragged_batch(12, seed=19, n_lo=600, n_hi=4000, d_lo=8, d_hi=150)
     At, bt = [], []
     for i, (n, d) in enumerate(shapes):
@@ -194,7 +198,8 @@ def test_batched_concurrent_runs_are_identical():
     mats = [pkg.dense_matrix(a) for a in At]
     ref = None
     for rep in range(8):
-        o = pkg.ski_opts_default(m=-2000, s=1, seed=70, tol=1e-10, tau_r=1e-12, streams=(3 if rep % 2 else 5))
+        o = pkg.ski_opts_default(m=-2000, s=1, seed=70, tol=1e-10, tau_r=1e-12, streams=(3 if rep % 2 else 5),
+                                 **prec)
         xs = [torch.empty(d, dtype=torch.float64, device="cuda") for _, d in shapes]
         infos = pkg.ski_solve_batched(mats, bt, o, xs)
         got = ([x.clone() for x in xs], [i.iters for i in infos])
