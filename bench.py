@@ -768,6 +768,54 @@ def run_batched(args, name):
             "gpu_launches": int(launches)}), flush=True)
 
 
+def run_sketch_sweep(args):
+    """The dense test-set sketch cases: d in {4000, 7000}, i.i.d. or high
+    coherence, s in {1, 2}, gamma in {1.5, 2, 3, 4}, premix to 65536 (FP64).
+    One JSON line per case: ski_sketch_hash on device-resident A, CUDA events
+    over `steps` calls after `warmup`."""
+    import torch
+
+    import paper_2105_11815_gb300 as pkg
+    from paper_2105_11815_gb300 import build, workloads
+    build.build()
+    pkg.lib()
+    n, npad = 50000, 65536
+    hbm, peak_kind, _ = peaks()
+    stream = torch.cuda.current_stream()
+    for d in (4000, 7000):
+        for kind in ("gauss", "coh"):
+            if kind == "gauss":
+                A, b = workloads.gaussian_torch(n, d, args.seed, "cuda")
+            else:
+                A, b = workloads.dense_high_coherence_torch(n, d, args.seed, "cuda")
+            mat = pkg.dense_matrix(A)
+            for s in (1, 2):
+                for gamma in (1.5, 2.0, 3.0, 4.0):
+                    m = int(round(gamma * d))
+                    o = pkg.ski_opts_default(m=m, s=s, seed=args.seed, premix=1, n_pad=npad)
+                    SA = torch.empty(m, d + 1, dtype=torch.float64, device="cuda")
+                    ws = torch.empty(pkg.ski_sketch_workspace_size(mat, 1, o), dtype=torch.uint8, device="cuda")
+                    for _ in range(args.warmup):
+                        pkg.ski_sketch_hash(mat, b, o, SA, d + 1, ws=ws)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    for _ in range(args.steps):
+                        pkg.ski_sketch_hash(mat, b, o, SA, d + 1, ws=ws)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / args.steps
+                    byt = 8.0 * (n * d + n + m * (d + 1))
+                    print(json.dumps({"metric": "sketch S·A GB/s (premix + hash, FP64)", "value": byt / (ms * 1e-3) / 1e9,
+                                      "unit": "GB/s", "ms": ms, "hbm_frac": byt / (ms * 1e-3) / 1e9 / hbm,
+                                      "peak_source": peak_kind, "config": {"n": n, "d": d, "A": kind, "s": s,
+                                                                           "gamma": gamma, "m": m, "n_pad": npad}}),
+                          flush=True)
+                    del SA, ws
+            del A, b, mat
+            torch.cuda.empty_cache()
+
+
 def qr_gemm_flops(m, d):
     """Flops of the QR trailing-update GEMMs, summed over the 32-column panels:
     W = V^T C and C -= V B' each cost 2 w nct mr."""
@@ -794,10 +842,15 @@ def main():
     ap.add_argument("--premix-slab", type=int, default=0, help="premix column slab width (0 = full width)")
     ap.add_argument("--qr-mixed", default="f32", choices=["f32", "tf32"],
                     help="QR precision of the mixed solve: f32 (three TF32 passes) or tf32 (one)")
+    ap.add_argument("--sketch-sweep", action="store_true",
+                    help="time the sketch alone on the 32 dense test-set cases (one JSON line each)")
     ap.add_argument("--batch-precision", default="f64", choices=["f64", "mixed"],
                     help="batched workload: sketch and QR in FP64, or FP32 with three TF32 passes "
                          "(LSQR, residuals and the acceptance test stay FP64 either way)")
     args = ap.parse_args()
+    if args.sketch_sweep:
+        run_sketch_sweep(args)
+        return
     kind = WORKLOADS[args.workload][5]
     if args.impl == "reference":
         if kind == "csr":

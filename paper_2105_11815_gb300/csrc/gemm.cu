@@ -15,15 +15,20 @@ template <class T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(
     int64_t M, int64_t N, int64_t K, int64_t kchunk, T alpha, const T* __restrict__ A, int64_t sa_m,
     int64_t sa_k, const T* __restrict__ B, int64_t sb_k, int64_t sb_n, T beta, T* __restrict__ C, int64_t ldc,
-    int64_t c_zstride, int tri) {
+    int64_t c_zstride, int tri, int64_t a_zstride, int64_t b_zstride) {
   constexpr int NT = (BM / TM) * (BN / TN);
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
   const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
-  int64_t kbeg = (int64_t)blockIdx.z * kchunk;
-  int64_t kend = min(K, kbeg + kchunk);
+  // z: a K split (a_zstride = b_zstride = 0) or a batch of independent
+  // products whose operands sit a_zstride / b_zstride elements apart
+  const bool batch = a_zstride != 0 || b_zstride != 0;
+  int64_t kbeg = batch ? 0 : (int64_t)blockIdx.z * kchunk;
+  int64_t kend = batch ? K : min(K, kbeg + kchunk);
+  A += (int64_t)blockIdx.z * a_zstride;
+  B += (int64_t)blockIdx.z * b_zstride;
   // tri bit 0: A upper triangular (A[i,k] = 0 for k < i); bit 1: B upper
   // triangular (B[k,j] = 0 for k > j).  Skip the k-range that is all zero.
   if (tri & 1) kbeg = max(kbeg, m0 - (m0 % BK));
@@ -93,15 +98,44 @@ ski_status ski_gemm_ex(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int
   if (M <= 32) {
     dim3 grid((unsigned)ski_cdiv(N, 64), (unsigned)ski_cdiv(M, 32), (unsigned)splits);
     k_gemm<T, 32, 64, BK, 2, 4><<<grid, 256, 0, st>>>(M, N, K, kchunk, alpha, A, sa_m, sa_k, B, sb_k, sb_n, beta,
-                                                      C, ldc, c_zstride, tri);
+                                                      C, ldc, c_zstride, tri, 0, 0);
   } else {
     dim3 grid((unsigned)ski_cdiv(N, 64), (unsigned)ski_cdiv(M, 64), (unsigned)splits);
     k_gemm<T, 64, 64, BK, 4, 4><<<grid, 256, 0, st>>>(M, N, K, kchunk, alpha, A, sa_m, sa_k, B, sb_k, sb_n, beta,
-                                                      C, ldc, c_zstride, tri);
+                                                      C, ldc, c_zstride, tri, 0, 0);
   }
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }
+
+// `batch` independent products C_z = beta C_z + alpha op(A_z) op(B_z) with the
+// operands of product z at A + z a_zs, B + z b_zs, C + z c_zs (one launch).
+template <class T>
+ski_status ski_gemm_batched(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t sa_m, int64_t sa_k,
+                            int64_t a_zs, const T* B, int64_t sb_k, int64_t sb_n, int64_t b_zs, T beta, T* C,
+                            int64_t ldc, int64_t c_zs, int64_t batch, int tri, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || batch <= 0) return SKI_OK;
+  if (batch > 65535 || (a_zs == 0 && b_zs == 0 && batch > 1)) return SKI_EINVAL;
+  constexpr int BK = 16;
+  const int64_t kchunk = ski_round_up(K > 0 ? K : 1, BK);
+  if (M <= 32) {
+    dim3 grid((unsigned)ski_cdiv(N, 64), (unsigned)ski_cdiv(M, 32), (unsigned)batch);
+    k_gemm<T, 32, 64, BK, 2, 4><<<grid, 256, 0, st>>>(M, N, K, kchunk, alpha, A, sa_m, sa_k, B, sb_k, sb_n, beta,
+                                                      C, ldc, c_zs, tri, a_zs, b_zs);
+  } else {
+    dim3 grid((unsigned)ski_cdiv(N, 64), (unsigned)ski_cdiv(M, 64), (unsigned)batch);
+    k_gemm<T, 64, 64, BK, 4, 4><<<grid, 256, 0, st>>>(M, N, K, kchunk, alpha, A, sa_m, sa_k, B, sb_k, sb_n, beta,
+                                                      C, ldc, c_zs, tri, a_zs, b_zs);
+  }
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+template ski_status ski_gemm_batched<double>(int64_t, int64_t, int64_t, double, const double*, int64_t, int64_t,
+                                             int64_t, const double*, int64_t, int64_t, int64_t, double, double*,
+                                             int64_t, int64_t, int64_t, int, cudaStream_t);
+template ski_status ski_gemm_batched<float>(int64_t, int64_t, int64_t, float, const float*, int64_t, int64_t, int64_t,
+                                            const float*, int64_t, int64_t, int64_t, float, float*, int64_t, int64_t,
+                                            int64_t, int, cudaStream_t);
 
 template <class T>
 ski_status ski_gemm(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t sa_m, int64_t sa_k,

@@ -114,5 +114,9 @@ ski_status ski_gemm_ex(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int
                        const T* B, int64_t sb_k, int64_t sb_n, T beta, T* C, int64_t ldc, int splits,
                        int64_t c_zstride, cudaStream_t st, int tri = 0);
 template <class T>
+ski_status ski_gemm_batched(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t sa_m, int64_t sa_k,
+                            int64_t a_zs, const T* B, int64_t sb_k, int64_t sb_n, int64_t b_zs, T beta, T* C,
+                            int64_t ldc, int64_t c_zs, int64_t batch, int tri, cudaStream_t st);
+template <class T>
 ski_status ski_gemm_tri(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t sa_m, int64_t sa_k,
                         const T* B, int64_t sb_k, int64_t sb_n, T beta, T* C, int64_t ldc, int tri, cudaStream_t st);

@@ -1,10 +1,10 @@
 // R^{-1} for the upper-triangular factor of Step 2, formed once so that the
 // two preconditioner applications per LSQR iteration (R^{-1} v, R^{-T} u) are
 // bandwidth-bound triangular matrix-vector products instead of
-// latency-bound back-substitutions.  Recursive 2x2 blocking:
+// latency-bound back-substitutions.  2x2 blocking,
 //   [R11 R12; 0 R22]^{-1} = [X11, -X11 R12 X22; 0, X22],  X11 = R11^{-1}, X22 = R22^{-1},
 // with all 32 x 32 diagonal blocks inverted by back-substitution in one launch
-// and the off-diagonal blocks formed by GEMMs (gemm.cu).  With perturb > 0
+// and the off-diagonal blocks formed level by level by batched GEMMs (gemm.cu).  With perturb > 0
 // each diagonal entry r_ii is replaced by r_ii + perturb (the perturbed
 // back-solve of Ski-LLS-sparse).
 #include "common.cuh"
@@ -64,21 +64,35 @@ __global__ void k_emit(int64_t d, const T* __restrict__ X, int64_t ldx, double* 
   if (Mt) Mt[c * ldm + i] = v;
 }
 
-// Off-diagonal blocks, bottom-up over the recursion tree.
+// Off-diagonal blocks, bottom-up by doubling: after the level of block size
+// b every aligned block [k 2b, (k+1) 2b) (and the tail) holds its inverse,
+// formed from its two halves as X12 = -X11 (R12 X22).  All full-size nodes of
+// a level are independent and go to one batched GEMM pair; a ragged tail node
+// (right half shorter than b) takes one more pair.  Eight launches per
+// doubling instead of two per node of a recursion tree.
 template <class T>
-ski_status rec(int64_t o, int64_t n, const T* R, int64_t ldr, T* X, int64_t ldx, T* tmp, cudaStream_t st) {
-  if (n <= LB) return SKI_OK;
-  int64_t n1 = ski_round_up(n / 2, LB);
-  int64_t n2 = n - n1;
-  SKI_TRY(rec<T>(o, n1, R, ldr, X, ldx, tmp, st));
-  SKI_TRY(rec<T>(o + n1, n2, R, ldr, X, ldx, tmp, st));
-  // tmp = R12 X22 (n1 x n2), X22 upper triangular: K = n2
-  const T* R12 = R + o * ldr + o + n1;
-  const T* X22 = X + (o + n1) * ldx + o + n1;
-  const T* X11 = X + o * ldx + o;
-  T* X12 = X + o * ldx + o + n1;
-  SKI_TRY(ski_gemm_tri<T>(n1, n2, n2, T(1), R12, ldr, 1, X22, ldx, 1, T(0), tmp, n2, 2, st));
-  SKI_TRY(ski_gemm_tri<T>(n1, n2, n1, T(-1), X11, ldx, 1, tmp, n2, 1, T(0), X12, ldx, 1, st));
+ski_status levels(int64_t d, const T* R, int64_t ldr, T* X, int64_t ldx, T* tmp, cudaStream_t st) {
+  for (int64_t b = LB; b < d; b *= 2) {
+    const int64_t nfull = d / (2 * b);
+    if (nfull > 0) {
+      // node i: left block at o = 2 b i, right block at o + b, both of size b
+      const int64_t zr = 2 * b * (ldr + 1), zx = 2 * b * (ldx + 1);
+      SKI_TRY(ski_gemm_batched<T>(b, b, b, T(1), R + b, ldr, 1, zr, X + b * ldx + b, ldx, 1, zx, T(0), tmp, b, b * b,
+                                  nfull, 2, st));
+      SKI_TRY(ski_gemm_batched<T>(b, b, b, T(-1), X, ldx, 1, zx, tmp, b, 1, b * b, T(0), X + b, ldx, zx, nfull, 1,
+                                  st));
+    }
+    const int64_t o = 2 * b * nfull;
+    const int64_t n2 = d - o - b;
+    if (n2 > 0) {
+      const T* R12 = R + o * ldr + o + b;
+      const T* X22 = X + (o + b) * ldx + o + b;
+      const T* X11 = X + o * ldx + o;
+      T* X12 = X + o * ldx + o + b;
+      SKI_TRY(ski_gemm_tri<T>(b, n2, n2, T(1), R12, ldr, 1, X22, ldx, 1, T(0), tmp, n2, 2, st));
+      SKI_TRY(ski_gemm_tri<T>(b, n2, b, T(-1), X11, ldx, 1, tmp, n2, 1, T(0), X12, ldx, 1, st));
+    }
+  }
   return SKI_OK;
 }
 
@@ -94,7 +108,7 @@ ski_status trinv_impl(int64_t d, const double* R, int64_t ldr, double* M, double
   SKI_LAUNCH_CHECK();
   k_diag_inv<T><<<ski_cdiv(d, LB), 32, 0, st>>>(d, Rt, d, X, d, perturb);
   SKI_LAUNCH_CHECK();
-  SKI_TRY(rec<T>(0, d, Rt, d, X, d, tmp, st));
+  SKI_TRY(levels<T>(d, Rt, d, X, d, tmp, st));
   k_emit<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, X, d, M, Mt, ldm);
   SKI_LAUNCH_CHECK();
   return SKI_OK;

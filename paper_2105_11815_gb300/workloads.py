@@ -123,6 +123,17 @@ def gaussian_torch(n, d, seed, device):
     return A, torch.ones(n, dtype=torch.float64, device=device)
 
 
+def dense_high_coherence_torch(n, d, seed, device, big=1e3, small_sd=1e-3):
+    """`dense_high_coherence` drawn on `device` with torch's seeded generator."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    A = torch.randn(n, d, generator=g, device=device, dtype=torch.float64)
+    A[:d] = big * torch.eye(d, device=device, dtype=torch.float64) + small_sd * torch.randn(
+        d, d, generator=g, device=device, dtype=torch.float64)
+    return A, torch.ones(n, dtype=torch.float64, device=device)
+
+
 def usv_torch(n, d, kappa, seed, device):
     """A = U diag(sigma) V^T with Haar U (n x d), V (d x d) (QR of a Gaussian,
     diag(R) made positive), sigma_i = kappa^{-(i-1)/(d-1)}; b = ones."""
