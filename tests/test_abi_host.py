@@ -73,6 +73,17 @@ def test_argument_errors_before_launch(lib):
     prem2 = lib.ski_opts_default(m=20, s=1, premix=1)
     assert L.ski_sketch_workspace_size(ctypes.byref(csr), 1, ctypes.byref(prem2)) == 0  # premix is dense-only
     assert L.ski_precondition(10, 20, 1, x, 21, 0, x, 20, None, None, None, x, 1 << 30, None) == 1  # m < d
+    # dense width above the LSQR pass's limit (8192 columns), negative options
+    wide = _fake_dense(lib, 20000, 8193)
+    ow = lib.ski_opts_default(m=16386, s=1)
+    assert L.ski_solve(ctypes.byref(wide), x, ctypes.byref(ow), x, None, ctypes.byref(info), x, 1 << 40, None) == 1
+    assert L.ski_solve_adjoint(ctypes.byref(wide), x, x, x, 8193, x, x, 8193, x, ctypes.byref(ow), None, x, 1 << 40,
+                               None) == 1
+    for field, v in (("premix_slab", -1), ("streams", -1), ("s", 0), ("qr_dtype", 2), ("it_max", -1)):
+        o2 = lib.ski_opts_default(m=20, s=1)
+        setattr(o2, field, v)
+        assert L.ski_solve(ctypes.byref(A), x, ctypes.byref(o2), x, None, ctypes.byref(info), x, 1 << 40, None) == 1, \
+            field
 
 
 def test_workspace_queries_are_consistent(lib):

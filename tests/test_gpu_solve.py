@@ -113,6 +113,24 @@ def test_edge_shapes(n, d, m, s):
         _assert_solution(A, b, x, tol_x=1e-7)
 
 
+def test_widest_dense_problem():
+    # d = 8192, the widest dense A the LSQR pass takes (8 x 2 columns per
+    # thread of 512); mixed precision keeps the factorisation short
+    torch, pkg = cuda()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(8192)
+    n, d = 20000, 8192
+    At = torch.randn(n, d, generator=g, device="cuda", dtype=torch.float64)
+    bt = torch.randn(n, generator=g, device="cuda", dtype=torch.float64)
+    o = pkg.ski_opts_default(m=2 * d, s=1, seed=4, tol=1e-10, tau_r=1e-12, sketch_dtype=pkg.SKI_F32,
+                             qr_dtype=pkg.SKI_F32)
+    x = torch.empty(d, dtype=torch.float64, device="cuda")
+    info = pkg.ski_solve(pkg.dense_matrix(At), bt, o, x)
+    assert info.status == 0
+    A, b = At.cpu().numpy(), bt.cpu().numpy()
+    assert olsqr.residual_metric(A, b, x.cpu().numpy()) <= 1e-10
+
+
 def test_early_exit_on_consistent_system():
     torch, pkg = cuda()
     g = np.random.default_rng(0)
