@@ -71,11 +71,12 @@ FP64_PEAK_TFLOPS = 1.26
 FP32_PEAK_TFLOPS = 72.0
 # DRAM bytes (read + write) per launch from ncu for the current kernels
 # (profiles/hash_gather_and_premix_dense_50000x4000.md): the whole sketch stage
-# (both premix passes, the column-exponent bound, the bucket lists and the
-# hash gather) and the hash gather alone; None where not captured.
-SKETCH_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 1651373056 + 1558533120 + 1587456 + 1619061760 + 2044707840 +
-                  2425030400 + 236545536 + 805632}
-GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2425030400 + 236545536}
+# (bucket lists, both premix passes, the nonfinite scan, the column-unit
+# bound, the hash gather and the NaN post-pass) and the hash gather alone;
+# None where not captured.
+SKETCH_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 43264 + 44288 + 428288 + 332544 + 1672682496 + 1555713280 + 7680 +
+                  1598464 + 1618831616 + 2044199936 + 2424849664 + 236686848 + 20480}
+GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2424849664 + 236686848}
 
 
 class ClockSampler:

@@ -407,6 +407,14 @@ struct FxA {
   }
 };
 
+// Column c of SA (m rows) := NaN where nf[c] is set.
+__global__ void __launch_bounds__(256) k_poison_columns(double* __restrict__ SA, int64_t ld_sa, int64_t m,
+                                                        int64_t ncols, const int* __restrict__ nf) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols || !nf[c]) return;
+  for (int64_t i = 0; i < m; ++i) SA[i * ld_sa + c] = __longlong_as_double(0x7FF8000000000000ll);
+}
+
 // Hash gather over the column-aligned premix output (SkiPremixQ with ecol):
 // the layout and work split of k_sketch_dense_f64acc, with 8 addends per
 // renormalisation check and no per-addend exponent.
@@ -711,6 +719,9 @@ ski_status ski_gather_q(const SkiPremixQ& y, int64_t ncols, const SkiBuckets& bk
   else
     k_sketch_q_f64acc<<<grid, 128, 0, st>>>(y.Q, y.ldq, y.X, y.ldx, y.lo, y.nb, y.yshift, ncols, bk.offsets, bk.list,
                                              c, e, SA, ld_sa, bk.m);
+  SKI_LAUNCH_CHECK();
+  // the integer path cannot carry a NaN or Inf: columns flagged by the premix become NaN
+  k_poison_columns<<<(unsigned)ski_cdiv(ncols, 256), 256, 0, st>>>(SA, ld_sa, bk.m, ncols, y.nonfinite);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }

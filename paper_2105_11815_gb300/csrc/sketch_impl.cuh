@@ -50,7 +50,7 @@ struct SkiPremixPlan {
   int nbs[8];
   double residual_scale;
   int8_t* D;
-  int* nonfinite;
+  int* nonfinite;  // [ldq + 1]: per column, set when the column holds a NaN or Inf; then any column
   int* err;  // set when a bounded wait of the TMA-fed pass gave up
   void *Qa, *Qb;
   int16_t *Xa, *Xb;
@@ -71,6 +71,7 @@ ski_status ski_premix_cols(const SkiPremixPlan& plan, const double* A, int64_t l
 // 2^(ecol[c] + headroom - yshift).
 struct SkiPremixQ {
   const long long* Q;
+  const int* nonfinite;  // per column: the column's sketch is NaN
   const int16_t* X;
   const int* ecol;
   int headroom;

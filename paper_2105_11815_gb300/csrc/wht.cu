@@ -48,6 +48,7 @@ struct FxIn {
   const int16_t* X;
   int64_t ldq, ldx, nvalid;
   int lo_p, nb_p;
+  const int* nf;  // per-column nonfinite flags of the first pass
 };
 struct FxOut {
   long long* Q;
@@ -56,15 +57,18 @@ struct FxOut {
   double* Y;
   int64_t ldy;
   int yshift;
-  int* nonfinite;
+  int* nf;          // per column: set when the column holds a NaN or Inf
+  int* nf_any;      // TMA-fed first pass: set when any column does (then a scan sets nf)
   const int* ecol;  // OUT == 2: per-column exponent all tiles are aligned to
 };
 
 // OUT == 2 (last pass feeding the hash gather): values are stored as
 // q >> (ecol[c] - X + kAlignHeadroom), i.e. in units of 2^(ecol[c] + headroom)
 // shared by the whole column, so the gather sums them with plain int64 adds;
-// |q| < 2^62 becomes < 2^55, leaving room for 2^6 addends between renorms.
+// outputs below 2^(ecol[c] + 62) become < 2^55, leaving room for 2^6 addends
+// between renorms.
 constexpr int kAlignHeadroom = 7;
+constexpr int kZeroTile = -32768;  // exponent of an all-zero tile column
 
 // CW: columns per tile (32, or 16 for twice the CTAs per SM where the pass is
 // latency-bound).
@@ -84,7 +88,6 @@ __global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4
   long long q[R];
   int xsrc[IN == 1 ? R : 1];
   int emax = -100000;
-  bool bad = false;
   if (IN == 0) {
 #pragma unroll
     for (int t = 0; t < R; ++t) {
@@ -95,7 +98,6 @@ __global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4
         if (in.D[row] < 0) bits ^= (1ll << 63);  // D_jj = -1: flip the sign bit (no FP64 op)
       }
       int e = (int)((bits >> 52) & 0x7FF);
-      bad |= (e == 0x7FF);
       emax = max(emax, e ? e : 1);
       q[t] = bits;
     }
@@ -114,12 +116,17 @@ __global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4
       emax = max(emax, xsrc[t]);
     }
   }
-  if (bad && out.nonfinite) atomicOr(out.nonfinite, 1);
   sx[g][c] = emax;
   __syncthreads();
   int E = sx[0][c];
 #pragma unroll
   for (int gg = 1; gg < G; ++gg) E = max(E, sx[gg][c]);
+  // a NaN or Inf in the tile column: the largest exponent field is all ones
+  if (IN == 0 && g == 0 && cok && E == 0x7FF && out.nf) atomicOr(&out.nf[col], 1);
+  // OUT == 1: a column with a NaN or Inf becomes NaN.  With one pass (IN == 0)
+  // the tile is the whole column and E its largest exponent field.
+  bool colbad = false;
+  if (OUT == 1) colbad = IN == 0 ? (E == 0x7FF) : (cok && in.nf && in.nf[col] != 0);
   int X;  // value = q * 2^X after quantisation
   if (IN == 0) {
     constexpr int LIFT = 9 - NB;  // |q| < 2^(62 - NB) before the NB levels
@@ -134,13 +141,19 @@ __global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4
     }
     X = E - 1075 - LIFT;
   } else {
-    if (E == -32768) E = 0;
+    const bool zero = E == -32768;  // all-zero tile column
+    if (zero) E = 0;
+    // units 2^Xq: NB bits of headroom for the levels, or (OUT == 2) at most
+    // the column's output unit 2^(ecol + headroom) -- the family bound keeps
+    // every partial sum below 2^(ecol + 62) -- so the output shift is >= 0
+    int Xq = E + NB;
+    if (OUT == 2 && cok && !zero) Xq = min(Xq, out.ecol[col] + kAlignHeadroom);
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      int sh = E - xsrc[IN == 1 ? t : 0] + NB;
+      int sh = Xq - xsrc[IN == 1 ? t : 0];
       q[t] = (q[t] == 0 || sh > 63) ? 0 : (q[t] >> sh);
     }
-    X = E + NB;
+    X = zero ? kZeroTile : Xq;
   }
   // RB levels in registers: row bits [GB, GB+RB) of the tile index
 #pragma unroll
@@ -172,7 +185,7 @@ __global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4
     }
   }
   if (!cok) return;
-  int ash = 0;
+  int ash = 0;  // OUT == 2: to units of 2^(ecol + headroom); X <= ecol + headroom
   if (OUT == 2) ash = max(0, min(63, out.ecol[col] - X + kAlignHeadroom));
 #pragma unroll
   for (int t = 0; t < R; ++t) {
@@ -183,21 +196,65 @@ __global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4
     } else if (OUT == 2) {
       out.Q[row * out.ldq + col] = q[t] >> ash;
     } else {
-      out.Y[row * out.ldy + col] = fx_to_double(q[t], X - out.yshift + 1075 + FX_LIFT, 0);
+      out.Y[row * out.ldy + col] =
+          colbad ? __longlong_as_double(0x7FF8000000000000ll) : fx_to_double(q[t], X - out.yshift + 1075 + FX_LIFT, 0);
     }
   }
   if (OUT == 0 && g == 0) out.X[tile * out.ldx + col] = (int16_t)X;
 }
 
-// ecol[c] = max over the first ntiles tiles of X[t][c], plus nb: an upper bound
-// of the exponent X that the next pass (nb levels) gives any tile of column c.
-__global__ void k_colmax_exp(int64_t ncols, const int16_t* __restrict__ X, int64_t ldx, int64_t ntiles, int nb,
-                             int* __restrict__ ecol) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= ncols) return;
-  int e = -32768;
-  for (int64_t tt = 0; tt < ntiles; ++tt) e = max(e, (int)X[tt * ldx + c]);
-  ecol[c] = (e == -32768 ? 0 : e) + nb;
+// ecol[c]: an exponent with every output of the next (last) pass in column c
+// below 2^(ecol[c] + 62).  An output of that pass sums one row from each of
+// 2^nb tiles of the previous pass -- the tiles t = f + k 2^lo_p of one family
+// f (the row's bits below lo_p) -- and tile t's values are below
+// 2^(X[t][c] + 62).  So 2^ecol[c] = max over families of the sum of 2^X[t][c]
+// bounds them; rounded up to a power of two in exact integer arithmetic
+// (units of 2^-30 relative to the largest X, tiny terms counted as one unit;
+// at most 2^24 tiles).  The plain max + nb bound would give up nb bits where
+// one tile dominates a column (a coherent row of A).
+// CTA: 32 columns x 8 lanes over the tiles (one family) or the families.
+__global__ void __launch_bounds__(256) k_colmax_exp(int64_t ncols, const int16_t* __restrict__ X, int64_t ldx,
+                                                    int64_t ntiles, int lo_p, int* __restrict__ ecol) {
+  constexpr int LN = 8, FRAC = 30;
+  __shared__ int se[LN][32];
+  __shared__ unsigned long long ss[LN][32];
+  const int cl = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int64_t c = (int64_t)blockIdx.x * 32 + cl;
+  const bool ok = c < ncols;
+  int e = kZeroTile;
+  if (ok)
+    for (int64_t tt = r; tt < ntiles; tt += LN) e = max(e, (int)X[tt * ldx + c]);
+  se[r][cl] = e;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < LN; ++k) e = max(e, se[k][cl]);
+  const int64_t fam = 1ll << lo_p;
+  auto term = [&](int x) -> unsigned long long {
+    if (x == kZeroTile) return 0ull;
+    const int sh = x - e + FRAC;  // <= FRAC
+    return sh > 0 ? (1ull << sh) : 1ull;
+  };
+  unsigned long long v = 0;
+  if (ok && e != kZeroTile) {
+    if (fam == 1) {  // one family: partial sums over strided tiles
+      for (int64_t tt = r; tt < ntiles; tt += LN) v += term(X[tt * ldx + c]);
+    } else {  // several: whole families per lane
+      for (int64_t f = r; f < fam && f < ntiles; f += LN) {
+        unsigned long long s = 0;
+        for (int64_t tt = f; tt < ntiles; tt += fam) s += term(X[tt * ldx + c]);
+        v = max(v, s);
+      }
+    }
+  }
+  ss[r][cl] = v;
+  __syncthreads();
+  if (r != 0 || !ok) return;
+  unsigned long long best = 0;
+#pragma unroll
+  for (int k = 0; k < LN; ++k) best = fam == 1 ? best + ss[k][cl] : max(best, ss[k][cl]);
+  // all-zero column: every output is 0.  Else sum of 2^(X - e) <= best 2^-FRAC
+  // < 2^(bitlen(best) - FRAC)
+  ecol[c] = e == kZeroTile ? 0 : e + (64 - __clzll((long long)best)) - FRAC;
 }
 
 // ---- first pass fed by the tensor memory accelerator
@@ -363,7 +420,20 @@ __global__ void __launch_bounds__(256, 2) k_wht_p1_tma(const __grid_constant__ C
       }
     }
   }
-  if (bad && out.nonfinite) atomicOr(out.nonfinite, 1);
+  if (bad && out.nf_any) atomicOr(out.nf_any, 1);
+}
+
+// After the TMA-fed pass, only if it met a NaN or Inf: nf[c] for every
+// column c of [A b] that holds one.
+__global__ void __launch_bounds__(256) k_column_nonfinite(const double* __restrict__ A, int64_t lda, int64_t n,
+                                                          int64_t d, const double* __restrict__ b, int64_t ncols,
+                                                          const int* __restrict__ any, int* __restrict__ nf) {
+  if (*any == 0) return;
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x)
+    for (int64_t c = threadIdx.x; c < ncols; c += blockDim.x) {
+      const long long bits = __double_as_longlong(c < d ? A[j * lda + c] : b[j]);
+      if (((bits >> 52) & 0x7FF) == 0x7FF) atomicOr(&nf[c], 1);
+    }
 }
 
 template <class TOUT>
@@ -477,6 +547,11 @@ ski_status launch_fx(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& i
       const unsigned grid1 = (unsigned)std::min<int64_t>(ntotal, 2ll * sms);
       if (ntotal > 0) k_wht_p1_tma<<<grid1, 256, sm1, st>>>(ta, in, out, n_pad, ncols, nct, ntotal, in.err);
       SKI_LAUNCH_CHECK();
+      if (out.nf && out.nf_any && in.n > 0) {
+        k_column_nonfinite<<<(unsigned)(2 * sms), 256, 0, st>>>(in.A, in.lda, in.n, in.d, in.b, ncols, out.nf_any,
+                                                                 out.nf);
+        SKI_LAUNCH_CHECK();
+      }
       return SKI_OK;
     }
   }
@@ -532,19 +607,28 @@ ski_status launch_f32(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& 
   return SKI_EINVAL;
 }
 
+// Tiles of the pass with the fewest row bits: rows of a per-tile exponent plane.
+int64_t fx_max_tiles(int64_t n_pad) {
+  int nbs[8], np = 0;
+  plan_passes(ilog2(n_pad), nbs, &np);
+  int nbmin = nbs[0];
+  for (int p = 1; p < np; ++p) nbmin = std::min(nbmin, nbs[p]);
+  return std::max<int64_t>(1, n_pad >> nbmin);
+}
+
 }  // namespace
 
 size_t ski_premix_ws_bytes(int64_t n, int64_t ncols, int64_t n_pad, int32_t dtype) {
   SkiArena ar{nullptr, 0, 0, true};
   const int64_t ldq = ski_round_up(ncols, CT);
   ar.take<int8_t>(ski_round_up(n, 256));
-  ar.take<int>(1);
+  ar.take<int>(ldq + 1);
   ar.take<int>(1);
   if (dtype == SKI_F64) {
     ar.take<long long>(n_pad * ldq);
     ar.take<long long>(n_pad * ldq);
-    ar.take<int16_t>(n_pad * ldq);
-    ar.take<int16_t>(n_pad * ldq);
+    ar.take<int16_t>(fx_max_tiles(n_pad) * ldq);
+    ar.take<int16_t>(fx_max_tiles(n_pad) * ldq);
     ar.take<int>(ldq);
   } else {
     ar.take<float>(n_pad * ldq);
@@ -561,7 +645,7 @@ ski_status ski_premix_plan(int64_t n, int64_t ncols_max, int64_t n_pad, int32_t 
   P.dtype = dtype;
   P.ldq = ski_round_up(ncols_max, CT);
   P.D = ar.take<int8_t>(ski_round_up(n, 256));  // padded: the TMA pass copies 256 signs per tile
-  P.nonfinite = ar.take<int>(1);
+  P.nonfinite = ar.take<int>(P.ldq + 1);  // per column, then the any-column flag
   int* own_err = ar.take<int>(1);
   P.err = err_flag ? err_flag : own_err;
   P.L = ilog2(n_pad);
@@ -571,8 +655,8 @@ ski_status ski_premix_plan(int64_t n, int64_t ncols_max, int64_t n_pad, int32_t 
   if (dtype == SKI_F64) {
     P.Qa = ar.take<long long>(n_pad * P.ldq);
     P.Qb = ar.take<long long>(n_pad * P.ldq);
-    P.Xa = ar.take<int16_t>(n_pad * P.ldq);
-    P.Xb = ar.take<int16_t>(n_pad * P.ldq);
+    P.Xa = ar.take<int16_t>(fx_max_tiles(n_pad) * P.ldq);
+    P.Xb = ar.take<int16_t>(fx_max_tiles(n_pad) * P.ldq);
     P.ecol = ar.take<int>(P.ldq);
   } else {
     P.Qa = ar.take<float>(n_pad * P.ldq);
@@ -583,7 +667,7 @@ ski_status ski_premix_plan(int64_t n, int64_t ncols_max, int64_t n_pad, int32_t 
   if (!ar.ok() || !P.Qb) return SKI_ENOMEM;
   SKI_TRY(ski_premix_signs(seed, n, P.D, st));
   if (ski_round_up(n, 256) > n) SKI_CUDA_TRY(cudaMemsetAsync(P.D + n, 0, ski_round_up(n, 256) - n, st));
-  SKI_CUDA_TRY(cudaMemsetAsync(P.nonfinite, 0, sizeof(int), st));
+  SKI_CUDA_TRY(cudaMemsetAsync(P.nonfinite, 0, (P.ldq + 1) * sizeof(int), st));
   if (!err_flag) SKI_CUDA_TRY(cudaMemsetAsync(P.err, 0, sizeof(int), st));
   return SKI_OK;
 }
@@ -596,6 +680,8 @@ ski_status premix_fx_passes(const SkiPremixPlan& P, const FxIn& in, int64_t ncol
   const int64_t n = P.n, n_pad = P.n_pad, ldq = P.ldq;
   long long* Qa = (long long*)P.Qa;
   long long* Qb = (long long*)P.Qb;
+  // per-column flags of this call's columns (a slab reuses the plan)
+  SKI_CUDA_TRY(cudaMemsetAsync(P.nonfinite, 0, (ldq + 1) * sizeof(int), st));
   int lo = 0;
   int64_t nvalid = n;
   long long* Qin = nullptr;
@@ -610,15 +696,16 @@ ski_status premix_fx_passes(const SkiPremixPlan& P, const FxIn& in, int64_t ncol
     int16_t* Xo = (p & 1) ? P.Xb : P.Xa;
     FxOut out{};
     out.Q = Qo; out.X = Xo; out.ldq = ldq; out.ldx = ldq; out.Y = (double*)Y; out.ldy = ldy;
-    out.yshift = P.yshift; out.nonfinite = P.nonfinite; out.ecol = P.ecol;
+    out.yshift = P.yshift; out.nf = P.nonfinite; out.nf_any = P.nonfinite + ldq; out.ecol = P.ecol;
     FxIn cur = in;
     cur.Q = Qin; cur.X = Xin; cur.ldq = ldq; cur.ldx = ldq; cur.nvalid = nvalid; cur.lo_p = lo_p; cur.nb_p = nb_p;
+    cur.nf = P.nonfinite;
     if (aligned) {
       // exponent bound of every tile of the last pass, per column, from the
       // previous pass's exponents (its tiles that hold rows below nvalid)
       const int64_t ntp = ski_cdiv(nvalid, 1ll << nb_p) << lo_p;
-      k_colmax_exp<<<(unsigned)ski_cdiv(ncols, 256), 256, 0, st>>>(ncols, Xin, ldq, std::min<int64_t>(ntp, n_pad >> nb_p),
-                                                                   nb, P.ecol);
+      k_colmax_exp<<<(unsigned)ski_cdiv(ncols, 32), 256, 0, st>>>(ncols, Xin, ldq, std::min<int64_t>(ntp, n_pad >> nb_p),
+                                                                  lo_p, P.ecol);
       SKI_LAUNCH_CHECK();
     }
     ski_status s;
@@ -628,6 +715,7 @@ ski_status premix_fx_passes(const SkiPremixPlan& P, const FxIn& in, int64_t ncol
     if (s != SKI_OK) return s;
     if (last && qfinal) {
       qo->Q = Qo;
+      qo->nonfinite = P.nonfinite;
       qo->X = aligned ? nullptr : Xo;
       qo->ecol = aligned ? P.ecol : nullptr;
       qo->headroom = kAlignHeadroom;

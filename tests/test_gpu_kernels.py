@@ -163,17 +163,66 @@ def test_hrht_sketch_column_slabs(d, slab, with_b):
     assert rel_fro(got32, want) <= 1e-5
 
 
-def test_hrht_sketch_full_size_sampled_columns():
-    # The dense test-set shape: n = 50000, d = 4000, n_pad = 65536, s = 2, m = 2d.
+@pytest.mark.parametrize("kind,s", [("gauss", 2), ("coherent", 1)])
+def test_hrht_sketch_full_size_sampled_columns(kind, s):
+    # The dense test-set shapes: n = 50000, d = 4000, n_pad = 65536, m = 2d,
+    # iid Gaussian and high-coherence (first d rows 1e3 I + N(0, 1e-6)).
     # Checked on sampled columns: column c of S_h H D A is S_h H D A[:, c].
     torch, pkg = cuda()
     n, d, m = 50000, 4000, 8000
-    A, b = workloads.dense_gaussian(n, d, seed=20210527)
-    got = _sketch(torch, pkg, A, b, m=m, s=2, seed=3, premix=1, n_pad=65536)
+    if kind == "gauss":
+        A, b = workloads.dense_gaussian(n, d, seed=20210527)
+    else:
+        A, b = workloads.dense_high_coherence(n, d, seed=20210527)
+    got = _sketch(torch, pkg, A, b, m=m, s=s, seed=3, premix=1, n_pad=65536)
     cols = [0, 1, 1234, 2047, 3999, 4000]
     Ab = np.column_stack([A[:, cols[:-1]], b])
-    want = owht.hrht_sketch(3, 2, m, Ab, None, 65536)
+    want = owht.hrht_sketch(3, s, m, Ab, None, 65536)
     assert rel_fro(got[:, cols], want) <= 1e-12
+
+
+# The FP64 premix's last pass stores each column in one shared unit, bounded
+# by the sum over the previous pass's tiles of their bounds (high-coherence
+# columns, where one tile dominates, keep their precision).  Cases: buckets
+# of more than 2^6 rows (the gather renormalises its sums), s = 3, a first
+# pass of 5 row bits (not TMA-fed), 9 + 9 row bits (n_pad = 2^18), and three
+# passes (n_pad = 2^19: tile families, and all-zero middle-pass tiles in the
+# padding).
+@pytest.mark.parametrize("n,d,m,s,npad", [(3000, 20, 16, 1, 4096), (3000, 20, 16, 3, 4096), (600, 10, 12, 2, 1024),
+                                          (130000, 3, 40, 1, 262144), (300000, 2, 50, 2, 524288),
+                                          (5000, 64, 130, 2, 8192)])
+def test_hrht_sketch_column_units(n, d, m, s, npad):
+    torch, pkg = cuda()
+    A, b = workloads.dense_high_coherence(n, d, seed=n + d)
+    got = _sketch(torch, pkg, A, b, m=m, s=s, seed=17, premix=1, n_pad=npad)
+    again = _sketch(torch, pkg, A, b, m=m, s=s, seed=17, premix=1, n_pad=npad)
+    assert np.array_equal(got, again)
+    want = owht.hrht_sketch(17, s, m, A, b, npad)
+    assert rel_fro(got, want) <= 1e-12
+
+
+# A NaN or Inf in a column of A makes that column of the premixed result NaN
+# (every output row of the column sums it); the other columns are unaffected.
+@pytest.mark.parametrize("n,npad,slab", [(3000, 4096, 0), (300, 512, 0), (3000, 4096, 32)])
+def test_premix_nonfinite_columns(n, npad, slab):
+    torch, pkg = cuda()
+    d = 70
+    A, b, _ = workloads.gaussian_lls(n, d, seed=n)
+    A[17, 3] = np.nan
+    A[n - 5, 5] = np.inf
+    bad = [3, 5]
+    good = [c for c in range(d + 1) if c not in bad]
+    got = _sketch(torch, pkg, A, b, m=150, s=2, seed=4, premix=1, n_pad=npad, premix_slab=slab)
+    assert np.isnan(got[:, bad]).all()
+    want = owht.hrht_sketch(4, 2, 150, A[:, good[:-1]], b, npad)
+    assert rel_fro(got[:, good], want) <= 1e-12
+    if slab == 0:
+        o = pkg.ski_opts_default(seed=77, n_pad=npad)
+        Y = torch.empty(npad, d + 1, dtype=torch.float64, device="cuda")
+        pkg.ski_premix(pkg.dense_matrix(to_dev(torch, A)), to_dev(torch, b), o, Y, d + 1)
+        Yh = Y.cpu().numpy()
+        assert np.isnan(Yh[:, bad]).all()
+        assert rel_fro(Yh[:, good], owht.premix(77, np.column_stack([A, b])[:, good], npad)) <= 1e-12
 
 
 def _signfix(R):
