@@ -74,9 +74,9 @@ FP32_PEAK_TFLOPS = 72.0
 # (bucket lists, both premix passes, the nonfinite scan, the column-unit
 # bound, the hash gather and the NaN post-pass) and the hash gather alone;
 # None where not captured.
-SKETCH_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 43264 + 44288 + 428288 + 332544 + 1672682496 + 1555713280 + 7680 +
-                  1598464 + 1618831616 + 2044199936 + 2424849664 + 236686848 + 20480}
-GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2424849664 + 236686848}
+SKETCH_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 43264 + 38656 + 428544 + 333056 + 1669957376 + 1555677696 + 7936 +
+                  1597952 + 1618928896 + 2050959616 + 2425019904 + 236484096 + 20736}
+GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2425019904 + 236484096}
 
 
 class ClockSampler:

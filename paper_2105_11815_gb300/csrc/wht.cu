@@ -18,6 +18,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "hash.cuh"
@@ -73,7 +74,10 @@ constexpr int kZeroTile = -32768;  // exponent of an all-zero tile column
 // CW: columns per tile (32, or 16 for twice the CTAs per SM where the pass is
 // latency-bound).
 template <int RB, int GB, int IN, int OUT, int CW = CT>
-__global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4 : 2) : 1) k_wht_fx(int lo, int64_t n_pad, int64_t ncols, FxIn in, FxOut out, int colx) {
+// off32: every per-thread offset below ((R - 1) * stride) fits in 32 bits, so
+// the row loops index with 32-bit offsets (address math on the FMA pipe; the
+// integer ALU pipe is the pass's bound).
+__global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4 : 2) : 1) k_wht_fx(int lo, int64_t n_pad, int64_t ncols, FxIn in, FxOut out, int colx, int off32) {
   constexpr int R = 1 << RB, G = 1 << GB, NB = RB + GB;
   extern __shared__ long long sq[];            // [R*G][CW]
   __shared__ int sx[G][CW];
@@ -88,32 +92,62 @@ __global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4
   long long q[R];
   int xsrc[IN == 1 ? R : 1];
   int emax = -100000;
+  // input rows of this thread: in0 + t 2^(GB + lo), t < R; the first tv exist
+  const int64_t in0 = base + ((int64_t)g << lo);
+  const int64_t nin = IN == 0 ? in.n : in.nvalid;
+  const int tv = (!cok || in0 >= nin) ? 0 : (int)min((int64_t)R, ((nin - in0 - 1) >> (GB + lo)) + 1);
   if (IN == 0) {
+    // A[row][col] (or b[row] for col == d) and D[row]
+    const bool isb = col >= in.d;
+    const double* ap = isb ? in.b + in0 : in.A + (tv ? in0 * in.lda + col : 0);
+    const int64_t as = isb ? ((int64_t)1 << (GB + lo)) : (in.lda << (GB + lo));
+    const int8_t* dp = in.D + in0;
+    auto ld = [&](auto o, auto full) {
+      using O = decltype(o);
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      const int64_t row = base + ((int64_t)(g + (t << GB)) << lo);
-      long long bits = 0;
-      if (cok && row < in.n) {
-        bits = __double_as_longlong(col < in.d ? in.A[row * in.lda + col] : in.b[row]);
-        if (in.D[row] < 0) bits ^= (1ll << 63);  // D_jj = -1: flip the sign bit (no FP64 op)
+      for (int t = 0; t < R; ++t) {
+        long long bits = 0;
+        if (decltype(full)::value || t < tv) {
+          bits = __double_as_longlong(ap[(O)t * (O)as]);
+          if (dp[(O)t << (GB + lo)] < 0) bits ^= (1ll << 63);  // D_jj = -1: flip the sign bit (no FP64 op)
+        }
+        const int e = (int)((bits >> 52) & 0x7FF);
+        emax = max(emax, e ? e : 1);
+        q[t] = bits;
       }
-      int e = (int)((bits >> 52) & 0x7FF);
-      emax = max(emax, e ? e : 1);
-      q[t] = bits;
+    };
+    if (off32) {
+      if (tv == R) ld(uint32_t{}, std::true_type{});
+      else ld(uint32_t{}, std::false_type{});
+    } else {
+      ld(int64_t{}, std::false_type{});
     }
   } else {
+    // Q[row][col] and the previous pass's exponent of row's tile, which is
+    // tile_of_row(in0) + t 2^(GB + lo_p) (the passes' row bits are adjacent)
+    const long long* qp = in.Q + (tv ? in0 * in.ldq + col : 0);
+    const int16_t* xp = in.X + (tv ? tile_of_row(in0, in.lo_p, in.nb_p) * in.ldx + col : 0);
+    const int64_t qs = in.ldq << (GB + lo), xst = in.ldx << (GB + in.lo_p);
+    auto ld = [&](auto o, auto full) {
+      using O = decltype(o);
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      const int64_t row = base + ((int64_t)(g + (t << GB)) << lo);
-      long long v = 0;
-      int xs = -32768;
-      if (cok && row < in.nvalid) {
-        v = in.Q[row * in.ldq + col];
-        xs = in.X[tile_of_row(row, in.lo_p, in.nb_p) * in.ldx + col];
+      for (int t = 0; t < R; ++t) {
+        long long v = 0;
+        int xs = kZeroTile;
+        if (decltype(full)::value || t < tv) {
+          v = qp[(O)t * (O)qs];
+          xs = xp[(O)t * (O)xst];
+        }
+        q[t] = v;
+        xsrc[t] = xs;  // a zero in a nonzero tile may raise E: harmless, the column unit caps Xq
+        emax = max(emax, xs);
       }
-      q[t] = v;
-      xsrc[t] = v ? xs : -32768;
-      emax = max(emax, xsrc[t]);
+    };
+    if (off32) {
+      if (tv == R) ld(uint32_t{}, std::true_type{});
+      else ld(uint32_t{}, std::false_type{});
+    } else {
+      ld(int64_t{}, std::false_type{});
     }
   }
   sx[g][c] = emax;
@@ -149,10 +183,7 @@ __global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4
     int Xq = E + NB;
     if (OUT == 2 && cok && !zero) Xq = min(Xq, out.ecol[col] + kAlignHeadroom);
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      int sh = Xq - xsrc[IN == 1 ? t : 0];
-      q[t] = (q[t] == 0 || sh > 63) ? 0 : (q[t] >> sh);
-    }
+    for (int t = 0; t < R; ++t) q[t] >>= min(Xq - xsrc[IN == 1 ? t : 0], 63);  // >= 0; absent rows hold 0
     X = zero ? kZeroTile : Xq;
   }
   // RB levels in registers: row bits [GB, GB+RB) of the tile index
@@ -185,19 +216,36 @@ __global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4
     }
   }
   if (!cok) return;
-  int ash = 0;  // OUT == 2: to units of 2^(ecol + headroom); X <= ecol + headroom
-  if (OUT == 2) ash = max(0, min(63, out.ecol[col] - X + kAlignHeadroom));
+  // output rows of this thread: out0 + t 2^lo, t < R; the first to exist
+  const int64_t out0 = base + ((int64_t)(g << RB) << lo);
+  const int to = out0 >= n_pad ? 0 : (int)min((int64_t)R, ((n_pad - out0 - 1) >> lo) + 1);
+  if (OUT == 0 || OUT == 2) {
+    if (OUT == 2) {  // to units of 2^(ecol + headroom); X <= ecol + headroom
+      const int ash = max(0, min(63, out.ecol[col] - X + kAlignHeadroom));
 #pragma unroll
-  for (int t = 0; t < R; ++t) {
-    const int64_t row = base + ((int64_t)((g << RB) + t) << lo);
-    if (row >= n_pad) continue;
-    if (OUT == 0) {
-      out.Q[row * out.ldq + col] = q[t];
-    } else if (OUT == 2) {
-      out.Q[row * out.ldq + col] = q[t] >> ash;
+      for (int t = 0; t < R; ++t) q[t] >>= ash;
+    }
+    long long* op = out.Q + (to ? out0 * out.ldq + col : 0);
+    const int64_t os = out.ldq << lo;
+    auto st = [&](auto o, auto full) {
+      using O = decltype(o);
+#pragma unroll
+      for (int t = 0; t < R; ++t)
+        if (decltype(full)::value || t < to) op[(O)t * (O)os] = q[t];
+    };
+    if (off32) {
+      if (to == R) st(uint32_t{}, std::true_type{});
+      else st(uint32_t{}, std::false_type{});
     } else {
-      out.Y[row * out.ldy + col] =
-          colbad ? __longlong_as_double(0x7FF8000000000000ll) : fx_to_double(q[t], X - out.yshift + 1075 + FX_LIFT, 0);
+      st(int64_t{}, std::false_type{});
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int64_t row = out0 + ((int64_t)t << lo);
+      if (t < to)
+        out.Y[row * out.ldy + col] = colbad ? __longlong_as_double(0x7FF8000000000000ll)
+                                            : fx_to_double(q[t], X - out.yshift + 1075 + FX_LIFT, 0);
     }
   }
   if (OUT == 0 && g == 0) out.X[tile * out.ldx + col] = (int16_t)X;
@@ -521,6 +569,17 @@ void plan_passes(int L, int* nbs, int* np) {
   *np = P;
 }
 
+// Whether a k_wht_fx launch may index rows with 32-bit offsets: (R - 1)
+// times each per-row stride (elements) below 2^32.
+bool fx_off32(int IN, int RB, int GB, int lo, const FxIn& in, const FxOut& out) {
+  const int64_t R1 = (1ll << RB) - 1;
+  int64_t s = 0;
+  if (IN == 0) s = std::max(in.lda << (GB + lo), (int64_t)1 << (GB + lo));
+  else s = std::max(in.ldq << (GB + lo), in.ldx << (GB + in.lo_p));
+  s = std::max(s, out.ldq << lo);
+  return R1 * s < (1ll << 32) - 1;
+}
+
 template <int IN, int OUT>
 ski_status launch_fx(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& in, const FxOut& out,
                      cudaStream_t st) {
@@ -563,7 +622,7 @@ ski_status launch_fx(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& i
                     : dim3((unsigned)ntiles, (unsigned)ski_cdiv(ncols, CW));
     if (sm16 > 48 * 1024)
       SKI_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm16));
-    kfn<<<g16, CW << 4, sm16, st>>>(lo, n_pad, ncols, in, out, colx);
+    kfn<<<g16, CW << 4, sm16, st>>>(lo, n_pad, ncols, in, out, colx, fx_off32(IN, 4, 4, lo, in, out) ? 1 : 0);
     SKI_LAUNCH_CHECK();
     return SKI_OK;
   }
@@ -572,7 +631,7 @@ ski_status launch_fx(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& i
     auto kfn = k_wht_fx<rb, gb, IN, OUT>;                                                        \
     if (smem > 48 * 1024)                                                                        \
       SKI_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    kfn<<<grid, threads, smem, st>>>(lo, n_pad, ncols, in, out, colx);                           \
+    kfn<<<grid, threads, smem, st>>>(lo, n_pad, ncols, in, out, colx, fx_off32(IN, rb, gb, lo, in, out) ? 1 : 0); \
     SKI_LAUNCH_CHECK();                                                                          \
     return SKI_OK;                                                                               \
   }
