@@ -396,18 +396,29 @@ __global__ void __launch_bounds__(256, 2) k_wht_p1_tma(const __grid_constant__ C
     if (!sm.ok) break;
     long long q[R];
     int emax = -100000;
+    if (col < in.d) {  // A: zero outside it (TMA fill)
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      const int rl = g + (t << GB);
-      const int64_t row = base + rl;
-      long long bits = 0;
-      if (col < in.d) bits = sm.tile[s][rl * CW + c];  // zero outside A (TMA fill)
-      else if (col == in.d && in.b && row < in.n) bits = __double_as_longlong(in.b[row]);
-      if (sm.dseg[s][rl] < 0) bits ^= (1ll << 63);
-      const int e = (int)((bits >> 52) & 0x7FF);
-      bad |= (e == 0x7FF);
-      emax = max(emax, e ? e : 1);
-      q[t] = bits;
+      for (int t = 0; t < R; ++t) {
+        const int rl = g + (t << GB);
+        long long bits = sm.tile[s][rl * CW + c];
+        bits ^= (long long)((unsigned long long)(sm.dseg[s][rl] < 0) << 63);  // D_jj = -1: flip the sign bit
+        const int e = (int)((bits >> 52) & 0x7FF);
+        bad |= (e == 0x7FF);
+        emax = max(emax, e ? e : 1);
+        q[t] = bits;
+      }
+    } else {  // b (column d), or nothing
+      const bool isb = col == in.d && in.b;
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const int rl = g + (t << GB);
+        long long bits = (isb && base + rl < in.n) ? __double_as_longlong(in.b[base + rl]) : 0ll;
+        bits ^= (long long)((unsigned long long)(sm.dseg[s][rl] < 0) << 63);
+        const int e = (int)((bits >> 52) & 0x7FF);
+        bad |= (e == 0x7FF);
+        emax = max(emax, e ? e : 1);
+        q[t] = bits;
+      }
     }
     sm.sx[g][c] = emax;
     __syncthreads();
@@ -420,8 +431,7 @@ __global__ void __launch_bounds__(256, 2) k_wht_p1_tma(const __grid_constant__ C
       const unsigned long long bits = (unsigned long long)q[t];
       const int e = (int)((bits >> 52) & 0x7FF);
       const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
-      const int sh = E - (e ? e : 1);
-      const unsigned long long mq = sh > 63 ? 0ull : ((M << LIFT) >> sh);
+      const unsigned long long mq = (M << LIFT) >> min(E - (e ? e : 1), 63);  // 0 for shifts >= 63
       q[t] = (bits >> 63) ? -(long long)mq : (long long)mq;
     }
     const int X = E - 1075 - LIFT;
@@ -451,11 +461,10 @@ __global__ void __launch_bounds__(256, 2) k_wht_p1_tma(const __grid_constant__ C
     __syncthreads();  // stage s is free again
     if (threadIdx.x == 0 && issued < mine) issue(issued++);
     if (cok) {
+      // rows base + (g << RB) + t: all below round_up(n, 256) <= n_pad
+      long long* op = out.Q + (base + (g << RB)) * out.ldq + col;
 #pragma unroll
-      for (int t = 0; t < R; ++t) {
-        const int64_t row = base + ((g << RB) + t);
-        if (row < n_pad) out.Q[row * out.ldq + col] = q[t];
-      }
+      for (int t = 0; t < R; ++t) op[(uint32_t)t * (uint32_t)out.ldq] = q[t];
       if (g == 0) out.X[tile * out.ldx + col] = (int16_t)X;
     }
   }
@@ -593,7 +602,7 @@ ski_status launch_fx(int nb, int lo, int64_t n_pad, int64_t ncols, const FxIn& i
   // the first pass (FP64 in) is latency-bound: fed by TMA when A's layout
   // allows a tensor map (row stride a multiple of 16 bytes), else 16-column
   // tiles at four CTAs per SM
-  if (IN == 0 && OUT == 0 && RB == 4 && GB == 4 && lo == 0 && in.err) {
+  if (IN == 0 && OUT == 0 && RB == 4 && GB == 4 && lo == 0 && in.err && 15 * out.ldq < (1ll << 32)) {
     CUtensorMap ta;
     if (ski_tmap_f64_2d(&ta, in.A, in.n, in.d, in.lda, P1_ROWS, P1_CW)) {
       const int64_t nct = ski_cdiv(ncols, P1_CW);
