@@ -74,9 +74,9 @@ FP32_PEAK_TFLOPS = 72.0
 # (bucket lists, both premix passes, the nonfinite scan, the column-unit
 # bound, the hash gather and the NaN post-pass) and the hash gather alone;
 # None where not captured.
-SKETCH_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 43264 + 38656 + 428544 + 333056 + 1669957376 + 1555677696 + 7936 +
-                  1597952 + 1618928896 + 2050959616 + 2425019904 + 236484096 + 20736}
-GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2425019904 + 236484096}
+SKETCH_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 43264 + 38400 + 429056 + 333056 + 1612551424 + 1555619072 + 7936 +
+                  1598208 + 1618771200 + 2050941696 + 2425076480 + 236391168 + 20480}
+GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2425076480 + 236391168}
 
 
 class ClockSampler:
