@@ -648,7 +648,7 @@ def run_batched(args, name):
     wsz = {}
 
     def workspace(o):
-        k = o.streams
+        k = (o.streams, o.lsqr_ctas)
         if k not in wsz:
             nb = max(pkg.ski_solve_batched_workspace_size(mats, o),
                      pkg.ski_solve_adjoint_batched_workspace_size(mats, o))
@@ -681,6 +681,15 @@ def run_batched(args, name):
         return ms, res, fwd
 
     o_main = opts(args.streams)
+    tuned = None
+    if args.autotune is not None:
+        # launch parameters timed on a sample of this batch (outside the timed
+        # region) or read back from the cache file
+        from paper_2105_11815_gb300 import autotune
+        t_tune = time.perf_counter()
+        o_main, rec = autotune.tune_batched(mats, bs, xs, o_main, cache_path=args.autotune or None, sample=16,
+                                            reps=1)
+        tuned = dict(rec, tuning_s=time.perf_counter() - t_tune)
     clocks = ClockSampler(local)
     clocks.start()
     l0 = pkg.ski_launch_count()
@@ -753,7 +762,8 @@ def run_batched(args, name):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": name, "problems": count, "gamma": gamma, "s": 1,
                        "sketch_qr": args.batch_precision,
-                       "streams": o_main.streams or "auto", "A_bytes": 8 * nA,
+                       "streams": o_main.streams or "auto", "lsqr_pass": o_main.lsqr_pass,
+                       "lsqr_ctas": o_main.lsqr_ctas, "graphs": o_main.graphs, "autotune": tuned, "A_bytes": 8 * nA,
                        "l2": "inputs larger than L2 (%.1f GB)" % (8e-9 * nA),
                        "parallelism": "replicas" if world > 1 else "single"},
             "forward_ms": fwd_ms, "backward_ms": ms_step - fwd_ms, "worst_metric": worst,
@@ -838,6 +848,8 @@ def main():
     ap.add_argument("--ref-cols", type=int, default=1024)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--streams", type=int, default=0, help="batched workload: problems in flight (0 = auto)")
+    ap.add_argument("--autotune", nargs="?", const="", default=None,
+                    help="batched workload: tune the launch parameters first (optional JSON cache path)")
     ap.add_argument("--sweep", type=int, nargs="*", default=[1], help="batched workload: also time these")
     ap.add_argument("--ref-problems", type=int, default=3, help="batched workload: oracle sample size")
     ap.add_argument("--premix-slab", type=int, default=0, help="premix column slab width (0 = full width)")

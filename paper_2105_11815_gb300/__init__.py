@@ -57,7 +57,9 @@ class ski_opts(ctypes.Structure):
                 ("sketch_dtype", ctypes.c_int32), ("qr_dtype", ctypes.c_int32),
                 ("tau_a", ctypes.c_double), ("tau_r", ctypes.c_double), ("tol", ctypes.c_double),
                 ("rcond", ctypes.c_double), ("perturb", ctypes.c_double), ("it_max", ctypes.c_int64),
-                ("streams", ctypes.c_int32), ("premix_slab", ctypes.c_int32)]
+                ("streams", ctypes.c_int32), ("premix_slab", ctypes.c_int32),
+                ("lsqr_pass", ctypes.c_int32), ("lsqr_ctas", ctypes.c_int32), ("graphs", ctypes.c_int32),
+                ("pad2_", ctypes.c_int32)]
 
 
 class ski_info(ctypes.Structure):

@@ -88,10 +88,15 @@ static ski_status check_matrix(const ski_matrix* A) {
   return SKI_OK;
 }
 
+static bool launch_opts_ok(const ski_opts* o) {
+  return o->lsqr_pass >= 0 && o->lsqr_pass <= 3 && o->lsqr_ctas >= 0 && (o->graphs == 0 || o->graphs == 1);
+}
+
 static ski_status check_sketch_opts(const ski_matrix* A, const ski_opts* o) {
   if (!o) return SKI_EINVAL;
   if (o->s < 1 || o->s > 64 || o->m < o->s || o->m >= (1ll << 31)) return SKI_EINVAL;
   if (o->premix_slab < 0 || o->streams < 0) return SKI_EINVAL;
+  if (!launch_opts_ok(o)) return SKI_EINVAL;
   if (!dtype_ok(o->sketch_dtype)) return SKI_EINVAL;
   if (o->premix) {
     if (A->kind != SKI_DENSE) return SKI_EINVAL;
@@ -101,6 +106,15 @@ static ski_status check_sketch_opts(const ski_matrix* A, const ski_opts* o) {
   const int64_t rows = o->premix ? (o->n_pad ? o->n_pad : next_pow2(A->n)) : A->n;
   if (rows * (int64_t)o->s >= (1ll << 31) || rows >= (1ll << 31)) return SKI_EINVAL;
   return SKI_OK;
+}
+
+// CTAs of the LSQR passes (row tiles of ceil(n / ctas) rows): the option, or
+// the default; at least n / 16384 (the register-blocked pass keeps a tile's
+// row values in shared memory), at most n and 65535.
+static int lsqr_ctas(int64_t n, const ski_opts* o) {
+  if (!o || o->lsqr_ctas <= 0) return ski_fused_ctas(n);
+  int64_t c = std::min<int64_t>({(int64_t)o->lsqr_ctas, std::max<int64_t>(1, n), 65535});
+  return (int)std::max<int64_t>(c, ski_cdiv(n, 16384));
 }
 
 static int64_t eff_npad(const ski_matrix* A, const ski_opts* o) {
@@ -328,6 +342,7 @@ struct SolvePlan {
   int32_t qr_dt;    // storage of the QR (F64 or F32)
   int32_t qr_prec;  // its precision (F64, F32 or TF32)
   int nblk;
+  int lsqr_pass;  // variant of the dense LSQR pass (ski_opts.lsqr_pass)
   bool csr;
   // persistent
   double *R, *qtsb, *M, *Mt, *xs, *t, *v, *w, *y, *z, *p, *q, *part, *part_tt, *part_aa;
@@ -409,7 +424,8 @@ size_t plan_solve(const ski_matrix* A, const ski_opts* o, char* base, size_t cap
   P->qr_dt = qr_storage(o->qr_dtype);
   P->qr_prec = o->qr_dtype;
   P->ld_sa = ski_round_up(ncols, 4);
-  P->nblk = ski_fused_ctas(n);
+  P->nblk = lsqr_ctas(n, o);
+  P->lsqr_pass = o->lsqr_pass;
   P->R = ar.take<double>(d * d);
   P->qtsb = ar.take<double>(d);
   P->M = ar.take<double>(d * d);
@@ -487,23 +503,16 @@ struct Events {
 // Recorded on a private stream in thread-local capture mode, so other host
 // threads (the batched workers) are unaffected; the graph is launched on the
 // solve's own stream.  Disabled or failed: the launches are enqueued directly.
-// Chunk graphs are used when SKI_CHUNK_GRAPHS=1: they saved 0.6 ms of 36 ms
-// of LSQR on one 50000 x 4000 solve, but recording and instantiating a graph
-// per solve cost more than the launches it saved on the ragged batch of small
+// Chunk graphs are used when opts.graphs = 1: they saved 0.6 ms of 36 ms of
+// LSQR on one 50000 x 4000 solve, but recording and instantiating a graph per
+// solve cost more than the launches it saved on the ragged batch of small
 // problems (45 against 57 problems/s), so direct launches are the default.
-static bool chunk_graphs_enabled() {
-  static const bool on = [] {
-    const char* e = getenv("SKI_CHUNK_GRAPHS");
-    return e && e[0] == '1';
-  }();
-  return on;
-}
-
 struct ChunkGraph {
+  explicit ChunkGraph(bool on) : failed(!on) {}
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  bool failed = !chunk_graphs_enabled();
+  bool failed;
   long long nkern = 0;  // kernels per replay (counted as launches when they run)
   ~ChunkGraph() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -610,6 +619,7 @@ ski_status lsqr_iteration(const ski_matrix* A, SolvePlan& P, cudaStream_t st) {
     f.part_tt = P.part_tt;
     f.nblk = P.nblk;
     f.sc = P.sc;
+    f.variant = P.lsqr_pass;
     SKI_TRY(ski_fused_df_launch(f, st));
     SKI_TRY(ski_reduce_par_launch(P.nblk, P.d, P.part, P.part_tt, P.q, P.sc, st));
   }
@@ -769,7 +779,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   }
   int64_t iters_total = 0;
   int restarts = 0;
-  ChunkGraph lsqr_graph;
+  ChunkGraph lsqr_graph(o->graphs == 1);
   double metric = 0.0, lsqr_test = 0.0;
   bool early = false;
   if (sqrt(hs.rnorm2) <= o->tau_a) {
@@ -879,11 +889,13 @@ struct AdjPlan {
   char* tw;
   size_t tw_bytes;
   int nblk;
+  int lsqr_pass;  // variant of the dense LSQR pass (ski_opts.lsqr_pass)
 };
-size_t plan_adjoint(const ski_matrix* A, char* base, size_t cap, AdjPlan* P) {
+size_t plan_adjoint(const ski_matrix* A, const ski_opts* o, char* base, size_t cap, AdjPlan* P) {
   SkiArena ar{base, cap, 0, base == nullptr};
   const int64_t n = A->n, d = A->d;
-  P->nblk = ski_fused_ctas(n);
+  P->nblk = lsqr_ctas(n, o);
+  P->lsqr_pass = o ? o->lsqr_pass : 0;
   P->M = ar.take<double>(d * d);
   P->Mt = ar.take<double>(d * d);
   P->t = ar.take<double>(n);
@@ -926,10 +938,9 @@ FusedArgs dense_pass(const ski_matrix* A, const AdjPlan& P, const double* z, dou
 }  // namespace
 
 extern "C" size_t ski_solve_adjoint_workspace_size(const ski_matrix* A, const ski_opts* o) {
-  (void)o;
   if (check_matrix(A) != SKI_OK || A->kind != SKI_DENSE) return 0;
   AdjPlan P;
-  return plan_adjoint(A, nullptr, 0, &P);
+  return plan_adjoint(A, o, nullptr, 0, &P);
 }
 
 // Backward pass (see include/skills.h).  The CG products W^T W p = M^T A^T A M p
@@ -944,13 +955,14 @@ extern "C" ski_status ski_solve_adjoint(const ski_matrix* A, const double* b, co
     info->status = SKI_EINVAL;
   }
   SKI_TRY(check_matrix(A));
-  if (A->kind != SKI_DENSE || A->d > SKI_DENSE_DMAX || !o || !b || !x || !R || !g || !db || ldr < A->d)
+  if (A->kind != SKI_DENSE || A->d > SKI_DENSE_DMAX || !o || !b || !x || !R || !g || !db || ldr < A->d ||
+      !launch_opts_ok(o))
     return SKI_EINVAL;
   if (dA && ld_da < A->d) return SKI_EINVAL;
   AdjPlan P;
-  const size_t need = plan_adjoint(A, nullptr, 0, &P);
+  const size_t need = plan_adjoint(A, o, nullptr, 0, &P);
   if (ws_bytes < need || !ws) return SKI_ENOMEM;
-  plan_adjoint(A, (char*)ws, ws_bytes, &P);
+  plan_adjoint(A, o, (char*)ws, ws_bytes, &P);
   cudaStream_t st = ski_stream(stream);
   const int64_t d = A->d, n = A->n;
   {
@@ -989,8 +1001,9 @@ extern "C" ski_status ski_solve_adjoint(const ski_matrix* A, const double* b, co
   f.part_tt = P.part_tt;
   f.nblk = P.nblk;
   f.sc = P.sc;
+  f.variant = P.lsqr_pass;
   int64_t polled = 0;
-  ChunkGraph cg_graph;
+  ChunkGraph cg_graph(o->graphs == 1);
   for (;;) {
     SKI_TRY(cg_graph.run(st, [&](cudaStream_t s) -> ski_status {
       for (int k = 0; k < 8; ++k) {

@@ -683,20 +683,10 @@ bool ski_df_supported(int64_t d) { return d <= SKI_DENSE_DMAX; }
 
 int64_t ski_a2_ld(int64_t d) { return ski_round_up(d, 2); }  // rows 16-byte aligned
 
-// Variant selection of the LSQR pass.  The default is the register-blocked
-// kernel (k_fused_df), measured fastest at 50000 x 4000 (0.55 ms per
-// iteration against 0.68 for the TMA-staged and 0.75 for the row-per-warp
-// variants); SKI_LSQR_PASS = "rows" | "tma" selects another for measurements.
-static int lsqr_pass_choice() {
-  static const int v = [] {
-    const char* e = getenv("SKI_LSQR_PASS");
-    return (e && e[0] == 't') ? 1 : (e && e[0] == 'r' && e[1] == 'o') ? 0 : 2;
-  }();
-  return v;
-}
-static bool getenv_flag_df_rows() { return lsqr_pass_choice() == 0; }
-static bool getenv_flag_df_tma() { return lsqr_pass_choice() == 1; }
-
+// Variant of the LSQR pass (DfArgs.variant, from ski_opts.lsqr_pass): the
+// register-blocked kernel (k_fused_df, 0 and 1) measured fastest at
+// 50000 x 4000 (0.55 ms per iteration against 0.68 for the TMA-staged ring (2)
+// and 0.75 for row per warp (3)); the autotuner times them per shape.
 ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
   DfArgs f = f0;
   f.ld2 = ski_a2_ld(f.d);
@@ -705,7 +695,7 @@ ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
   // row-per-warp variant (z and u staged in shared memory)
   {
     const size_t sm = (size_t)f.ld2 * sizeof(float2) + (size_t)f.rows_per * sizeof(double);
-    if (sm <= 200 * 1024 && getenv_flag_df_rows()) {
+    if (sm <= 200 * 1024 && f.variant == 3) {
 #define SKI_DFR_CASE(C)                                                                                  \
       if (cpt <= C) {                                                                                    \
         SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df_rows<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
@@ -722,7 +712,7 @@ ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
     }
   }
   // TMA-staged variant: nstage x RR rows of A2 in shared memory
-  if (getenv_flag_df_tma()) {
+  if (f.variant == 2) {
     const size_t rowb = (size_t)f.ld2 * sizeof(float2);
     const size_t ub = (size_t)f.rows_per * sizeof(double);
     const size_t budget = 200 * 1024;

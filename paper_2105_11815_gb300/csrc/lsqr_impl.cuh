@@ -65,6 +65,7 @@ struct DfArgs {
   int nblk;
   int64_t rows_per;
   LsqrScalars* sc;
+  int variant;  // 0, 1: register-blocked rows; 2: TMA-staged row ring; 3: row per warp
 };
 
 ski_status ski_split_a_launch(int64_t n, int64_t d, const double* A, int64_t lda, int sA, float2* A2,
