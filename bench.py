@@ -135,13 +135,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_init(n_gpus):
+def dist_init(n_gpus, backend=None):
+    """Rank, world size and local rank from the launcher's environment.  With
+    more than one rank: one process group (NCCL on GPUs, gloo otherwise) used
+    only for the barrier and the max-over-ranks of the timings -- the ranks
+    are independent replicas, nothing of the data path crosses it."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
     return rank, world, local
 
 
@@ -156,7 +163,8 @@ def max_over_ranks(v, world):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -207,7 +215,7 @@ def oracle_sample(A, b, cfg, cols, seed):
 
 
 def run_reference(args, name):
-    rank, world, _ = dist_init(args.gpus)
+    rank = int(os.environ.get("RANK", "0"))  # the oracle runs on rank 0 alone: no process group
     if rank != 0:
         return
     A, b, cfg = make_problem(name, args.seed)
@@ -440,7 +448,7 @@ def csr_oracle_sample(rowptr, colidx, val, b, cfg, cols, seed):
 
 
 def run_reference_csr(args, name):
-    rank, world, _ = dist_init(args.gpus)
+    rank = int(os.environ.get("RANK", "0"))  # the oracle runs on rank 0 alone: no process group
     if rank != 0:
         return
     rowptr, colidx, val, b, cfg = make_csr(name, args.seed)
@@ -592,7 +600,7 @@ def batch_oracle_sample(shapes, seed, count):
 
 
 def run_reference_batched(args, name):
-    rank, world, _ = dist_init(args.gpus)
+    rank = int(os.environ.get("RANK", "0"))  # the oracle runs on rank 0 alone: no process group
     if rank != 0:
         return
     from paper_2105_11815_gb300 import workloads
