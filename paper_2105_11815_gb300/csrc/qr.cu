@@ -126,6 +126,9 @@ __device__ __forceinline__ void panel_step_body(PanelArgs<T> a, int s, const Par
   const int64_t r0 = (int64_t)rank * a.rows_per;
   const int64_t r1 = min(a.mr, r0 + a.rows_per);
   T acc = T(0);
+  // independent rows: unrolled so the shuffles and shared-memory round trips
+  // of several rows overlap (each step's latency is on the QR's critical path)
+#pragma unroll 4
   for (int64_t r = r0 + warp; r < r1; r += WARPS) {
     T val = lane < a.w ? a.P[r * a.ld + lane] : T(0);
     if (s > 0 && r >= j) {
@@ -605,7 +608,7 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
   const int64_t max_slab_rows = (200 * 1024) / ((NB + 1) * (int64_t)sizeof(T));
   // cluster panels: 16 CTAs (non-portable size) when the device runs such a
   // cluster with the largest slab, else 8
-  constexpr int CNW = 16;
+  constexpr int CNW = 32;  // 32 warps: 16 hid too little of each step's row-loop latency (36.5 -> 32.1 ms at 8000 x 4000)
   int CL = 0;
   bool cluster_ok = false;
   // FP32 only: an FP64 panel does its rank-1 updates on the 1/64-rate FP64
