@@ -371,11 +371,19 @@ struct SolvePlan {
 constexpr int64_t kMixedLsqrBudget = 150;
 // Largest max|r_ii| / min|r_ii| of an FP32 (TF32) factor kept as the
 // preconditioner: kappa(SA) u must stay well below 1 for R^{-1} to
-// precondition, with u ~ 2^-22 for the three-pass products (2^-11 for one).
+// precondition, with u the coarser of the factorisation's unit roundoff
+// (~2^-22 for the three-pass products, 2^-11 for one) and the sketch's
+// (2^-9 for a BF16 SA).
 // The ratio underestimates kappa: at 200000 x 4000, kappa = 1e6 it was 5.9e4
 // (FP32 factor kept, 60 LSQR iterations), at kappa = 1e10 the FP32 factor's
-// ratio saturated at 3.2e6 (FP64: 3.7e8).
-double mixed_ratio_limit(int32_t qr_dtype) { return qr_dtype == SKI_TF32 ? 0x1p7 : 0x1p19; }
+// ratio saturated at 3.2e6 (FP64: 3.7e8).  A BF16 sketch at kappa = 1e6
+// spent the 150-iteration LSQR budget before refactoring (553 ms against
+// 412 ms for FP64); on the i.i.d. dense test set (ratio 1.5) it matched FP32.
+double mixed_ratio_limit(int32_t qr_dtype, int32_t sketch_dtype) {
+  double lim = qr_dtype == SKI_TF32 ? 0x1p7 : 0x1p19;
+  if (sketch_dtype == SKI_BF16) lim = std::min(lim, 0x1p5);
+  return lim;
+}
 // After >= 24 iterations, the Eq. TC-lsqr estimate extrapolated geometrically
 // (test_k ~ rho^k from test_0 = 1) predicts more than the budget: the FP32
 // preconditioner is too weak, so stop early instead of spending the budget.
@@ -743,7 +751,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   ski_status fs = factor(o);
   const double ratio_first = rdiag_ratio;
   if (mixed && (fs == SKI_ESINGULAR || fs == SKI_ENONFINITE ||
-                (fs == SKI_OK && !(rdiag_ratio <= mixed_ratio_limit(o->qr_dtype))))) {
+                (fs == SKI_OK && !(rdiag_ratio <= mixed_ratio_limit(o->qr_dtype, o->sketch_dtype))))) {
     fell_back = 1;
     fs = factor(&o64);
   }

@@ -82,6 +82,22 @@ def test_mixed_precision_solve(sd, qd):
     assert olsqr.residual_metric(A, b, x) <= 1e-10
 
 
+def test_bf16_sketch_factor_kept_only_when_well_conditioned():
+    # A BF16 sketch carries 2^-9 rounding: its FP32 factor preconditions a
+    # well-conditioned A (kept) but not kappa = 1e6, where the diagonal ratio
+    # sends Steps 1-2 to FP64 at once (qr_fallback = 1) instead of after the
+    # LSQR budget (2).  Both solves meet the tolerance.
+    torch, pkg = cuda()
+    A, b, _ = workloads.gaussian_lls(6000, 100, seed=3)
+    x, info = _solve(torch, pkg, A, b, m=300, s=1, seed=5, premix=1, sketch_dtype=2, qr_dtype=1)
+    assert info.status == 0 and info.qr_fallback == 0
+    assert olsqr.residual_metric(A, b, x) <= 1e-10
+    A, b = workloads.usv(8000, 200, 1e6, seed=2)
+    x, info = _solve(torch, pkg, A, b, m=400, s=1, seed=5, premix=1, sketch_dtype=2, qr_dtype=1)
+    assert info.status == 0 and info.qr_fallback == 1 and info.rdiag_ratio > 32
+    assert olsqr.residual_metric(A, b, x) <= 1e-10
+
+
 def test_square_one_hashing_loses_rank_exactly_on_collisions():
     # Example 1: with n = d and s = 1, SA = S A has full rank iff the d columns
     # of S land in distinct rows (probability prod_k (1 - k/m)); otherwise R is
