@@ -77,6 +77,10 @@ FP32_PEAK_TFLOPS = 72.0
 SKETCH_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 43264 + 38400 + 429056 + 333056 + 1612551424 + 1555619072 + 7936 +
                   1598208 + 1618771200 + 2050941696 + 2425076480 + 236391168 + 20480}
 GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2425076480 + 236391168}
+# DRAM bytes (read + write) per step of the FP64 GEMM launches (k_gemm<double>:
+# the QR trailing updates and the R^{-1} products of one FP64 solve), from
+# ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:"k_gemm<double"
+GEMM64_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 27581475328 + 6934643712}
 
 
 class ClockSampler:
@@ -319,7 +323,8 @@ def run_ours(args, name):
     g32 = statistics.mean(j.ms_qr_gemm for _, j in infos)
     roofline = {"kernel": "k_gemm<double> (FP64 QR trailing update)", "bound": "alu",
                 "achieved": gemm_flops / (g64 * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": gemm_flops / (g64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": gemm_flops / (g64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": GEMM64_TRAFFIC.get(name),
+                "traffic_scope": "bytes per step, all k_gemm<double> launches (QR updates + R^-1 products)",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (DFMA loop measured 1.00)",
                 "flops_per_step": gemm_flops, "ms_per_step": g64}
     sketch_roofline = {"kernel": ("premix + hash stage (k_wht_p1_tma, k_wht_fx, k_sketch_qa_f64acc)"

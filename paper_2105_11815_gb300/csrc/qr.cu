@@ -33,6 +33,7 @@ namespace {
 
 constexpr int NB = 32;
 constexpr int PW = 2 * NB;  // partial slot: g[32] then the diagonal row[32]
+constexpr int64_t kClusterRowsF64 = 4096;  // FP64 panels this short take the cluster kernel
 constexpr int WARPS = 8;
 constexpr long long kSpinLimit = 1ll << 24;  // ~1 s of polling at ~64 ns per poll
 
@@ -611,9 +612,13 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
   constexpr int CNW = 32;  // 32 warps: 16 hid too little of each step's row-loop latency (36.5 -> 32.1 ms at 8000 x 4000)
   int CL = 0;
   bool cluster_ok = false;
-  // FP32 only: an FP64 panel does its rank-1 updates on the 1/64-rate FP64
-  // pipe, which 64 SMs (grid-barrier kernel) finish sooner than 16.
-  if (sizeof(T) == 4) {
+  // FP32, and FP64 panels of at most kClusterRowsF64 rows: a tall FP64 panel
+  // does its rank-1 updates on the 1/64-rate FP64 pipe, which 64 SMs
+  // (grid-barrier kernel) finish sooner than 16; a short one is bound by the
+  // per-column synchronisation, which the cluster barrier does faster -- and
+  // 16-CTA clusters run beside the other streams' work, where a cooperative
+  // grid waits for 64 free SMs.
+  if (sizeof(T) == 4 || m <= kClusterRowsF64) {
     const size_t big = (size_t)(200 * 1024 + 2 * PW * sizeof(T));
     if (cudaFuncSetAttribute(k_panel_cluster<T, CNW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
             cudaSuccess &&
@@ -665,7 +670,7 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     T* Vk = ((k0 / NB) & 1) ? bf.V2 : bf.V;
     PanelArgs<T> pa{bf.P, NB, mr, w, rows_per, ncta, nullptr, nullptr, bf.tau, Vk, bf.Vt, ldt, Ctp, ldt};
     bool done_panel = false;
-    if (cluster_ok) {
+    if (cluster_ok && (sizeof(T) == 4 || mr <= kClusterRowsF64)) {
       // one cluster of CL CTAs: the slab of each must fit in shared memory
       const int64_t rp = ski_cdiv(mr, CL);
       const size_t csm = (size_t)(2 * PW + rp * (NB + 1)) * sizeof(T);
