@@ -229,7 +229,11 @@ def _signfix(R):
     return np.sign(np.diag(R))[:, None] * R
 
 
+# FP64 panels of at most 4096 rows run on the 16-CTA cluster kernel, taller
+# ones on the cooperative grid-barrier kernel: (5000, 300) is cooperative
+# throughout, (4200, 400) switches after its fourth panel.
 @pytest.mark.parametrize("m,d,dt", [(512, 256, 0), (1000, 100, 0), (64, 64, 0), (300, 1, 0), (777, 45, 0),
+                                    (5000, 300, 0), (4200, 400, 0),
                                     (2000, 300, 1), (2000, 300, 3), (3000, 1000, 1)])
 def test_precondition_qr(m, d, dt):
     torch, pkg = cuda()
