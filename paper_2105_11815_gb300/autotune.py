@@ -35,7 +35,7 @@ import numpy as np
 # Candidate values per field, the default first.
 SPACE_BATCHED = {
     "lsqr_pass": (1, 2, 3),
-    "lsqr_ctas": (0, 76, 304, 608),
+    "lsqr_ctas": (0, 19, 38, 76, 304, 608),  # few CTAs: passes of different problems share the SMs
     "graphs": (0, 1),
     "streams": (8, 1, 2, 4, 16),
 }
