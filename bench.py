@@ -232,8 +232,8 @@ def run_reference(args, name):
         vals.append(v)
         times.append(dt)
     value = statistics.mean(vals)
-    sample = "oracle HRHT sketch (numpy FP64) of A[:, :%d] (%d x %d) + b, m=%d, s=%d" % (
-        cols, cfg["n"], cols, cfg["m"], cfg["s"])
+    sample = "oracle %s sketch (numpy FP64) of A[:, :%d] (%d x %d) + b, m=%d, s=%d" % (
+        "HRHT" if cfg["n_pad"] else "s-hashing", cols, cfg["n"], cols, cfg["m"], cfg["s"])
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
