@@ -178,6 +178,8 @@ ski_status ski_premix_signs(uint64_t seed, int64_t n, int8_t* D, void* stream);
  * A dense FP64 n x d; b device FP64 [n] or NULL.  Y: device, n_pad rows of
  * d (+1 when b != NULL) columns, row stride ld_y, element type o->sketch_dtype
  * (FP64 or FP32).  Asynchronous.  Uses o->seed and o->n_pad.
+ * A NaN or Inf in a column of [A b] makes that column of Y NaN (FP64 also when
+ * a bounded wait of the first pass gave up: then all of Y).
  */
 size_t ski_premix_workspace_size(const ski_matrix* A, int32_t with_b, const ski_opts* o);
 ski_status ski_premix(const ski_matrix* A, const double* b, const ski_opts* o,
@@ -191,7 +193,9 @@ ski_status ski_premix(const ski_matrix* A, const double* b, const ski_opts* o,
  *       ld_sa >= d + (b != NULL).
  * Row i of SA is the sum over the rows j hashed to i of sign/sqrt(s) * A[j,:],
  * formed per output element in a fixed order (deterministic, bit-reproducible
- * for a given seed).  Asynchronous.
+ * for a given seed).  Asynchronous.  With the FP64 premix, a NaN or Inf in a
+ * column of [A b] makes that column of SA NaN, and a bounded wait of the
+ * premix that gave up makes all of SA NaN (ski_solve returns SKI_ETIMEOUT).
  */
 size_t ski_sketch_workspace_size(const ski_matrix* A, int32_t with_b, const ski_opts* o);
 ski_status ski_sketch_hash(const ski_matrix* A, const double* b, const ski_opts* o,

@@ -407,11 +407,14 @@ struct FxA {
   }
 };
 
-// Column c of SA (m rows) := NaN where nf[c] is set.
+// Column c of SA (m rows) := NaN where nf[c] is set, or everywhere when *err
+// is (a bounded wait of the premix gave up: the sketch is incomplete, and the
+// asynchronous entry points report it through SA).
 __global__ void __launch_bounds__(256) k_poison_columns(double* __restrict__ SA, int64_t ld_sa, int64_t m,
-                                                        int64_t ncols, const int* __restrict__ nf) {
+                                                        int64_t ncols, const int* __restrict__ nf,
+                                                        const int* __restrict__ err) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncols || !nf[c]) return;
+  if (c >= ncols || !(nf[c] || (err && *err))) return;
   for (int64_t i = 0; i < m; ++i) SA[i * ld_sa + c] = __longlong_as_double(0x7FF8000000000000ll);
 }
 
@@ -721,7 +724,7 @@ ski_status ski_gather_q(const SkiPremixQ& y, int64_t ncols, const SkiBuckets& bk
                                              c, e, SA, ld_sa, bk.m);
   SKI_LAUNCH_CHECK();
   // the integer path cannot carry a NaN or Inf: columns flagged by the premix become NaN
-  k_poison_columns<<<(unsigned)ski_cdiv(ncols, 256), 256, 0, st>>>(SA, ld_sa, bk.m, ncols, y.nonfinite);
+  k_poison_columns<<<(unsigned)ski_cdiv(ncols, 256), 256, 0, st>>>(SA, ld_sa, bk.m, ncols, y.nonfinite, y.err);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }

@@ -72,6 +72,7 @@ ski_status ski_premix_cols(const SkiPremixPlan& plan, const double* A, int64_t l
 struct SkiPremixQ {
   const long long* Q;
   const int* nonfinite;  // per column: the column's sketch is NaN
+  const int* err;        // set: a bounded wait of the premix gave up, the whole sketch is NaN
   const int16_t* X;
   const int* ecol;
   int headroom;

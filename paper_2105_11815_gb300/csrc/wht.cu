@@ -161,6 +161,8 @@ __global__ void __launch_bounds__(CW << GB, (GB >= 4 && RB <= 4) ? (CW == 16 ? 4
   // the tile is the whole column and E its largest exponent field.
   bool colbad = false;
   if (OUT == 1) colbad = IN == 0 ? (E == 0x7FF) : (cok && in.nf && in.nf[col] != 0);
+  // ... and every column when a bounded wait of an earlier pass gave up
+  if (OUT == 1 && IN == 1 && in.err && *in.err) colbad = true;
   int X;  // value = q * 2^X after quantisation
   if (IN == 0) {
     constexpr int LIFT = 9 - NB;  // |q| < 2^(62 - NB) before the NB levels
@@ -784,6 +786,7 @@ ski_status premix_fx_passes(const SkiPremixPlan& P, const FxIn& in, int64_t ncol
     if (last && qfinal) {
       qo->Q = Qo;
       qo->nonfinite = P.nonfinite;
+      qo->err = P.err;
       qo->X = aligned ? nullptr : Xo;
       qo->ecol = aligned ? P.ecol : nullptr;
       qo->headroom = kAlignHeadroom;
