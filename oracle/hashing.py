@@ -21,6 +21,8 @@ definition:
 * without replacement (s >= 2): nonzero k takes the first draw t = 0, 1, ...
   that differs from the rows already taken by nonzeros 0..k-1 (rejection), so
   the s rows are a uniform s-subset of [m] in draw order.
+* with replacement (the s-hashing variant of Def. 7): draw k is the t = 0
+  bucket draw of nonzero k, whatever the earlier draws were.
 * sign of nonzero k: -1 when the top bit of key(seed, SIGN, j, k, 0) is set, else +1.
 * premix sign D_j (Def. 8): -1 when the top bit of key(seed, PREMIX, j, 0, 0) is set.
 """
@@ -65,6 +67,17 @@ def column_rows_int(seed, s, m, j):
             t += 1
         rows.append(i)
         signs.append(-1 if key(seed, TAG_SIGN, j, k, 0) >> 63 else 1)
+    return rows, signs
+
+
+def variant_column_rows_int(seed, s, m, j):
+    """Draws i_1..i_s and signs of column j of the s-hashing variant (Def. 7), pure Python.
+
+    Def. 7 samples the s rows uniformly WITH replacement, so draw k is simply
+    the t = 0 bucket draw of nonzero k; rows may repeat.
+    """
+    rows = [(key(seed, TAG_BUCKET, j, k, 0) * m) >> 64 for k in range(s)]
+    signs = [-1 if key(seed, TAG_SIGN, j, k, 0) >> 63 else 1 for k in range(s)]
     return rows, signs
 
 

@@ -80,17 +80,18 @@ def residual_metric(A, b, x):
 
 
 def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
-            it_max=10000, rcond=1e-12):
+            it_max=10000, rcond=1e-12, variant=False):
     """Algorithm 1 with an s-hashing (optionally HRHT) sketch and Householder QR.
+    variant=True sketches with the s-hashing variant of Def. 7.
 
     A: dense n x d ndarray or scipy sparse; b: length n.
     Returns (x, info) with info = {iters, early_exit, x_s, R, qtsb, rank, trace}.
     """
     n, d = A.shape
     if premix:
-        SAb = _wht.hrht_sketch(seed, s, m, np.asarray(A), b, n_pad)
+        SAb = _wht.hrht_sketch(seed, s, m, np.asarray(A), b, n_pad, variant=variant)
     else:
-        SAb = _sketch.sketch_rows(seed, s, m, A, b)
+        SAb = _sketch.sketch_rows(seed, s, m, A, b, variant=variant)
     R, C = _qr.householder_qr(SAb, ncols=d)                       # Step 2
     qtsb = C[:, 0]
     p = _qr.numerical_rank(R, rcond)

@@ -23,24 +23,32 @@ def s_hashing_matrix(seed, s, m, n):
 
 
 def s_hashing_variant_matrix(seed, s, m, n):
-    """The m x n s-hashing VARIANT of Def. 7: s draws with replacement, entries add."""
-    idx, sign = hashing.variant_table(seed, s, m, n)
+    """The m x n s-hashing VARIANT of Def. 7, built column by column (dense).
+
+    For each column j, each of the s draws (with replacement) ADDS +-1/sqrt(s)
+    to its row, so a row drawn twice holds the sum.  Only for small n.
+    """
     T = np.zeros((m, n), dtype=np.float64)
-    for k in range(s):
-        np.add.at(T, (idx[:, k], np.arange(n)), sign[:, k] / np.sqrt(s))
+    scale = 1.0 / np.sqrt(s)
+    for j in range(n):
+        rows, signs = hashing.variant_column_rows_int(seed, s, m, j)
+        for i, sg in zip(rows, signs):
+            T[i, j] += sg * scale
     return T
 
 
-def sketch_rows(seed, s, m, A, b=None):
+def sketch_rows(seed, s, m, A, b=None, variant=False):
     """S*A (and S*b) for the s-hashing matrix of Def. 5, row by row of A.
 
     Row j of A is added, with sign sign[j,k]/sqrt(s), to row idx[j,k] of SA for
     each k < s: the product S*A written out over the nonzeros of S (Step 1 of
     Algorithm 1).  A may be dense (n x d ndarray) or a scipy CSR matrix.
+    variant=True uses the draws of the s-hashing variant T (Def. 7) instead;
+    the same accumulation then adds coinciding draws.
     Returns SA (m x d) or, when b is given, the augmented [SA | Sb] (m x (d+1)).
     """
     n, d = A.shape
-    idx, sign = hashing.hash_table(seed, s, m, n)
+    idx, sign = (hashing.variant_table if variant else hashing.hash_table)(seed, s, m, n)
     scale = 1.0 / np.sqrt(s)
     cols = d + (1 if b is not None else 0)
     out = np.zeros((m, cols), dtype=np.float64)

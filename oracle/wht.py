@@ -52,11 +52,12 @@ def premix(seed, A, n_pad):
     return fwht_rows(Y) / np.sqrt(n_pad)
 
 
-def hrht_sketch(seed, s, m, A, b=None, n_pad=None):
-    """[S_h H D A | S_h H D b] for the HRHT sketch of Def. 8 with an s-hashing S_h."""
+def hrht_sketch(seed, s, m, A, b=None, n_pad=None, variant=False):
+    """[S_h H D A | S_h H D b] for the HRHT sketch of Def. 8 with an s-hashing S_h
+    (the s-hashing variant of Def. 7 when variant=True)."""
     n = A.shape[0]
     if n_pad is None:
         n_pad = 1 << max(0, (n - 1).bit_length())
     Y = premix(seed, A, n_pad)
     yb = premix(seed, b, n_pad) if b is not None else None
-    return sketch.sketch_rows(seed, s, m, Y, yb)
+    return sketch.sketch_rows(seed, s, m, Y, yb, variant=variant)

@@ -52,6 +52,17 @@ def test_ski_lls_matches_lstsq(premix):
     assert info["iters"] > 0
 
 
+@pytest.mark.parametrize("premix,s", [(False, 3), (True, 2)])
+def test_ski_lls_with_s_hashing_variant(premix, s):
+    # Def. 7's variant (Theorems 4-5: an embedding like s-hashing) preconditions
+    # Algorithm 1 as well; the accepted x is the least-squares solution
+    A, b, _ = workloads.gaussian_lls(1024, 64, seed=8)
+    x, info = lsqr.ski_lls(A, b, seed=19, s=s, m=128, premix=premix, variant=True)
+    xr = lsqr.lstsq_reference(A, b)
+    assert np.linalg.norm(x - xr) <= 1e-10 * np.linalg.norm(xr)
+    assert lsqr.residual_metric(A, b, x) <= 1e-10
+
+
 def test_ski_lls_sparse():
     rp, ci, v, b = workloads.csr_heavy_rows(4000, 100, seed=3, nnz_row=8, heavy_frac=0.005, heavy_nnz=60)
     A = sp.csr_matrix((v, ci, rp), shape=(4000, 100))
