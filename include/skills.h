@@ -54,6 +54,8 @@ typedef enum {
  * significant bits), where SKI_F32 takes three passes (about FP32 accuracy). */
 typedef enum { SKI_F64 = 0, SKI_F32 = 1, SKI_BF16 = 2, SKI_TF32 = 3 } ski_dtype;
 typedef enum { SKI_DENSE = 0, SKI_CSR = 1 } ski_kind;
+/* The sketching matrix: s-hashing (Def. 5) or the s-hashing variant (Def. 7). */
+typedef enum { SKI_S_HASHING = 0, SKI_S_HASHING_VARIANT = 1 } ski_hash_kind;
 
 /* The data matrix A (n x d).  Values are FP64 in both layouts. */
 typedef struct {
@@ -95,7 +97,9 @@ typedef struct {
                           /* 0 = auto (min(152, n / 16)); raised to n / 16384 at least  */
   int32_t graphs;         /* 1: each chunk of 8 LSQR (or CG) iterations is recorded    */
                           /* once per solve as a CUDA graph and replayed; 0: launched   */
-  int32_t pad2_;
+  int32_t hash_kind;      /* ski_hash_kind of S_h: 0 = s-hashing (Def. 5: s distinct    */
+                          /* rows per column), 1 = the s-hashing variant (Def. 7: s     */
+                          /* rows drawn with replacement, coinciding entries add)       */
 } ski_opts;
 
 /* Result record of a solve (host memory). */
@@ -161,10 +165,29 @@ ski_status ski_selftest_wait_timeout(int64_t spin_limit, void* ws, size_t ws_byt
  * whose row differs from those of nonzeros 0..k-1, and sign -1 exactly when
  * the top bit of key(0x5A, j, k, 0) is set.  D of Def. 8 uses key(0xD3, j, 0, 0).
  *   idx  device int32 [n*s], sign device int8 [n*s] (+1 / -1).
- * Asynchronous.  Errors: SKI_EINVAL unless 1 <= s <= m < 2^31 and n >= 0.
+ * Asynchronous.  Errors: SKI_EINVAL unless 1 <= s <= min(m, 64), m < 2^31
+ * and n >= 0.
  */
 ski_status ski_hash_indices(uint64_t seed, int32_t s, int64_t m, int64_t n,
                             int32_t* idx, int8_t* sign, void* stream);
+
+/*
+ * ski_hash_variant_indices -- the draws of the s-hashing variant T (Def. 7).
+ * Column j < n of T adds sign[j*s+k] / sqrt(s) to row idx[j*s+k] for each
+ * k < s; the s rows are drawn with replacement, so two draws may name the same
+ * row, whose entry is then their sum (0 or +-2/sqrt(s) when s >= 2).  Draw k
+ * is the retry-0 draw of ski_hash_indices: row floor(key(0xB1, j, k, 0) * m /
+ * 2^64), sign from key(0x5A, j, k, 0).  Wherever the s rows of a column of T
+ * are distinct, that column equals the column of the s-hashing matrix with
+ * the same seed; with s = 1 the two are the same 1-hashing matrix.  Setting
+ * ski_opts.hash_kind = 1 sketches with T (Lemma 5: T = (S1 + ... + Ss) / sqrt(s)
+ * for independent 1-hashing matrices Sk).
+ *   idx  device int32 [n*s], sign device int8 [n*s] (+1 / -1).
+ * Asynchronous.  Errors: SKI_EINVAL unless 1 <= s <= 64, 1 <= m < 2^31 and
+ * n >= 0.
+ */
+ski_status ski_hash_variant_indices(uint64_t seed, int32_t s, int64_t m, int64_t n,
+                                    int32_t* idx, int8_t* sign, void* stream);
 
 /*
  * ski_premix_signs -- the diagonal of D in the HRHT premix (Def. 8), D[j] in

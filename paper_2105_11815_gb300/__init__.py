@@ -13,11 +13,11 @@ import ctypes
 import os
 
 __all__ = [
-    "SKI_F64", "SKI_F32", "SKI_BF16", "SKI_DENSE", "SKI_CSR", "SkiError",
+    "SKI_F64", "SKI_F32", "SKI_BF16", "SKI_DENSE", "SKI_CSR", "SKI_S_HASHING", "SKI_S_HASHING_VARIANT", "SkiError",
     "ski_opts", "ski_info", "ski_matrix", "lib", "lib_path",
     "ski_opts_default", "ski_status_string", "ski_version", "ski_last_cuda_error", "ski_launch_count",
     "ski_selftest_wait_timeout",
-    "ski_hash_indices", "ski_premix_signs", "ski_premix_workspace_size", "ski_premix",
+    "ski_hash_indices", "ski_hash_variant_indices", "ski_premix_signs", "ski_premix_workspace_size", "ski_premix",
     "ski_sketch_workspace_size", "ski_sketch_hash", "ski_sketch_hash_noalloc",
     "ski_precondition_workspace_size", "ski_precondition",
     "ski_gemm_tc_f32", "ski_trinv_workspace_size", "ski_trinv",
@@ -30,6 +30,7 @@ __all__ = [
 
 SKI_F64, SKI_F32, SKI_BF16, SKI_TF32 = 0, 1, 2, 3
 SKI_DENSE, SKI_CSR = 0, 1
+SKI_S_HASHING, SKI_S_HASHING_VARIANT = 0, 1
 STATUS = ["SKI_OK", "SKI_EINVAL", "SKI_ENOMEM", "SKI_ECUDA", "SKI_ENONFINITE",
           "SKI_ESINGULAR", "SKI_ENOCONV", "SKI_ETIMEOUT"]
 
@@ -59,7 +60,7 @@ class ski_opts(ctypes.Structure):
                 ("rcond", ctypes.c_double), ("perturb", ctypes.c_double), ("it_max", ctypes.c_int64),
                 ("streams", ctypes.c_int32), ("premix_slab", ctypes.c_int32),
                 ("lsqr_pass", ctypes.c_int32), ("lsqr_ctas", ctypes.c_int32), ("graphs", ctypes.c_int32),
-                ("pad2_", ctypes.c_int32)]
+                ("hash_kind", ctypes.c_int32)]
 
 
 class ski_info(ctypes.Structure):
@@ -89,6 +90,7 @@ _SIGS = {
     "ski_launch_count": (_I64, []),
     "ski_selftest_wait_timeout": (_I32, [_I64, _P, _SZ, _P]),
     "ski_hash_indices": (_I32, [_U64, _I32, _I64, _I64, _P, _P, _P]),
+    "ski_hash_variant_indices": (_I32, [_U64, _I32, _I64, _I64, _P, _P, _P]),
     "ski_premix_signs": (_I32, [_U64, _I64, _P, _P]),
     "ski_premix_workspace_size": (_SZ, [_MP, _I32, _OP]),
     "ski_premix": (_I32, [_MP, _P, _OP, _P, _I64, _P, _SZ, _P]),
@@ -213,6 +215,11 @@ def ski_selftest_wait_timeout(spin_limit, ws=None, stream=None):
 # ---------------------------------------------------------------- entry points
 def ski_hash_indices(seed, s, m, n, idx, sign, stream=None):
     return _check(lib().ski_hash_indices(seed, s, m, n, _ptr(idx), _ptr(sign), _stream(stream)), "ski_hash_indices")
+
+
+def ski_hash_variant_indices(seed, s, m, n, idx, sign, stream=None):
+    return _check(lib().ski_hash_variant_indices(seed, s, m, n, _ptr(idx), _ptr(sign), _stream(stream)),
+                  "ski_hash_variant_indices")
 
 
 def ski_premix_signs(seed, n, D, stream=None):

@@ -94,14 +94,14 @@ static bool launch_opts_ok(const ski_opts* o) {
 
 static ski_status check_sketch_opts(const ski_matrix* A, const ski_opts* o) {
   if (!o) return SKI_EINVAL;
-  if (o->s < 1 || o->s > 64 || o->m < o->s || o->m >= (1ll << 31)) return SKI_EINVAL;
+  if (o->hash_kind != 0 && o->hash_kind != 1) return SKI_EINVAL;
+  if (o->s < 1 || o->s > 64 || o->m < (o->hash_kind ? 1 : o->s) || o->m >= (1ll << 31)) return SKI_EINVAL;
   if (o->premix_slab < 0 || o->streams < 0) return SKI_EINVAL;
   if (!launch_opts_ok(o)) return SKI_EINVAL;
   if (!dtype_ok(o->sketch_dtype)) return SKI_EINVAL;
   if (o->premix) {
     if (A->kind != SKI_DENSE) return SKI_EINVAL;
     if (o->n_pad != 0 && (!pow2(o->n_pad) || o->n_pad < A->n)) return SKI_EINVAL;
-    if (o->sketch_dtype == SKI_BF16 && false) return SKI_EINVAL;
   }
   const int64_t rows = o->premix ? (o->n_pad ? o->n_pad : next_pow2(A->n)) : A->n;
   if (rows * (int64_t)o->s >= (1ll << 31) || rows >= (1ll << 31)) return SKI_EINVAL;
@@ -173,7 +173,7 @@ static ski_status sketch_run(const ski_matrix* A, const double* b, const ski_opt
   if (!ar.ok() || !bkws) return SKI_ENOMEM;
   SkiArena bar{bkws, bkb, 0, false};
   SkiBuckets bk;
-  SKI_TRY(ski_build_buckets(o->seed, o->s, o->m, rows, bar, st, &bk));
+  SKI_TRY(ski_build_buckets(o->seed, o->s, o->hash_kind, o->m, rows, bar, st, &bk));
   if (e_bk) SKI_CUDA_TRY(cudaEventRecord(e_bk, st));
   const double inv_sqrt_s = 1.0 / sqrt((double)o->s);
   if (!o->premix) {

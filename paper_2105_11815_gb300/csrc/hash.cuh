@@ -7,6 +7,8 @@
 //   key     = sm(sm(sm(seed ^ tag<<56) ^ j) ^ (k<<32 | t))      (mod 2^64)
 //   row     = high 64 bits of key(BUCKET, j, k, t) * m; nonzero k keeps the
 //             first t whose row differs from the rows of nonzeros 0..k-1
+//             (Def. 5, without replacement); the s-hashing variant (Def. 7,
+//             with replacement) keeps t = 0 for every k
 //   sign    = -1 iff the top bit of key(SIGN, j, k, 0) is set
 //   D_j     = -1 iff the top bit of key(PREMIX, j, 0, 0) is set
 #pragma once
@@ -32,9 +34,11 @@ __device__ __forceinline__ uint64_t ski_key(uint64_t base, uint64_t j, uint32_t 
   return ski_sm64(ski_sm64(base ^ j) ^ (((uint64_t)k << 32) | (uint64_t)t));
 }
 
-// Rows and signs of column j (s <= SMAX).  Rows are distinct.
+// Rows and signs of column j (s <= SMAX).  Rows are distinct unless
+// `replace` (the s-hashing variant), where coinciding rows are kept and their
+// entries add.
 template <int SMAX>
-__device__ __forceinline__ void ski_column(uint64_t kb, uint64_t ks, int s, uint64_t m, uint64_t j,
+__device__ __forceinline__ void ski_column(uint64_t kb, uint64_t ks, int s, uint64_t m, uint64_t j, int replace,
                                            int32_t* rows, int* neg) {
   for (int k = 0; k < s && k < SMAX; ++k) {
     uint32_t t = 0;
@@ -43,7 +47,7 @@ __device__ __forceinline__ void ski_column(uint64_t kb, uint64_t ks, int s, uint
       r = (int32_t)__umul64hi(ski_key(kb, j, (uint32_t)k, t), m);
       bool clash = false;
       for (int kk = 0; kk < k; ++kk) clash |= (rows[kk] == r);
-      if (!clash) break;
+      if (!clash || replace) break;
       ++t;
     }
     rows[k] = r;

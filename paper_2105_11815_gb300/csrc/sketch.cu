@@ -16,13 +16,13 @@
 
 // ------------------------------------------------------------ hash tables
 template <int SMAX>
-__global__ void k_hash_table(uint64_t kb, uint64_t ks, int s, uint64_t m, int64_t n, int32_t* idx,
+__global__ void k_hash_table(uint64_t kb, uint64_t ks, int s, uint64_t m, int64_t n, int replace, int32_t* idx,
                              int8_t* sign) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n) return;
   int32_t rows[SMAX];
   int neg[SMAX];
-  ski_column<SMAX>(kb, ks, s, m, (uint64_t)j, rows, neg);
+  ski_column<SMAX>(kb, ks, s, m, (uint64_t)j, replace, rows, neg);
   for (int k = 0; k < s; ++k) {
     idx[j * s + k] = rows[k];
     sign[j * s + k] = neg[k] ? (int8_t)-1 : (int8_t)1;
@@ -36,14 +36,14 @@ __global__ void k_premix_signs(uint64_t kd, int64_t n, int8_t* D) {
 
 // Count pass: draw the column, store its (row, sign) pairs, count per bucket.
 template <int SMAX>
-__global__ void k_bucket_count(uint64_t kb, uint64_t ks, int s, uint64_t m, int64_t n,
+__global__ void k_bucket_count(uint64_t kb, uint64_t ks, int s, uint64_t m, int64_t n, int replace,
                                int32_t* __restrict__ pair_row, uint8_t* __restrict__ pair_neg,
                                int32_t* __restrict__ counts) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n) return;
   int32_t rows[SMAX];
   int neg[SMAX];
-  ski_column<SMAX>(kb, ks, s, m, (uint64_t)j, rows, neg);
+  ski_column<SMAX>(kb, ks, s, m, (uint64_t)j, replace, rows, neg);
   for (int k = 0; k < s; ++k) {
     pair_row[j * s + k] = rows[k];
     pair_neg[j * s + k] = (uint8_t)neg[k];
@@ -101,7 +101,9 @@ __global__ void k_bucket_fill(int s, int64_t n, const int32_t* __restrict__ pair
 
 // Canonical order inside each bucket (ascending entry), so that the sketch is
 // bit-reproducible whatever order the fill's atomics took.  One warp per
-// bucket: rank sort (entries are distinct), O(K^2 / 32) per bucket.
+// bucket: rank sort, O(K^2 / 32) per bucket.  Entries are distinct for
+// s-hashing; the variant can repeat one (same j and sign twice), and equal
+// entries take consecutive ranks in list order (they are interchangeable).
 __global__ void k_bucket_sort(int64_t m, const int64_t* __restrict__ offsets, const uint32_t* __restrict__ list_in,
                               uint32_t* __restrict__ list_out) {
   int64_t bkt = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -112,7 +114,10 @@ __global__ void k_bucket_sort(int64_t m, const int64_t* __restrict__ offsets, co
   for (int64_t a = lane; a < K; a += 32) {
     uint32_t v = list_in[lo + a];
     int64_t rank = 0;
-    for (int64_t c = 0; c < K; ++c) rank += (list_in[lo + c] < v);
+    for (int64_t c = 0; c < K; ++c) {
+      const uint32_t w = list_in[lo + c];
+      rank += (w < v) | ((w == v) & (c < a));
+    }
     list_out[lo + rank] = v;
   }
 }
@@ -637,7 +642,7 @@ size_t ski_bucket_ws_bytes(int64_t nrows, int32_t s, int64_t m) {
   return ar.off;
 }
 
-ski_status ski_build_buckets(uint64_t seed, int32_t s, int64_t m, int64_t nrows, SkiArena& ar,
+ski_status ski_build_buckets(uint64_t seed, int32_t s, int32_t replace, int64_t m, int64_t nrows, SkiArena& ar,
                              cudaStream_t st, SkiBuckets* out) {
   int32_t* pair_row = ar.take<int32_t>(nrows * s);
   uint8_t* pair_neg = ar.take<uint8_t>(nrows * s);
@@ -653,9 +658,9 @@ ski_status ski_build_buckets(uint64_t seed, int32_t s, int64_t m, int64_t nrows,
   const int T = 256;
   if (nrows > 0) {
     if (s <= 4)
-      k_bucket_count<4><<<ski_cdiv(nrows, T), T, 0, st>>>(kb, ks, s, m, nrows, pair_row, pair_neg, counts);
+      k_bucket_count<4><<<ski_cdiv(nrows, T), T, 0, st>>>(kb, ks, s, m, nrows, replace, pair_row, pair_neg, counts);
     else
-      k_bucket_count<64><<<ski_cdiv(nrows, T), T, 0, st>>>(kb, ks, s, m, nrows, pair_row, pair_neg, counts);
+      k_bucket_count<64><<<ski_cdiv(nrows, T), T, 0, st>>>(kb, ks, s, m, nrows, replace, pair_row, pair_neg, counts);
     SKI_LAUNCH_CHECK();
   }
   k_scan_counts<<<1, 1024, 0, st>>>(counts, m, offsets);
@@ -787,19 +792,29 @@ ski_status ski_gather_csr(const ski_matrix* A, const double* b, const SkiBuckets
   return SKI_OK;
 }
 
-extern "C" ski_status ski_hash_indices(uint64_t seed, int32_t s, int64_t m, int64_t n, int32_t* idx,
-                                       int8_t* sign, void* stream) {
-  if (s < 1 || m < s || m >= (1ll << 31) || n < 0 || s > 64) return SKI_EINVAL;
+static ski_status hash_indices(uint64_t seed, int32_t s, int replace, int64_t m, int64_t n, int32_t* idx,
+                               int8_t* sign, void* stream) {
+  if (s < 1 || m < (replace ? 1 : s) || m >= (1ll << 31) || n < 0 || s > 64) return SKI_EINVAL;
   if (n == 0) return SKI_OK;
   if (!idx || !sign) return SKI_EINVAL;
   uint64_t kb = ski_tag_base(seed, SKI_TAG_BUCKET), ks = ski_tag_base(seed, SKI_TAG_SIGN);
   const int T = 256;
   if (s <= 4)
-    k_hash_table<4><<<ski_cdiv(n, T), T, 0, ski_stream(stream)>>>(kb, ks, s, (uint64_t)m, n, idx, sign);
+    k_hash_table<4><<<ski_cdiv(n, T), T, 0, ski_stream(stream)>>>(kb, ks, s, (uint64_t)m, n, replace, idx, sign);
   else
-    k_hash_table<64><<<ski_cdiv(n, T), T, 0, ski_stream(stream)>>>(kb, ks, s, (uint64_t)m, n, idx, sign);
+    k_hash_table<64><<<ski_cdiv(n, T), T, 0, ski_stream(stream)>>>(kb, ks, s, (uint64_t)m, n, replace, idx, sign);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
+}
+
+extern "C" ski_status ski_hash_indices(uint64_t seed, int32_t s, int64_t m, int64_t n, int32_t* idx,
+                                       int8_t* sign, void* stream) {
+  return hash_indices(seed, s, 0, m, n, idx, sign, stream);
+}
+
+extern "C" ski_status ski_hash_variant_indices(uint64_t seed, int32_t s, int64_t m, int64_t n, int32_t* idx,
+                                               int8_t* sign, void* stream) {
+  return hash_indices(seed, s, 1, m, n, idx, sign, stream);
 }
 
 extern "C" ski_status ski_premix_signs(uint64_t seed, int64_t n, int8_t* D, void* stream) {

@@ -20,7 +20,7 @@ __device__ __forceinline__ double fx_scaled(const FxAcc& a, long long c, int e) 
 
 // ---- sketch.cu
 size_t ski_bucket_ws_bytes(int64_t nrows, int32_t s, int64_t m);
-ski_status ski_build_buckets(uint64_t seed, int32_t s, int64_t m, int64_t nrows, SkiArena& ar,
+ski_status ski_build_buckets(uint64_t seed, int32_t s, int32_t replace, int64_t m, int64_t nrows, SkiArena& ar,
                              cudaStream_t st, SkiBuckets* out);
 ski_status ski_gather_dense(const double* A, int64_t lda, int64_t nrows, int64_t d, const double* b,
                             const SkiBuckets& bk, double scale, int32_t out_dtype, void* SA, int64_t ld_sa,

@@ -57,6 +57,19 @@ def test_argument_errors_before_launch(lib):
     assert L.ski_hash_indices(1, 1, 1 << 31, 10, None, None, None) == 1
     assert L.ski_hash_indices(1, 1, 4, -1, None, None, None) == 1
     assert L.ski_hash_indices(1, 1, 4, 0, None, None, None) == 0  # empty: nothing to do
+    # the variant (Def. 7) draws with replacement: s > m is valid, s > 64 and m < 1 are not
+    assert L.ski_hash_variant_indices(1, 5, 4, 0, None, None, None) == 0
+    assert L.ski_hash_variant_indices(1, 5, 4, 10, None, None, None) == 1   # valid sizes, null outputs
+    assert L.ski_hash_variant_indices(1, 65, 100, 0, None, None, None) == 1
+    assert L.ski_hash_variant_indices(1, 1, 0, 0, None, None, None) == 1
+    A_ = _fake_dense(lib, 100, 3)
+    for hk, ok_ in ((0, True), (1, True), (2, False), (-1, False)):
+        o_ = lib.ski_opts_default(m=20, s=2, hash_kind=hk)
+        assert (L.ski_sketch_workspace_size(ctypes.byref(A_), 1, ctypes.byref(o_)) > 0) == ok_
+    o_ = lib.ski_opts_default(m=2, s=3, hash_kind=1)    # s > m: only the variant allows it
+    assert L.ski_sketch_workspace_size(ctypes.byref(A_), 1, ctypes.byref(o_)) > 0
+    o_.hash_kind = 0
+    assert L.ski_sketch_workspace_size(ctypes.byref(A_), 1, ctypes.byref(o_)) == 0
     A = _fake_dense(lib, 100, 10)
     bad = lib.ski_opts_default(m=5, s=1)          # m < d
     x = ctypes.c_void_p(0x2000)
