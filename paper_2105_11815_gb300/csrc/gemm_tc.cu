@@ -342,7 +342,7 @@ bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, i
 
 // 2-D FP64 tensor map over a row-major rows x cols matrix (row stride ld
 // elements, a multiple of 2), box = box_rows x box_cols, no swizzle, zero
-// fill outside the matrix.  False when the driver entry point is missing or
+// fill outside the matrix.  False when the CUDA driver's cuTensorMapEncodeTiled is missing or
 // the encoding is refused.
 bool ski_tmap_f64_2d(CUtensorMap* map, const double* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
                      int box_cols) {

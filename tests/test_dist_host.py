@@ -74,7 +74,7 @@ def test_reference_arm_runs_on_rank_zero_only(workload):
 
 def test_reference_arm_line_keeps_the_bench_contract():
     # the oracle arm on the small dense workload (CPU only): one JSON line with
-    # the keys the driver reads, its value equal to its own cpu_baseline and e2e
+    # every key of the benchmark line contract, its value equal to its own cpu_baseline and e2e
     import json
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
