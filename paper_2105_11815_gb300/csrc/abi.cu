@@ -366,9 +366,21 @@ struct SolvePlan {
 };
 
 // Mixed form: LSQR iterations allowed with an FP32 / TF32 preconditioner
-// before Steps 1-2 are redone in FP64 (an FP64-preconditioned solve of the
-// dense test set takes ~60).
-constexpr int64_t kMixedLsqrBudget = 150;
+// before Steps 1-2 are redone in FP64.  Theorem 10 bounds the iterations with
+// an eps-subspace embedding by (log 2 + |log tau_r|) / |log eps|, and a hashing
+// sketch of m = gamma d rows embeds with eps ~ gamma^(-1/2) (m = O(d / eps^2)).
+// The budget is 2.2 times that bound with eps = sqrt(d / m), and at least 150.
+// At m = 2d and tau_r = 1e-10 the two coincide (an FP64-preconditioned solve
+// of the dense test set takes 58 there).  A fixed 150 made every mixed solve
+// with m < 1.4 d refactor in FP64 although its FP32 factor preconditioned as
+// well as the FP64 one: 197 iterations against 192 at m = 1.2 d.
+int64_t mixed_lsqr_budget(int64_t m, int64_t d, double tau_r) {
+  constexpr double kFloor = 150.0, kCap = 4000.0;
+  if (!(tau_r > 0.0 && tau_r < 1.0) || d < 1) return (int64_t)kFloor;
+  if (m <= d) return (int64_t)kCap;
+  const double bound = (log(2.0) - log(tau_r)) / (0.5 * log((double)m / (double)d));
+  return (int64_t)std::max(kFloor, std::min(kCap, ceil(2.2 * bound)));
+}
 // Largest max|r_ii| / min|r_ii| of an FP32 (TF32) factor kept as the
 // preconditioner: kappa(SA) u must stay well below 1 for R^{-1} to
 // precondition, with u the coarser of the factorisation's unit roundoff
@@ -387,11 +399,11 @@ double mixed_ratio_limit(int32_t qr_dtype, int32_t sketch_dtype) {
 // After >= 24 iterations, the Eq. TC-lsqr estimate extrapolated geometrically
 // (test_k ~ rho^k from test_0 = 1) predicts more than the budget: the FP32
 // preconditioner is too weak, so stop early instead of spending the budget.
-bool weak_preconditioner(double test, long long iters, double tau_r) {
+bool weak_preconditioner(double test, long long iters, double tau_r, int64_t budget) {
   if (iters < 24 || !(tau_r > 0.0) || !(tau_r < 1.0)) return false;
   if (!(test < 1.0)) return true;
   if (test <= tau_r) return false;
-  return (double)iters * log(tau_r) / log(test) > (double)kMixedLsqrBudget;
+  return (double)iters * log(tau_r) / log(test) > (double)budget;
 }
 
 // Bytes of the phase region for the sketch / QR / trinv precisions of o.
@@ -804,8 +816,9 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
       LsqrScalars init = hs;
       init.iters = 0;
       init.it_max = o->it_max - iters_total;
-      const bool budgeted = mixed && !fell_back && init.it_max > kMixedLsqrBudget;
-      if (budgeted) init.it_max = kMixedLsqrBudget;
+      const int64_t budget = mixed_lsqr_budget(o->m, d, o->tau_r);
+      const bool budgeted = mixed && !fell_back && init.it_max > budget;
+      if (budgeted) init.it_max = budget;
       init.flag_a = 0;
       init.flag_b = 0;
       init.conv = 0;
@@ -824,7 +837,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
         SKI_TRY(read_scalars(P, &hs, st));
         if (hs.flag_a) break;
         if (polled > o->it_max + CHUNK) break;
-        if (budgeted && weak_preconditioner(hs.test, hs.iters, o->tau_r)) break;
+        if (budgeted && weak_preconditioner(hs.test, hs.iters, o->tau_r, budget)) break;
       }
       iters_total += hs.iters;
       lsqr_test = hs.test;

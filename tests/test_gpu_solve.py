@@ -82,6 +82,25 @@ def test_mixed_precision_solve(sd, qd):
     assert olsqr.residual_metric(A, b, x) <= 1e-10
 
 
+def test_mixed_budget_grows_as_the_sketch_shrinks():
+    # m = 1.2 d: the larger distortion of the smaller sketch raises the LSQR
+    # iteration count for the FP64 and the FP32 factor alike.  The mixed
+    # form's budget follows Theorem 10's bound with eps = sqrt(d / m), so the
+    # FP32 factor is kept where a fixed 150 iterations would have refactored
+    torch, pkg = cuda()
+    n, d = 20000, 400
+    A, b = workloads.dense_gaussian(n, d, seed=12)
+    kw = dict(m=480, s=1, seed=5, premix=1, n_pad=32768)
+    x64, i64 = _solve(torch, pkg, A, b, **kw)
+    xm, im = _solve(torch, pkg, A, b, sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32, **kw)
+    assert i64.status == 0 and im.status == 0
+    assert i64.iters > 150
+    assert im.qr_fallback == 0, (im.iters, i64.iters)
+    assert abs(im.iters - i64.iters) <= 0.1 * i64.iters + 5
+    _assert_solution(A, b, xm)
+    _assert_solution(A, b, x64)
+
+
 def test_bf16_sketch_factor_kept_only_when_well_conditioned():
     # A BF16 sketch carries 2^-9 rounding: its FP32 factor preconditions a
     # well-conditioned A (kept) but not kappa = 1e6, where the diagonal ratio
