@@ -33,7 +33,7 @@ namespace {
 
 constexpr int NB = 32;
 constexpr int PW = 2 * NB;  // partial slot: g[32] then the diagonal row[32]
-constexpr int64_t kClusterRowsF64 = 4096;  // FP64 panels this short take the cluster kernel
+constexpr int64_t kClusterRowsF64 = 16384;  // FP64 panels up to this height may take the cluster kernel
 constexpr int WARPS = 8;
 constexpr long long kSpinLimit = 1ll << 24;  // ~1 s of polling at ~64 ns per poll
 
@@ -612,12 +612,16 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
   constexpr int CNW = 32;  // 32 warps: 16 hid too little of each step's row-loop latency (36.5 -> 32.1 ms at 8000 x 4000)
   int CL = 0;
   bool cluster_ok = false;
-  // FP32, and FP64 panels of at most kClusterRowsF64 rows: a tall FP64 panel
-  // does its rank-1 updates on the 1/64-rate FP64 pipe, which 64 SMs
-  // (grid-barrier kernel) finish sooner than 16; a short one is bound by the
-  // per-column synchronisation, which the cluster barrier does faster -- and
-  // 16-CTA clusters run beside the other streams' work, where a cooperative
-  // grid waits for 64 free SMs.
+  // FP32, and FP64 panels of at most kClusterRowsF64 rows whose slabs fit in
+  // shared memory (about 12400 rows with 16 CTAs).  A tall FP64 panel does its
+  // rank-1 updates on the 1/64-rate FP64 pipe, which 64 SMs (grid-barrier
+  // kernel) finish sooner than 16.  But the FP64 QR is bound by the trailing
+  // update that runs beside the panel, and a 16-CTA cluster leaves it 136
+  // SMs instead of 88: the FP64 QR of 8000 x 4001 took 245.5 ms with cluster
+  // panels against 250.3 ms with grid-barrier panels above 4096 rows.  A
+  // short panel is bound by the per-column synchronisation, which the cluster
+  // barrier does faster; and 16-CTA clusters run beside the other streams'
+  // work, where a cooperative grid waits for 64 free SMs.
   if (sizeof(T) == 4 || m <= kClusterRowsF64) {
     const size_t big = (size_t)(200 * 1024 + 2 * PW * sizeof(T));
     if (cudaFuncSetAttribute(k_panel_cluster<T, CNW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
