@@ -143,6 +143,16 @@ int32_t ski_last_cuda_error(void);
  * (all threads).  Diagnostic: lets a caller count the kernels of a region. */
 int64_t ski_launch_count(void);
 
+/* LSQR iterations the mixed form (qr_dtype or sketch_dtype not SKI_F64) runs
+ * with its FP32 / TF32 factor before Steps 1-2 are redone in FP64 (reported as
+ * ski_info.qr_fallback = 2).  Theorem 10 bounds the iterations with an
+ * eps-subspace embedding by (log 2 + |log tau_r|) / |log eps|; a hashing sketch
+ * of m rows for d columns embeds with eps ~ sqrt(d / m) (m = O(d / eps^2)).
+ * The budget is ceil(2.2 * that bound) at eps = sqrt(d / m), at least 150 and
+ * at most 4000; 150 when tau_r is not in (0, 1) or d < 1, 4000 when m <= d.
+ * Host only: launches nothing. */
+int64_t ski_mixed_lsqr_budget(int64_t m, int64_t d, double tau_r);
+
 /*
  * ski_selftest_wait_timeout -- checks the library's bounded device-side wait
  * (the grid barrier of the persistent QR panel kernel) on the GPU without a

@@ -16,7 +16,7 @@ __all__ = [
     "SKI_F64", "SKI_F32", "SKI_BF16", "SKI_DENSE", "SKI_CSR", "SKI_S_HASHING", "SKI_S_HASHING_VARIANT", "SkiError",
     "ski_opts", "ski_info", "ski_matrix", "lib", "lib_path",
     "ski_opts_default", "ski_status_string", "ski_version", "ski_last_cuda_error", "ski_launch_count",
-    "ski_selftest_wait_timeout",
+    "ski_selftest_wait_timeout", "ski_mixed_lsqr_budget",
     "ski_hash_indices", "ski_hash_variant_indices", "ski_premix_signs", "ski_premix_workspace_size", "ski_premix",
     "ski_sketch_workspace_size", "ski_sketch_hash", "ski_sketch_hash_noalloc",
     "ski_precondition_workspace_size", "ski_precondition",
@@ -88,6 +88,7 @@ _SIGS = {
     "ski_version": (_I32, []),
     "ski_last_cuda_error": (_I32, []),
     "ski_launch_count": (_I64, []),
+    "ski_mixed_lsqr_budget": (_I64, [_I64, _I64, _D]),
     "ski_selftest_wait_timeout": (_I32, [_I64, _P, _SZ, _P]),
     "ski_hash_indices": (_I32, [_U64, _I32, _I64, _I64, _P, _P, _P]),
     "ski_hash_variant_indices": (_I32, [_U64, _I32, _I64, _I64, _P, _P, _P]),
@@ -203,6 +204,10 @@ def ski_last_cuda_error():
 
 def ski_launch_count():
     return lib().ski_launch_count()
+
+
+def ski_mixed_lsqr_budget(m, d, tau_r):
+    return lib().ski_mixed_lsqr_budget(m, d, tau_r)
 
 
 def ski_selftest_wait_timeout(spin_limit, ws=None, stream=None):

@@ -62,6 +62,11 @@ extern "C" int32_t ski_version(void) { return 100; }
 
 extern "C" int32_t ski_last_cuda_error(void) { return (int32_t)g_last_cuda; }
 
+namespace {
+int64_t mixed_lsqr_budget(int64_t m, int64_t d, double tau_r);
+}
+extern "C" int64_t ski_mixed_lsqr_budget(int64_t m, int64_t d, double tau_r) { return mixed_lsqr_budget(m, d, tau_r); }
+
 // ------------------------------------------------------------ validation
 static bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 static int64_t next_pow2(int64_t v) {

@@ -46,6 +46,28 @@ def test_host_only_entry_points(lib):
     assert (o.s, o.m, o.tau_a, o.tau_r, o.it_max, o.rcond) == (1, 10, 1e-8, 1e-6, 10000, 1e-12)
 
 
+def test_mixed_lsqr_budget_follows_theorem10(lib):
+    # 2.2 x (log 2 + |log tau_r|) / |log eps| with eps = sqrt(d / m), in [150, 4000]
+    import math
+
+    def bound(m, d, tau):
+        return (math.log(2) - math.log(tau)) / (0.5 * math.log(m / d))
+    assert lib.ski_mixed_lsqr_budget(8000, 4000, 1e-10) == 151          # m = 2d: the former fixed 150
+    assert lib.ski_mixed_lsqr_budget(8000, 4000, 1e-10) == math.ceil(2.2 * bound(8000, 4000, 1e-10))
+    assert lib.ski_mixed_lsqr_budget(4800, 4000, 1e-10) == math.ceil(2.2 * bound(4800, 4000, 1e-10)) > 500
+    assert lib.ski_mixed_lsqr_budget(480, 400, 1e-12) == math.ceil(2.2 * bound(480, 400, 1e-12))
+    assert lib.ski_mixed_lsqr_budget(40000, 1000, 1e-10) == 150           # large gamma: the floor
+    assert lib.ski_mixed_lsqr_budget(4000, 4000, 1e-10) == 4000           # m = d: no embedding bound
+    assert lib.ski_mixed_lsqr_budget(4001, 4000, 1e-10) == 4000           # capped
+    assert lib.ski_mixed_lsqr_budget(8000, 4000, 0.0) == 150              # tau_r outside (0, 1)
+    assert lib.ski_mixed_lsqr_budget(8000, 4000, 1.0) == 150
+    # monotone: a smaller sketch is allowed more iterations, a tighter tau_r too
+    ms = [4400, 4800, 5600, 6800, 8000]
+    b = [lib.ski_mixed_lsqr_budget(m, 4000, 1e-10) for m in ms]
+    assert b == sorted(b, reverse=True)
+    assert lib.ski_mixed_lsqr_budget(4800, 4000, 1e-12) > lib.ski_mixed_lsqr_budget(4800, 4000, 1e-10)
+
+
 def _fake_dense(lib, n, d):
     return lib.ski_matrix(kind=lib.SKI_DENSE, n=n, d=d, ld=d, val=0x1000, rowptr=None, colidx=None, nnz=0)
 
