@@ -77,8 +77,9 @@ typedef struct {
   int64_t m;              /* sketch rows, d <= m < 2^31                                */
   int64_t n_pad;          /* premix height, a power of two >= n; 0: next power of two */
   int32_t sketch_dtype;   /* ski_dtype of the premix, the sketch and its output SA     */
-  int32_t qr_dtype;       /* QR of SA and R^{-1}: SKI_F64, SKI_F32 (tensor-core products */
-                          /* in three TF32 passes) or SKI_TF32 (one); R kept in FP64    */
+  int32_t qr_dtype;       /* QR of SA: SKI_F64, SKI_F32 (tensor-core products in three  */
+                          /* TF32 passes) or SKI_TF32 (one); R kept in FP64.  R^{-1} is */
+                          /* formed in FP32 unless the FP64 form is needed (inv_dtype) */
   double tau_a;           /* Step 3: accept x_s when ||A x_s - b|| <= tau_a            */
   double tau_r;           /* Step 4: LSQR tolerance of Eq. TC-lsqr                     */
   double tol;             /* acceptance: ||A^T r|| / (||A||_F ||r||) <= tol, 0 = off   */
@@ -119,7 +120,12 @@ typedef struct {
   int32_t qr_fallback;         /* mixed form: 0 kept the FP32/TF32 factor; 1 redid     */
                                /* Steps 1-2 in FP64 (ratio or rank), 2 after its LSQR  */
                                /* run exhausted, or was predicted to exceed, a budget  */
-  int32_t pad_;
+                               /* (ski_mixed_lsqr_budget).  FP64 factor: 3 when its    */
+                               /* FP32 inverse met that budget and was redone in FP64  */
+  int32_t inv_dtype;           /* precision M = R^{-1} was formed in at the end:        */
+                               /* SKI_F32 when max|r_ii|/min|r_ii| <= 2^19 (the FP32   */
+                               /* factor's limit) and no fallback, else SKI_F64; the   */
+                               /* preconditioner is applied in FP64 either way         */
   double rdiag_ratio;          /* max |r_ii| / min |r_ii| of the first factor (the     */
                                /* requested precision; it decides the fallback)        */
 } ski_info;
@@ -145,7 +151,8 @@ int64_t ski_launch_count(void);
 
 /* LSQR iterations the mixed form (qr_dtype or sketch_dtype not SKI_F64) runs
  * with its FP32 / TF32 factor before Steps 1-2 are redone in FP64 (reported as
- * ski_info.qr_fallback = 2).  Theorem 10 bounds the iterations with an
+ * ski_info.qr_fallback = 2), and an FP64 factor with its inverse formed in FP32
+ * runs before that inverse is redone in FP64 (qr_fallback = 3).  Theorem 10 bounds the iterations with an
  * eps-subspace embedding by (log 2 + |log tau_r|) / |log eps|; a hashing sketch
  * of m rows for d columns embeds with eps ~ sqrt(d / m) (m = O(d / eps^2)).
  * The budget is ceil(2.2 * that bound) at eps = sqrt(d / m), at least 150 and

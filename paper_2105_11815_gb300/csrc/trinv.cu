@@ -6,7 +6,9 @@
 // with all 32 x 32 diagonal blocks inverted by back-substitution in one launch
 // and the off-diagonal blocks formed level by level by batched GEMMs (gemm.cu).  With perturb > 0
 // each diagonal entry r_ii is replaced by r_ii + perturb (the perturbed
-// back-solve of Ski-LLS-sparse).
+// back-solve of Ski-LLS-sparse).  The FP32 inverse works on R * 2^-e, with
+// 2^e the power of two of max |r_ij| (exact scaling), so that any FP64 R is in
+// FP32 range; M = (R 2^-e)^{-1} 2^-e.
 #include "common.cuh"
 #include "sketch_impl.cuh"
 
@@ -45,21 +47,44 @@ __global__ void k_diag_inv(int64_t d, const T* __restrict__ R, int64_t ldr, T* _
     if (lane < nbk) X[(o + i) * ldx + o + lane] = x[i];
 }
 
+// Largest biased exponent field over the upper triangle of R (atomicMax into
+// *emax, which starts at 0).
+__global__ void k_upper_max_exp(int64_t d, const double* __restrict__ R, int64_t ldr, int* __restrict__ emax) {
+  int e = 0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < d * d;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / d, c = idx % d;
+    if (c >= i) e = max(e, (int)((__double_as_longlong(R[i * ldr + c]) >> 52) & 0x7FF));
+  }
+  e = __reduce_max_sync(0xffffffffu, e);
+  if ((threadIdx.x & 31) == 0 && e > 0) atomicMax(emax, e);
+}
+// Scale shift of R for the FP32 inverse: max |r_ij| * 2^-sh lies in [1, 2).
+// No shift when R is all zero or holds a NaN / Inf (then the inverse is
+// non-finite in either precision).
+__device__ __forceinline__ int trinv_shift(const int* emax) {
+  if (!emax) return 0;
+  const int e = *emax;
+  return (e == 0 || e == 0x7FF) ? 0 : e - 1023;
+}
 template <class T>
-__global__ void k_cast_upper(int64_t d, const double* __restrict__ R, int64_t ldr, T* __restrict__ Rt, int64_t ldt) {
+__global__ void k_cast_upper(int64_t d, const double* __restrict__ R, int64_t ldr, T* __restrict__ Rt, int64_t ldt,
+                             const int* __restrict__ emax) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= d * d) return;
   int64_t i = idx / d, c = idx % d;
-  Rt[i * ldt + c] = c >= i ? (T)R[i * ldr + c] : T(0);
+  const int sh = trinv_shift(emax);
+  Rt[i * ldt + c] = c >= i ? (T)ldexp(R[i * ldr + c], -sh) : T(0);
 }
 
 template <class T>
 __global__ void k_emit(int64_t d, const T* __restrict__ X, int64_t ldx, double* __restrict__ M,
-                       double* __restrict__ Mt, int64_t ldm) {
+                       double* __restrict__ Mt, int64_t ldm, const int* __restrict__ emax) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= d * d) return;
   int64_t i = idx / d, c = idx % d;
-  double v = c >= i ? (double)X[i * ldx + c] : 0.0;
+  const int sh = trinv_shift(emax);
+  double v = c >= i ? ldexp((double)X[i * ldx + c], -sh) : 0.0;
   M[i * ldm + c] = v;
   if (Mt) Mt[c * ldm + i] = v;
 }
@@ -102,14 +127,21 @@ ski_status trinv_impl(int64_t d, const double* R, int64_t ldr, double* M, double
   T* Rt = ar.take<T>(d * d);
   T* X = ar.take<T>(d * d);
   T* tmp = ar.take<T>(ski_cdiv(d, 2) * d + LB * d);
-  if (!ar.ok() || !tmp) return SKI_ENOMEM;
+  int* emax = ar.take<int>(1);
+  if (!ar.ok() || !emax) return SKI_ENOMEM;
+  if (sizeof(T) == 8) emax = nullptr;  // the FP64 inverse needs no scaling
   SKI_CUDA_TRY(cudaMemsetAsync(X, 0, d * d * sizeof(T), st));
-  k_cast_upper<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, R, ldr, Rt, d);
+  if (emax) {
+    SKI_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(int), st));
+    k_upper_max_exp<<<(unsigned)std::min<int64_t>(4 * 152, ski_cdiv(d * d, 256)), 256, 0, st>>>(d, R, ldr, emax);
+    SKI_LAUNCH_CHECK();
+  }
+  k_cast_upper<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, R, ldr, Rt, d, emax);
   SKI_LAUNCH_CHECK();
   k_diag_inv<T><<<ski_cdiv(d, LB), 32, 0, st>>>(d, Rt, d, X, d, perturb);
   SKI_LAUNCH_CHECK();
   SKI_TRY(levels<T>(d, Rt, d, X, d, tmp, st));
-  k_emit<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, X, d, M, Mt, ldm);
+  k_emit<T><<<ski_cdiv(d * d, 256), 256, 0, st>>>(d, X, d, M, Mt, ldm, emax);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }
@@ -122,6 +154,7 @@ size_t ski_trinv_ws_bytes(int64_t d, int32_t dtype) {
   ar.take<char>(es * d * d);
   ar.take<char>(es * d * d);
   ar.take<char>(es * (ski_cdiv(d, 2) * d + LB * d));
+  ar.take<int>(1);
   return ar.off;
 }
 

@@ -39,6 +39,7 @@ def test_config1_plain_fp64():
     A, b, _ = workloads.gaussian_lls(4096, 256, seed=20210525)
     x, info = _solve(torch, pkg, A, b, m=512, s=1, seed=1)
     assert info.status == 0 and info.rank == 256
+    assert info.inv_dtype == pkg.SKI_F32 and info.qr_fallback == 0   # small diagonal ratio: R^{-1} in FP32
     _assert_solution(A, b, x)
     # same algorithm step by step in the oracle: iteration counts agree
     xo, oinfo = olsqr.ski_lls(A, b, seed=1, s=1, m=512, tau_r=1e-12)
@@ -79,6 +80,60 @@ def test_mixed_precision_solve(sd, qd):
     A, b = workloads.usv(8000, 200, 1e6, seed=2)
     x, info = _solve(torch, pkg, A, b, m=400, s=1, seed=5, premix=1, sketch_dtype=sd, qr_dtype=qd)
     assert info.status == 0
+    assert olsqr.residual_metric(A, b, x) <= 1e-10
+
+
+def _orthogonal_rows(n, d, seed):
+    return np.linalg.qr(np.random.default_rng(seed).standard_normal((n, d)))[0]
+
+
+def _rhs_with_orthogonal_residual(A, seed, Q=None):
+    # b = A x_true + e, e orthogonal to range(A) (spanned by the orthonormal Q):
+    # x stays O(1), so the FP64 metric's rounding floor u ||A|| ||x|| / ||r||
+    # is far below 1e-10
+    g = np.random.default_rng(seed)
+    Q = np.linalg.qr(A)[0] if Q is None else Q
+    e = g.standard_normal(A.shape[0])
+    e -= Q @ (Q.T @ e)
+    return A @ g.standard_normal(A.shape[1]) + e
+
+
+def test_fp64_factor_inverse_precision_follows_the_diagonal_ratio():
+    # kappa = 1e9: the FP64 factor's diagonal ratio is far above 2^19, so R^{-1}
+    # is formed in FP64 from the start
+    torch, pkg = cuda()
+    A, _ = workloads.usv(4000, 200, 1e9, seed=9)
+    b = _rhs_with_orthogonal_residual(A, 4)
+    x, info = _solve(torch, pkg, A, b, m=400, s=1, seed=2)
+    assert info.status == 0 and info.qr_fallback == 0
+    assert info.rdiag_ratio > 2 ** 19 and info.inv_dtype == pkg.SKI_F64
+    assert olsqr.residual_metric(A, b, x) <= 1e-10
+
+
+def kahan_problem(n=4000, d=100, c=0.2, seed=5):
+    """A = Q0 K, K the d x d Kahan matrix diag(s^i) (I - c U) with s^2 + c^2 = 1
+    and U the strictly upper ones: diagonal ratio s^-(d-1), about 7.5, while
+    kappa(K) is about 2e9 -- the diagonal understates kappa by 8 orders.
+    b = A x_true + e with e orthogonal to range(Q0)."""
+    K = np.diag(np.sqrt(1 - c * c) ** np.arange(d)) @ (np.eye(d) - c * np.triu(np.ones((d, d)), 1))
+    Q0 = _orthogonal_rows(n, d, seed)
+    A = Q0 @ K
+    return A, _rhs_with_orthogonal_residual(A, seed + 1, Q0)
+
+
+def test_fp64_factor_with_a_misleading_diagonal_still_meets_the_tolerance():
+    # The diagonal ratio admits an FP32 inverse, but K's inverse in FP32 is off
+    # by more than its own size (||K X - I|| ~ 10), so it cannot precondition.
+    # The LSQR budget then sends the solve to the FP64 inverse (qr_fallback = 3)
+    # and the solve meets the tolerance.  The report stays consistent: an FP32
+    # inverse at the end means no fallback happened.
+    torch, pkg = cuda()
+    A, b = kahan_problem()
+    x, info = _solve(torch, pkg, A, b, m=200, s=1, seed=3)
+    assert info.status == 0, (info.status, info.iters, info.qr_fallback)
+    assert info.rdiag_ratio < 2 ** 19
+    assert info.qr_fallback in (0, 3)
+    assert (info.qr_fallback == 3) == (info.inv_dtype == pkg.SKI_F64), (info.qr_fallback, info.inv_dtype)
     assert olsqr.residual_metric(A, b, x) <= 1e-10
 
 
