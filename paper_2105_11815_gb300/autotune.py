@@ -51,7 +51,8 @@ def _bucket(v):
 def signature(mats, opts, kind="batched"):
     """A string key for the shapes and the options that matter to the timing:
     the number of problems and the log2 buckets of the smallest, median and
-    largest n and d, the sketch size rule, s, the premix, the dtypes."""
+    largest n and d, the sketch size rule, s, the premix, the dtypes, and the
+    sketching matrix (s-hashing or its variant)."""
     ns = sorted(int(a.n) for a in mats)
     ds = sorted(int(a.d) for a in mats)
     nnz = sorted(int(a.nnz) if int(a.kind) == 1 else 0 for a in mats)
@@ -63,6 +64,7 @@ def signature(mats, opts, kind="batched"):
         "n": q(ns), "d": q(ds), "nnz": q(nnz) if nnz[-1] else 0,
         "m": int(opts.m) if int(opts.m) <= 0 else _bucket(int(opts.m)), "s": int(opts.s),
         "premix": int(opts.premix), "sketch": int(opts.sketch_dtype), "qr": int(opts.qr_dtype),
+        "hash": int(opts.hash_kind),
     }
     return json.dumps(key, sort_keys=True)
 

@@ -80,6 +80,7 @@ def test_signature_separates_what_matters():
     assert s != at.signature(_mats([(4000, 64), (20000, 3000)]), _opts())
     assert s != at.signature(mats, _opts(qr_dtype=1))
     assert s != at.signature(mats, _opts(premix=1))
+    assert s != at.signature(mats, _opts(hash_kind=1))
     assert s != at.signature(mats, _opts(), "solve")
     csr = [pkg.ski_matrix(kind=1, n=4000, d=64, ld=0, val=4096, rowptr=4096, colidx=4096, nnz=32000)]
     assert json.loads(at.signature(csr, _opts()))["csr"] == 1
