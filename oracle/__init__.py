@@ -18,8 +18,10 @@ Modules
 hashing   counter-based draw of the s-hashing matrix (Def. 5) and of D (Def. 8)
 sketch    S built entry by entry, S*A by rows, the s-hashing variant (Def. 7)
 wht       Walsh-Hadamard butterflies and the HRHT premix H*D (Def. 8)
-qr        unblocked Householder QR of [SA | Sb] (Algorithm 1, Step 2)
-lsqr      LSQR (Paige & Saunders) and the whole of Algorithm 1 (Ski-LLS)
+qr        unblocked Householder QR of [SA | Sb] (Algorithm 1, Step 2), with column
+          pivoting and the complete orthogonal form for rank-deficient sketches
+lsqr      LSQR (Paige & Saunders) and the whole of Algorithm 1 (Ski-LLS), with
+          plain QR or a rank-revealing Step 2
 embedding subspace-embedding distortion (Lemma 2), coherence (Def. 6)
 adjoint   gradient of x = argmin ||Ax-b|| with respect to A and b
 """

@@ -80,9 +80,14 @@ def residual_metric(A, b, x):
 
 
 def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
-            it_max=10000, rcond=1e-12, variant=False):
+            it_max=10000, rcond=1e-12, variant=False, factorization="qr"):
     """Algorithm 1 with an s-hashing (optionally HRHT) sketch and Householder QR.
     variant=True sketches with the s-hashing variant of Def. 7.
+
+    factorization: "qr" (plain QR, full-rank sketches only: raises when R fails
+    the rank rule), or the rank-revealing forms of Step 2 for any rank:
+    "qrcp" (column-pivoted QR) or "cod" (complete orthogonal, R12 = 0); see
+    ``ski_lls_rank_revealing``.
 
     A: dense n x d ndarray or scipy sparse; b: length n.
     Returns (x, info) with info = {iters, early_exit, x_s, R, qtsb, rank, trace}.
@@ -92,6 +97,8 @@ def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
         SAb = _wht.hrht_sketch(seed, s, m, np.asarray(A), b, n_pad, variant=variant)
     else:
         SAb = _sketch.sketch_rows(seed, s, m, A, b, variant=variant)
+    if factorization != "qr":
+        return ski_lls_rank_revealing(A, b, SAb, factorization, tau_a, tau_r, it_max, rcond)
     R, C = _qr.householder_qr(SAb, ncols=d)                       # Step 2
     qtsb = C[:, 0]
     p = _qr.numerical_rank(R, rcond)
@@ -112,6 +119,57 @@ def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
 
     delta, iters, trace = lsqr(Wmul, WTmul, r0, d, tau_r, it_max)  # Step 4
     x = x_s + solve_triangular(R, delta)                          # Step 5
+    info.update(iters=iters, trace=trace)
+    return x, info
+
+
+def ski_lls_rank_revealing(A, b, SAb, factorization, tau_a, tau_r, it_max, rcond):
+    """Steps 2-5 of Algorithm 1 with a rank-revealing factorization of SA.
+
+    Step 2: SA = Q R V^T with R = [R11 R12; 0 0], R11 (p x p) nonsingular.
+    "qrcp": column-pivoted Householder QR of [SA | Sb] (pivoting the d columns
+    of SA only), p by the rcond rule, the trailing rows of R dropped; V = the
+    column permutation, V1 its first p columns, Q1^T Sb the first p entries of
+    the reflected Sb.  "cod": the same, then [R11 R12] = T Z1^T
+    (``complete_orthogonal``), so R11 becomes T, R12 = 0, and V1 = P Z1.
+    Step 3: x_s = V1 R11^{-1} Q1^T Sb; stop if ||A x_s - b|| <= tau_a.
+    Step 4: LSQR on W = A V1 R11^{-1} (n x p) from y_0 = Q1^T Sb.
+    Step 5: x = V1 R11^{-1} y.
+    """
+    n, d = A.shape
+    R, C, piv = _qr.householder_qrcp(SAb, ncols=d)
+    qtsb = C[:, 0]
+    p = _qr.numerical_rank(R, rcond)
+    if p == 0:
+        raise np.linalg.LinAlgError("sketch is zero")
+    P1 = np.eye(d)[:, piv[:p]]
+    if factorization == "qrcp":
+        R11, lower, V1 = R[:p, :p], False, P1
+    elif factorization == "cod":
+        T, Z1 = _qr.complete_orthogonal(R[:p, :])
+        R11, lower, V1 = T, True, np.eye(d)[:, piv] @ Z1
+    else:
+        raise ValueError("factorization must be qr, qrcp or cod")
+    c1 = qtsb[:p]
+
+    def solve(v, trans="N"):
+        return solve_triangular(R11, v, lower=lower, trans=trans)
+
+    x_s = V1 @ solve(c1)                                          # Step 3
+    r0 = b - A @ x_s
+    info = dict(x_s=x_s, R=R, R11=R11, V1=V1, piv=piv, qtsb=qtsb, rank=p, early_exit=False, iters=0, trace=[])
+    if np.linalg.norm(r0) <= tau_a:
+        info["early_exit"] = True
+        return x_s, info
+
+    def Wmul(v):
+        return A @ (V1 @ solve(v))
+
+    def WTmul(u):
+        return solve(V1.T @ (A.T @ u), trans="T")
+
+    delta, iters, trace = lsqr(Wmul, WTmul, r0, p, tau_r, it_max)  # Step 4
+    x = x_s + V1 @ solve(delta)                                   # Step 5
     info.update(iters=iters, trace=trace)
     return x, info
 

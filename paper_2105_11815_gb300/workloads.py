@@ -14,6 +14,8 @@ laws below stand in for them:
 * ``usv``: A = U Sigma V^T with Haar U, V and geometric singular values of a
   given condition number (Test Set 1 (a) with a geometric spectrum).
 * ``ragged_batch``: shapes of a ragged batch of problems.
+* ``low_rank_lls``: dense A = G1 G2 of rank r < d (the rank-deficient problems
+  of Test Set 2 and Table 2), b ~ N(0,1).
 """
 import numpy as np
 
@@ -96,6 +98,13 @@ def usv(n, d, kappa, seed):
     V = haar(d, d, g)
     sig = kappa ** (-np.arange(d) / max(d - 1, 1))
     return (U * sig[None, :]) @ V.T, np.ones(n)
+
+
+def low_rank_lls(n, d, r, seed):
+    """A = G1 G2 with G1 (n x r) and G2 (r x d) i.i.d. N(0,1): rank r; b ~ N(0,1)."""
+    g = rng(seed)
+    A = g.standard_normal((n, r)) @ g.standard_normal((r, d))
+    return A, g.standard_normal(n)
 
 
 def ragged_batch(count, seed, n_lo=2000, n_hi=60000, d_lo=64, d_hi=1024, ratio=4):

@@ -3,6 +3,7 @@ import math
 
 import numpy as np
 import pytest
+import scipy.linalg
 import scipy.sparse as sp
 from scipy.linalg import solve_triangular
 
@@ -61,6 +62,83 @@ def test_ski_lls_with_s_hashing_variant(premix, s):
     xr = lsqr.lstsq_reference(A, b)
     assert np.linalg.norm(x - xr) <= 1e-10 * np.linalg.norm(xr)
     assert lsqr.residual_metric(A, b, x) <= 1e-10
+
+
+def test_qrcp_matches_lapack_pivoting():
+    # Businger-Golub pivoting: same permutation as LAPACK's dgeqp3 on a
+    # generic matrix (distinct norms), the same R up to row signs, a
+    # non-increasing |diag R|, and B[:, piv] = Q R through R^T R = B_p^T B_p
+    g = np.random.default_rng(21)
+    B = g.standard_normal((60, 13)) * np.linspace(0.5, 3.0, 13)
+    R, C, piv = qr.householder_qrcp(B, ncols=12)
+    _, R2, P2 = scipy.linalg.qr(B[:, :12], pivoting=True, mode="economic")
+    assert np.array_equal(piv, P2)
+    assert np.allclose(np.abs(R), np.abs(R2), rtol=0, atol=1e-12)
+    dg = np.abs(np.diag(R))
+    assert np.all(dg[:-1] >= dg[1:])
+    Bp = B[:, piv]
+    assert np.allclose(R.T @ R, Bp.T @ Bp, rtol=0, atol=1e-10)
+    # the extra column is reflected too: ||Q^T b||^2 splits into C and the rest
+    assert np.linalg.norm(C[:, 0]) <= np.linalg.norm(B[:, 12]) + 1e-12
+
+
+def test_complete_orthogonal_form():
+    g = np.random.default_rng(22)
+    Rtop = np.triu(g.standard_normal((7, 11)))
+    Rtop[np.arange(7), np.arange(7)] += 3.0
+    T, Z1 = qr.complete_orthogonal(Rtop)
+    assert np.allclose(T, np.tril(T)) and np.all(np.abs(np.diag(T)) > 0)
+    assert np.allclose(Z1.T @ Z1, np.eye(7), atol=1e-13)
+    assert np.allclose(T @ Z1.T, Rtop, atol=1e-12)
+
+
+@pytest.mark.parametrize("factorization", ["qrcp", "cod"])
+def test_rank_revealing_forms_agree_on_full_rank(factorization):
+    A, b, _ = workloads.gaussian_lls(1024, 64, seed=5)
+    x0, _ = lsqr.ski_lls(A, b, seed=17, s=1, m=128)
+    x1, info = lsqr.ski_lls(A, b, seed=17, s=1, m=128, factorization=factorization)
+    assert info["rank"] == 64
+    assert np.linalg.norm(x1 - x0) <= 1e-10 * np.linalg.norm(x0)
+
+
+def test_rank_deficient_algorithm1():
+    # A of rank r = 20 < d = 30.  Lemma 7: under an embedding p = r.  Lemma 6:
+    # W = A V1 R11^{-1} has full rank p (here it is well conditioned, Theorem
+    # 10).  Theorem 8: x attains the least-squares residual.  Theorem 9: with
+    # R12 = 0 (the complete orthogonal form) x is the minimal-norm solution;
+    # with R12 != 0 (plain pivoting) it is a different minimiser.
+    n, d, r = 1000, 30, 20
+    A, b = workloads.low_rank_lls(n, d, r, seed=3)
+    xmin = np.linalg.pinv(A) @ b
+    rmin = np.linalg.norm(A @ xmin - b)
+    sols = {}
+    for f in ("qrcp", "cod"):
+        x, info = lsqr.ski_lls(A, b, seed=3, s=1, m=120, factorization=f)
+        assert info["rank"] == r
+        W = A @ info["V1"] @ np.linalg.inv(info["R11"])
+        sv = np.linalg.svd(W, compute_uv=False)
+        assert sv.size == r and sv[-1] / sv[0] > 0.1
+        assert abs(np.linalg.norm(A @ x - b) - rmin) <= 1e-12 * rmin
+        assert lsqr.residual_metric(A, b, x) <= 1e-10
+        sols[f] = x
+    assert np.linalg.norm(sols["cod"] - xmin) <= 1e-9 * np.linalg.norm(xmin)
+    assert np.linalg.norm(sols["qrcp"]) > 1.01 * np.linalg.norm(xmin)
+    # the plain-QR form refuses a rank-deficient sketch
+    with pytest.raises(np.linalg.LinAlgError):
+        lsqr.ski_lls(A, b, seed=3, s=1, m=120)
+
+
+def test_lemma8_rank_deficient():
+    # Lemma 8 holds for the rank-revealing x_s: ||A x_s - b|| <= (1+eps)/(1-eps) ||A x* - b||,
+    # eps the distortion of S on range([A b])
+    n, d, r, m = 2000, 30, 12, 300
+    A, b = workloads.low_rank_lls(n, d, r, seed=8)
+    rstar = np.linalg.norm(A @ np.linalg.pinv(A) @ b - b)
+    U = embedding.orth(np.column_stack([A, b]))
+    eps = embedding.distortion(sketch.sketch_rows(4, 2, m, U))
+    assert eps < 1
+    _, info = lsqr.ski_lls(A, b, seed=4, s=2, m=m, factorization="qrcp", tau_r=1e-6)
+    assert np.linalg.norm(A @ info["x_s"] - b) <= (1 + eps) / (1 - eps) * rstar
 
 
 def test_ski_lls_sparse():
