@@ -18,6 +18,7 @@ Modules
 hashing   counter-based draw of the s-hashing matrix (Def. 5) and of D (Def. 8)
 sketch    S built entry by entry, S*A by rows, the s-hashing variant (Def. 7)
 wht       Walsh-Hadamard butterflies and the HRHT premix H*D (Def. 8)
+dht       the normalized Hartley transform and the HR-DHT premix F*D (Section 6)
 qr        unblocked Householder QR of [SA | Sb] (Algorithm 1, Step 2), with column
           pivoting and the complete orthogonal form for rank-deficient sketches
 lsqr      LSQR (Paige & Saunders) and the whole of Algorithm 1 (Ski-LLS), with

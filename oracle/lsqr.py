@@ -12,6 +12,7 @@ problem min ||W delta - (b - W y_0)|| and y = y_0 + delta.
 import numpy as np
 from scipy.linalg import solve_triangular
 
+from . import dht as _dht
 from . import qr as _qr
 from . import sketch as _sketch
 from . import wht as _wht
@@ -83,6 +84,8 @@ def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
             it_max=10000, rcond=1e-12, variant=False, factorization="qr"):
     """Algorithm 1 with an s-hashing (optionally HRHT) sketch and Householder QR.
     variant=True sketches with the s-hashing variant of Def. 7.
+    premix: False, True (the Walsh-Hadamard premix H D of Def. 8, padded to
+    n_pad) or "dht" (the HR-DHT premix F D of Ski-LLS-dense, no padding).
 
     factorization: "qr" (plain QR, full-rank sketches only: raises when R fails
     the rank rule), or the rank-revealing forms of Step 2 for any rank:
@@ -93,7 +96,9 @@ def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
     Returns (x, info) with info = {iters, early_exit, x_s, R, qtsb, rank, trace}.
     """
     n, d = A.shape
-    if premix:
+    if premix == "dht":
+        SAb = _dht.hrdht_sketch(seed, s, m, np.asarray(A), b, variant=variant)
+    elif premix:
         SAb = _wht.hrht_sketch(seed, s, m, np.asarray(A), b, n_pad, variant=variant)
     else:
         SAb = _sketch.sketch_rows(seed, s, m, A, b, variant=variant)

@@ -1,0 +1,68 @@
+"""Pins for the HR-DHT premix of Ski-LLS-dense (Section 6, Eq. HR-DHT)."""
+import numpy as np
+import pytest
+
+from oracle import dht, embedding, hashing, sketch
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 16, 50, 97])
+def test_fft_route_equals_the_definition(n):
+    X = np.random.default_rng(n).standard_normal((n, 5))
+    assert np.allclose(dht.dht_rows(X), dht.dht_matrix(n) @ X, rtol=0, atol=1e-12)
+    assert np.allclose(dht.dht_rows(X[:, 0]), dht.dht_matrix(n) @ X[:, 0], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [5, 12, 64])
+def test_normalized_dht_is_symmetric_orthogonal_and_involutory(n):
+    F = dht.dht_matrix(n)
+    assert np.allclose(F, F.T, atol=1e-14)
+    assert np.allclose(F @ F, np.eye(n), atol=1e-12)          # the DHT is its own inverse
+    x = np.random.default_rng(2).standard_normal(n)
+    assert np.isclose(np.linalg.norm(dht.dht_rows(x)), np.linalg.norm(x), rtol=1e-13)
+
+
+def test_small_cases_by_hand():
+    # n = 1: F = [1]; n = 2: cas(0) = 1, cas(pi) = -1, F = [[1, 1], [1, -1]] / sqrt(2);
+    # n = 4: cas(k pi / 2) for k = 0..3 is 1, 1, -1, -1
+    assert np.allclose(dht.dht_matrix(1), [[1.0]])
+    assert np.allclose(dht.dht_matrix(2), np.array([[1, 1], [1, -1]]) / np.sqrt(2))
+    F4 = np.array([[1, 1, 1, 1], [1, 1, -1, -1], [1, -1, 1, -1], [1, -1, -1, 1]]) / 2.0
+    assert np.allclose(dht.dht_matrix(4), F4, atol=1e-15)
+
+
+def test_premix_applies_the_def8_signs_first():
+    n = 33
+    A = np.random.default_rng(4).standard_normal((n, 3))
+    D = np.diag(hashing.premix_signs(9, n).astype(float))
+    assert np.allclose(dht.premix(9, A), dht.dht_matrix(n) @ D @ A, atol=1e-12)
+
+
+def test_coherence_reduced_to_the_entry_bound():
+    # |F_ij| <= sqrt(2/n), so every row of F D [I_d; 0] has norm <= sqrt(2 d / n):
+    # the coherence of the fully coherent [I_d; 0] (mu = 1) drops below that bound
+    n, d = 1000, 10
+    A = np.zeros((n, d))
+    A[:d] = np.eye(d)
+    assert embedding.coherence(A) == pytest.approx(1.0)
+    assert np.max(np.abs(dht.dht_matrix(n))) <= np.sqrt(2.0 / n) + 1e-15
+    assert embedding.coherence(dht.premix(5, A)) <= np.sqrt(2.0 * d / n) + 1e-12
+
+
+def test_ski_lls_with_the_dht_premix():
+    # Algorithm 1 with S = S_h F D on a coherent problem reaches the least-squares solution
+    from oracle import lsqr
+    from paper_2105_11815_gb300 import workloads
+    A, b = workloads.dense_high_coherence(3000, 40, seed=2)
+    x, info = lsqr.ski_lls(A, b, seed=7, s=1, m=120, premix="dht")
+    xr = lsqr.lstsq_reference(A, b)
+    assert np.linalg.norm(x - xr) <= 1e-8 * np.linalg.norm(xr)
+    assert lsqr.residual_metric(A, b, x) <= 1e-10
+
+
+def test_hrdht_sketch_equals_explicit_product():
+    n, d, m, s = 300, 6, 40, 2
+    g = np.random.default_rng(6)
+    A, b = g.standard_normal((n, d)), g.standard_normal(n)
+    S = sketch.s_hashing_matrix(11, s, m, n) @ dht.dht_matrix(n) @ np.diag(hashing.premix_signs(11, n).astype(float))
+    out = dht.hrdht_sketch(11, s, m, A, b)
+    assert np.allclose(out, np.column_stack([S @ A, S @ b]), atol=1e-12)
