@@ -50,7 +50,8 @@ extern "C" ski_status ski_sketch_hash_noalloc(const ski_matrix* A, const double*
                                               int64_t ld_sa, void* stream) {
   if (!A || !o || !SA) return SKI_EINVAL;
   if (o->premix) return SKI_EINVAL;
-  if (A->n < 1 || A->d < 1 || o->s < 1 || o->s > 64 || o->m < o->s) return SKI_EINVAL;
+  // the s-hashing variant (hash_kind 1) draws with replacement: s may exceed m
+  if (A->n < 1 || A->d < 1 || o->s < 1 || o->s > 64 || o->m < (o->hash_kind == 1 ? 1 : o->s)) return SKI_EINVAL;
   if (A->n * (int64_t)o->s > SKI_NOALLOC_MAX_PAIRS || o->m > SKI_NOALLOC_MAX_M) return SKI_EINVAL;
   if (ld_sa < A->d + (b ? 1 : 0)) return SKI_EINVAL;
   const size_t need = ski_sketch_workspace_size(A, b != nullptr, o);

@@ -19,12 +19,12 @@ from gpu_util import cuda, rel_fro, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def _pair(torch, pkg, n, d, m, s, seed, with_b):
+def _pair(torch, pkg, n, d, m, s, seed, with_b, hash_kind=0):
     A, b, _ = workloads.gaussian_lls(n, d, seed=seed)
     At = to_dev(torch, A)
     bt = to_dev(torch, b) if with_b else None
     M = pkg.dense_matrix(At)
-    o = pkg.ski_opts_default(m=m, s=s, seed=seed)
+    o = pkg.ski_opts_default(m=m, s=s, seed=seed, hash_kind=hash_kind)
     ncols = d + (1 if with_b else 0)
     ref = torch.full((m, ncols), float("nan"), dtype=torch.float64, device="cuda")
     got = torch.full((m, ncols), float("nan"), dtype=torch.float64, device="cuda")
@@ -44,6 +44,14 @@ def test_noalloc_sketch_matches_workspace_sketch_twice_in_a_row():
     assert np.isfinite(got1).all() and np.isfinite(got2).all()
     assert rel_fro(got1, ref1) <= 1e-12
     assert rel_fro(got2, ref2) <= 1e-12
+
+
+def test_noalloc_sketch_with_the_s_hashing_variant():
+    # Def. 7's variant draws with replacement, so s = 5 > m = 3 is a valid sketch
+    torch, pkg = cuda()
+    st, got, ref = _pair(torch, pkg, 2000, 20, 3, 5, seed=3, with_b=True, hash_kind=1)
+    assert st == 0 and np.isfinite(got).all()
+    assert rel_fro(got, ref) <= 1e-12
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
