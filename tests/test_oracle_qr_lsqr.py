@@ -118,6 +118,13 @@ def test_rank_deficient_algorithm1():
         W = A @ info["V1"] @ np.linalg.inv(info["R11"])
         sv = np.linalg.svd(W, compute_uv=False)
         assert sv.size == r and sv[-1] / sv[0] > 0.1
+        # the lemma behind Theorem 8: ker(V1^T) and range(A^T) meet only in 0,
+        # i.e. their bases (d - p and r vectors) together span R^d
+        V1 = info["V1"]
+        ker = np.linalg.svd(V1.T)[2][r:].T                    # d x (d - p), V1^T ker = 0
+        rowsp = np.linalg.svd(A, full_matrices=False)[2][:r].T  # d x r, range(A^T)
+        assert np.allclose(V1.T @ ker, 0, atol=1e-12)
+        assert np.linalg.matrix_rank(np.hstack([ker, rowsp]), tol=1e-8) == d
         assert abs(np.linalg.norm(A @ x - b) - rmin) <= 1e-12 * rmin
         assert lsqr.residual_metric(A, b, x) <= 1e-10
         sols[f] = x
