@@ -82,6 +82,28 @@ def test_qrcp_matches_lapack_pivoting():
     assert np.linalg.norm(C[:, 0]) <= np.linalg.norm(B[:, 12]) + 1e-12
 
 
+def test_pivoting_r_equals_pivoting_sa():
+    # SA = Q R with orthonormal Q keeps every column norm (and every partial
+    # column norm below a row) of SA in R, so the column-pivoted QR of the d x d
+    # R picks the pivots of the column-pivoted QR of the m x d SA and yields the
+    # same R' up to row signs: SA P = Q (R P) = (Q Q') R'.  A GPU path can keep
+    # its unpivoted QR of SA and pivot only R when the rank rule fails.
+    n, d, r = 600, 24, 15
+    A, b = workloads.low_rank_lls(n, d, r, seed=12)
+    SAb = sketch.sketch_rows(5, 1, 80, A, b)
+    R, C = qr.householder_qr(SAb, ncols=d)
+    Rp_sa, _, piv_sa = qr.householder_qrcp(SAb[:, :d])
+    Rp_r, _, piv_r = qr.householder_qrcp(R)
+    p = qr.numerical_rank(Rp_sa, 1e-12)
+    assert p == r and qr.numerical_rank(Rp_r, 1e-12) == r
+    assert np.array_equal(piv_sa[:p], piv_r[:p])
+    # the leading p rows [R11 R12], columns back in their original order (the
+    # pivots after p are picked among rounding-level norms and may differ)
+    top_sa = np.abs(Rp_sa[:p])[:, np.argsort(piv_sa)]
+    top_r = np.abs(Rp_r[:p])[:, np.argsort(piv_r)]
+    assert np.allclose(top_sa, top_r, rtol=0, atol=1e-10 * np.abs(Rp_sa[0, 0]))
+
+
 def test_complete_orthogonal_form():
     g = np.random.default_rng(22)
     Rtop = np.triu(g.standard_normal((7, 11)))
