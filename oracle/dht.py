@@ -37,6 +37,12 @@ def premix(seed, A):
     return dht_rows(D.reshape((-1,) + (1,) * (A.ndim - 1)) * A)
 
 
+def srdht_sketch(seed, m, A):
+    """S_s F D A (Eq. SR-DHT, the sampling sketch the paper compares against):
+    m rows of F D A, each chosen uniformly at random with replacement."""
+    return premix(seed, A)[hashing.sample_rows(seed, m, np.asarray(A).shape[0])]
+
+
 def hrdht_sketch(seed, s, m, A, b=None, variant=False):
     """[S_h F D A | S_h F D b] with S_h an s-hashing matrix (the variant of
     Def. 7 when variant=True) over the n rows of F D A."""

@@ -36,6 +36,7 @@ SM_MUL2 = 0x94D049BB133111EB
 TAG_BUCKET = 0xB1
 TAG_SIGN = 0x5A
 TAG_PREMIX = 0xD3
+TAG_SAMPLE = 0x5E
 
 
 def splitmix64(z):
@@ -145,6 +146,14 @@ def premix_signs(seed, n):
     j = np.arange(n, dtype=np.uint64)
     w = _key_np(seed, TAG_PREMIX, j, 0, np.zeros(n, dtype=np.uint64))
     return np.where((w >> np.uint64(63)) != 0, -1, 1).astype(np.int8)
+
+
+def sample_rows(seed, m, n):
+    """Columns c_0..c_{m-1} of a sampling matrix S_s (m x n): row i of S_s holds
+    a single 1 in column c_i, drawn uniformly from [n] (independently for every
+    row, so columns may repeat): c_i = floor(key(seed, SAMPLE, i, 0, 0) n / 2^64)."""
+    i = np.arange(m, dtype=np.uint64)
+    return _mulhi_np(_key_np(seed, TAG_SAMPLE, i, 0, np.zeros(m, dtype=np.uint64)), n).astype(np.int64)
 
 
 def variant_table(seed, s, m, n):

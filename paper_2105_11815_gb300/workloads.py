@@ -14,6 +14,7 @@ laws below stand in for them:
 * ``usv``: A = U Sigma V^T with Haar U, V and geometric singular values of a
   given condition number (Test Set 1 (a) with a geometric spectrum).
 * ``ragged_batch``: shapes of a ragged batch of problems.
+* ``coherent_dense``: [I_d; 0] + 1e-8 J (Section 7.1, Test Set 1 (c)).
 * ``low_rank_lls``: dense A = G1 G2 of rank r < d (the rank-deficient problems
   of Test Set 2 and Table 2), b ~ N(0,1).
 """
@@ -98,6 +99,13 @@ def usv(n, d, kappa, seed):
     V = haar(d, d, g)
     sig = kappa ** (-np.arange(d) / max(d - 1, 1))
     return (U * sig[None, :]) @ V.T, np.ones(n)
+
+
+def coherent_dense(n, d):
+    """A = [I_d; 0] + 1e-8 J, J all ones (Test Set 1 (c)): coherence ~ 1."""
+    A = np.full((n, d), 1e-8)
+    A[np.arange(d), np.arange(d)] += 1.0
+    return A
 
 
 def low_rank_lls(n, d, r, seed):

@@ -59,6 +59,36 @@ def test_ski_lls_with_the_dht_premix():
     assert lsqr.residual_metric(A, b, x) <= 1e-10
 
 
+def test_sample_rows_uniform_with_replacement():
+    c = hashing.sample_rows(3, 200000, 10)
+    counts = np.bincount(c, minlength=10)
+    chi2 = np.sum((counts - 20000.0) ** 2 / 20000.0)
+    assert c.min() >= 0 and c.max() < 10 and chi2 < 33.7          # chi^2_9 at p = 1e-4
+    assert len(set(hashing.sample_rows(3, 50, 40).tolist())) < 50   # repeats occur
+
+
+def test_hashing_preconditions_better_than_sampling():
+    # Fig. blen_motivation: on the coherent [I; 0] + 1e-8 J (4000 x 400), the
+    # R of a hashed F D A preconditions better than the R of sampled rows of
+    # F D A at the same m, and improves with m
+    from paper_2105_11815_gb300 import workloads
+    n, d = 4000, 400
+    A = workloads.coherent_dense(n, d)
+    Y = dht.premix(7, A)
+
+    def kappa(SA):
+        R = np.linalg.qr(SA, mode="r")
+        sv = np.linalg.svd(A @ np.linalg.inv(R), compute_uv=False)
+        return sv[0] / sv[-1]
+    kh, ks = [], []
+    for g in (1.5, 2.0, 3.0):
+        m = int(g * d)
+        kh.append(kappa(sketch.sketch_rows(1, 1, m, Y)))
+        ks.append(kappa(dht.srdht_sketch(7, m, A)))
+    assert all(h < s for h, s in zip(kh, ks)), (kh, ks)
+    assert kh[0] > kh[1] > kh[2] and kh[1] < 10
+
+
 def test_hrdht_sketch_equals_explicit_product():
     n, d, m, s = 300, 6, 40, 2
     g = np.random.default_rng(6)
