@@ -14,6 +14,8 @@ laws below stand in for them:
 * ``usv``: A = U Sigma V^T with Haar U, V and geometric singular values of a
   given condition number (Test Set 1 (a) with a geometric spectrum).
 * ``ragged_batch``: shapes of a ragged batch of problems.
+* ``semi_coherent_sparse``: D^5 B (Test Set 2 (b)) with B an incoherent sparse
+  pattern of N(0,1) values and D a diagonal of N(0,1) entries, stored dense.
 * ``coherent_dense``: [I_d; 0] + 1e-8 J (Section 7.1, Test Set 1 (c)).
 * ``low_rank_lls``: dense A = G1 G2 of rank r < d (the rank-deficient problems
   of Test Set 2 and Table 2), b ~ N(0,1).
@@ -99,6 +101,14 @@ def usv(n, d, kappa, seed):
     V = haar(d, d, g)
     sig = kappa ** (-np.arange(d) / max(d - 1, 1))
     return (U * sig[None, :]) @ V.T, np.ones(n)
+
+
+def semi_coherent_sparse(n, d, seed, density=0.1, power=5):
+    """A = D^power B, B with N(0,1) values at a uniform fraction ``density`` of
+    positions, D = diag(N(0,1)) (the row scaling makes a few rows dominate)."""
+    g = rng(seed)
+    B = g.standard_normal((n, d)) * (g.random((n, d)) < density)
+    return (g.standard_normal(n) ** power)[:, None] * B
 
 
 def coherent_dense(n, d):

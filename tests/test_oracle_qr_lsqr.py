@@ -251,6 +251,26 @@ def test_distortion_decreases_with_gamma():
     assert eps[0] > eps[1] > eps[2]
 
 
+def test_s_above_one_preconditions_coherent_input_better():
+    # Theorems 3-5: s-hashing (and its variant) relax the coherence needed for
+    # an embedding by sqrt(s).  On the semi-coherent D^5 B of the paper's sparse
+    # illustration (coherence ~ 0.99), the R of an s = 2 or 3 sketch gives a
+    # lower kappa(A R^-1) than s = 1 at the same m, for both kinds of hashing
+    n, d = 4000, 40
+    A = workloads.semi_coherent_sparse(n, d, seed=3)
+    assert embedding.coherence(A) > 0.9
+
+    def kappa(SA):
+        R = np.linalg.qr(SA, mode="r")
+        sv = np.linalg.svd(A @ np.linalg.inv(R), compute_uv=False)
+        return sv[0] / sv[-1]
+    for m in (4 * d, 8 * d):
+        for variant in (False, True):
+            k = {s: np.median([kappa(sketch.sketch_rows(sd, s, m, A, variant=variant)) for sd in range(5)])
+                 for s in (1, 2, 3)}
+            assert k[2] < k[1] and k[3] < k[1], (m, variant, k)
+
+
 def test_adjoint_against_finite_differences():
     g = np.random.default_rng(11)
     A, b = g.standard_normal((512, 32)), g.standard_normal(512)
