@@ -18,7 +18,7 @@ from . import sketch as _sketch
 from . import wht as _wht
 
 
-def lsqr(Wmul, WTmul, rhs, nvar, tau_r, it_max):
+def lsqr(Wmul, WTmul, rhs, nvar, tau_r, it_max, history=None):
     """LSQR of Paige & Saunders (ACM TOMS 8, 1982) for min ||W y - rhs||, y_0 = 0.
 
     Golub-Kahan bidiagonalisation beta_1 u_1 = rhs, alpha_1 v_1 = W^T u_1, then
@@ -26,6 +26,8 @@ def lsqr(Wmul, WTmul, rhs, nvar, tau_r, it_max):
     rotation (rho, c, s) eliminates beta; y and w are updated.  The estimates
     ||r|| = phibar, ||W^T r|| = phibar * alpha * |c| and ||W||_F ~ sqrt(sum of
     alpha^2 + beta^2) give the stopping test of Eq. TC-lsqr.
+    history, when given, is called after iteration k as
+    history(k, y_k, rnorm, arnorm, anorm) with the estimates of that iterate.
     Returns (y, iterations, list of test values).
     """
     u = np.array(rhs, dtype=np.float64, copy=True)
@@ -67,6 +69,8 @@ def lsqr(Wmul, WTmul, rhs, nvar, tau_r, it_max):
         arnorm = phibar * alpha * abs(c)
         test = arnorm / (np.sqrt(anorm2) * rnorm) if rnorm > 0 else 0.0
         trace.append(test)
+        if history is not None:
+            history(it, y.copy(), rnorm, arnorm, np.sqrt(anorm2))
         if test <= tau_r:
             break
     return y, it, trace
@@ -80,15 +84,36 @@ def residual_metric(A, b, x):
     return float(np.linalg.norm(A.T @ r) / (fro * rn)) if rn > 0 else 0.0
 
 
+def perturbed_back_solve(R, c, perturb, trans=False):
+    """Solve R x = c (R^T x = c when trans) by substitution, dividing by
+    r_ii + perturb wherever the diagonal entry r_ii is needed: the perturbed
+    back-solve of Ski-LLS-sparse (Section 6, parameter rcond_thres), a safeguard
+    for a triangular factor whose rank detection failed.  perturb = 0 is the
+    plain back-solve."""
+    R = np.asarray(R, dtype=np.float64)
+    d = R.shape[0]
+    x = np.zeros(d)
+    order = range(d) if trans else range(d - 1, -1, -1)
+    for i in order:
+        if trans:                      # forward substitution with R^T (lower)
+            acc = c[i] - R[:i, i] @ x[:i]
+        else:                          # back substitution with R (upper)
+            acc = c[i] - R[i, i + 1:] @ x[i + 1:]
+        x[i] = acc / (R[i, i] + perturb)
+    return x
+
+
 def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
-            it_max=10000, rcond=1e-12, variant=False, factorization="qr"):
+            it_max=10000, rcond=1e-12, variant=False, factorization="qr", perturb=0.0):
     """Algorithm 1 with an s-hashing (optionally HRHT) sketch and Householder QR.
     variant=True sketches with the s-hashing variant of Def. 7.
     premix: False, True (the Walsh-Hadamard premix H D of Def. 8, padded to
     n_pad) or "dht" (the HR-DHT premix F D of Ski-LLS-dense, no padding).
 
-    factorization: "qr" (plain QR, full-rank sketches only: raises when R fails
-    the rank rule), or the rank-revealing forms of Step 2 for any rank:
+    factorization: "qr" (plain QR: when R fails the rank rule it raises, or,
+    with perturb > 0, every back-solve with R divides by r_ii + perturb -- the
+    perturbed back-solve of Ski-LLS-sparse), or the rank-revealing forms of
+    Step 2 for any rank:
     "qrcp" (column-pivoted QR) or "cod" (complete orthogonal, R12 = 0); see
     ``ski_lls_rank_revealing``.
 
@@ -107,23 +132,32 @@ def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
     R, C = _qr.householder_qr(SAb, ncols=d)                       # Step 2
     qtsb = C[:, 0]
     p = _qr.numerical_rank(R, rcond)
+    pert = 0.0
     if p < d:
-        raise np.linalg.LinAlgError(f"sketch has numerical rank {p} < {d}")
-    x_s = solve_triangular(R, qtsb)                               # Step 3
+        if perturb <= 0.0:
+            raise np.linalg.LinAlgError(f"sketch has numerical rank {p} < {d}")
+        pert = perturb
+
+    def Rinv(v, trans=False):
+        if pert > 0.0:
+            return perturbed_back_solve(R, v, pert, trans=trans)
+        return solve_triangular(R, v, trans="T" if trans else "N")
+
+    x_s = Rinv(qtsb)                                              # Step 3
     r0 = b - A @ x_s
-    info = dict(x_s=x_s, R=R, qtsb=qtsb, rank=p, early_exit=False, iters=0, trace=[])
+    info = dict(x_s=x_s, R=R, qtsb=qtsb, rank=p, early_exit=False, iters=0, trace=[], perturb=pert)
     if np.linalg.norm(r0) <= tau_a:
         info["early_exit"] = True
         return x_s, info
 
     def Wmul(v):
-        return A @ solve_triangular(R, v)
+        return A @ Rinv(v)
 
     def WTmul(u):
-        return solve_triangular(R, A.T @ u, trans="T")
+        return Rinv(A.T @ u, trans=True)
 
     delta, iters, trace = lsqr(Wmul, WTmul, r0, d, tau_r, it_max)  # Step 4
-    x = x_s + solve_triangular(R, delta)                          # Step 5
+    x = x_s + Rinv(delta)                                         # Step 5
     info.update(iters=iters, trace=trace)
     return x, info
 

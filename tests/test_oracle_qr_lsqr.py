@@ -287,3 +287,156 @@ def test_adjoint_against_finite_differences():
         fd = (L(A + h * EA, b + h * eb) - L(A - h * EA, b - h * eb)) / (2 * h)
         an = np.sum(dA * EA) + db @ eb
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
+
+
+# ---------------------------------------------------------------- the acceptance metric
+@pytest.mark.parametrize("sparse", [False, True])
+def test_residual_metric_hand_worked(sparse):
+    # ||A^T r|| / (||A||_F ||r||), r = b - A x, worked by hand on matrices where
+    # the plausible slips give other numbers.
+    # (i) A = [1 2 2]^T, x = 1, r = [2 2 1]: A^T r = 8, ||A||_F = 3, ||r|| = 3
+    #     -> 8/9 (||b|| = sqrt(34) in place of ||r|| would give 8/(3 sqrt 34))
+    A1 = np.array([[1.0], [2.0], [2.0]])
+    b1 = np.array([3.0, 4.0, 3.0])
+    # (ii) A = [[2 0 0] [1 1 0] [0 0 1]], x = [1 1 1], r = e_1, b = [3 2 1]:
+    #     A^T r = [2 0 0] -> 2; ||A||_F = sqrt 7 -> 2 / sqrt 7.  A r = [2 1 0]
+    #     (norm sqrt 5), ||A||_2 = sqrt(3 + sqrt 5) and ||b|| = sqrt 14 all differ
+    A2 = np.array([[2.0, 0.0, 0.0], [1.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    b2 = np.array([3.0, 2.0, 1.0])
+    cases = [(A1, b1, np.array([1.0]), 8.0 / 9.0), (A2, b2, np.ones(3), 2.0 / np.sqrt(7.0))]
+    for A, b, x, want in cases:
+        M = sp.csr_matrix(A) if sparse else A
+        assert lsqr.residual_metric(M, b, x) == pytest.approx(want, rel=1e-15)
+    # the slips named above give different values on (ii)
+    assert abs(2.0 / np.sqrt(3.0 + np.sqrt(5.0)) - 2.0 / np.sqrt(7.0)) > 0.1
+    assert abs(np.sqrt(5.0) / np.sqrt(7.0) - 2.0 / np.sqrt(7.0)) > 0.05
+    # an exact least-squares solution has A^T r = 0, an interpolating one r = 0
+    assert lsqr.residual_metric(A2, b2, np.linalg.solve(A2, b2)) == 0.0
+    xr = np.linalg.lstsq(A1, b1, rcond=None)[0]
+    assert lsqr.residual_metric(A1, b1, xr) <= 1e-15
+
+
+# ---------------------------------------------------------------- LSQR's estimates
+def _golub_kahan(W, rhs, k):
+    """k steps of Golub-Kahan bidiagonalisation with full reorthogonalisation:
+    U (n x k+1), V (d x k), alphas (k), betas (k+1), so that W V_k = U_{k+1} B_k
+    with B_k lower bidiagonal (alphas on the diagonal, betas[1:] below it)."""
+    n, d = W.shape
+    U = np.zeros((n, k + 1))
+    V = np.zeros((d, k))
+    al = np.zeros(k)
+    be = np.zeros(k + 1)
+    be[0] = np.linalg.norm(rhs)
+    U[:, 0] = rhs / be[0]
+    for i in range(k):
+        v = W.T @ U[:, i] - (be[i] * V[:, i - 1] if i > 0 else 0.0)
+        v -= V[:, :i] @ (V[:, :i].T @ v)
+        al[i] = np.linalg.norm(v)
+        V[:, i] = v / al[i]
+        u = W @ V[:, i] - al[i] * U[:, i]
+        u -= U[:, :i + 1] @ (U[:, :i + 1].T @ u)
+        be[i + 1] = np.linalg.norm(u)
+        U[:, i + 1] = u / be[i + 1]
+    return U, V, al, be
+
+
+def test_lsqr_estimates_match_the_explicit_quantities():
+    # Paige & Saunders: after k steps the LSQR iterate is y_k = V_k z_k with
+    # z_k = argmin ||beta_1 e_1 - B_k z||, its residual norm is phibar, ||W^T r_k||
+    # is phibar * alpha_{k+1} |c_k|, and the running ||W|| estimate is the
+    # Frobenius norm of B_k.  Each is compared with the quantity formed
+    # explicitly from an independent bidiagonalisation of W.
+    g = np.random.default_rng(31)
+    n, d = 40, 10
+    Q1, _ = np.linalg.qr(g.standard_normal((n, d)))
+    Q2, _ = np.linalg.qr(g.standard_normal((d, d)))
+    W = Q1 @ np.diag(np.linspace(1.0, 8.0, d)) @ Q2.T
+    rhs = g.standard_normal(n)
+    seen = {}
+
+    def hist(k, y, rnorm, arnorm, anorm):
+        seen[k] = (y, rnorm, arnorm, anorm)
+
+    lsqr.lsqr(lambda v: W @ v, lambda u: W.T @ u, rhs, d, 0.0, d - 1, history=hist)
+    assert sorted(seen) == list(range(1, d))
+    U, V, al, be = _golub_kahan(W, rhs, d - 1)
+    for k in range(1, d):
+        y, rnorm, arnorm, anorm = seen[k]
+        B = np.zeros((k + 1, k))
+        B[np.arange(k), np.arange(k)] = al[:k]
+        B[np.arange(1, k + 1), np.arange(k)] = be[1:k + 1]
+        e1 = np.zeros(k + 1)
+        e1[0] = be[0]
+        z = np.linalg.lstsq(B, e1, rcond=None)[0]
+        yk = V[:, :k] @ z
+        r = rhs - W @ yk
+        assert np.allclose(y, yk, rtol=0, atol=1e-10 * np.linalg.norm(yk))
+        assert rnorm == pytest.approx(np.linalg.norm(r), rel=1e-9)
+        assert arnorm == pytest.approx(np.linalg.norm(W.T @ r), rel=1e-7)
+        assert anorm == pytest.approx(np.linalg.norm(B), rel=1e-12)
+
+
+def test_lsqr_test_value_is_eq_tc_lsqr():
+    # the stopping value is ||W^T r|| / (||B_k||_F ||r||): with the estimates
+    # pinned above, the trace equals that ratio formed from them
+    g = np.random.default_rng(32)
+    W = g.standard_normal((30, 6))
+    rhs = g.standard_normal(30)
+    seen = []
+    _, it, trace = lsqr.lsqr(lambda v: W @ v, lambda u: W.T @ u, rhs, 6, 0.0, 5,
+                             history=lambda k, y, rn, arn, an: seen.append(arn / (an * rn)))
+    assert it == 5 and np.allclose(trace, seen, rtol=1e-15)
+
+
+# ---------------------------------------------------------------- perturbed back-solve
+def test_perturbed_back_solve_hand_worked():
+    # R = [[2 1] [0 0]], c = [3 1], perturb 1/2: dividing by r_ii + 1/2,
+    # x_2 = 1 / (1/2) = 2 and x_1 = (3 - 2) / (5/2) = 2/5; with R^T (forward
+    # substitution) x_1 = 3 / (5/2) = 6/5 and x_2 = (1 - 6/5) / (1/2) = -2/5
+    R = np.array([[2.0, 1.0], [0.0, 0.0]])
+    c = np.array([3.0, 1.0])
+    assert np.allclose(lsqr.perturbed_back_solve(R, c, 0.5), [0.4, 2.0], rtol=0, atol=1e-15)
+    assert np.allclose(lsqr.perturbed_back_solve(R, c, 0.5, trans=True), [1.2, -0.4], rtol=0, atol=1e-15)
+    # a 3 x 3 case: R = [[1 2 3] [0 4 5] [0 0 0]], c = [1 2 3], perturb 1:
+    # x_3 = 3, x_2 = (2 - 15) / 5 = -13/5, x_1 = (1 + 26/5 - 9) / 2 = -7/5
+    R3 = np.array([[1.0, 2.0, 3.0], [0.0, 4.0, 5.0], [0.0, 0.0, 0.0]])
+    assert np.allclose(lsqr.perturbed_back_solve(R3, np.array([1.0, 2.0, 3.0]), 1.0), [-1.4, -2.6, 3.0],
+                       rtol=0, atol=1e-14)
+    # perturb = 0 is LAPACK's triangular solve
+    g = np.random.default_rng(33)
+    Rg = np.triu(g.standard_normal((7, 7))) + 4 * np.eye(7)
+    cg = g.standard_normal(7)
+    assert np.allclose(lsqr.perturbed_back_solve(Rg, cg, 0.0), solve_triangular(Rg, cg), rtol=1e-13, atol=0)
+    assert np.allclose(lsqr.perturbed_back_solve(Rg, cg, 0.0, trans=True), solve_triangular(Rg, cg, trans="T"),
+                       rtol=1e-13, atol=0)
+
+
+def zero_column_lls(n=600, d=12, zero=5, seed=41):
+    """A Gaussian LLS whose column ``zero`` is exactly zero (rank d - 1); its
+    sketch then has an exactly zero column, and the Householder QR gives
+    r_zz = 0 exactly."""
+    A, b, _ = workloads.gaussian_lls(n, d, seed=seed)
+    A = A.copy()
+    A[:, zero] = 0.0
+    return A, b
+
+
+def test_perturbed_ski_lls_solves_the_reduced_problem():
+    # With column z of A zero, the rank rule stops at p = z (the leading count)
+    # and plain QR cannot continue.  The perturbed back-solve divides by
+    # r_zz + perturb = perturb; column z of (R + perturb e_z e_z^T)^{-1} is then
+    # e_z / perturb, so the entries of x other than x_z depend only on the other
+    # columns: they equal the least-squares solution of A without column z,
+    # which is unique, and the residual is the least-squares residual.
+    A, b = zero_column_lls()
+    z = 5
+    with pytest.raises(np.linalg.LinAlgError):
+        lsqr.ski_lls(A, b, seed=3, s=1, m=48)
+    x, info = lsqr.ski_lls(A, b, seed=3, s=1, m=48, perturb=1e-10)
+    assert info["rank"] == z and info["perturb"] == 1e-10
+    keep = np.arange(A.shape[1]) != z
+    xr = np.linalg.lstsq(A[:, keep], b, rcond=None)[0]
+    assert np.linalg.norm(x[keep] - xr) <= 1e-10 * np.linalg.norm(xr)
+    assert np.linalg.norm(b - A @ x) == pytest.approx(np.linalg.norm(b - A[:, keep] @ xr), rel=1e-12)
+    assert lsqr.residual_metric(A, b, x) <= 1e-10
+    assert np.isfinite(x[z])
