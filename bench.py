@@ -13,8 +13,14 @@ bytes of [SA | Sb] written) / time of the sketch stage (premix + hash), with
 the time-to-1e-10 of both solves reported beside it.  Inputs are resident in
 HBM and larger than L2 (1.6 GB vs 129 MB), so no flush is needed.
 
---impl reference times the CPU FP64 oracle on a bounded sample of the same
-workload (a slice of A's columns) -- the slow reference arm.
+Outside the timed step the line also carries: the BF16 form of the same
+solve; the mixed-precision workload at its own size (A = U diag(sigma) V^T,
+200000 x 4000, kappa 1e6 and 1e10), FP64 against mixed; the whole solve end
+to end with host buffers; and the oracle timed on the host cores.
+
+--impl reference times the CPU FP64 oracle on the host cores: one oracle
+process per core, each on an independent block of A's columns (or whole
+problems of the batch) -- the slow reference arm.
 """
 import argparse
 import json
@@ -27,8 +33,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-# the CPU oracle is timed sequentially (one BLAS / OpenMP thread), as the
-# paper's own timings are; set before numpy loads its BLAS
+# each process of the CPU oracle runs one BLAS / OpenMP thread (the paper's
+# own timings are sequential); the host cores are used by running one oracle
+# process per core on independent parts of the workload.  Set before numpy
+# loads its BLAS, and inherited by the oracle's spawned processes.
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
@@ -69,11 +77,11 @@ def peaks():
 # 2.07 GHz = 1.26 TFLOP/s (a DFMA loop measured 1.00 on this machine).
 FP64_PEAK_TFLOPS = 1.26
 FP32_PEAK_TFLOPS = 72.0
-# DRAM bytes (read + write) per launch from ncu for the current kernels
-# (profiles/hash_gather_and_premix_dense_50000x4000.md): the whole sketch stage
-# (bucket lists, both premix passes, the nonfinite scan, the column-unit
-# bound, the hash gather and the NaN post-pass) and the hash gather alone;
-# None where not captured.
+# DRAM bytes (read + write) per launch, from ncu's dram__bytes_read.sum and
+# dram__bytes_write.sum of the current kernels: the whole sketch stage (bucket
+# lists, both premix passes, the nonfinite scan, the column-unit bound, the
+# hash gather and the NaN post-pass) and the hash gather alone; None where not
+# captured.
 SKETCH_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 43264 + 38400 + 429056 + 333056 + 1612551424 + 1555619072 + 7936 +
                   1598208 + 1618771200 + 2050941696 + 2425076480 + 236391168 + 20480}
 GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2425076480 + 236391168}
@@ -205,6 +213,93 @@ def host_vec(b):
     return b.cpu().numpy() if hasattr(b, "detach") else b
 
 
+def host_cores():
+    """The host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class HostOracle:
+    """The CPU oracle, as it stands, run on every host core: a process pool
+    (started with spawn, safe beside CUDA) whose workers each run the oracle on
+    one independent part of the workload -- a block of A's columns for the
+    sketch (S*A acts on every column alone), whole problems for the batch.
+    The inputs are placed once in shared memory; the timed region is the pool's
+    map, wall clock, so it includes each worker's attach and dispatch."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or host_cores()
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.shm = []
+
+    def share(self, arr):
+        import numpy as np
+        from multiprocessing import shared_memory
+        arr = np.ascontiguousarray(arr)
+        sh = shared_memory.SharedMemory(create=True, size=max(1, arr.nbytes))
+        np.ndarray(arr.shape, dtype=arr.dtype, buffer=sh.buf)[...] = arr
+        self.shm.append(sh)
+        return (sh.name, arr.shape, arr.dtype.str)
+
+    def run(self, fn, jobs):
+        t0 = time.perf_counter()
+        out = self.pool.map(fn, jobs, chunksize=1)
+        return out, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+        for sh in self.shm:
+            sh.close()
+            sh.unlink()
+        self.shm = []
+
+
+def _attach(ref):
+    """A read-only view of an array that HostOracle.share placed in shared memory."""
+    import numpy as np
+    from multiprocessing import shared_memory
+    name, shape, dt = ref
+    # the spawned workers share the parent's resource tracker: the segment stays
+    # registered once, and the parent unlinks it
+    sh = shared_memory.SharedMemory(name=name)
+    return sh, np.ndarray(shape, dtype=np.dtype(dt), buffer=sh.buf)
+
+
+def _oracle_dense_block(job):
+    aref, bref, c0, c1, seed, s, m, n_pad = job
+    from oracle import sketch as osk, wht as owht
+    sha, A = _attach(aref)
+    shb, b = _attach(bref) if bref is not None else (None, None)
+    Ab = A[:, c0:c1]
+    if n_pad:
+        owht.hrht_sketch(seed, s, m, Ab, b, n_pad)
+    else:
+        osk.sketch_rows(seed, s, m, Ab, b)
+    del A, Ab, b
+    sha.close()
+    if shb is not None:
+        shb.close()
+    return c1 - c0
+
+
+def dense_oracle_all_cores(ho, aref, bref, cfg, seed):
+    """The oracle's sketch of the whole of [A | b], columns split over the host
+    cores (b with the first block).  Returns (GB/s, wall s, sample text)."""
+    d = cfg["d"]
+    chunk = -(-d // ho.cores)
+    jobs = [(aref, bref if c0 == 0 else None, c0, min(d, c0 + chunk), seed, cfg["s"], cfg["m"], cfg["n_pad"])
+            for c0 in range(0, d, chunk)]
+    _, dt = ho.run(_oracle_dense_block, jobs)
+    sample = "oracle %s sketch (numpy FP64) of all of A (%d x %d) and b, m=%d, s=%d: %d column blocks of %d on %d " \
+             "host processes" % ("HRHT" if cfg["n_pad"] else "s-hashing", cfg["n"], d, cfg["m"], cfg["s"],
+                                 len(jobs), chunk, ho.cores)
+    return sketch_bytes(cfg) / dt / 1e9, dt, sample
+
+
 def oracle_sample(A, b, cfg, cols, seed):
     """Time the CPU oracle's sketch on A[:, :cols] (the bounded CPU sample)."""
     from oracle import sketch as osk, wht as owht
@@ -225,26 +320,82 @@ def run_reference(args, name):
     if rank != 0:
         return
     A, b, cfg = make_problem(name, args.seed)
-    cols = args.ref_cols
-    for _ in range(args.warmup):
-        oracle_sample(A, b, cfg, cols, args.seed)
-    vals, times = [], []
-    for _ in range(args.steps):
-        v, dt = oracle_sample(A, b, cfg, cols, args.seed)
-        vals.append(v)
-        times.append(dt)
+    A, b = host_cols(A, cfg["d"]), host_vec(b)
+    ho = HostOracle(args.ref_cores or None)
+    try:
+        aref, bref = ho.share(A), ho.share(b)
+        for _ in range(args.warmup):
+            dense_oracle_all_cores(ho, aref, bref, cfg, args.seed)
+        vals, times = [], []
+        sample = ""
+        for _ in range(args.steps):
+            v, dt, sample = dense_oracle_all_cores(ho, aref, bref, cfg, args.seed)
+            vals.append(v)
+            times.append(dt)
+    finally:
+        ho.close()
     value = statistics.mean(vals)
-    sample = "oracle %s sketch (numpy FP64) of A[:, :%d] (%d x %d) + b, m=%d, s=%d" % (
-        "HRHT" if cfg["n_pad"] else "s-hashing", cols, cfg["n"], cols, cfg["m"], cfg["s"])
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": name, **cfg},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": ho.cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_dense(args, A, b, cfg):
+    """The oracle's sketch timed on the host: the whole of [A | b] on every
+    host core (the reported value), and a column sample on one thread."""
+    Ah, bh = host_cols(A, cfg["d"]), host_vec(b)
+    ho = HostOracle(args.ref_cores or None)
+    try:
+        aref, bref = ho.share(Ah), ho.share(bh)
+        dense_oracle_all_cores(ho, aref, bref, cfg, args.seed)
+        runs = [dense_oracle_all_cores(ho, aref, bref, cfg, args.seed) for _ in range(2)]
+    finally:
+        ho.close()
+    cols = min(args.ref_cols, cfg["d"])
+    v1, dt1 = oracle_sample(Ah, bh, cfg, cols, args.seed)
+    return {"value": statistics.mean(r[0] for r in runs), "unit": "GB/s", "cores": ho.cores, "kind": "oracle",
+            "sample": runs[-1][2], "s_per_run": statistics.mean(r[1] for r in runs),
+            "single_thread": {"value": v1, "unit": "GB/s", "cores": 1, "s": dt1,
+                              "sample": "oracle %s sketch (numpy FP64) of A[:, :%d] + b, same n, n_pad, m, s" % (
+                                  "HRHT" if cfg["n_pad"] else "s-hashing", cols)}}
+
+
+def usv_solves(pkg, torch, args, n=200000, d=4000, n_pad=262144):
+    """The mixed-precision workload at its own size, outside the timed step:
+    A = U diag(sigma) V^T (Haar U, V; sigma geometric to kappa), b = ones,
+    premix to 262144, s = 1, m = 2d, at kappa = 1e6 and 1e10; the all-FP64
+    solve and the mixed form (FP32 premix and sketch, three-pass TF32 QR, FP64
+    LSQR), each solved once untimed and then twice, to the FP64 test 1e-10.
+    Times are the library's own CUDA-event time of the whole solve."""
+    from paper_2105_11815_gb300 import workloads
+    out = {}
+    for kappa in (1e6, 1e10):
+        A, b = workloads.usv_torch(n, d, kappa, args.seed, "cuda")
+        M = pkg.dense_matrix(A)
+        common = dict(m=2 * d, s=1, seed=args.seed, premix=1, n_pad=n_pad, tol=1e-10, tau_r=1e-10)
+        forms = (("fp64", pkg.ski_opts_default(**common)),
+                 ("mixed_fp32", pkg.ski_opts_default(sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32, **common)))
+        ws = torch.empty(max(pkg.ski_solve_workspace_size(M, o) for _, o in forms), dtype=torch.uint8, device="cuda")
+        x = torch.empty(d, dtype=torch.float64, device="cuda")
+        rec = {}
+        for lab, o in forms:
+            pkg.ski_solve(M, b, o, x, ws=ws, check=False)
+            infos = [pkg.ski_solve(M, b, o, x, ws=ws, check=False) for _ in range(2)]
+            i = infos[-1]
+            rec[lab] = {"ms": statistics.mean(v.ms_total for v in infos), "iters": i.iters, "restarts": i.restarts,
+                        "status": i.status, "qr_fallback": i.qr_fallback, "rdiag_ratio": i.rdiag_ratio,
+                        "metric": max(v.metric for v in infos), "ms_sketch": i.ms_sketch, "ms_qr": i.ms_qr,
+                        "ms_trinv": i.ms_trinv, "ms_lsqr": i.ms_lsqr, "timed": False}
+        out["kappa_%.0e" % kappa] = rec
+        del A, b, M, ws, x
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args, name):
@@ -392,6 +543,27 @@ def run_ours(args, name):
     # ski_sketch_hash, [SA | Sb] -> pinned host
     Ah = (A.cpu() if torch.is_tensor(A) else torch.from_numpy(A)).pin_memory()
     bh = (b.cpu() if torch.is_tensor(b) else torch.from_numpy(b)).pin_memory()
+    # the whole solve end to end, outside the timed step: pinned A, b -> device,
+    # ski_solve (FP64, then mixed), x -> pinned host
+    xh = torch.empty(d, dtype=torch.float64).pin_memory()
+    e2e_solve = {"h2d_bytes_per_solve": int(8 * (n * d + n)), "d2h_bytes_per_solve": int(8 * d)}
+    for lab, oo in (("fp64", o64), ("mixed_fp32", omx)):
+        t_s = []
+        for rep in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            At.copy_(Ah, non_blocking=True)
+            bt.copy_(bh, non_blocking=True)
+            pkg.ski_solve(Amat, bt, oo, x, ws=ws, check=False)
+            xh.copy_(x, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                t_s.append(e0.elapsed_time(e1))
+        e2e_solve[lab + "_ms"] = statistics.mean(t_s)
+    if not args.no_usv and npad:
+        lls["usv_200000x4000"] = usv_solves(pkg, torch, args)
     SAd = torch.empty(m, d + 1, dtype=torch.float64, device="cuda")
     SAh = torch.empty(m, d + 1, dtype=torch.float64).pin_memory()
     sws = torch.empty(pkg.ski_sketch_workspace_size(Amat, 1, o64), dtype=torch.uint8, device="cuda")
@@ -418,9 +590,7 @@ def run_ours(args, name):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        vals = [oracle_sample(A, b, cfg, args.ref_cols, args.seed)[0] for _ in range(2)]
-        cpu = {"value": statistics.mean(vals), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": "oracle HRHT sketch (numpy FP64) of A[:, :%d] + b, same n, n_pad, m, s" % args.ref_cols}
+        cpu = cpu_baseline_dense(args, A, b, cfg)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -433,7 +603,7 @@ def run_ours(args, name):
                        "parallelism": "replicas" if world > 1 else "single"},
             "hbm_frac": value / world / hbm, "roofline": roofline, "sketch_roofline": sketch_roofline,
             "hash_roofline": hash_roofline, "tc_roofline": tc_roofline, "stages": stages, "lls": lls,
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
+            "e2e": e2e, "e2e_solve": e2e_solve, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line), flush=True)
 
@@ -468,29 +638,67 @@ def csr_oracle_sample(rowptr, colidx, val, b, cfg, cols, seed):
     return csr_bytes(n, int(keep.sum()), cfg["m"], cols) / dt / 1e9, dt, int(keep.sum())
 
 
+def _oracle_csr_block(job):
+    rref, cref, vref, bref, c0, c1, n, seed, s, m = job
+    import numpy as np
+    import scipy.sparse as sp
+    from oracle import sketch as osk
+    shs = [_attach(r) for r in (rref, cref, vref)]
+    (_, rowptr), (_, colidx), (_, val) = shs
+    shb, b = _attach(bref) if bref is not None else (None, None)
+    keep = (colidx >= c0) & (colidx < c1)
+    rows = np.repeat(np.arange(n), np.diff(rowptr))[keep]
+    A = sp.csr_matrix((val[keep], (rows, colidx[keep] - c0)), shape=(n, c1 - c0))
+    osk.sketch_rows(seed, s, m, A, b)
+    nnz = int(keep.sum())
+    del rowptr, colidx, val, b, keep, rows, A
+    for sh, _ in shs:
+        sh.close()
+    if shb is not None:
+        shb.close()
+    return nnz
+
+
+def csr_oracle_all_cores(ho, refs, cfg, seed):
+    """The oracle's CSR sketch of all of [A | b], columns split over the host
+    cores (each process builds its column block's CSR, then sketches it)."""
+    d = cfg["d"]
+    chunk = -(-d // ho.cores)
+    rref, cref, vref, bref = refs
+    jobs = [(rref, cref, vref, bref if c0 == 0 else None, c0, min(d, c0 + chunk), cfg["n"], seed, cfg["s"], cfg["m"])
+            for c0 in range(0, d, chunk)]
+    nnzs, dt = ho.run(_oracle_csr_block, jobs)
+    sample = ("oracle CSR sketch (numpy FP64) of all of A (%d x %d, %d nonzeros) and b, m=%d, s=%d: %d column blocks "
+              "of %d on %d host processes, each also extracting its block" % (cfg["n"], d, sum(nnzs), cfg["m"],
+                                                                              cfg["s"], len(jobs), chunk, ho.cores))
+    return csr_bytes(cfg["n"], sum(nnzs), cfg["m"], d) / dt / 1e9, dt, sample
+
+
 def run_reference_csr(args, name):
     rank = int(os.environ.get("RANK", "0"))  # the oracle runs on rank 0 alone: no process group
     if rank != 0:
         return
     rowptr, colidx, val, b, cfg = make_csr(name, args.seed)
-    cols = args.ref_cols
-    for _ in range(args.warmup):
-        csr_oracle_sample(rowptr, colidx, val, b, cfg, cols, args.seed)
-    vals, times = [], []
-    nnz_s = 0
-    for _ in range(args.steps):
-        v, dt, nnz_s = csr_oracle_sample(rowptr, colidx, val, b, cfg, cols, args.seed)
-        vals.append(v)
-        times.append(dt)
+    ho = HostOracle(args.ref_cores or None)
+    try:
+        refs = (ho.share(rowptr), ho.share(colidx), ho.share(val), ho.share(b))
+        for _ in range(args.warmup):
+            csr_oracle_all_cores(ho, refs, cfg, args.seed)
+        vals, times = [], []
+        sample = ""
+        for _ in range(args.steps):
+            v, dt, sample = csr_oracle_all_cores(ho, refs, cfg, args.seed)
+            vals.append(v)
+            times.append(dt)
+    finally:
+        ho.close()
     value = statistics.mean(vals)
-    sample = "oracle CSR sketch (numpy FP64) of the columns < %d (%d nonzeros), all rows, m=%d, s=%d" % (
-        cols, nnz_s, cfg["m"], cfg["s"])
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": name, **cfg},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": ho.cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 
 
@@ -582,10 +790,17 @@ def run_csr(args, name):
            "ms_per_step": e2e_ms}
     cpu = None
     if rank == 0 and not args.no_cpu:
-        v, _, nnz_s = csr_oracle_sample(rowptr, colidx, val, b, cfg, args.ref_cols, args.seed)
-        cpu = {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": "oracle CSR sketch (numpy FP64) of the columns < %d (%d nonzeros), all rows" % (
-                   args.ref_cols, nnz_s)}
+        ho = HostOracle(args.ref_cores or None)
+        try:
+            refs = (ho.share(rowptr), ho.share(colidx), ho.share(val), ho.share(b))
+            v, dt, smp = csr_oracle_all_cores(ho, refs, cfg, args.seed)
+        finally:
+            ho.close()
+        v1, dt1, nnz_s = csr_oracle_sample(rowptr, colidx, val, b, cfg, args.ref_cols, args.seed)
+        cpu = {"value": v, "unit": "GB/s", "cores": ho.cores, "kind": "oracle", "sample": smp, "s_per_run": dt,
+               "single_thread": {"value": v1, "unit": "GB/s", "cores": 1, "s": dt1,
+                                 "sample": "oracle CSR sketch (numpy FP64) of the columns < %d (%d nonzeros), all "
+                                           "rows" % (args.ref_cols, nnz_s)}}
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -603,21 +818,30 @@ def run_csr(args, name):
 BATCH_METRIC = "batched LLS problems/s to ||A^T r||/(||A||_F ||r||) <= 1e-10, forward + adjoint backward"
 
 
-def batch_oracle_sample(shapes, seed, count):
-    """Time the oracle's Ski-LLS and adjoint on the first `count` problems."""
+def _oracle_problem(job):
+    i, n, d, seed = job
     import numpy as np
     from oracle import adjoint as oadj, lsqr as olsqr
-    g = np.random.default_rng(seed)
-    t = 0.0
-    for i, (n, d) in enumerate(shapes[:count]):
-        A = g.standard_normal((n, d))
-        b = g.standard_normal(n)
-        c = g.standard_normal(d)
-        t0 = time.perf_counter()
-        x, _ = olsqr.ski_lls(A, b, seed + i, 1, int(2 * d), tau_r=1e-10)
-        oadj.lstsq_grad(A, b, x, c)
-        t += time.perf_counter() - t0
-    return count / t, t
+    g = np.random.default_rng((seed, i))
+    A = g.standard_normal((n, d))
+    b = g.standard_normal(n)
+    c = g.standard_normal(d)
+    t0 = time.perf_counter()
+    x, _ = olsqr.ski_lls(A, b, seed + i, 1, int(2 * d), tau_r=1e-10)
+    oadj.lstsq_grad(A, b, x, c)
+    return time.perf_counter() - t0
+
+
+def batch_oracle_all_cores(ho, shapes, seed, count):
+    """The oracle's Ski-LLS and adjoint on the first `count` problems of the
+    batch, one problem per host process at a time.  The timed region is the
+    wall clock of the map; each process draws its problem before its own
+    timer starts, so the wall clock also covers those draws."""
+    jobs = [(i, n, d, seed) for i, (n, d) in enumerate(shapes[:count])]
+    per, dt = ho.run(_oracle_problem, jobs)
+    sample = ("oracle Ski-LLS + adjoint (numpy FP64) on the first %d problems of the batch, one per host process "
+              "(%d processes); slowest problem %.2f s" % (count, ho.cores, max(per)))
+    return count / dt, dt, sample
 
 
 def run_reference_batched(args, name):
@@ -627,20 +851,26 @@ def run_reference_batched(args, name):
     from paper_2105_11815_gb300 import workloads
     count = WORKLOADS[name][0]
     shapes = workloads.ragged_batch(count, args.seed)
-    batch_oracle_sample(shapes, args.seed, 1)
-    vals, times = [], []
-    for _ in range(args.steps):
-        v, dt = batch_oracle_sample(shapes, args.seed, args.ref_problems)
-        vals.append(v)
-        times.append(dt)
+    ho = HostOracle(args.ref_cores or None)
+    sample_n = min(count, max(args.ref_problems, ho.cores))
+    try:
+        for _ in range(args.warmup):
+            batch_oracle_all_cores(ho, shapes, args.seed, sample_n)
+        vals, times = [], []
+        sample = ""
+        for _ in range(args.steps):
+            v, dt, sample = batch_oracle_all_cores(ho, shapes, args.seed, sample_n)
+            vals.append(v)
+            times.append(dt)
+    finally:
+        ho.close()
     value = statistics.mean(vals)
-    sample = "oracle Ski-LLS + adjoint (numpy FP64) on the first %d problems of the batch" % args.ref_problems
     print(json.dumps({
         "impl": "reference", "metric": BATCH_METRIC, "value": value, "unit": "problems/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": name, "problems": count},
-        "cpu_baseline": {"value": value, "unit": "problems/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "problems/s", "cores": ho.cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "problems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
         flush=True)
 
@@ -781,9 +1011,12 @@ def run_batched(args, name):
            "ms_per_step": e2e_ms}
     cpu = None
     if rank == 0 and not args.no_cpu:
-        v, _ = batch_oracle_sample(shapes, args.seed, args.ref_problems)
-        cpu = {"value": v, "unit": "problems/s", "cores": 1, "kind": "oracle",
-               "sample": "oracle Ski-LLS + adjoint (numpy FP64) on the first %d problems" % args.ref_problems}
+        ho = HostOracle(args.ref_cores or None)
+        try:
+            v, dt, smp = batch_oracle_all_cores(ho, shapes, args.seed, min(count, max(args.ref_problems, ho.cores)))
+        finally:
+            ho.close()
+        cpu = {"value": v, "unit": "problems/s", "cores": ho.cores, "kind": "oracle", "sample": smp, "s_per_run": dt}
     if rank == 0:
         print(json.dumps({
             "metric": BATCH_METRIC, "value": value, "unit": "problems/s", "n_gpus": world, "steps": args.steps,
@@ -874,8 +1107,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=20210525)
-    ap.add_argument("--ref-cols", type=int, default=1024)
+    ap.add_argument("--ref-cols", type=int, default=1024, help="one-thread oracle sample: columns of A")
+    ap.add_argument("--ref-cores", type=int, default=0, help="host processes of the oracle (0 = every host core)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-usv", action="store_true",
+                    help="skip the untimed mixed-precision-workload solves of the default line")
     ap.add_argument("--streams", type=int, default=0, help="batched workload: problems in flight (0 = auto)")
     ap.add_argument("--autotune", nargs="?", const="", default=None,
                     help="batched workload: tune the launch parameters first (optional JSON cache path)")

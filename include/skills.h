@@ -244,15 +244,16 @@ ski_status ski_sketch_hash(const ski_matrix* A, const double* b, const ski_opts*
 /*
  * ski_sketch_hash_noalloc -- ski_sketch_hash for callers that cannot allocate
  * device memory (no cudaMalloc of their own, no workspace to pass).  The
- * paper has no counterpart: this is a deployment variant of Step 1.
+ * paper has no counterpart.
  *   Same arguments and result as ski_sketch_hash without `ws`/`ws_bytes`; the
  *   bucket-list scratch lives in one 4 MiB __device__ array inside this
  *   library, held by every GPU that loads it until the process exits.
  *   Limits: o->premix = 0 (the premix needs O(n_pad * d) scratch), rows * s
  *   <= 262144 and m <= 32768; beyond them SKI_EINVAL, with nothing launched.
  *   Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).
- *   The first call on a device looks up the array's device address with that
- *   device current; make that first call before any stream capture.  Every
+ *   Each call looks up the array's device address on the current device; the
+ *   first call on a device may load the module there, so make that first
+ *   call before any stream capture.  Every
  *   call reuses the same array, so calls that overlap on the GPU race: the
  *   caller must serialise them.  Asynchronous.
  */

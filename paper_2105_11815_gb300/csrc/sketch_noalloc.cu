@@ -10,13 +10,13 @@
 //
 // The scratch is one file-scope __device__ array of SKI_NOALLOC_SCRATCH_BYTES
 // (4 MiB); every GPU that loads the library holds it until the process
-// exits.  Its device address is looked up once per device, with that device
-// current, on the first call made there (so that first call should come
-// before any stream capture).  All calls share the array: calls that overlap
-// on the GPU (different streams, or different host threads on one device)
-// race on it and must be serialised by the caller.
-#include <mutex>
-
+// exits.  Its device address is looked up on every call, with the caller's
+// device current, so it stays right if the context is torn down and created
+// again (the module may then load at another address).  The first call on a
+// device may load the module there, so that first call should come before
+// any stream capture.  All calls share the array: calls that overlap on the
+// GPU (different streams, or different host threads on one device) race on
+// it and must be serialised by the caller.
 #include "common.cuh"
 #include "sketch_impl.cuh"
 
@@ -27,21 +27,12 @@
 static __device__ __align__(256) unsigned char g_ski_noalloc_scratch[SKI_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_ptr[kMaxDevices] = {nullptr};
-
+// The array's address on the current device.  In host code the array's name
+// is only a host-side stand-in, never a device address.
 ski_status scratch_for_current_device(void** out) {
-  int dev = -1;
-  SKI_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return SKI_EINVAL;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_ptr[dev]) {
-    void* p = nullptr;
-    SKI_CUDA_TRY(cudaGetSymbolAddress(&p, g_ski_noalloc_scratch));
-    g_ptr[dev] = p;
-  }
-  *out = g_ptr[dev];
+  void* p = nullptr;
+  SKI_CUDA_TRY(cudaGetSymbolAddress(&p, g_ski_noalloc_scratch));
+  *out = p;
   return SKI_OK;
 }
 }  // namespace

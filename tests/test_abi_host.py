@@ -172,3 +172,21 @@ def test_batched_workspace_scales_with_streams_and_rejects_negative(lib):
     st = pkg.lib().ski_solve_adjoint_batched(5, arr, ptrs, ptrs, ptrs, ptrs, None, ptrs, ctypes.byref(bad), None,
                                              ctypes.c_void_p(4096), 1 << 40, None)
     assert st == 1  # SKI_EINVAL
+
+
+def test_noalloc_limits_fit_its_fixed_scratch(lib):
+    # ski_sketch_hash_noalloc takes rows * s <= 262144 and m <= 32768 into a
+    # 4 MiB array: at those limits the bucket-list scratch must fit, for every
+    # s it accepts, dense or CSR, with or without b
+    pkg = lib
+    cap = 4 << 20
+    for s in range(1, 65):
+        rows = 262144 // s
+        dense = pkg.ski_matrix(kind=pkg.SKI_DENSE, n=rows, d=4, ld=4, val=4096)
+        csr = pkg.ski_matrix(kind=pkg.SKI_CSR, n=rows, d=4, ld=0, val=4096, rowptr=4096, colidx=4096, nnz=rows)
+        for hk in (0, 1):
+            o = pkg.ski_opts_default(m=32768, s=s, seed=1, hash_kind=hk)
+            for M in (dense, csr):
+                for wb in (0, 1):
+                    need = pkg.lib().ski_sketch_workspace_size(ctypes.byref(M), wb, ctypes.byref(o))
+                    assert 0 < need <= cap, (s, hk, M.kind, wb, need)

@@ -398,14 +398,15 @@ def test_adjoint_matches_closed_form_and_finite_differences():
         dA, db = oadj.lstsq_grad(A, b, xr, c)
         assert rel_fro(At.grad.cpu().numpy(), dA) <= 1e-9
         assert rel_fro(bt.grad.cpu().numpy(), db) <= 1e-9
-        if trial < 2:
-            EA, eb = g.standard_normal(A.shape), g.standard_normal(b.shape)
-            h = 1e-6
-            lp = c @ np.linalg.lstsq(A + h * EA, b + h * eb, rcond=None)[0]
-            lm = c @ np.linalg.lstsq(A - h * EA, b - h * eb, rcond=None)[0]
-            fd = (lp - lm) / (2 * h)
-            an = float((At.grad.cpu().numpy() * EA).sum() + bt.grad.cpu().numpy() @ eb)
-            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
+        # central finite differences of L along a random direction (EA, eb),
+        # on every one of the 8 problems
+        EA, eb = g.standard_normal(A.shape), g.standard_normal(b.shape)
+        h = 1e-6
+        lp = c @ np.linalg.lstsq(A + h * EA, b + h * eb, rcond=None)[0]
+        lm = c @ np.linalg.lstsq(A - h * EA, b - h * eb, rcond=None)[0]
+        fd = (lp - lm) / (2 * h)
+        an = float((At.grad.cpu().numpy() * EA).sum() + bt.grad.cpu().numpy() @ eb)
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
 
 
 def test_lstsq_batched_autograd():
@@ -452,3 +453,79 @@ def test_mixed_precision_fallback(kappa, qr, expect):
     # 1: the diagonal ratio triggered it; 2: the LSQR budget did
     assert (info.qr_fallback > 0) == (expect > 0), (info.qr_fallback, info.rdiag_ratio, info.iters)
     assert olsqr.residual_metric(A, b, x.cpu().numpy()) <= 1e-10
+
+
+# ---------------------------------------------------------------- perturbed back-solve
+def test_perturbed_back_solve_matches_the_oracle_on_a_zero_column():
+    # Column 5 of A is exactly zero: the sketch's column 5 is zero, r_55 = 0,
+    # and the rank rule stops at p = 5.  Without perturb the solve reports the
+    # singular factor; with perturb it divides by r_ii + perturb (Ski-LLS-sparse,
+    # Section 6).  x_5 is then arbitrary (A's column 5 is zero) while the other
+    # entries solve the reduced problem, as in the oracle's perturbed solve.
+    from test_oracle_qr_lsqr import zero_column_lls
+    torch, pkg = cuda()
+    A, b = zero_column_lls()
+    keep = np.arange(A.shape[1]) != 5
+    _, info = _solve(torch, pkg, A, b, check=False, m=48, s=1, seed=3)
+    assert info.status == pkg.STATUS.index("SKI_ESINGULAR") and info.rank == 5
+    x, info = _solve(torch, pkg, A, b, m=48, s=1, seed=3, perturb=1e-10)
+    assert info.status == 0 and info.rank == 5 and info.inv_dtype == pkg.SKI_F64
+    xo, oinfo = olsqr.ski_lls(A, b, seed=3, s=1, m=48, perturb=1e-10)
+    assert oinfo["rank"] == 5
+    assert rel_fro(x[keep], xo[keep]) <= 1e-9
+    xr = np.linalg.lstsq(A[:, keep], b, rcond=None)[0]
+    assert rel_fro(x[keep], xr) <= 1e-9
+    assert np.isfinite(x[5])
+    assert olsqr.residual_metric(A, b, x) <= 1e-10
+    assert abs(info.iters - oinfo["iters"]) <= 2 + info.restarts * 5
+
+
+@pytest.mark.parametrize("premix", [0, 1])
+def test_perturbed_back_solve_on_a_repeated_column(premix):
+    # Column 7 repeats column 3, so r_77 is rounding noise and the rank rule
+    # stops at p = 7.  On a consistent system b = A x_true, Q^T Sb = R x_true
+    # has a rounding-level entry 7, x_s = (R + perturb I)^{-1} Q^T Sb stays
+    # O(1), and Step 3 already meets tau_a, on the GPU as in the oracle.  (With
+    # an inconsistent b that entry is O(||r|| / sqrt(m)), x_3 and x_7 become
+    # about 1e7 with opposite signs, and A x cancels to a residual whose FP64
+    # rounding is far above 1e-10: the perturbed back-solve is a safeguard,
+    # not a solver for rank-deficient problems.)
+    torch, pkg = cuda()
+    g = np.random.default_rng(44)
+    A = g.standard_normal((3000, 40))
+    A[:, 7] = A[:, 3]
+    b = A @ g.standard_normal(40)
+    kw = dict(m=100, s=2, seed=6, perturb=1e-10, tau_a=1e-6)
+    if premix:
+        kw.update(premix=1, n_pad=4096)
+    x, info = _solve(torch, pkg, A, b, **kw)
+    assert info.status == 0 and info.rank == 7 and info.early_exit == 1
+    xo, oinfo = olsqr.ski_lls(A, b, seed=6, s=2, m=100, perturb=1e-10, tau_a=1e-6, premix=bool(premix),
+                              n_pad=4096 if premix else None)
+    assert oinfo["rank"] == 7 and oinfo["early_exit"]
+    assert np.linalg.norm(A @ x - b) <= 1e-6
+    assert np.linalg.norm(A @ xo - b) <= 1e-6
+
+
+# ---------------------------------------------------------------- wide dynamic range
+@pytest.mark.parametrize("premix", [0, 1])
+def test_rows_spanning_sixty_decades(premix):
+    # Row j of A and b is scaled by 10^e_j, e_j ~ U(-30, 30).  The LSQR pass
+    # keeps A as a (hi, lo) float pair after one global power-of-two scale
+    # (about 48 significant bits): rows 40 decades below the largest fall
+    # under FP32's range there and act as zero in that operator.  The FP64
+    # residual and metric see every row, and the warm restarts (iterative
+    # refinement against the FP64 residual) must still meet the test.
+    torch, pkg = cuda()
+    g = np.random.default_rng(77)
+    n, d = 20000, 100
+    G = g.standard_normal((n, d))
+    w = 10.0 ** g.uniform(-30.0, 30.0, n)
+    A = w[:, None] * G
+    b = w * (G @ g.standard_normal(d) + 1e-3 * g.standard_normal(n))
+    kw = dict(m=200, s=1, seed=12)
+    if premix:
+        kw.update(premix=1, n_pad=32768)
+    x, info = _solve(torch, pkg, A, b, **kw)
+    assert info.status == 0, (info.status, info.iters, info.restarts)
+    assert olsqr.residual_metric(A, b, x) <= 1e-10
