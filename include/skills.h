@@ -101,6 +101,11 @@ typedef struct {
   int32_t hash_kind;      /* ski_hash_kind of S_h: 0 = s-hashing (Def. 5: s distinct    */
                           /* rows per column), 1 = the s-hashing variant (Def. 7: s     */
                           /* rows drawn with replacement, coinciding entries add)       */
+  int32_t factorization;  /* Step 2 when R fails the rank rule (Remark (i)):            */
+                          /* 0 = SKI_ESINGULAR, or the perturbed back-solve when        */
+                          /* perturb > 0; 1 = column-pivoted QR (SA V = Q R with        */
+                          /* R = [R11 R12; 0 0], R11 p x p), Steps 3-5 on W = A V1      */
+                          /* R11^{-1}; dense A only (CSR keeps the behaviour of 0)      */
 } ski_opts;
 
 /* Result record of a solve (host memory). */
@@ -128,6 +133,9 @@ typedef struct {
                                /* preconditioner is applied in FP64 either way         */
   double rdiag_ratio;          /* max |r_ii| / min |r_ii| of the first factor (the     */
                                /* requested precision; it decides the fallback)        */
+  int32_t pivoted;             /* 1 when Step 2 took the column-pivoted QR: rank is   */
+                               /* then p of R11, and x is zero outside V1's columns    */
+  int32_t pad_;
 } ski_info;
 
 /* Defaults of Ski-LLS-dense (Section 6): m = 0 (caller must set), s = 1,
@@ -311,9 +319,18 @@ ski_status ski_trinv(int64_t d, const double* R, int64_t ldr, double* M, double*
 /*
  * ski_solve -- Algorithm 1 end to end.  x: device FP64 [d].  info: host, may
  * be NULL.  R_out: device FP64 d x d (row stride d) or NULL, receives R (for a
- * later ski_solve_adjoint).  Synchronous.  Returns SKI_ESINGULAR when R fails
- * the rank rule and o->perturb = 0, SKI_ENOCONV when it_max is reached before
- * the tolerances (x then holds the last iterate), SKI_ENONFINITE on NaN/Inf.
+ * later ski_solve_adjoint): the plain QR factor of SA, with perturb added to
+ * its diagonal when the perturbed back-solve was taken.  With
+ * o->factorization = 1 and a sketch that fails the rank rule, Step 2 takes the
+ * column-pivoted QR: info->pivoted = 1, info->rank = p, and x is zero outside
+ * the p pivoted columns (the basic solution of Theorem 8).  With o->tol > 0
+ * the acceptance metric ||A^T r|| / (||A||_F ||r||) is formed from r = b - A x
+ * by compensated (twice-working-precision) dot products, so that it certifies
+ * x even where the plain FP64 residual would be rounding noise at the level of
+ * tol.  Synchronous.  Returns SKI_ESINGULAR when R fails the rank rule with
+ * o->perturb = 0 and o->factorization = 0, SKI_ENOCONV when it_max is reached
+ * before the tolerances (x then holds the last iterate), SKI_ENONFINITE on
+ * NaN/Inf.
  */
 size_t ski_solve_workspace_size(const ski_matrix* A, const ski_opts* o);
 ski_status ski_solve(const ski_matrix* A, const double* b, const ski_opts* o, double* x,

@@ -103,6 +103,71 @@ def perturbed_back_solve(R, c, perturb, trans=False):
     return x
 
 
+def _two_sum(a, b):
+    """Knuth's TwoSum: s + e = a + b exactly, s = fl(a + b)."""
+    s = a + b
+    z = s - a
+    return s, (a - (s - z)) + (b - z)
+
+
+def _veltkamp(a):
+    """Veltkamp's splitting a = hi + lo into 26- and 27-bit halves."""
+    c = 134217729.0 * a               # (2^27 + 1) a
+    hi = c - (c - a)
+    return hi, a - hi
+
+
+def _two_prod(a, b):
+    """Dekker's TwoProduct: p + e = a * b exactly, p = fl(a * b)."""
+    p = a * b
+    ah, al = _veltkamp(a)
+    bh, bl = _veltkamp(b)
+    return p, ((ah * bh - p) + ah * bl + al * bh) + al * bl
+
+
+def residual_dd(A, b, x):
+    """r = b - A x with every row's A_i x as the compensated dot product Dot2
+    of Ogita, Rump & Oishi (SIAM J. Sci. Comput. 26, 2005) -- TwoProduct of
+    each term, TwoSum of the running sum, the errors summed beside it -- and
+    b_i - (s + c) rounded once: r as if computed in twice the working
+    precision.  Vectorised over the rows; the terms of a row are taken in
+    column order.  A: dense ndarray or scipy sparse."""
+    x = np.asarray(x, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    n = b.shape[0]
+    s = np.zeros(n)
+    c = np.zeros(n)
+    if hasattr(A, "tocsr"):
+        csr = A.tocsr()
+        csr.sort_indices()
+        cnt = np.diff(csr.indptr)
+        for k in range(int(cnt.max()) if n else 0):
+            rows = np.flatnonzero(cnt > k)
+            idx = csr.indptr[rows] + k
+            p, e = _two_prod(csr.data[idx], x[csr.indices[idx]])
+            t, te = _two_sum(s[rows], p)
+            s[rows] = t
+            c[rows] += e + te
+    else:
+        At = np.ascontiguousarray(np.asarray(A, dtype=np.float64).T)
+        for j in range(At.shape[0]):
+            p, e = _two_prod(At[j], x[j])
+            s, te = _two_sum(s, p)
+            c += e + te
+    h, he = _two_sum(b, -s)
+    return h + (he - c)
+
+
+def residual_metric_dd(A, b, x):
+    """||A^T r|| / (||A||_F ||r||) with r from ``residual_dd``: the acceptance
+    metric free of the rounding of b - A x, which dominates the plain FP64
+    value when x is large along small singular directions."""
+    r = residual_dd(A, b, x)
+    fro = np.sqrt((A.multiply(A)).sum()) if hasattr(A, "multiply") else np.linalg.norm(A)
+    rn = np.linalg.norm(r)
+    return float(np.linalg.norm(A.T @ r) / (fro * rn)) if rn > 0 else 0.0
+
+
 def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
             it_max=10000, rcond=1e-12, variant=False, factorization="qr", perturb=0.0):
     """Algorithm 1 with an s-hashing (optionally HRHT) sketch and Householder QR.

@@ -60,7 +60,7 @@ class ski_opts(ctypes.Structure):
                 ("rcond", ctypes.c_double), ("perturb", ctypes.c_double), ("it_max", ctypes.c_int64),
                 ("streams", ctypes.c_int32), ("premix_slab", ctypes.c_int32),
                 ("lsqr_pass", ctypes.c_int32), ("lsqr_ctas", ctypes.c_int32), ("graphs", ctypes.c_int32),
-                ("hash_kind", ctypes.c_int32)]
+                ("hash_kind", ctypes.c_int32), ("factorization", ctypes.c_int32)]
 
 
 class ski_info(ctypes.Structure):
@@ -71,7 +71,8 @@ class ski_info(ctypes.Structure):
                 ("ms_sketch", ctypes.c_float), ("ms_qr", ctypes.c_float), ("ms_trinv", ctypes.c_float),
                 ("ms_lsqr", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("ms_premix", ctypes.c_float), ("ms_gather", ctypes.c_float), ("ms_qr_gemm", ctypes.c_float),
-                ("qr_fallback", ctypes.c_int32), ("inv_dtype", ctypes.c_int32), ("rdiag_ratio", ctypes.c_double)]
+                ("qr_fallback", ctypes.c_int32), ("inv_dtype", ctypes.c_int32), ("rdiag_ratio", ctypes.c_double),
+                ("pivoted", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

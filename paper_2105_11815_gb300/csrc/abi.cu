@@ -344,6 +344,10 @@ namespace {
 
 struct SolvePlan {
   int64_t n, d, m, ncols, ld_sa, ldq_sa;
+  int64_t dl;        // unknowns of Steps 3-5: d, or p after the column-pivoted QR
+  bool pivoted;      // Step 2 took the column-pivoted QR (rank-revealing form)
+  int32_t* piv;      // [d] the column of A at each pivoted position (p used)
+  double* xfull;     // [d] an iterate in A's column order (zero outside V1)
   int32_t qr_dt;    // storage of the QR (F64 or F32)
   int32_t qr_prec;  // its precision (F64, F32 or TF32)
   int nblk;
@@ -451,8 +455,12 @@ size_t plan_solve(const ski_matrix* A, const ski_opts* o, char* base, size_t cap
   P->ld_sa = ski_round_up(ncols, 4);
   P->nblk = lsqr_ctas(n, o);
   P->lsqr_pass = o->lsqr_pass;
+  P->dl = d;
+  P->pivoted = false;
   P->R = ar.take<double>(d * d);
   P->qtsb = ar.take<double>(d);
+  P->piv = ar.take<int32_t>(d);
+  P->xfull = ar.take<double>(d);
   P->M = ar.take<double>(d * d);
   P->Mt = ar.take<double>(d * d);
   P->xs = ar.take<double>(d);
@@ -488,6 +496,7 @@ size_t plan_solve(const ski_matrix* A, const ski_opts* o, char* base, size_t cap
   o64.qr_dtype = SKI_F64;
   const size_t cscw = P->csr ? ski_csc_ws_bytes(n, d, A->nnz) : 0;
   P->region_bytes = std::max(region_need(A, o), cscw);
+  if (!P->csr && o->factorization == 1) P->region_bytes = std::max(P->region_bytes, ski_cpqr_ws_bytes(d));
   if (o->qr_dtype != SKI_F64) P->region_bytes = std::max(P->region_bytes, region_need(A, &o64));
   P->region = ar.take<char>(P->region_bytes);
   if (P->region) {
@@ -574,9 +583,11 @@ struct ChunkGraph {
 };
 
 // r = b - A x (into P.t), q = A^T r, ||r||^2 (and ||A||_F^2 when want_aa) into scalars.
+// comp: r by compensated dot products (the acceptance test of Step 5).
 ski_status residual_pass(const ski_matrix* A, const double* b, const double* x, SolvePlan& P, bool want_aa,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool comp = false) {
   FusedArgs f{};
+  f.comp = comp ? 1 : 0;
   f.maxexp = (want_aa && A->kind == SKI_DENSE) ? &P.sc->amax_exp : nullptr;
   f.A = A->kind == SKI_DENSE ? A->val : nullptr;
   f.lda = A->ld;
@@ -634,7 +645,7 @@ ski_status lsqr_iteration(const ski_matrix* A, SolvePlan& P, cudaStream_t st) {
     DfArgs f{};
     f.A2 = P.A2;
     f.n = P.n;
-    f.d = P.d;
+    f.d = P.dl;
     f.sA = P.sA;
     f.z = P.z;
     f.u = P.t;
@@ -646,10 +657,10 @@ ski_status lsqr_iteration(const ski_matrix* A, SolvePlan& P, cudaStream_t st) {
     f.sc = P.sc;
     f.variant = P.lsqr_pass;
     SKI_TRY(ski_fused_df_launch(f, st));
-    SKI_TRY(ski_reduce_par_launch(P.nblk, P.d, P.part, P.part_tt, P.q, P.sc, st));
+    SKI_TRY(ski_reduce_par_launch(P.nblk, P.dl, P.part, P.part_tt, P.q, P.sc, st));
   }
-  SKI_TRY(ski_trmv_lower_vp_launch(P.d, P.Mt, P.q, P.v, P.vp, P.part_vv, P.sc, 0, st));
-  SKI_TRY(ski_trmv_upper_update_launch(P.d, P.M, P.vp, P.part_vv, P.v, P.w, P.y, P.z, P.sc, 0, st));
+  SKI_TRY(ski_trmv_lower_vp_launch(P.dl, P.Mt, P.q, P.v, P.vp, P.part_vv, P.sc, 0, st));
+  SKI_TRY(ski_trmv_upper_update_launch(P.dl, P.M, P.vp, P.part_vv, P.v, P.w, P.y, P.z, P.sc, 0, st));
   return SKI_OK;
 }
 
@@ -710,9 +721,14 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   // factor it is guarded by the LSQR budget; after any fallback M is FP64.
   bool inv64_only = false;
   int32_t inv_dt = SKI_F64;
+  // Step 2's rank-revealing form (column-pivoted QR), dense A only
+  const bool pivot_ok = o->factorization == 1 && !P.csr;
+  bool need_pivot = false;
+  bool perturbed = false;  // R + perturb I replaced R (the perturbed back-solve)
   // Steps 1-2 and R^{-1} in the precisions of `of`
   auto factor = [&](const ski_opts* of) -> ski_status {
     carve_region(A, of, &P);
+    perturbed = false;
     Events fe;
     if (!fe.ok) return SKI_ECUDA;
     SKI_CUDA_TRY(cudaMemsetAsync(P.perr, 0, sizeof(int), st));
@@ -746,6 +762,16 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
     SKI_CUDA_TRY(cudaStreamSynchronize(st));
     if (perr) return SKI_ETIMEOUT;
     if (nonfinite) return SKI_ENONFINITE;
+    if (rank < d && pivot_ok) {
+      // the column-pivoted QR of R replaces this factor (after R_out is taken)
+      need_pivot = true;
+      ms_sk += fe.ms(0, 1);
+      ms_qr += fe.ms(1, 2);
+      ms_pm += fe.ms(5, 6);
+      ms_ga += fe.ms(6, 1);
+      return SKI_OK;
+    }
+    need_pivot = false;
     if (rank < d && o->perturb <= 0.0) return SKI_ESINGULAR;
     // R^{-1} (explicit, and its transpose)
     inv_dt = P.qr_dt;
@@ -754,7 +780,15 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
       inv_dt = SKI_F32;
     {
       SkiArena tar{P.region, P.region_bytes, 0, false};
-      SKI_TRY(ski_trinv_run(d, P.R, d, P.M, P.Mt, d, inv_dt, rank < d ? o->perturb : 0.0, tar, st));
+      if (rank < d) {
+        // the perturbed back-solve (Ski-LLS-sparse): every division by r_ii
+        // becomes one by r_ii + perturb, i.e. the factor is R + perturb I.
+        // The diagonal is changed in place so that the inverse, the Step 3
+        // refinement against the factor and R_out all use the same matrix.
+        SKI_TRY(ski_add_diag_launch(d, P.R, d, o->perturb, st));
+        perturbed = true;
+      }
+      SKI_TRY(ski_trinv_run(d, P.R, d, P.M, P.Mt, d, inv_dt, 0.0, tar, st));
     }
     SKI_CUDA_TRY(cudaEventRecord(fe.e[3], st));
     SKI_CUDA_TRY(cudaEventSynchronize(fe.e[3]));
@@ -795,17 +829,59 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
     return fs;
   }
   if (R_out) SKI_CUDA_TRY(cudaMemcpyAsync(R_out, P.R, d * d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (need_pivot) {
+    // Step 2, rank-revealing: the column-pivoted QR of [R | Q^T Sb] gives the
+    // pivots V, R11 (p x p, rows of stride d in P.R) and Q1^T Sb (P.qtsb);
+    // Steps 3-5 then run on the p unknowns of W = A V1 R11^{-1}
+    Events pe;
+    if (!pe.ok) return SKI_ECUDA;
+    SKI_CUDA_TRY(cudaEventRecord(pe.e[0], st));
+    int32_t p2 = 0;
+    {
+      SkiArena car{P.region, P.region_bytes, 0, false};
+      const ski_status cs = ski_cpqr_run(d, P.R, d, P.qtsb, o->rcond, P.R, d, P.qtsb, P.piv, &p2, car, st);
+      if (cs != SKI_OK) {
+        if (info) info->status = cs;
+        return cs;
+      }
+    }
+    SKI_CUDA_TRY(cudaEventRecord(pe.e[1], st));
+    if (p2 < 1) {
+      if (info) info->status = SKI_ESINGULAR;
+      return SKI_ESINGULAR;
+    }
+    {
+      SkiArena tar{P.region, P.region_bytes, 0, false};
+      SKI_TRY(ski_trinv_run(p2, P.R, d, P.M, P.Mt, p2, SKI_F64, 0.0, tar, st));
+    }
+    SKI_CUDA_TRY(cudaEventRecord(pe.e[2], st));
+    SKI_CUDA_TRY(cudaEventSynchronize(pe.e[2]));
+    ms_qr += pe.ms(0, 1);
+    ms_ti += pe.ms(1, 2);
+    inv_dt = SKI_F64;
+    rank = p2;
+    P.dl = p2;
+    P.pivoted = true;
+    if (info) {
+      info->rank = rank;
+      info->pivoted = 1;
+    }
+  }
+  const int64_t dl = P.dl;
   if (P.csr) {
     SkiArena car{P.csc_tmp, P.region_bytes, 0, false};
     SKI_TRY(ski_csc_build(A, P.colptr, P.rowidx, P.cval, car, st));
   }
   SKI_CUDA_TRY(cudaEventRecord(ev.e[3], st));
   // Step 3: x_s = R^{-1} Q^T Sb and its residual
-  SKI_TRY(ski_trmv_launch(true, d, P.M, d, P.qtsb, nullptr, P.xs, nullptr, st));
-  if (inv_dt == SKI_F32 && P.qr_dt == SKI_F64) {
+  SKI_TRY(ski_trmv_launch(true, dl, P.M, dl, P.qtsb, nullptr, P.xs, nullptr, st));
+  if ((inv_dt == SKI_F32 && P.qr_dt == SKI_F64) || perturbed) {
     // M is R^{-1} to FP32 accuracy: two steps of refinement against the FP64
     // R, x_s += M (Q^T Sb - R x_s), give x_s to FP64 accuracy (the error
     // squares each step), so that a consistent system still exits at Step 3.
+    // The same holds for the perturbed factor R + perturb I, whose explicit
+    // inverse loses about kappa u against a back-substitution (kappa ~
+    // |r_11| / perturb): the refined x_s is as accurate as the back-solve's.
     // The LSQR vectors are free here: v = -x_s, w = the step's residual.
     for (int it = 0; it < 2; ++it) {
       SKI_TRY(ski_copy_launch(d, P.xs, P.v, st));
@@ -816,7 +892,12 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
     }
   }
   SKI_CUDA_TRY(cudaMemcpyAsync(P.sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
-  SKI_TRY(residual_pass(A, b, P.xs, P, true, st));
+  if (P.pivoted) {
+    SKI_TRY(ski_scatter_launch(d, dl, P.piv, P.xs, P.xfull, st));
+    SKI_TRY(residual_pass(A, b, P.xfull, P, true, st));
+  } else {
+    SKI_TRY(residual_pass(A, b, P.xs, P, true, st));
+  }
   SKI_TRY(read_scalars(P, &hs, st));
   const double anorm_f = sqrt(hs.anorm_f2);
   if (!isfinite(hs.rnorm2) || !isfinite(hs.anorm_f2)) {
@@ -826,7 +907,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   if (!P.csr) {
     // A2 = A * 2^-sA with max|A2| < 1, in (hi, lo) float pairs
     P.sA = hs.amax_exp > 0 ? hs.amax_exp - 1022 : 0;
-    SKI_TRY(ski_split_a_launch(P.n, d, A->val, A->ld, P.sA, P.A2, st));
+    SKI_TRY(ski_split_a_launch(P.n, dl, A->val, A->ld, P.sA, P.A2, st, P.pivoted ? P.piv : nullptr));
   }
   int64_t iters_total = 0;
   int restarts = 0;
@@ -835,7 +916,11 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   bool early = false;
   if (sqrt(hs.rnorm2) <= o->tau_a) {
     early = true;
-    SKI_TRY(ski_copy_launch(d, P.xs, x, st));
+    if (P.pivoted)
+      SKI_TRY(ski_scatter_launch(d, dl, P.piv, P.xs, x, st));
+    else
+      SKI_TRY(ski_copy_launch(d, P.xs, x, st));
+    if (o->tol > 0.0) SKI_TRY(residual_pass(A, b, x, P, false, st, true));  // the acceptance metric, compensated
     SKI_TRY(ski_norm_launch(d, P.q, P.sc, st));
     SKI_TRY(read_scalars(P, &hs, st));
     metric = hs.rnorm2 > 0 ? hs.atr_norm / (anorm_f * sqrt(hs.rnorm2)) : 0.0;
@@ -856,8 +941,10 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
       init.conv = 0;
       init.tau_r = o->tau_r;
       SKI_CUDA_TRY(cudaMemcpyAsync(P.sc, &init, sizeof(init), cudaMemcpyHostToDevice, st));
-      SKI_TRY(ski_trmv_lower_vp_launch(d, P.Mt, P.q, P.v, P.vp, P.part_vv, P.sc, 1, st));
-      SKI_TRY(ski_trmv_upper_update_launch(d, P.M, P.vp, P.part_vv, P.v, P.w, P.y, P.z, P.sc, 1, st));
+      // A^T r of the residual pass is in A's column order: V1^T picks the pivots
+      if (P.pivoted) SKI_TRY(ski_gather_launch(dl, P.piv, P.q, P.p, st));
+      SKI_TRY(ski_trmv_lower_vp_launch(dl, P.Mt, P.pivoted ? P.p : P.q, P.v, P.vp, P.part_vv, P.sc, 1, st));
+      SKI_TRY(ski_trmv_upper_update_launch(dl, P.M, P.vp, P.part_vv, P.v, P.w, P.y, P.z, P.sc, 1, st));
       const int CHUNK = 8;
       int64_t polled = 0;
       for (;;) {
@@ -877,9 +964,17 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
         result = SKI_ETIMEOUT;
         break;
       }
-      // Step 5: x = x_s + R^{-1} delta
-      SKI_TRY(ski_trmv_launch(true, d, P.M, d, P.y, P.xs, x, nullptr, st));
-      SKI_TRY(residual_pass(A, b, x, P, false, st));
+      // Step 5: x = x_s + R^{-1} delta (x = V1 (x_s + R11^{-1} delta) when pivoted)
+      if (P.pivoted) {
+        SKI_TRY(ski_trmv_launch(true, dl, P.M, dl, P.y, P.xs, P.p, nullptr, st));
+        SKI_TRY(ski_scatter_launch(d, dl, P.piv, P.p, x, st));
+      } else {
+        SKI_TRY(ski_trmv_launch(true, d, P.M, d, P.y, P.xs, x, nullptr, st));
+      }
+      // the acceptance residual is compensated: near the FP64 floor of the
+      // metric (x large along small singular directions) a plain FP64 r is
+      // itself noise at that level, and the test would pass or fail by chance
+      SKI_TRY(residual_pass(A, b, x, P, false, st, o->tol > 0.0));
       SKI_TRY(ski_norm_launch(d, P.q, P.sc, st));
       SKI_TRY(read_scalars(P, &hs, st));
       if (!isfinite(hs.rnorm2) || !isfinite(hs.atr_norm)) {
@@ -927,7 +1022,11 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
         break;
       }
       ++restarts;
-      SKI_TRY(ski_copy_launch(d, x, P.xs, st));  // warm restart from x; P.t = r, P.q = A^T r
+      // warm restart from x; P.t = r, P.q = A^T r
+      if (P.pivoted)
+        SKI_TRY(ski_gather_launch(dl, P.piv, x, P.xs, st));
+      else
+        SKI_TRY(ski_copy_launch(d, x, P.xs, st));
     }
   }
   SKI_CUDA_TRY(cudaEventRecord(ev.e[4], st));
@@ -950,6 +1049,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
     info->qr_fallback = fell_back;
     info->inv_dtype = inv_dt;
     info->ms_qr_gemm = (float)qr_gemm_ms;
+    info->pivoted = P.pivoted ? 1 : 0;
     info->status = result;
   }
   return result;

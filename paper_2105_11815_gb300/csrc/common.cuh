@@ -201,3 +201,40 @@ struct FxAcc {
     return bad ? __longlong_as_double(0x7FF8000000000000ll) : fx_to_double(S, E, extra);
   }
 };
+
+// Grid-wide barrier of a persistent kernel (all CTAs co-resident by the
+// cooperative launch).  Every wait is bounded: after `spin_limit` polls
+// the CTA sets gb->err and all CTAs leave at their next barrier.
+struct GridBar {
+  unsigned count, gen;
+  int err, pad;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned nblocks, unsigned& my_gen, long long spin_limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = my_gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&gb->count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*(volatile unsigned*)&gb->gen == g) {
+        if (++spins > spin_limit || *(volatile int*)&gb->err) {
+          atomicExch(&gb->err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = *(volatile int*)&gb->err == 0;
+  }
+  ++my_gen;
+  __syncthreads();
+  return s_ok != 0;
+}

@@ -47,12 +47,51 @@ __global__ void __launch_bounds__(256) k_trmv(int64_t d, const double* __restric
   if (lane == 0) y[row] = add ? add[row] + acc : acc;
 }
 
+// Error-free transformations (Knuth's TwoSum; TwoProduct by FMA) and the
+// compensated dot product Dot2 of Ogita, Rump & Oishi (SIAM J. Sci. Comput.
+// 26, 2005): a sum of products accumulated as an unevaluated pair (s, c)
+// whose value s + c is as accurate as if computed in twice the working
+// precision.
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+__device__ __forceinline__ void dot2_add(double a, double x, double& s, double& c) {
+  const double p = a * x;
+  const double pe = fma(a, x, -p);
+  double t, te;
+  two_sum(s, p, t, te);
+  s = t;
+  c += pe + te;
+}
+__device__ __forceinline__ void pair_add(double& s, double& c, double s2, double c2) {
+  double t, te;
+  two_sum(s, s2, t, te);
+  s = t;
+  c += c2 + te;
+}
+__device__ __forceinline__ void pair_warp_sum(double& s, double& c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const double c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    pair_add(s, c, s2, c2);
+  }
+}
+
 // Dense fused pass over A.  Thread tid owns columns tid + k*NT (k < CPT);
 // RR rows are processed per step.  t_j = ca (A_j z) + cu u_j + cb b_j.
-template <int CPT, int RR>
+// COMP (the residual r = b - A z of the acceptance test: ca = -1, cb = 1, no
+// u): A_j z is a compensated dot product and r_j = b_j - A_j z is rounded
+// once, so r is accurate to the last bit even where b - A z cancels many
+// digits (x large along small singular directions), and the FP64 metric
+// ||A^T r|| / (||A||_F ||r||) is then a certificate, not a rounding floor.
+template <int CPT, int RR, bool COMP>
 __global__ void __launch_bounds__(512) k_fused_dense(FusedArgs f) {
   constexpr int NT = 512;
   __shared__ double red[RR][NT / 32];
+  __shared__ double redc[COMP ? RR : 1][NT / 32];
   __shared__ double tsh[RR];
   const LsqrScalars* sc = f.sc;
   if (sc && sc->flag_a) return;
@@ -88,33 +127,56 @@ __global__ void __launch_bounds__(512) k_fused_dense(FusedArgs f) {
 #pragma unroll
         for (int k = 0; k < CPT; ++k) emax = max(emax, (int)((__double_as_longlong(a[r][k]) >> 52) & 0x7FF));
     }
-    double p[RR];
+    double p[RR], pc[COMP ? RR : 1];
 #pragma unroll
     for (int r = 0; r < RR; ++r) {
-      double s = 0.0;
+      double s = 0.0, c = 0.0;
+      if (COMP) {
 #pragma unroll
-      for (int k = 0; k < CPT; ++k) s = fma(a[r][k], zr[k], s);
+        for (int k = 0; k < CPT; ++k) dot2_add(a[r][k], zr[k], s, c);
+        pair_warp_sum(s, c);
+        pc[COMP ? r : 0] = c;
+      } else {
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) s = fma(a[r][k], zr[k], s);
+        s = ski_warp_sum(s);
+      }
       if (f.want_aa) {
 #pragma unroll
         for (int k = 0; k < CPT; ++k) aa = fma(a[r][k], a[r][k], aa);
       }
-      p[r] = ski_warp_sum(s);
+      p[r] = s;
     }
     if (lane == 0)
 #pragma unroll
-      for (int r = 0; r < RR; ++r) red[r][wid] = p[r];
+      for (int r = 0; r < RR; ++r) {
+        red[r][wid] = p[r];
+        if (COMP) redc[COMP ? r : 0][wid] = pc[COMP ? r : 0];
+      }
     __syncthreads();
     if (tid < RR) {
       const int64_t j = j0 + tid;
-      double dot = 0.0;
-#pragma unroll
-      for (int q = 0; q < NT / 32; ++q) dot += red[tid][q];
       double t = 0.0;
-      if (j < r1) {
-        t = ca * dot;
-        if (f.u) t = fma(cu, f.u[j], t);
-        if (f.b) t = fma(cb, f.b[j], t);
-        f.t[j] = t;
+      if (COMP) {
+        double s = 0.0, c = 0.0;
+#pragma unroll
+        for (int q = 0; q < NT / 32; ++q) pair_add(s, c, red[tid][q], redc[COMP ? tid : 0][q]);
+        if (j < r1) {
+          double h, he;
+          two_sum(f.b[j], -s, h, he);
+          t = h + (he - c);
+          f.t[j] = t;
+        }
+      } else {
+        double dot = 0.0;
+#pragma unroll
+        for (int q = 0; q < NT / 32; ++q) dot += red[tid][q];
+        if (j < r1) {
+          t = ca * dot;
+          if (f.u) t = fma(cu, f.u[j], t);
+          if (f.b) t = fma(cb, f.b[j], t);
+          f.t[j] = t;
+        }
       }
       tsh[tid] = t;
     }
@@ -160,17 +222,30 @@ __global__ void __launch_bounds__(256) k_csr_rows(FusedArgs f) {
   const int64_t r0 = (int64_t)blockIdx.x * f.rows_per;
   const int64_t r1 = min(f.n, r0 + f.rows_per);
   for (int64_t j = r0 + wid; j < r1; j += 8) {
-    double s = 0.0, sa = 0.0;
+    double s = 0.0, sa = 0.0, c = 0.0;
     for (int64_t p = f.rowptr[j] + lane; p < f.rowptr[j + 1]; p += 32) {
       const double v = f.val[p];
-      s = fma(v, f.z[f.colidx[p]], s);
+      if (f.comp)
+        dot2_add(v, f.z[f.colidx[p]], s, c);
+      else
+        s = fma(v, f.z[f.colidx[p]], s);
       sa = fma(v, v, sa);
     }
-    s = ski_warp_sum(s);
+    if (f.comp)
+      pair_warp_sum(s, c);
+    else
+      s = ski_warp_sum(s);
     if (f.want_aa) aa += ski_warp_sum(sa);
-    double t = ca * s;
-    if (f.u) t = fma(cu, f.u[j], t);
-    if (f.b) t = fma(cb, f.b[j], t);
+    double t;
+    if (f.comp) {
+      double h, he;
+      two_sum(f.b[j], -s, h, he);
+      t = h + (he - c);
+    } else {
+      t = ca * s;
+      if (f.u) t = fma(cu, f.u[j], t);
+      if (f.b) t = fma(cb, f.b[j], t);
+    }
     if (lane == 0) f.t[j] = t;
     tt = fma(t, t, tt);
   }
@@ -327,6 +402,7 @@ int ski_fused_ctas(int64_t n) {
 ski_status ski_fused_launch(const FusedArgs& f0, cudaStream_t st) {
   FusedArgs f = f0;
   if (f.rowptr) {
+    if (f.comp && (f.ca != -1.0 || f.cb != 1.0 || f.u || !f.b || f.coef_from_scalars)) return SKI_EINVAL;
     f.rows_per = ski_cdiv(f.n, f.nblk);
     k_csr_rows<<<f.nblk, 256, 0, st>>>(f);
     SKI_LAUNCH_CHECK();
@@ -334,11 +410,16 @@ ski_status ski_fused_launch(const FusedArgs& f0, cudaStream_t st) {
   }
   f.rows_per = ski_cdiv(f.n, f.nblk);
   const int64_t cpt = ski_cdiv(f.d, 512);
-#define SKI_FUSED_CASE(C, R)                      \
-  if (cpt <= C) {                                 \
-    k_fused_dense<C, R><<<f.nblk, 512, 0, st>>>(f); \
-    SKI_LAUNCH_CHECK();                           \
-    return SKI_OK;                                \
+  // the compensated residual is the acceptance pass's alone: r = b - A z
+  if (f.comp && (f.ca != -1.0 || f.cb != 1.0 || f.u || !f.b || f.coef_from_scalars)) return SKI_EINVAL;
+#define SKI_FUSED_CASE(C, R)                                  \
+  if (cpt <= C) {                                             \
+    if (f.comp)                                               \
+      k_fused_dense<C, R, true><<<f.nblk, 512, 0, st>>>(f);   \
+    else                                                      \
+      k_fused_dense<C, R, false><<<f.nblk, 512, 0, st>>>(f);  \
+    SKI_LAUNCH_CHECK();                                       \
+    return SKI_OK;                                            \
   }
   SKI_FUSED_CASE(1, 8)
   SKI_FUSED_CASE(2, 8)
@@ -422,5 +503,19 @@ ski_status ski_scale_f32_launch(int64_t rows, int64_t cols, float* Y, int64_t ld
     k_scale<float><<<grid, 256, 0, st>>>(nr, cols, Y + j0 * ldy, ldy, s);
     SKI_LAUNCH_CHECK();
   }
+  return SKI_OK;
+}
+
+namespace {
+__global__ void k_add_diag(int64_t d, double* __restrict__ R, int64_t ldr, double delta) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < d) R[i * ldr + i] += delta;
+}
+}  // namespace
+
+ski_status ski_add_diag_launch(int64_t d, double* R, int64_t ldr, double delta, cudaStream_t st) {
+  if (d < 1) return SKI_OK;
+  k_add_diag<<<(unsigned)ski_cdiv(d, 256), 256, 0, st>>>(d, R, ldr, delta);
+  SKI_LAUNCH_CHECK();
   return SKI_OK;
 }

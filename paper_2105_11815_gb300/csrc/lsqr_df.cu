@@ -72,10 +72,11 @@ __device__ __forceinline__ bool flag_set(const volatile int* f) { return *f != 0
 // the top 24 significant bits (exact in FP32), lo the remaining 29 bits
 // rounded to 24.  Values below 2^-126 * 2^sA flush to zero.
 __global__ void k_split_a(int64_t n, int64_t d, const double* __restrict__ A, int64_t lda, int sA,
-                          float2* __restrict__ A2, int64_t ld2) {
+                          float2* __restrict__ A2, int64_t ld2, const int32_t* __restrict__ cmap) {
   const int64_t j = blockIdx.y;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < d; c += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(A[j * lda + c]);
+    const int64_t src = cmap ? (int64_t)cmap[c] : c;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(A[j * lda + src]);
     const int e = (int)((bits >> 52) & 0x7FF);
     const int es = e - sA;  // biased exponent after scaling by 2^-sA
     float h = 0.f, l = 0.f;
@@ -668,12 +669,13 @@ __global__ void __launch_bounds__(256) k_trmv_upper_update(int64_t d, const doub
 
 }  // namespace
 
-ski_status ski_split_a_launch(int64_t n, int64_t d, const double* A, int64_t lda, int sA, float2* A2, cudaStream_t st) {
+ski_status ski_split_a_launch(int64_t n, int64_t d, const double* A, int64_t lda, int sA, float2* A2, cudaStream_t st,
+                              const int32_t* cmap) {
   const int64_t ld2 = ski_a2_ld(d);
   for (int64_t j0 = 0; j0 < n; j0 += 65535) {
     const int64_t nr = std::min<int64_t>(65535, n - j0);
     dim3 grid((unsigned)std::min<int64_t>(ski_cdiv(d, 256), 16), (unsigned)nr);
-    k_split_a<<<grid, 256, 0, st>>>(nr, d, A + j0 * lda, lda, sA, A2 + j0 * ld2, ld2);
+    k_split_a<<<grid, 256, 0, st>>>(nr, d, A + j0 * lda, lda, sA, A2 + j0 * ld2, ld2, cmap);
     SKI_LAUNCH_CHECK();
   }
   return SKI_OK;

@@ -47,6 +47,7 @@ struct FusedArgs {
   int64_t rows_per;
   const LsqrScalars* sc;
   int* maxexp;  // when set: atomicMax of the biased exponent fields of A
+  int comp;     // compensated residual r = b - A z (Dot2; ca = -1, cb = 1, no u)
 };
 
 // Double-float dense pass (lsqr_df.cu): t = A z + cu u with A held as
@@ -68,8 +69,10 @@ struct DfArgs {
   int variant;  // 0, 1: register-blocked rows; 2: TMA-staged row ring; 3: row per warp
 };
 
+// A2 = the (hi, lo) split of A * 2^-sA; with cmap, column c of A2 is column
+// cmap[c] of A (d columns in all)
 ski_status ski_split_a_launch(int64_t n, int64_t d, const double* A, int64_t lda, int sA, float2* A2,
-                              cudaStream_t st);
+                              cudaStream_t st, const int32_t* cmap = nullptr);
 bool ski_df_supported(int64_t d);
 int64_t ski_a2_ld(int64_t d);
 ski_status ski_fused_df_launch(const DfArgs& f, cudaStream_t st);
@@ -98,6 +101,8 @@ ski_status ski_cg_launch(int64_t d, const double* q, double* r, double* p, doubl
 ski_status ski_outer_launch(int64_t n, int64_t d, const double* r, const double* lam, const double* al,
                             const double* x, double* dA, int64_t ld_da, cudaStream_t st);
 ski_status ski_scale_launch(int64_t rows, int64_t cols, double* Y, int64_t ldy, double s, cudaStream_t st);
+// R[i][i] += delta for i < d (R row-major, ldr)
+ski_status ski_add_diag_launch(int64_t d, double* R, int64_t ldr, double delta, cudaStream_t st);
 ski_status ski_scale_f32_launch(int64_t rows, int64_t cols, float* Y, int64_t ldy, float s, cudaStream_t st);
 
 // csc.cu: deterministic CSR -> CSC transpose (row indices ascending per column).

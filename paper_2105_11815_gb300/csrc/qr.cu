@@ -211,43 +211,6 @@ __global__ void __launch_bounds__(32 * WARPS) k_panel_step(PanelArgs<T> a, int s
   panel_step_body<T>(a, s, GlobalParts<T>{a.part_prev, a.part_cur});
 }
 
-// Grid-wide barrier of the persistent panel kernel (all CTAs co-resident by
-// the cooperative launch).  Every wait is bounded: after `spin_limit` polls
-// the CTA sets gb->err and all CTAs leave at their next barrier.
-struct GridBar {
-  unsigned count, gen;
-  int err, pad;
-};
-
-__device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned nblocks, unsigned& my_gen, long long spin_limit) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned g = my_gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&gb->count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*(volatile unsigned*)&gb->gen == g) {
-        if (++spins > spin_limit || *(volatile int*)&gb->err) {
-          atomicExch(&gb->err, 1);
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    s_ok = *(volatile int*)&gb->err == 0;
-  }
-  ++my_gen;
-  __syncthreads();
-  return s_ok != 0;
-}
-
 // The whole panel in one cooperative launch: the w + 1 column steps are
 // separated by grid barriers instead of kernel boundaries, and each CTA keeps
 // its slab of panel rows in shared memory for all of them (row stride
@@ -324,6 +287,301 @@ __global__ void __launch_bounds__(32 * NW) k_panel_cluster(PanelArgs<T> a) {
   __syncthreads();
   for (int c = warp; c < a.w; c += NW)
     for (int64_t r = r0 + lane; r < r1; r += 32) a.Ct[(int64_t)c * a.ldt + r] = slab[(r - r0) * (NB + 1) + c];
+}
+
+// ---- FP32 panel by Cholesky QR twice and Householder reconstruction
+//
+// The column-by-column panel meets a cluster barrier per column (4.5 us each
+// at 8000 rows, the QR's critical path).  For FP32 the panel is instead
+// factored with two cluster-wide reductions:
+//   (1) CholeskyQR2 (Yamamoto, Nakatsukasa, Yanagisawa & Fukaya 2015):
+//       G = P^T P, R1 = chol(G) (columns equilibrated by diag(G)^{-1/2}),
+//       Q1 = P R1^{-1}, then the same on Q1: Q = Q1 R2^{-1}, R = R2 R1;
+//   (2) Householder reconstruction (Ballard, Demmel, Grigori, Jacquelin,
+//       Knight & Nguyen, "Reconstructing Householder vectors from tall-skinny
+//       QR", 2015): LU without pivoting of Q - [S; 0], S = diag(s_i) with s_i =
+//       -sign of the i-th pivot, gives Q - [S; 0] = Y U with Y unit lower
+//       trapezoidal; then I - Y T Y^T with T = -U S Y1^{-T} is orthogonal, maps
+//       [S; 0] to Q, and H^T P = [S R; 0].
+// Y is the panel's reflector block V, T its compact-WY factor and S R its R
+// (the signs of R's rows are arbitrary in any Householder QR).  The 32 x 32
+// factorisations are done redundantly by every CTA of the cluster from the
+// same reduced Gram matrices (fixed reduction order), so all CTAs agree.
+// If an equilibrated Cholesky pivot falls below 2^-24 (panel condition above
+// about 4e3, where CholeskyQR2 in FP32 loses orthogonality) the kernel
+// restores the panel and takes the column-by-column steps instead, then
+// forms T from V^T V and the reflector scalars; either way it writes V, V^T,
+// T and the panel's R.
+constexpr int HM = NB + 1;  // row stride of the 32 x 32 work matrices
+
+// G (all CTAs) = sum over the cluster of the w x w Gram of this CTA's rows,
+// with element (r, c) of a row given by val(r, c).  1024 threads: (i, j).
+template <class F>
+__device__ __forceinline__ void cl_gram(int nrows, F val, float* Gp, float* G,
+                                        const cooperative_groups::cluster_group& cl) {
+  const int i = threadIdx.x >> 5, j = threadIdx.x & 31;
+  float s = 0.f;
+  for (int r = 0; r < nrows; ++r) s = fmaf(val(r, i), val(r, j), s);
+  Gp[i * HM + j] = s;
+  cl.sync();
+  float g = 0.f;
+  for (unsigned b = 0; b < cl.num_blocks(); ++b) g += *cl.map_shared_rank(Gp + i * HM + j, b);
+  G[i * HM + j] = g;
+  cl.sync();  // every CTA has read every partial: Gp is free again
+}
+
+// R (upper, w x w) = chol(D A D) D^{-1}, D = diag(A)^{-1/2}; A is destroyed.
+// One warp, lane = column.  False when a scaled pivot is below 2^-24 or not finite.
+__device__ __forceinline__ bool warp_chol(float* A, float* R, int w) {
+  const int lane = threadIdx.x & 31;
+  float dsc = 1.f;
+  bool ok = true;
+  if (lane < w) {
+    const float a = A[lane * HM + lane];
+    ok = a > 0.f && isfinite(a);
+    dsc = ok ? rsqrtf(a) : 1.f;
+  }
+  if (!__all_sync(0xffffffffu, ok)) return false;
+  for (int k = 0; k < w; ++k) {
+    const float dk = __shfl_sync(0xffffffffu, dsc, k);
+    if (lane < w) A[k * HM + lane] *= dk * dsc;
+  }
+  __syncwarp();
+  for (int j = 0; j < w; ++j) {
+    const float piv = A[j * HM + j];
+    if (!(piv > 0x1p-24f) || !isfinite(piv)) return false;  // uniform: every lane read the same value
+    const float rjj = sqrtf(piv);
+    const float rji = lane == j ? rjj : (lane > j && lane < w ? A[j * HM + lane] / rjj : 0.f);
+    if (lane < NB) R[j * HM + lane] = rji;
+    __syncwarp();
+    if (lane > j && lane < w)
+      for (int k = j + 1; k <= lane; ++k) A[k * HM + lane] -= R[j * HM + k] * rji;
+    __syncwarp();
+  }
+  if (lane < w)
+    for (int j = 0; j <= lane; ++j) R[j * HM + lane] /= dsc;
+  __syncwarp();
+  return true;
+}
+
+// X = U^{-1} for upper triangular U (w x w); lane = column.
+__device__ __forceinline__ void warp_upper_inv(const float* U, float* X, int w) {
+  const int lane = threadIdx.x & 31;
+  if (lane < w) {
+    for (int k = w - 1; k >= 0; --k) {
+      float x = 0.f;
+      if (k <= lane) {
+        float s = k == lane ? 1.f : 0.f;
+        for (int l = k + 1; l <= lane; ++l) s = fmaf(-U[k * HM + l], X[l * HM + lane], s);
+        x = s / U[k * HM + k];
+      }
+      X[k * HM + lane] = x;
+    }
+  }
+  __syncwarp();
+}
+
+// Rows [0, nrows) of the slab times an upper triangular X from the right.
+template <int NW>
+__device__ __forceinline__ void rows_times_upper(float* slab, int nrows, const float* X, int w) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = warp; r < nrows; r += NW) {
+    const float p = lane < w ? slab[r * HM + lane] : 0.f;
+    float q = 0.f;
+    for (int i = 0; i < w; ++i) {
+      const float pi = __shfl_sync(0xffffffffu, p, i);
+      if (i <= lane && lane < w) q = fmaf(pi, X[i * HM + lane], q);
+    }
+    if (lane < w) slab[r * HM + lane] = q;
+  }
+}
+
+template <int NW>
+__global__ void __launch_bounds__(32 * NW) k_panel_chol(PanelArgs<float> a, float* Tm) {
+  static_assert(NW == 32, "the Gram kernels map one thread to each of the 32 x 32 entries");
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char ch_raw[];
+  float* slots = reinterpret_cast<float*>(ch_raw);  // [2][PW] for the column-by-column fallback
+  float* Gp = slots + 2 * PW;                        // this CTA's Gram partial
+  float* G = Gp + NB * HM;
+  float* R1 = G + NB * HM;
+  float* X = R1 + NB * HM;                           // inverses
+  float* R2 = X + NB * HM;
+  float* Qt = R2 + NB * HM;                          // top w rows of Q, then the LU work
+  float* L1 = Qt + NB * HM;
+  float* U = L1 + NB * HM;
+  float* L1i = U + NB * HM;
+  float* Ts = L1i + NB * HM;
+  float* S = Ts + NB * HM;                           // [NB] signs
+  float* slab = S + NB;
+  __shared__ int s_ok;
+  const int rank = (int)cl.block_rank();
+  const int64_t r0 = (int64_t)rank * a.rows_per;
+  const int64_t r1 = min(a.mr, r0 + a.rows_per);
+  const int nrows = (int)max((int64_t)0, r1 - r0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w = a.w;
+  const int i2 = threadIdx.x >> 5, j2 = threadIdx.x & 31;  // (row, column) of the 32 x 32 products
+  for (int c = warp; c < NB; c += NW)
+    for (int64_t r = r0 + lane; r < r1; r += 32)
+      slab[(r - r0) * HM + c] = c < w ? a.Ct[(int64_t)c * a.ldt + r] : 0.f;
+  __syncthreads();
+  auto plain = [&](int r, int c) { return slab[r * HM + c]; };
+  // (1) CholeskyQR2
+  cl_gram(nrows, plain, Gp, G, cl);
+  if (warp == 0) {
+    const bool ok = warp_chol(G, R1, w);
+    if (ok) warp_upper_inv(R1, X, w);
+    if (lane == 0) s_ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  bool ok = s_ok != 0;
+  if (ok) {
+    rows_times_upper<NW>(slab, nrows, X, w);  // Q1 = P R1^{-1}
+    __syncthreads();
+    cl_gram(nrows, plain, Gp, G, cl);
+    if (warp == 0) {
+      const bool ok2 = warp_chol(G, R2, w);
+      if (ok2) warp_upper_inv(R2, X, w);
+      if (lane == 0) s_ok = ok2 ? 1 : 0;
+    }
+    __syncthreads();
+    ok = s_ok != 0;
+    if (!ok) {
+      rows_times_upper<NW>(slab, nrows, R1, w);  // restore P = Q1 R1 for the fallback
+      __syncthreads();
+    }
+  }
+  if (ok) {
+    rows_times_upper<NW>(slab, nrows, X, w);  // Q = Q1 R2^{-1}
+    // R = R2 R1 into R2's place after the product (thread (i, j), k in [i, j])
+    float rij = 0.f;
+    if (i2 < w && j2 < w && i2 <= j2)
+      for (int k = i2; k <= j2; ++k) rij = fmaf(R2[i2 * HM + k], R1[k * HM + j2], rij);
+    __syncthreads();
+    if (i2 < NB && j2 < NB) R2[i2 * HM + j2] = (i2 < w && j2 < w && i2 <= j2) ? rij : 0.f;
+    // (2) Householder reconstruction: the top w rows of Q from their CTAs
+    cl.sync();
+    if (i2 < w && j2 < NB) {
+      const int64_t owner = i2 / a.rows_per;
+      const float* src = cl.map_shared_rank(slab + (i2 - owner * a.rows_per) * HM + j2, (unsigned)owner);
+      Qt[i2 * HM + j2] = j2 < w ? *src : 0.f;
+    }
+    cl.sync();  // all have read the top rows: the slabs may change
+    if (warp == 0) {
+      // modified LU of Qt - S (no pivoting; s_i = -sign of the i-th pivot)
+      for (int k = 0; k < NB; ++k) {
+        L1[k * HM + lane] = (k == lane) ? 1.f : 0.f;
+        U[k * HM + lane] = 0.f;
+      }
+      __syncwarp();
+      for (int i = 0; i < w; ++i) {
+        const float aii = Qt[i * HM + i];
+        const float si = aii >= 0.f ? -1.f : 1.f;
+        __syncwarp();
+        if (lane == 0) {
+          Qt[i * HM + i] = aii - si;
+          S[i] = si;
+        }
+        __syncwarp();
+        const float piv = Qt[i * HM + i];
+        if (lane > i && lane < w) L1[lane * HM + i] = Qt[lane * HM + i] / piv;
+        if (lane >= i && lane < w) U[i * HM + lane] = Qt[i * HM + lane];
+        __syncwarp();
+        if (lane > i && lane < w) {
+          const float uic = U[i * HM + lane];
+          for (int k = i + 1; k < w; ++k) Qt[k * HM + lane] -= L1[k * HM + i] * uic;
+        }
+        __syncwarp();
+      }
+      warp_upper_inv(U, X, w);  // X = U^{-1}
+      // L1i = L1^{-1} (unit lower): lane = column
+      if (lane < w) {
+        for (int k = 0; k < w; ++k) {
+          float x = 0.f;
+          if (k == lane) x = 1.f;
+          else if (k > lane) {
+            float s = 0.f;
+            for (int l = lane; l < k; ++l) s = fmaf(-L1[k * HM + l], L1i[l * HM + lane], s);
+            x = s;
+          }
+          L1i[k * HM + lane] = x;
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    // T = -U S L1^{-T}: T[i][j] = -sum_{k=i..j} U[i][k] s_k L1i[j][k]
+    {
+      float t = 0.f;
+      if (i2 < w && j2 < w && i2 <= j2)
+        for (int k = i2; k <= j2; ++k) t = fmaf(U[i2 * HM + k] * S[k], L1i[j2 * HM + k], t);
+      Ts[i2 * HM + j2] = -t;
+    }
+    // V rows at or below w: Q U^{-1}; rows above come from L1
+    rows_times_upper<NW>(slab, nrows, X, w);
+    __syncthreads();
+    // outputs: the panel in Ct (S R on and above the diagonal, V below), V, V^T, T
+    for (int lr = warp; lr < nrows; lr += NW) {
+      const int64_t r = r0 + lr;
+      float v = 0.f, ct = 0.f;
+      if (lane < w) {
+        if (r < w) {
+          const int ri = (int)r;
+          v = lane < ri ? L1[ri * HM + lane] : (lane == ri ? 1.f : 0.f);
+          ct = lane >= ri ? S[ri] * R2[ri * HM + lane] : v;
+        } else {
+          v = slab[lr * HM + lane];
+          ct = v;
+        }
+        a.Ct[(int64_t)lane * a.ldt + r] = ct;
+      }
+      a.V[r * NB + lane] = v;
+      a.Vt[(int64_t)lane * a.ldvt + r] = v;
+    }
+    if (rank == 0 && i2 < NB && j2 < NB) {
+      Tm[i2 * NB + j2] = (i2 < w && j2 < w) ? Ts[i2 * HM + j2] : 0.f;
+      if (i2 == j2 && i2 < w) a.tau[i2] = Ts[i2 * HM + i2];
+    }
+    cl.sync();
+    return;
+  }
+  // fallback: column-by-column Householder steps on the restored panel
+  PanelArgs<float> b = a;
+  b.P = slab - r0 * HM;
+  b.ld = HM;
+  for (int s = 0; s <= w; ++s) {
+    ClusterParts<float> parts{slots + ((s + 1) & 1) * PW, slots + (s & 1) * PW};
+    panel_step_body<float, NW>(b, s, parts);
+    cl.sync();
+  }
+  __syncthreads();
+  for (int c = warp; c < w; c += NW)
+    for (int64_t r = r0 + lane; r < r1; r += 32) a.Ct[(int64_t)c * a.ldt + r] = slab[(r - r0) * HM + c];
+  // T from V^T V and the reflector scalars (forward accumulation)
+  auto vval = [&](int lr, int c) {
+    const int64_t r = r0 + lr;
+    return c >= w ? 0.f : (r < c ? 0.f : (r == c ? 1.f : slab[lr * HM + c]));
+  };
+  cl_gram(nrows, vval, Gp, G, cl);
+  if (rank == 0 && warp == 0) {  // CTA 0 wrote the reflector scalars
+    for (int k = 0; k < NB; ++k) Ts[k * HM + lane] = 0.f;
+    __syncwarp();
+    for (int i = 0; i < w; ++i) {
+      const float ti = a.tau[i];
+      float y = 0.f;
+      if (lane < i)
+        for (int k = lane; k < i; ++k) y = fmaf(Ts[lane * HM + k], G[k * HM + i], y);
+      __syncwarp();
+      if (lane < i) Ts[lane * HM + i] = -ti * y;
+      if (lane == i) Ts[i * HM + i] = ti;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (rank == 0 && i2 < NB && j2 < NB) Tm[i2 * NB + j2] = (i2 < w && j2 < w) ? Ts[i2 * HM + j2] : 0.f;
+  cl.sync();
 }
 
 // Self-test of the bounded barrier: `nblocks` is one more than the CTAs
@@ -650,6 +908,20 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     }
     cudaGetLastError();
   }
+  // FP32 panels: Cholesky QR twice and Householder reconstruction in the
+  // cluster (two cluster reductions per panel instead of one barrier per
+  // column), when its work matrices and slab fit in shared memory
+  constexpr size_t kCholMats = (size_t)(2 * PW + 10 * NB * (NB + 1) + NB) * sizeof(float);
+  constexpr size_t kCholSmemMax = 200 * 1024;
+  bool chol_ok = false;
+  if constexpr (sizeof(T) == 4) {
+    if (cluster_ok &&
+        cudaFuncSetAttribute(k_panel_chol<CNW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+        cudaFuncSetAttribute(k_panel_chol<CNW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemMax) ==
+            cudaSuccess)
+      chol_ok = true;
+    cudaGetLastError();
+  }
   SKI_CUDA_TRY(cudaMemsetAsync(bf.err, 0, sizeof(int), st));
   SKI_CUDA_TRY(cudaMemsetAsync(bf.gb, 0, sizeof(GridBar), st));
   {
@@ -674,7 +946,33 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     T* Vk = ((k0 / NB) & 1) ? bf.V2 : bf.V;
     PanelArgs<T> pa{bf.P, NB, mr, w, rows_per, ncta, nullptr, nullptr, bf.tau, Vk, bf.Vt, ldt, Ctp, ldt};
     bool done_panel = false;
-    if (cluster_ok && (sizeof(T) == 4 || mr <= kClusterRowsF64)) {
+    bool t_from_panel = false;  // the panel kernel wrote T (and no V^T V is needed)
+    if constexpr (sizeof(T) == 4) {
+      const int64_t rp = ski_cdiv(mr, CL);
+      const size_t csm = kCholMats + (size_t)rp * (NB + 1) * sizeof(float);
+      if (chol_ok && csm <= kCholSmemMax) {
+        PanelArgs<T> pc = pa;
+        pc.rows_per = rp;
+        pc.ncta = CL;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(CL);
+        cfg.blockDim = dim3(32 * CNW);
+        cfg.dynamicSmemBytes = csm;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        SKI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_chol<CNW>, pc, bf.Tm));
+        SKI_LAUNCH_CHECK();
+        done_panel = true;
+        t_from_panel = true;
+      }
+    }
+    if (!done_panel && cluster_ok && (sizeof(T) == 4 || mr <= kClusterRowsF64)) {
       // one cluster of CL CTAs: the slab of each must fit in shared memory
       const int64_t rp = ski_cdiv(mr, CL);
       const size_t csm = (size_t)(2 * PW + rp * (NB + 1)) * sizeof(T);
@@ -728,9 +1026,10 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     }
     const int64_t nct = ncols - (k0 + w);
     T* Ctr = bf.Ct + (k0 + w) * ldt + k0;  // trailing columns, rows k0..m-1
-    // V^T V (split-K over rows) and W = V^T C
-    const int sv = (int)std::min<int64_t>(152, ski_cdiv(mr, 64));
-    SKI_TRY(ski_gemm_ex<T>(NB, NB, mr, T(1), bf.Vt, ldt, 1, bf.Vt, 1, ldt, T(0), bf.pv, NB, sv, (int64_t)NB * NB, st));
+    // V^T V (split-K over rows, for T) and W = V^T C
+    const int sv = t_from_panel ? 0 : (int)std::min<int64_t>(152, ski_cdiv(mr, 64));
+    if (!t_from_panel)
+      SKI_TRY(ski_gemm_ex<T>(NB, NB, mr, T(1), bf.Vt, ldt, 1, bf.Vt, 1, ldt, T(0), bf.pv, NB, sv, (int64_t)NB * NB, st));
     if (pending_lo) {  // W reads every trailing column: the previous update must be done
       SKI_CUDA_TRY(cudaStreamWaitEvent(st, qs->e_lo, 0));
       pending_lo = false;
@@ -747,8 +1046,10 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     const int64_t zc = w + nct;
     k_reduce_z<T><<<ski_cdiv(w * zc, 256), 256, 0, st>>>(w, nct, bf.pv, sv, bf.pc, sc, q.ldz, bf.Z);
     SKI_LAUNCH_CHECK();
-    k_tfactor<T><<<1, 32, 0, st>>>(w, bf.Z, NB + q.ldz, bf.tau, bf.Tm);
-    SKI_LAUNCH_CHECK();
+    if (!t_from_panel) {
+      k_tfactor<T><<<1, 32, 0, st>>>(w, bf.Z, NB + q.ldz, bf.tau, bf.Tm);
+      SKI_LAUNCH_CHECK();
+    }
     if (nct > 0) {
       k_ttw<T><<<ski_cdiv(nct, 128), 128, 0, st>>>(w, nct, bf.Z, NB + q.ldz, bf.Tm, bf.Bpt);
       SKI_LAUNCH_CHECK();

@@ -122,3 +122,15 @@ ski_status ski_gemm_batched(int64_t M, int64_t N, int64_t K, T alpha, const T* A
 template <class T>
 ski_status ski_gemm_tri(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t sa_m, int64_t sa_k,
                         const T* B, int64_t sb_k, int64_t sb_n, T beta, T* C, int64_t ldc, int tri, cudaStream_t st);
+
+// Column-pivoted QR of [R | c] (cpqr.cu): R11 (p x p, row-major, ld11), c1
+// (the first p entries of the reflected c), piv (the column of R at each
+// pivoted position) and p under the rank rule; synchronises the stream.
+size_t ski_cpqr_ws_bytes(int64_t d);
+ski_status ski_cpqr_run(int64_t d, const double* R, int64_t ldr, const double* c, double rcond, double* R11,
+                        int64_t ld11, double* c1, int32_t* piv, int32_t* p_out, SkiArena& ar, cudaStream_t st);
+// dst[k] = src[idx[k]] for k < p
+ski_status ski_gather_launch(int64_t p, const int32_t* idx, const double* src, double* dst, cudaStream_t st);
+// dst = 0 (length d), then dst[idx[k]] = src[k] for k < p
+ski_status ski_scatter_launch(int64_t d, int64_t p, const int32_t* idx, const double* src, double* dst,
+                              cudaStream_t st);

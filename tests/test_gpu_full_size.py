@@ -1,8 +1,13 @@
 """Full-size solves in the launch configuration the benchmark times, checked
 by properties that hold at any size.  The oracle's step-by-step solve takes
 minutes at these sizes, so the acceptance criterion is recomputed on the host
-in FP64 from the returned x by the oracle's (pinned) ``residual_metric``:
-||A^T r|| / (||A||_F ||r||) <= 1e-10 with r = b - A x.
+from the returned x by the oracle's (pinned) ``residual_metric_dd``:
+||A^T r|| / (||A||_F ||r||) <= 1e-10 with r = b - A x formed by compensated
+dot products, as the library's own acceptance test forms it.  Near the
+metric's FP64 floor (the mixed-precision workload at kappa = 1e10 with
+b = ones, where x reaches 1e11 along the small singular directions) a plain
+FP64 residual is itself noise at the 1e-10 level: the device's plain value
+and the host's differed there by 7% (9.75e-11 against 1.04e-10).
 """
 import numpy as np
 import pytest
@@ -29,7 +34,7 @@ def test_dense_test_set_solve_full_size(mixed):
     assert info.status == 0 and info.metric <= 1e-10
     if mixed:
         assert info.qr_fallback == 0      # i.i.d. Gaussian: the FP32 factor preconditions
-    assert olsqr.residual_metric(At.cpu().numpy(), bt.cpu().numpy(), x.cpu().numpy()) <= 1e-10
+    assert olsqr.residual_metric_dd(At.cpu().numpy(), bt.cpu().numpy(), x.cpu().numpy()) <= 1e-10
 
 
 _USV = {}
@@ -64,10 +69,13 @@ def test_mixed_precision_workload_full_size(kappa, mixed):
     assert info.status == 0 and info.metric <= 1e-10, (info.status, info.metric, info.iters, info.restarts)
     if mixed:
         assert info.qr_fallback == (0 if kappa == 1e6 else 1), (info.qr_fallback, info.rdiag_ratio)
-    host = olsqr.residual_metric(At.cpu().numpy(), bt.cpu().numpy(), x.cpu().numpy())
+    host = olsqr.residual_metric_dd(At.cpu().numpy(), bt.cpu().numpy(), x.cpu().numpy())
     print("kappa %.0e mixed %d: iters %d restarts %d fallback %d device metric %.3e host metric %.3e ms %.1f" % (
         kappa, mixed, info.iters, info.restarts, info.qr_fallback, info.metric, host, info.ms_total))
     assert host <= 1e-10
+    # both sides evaluate r accurately: they differ only by the FP64 rounding
+    # of A^T r (about sqrt(n) u relative to ||A|| ||r||, 5e-4 of the metric here)
+    assert abs(host - info.metric) <= 0.01 * host
 
 
 @pytest.mark.parametrize("mixed", [False, True])
@@ -85,4 +93,4 @@ def test_sparse_solve_full_size(mixed):
     info = pkg.ski_solve(M, to_dev(torch, b), o, x)
     assert info.status == 0 and info.metric <= 1e-10
     A = sp.csr_matrix((v, ci, rp), shape=(n, d))
-    assert olsqr.residual_metric(A, b, x.cpu().numpy()) <= 1e-10
+    assert olsqr.residual_metric_dd(A, b, x.cpu().numpy()) <= 1e-10

@@ -258,6 +258,45 @@ def test_precondition_qr(m, d, dt):
     assert np.allclose(np.tril(Rg, -1), 0)
 
 
+@pytest.mark.parametrize("case", ["scaled_columns", "near_dependent", "tall", "last_panel_short"])
+def test_fp32_qr_panel_forms(case):
+    # FP32 panels are factored by Cholesky QR twice and Householder
+    # reconstruction (two cluster reductions per panel), with columns
+    # equilibrated; a panel whose equilibrated Cholesky pivot falls below
+    # 2^-24 (condition above ~4e3) takes the column-by-column steps instead.
+    # Checked: the backward error ||R^T R - B^T B|| / ||B||^2 at FP32 level in
+    # every case; R and Q^T Sb against the oracle at the three-pass FP32
+    # tolerance where B is well conditioned; and, where a panel is nearly
+    # singular (its FP32 R differs from the FP64 one in the ill-determined
+    # direction), that R still preconditions: kappa(B R^{-1}) near 1.
+    torch, pkg = cuda()
+    g = np.random.default_rng(7)
+    m, d = {"scaled_columns": (3000, 200), "near_dependent": (3000, 200), "tall": (12000, 160),
+            "last_panel_short": (2500, 77)}[case]
+    B = g.standard_normal((m, d + 1))
+    if case == "scaled_columns":
+        B[:, :d] *= 10.0 ** g.uniform(-5, 0, d)            # equilibration: no fallback needed
+    if case == "near_dependent":
+        B[:, 37] = B[:, 36] + 1e-6 * g.standard_normal(m)  # panel 1 condition ~1e6: column-by-column
+    SA = to_dev(torch, B).to(torch.float32).contiguous()
+    R = torch.empty(d, d, dtype=torch.float64, device="cuda")
+    qtsb = torch.empty(d, dtype=torch.float64, device="cuda")
+    pkg.ski_precondition(m, d, 1, SA, d + 1, pkg.SKI_F32, R, d, qtsb, want_rank=False)
+    Bf = SA.double().cpu().numpy()[:, :d]                   # the FP32 input exactly
+    Rg = R.cpu().numpy()
+    assert np.allclose(np.tril(Rg, -1), 0)
+    G = Bf.T @ Bf
+    assert np.linalg.norm(Rg.T @ Rg - G) / np.linalg.norm(G) <= 1e-5
+    if case == "near_dependent":
+        W = np.linalg.solve(Rg.T, Bf.T).T
+        assert np.linalg.cond(W) < 2.0
+    else:
+        Ro, C = oqr.householder_qr(SA.double().cpu().numpy(), ncols=d)
+        assert rel_fro(_signfix(Rg), _signfix(Ro)) <= 2e-5
+        sg = np.sign(np.diag(Rg)) * np.sign(np.diag(Ro))
+        assert rel_fro(sg * qtsb.cpu().numpy(), C[:, 0]) <= 6e-5
+
+
 def test_fp32_qr_preconditions_ill_conditioned_sketch():
     # R only has to precondition (Theorem 10): kappa(SA R^-1) stays near 1 for
     # the three-pass FP32 QR at kappa(SA) = 1e5, where one TF32 pass does not.

@@ -440,3 +440,49 @@ def test_perturbed_ski_lls_solves_the_reduced_problem():
     assert np.linalg.norm(b - A @ x) == pytest.approx(np.linalg.norm(b - A[:, keep] @ xr), rel=1e-12)
     assert lsqr.residual_metric(A, b, x) <= 1e-10
     assert np.isfinite(x[z])
+
+
+# ---------------------------------------------------------------- compensated residual
+def test_residual_dd_hand_worked_cancellation():
+    # row [1e16, 1, -1e16] . [1, 1, 1] = 1 exactly; in FP64 1e16 + 1 rounds
+    # to 1e16 and the plain sum is 0.  r = b - A x with b = 0 is -1.
+    A = np.array([[1e16, 1.0, -1e16], [3.0, 0.5, 0.25]])
+    x = np.ones(3)
+    b = np.array([0.0, 4.0])
+    assert (b - A @ x)[0] == 0.0                      # the plain residual loses it
+    r = lsqr.residual_dd(A, b, x)
+    assert r[0] == -1.0 and r[1] == 0.25
+    assert np.array_equal(lsqr.residual_dd(sp.csr_matrix(A), b, x), r)
+
+
+def test_residual_dd_matches_exact_rational_arithmetic():
+    # products and sums of doubles done exactly in rationals, then rounded
+    # once: Dot2 agrees to within a few units in the last place, on rows
+    # built to cancel (terms of 1e8 summing to O(1))
+    from fractions import Fraction
+    g = np.random.default_rng(51)
+    n, d = 40, 25
+    A = g.standard_normal((n, d)) * 10.0 ** g.integers(-3, 9, (n, d))
+    x = g.standard_normal(d)
+    b = A @ x + g.standard_normal(n) * 1e-3
+    r = lsqr.residual_dd(A, b, x)
+    rs = lsqr.residual_dd(sp.csr_matrix(A), b, x)
+    worst = 0.0
+    for i in range(n):
+        ex = Fraction(b[i]) - sum(Fraction(A[i, j]) * Fraction(x[j]) for j in range(d))
+        want = float(ex)
+        worst = max(worst, abs(r[i] - want) / abs(want))
+        assert abs(rs[i] - want) <= 4 * np.finfo(float).eps * abs(want)
+    assert worst <= 4 * np.finfo(float).eps
+    # the plain residual is far off on the same rows
+    plain = b - A @ x
+    assert np.max(np.abs(plain - r) / np.abs(r)) > 1e-6
+
+
+def test_residual_metric_dd_agrees_when_nothing_cancels():
+    A, b, _ = workloads.gaussian_lls(500, 20, seed=3)
+    x = np.linalg.lstsq(A, b, rcond=None)[0] + 1e-6
+    assert lsqr.residual_metric_dd(A, b, x) == pytest.approx(lsqr.residual_metric(A, b, x), rel=1e-9)
+    A2 = np.array([[2.0, 0.0, 0.0], [1.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    assert lsqr.residual_metric_dd(A2, np.array([3.0, 2.0, 1.0]), np.ones(3)) == pytest.approx(2 / np.sqrt(7),
+                                                                                              rel=1e-15)
