@@ -106,6 +106,12 @@ typedef struct {
                           /* perturb > 0; 1 = column-pivoted QR (SA V = Q R with        */
                           /* R = [R11 R12; 0 0], R11 p x p), Steps 3-5 on W = A V1      */
                           /* R11^{-1}; dense A only (CSR keeps the behaviour of 0)      */
+  int32_t pad_;
+  int64_t row_offset;     /* A holds rows [row_offset, row_offset + n) of a larger      */
+                          /* matrix: the sketch entry points draw the columns of S for */
+                          /* those global rows, so the sketches of row blocks sum to   */
+                          /* the sketch of the whole (row-block sharding); 0 for a     */
+                          /* whole A; premix and the solve entry points need 0         */
 } ski_opts;
 
 /* Result record of a solve (host memory). */
@@ -333,6 +339,38 @@ ski_status ski_trinv(int64_t d, const double* R, int64_t ldr, double* M, double*
  * NaN/Inf.
  */
 size_t ski_solve_workspace_size(const ski_matrix* A, const ski_opts* o);
+
+/*
+ * The sum over the processes of a row-block solve: replace the `count`
+ * elements of type `dtype` (ski_dtype) at the device address `buf` by their
+ * sum over all processes, in the order of `stream` (e.g. an NCCL all-reduce
+ * enqueued on it, or a synchronise-copy-add-copy); every process must see the
+ * same sum.  Returns SKI_OK, or a status that ends the solve.
+ */
+typedef ski_status (*ski_allreduce_fn)(void* buf, int64_t count, int32_t dtype, void* ctx, void* stream);
+
+/*
+ * ski_solve_rowblock -- Algorithm 1 on A split by rows over processes (one
+ * GPU each).  The paper solves on one machine; this is the data-parallel form
+ * of the same computation.  This process holds rows [o->row_offset,
+ * o->row_offset + A->n) of the whole A and the same rows of b; x (device FP64
+ * [d]) receives the whole solution on every process.
+ *   Step 1: each process sketches its rows with the columns of S of its
+ *     global rows, and one sum of [SA | Sb] (m x ld_sa) gives every process
+ *     S A = sum over row blocks of S[:, rows] A[rows, :] (Def. 5); Steps 2-3
+ *     then run on every process on the same sketch.
+ *   Step 4: every LSQR iteration sums A^T t (d) and ||t||^2 over the
+ *     processes; the residual passes of Steps 3 and 5 sum A^T r, ||r||^2 and
+ *     ||A||_F^2.  All other work is local or repeated on every process.
+ * Same options, workspace query (ski_solve_workspace_size of the local
+ * block), statuses and report as ski_solve, except: o->premix must be 0 (H D
+ * mixes every row of A), A->n may be below d, graph replay is off, and
+ * `allreduce` is called with the same sequence of buffers on every process
+ * (a collective).  Synchronous.  SKI_EINVAL when allreduce is NULL.
+ */
+ski_status ski_solve_rowblock(const ski_matrix* A, const double* b, const ski_opts* o, double* x,
+                              double* R_out, ski_info* info, void* ws, size_t ws_bytes, void* stream,
+                              ski_allreduce_fn allreduce, void* ctx);
 ski_status ski_solve(const ski_matrix* A, const double* b, const ski_opts* o, double* x,
                      double* R_out, ski_info* info, void* ws, size_t ws_bytes, void* stream);
 

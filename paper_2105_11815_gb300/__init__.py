@@ -60,7 +60,8 @@ class ski_opts(ctypes.Structure):
                 ("rcond", ctypes.c_double), ("perturb", ctypes.c_double), ("it_max", ctypes.c_int64),
                 ("streams", ctypes.c_int32), ("premix_slab", ctypes.c_int32),
                 ("lsqr_pass", ctypes.c_int32), ("lsqr_ctas", ctypes.c_int32), ("graphs", ctypes.c_int32),
-                ("hash_kind", ctypes.c_int32), ("factorization", ctypes.c_int32)]
+                ("hash_kind", ctypes.c_int32), ("factorization", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("row_offset", ctypes.c_int64)]
 
 
 class ski_info(ctypes.Structure):
@@ -76,6 +77,11 @@ class ski_info(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# ski_allreduce_fn: (buf, count, dtype, ctx, stream) -> ski_status
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                ctypes.c_void_p)
 
 
 _lib = None
@@ -106,6 +112,7 @@ _SIGS = {
     "ski_trinv": (_I32, [_I64, _P, _I64, _P, _P, _I64, _I32, _D, _P, _SZ, _P]),
     "ski_solve_workspace_size": (_SZ, [_MP, _OP]),
     "ski_solve": (_I32, [_MP, _P, _OP, _P, _P, _IP, _P, _SZ, _P]),
+    "ski_solve_rowblock": (_I32, [_MP, _P, _OP, _P, _P, _IP, _P, _SZ, _P, ALLREDUCE_FN, _P]),
     "ski_solve_batched_workspace_size": (_SZ, [_I32, _MP, _OP]),
     "ski_solve_batched": (_I32, [_I32, _MP, _P, _OP, _P, _P, _IP, _P, _SZ, _P]),
     "ski_solve_adjoint_workspace_size": (_SZ, [_MP, _OP]),
@@ -311,6 +318,37 @@ def ski_solve(A, b, opts, x, R_out=None, ws=None, stream=None, check=True):
                          _ptr(w), nb, _stream(stream))
     if check:
         _check(st, "ski_solve")
+    return info
+
+
+def ski_solve_rowblock(A, b, opts, x, allreduce, R_out=None, ws=None, stream=None, check=True):
+    """Algorithm 1 on this process's row block of A (opts.row_offset: the
+    global index of its first row).  allreduce(ptr, count, dtype, stream_ptr)
+    sums `count` elements of ski_dtype `dtype` at device address `ptr` over the
+    processes, in place and in the order of the CUDA stream `stream_ptr`.
+    Returns the ski_info record."""
+    nb = ski_solve_workspace_size(A, opts)
+    if nb == 0:
+        raise SkiError(1, "ski_solve_workspace_size")
+    w = _ws(nb, x.device, ws)
+    info = ski_info()
+    failed = []
+
+    def _cb(buf, count, dtype, ctx, st):
+        try:
+            allreduce(buf, count, dtype, st)
+            return 0
+        except Exception as e:  # the status ends the solve; the exception is re-raised below
+            failed.append(e)
+            return STATUS.index("SKI_ECUDA")
+
+    cb = ALLREDUCE_FN(_cb)
+    st = lib().ski_solve_rowblock(ctypes.byref(A), _ptr(b), ctypes.byref(opts), _ptr(x), _ptr(R_out),
+                                  ctypes.byref(info), _ptr(w), nb, _stream(stream), cb, None)
+    if failed:
+        raise failed[0]
+    if check:
+        _check(st, "ski_solve_rowblock")
     return info
 
 

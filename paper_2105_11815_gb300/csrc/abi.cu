@@ -107,7 +107,9 @@ static ski_status check_sketch_opts(const ski_matrix* A, const ski_opts* o) {
   if (o->premix) {
     if (A->kind != SKI_DENSE) return SKI_EINVAL;
     if (o->n_pad != 0 && (!pow2(o->n_pad) || o->n_pad < A->n)) return SKI_EINVAL;
+    if (o->row_offset != 0) return SKI_EINVAL;  // H mixes every row of A: no row block premixes alone
   }
+  if (o->row_offset < 0 || o->row_offset + A->n >= (1ll << 62)) return SKI_EINVAL;
   const int64_t rows = o->premix ? (o->n_pad ? o->n_pad : next_pow2(A->n)) : A->n;
   if (rows * (int64_t)o->s >= (1ll << 31) || rows >= (1ll << 31)) return SKI_EINVAL;
   return SKI_OK;
@@ -178,7 +180,7 @@ static ski_status sketch_run(const ski_matrix* A, const double* b, const ski_opt
   if (!ar.ok() || !bkws) return SKI_ENOMEM;
   SkiArena bar{bkws, bkb, 0, false};
   SkiBuckets bk;
-  SKI_TRY(ski_build_buckets(o->seed, o->s, o->hash_kind, o->m, rows, bar, st, &bk));
+  SKI_TRY(ski_build_buckets(o->seed, o->s, o->hash_kind, o->m, rows, bar, st, &bk, o->row_offset));
   if (e_bk) SKI_CUDA_TRY(cudaEventRecord(e_bk, st));
   const double inv_sqrt_s = 1.0 / sqrt((double)o->s);
   if (!o->premix) {
@@ -342,8 +344,19 @@ extern "C" ski_status ski_trinv(int64_t d, const double* R, int64_t ldr, double*
 // ------------------------------------------------------------ solve
 namespace {
 
+// The sum over the processes of a row-block solve (ski_solve_rowblock), or
+// none for a whole A.
+struct ShardHook {
+  ski_allreduce_fn fn;
+  void* ctx;
+  ski_status sum(void* buf, int64_t count, int32_t dtype, cudaStream_t st) const {
+    return fn(buf, count, dtype, ctx, (void*)st);
+  }
+};
+
 struct SolvePlan {
   int64_t n, d, m, ncols, ld_sa, ldq_sa;
+  const ShardHook* sh;  // row-block form: partial sums are summed over the processes
   int64_t dl;        // unknowns of Steps 3-5: d, or p after the column-pivoted QR
   bool pivoted;      // Step 2 took the column-pivoted QR (rank-revealing form)
   int32_t* piv;      // [d] the column of A at each pivoted position (p used)
@@ -470,7 +483,7 @@ size_t plan_solve(const ski_matrix* A, const ski_opts* o, char* base, size_t cap
   P->y = ar.take<double>(d);
   P->z = ar.take<double>(d);
   P->p = ar.take<double>(d);
-  P->q = ar.take<double>(d);
+  P->q = ar.take<double>(d + 2);  // + ||t||^2, ||A||_F^2 of the row-block form
   P->part = ar.take<double>((int64_t)P->nblk * d);
   P->part_tt = ar.take<double>(P->nblk);
   P->part_aa = ar.take<double>(P->nblk);
@@ -612,11 +625,18 @@ ski_status residual_pass(const ski_matrix* A, const double* b, const double* x, 
   f.nblk = P.nblk;
   f.sc = nullptr;
   SKI_TRY(ski_fused_launch(f, st));
+  const int shard = P.sh ? 1 : 0;
   if (P.csr) {
     SKI_TRY(ski_csc_launch(P.d, P.colptr, P.rowidx, P.cval, P.t, P.q, nullptr, st));
-    SKI_TRY(ski_reduce_launch(P.nblk, P.d, nullptr, P.d, P.part_tt, want_aa ? P.part_aa : nullptr, P.q, P.sc, 2, st));
+    SKI_TRY(ski_reduce_launch(P.nblk, P.d, nullptr, P.d, P.part_tt, want_aa ? P.part_aa : nullptr, P.q, P.sc, 2, st,
+                              shard));
   } else {
-    SKI_TRY(ski_reduce_launch(P.nblk, P.d, P.part, P.d, P.part_tt, want_aa ? P.part_aa : nullptr, P.q, P.sc, 2, st));
+    SKI_TRY(ski_reduce_launch(P.nblk, P.d, P.part, P.d, P.part_tt, want_aa ? P.part_aa : nullptr, P.q, P.sc, 2, st,
+                              shard));
+  }
+  if (P.sh) {  // A^T r, ||r||^2, ||A||_F^2 of the whole A
+    SKI_TRY(P.sh->sum(P.q, P.d + 2, SKI_F64, st));
+    SKI_TRY(ski_finish_shard_launch(P.q, P.d, P.sc, 2, want_aa ? 1 : 0, st));
   }
   return SKI_OK;
 }
@@ -640,7 +660,7 @@ ski_status lsqr_iteration(const ski_matrix* A, SolvePlan& P, cudaStream_t st) {
     f.sc = P.sc;
     SKI_TRY(ski_fused_launch(f, st));
     SKI_TRY(ski_csc_launch(P.d, P.colptr, P.rowidx, P.cval, P.t, P.q, P.sc, st));
-    SKI_TRY(ski_reduce_par_launch(P.nblk, P.d, nullptr, P.part_tt, P.q, P.sc, st));
+    SKI_TRY(ski_reduce_par_launch(P.nblk, P.d, nullptr, P.part_tt, P.q, P.sc, st, P.sh ? 1 : 0));
   } else {
     DfArgs f{};
     f.A2 = P.A2;
@@ -657,7 +677,11 @@ ski_status lsqr_iteration(const ski_matrix* A, SolvePlan& P, cudaStream_t st) {
     f.sc = P.sc;
     f.variant = P.lsqr_pass;
     SKI_TRY(ski_fused_df_launch(f, st));
-    SKI_TRY(ski_reduce_par_launch(P.nblk, P.dl, P.part, P.part_tt, P.q, P.sc, st));
+    SKI_TRY(ski_reduce_par_launch(P.nblk, P.dl, P.part, P.part_tt, P.q, P.sc, st, P.sh ? 1 : 0));
+  }
+  if (P.sh) {  // q = A^T t and ||t||^2 of the whole A
+    SKI_TRY(P.sh->sum(P.q, P.dl + 1, SKI_F64, st));
+    SKI_TRY(ski_finish_shard_launch(P.q, P.dl, P.sc, 0, 0, st));
   }
   SKI_TRY(ski_trmv_lower_vp_launch(P.dl, P.Mt, P.q, P.v, P.vp, P.part_vv, P.sc, 0, st));
   SKI_TRY(ski_trmv_upper_update_launch(P.dl, P.M, P.vp, P.part_vv, P.v, P.w, P.y, P.z, P.sc, 0, st));
@@ -678,8 +702,8 @@ extern "C" size_t ski_solve_workspace_size(const ski_matrix* A, const ski_opts* 
   return plan_solve(A, o, nullptr, 0, &P);
 }
 
-extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_opts* o, double* x, double* R_out,
-                                ski_info* info, void* ws, size_t ws_bytes, void* stream) {
+static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opts* o, double* x, double* R_out,
+                             ski_info* info, void* ws, size_t ws_bytes, void* stream, const ShardHook* sh) {
   if (info) {
     memset(info, 0, sizeof(*info));
     info->status = SKI_EINVAL;
@@ -687,7 +711,9 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   SKI_TRY(check_matrix(A));
   SKI_TRY(check_sketch_opts(A, o));
   if (!b || !x) return SKI_EINVAL;
-  if (o->m < A->d || A->n < A->d) return SKI_EINVAL;
+  if (!sh && o->row_offset != 0) return SKI_EINVAL;  // a solve of a whole A
+  if (sh && o->premix) return SKI_EINVAL;             // H D mixes every row: no row block premixes alone
+  if (o->m < A->d || (!sh && A->n < A->d)) return SKI_EINVAL;
   if (o->qr_dtype != SKI_F64 && o->qr_dtype != SKI_F32 && o->qr_dtype != SKI_TF32) return SKI_EINVAL;
   if (A->kind == SKI_DENSE && A->d > SKI_DENSE_DMAX) return SKI_EINVAL;
   if (o->it_max < 0) return SKI_EINVAL;
@@ -698,6 +724,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
     return SKI_ENOMEM;
   }
   plan_solve(A, o, (char*)ws, ws_bytes, &P);
+  P.sh = sh;
   cudaStream_t st = ski_stream(stream);
   Events ev;
   if (!ev.ok) return SKI_ECUDA;
@@ -733,8 +760,9 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
     if (!fe.ok) return SKI_ECUDA;
     SKI_CUDA_TRY(cudaMemsetAsync(P.perr, 0, sizeof(int), st));
     SKI_CUDA_TRY(cudaEventRecord(fe.e[0], st));
-    // Step 1: sketch [SA | Sb]
+    // Step 1: sketch [SA | Sb] (a row block's partial sketch, summed over the processes)
     SKI_TRY(sketch_run(A, b, of, P.SA, P.ld_sa, P.stage, P.stage_bytes, st, fe.e[5], fe.e[6], P.perr));
+    if (P.sh) SKI_TRY(P.sh->sum(P.SA, P.m * P.ld_sa, of->sketch_dtype, st));
     SKI_CUDA_TRY(cudaEventRecord(fe.e[1], st));
     // Step 2: QR of [SA | Sb] in qr_dtype
     if (P.SAq != P.SA) {
@@ -911,7 +939,7 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
   }
   int64_t iters_total = 0;
   int restarts = 0;
-  ChunkGraph lsqr_graph(o->graphs == 1);
+  ChunkGraph lsqr_graph(o->graphs == 1 && !sh);  // the row-block sums are host calls: no capture
   double metric = 0.0, lsqr_test = 0.0;
   bool early = false;
   if (sqrt(hs.rnorm2) <= o->tau_a) {
@@ -1053,6 +1081,19 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
     info->status = result;
   }
   return result;
+}
+
+extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_opts* o, double* x, double* R_out,
+                                ski_info* info, void* ws, size_t ws_bytes, void* stream) {
+  return solve_impl(A, b, o, x, R_out, info, ws, ws_bytes, stream, nullptr);
+}
+
+extern "C" ski_status ski_solve_rowblock(const ski_matrix* A, const double* b, const ski_opts* o, double* x,
+                                         double* R_out, ski_info* info, void* ws, size_t ws_bytes, void* stream,
+                                         ski_allreduce_fn allreduce, void* ctx) {
+  if (!allreduce) return SKI_EINVAL;
+  ShardHook h{allreduce, ctx};
+  return solve_impl(A, b, o, x, R_out, info, ws, ws_bytes, stream, &h);
 }
 
 // ------------------------------------------------------------ adjoint

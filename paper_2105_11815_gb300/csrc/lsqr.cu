@@ -282,15 +282,29 @@ __global__ void __launch_bounds__(256) k_csc_cols(int64_t d, const int64_t* __re
 
 // q[c] = sum over CTAs of part[blk][c]; CTA 0 also reduces ||t||^2 (and
 // ||A||_F^2) into the scalars.
+// shard: the row-block form -- ||r||^2 and ||A||_F^2 go to q[d] and q[d+1]
+// as this process's partial sums (k_finish_shard derives the scalars after
+// the sum over the processes).
 __global__ void k_reduce_cols(int nblk, int64_t d, const double* __restrict__ part, int64_t ldp,
                               const double* __restrict__ part_tt, const double* __restrict__ part_aa,
-                              double* __restrict__ q, LsqrScalars* __restrict__ sc, int mode) {
+                              double* __restrict__ q, LsqrScalars* __restrict__ sc, int mode, int shard) {
   if (sc->flag_a && mode == 0) return;
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (part && c < d) {
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * ldp + c];
     q[c] = s;
+  }
+  if (shard) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      double s = 0.0, a = 0.0;
+      for (int b = 0; b < nblk; ++b) s += part_tt[b];
+      if (part_aa)
+        for (int b = 0; b < nblk; ++b) a += part_aa[b];
+      q[d] = s;
+      q[d + 1] = a;
+    }
+    return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     double s = 0.0;
@@ -448,9 +462,10 @@ ski_status ski_csc_launch(int64_t d, const int64_t* colptr, const int32_t* rowid
 }
 
 ski_status ski_reduce_launch(int nblk, int64_t d, const double* part, int64_t ldp, const double* part_tt,
-                             const double* part_aa, double* q, LsqrScalars* sc, int mode, cudaStream_t st) {
+                             const double* part_aa, double* q, LsqrScalars* sc, int mode, cudaStream_t st,
+                             int shard) {
   k_reduce_cols<<<(unsigned)std::max<int64_t>(1, ski_cdiv(d, 256)), 256, 0, st>>>(nblk, d, part, ldp, part_tt, part_aa, q,
-                                                                            sc, mode);
+                                                                            sc, mode, shard);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }

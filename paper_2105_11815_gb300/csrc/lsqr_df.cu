@@ -497,9 +497,12 @@ __global__ void __launch_bounds__(512, 1) k_fused_df_rows(DfArgs f) {
 
 // K3: q[c] = sum_b part[b][c] (8 warps share the CTAs, fixed order), beta;
 // CTA 0 also copies flag_a to flag_b for the next K1 (also once stopped).
+// shard: the row-block form -- q and ||t||^2 (in q[d]) are this process's
+// partial sums, to be summed over the processes before k_finish_shard
+// derives the scalars; a finished iteration (flag_a) contributes zeros.
 __global__ void __launch_bounds__(256) k_reduce_par(int nblk, int64_t d, const double* __restrict__ part,
                                                     const double* __restrict__ part_tt, double* __restrict__ q,
-                                                    LsqrScalars* __restrict__ sc) {
+                                                    LsqrScalars* __restrict__ sc, int shard) {
   __shared__ double sh[8][33];
   const bool skip = sc && flag_set(&sc->flag_a);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -516,6 +519,20 @@ __global__ void __launch_bounds__(256) k_reduce_par(int nblk, int64_t d, const d
       for (int w = 0; w < 8; ++w) t += sh[w][lane];
       if (part && c < d) q[c] = t;
     }
+  } else if (shard && part) {
+    const int64_t c = (int64_t)blockIdx.x * 32 + lane;
+    if (wid == 0 && c < d) q[c] = 0.0;
+  }
+  if (shard) {
+    if (blockIdx.x == 0 && wid == 1) {
+      double t = 0.0;
+      if (!skip) {
+        for (int b = lane; b < nblk; b += 32) t += part_tt[b];
+        t = ski_warp_sum(t);
+      }
+      if (lane == 0) q[d] = t;
+    }
+    return;
   }
   if (blockIdx.x == 0 && wid == 1 && sc) {
     double t = 0.0;
@@ -758,8 +775,41 @@ ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
 }
 
 ski_status ski_reduce_par_launch(int nblk, int64_t d, const double* part, const double* part_tt, double* q,
-                                 LsqrScalars* sc, cudaStream_t st) {
-  k_reduce_par<<<(unsigned)std::max<int64_t>(1, ski_cdiv(d, 32)), 256, 0, st>>>(nblk, d, part, part_tt, q, sc);
+                                 LsqrScalars* sc, cudaStream_t st, int shard) {
+  k_reduce_par<<<(unsigned)std::max<int64_t>(1, ski_cdiv(d, 32)), 256, 0, st>>>(nblk, d, part, part_tt, q, sc, shard);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+namespace {
+// After the sum over the processes of a row-block form's partials q[0..d),
+// q[d] = ||t||^2 (and q[d+1] = ||A||_F^2 of a residual pass): the scalars
+// k_reduce_par (mode 0) or k_reduce_cols (mode 2) derive from them.
+__global__ void k_finish_shard(const double* __restrict__ q, int64_t d, LsqrScalars* __restrict__ sc, int mode,
+                               int want_aa) {
+  if (threadIdx.x != 0) return;
+  if (mode == 0) {
+    if (!flag_set(&sc->flag_a)) {
+      sc->beta_new = sqrt(q[d]);
+      sc->rnorm2 = q[d];
+    }
+    sc->flag_b = sc->flag_a;
+    sc->r_alpha = sc->alpha;
+    sc->r_rhobar = sc->rhobar;
+    sc->r_phibar = sc->phibar;
+    sc->r_anorm2 = sc->anorm2;
+    sc->r_iters = sc->iters;
+  } else {
+    sc->beta_new = sqrt(q[d]);
+    sc->rnorm2 = q[d];
+    if (want_aa) sc->anorm_f2 = q[d + 1];
+  }
+}
+}  // namespace
+
+ski_status ski_finish_shard_launch(const double* q, int64_t d, LsqrScalars* sc, int mode, int want_aa,
+                                   cudaStream_t st) {
+  k_finish_shard<<<1, 32, 0, st>>>(q, d, sc, mode, want_aa);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }

@@ -76,8 +76,14 @@ ski_status ski_split_a_launch(int64_t n, int64_t d, const double* A, int64_t lda
 bool ski_df_supported(int64_t d);
 int64_t ski_a2_ld(int64_t d);
 ski_status ski_fused_df_launch(const DfArgs& f, cudaStream_t st);
+// shard = 1: the row-block form (q and q[d] = ||t||^2 are partial sums; see
+// ski_finish_shard_launch)
 ski_status ski_reduce_par_launch(int nblk, int64_t d, const double* part, const double* part_tt, double* q,
-                                 LsqrScalars* sc, cudaStream_t st);
+                                 LsqrScalars* sc, cudaStream_t st, int shard = 0);
+// After q[0..d] (and q[d+1]) were summed over the processes of a row-block
+// solve: the scalars of an LSQR step (mode 0) or of a residual pass (mode 2)
+ski_status ski_finish_shard_launch(const double* q, int64_t d, LsqrScalars* sc, int mode, int want_aa,
+                                   cudaStream_t st);
 int ski_vv_blocks(int64_t d);
 ski_status ski_trmv_lower_vp_launch(int64_t d, const double* Mt, const double* q, const double* v, double* vp,
                                     double* part_vv, LsqrScalars* sc, int start, cudaStream_t st);
@@ -92,7 +98,8 @@ ski_status ski_trmv_launch(bool upper, int64_t d, const double* M, int64_t ldm, 
 ski_status ski_csc_launch(int64_t d, const int64_t* colptr, const int32_t* rowidx, const double* cval,
                           const double* t, double* q, const LsqrScalars* sc, cudaStream_t st);
 ski_status ski_reduce_launch(int nblk, int64_t d, const double* part, int64_t ldp, const double* part_tt,
-                             const double* part_aa, double* q, LsqrScalars* sc, int mode, cudaStream_t st);
+                             const double* part_aa, double* q, LsqrScalars* sc, int mode, cudaStream_t st,
+                             int shard = 0);
 
 ski_status ski_norm_launch(int64_t d, const double* q, LsqrScalars* sc, cudaStream_t st);
 ski_status ski_copy_launch(int64_t n, const double* a, double* b, cudaStream_t st);

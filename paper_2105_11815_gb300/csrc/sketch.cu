@@ -36,14 +36,15 @@ __global__ void k_premix_signs(uint64_t kd, int64_t n, int8_t* D) {
 
 // Count pass: draw the column, store its (row, sign) pairs, count per bucket.
 template <int SMAX>
-__global__ void k_bucket_count(uint64_t kb, uint64_t ks, int s, uint64_t m, int64_t n, int replace,
+__global__ void k_bucket_count(uint64_t kb, uint64_t ks, int s, uint64_t m, int64_t n, int replace, int64_t row0,
                                int32_t* __restrict__ pair_row, uint8_t* __restrict__ pair_neg,
                                int32_t* __restrict__ counts) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n) return;
   int32_t rows[SMAX];
   int neg[SMAX];
-  ski_column<SMAX>(kb, ks, s, m, (uint64_t)j, replace, rows, neg);
+  // the draw of column row0 + j of S: a row block of a larger A keeps its rows' columns of S
+  ski_column<SMAX>(kb, ks, s, m, (uint64_t)(row0 + j), replace, rows, neg);
   for (int k = 0; k < s; ++k) {
     pair_row[j * s + k] = rows[k];
     pair_neg[j * s + k] = (uint8_t)neg[k];
@@ -643,7 +644,7 @@ size_t ski_bucket_ws_bytes(int64_t nrows, int32_t s, int64_t m) {
 }
 
 ski_status ski_build_buckets(uint64_t seed, int32_t s, int32_t replace, int64_t m, int64_t nrows, SkiArena& ar,
-                             cudaStream_t st, SkiBuckets* out) {
+                             cudaStream_t st, SkiBuckets* out, int64_t row0) {
   int32_t* pair_row = ar.take<int32_t>(nrows * s);
   uint8_t* pair_neg = ar.take<uint8_t>(nrows * s);
   int32_t* counts = ar.take<int32_t>(m);
@@ -658,9 +659,11 @@ ski_status ski_build_buckets(uint64_t seed, int32_t s, int32_t replace, int64_t 
   const int T = 256;
   if (nrows > 0) {
     if (s <= 4)
-      k_bucket_count<4><<<ski_cdiv(nrows, T), T, 0, st>>>(kb, ks, s, m, nrows, replace, pair_row, pair_neg, counts);
+      k_bucket_count<4><<<ski_cdiv(nrows, T), T, 0, st>>>(kb, ks, s, m, nrows, replace, row0, pair_row, pair_neg,
+                                                           counts);
     else
-      k_bucket_count<64><<<ski_cdiv(nrows, T), T, 0, st>>>(kb, ks, s, m, nrows, replace, pair_row, pair_neg, counts);
+      k_bucket_count<64><<<ski_cdiv(nrows, T), T, 0, st>>>(kb, ks, s, m, nrows, replace, row0, pair_row, pair_neg,
+                                                            counts);
     SKI_LAUNCH_CHECK();
   }
   k_scan_counts<<<1, 1024, 0, st>>>(counts, m, offsets);

@@ -20,8 +20,10 @@ __device__ __forceinline__ double fx_scaled(const FxAcc& a, long long c, int e) 
 
 // ---- sketch.cu
 size_t ski_bucket_ws_bytes(int64_t nrows, int32_t s, int64_t m);
+// row0: the global index of the first of the nrows rows (a row block of a
+// larger A draws its rows' columns of S)
 ski_status ski_build_buckets(uint64_t seed, int32_t s, int32_t replace, int64_t m, int64_t nrows, SkiArena& ar,
-                             cudaStream_t st, SkiBuckets* out);
+                             cudaStream_t st, SkiBuckets* out, int64_t row0 = 0);
 ski_status ski_gather_dense(const double* A, int64_t lda, int64_t nrows, int64_t d, const double* b,
                             const SkiBuckets& bk, double scale, int32_t out_dtype, void* SA, int64_t ld_sa,
                             cudaStream_t st);

@@ -25,6 +25,7 @@ def lib():
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"typedef[^;]*;", "", text)  # types (the all-reduce callback), not entry points
     return sorted(set(re.findall(r"\b(ski_[a-z0-9_]+)\s*\(", text)))
 
 
