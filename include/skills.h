@@ -330,10 +330,11 @@ ski_status ski_trinv(int64_t d, const double* R, int64_t ldr, double* M, double*
  * o->factorization = 1 and a sketch that fails the rank rule, Step 2 takes the
  * column-pivoted QR: info->pivoted = 1, info->rank = p, and x is zero outside
  * the p pivoted columns (the basic solution of Theorem 8).  With o->tol > 0
- * the acceptance metric ||A^T r|| / (||A||_F ||r||) is formed from r = b - A x
- * by compensated (twice-working-precision) dot products, so that it certifies
- * x even where the plain FP64 residual would be rounding noise at the level of
- * tol.  Synchronous.  Returns SKI_ESINGULAR when R fails the rank rule with
+ * the acceptance metric ||A^T r|| / (||A||_F ||r||) is formed from the plain
+ * FP64 r = b - A x, and again from r by compensated (twice-working-precision)
+ * dot products whenever the plain value's estimated rounding noise could
+ * decide the test (x large along small singular directions), so that it
+ * certifies x.  Synchronous.  Returns SKI_ESINGULAR when R fails the rank rule with
  * o->perturb = 0 and o->factorization = 0, SKI_ENOCONV when it_max is reached
  * before the tolerances (x then holds the last iterate), SKI_ENONFINITE on
  * NaN/Inf.

@@ -470,6 +470,30 @@ ski_status ski_reduce_launch(int nblk, int64_t d, const double* part, int64_t ld
   return SKI_OK;
 }
 
+namespace {
+__global__ void __launch_bounds__(1024) k_norm2(int64_t d, const double* __restrict__ q, const double* __restrict__ x,
+                                                LsqrScalars* __restrict__ sc) {
+  __shared__ double sh[32];
+  double s = 0.0, t = 0.0;
+  for (int64_t c = threadIdx.x; c < d; c += blockDim.x) {
+    s = fma(q[c], q[c], s);
+    if (x) t = fma(x[c], x[c], t);
+  }
+  s = block_sum(s, sh);
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) {
+    sc->atr_norm = sqrt(s);
+    if (x) sc->xnorm = sqrt(t);
+  }
+}
+}  // namespace
+
+ski_status ski_norm2_launch(int64_t d, const double* q, const double* x, LsqrScalars* sc, cudaStream_t st) {
+  k_norm2<<<1, 1024, 0, st>>>(d, q, x, sc);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
 ski_status ski_norm_launch(int64_t d, const double* q, LsqrScalars* sc, cudaStream_t st) {
   k_norm<<<1, 1024, 0, st>>>(d, q, sc);
   SKI_LAUNCH_CHECK();

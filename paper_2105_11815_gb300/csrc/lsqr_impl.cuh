@@ -20,6 +20,7 @@ struct LsqrScalars {
   // CTA 0 of K1 can write the new state while its other CTAs still read the old
   double r_alpha, r_rhobar, r_phibar, r_anorm2;
   long long r_iters;
+  double xnorm;  // ||x|| of the last acceptance check (its rounding-noise estimate)
 };
 
 struct FusedArgs {
@@ -82,6 +83,8 @@ ski_status ski_reduce_par_launch(int nblk, int64_t d, const double* part, const 
                                  LsqrScalars* sc, cudaStream_t st, int shard = 0);
 // After q[0..d] (and q[d+1]) were summed over the processes of a row-block
 // solve: the scalars of an LSQR step (mode 0) or of a residual pass (mode 2)
+// ||q|| into sc->atr_norm and, when x is given, ||x|| into sc->xnorm (one launch)
+ski_status ski_norm2_launch(int64_t d, const double* q, const double* x, LsqrScalars* sc, cudaStream_t st);
 ski_status ski_finish_shard_launch(const double* q, int64_t d, LsqrScalars* sc, int mode, int want_aa,
                                    cudaStream_t st);
 int ski_vv_blocks(int64_t d);

@@ -330,55 +330,89 @@ __device__ __forceinline__ void cl_gram(int nrows, F val, float* Gp, float* G,
   cl.sync();  // every CTA has read every partial: Gp is free again
 }
 
+// The 32 x 32 factorisations below use the whole CTA (1024 threads; thread
+// (i, j) = (threadIdx.x / 32, threadIdx.x % 32)) with two barriers per
+// elimination step, or one warp per column for the triangular inverses:
+// they are on the panel's critical path.
+
 // R (upper, w x w) = chol(D A D) D^{-1}, D = diag(A)^{-1/2}; A is destroyed.
-// One warp, lane = column.  False when a scaled pivot is below 2^-24 or not finite.
-__device__ __forceinline__ bool warp_chol(float* A, float* R, int w) {
-  const int lane = threadIdx.x & 31;
-  float dsc = 1.f;
-  bool ok = true;
-  if (lane < w) {
-    const float a = A[lane * HM + lane];
-    ok = a > 0.f && isfinite(a);
-    dsc = ok ? rsqrtf(a) : 1.f;
+// False (the same in every thread) when a scaled pivot is below 2^-24 or not
+// finite.  Dv: [NB] scratch.
+__device__ __forceinline__ bool cta_chol(float* A, float* R, float* Dv, int w) {
+  const int i = threadIdx.x >> 5, j = threadIdx.x & 31;
+  if (i == 0) {
+    const float a = j < w ? A[j * HM + j] : 1.f;
+    Dv[j] = (a > 0.f && isfinite(a)) ? rsqrtf(a) : 0.f;
   }
-  if (!__all_sync(0xffffffffu, ok)) return false;
+  __syncthreads();
+  for (int k = 0; k < w; ++k)
+    if (!(Dv[k] > 0.f)) return false;  // uniform: every thread reads the same Dv
+  if (i < w && j < w) A[i * HM + j] *= Dv[i] * Dv[j];
+  R[i * HM + j] = 0.f;
+  __syncthreads();
   for (int k = 0; k < w; ++k) {
-    const float dk = __shfl_sync(0xffffffffu, dsc, k);
-    if (lane < w) A[k * HM + lane] *= dk * dsc;
+    const float piv = A[k * HM + k];
+    if (!(piv > 0x1p-24f) || !isfinite(piv)) return false;  // uniform
+    const float rkk = sqrtf(piv);
+    if (i == k && j >= k && j < w) R[k * HM + j] = j == k ? rkk : A[k * HM + j] / rkk;
+    __syncthreads();
+    if (i > k && i < w && j >= i && j < w) A[i * HM + j] -= R[k * HM + i] * R[k * HM + j];
+    __syncthreads();
   }
-  __syncwarp();
-  for (int j = 0; j < w; ++j) {
-    const float piv = A[j * HM + j];
-    if (!(piv > 0x1p-24f) || !isfinite(piv)) return false;  // uniform: every lane read the same value
-    const float rjj = sqrtf(piv);
-    const float rji = lane == j ? rjj : (lane > j && lane < w ? A[j * HM + lane] / rjj : 0.f);
-    if (lane < NB) R[j * HM + lane] = rji;
-    __syncwarp();
-    if (lane > j && lane < w)
-      for (int k = j + 1; k <= lane; ++k) A[k * HM + lane] -= R[j * HM + k] * rji;
-    __syncwarp();
-  }
-  if (lane < w)
-    for (int j = 0; j <= lane; ++j) R[j * HM + lane] /= dsc;
-  __syncwarp();
+  if (i < w && j < w && i <= j) R[i * HM + j] /= Dv[j];
+  __syncthreads();
   return true;
 }
 
-// X = U^{-1} for upper triangular U (w x w); lane = column.
-__device__ __forceinline__ void warp_upper_inv(const float* U, float* X, int w) {
-  const int lane = threadIdx.x & 31;
-  if (lane < w) {
-    for (int k = w - 1; k >= 0; --k) {
-      float x = 0.f;
-      if (k <= lane) {
-        float s = k == lane ? 1.f : 0.f;
-        for (int l = k + 1; l <= lane; ++l) s = fmaf(-U[k * HM + l], X[l * HM + lane], s);
-        x = s / U[k * HM + k];
+// X = U^{-1} for upper triangular U (w x w): warp c forms column c by back
+// substitution, the inner sums as warp reductions.
+__device__ __forceinline__ void cta_upper_inv(const float* U, float* X, int w) {
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (c < NB) {
+    float x = 0.f;  // lane l holds X[l][c]
+    if (c < w)
+      for (int k = c; k >= 0; --k) {
+        const float s = ski_warp_sumf(lane > k && lane <= c ? U[k * HM + lane] * x : 0.f);
+        if (lane == k) x = ((k == c ? 1.f : 0.f) - s) / U[k * HM + k];
       }
-      X[k * HM + lane] = x;
-    }
+    X[lane * HM + c] = x;
   }
-  __syncwarp();
+  __syncthreads();
+}
+
+// X = L^{-1} for unit lower triangular L (w x w), warp c forming column c.
+__device__ __forceinline__ void cta_unit_lower_inv(const float* L, float* X, int w) {
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (c < NB) {
+    float x = lane == c ? 1.f : 0.f;  // lane l holds X[l][c]
+    if (c < w)
+      for (int k = c + 1; k < w; ++k) {
+        const float s = ski_warp_sumf(lane >= c && lane < k ? L[k * HM + lane] * x : 0.f);
+        if (lane == k) x = -s;
+      }
+    X[lane * HM + c] = x;
+  }
+  __syncthreads();
+}
+
+// LU without pivoting of Q - S (Q: the top w x w block, destroyed), s_k = -sign
+// of the k-th pivot, so |pivot| >= 1: L1 unit lower, U upper, S the signs.
+__device__ __forceinline__ void cta_mod_lu(float* Q, float* L1, float* U, float* S, int w) {
+  const int i = threadIdx.x >> 5, j = threadIdx.x & 31;
+  L1[i * HM + j] = i == j ? 1.f : 0.f;
+  U[i * HM + j] = 0.f;
+  __syncthreads();
+  for (int k = 0; k < w; ++k) {
+    const float akk = Q[k * HM + k];
+    const float sk = akk >= 0.f ? -1.f : 1.f;
+    const float piv = akk - sk;
+    if (i == k && j >= k && j < w) U[k * HM + j] = j == k ? piv : Q[k * HM + j];
+    if (j == k && i > k && i < w) L1[i * HM + k] = Q[i * HM + k] / piv;
+    if (i == k && j == k) S[k] = sk;
+    __syncthreads();
+    if (i > k && i < w && j > k && j < w) Q[i * HM + j] -= L1[i * HM + k] * U[k * HM + j];
+    __syncthreads();
+  }
 }
 
 // Rows [0, nrows) of the slab times an upper triangular X from the right.
@@ -415,7 +449,6 @@ __global__ void __launch_bounds__(32 * NW) k_panel_chol(PanelArgs<float> a, floa
   float* Ts = L1i + NB * HM;
   float* S = Ts + NB * HM;                           // [NB] signs
   float* slab = S + NB;
-  __shared__ int s_ok;
   const int rank = (int)cl.block_rank();
   const int64_t r0 = (int64_t)rank * a.rows_per;
   const int64_t r1 = min(a.mr, r0 + a.rows_per);
@@ -430,24 +463,14 @@ __global__ void __launch_bounds__(32 * NW) k_panel_chol(PanelArgs<float> a, floa
   auto plain = [&](int r, int c) { return slab[r * HM + c]; };
   // (1) CholeskyQR2
   cl_gram(nrows, plain, Gp, G, cl);
-  if (warp == 0) {
-    const bool ok = warp_chol(G, R1, w);
-    if (ok) warp_upper_inv(R1, X, w);
-    if (lane == 0) s_ok = ok ? 1 : 0;
-  }
-  __syncthreads();
-  bool ok = s_ok != 0;
+  bool ok = cta_chol(G, R1, S, w);
   if (ok) {
+    cta_upper_inv(R1, X, w);
     rows_times_upper<NW>(slab, nrows, X, w);  // Q1 = P R1^{-1}
     __syncthreads();
     cl_gram(nrows, plain, Gp, G, cl);
-    if (warp == 0) {
-      const bool ok2 = warp_chol(G, R2, w);
-      if (ok2) warp_upper_inv(R2, X, w);
-      if (lane == 0) s_ok = ok2 ? 1 : 0;
-    }
-    __syncthreads();
-    ok = s_ok != 0;
+    ok = cta_chol(G, R2, S, w);
+    if (ok) cta_upper_inv(R2, X, w);
     if (!ok) {
       rows_times_upper<NW>(slab, nrows, R1, w);  // restore P = Q1 R1 for the fallback
       __syncthreads();
@@ -469,49 +492,9 @@ __global__ void __launch_bounds__(32 * NW) k_panel_chol(PanelArgs<float> a, floa
       Qt[i2 * HM + j2] = j2 < w ? *src : 0.f;
     }
     cl.sync();  // all have read the top rows: the slabs may change
-    if (warp == 0) {
-      // modified LU of Qt - S (no pivoting; s_i = -sign of the i-th pivot)
-      for (int k = 0; k < NB; ++k) {
-        L1[k * HM + lane] = (k == lane) ? 1.f : 0.f;
-        U[k * HM + lane] = 0.f;
-      }
-      __syncwarp();
-      for (int i = 0; i < w; ++i) {
-        const float aii = Qt[i * HM + i];
-        const float si = aii >= 0.f ? -1.f : 1.f;
-        __syncwarp();
-        if (lane == 0) {
-          Qt[i * HM + i] = aii - si;
-          S[i] = si;
-        }
-        __syncwarp();
-        const float piv = Qt[i * HM + i];
-        if (lane > i && lane < w) L1[lane * HM + i] = Qt[lane * HM + i] / piv;
-        if (lane >= i && lane < w) U[i * HM + lane] = Qt[i * HM + lane];
-        __syncwarp();
-        if (lane > i && lane < w) {
-          const float uic = U[i * HM + lane];
-          for (int k = i + 1; k < w; ++k) Qt[k * HM + lane] -= L1[k * HM + i] * uic;
-        }
-        __syncwarp();
-      }
-      warp_upper_inv(U, X, w);  // X = U^{-1}
-      // L1i = L1^{-1} (unit lower): lane = column
-      if (lane < w) {
-        for (int k = 0; k < w; ++k) {
-          float x = 0.f;
-          if (k == lane) x = 1.f;
-          else if (k > lane) {
-            float s = 0.f;
-            for (int l = lane; l < k; ++l) s = fmaf(-L1[k * HM + l], L1i[l * HM + lane], s);
-            x = s;
-          }
-          L1i[k * HM + lane] = x;
-        }
-      }
-      __syncwarp();
-    }
-    __syncthreads();
+    cta_mod_lu(Qt, L1, U, S, w);
+    cta_upper_inv(U, X, w);       // X = U^{-1}
+    cta_unit_lower_inv(L1, L1i, w);
     // T = -U S L1^{-T}: T[i][j] = -sum_{k=i..j} U[i][k] s_k L1i[j][k]
     {
       float t = 0.f;

@@ -161,9 +161,12 @@ def dense_high_coherence_torch(n, d, seed, device, big=1e3, small_sd=1e-3):
     return A, torch.ones(n, dtype=torch.float64, device=device)
 
 
-def usv_torch(n, d, kappa, seed, device):
+def usv_torch(n, d, kappa, seed, device, rhs="ones"):
     """A = U diag(sigma) V^T with Haar U (n x d), V (d x d) (QR of a Gaussian,
-    diag(R) made positive), sigma_i = kappa^{-(i-1)/(d-1)}; b = ones."""
+    diag(R) made positive), sigma_i = kappa^{-(i-1)/(d-1)}.
+    rhs="ones": b = ones.  rhs="perp": b = A x_true + e with x_true ~ N(0, 1)
+    and e orthogonal to range(A) (e = g - U U^T g, g ~ N(0, 1)) scaled to
+    ||e|| = ||A x_true||: the solution is x_true, O(1), whatever kappa."""
     import torch
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
@@ -177,10 +180,18 @@ def usv_torch(n, d, kappa, seed, device):
 
     U = haar_t(n, d)
     V = haar_t(d, d)
+    e = None
+    if rhs == "perp":
+        e = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+        e -= U @ (U.T @ e)
     sig = kappa ** (-torch.arange(d, dtype=torch.float64, device=device) / max(d - 1, 1))
     U *= sig[None, :]
     A = U @ V.T
     del U
+    if rhs == "perp":
+        xt = torch.randn(d, generator=g, device=device, dtype=torch.float64)
+        ax = A @ xt
+        return A, ax + e * (torch.linalg.norm(ax) / torch.linalg.norm(e))
     return A, torch.ones(n, dtype=torch.float64, device=device)
 
 

@@ -36,9 +36,17 @@ def _check_against_oracle(A, b, x, info, oinfo):
     S = np.array(sorted(support))
     xS = np.linalg.lstsq(A[:, S], b, rcond=None)[0]
     assert rel_fro(x[S], xS) <= 1e-8
-    r_ls = np.linalg.norm(b - A @ (np.linalg.pinv(A) @ b))
-    assert np.linalg.norm(b - A @ x) == pytest.approx(r_ls, rel=1e-10)
+    assert np.linalg.norm(b - A @ x) == pytest.approx(_ls_residual(A, b, p), rel=1e-10)
     assert olsqr.residual_metric(A, b, x) <= 1e-10
+
+
+def _ls_residual(A, b, p):
+    """||b - U_p U_p^T b||, U_p the leading p left singular vectors of A: the
+    least-squares residual of a rank-p A (a pseudo-inverse at its default
+    cutoff keeps rounding-level singular values of a product G1 G2 and misses
+    it by up to 4e-3 here)."""
+    U = np.linalg.svd(A, full_matrices=False)[0][:, :p]
+    return np.linalg.norm(b - U @ (U.T @ b))
 
 
 @pytest.mark.parametrize("n,d,r,m,s,premix", [(3000, 60, 40, 150, 1, 0), (5000, 120, 77, 300, 2, 0),
@@ -86,8 +94,7 @@ def test_zero_and_repeated_columns():
     assert len(S) == 28 and 5 not in S and ((2 in S) != (9 in S))
     xS = np.linalg.lstsq(A[:, S], b, rcond=None)[0]
     assert rel_fro(x[S], xS) <= 1e-8
-    r_ls = np.linalg.norm(b - A @ (np.linalg.pinv(A) @ b))
-    assert np.linalg.norm(b - A @ x) == pytest.approx(r_ls, rel=1e-10)
+    assert np.linalg.norm(b - A @ x) == pytest.approx(_ls_residual(A, b, 28), rel=1e-10)
     assert olsqr.residual_metric(A, b, x) <= 1e-10
 
 
