@@ -4,7 +4,8 @@ The library exposes, as ``ski_opts`` fields, the parameters that change how
 Steps 4-5 and the batched entry point run but not what they compute:
 
 - ``lsqr_pass``: which kernel runs the dense LSQR pass. 1 is register-blocked
-  rows, 2 a TMA-staged row ring, 3 one row per warp.
+  rows, 2 a TMA-staged row ring, 3 one row per warp, 4 register-blocked rows
+  with twice the rows between the two barriers of a row group.
 - ``lsqr_ctas``: its row tiles, i.e. the number of CTAs. 0 is the library
   default.
 - ``graphs``: replay each chunk of iterations as a CUDA graph (1) or launch
@@ -34,7 +35,7 @@ import numpy as np
 
 # Candidate values per field, the default first.
 SPACE_BATCHED = {
-    "lsqr_pass": (1, 2, 3),
+    "lsqr_pass": (1, 2, 3, 4),
     "lsqr_ctas": (0, 19, 38, 76, 304, 608),  # few CTAs: passes of different problems share the SMs
     "graphs": (0, 1),
     "streams": (8, 1, 2, 4, 16),

@@ -316,12 +316,32 @@ constexpr int HM = NB + 1;  // row stride of the 32 x 32 work matrices
 
 // G (all CTAs) = sum over the cluster of the w x w Gram of this CTA's rows,
 // with element (r, c) of a row given by val(r, c).  1024 threads: (i, j).
+// Warps 0..7 each take every 8th row: lane j holds the row's entry j and
+// accumulates column j of the Gram from the other entries by shuffles (no
+// shared-memory traffic in the row loop); the 8 warp partials are then summed
+// in a fixed order.  Wg: [8][NB][HM] scratch.
+constexpr int GRAM_WARPS = 8;
 template <class F>
-__device__ __forceinline__ void cl_gram(int nrows, F val, float* Gp, float* G,
+__device__ __forceinline__ void cl_gram(int nrows, F val, float* Wg, float* Gp, float* G,
                                         const cooperative_groups::cluster_group& cl) {
   const int i = threadIdx.x >> 5, j = threadIdx.x & 31;
+  if (i < GRAM_WARPS) {
+    float acc[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc[k] = 0.f;
+    for (int r = i; r < nrows; r += GRAM_WARPS) {
+      const float pj = val(r, j);
+#pragma unroll
+      for (int k = 0; k < NB; ++k) acc[k] = fmaf(__shfl_sync(0xffffffffu, pj, k), pj, acc[k]);
+    }
+    float* wp = Wg + i * NB * HM;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) wp[k * HM + j] = acc[k];
+  }
+  __syncthreads();
   float s = 0.f;
-  for (int r = 0; r < nrows; ++r) s = fmaf(val(r, i), val(r, j), s);
+#pragma unroll
+  for (int q = 0; q < GRAM_WARPS; ++q) s += Wg[q * NB * HM + i * HM + j];
   Gp[i * HM + j] = s;
   cl.sync();
   float g = 0.f;
@@ -415,17 +435,20 @@ __device__ __forceinline__ void cta_mod_lu(float* Q, float* L1, float* U, float*
   }
 }
 
-// Rows [0, nrows) of the slab times an upper triangular X from the right.
+// Rows [0, nrows) of the slab times an upper triangular X from the right;
+// lane j keeps column j of X in registers, so the row loop is shuffles and
+// FMAs only.
 template <int NW>
 __device__ __forceinline__ void rows_times_upper(float* slab, int nrows, const float* X, int w) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float xc[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) xc[i] = (i <= lane && lane < w && i < w) ? X[i * HM + lane] : 0.f;
   for (int r = warp; r < nrows; r += NW) {
     const float p = lane < w ? slab[r * HM + lane] : 0.f;
     float q = 0.f;
-    for (int i = 0; i < w; ++i) {
-      const float pi = __shfl_sync(0xffffffffu, p, i);
-      if (i <= lane && lane < w) q = fmaf(pi, X[i * HM + lane], q);
-    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) q = fmaf(__shfl_sync(0xffffffffu, p, i), xc[i], q);
     if (lane < w) slab[r * HM + lane] = q;
   }
 }
@@ -448,7 +471,8 @@ __global__ void __launch_bounds__(32 * NW) k_panel_chol(PanelArgs<float> a, floa
   float* L1i = U + NB * HM;
   float* Ts = L1i + NB * HM;
   float* S = Ts + NB * HM;                           // [NB] signs
-  float* slab = S + NB;
+  float* Wg = S + NB;                                // [GRAM_WARPS][NB][HM] Gram partials
+  float* slab = Wg + GRAM_WARPS * NB * HM;
   const int rank = (int)cl.block_rank();
   const int64_t r0 = (int64_t)rank * a.rows_per;
   const int64_t r1 = min(a.mr, r0 + a.rows_per);
@@ -462,13 +486,13 @@ __global__ void __launch_bounds__(32 * NW) k_panel_chol(PanelArgs<float> a, floa
   __syncthreads();
   auto plain = [&](int r, int c) { return slab[r * HM + c]; };
   // (1) CholeskyQR2
-  cl_gram(nrows, plain, Gp, G, cl);
+  cl_gram(nrows, plain, Wg, Gp, G, cl);
   bool ok = cta_chol(G, R1, S, w);
   if (ok) {
     cta_upper_inv(R1, X, w);
     rows_times_upper<NW>(slab, nrows, X, w);  // Q1 = P R1^{-1}
     __syncthreads();
-    cl_gram(nrows, plain, Gp, G, cl);
+    cl_gram(nrows, plain, Wg, Gp, G, cl);
     ok = cta_chol(G, R2, S, w);
     if (ok) cta_upper_inv(R2, X, w);
     if (!ok) {
@@ -505,24 +529,22 @@ __global__ void __launch_bounds__(32 * NW) k_panel_chol(PanelArgs<float> a, floa
     // V rows at or below w: Q U^{-1}; rows above come from L1
     rows_times_upper<NW>(slab, nrows, X, w);
     __syncthreads();
-    // outputs: the panel in Ct (S R on and above the diagonal, V below), V, V^T, T
-    for (int lr = warp; lr < nrows; lr += NW) {
-      const int64_t r = r0 + lr;
-      float v = 0.f, ct = 0.f;
-      if (lane < w) {
-        if (r < w) {
-          const int ri = (int)r;
-          v = lane < ri ? L1[ri * HM + lane] : (lane == ri ? 1.f : 0.f);
-          ct = lane >= ri ? S[ri] * R2[ri * HM + lane] : v;
-        } else {
-          v = slab[lr * HM + lane];
-          ct = v;
-        }
-        a.Ct[(int64_t)lane * a.ldt + r] = ct;
+    // outputs: the panel in Ct (S R on and above the diagonal, V below), V
+    // (row-major: a warp per row), and Ct's and V^T's columns (a warp per
+    // column, consecutive rows on consecutive lanes)
+    auto vat = [&](int64_t r, int lr, int c) -> float {
+      if (c >= w) return 0.f;
+      if (r < w) return c < r ? L1[r * HM + c] : (c == r ? 1.f : 0.f);
+      return slab[lr * HM + c];
+    };
+    for (int lr = warp; lr < nrows; lr += NW) a.V[(r0 + lr) * NB + lane] = vat(r0 + lr, lr, lane);
+    for (int c = warp; c < NB; c += NW)
+      for (int lr = lane; lr < nrows; lr += 32) {
+        const int64_t r = r0 + lr;
+        const float v = vat(r, lr, c);
+        a.Vt[(int64_t)c * a.ldvt + r] = v;
+        if (c < w) a.Ct[(int64_t)c * a.ldt + r] = (r < w && c >= r) ? S[r] * R2[r * HM + c] : v;
       }
-      a.V[r * NB + lane] = v;
-      a.Vt[(int64_t)lane * a.ldvt + r] = v;
-    }
     if (rank == 0 && i2 < NB && j2 < NB) {
       Tm[i2 * NB + j2] = (i2 < w && j2 < w) ? Ts[i2 * HM + j2] : 0.f;
       if (i2 == j2 && i2 < w) a.tau[i2] = Ts[i2 * HM + i2];
@@ -547,7 +569,7 @@ __global__ void __launch_bounds__(32 * NW) k_panel_chol(PanelArgs<float> a, floa
     const int64_t r = r0 + lr;
     return c >= w ? 0.f : (r < c ? 0.f : (r == c ? 1.f : slab[lr * HM + c]));
   };
-  cl_gram(nrows, vval, Gp, G, cl);
+  cl_gram(nrows, vval, Wg, Gp, G, cl);
   if (rank == 0 && warp == 0) {  // CTA 0 wrote the reflector scalars
     for (int k = 0; k < NB; ++k) Ts[k * HM + lane] = 0.f;
     __syncwarp();
@@ -680,7 +702,10 @@ QrWs qr_dims(int64_t m, int64_t ncols) {
 
 template <class T>
 struct QrBufs {
-  T *Ct, *P, *V, *V2, *Vt, *partA, *partB, *tau, *pv, *pc, *Z, *Tm, *Bpt;
+  // V, Vt, Tm alternate between panels (the low-priority update of panel k
+  // still reads them while panel k + 1 is factored); pc, Z, Bpt are the
+  // high-priority stream's, pc2, Z2, Bpt2 the low-priority stream's
+  T *Ct, *P, *V, *V2, *Vt, *Vt2, *partA, *partB, *tau, *pv, *pc, *pc2, *Z, *Z2, *Tm, *Tm2, *Bpt, *Bpt2;
   GridBar* gb;
   int* err;
 };
@@ -695,14 +720,19 @@ QrBufs<T> qr_carve(SkiArena& ar, int64_t m, int64_t ncols) {
   b.V = ar.take<T>(m * NB);
   b.V2 = ar.take<T>(m * NB);  // panels alternate: V of panel k is still read by its update
   b.Vt = ar.take<T>(NB * q.ldt);
+  b.Vt2 = ar.take<T>(NB * q.ldt);
   b.partA = ar.take<T>(q.ncta_max * PW);
   b.partB = ar.take<T>(q.ncta_max * PW);
   b.tau = ar.take<T>(NB);
   b.pv = ar.take<T>(152 * NB * NB);
   b.pc = ar.take<T>(q.splits_max * NB * q.ldz);
+  b.pc2 = ar.take<T>(q.splits_max * NB * q.ldz);
   b.Z = ar.take<T>(NB * (NB + q.ldz));
+  b.Z2 = ar.take<T>(NB * (NB + q.ldz));
   b.Tm = ar.take<T>(NB * NB);
+  b.Tm2 = ar.take<T>(NB * NB);
   b.Bpt = ar.take<T>(q.ldz * NB);
+  b.Bpt2 = ar.take<T>(q.ldz * NB);
   b.gb = ar.take<GridBar>(1);
   b.err = ar.take<int>(1);
   return b;
@@ -894,7 +924,7 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
   // FP32 panels: Cholesky QR twice and Householder reconstruction in the
   // cluster (two cluster reductions per panel instead of one barrier per
   // column), when its work matrices and slab fit in shared memory
-  constexpr size_t kCholMats = (size_t)(2 * PW + 10 * NB * (NB + 1) + NB) * sizeof(float);
+  constexpr size_t kCholMats = (size_t)(2 * PW + (10 + GRAM_WARPS) * NB * (NB + 1) + NB) * sizeof(float);
   constexpr size_t kCholSmemMax = 200 * 1024;
   bool chol_ok = false;
   if constexpr (sizeof(T) == 4) {
@@ -926,8 +956,11 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     if (use_coop) ncta = ncta_coop;
     const int64_t rows_per = ski_cdiv(mr, ncta);
     T* Ctp = bf.Ct + k0 * ldt + k0;
-    T* Vk = ((k0 / NB) & 1) ? bf.V2 : bf.V;
-    PanelArgs<T> pa{bf.P, NB, mr, w, rows_per, ncta, nullptr, nullptr, bf.tau, Vk, bf.Vt, ldt, Ctp, ldt};
+    const bool odd = ((k0 / NB) & 1) != 0;
+    T* Vk = odd ? bf.V2 : bf.V;
+    T* Vtk = odd ? bf.Vt2 : bf.Vt;
+    T* Tmk = odd ? bf.Tm2 : bf.Tm;
+    PanelArgs<T> pa{bf.P, NB, mr, w, rows_per, ncta, nullptr, nullptr, bf.tau, Vk, Vtk, ldt, Ctp, ldt};
     bool done_panel = false;
     bool t_from_panel = false;  // the panel kernel wrote T (and no V^T V is needed)
     if constexpr (sizeof(T) == 4) {
@@ -949,7 +982,7 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
         cfg.stream = st;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        SKI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_chol<CNW>, pc, bf.Tm));
+        SKI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_chol<CNW>, pc, Tmk));
         SKI_LAUNCH_CHECK();
         done_panel = true;
         t_from_panel = true;
@@ -1009,45 +1042,60 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     }
     const int64_t nct = ncols - (k0 + w);
     T* Ctr = bf.Ct + (k0 + w) * ldt + k0;  // trailing columns, rows k0..m-1
-    // V^T V (split-K over rows, for T) and W = V^T C
+    // V^T V (split-K over rows, for T) and W = V^T C.  Look-ahead: the next
+    // panel's NB columns first, on the high-priority stream -- W, T^T W and
+    // their update -- and the rest (its own W, T^T W and update) on the
+    // low-priority stream, so that neither the bulk of W nor of the update
+    // lies between this panel and the next.  Below ~4M updated elements the
+    // split costs more than it overlaps.
     const int sv = t_from_panel ? 0 : (int)std::min<int64_t>(152, ski_cdiv(mr, 64));
     if (!t_from_panel)
-      SKI_TRY(ski_gemm_ex<T>(NB, NB, mr, T(1), bf.Vt, ldt, 1, bf.Vt, 1, ldt, T(0), bf.pv, NB, sv, (int64_t)NB * NB, st));
-    if (pending_lo) {  // W reads every trailing column: the previous update must be done
+      SKI_TRY(ski_gemm_ex<T>(NB, NB, mr, T(1), Vtk, ldt, 1, Vtk, 1, ldt, T(0), bf.pv, NB, sv, (int64_t)NB * NB, st));
+    const int64_t na = (qs && nct > NB && mr * (nct - NB) >= (1ll << 22)) ? NB : nct;
+    if (pending_lo) {  // the previous panel's low-priority update covered the next panel's columns' inputs
       SKI_CUDA_TRY(cudaStreamWaitEvent(st, qs->e_lo, 0));
       pending_lo = false;
     }
-    int sc = 1;
-    if (nct > 0) {
-      const int64_t tiles = ski_cdiv(nct, 128);
-      sc = (int)std::max<int64_t>(1, std::min<int64_t>(q.splits_max, ski_cdiv(300, tiles)));
-      sc = (int)std::min<int64_t>(sc, ski_cdiv(mr, 128));
+    auto splits_for = [&](int64_t cols) {
+      const int64_t tiles = ski_cdiv(cols, 128);
+      int sc = (int)std::max<int64_t>(1, std::min<int64_t>(q.splits_max, ski_cdiv(300, tiles)));
+      return (int)std::min<int64_t>(sc, ski_cdiv(mr, 128));
+    };
+    int sca = 1;
+    if (na > 0) {
+      sca = splits_for(na);
       timer.mark(st);
-      SKI_TRY(gemm_w<T>(nct, mr, Ctr, ldt, bf.Vt, bf.pc, q.ldz, sc, bf.err, st, split3));
+      SKI_TRY(gemm_w<T>(na, mr, Ctr, ldt, Vtk, bf.pc, q.ldz, sca, bf.err, st, split3));
       timer.mark(st);
     }
-    const int64_t zc = w + nct;
-    k_reduce_z<T><<<ski_cdiv(w * zc, 256), 256, 0, st>>>(w, nct, bf.pv, sv, bf.pc, sc, q.ldz, bf.Z);
+    k_reduce_z<T><<<ski_cdiv(w * (w + na), 256), 256, 0, st>>>(w, na, bf.pv, sv, bf.pc, sca, q.ldz, bf.Z);
     SKI_LAUNCH_CHECK();
     if (!t_from_panel) {
-      k_tfactor<T><<<1, 32, 0, st>>>(w, bf.Z, NB + q.ldz, bf.tau, bf.Tm);
+      k_tfactor<T><<<1, 32, 0, st>>>(w, bf.Z, NB + q.ldz, bf.tau, Tmk);
       SKI_LAUNCH_CHECK();
     }
-    if (nct > 0) {
-      k_ttw<T><<<ski_cdiv(nct, 128), 128, 0, st>>>(w, nct, bf.Z, NB + q.ldz, bf.Tm, bf.Bpt);
+    if (na < nct) {
+      // the rest, on the low-priority stream once V, V^T and T of this panel exist
+      const int64_t nr = nct - na;
+      SKI_CUDA_TRY(cudaEventRecord(qs->e_upd, st));
+      SKI_CUDA_TRY(cudaStreamWaitEvent(st_lo, qs->e_upd, 0));
+      const int scb = splits_for(nr);
+      timer.mark(st_lo);
+      SKI_TRY(gemm_w<T>(nr, mr, Ctr + na * ldt, ldt, Vtk, bf.pc2, q.ldz, scb, bf.err, st_lo, split3));
+      timer.mark(st_lo);
+      k_reduce_z<T><<<ski_cdiv(w * (w + nr), 256), 256, 0, st_lo>>>(w, nr, bf.pv, 0, bf.pc2, scb, q.ldz, bf.Z2);
       SKI_LAUNCH_CHECK();
-      // the next panel's columns first (high priority), the rest alongside it;
-      // below ~4M updated elements the split costs more than it overlaps
-      const int64_t na = (qs && nct > NB && mr * (nct - NB) >= (1ll << 22)) ? NB : nct;
-      if (na < nct) {
-        SKI_CUDA_TRY(cudaEventRecord(qs->e_upd, st));
-        SKI_CUDA_TRY(cudaStreamWaitEvent(st_lo, qs->e_upd, 0));
-        timer.mark(st_lo);
-        SKI_TRY(gemm_update<T>(nct - na, mr, bf.Bpt + na * NB, Vk, Ctr + na * ldt, ldt, bf.err, st_lo, split3));
-        timer.mark(st_lo);
-        SKI_CUDA_TRY(cudaEventRecord(qs->e_lo, st_lo));
-        pending_lo = true;
-      }
+      k_ttw<T><<<ski_cdiv(nr, 128), 128, 0, st_lo>>>(w, nr, bf.Z2, NB + q.ldz, Tmk, bf.Bpt2);
+      SKI_LAUNCH_CHECK();
+      timer.mark(st_lo);
+      SKI_TRY(gemm_update<T>(nr, mr, bf.Bpt2, Vk, Ctr + na * ldt, ldt, bf.err, st_lo, split3));
+      timer.mark(st_lo);
+      SKI_CUDA_TRY(cudaEventRecord(qs->e_lo, st_lo));
+      pending_lo = true;
+    }
+    if (na > 0) {
+      k_ttw<T><<<ski_cdiv(na, 128), 128, 0, st>>>(w, na, bf.Z, NB + q.ldz, Tmk, bf.Bpt);
+      SKI_LAUNCH_CHECK();
       timer.mark(st);
       SKI_TRY(gemm_update<T>(na, mr, bf.Bpt, Vk, Ctr, ldt, bf.err, st, split3));
       timer.mark(st);
