@@ -903,14 +903,14 @@ def run_batched(args, name):
 
     prec = {} if args.batch_precision == "f64" else dict(sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32)
 
-    def opts(streams):
+    def opts(streams, batch_lsqr=args.batch_lsqr):
         return pkg.ski_opts_default(m=-int(round(1000 * gamma)), s=1, seed=args.seed, tol=1e-10, tau_r=1e-10,
-                                    streams=streams, **prec)
+                                    streams=streams, batch_lsqr=batch_lsqr, **prec)
 
     wsz = {}
 
     def workspace(o):
-        k = (o.streams, o.lsqr_ctas)
+        k = (o.streams, o.lsqr_ctas, o.batch_lsqr)
         if k not in wsz:
             nb = max(pkg.ski_solve_batched_workspace_size(mats, o),
                      pkg.ski_solve_adjoint_batched_workspace_size(mats, o))
@@ -981,6 +981,10 @@ def run_batched(args, name):
     for w in args.sweep:
         ms_w, _, fwd_w = timed(opts(w), 1, 1)
         sweep[str(w)] = {"ms_per_step": ms_w, "problems_s": count / (ms_w * 1e-3), "fwd_ms": fwd_w}
+    # the other form of Step 4 (per problem or grouped) for comparison
+    ms_o, _, fwd_o = timed(opts(args.streams, 1 - args.batch_lsqr), 1, 1)
+    sweep["batch_lsqr_%d" % (1 - args.batch_lsqr)] = {"ms_per_step": ms_o, "problems_s": count / (ms_o * 1e-3),
+                                                      "fwd_ms": fwd_o}
     # end to end: pinned host A_i, b_i -> device, solve + adjoint, x_i, dA_i, db_i -> host
     Ah = [a.cpu().pin_memory() for a in As]
     bh = [b.cpu().pin_memory() for b in bs]
@@ -1027,7 +1031,8 @@ def run_batched(args, name):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": name, "problems": count, "gamma": gamma, "s": 1,
                        "sketch_qr": args.batch_precision,
-                       "streams": o_main.streams or "auto", "lsqr_pass": o_main.lsqr_pass,
+                       "streams": o_main.streams or "auto", "batch_lsqr": o_main.batch_lsqr,
+                       "lsqr_pass": o_main.lsqr_pass,
                        "lsqr_ctas": o_main.lsqr_ctas, "graphs": o_main.graphs, "autotune": tuned, "A_bytes": 8 * nA,
                        "l2": "inputs larger than L2 (%.1f GB)" % (8e-9 * nA),
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -1116,6 +1121,8 @@ def main():
     ap.add_argument("--no-usv", action="store_true",
                     help="skip the untimed mixed-precision-workload solves of the default line")
     ap.add_argument("--streams", type=int, default=0, help="batched workload: problems in flight (0 = auto)")
+    ap.add_argument("--batch-lsqr", type=int, default=0, choices=(0, 1),
+                    help="batched workload: 0 = Step 4 per problem, 1 = grouped over the problems in flight")
     ap.add_argument("--autotune", nargs="?", const="", default=None,
                     help="batched workload: tune the launch parameters first (optional JSON cache path)")
     ap.add_argument("--sweep", type=int, nargs="*", default=[1], help="batched workload: also time these")

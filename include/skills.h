@@ -108,7 +108,10 @@ typedef struct {
                           /* perturb > 0; 1 = column-pivoted QR (SA V = Q R with        */
                           /* R = [R11 R12; 0 0], R11 p x p), Steps 3-5 on W = A V1      */
                           /* R11^{-1}; dense A only (CSR keeps the behaviour of 0)      */
-  int32_t pad_;
+  int32_t batch_lsqr;     /* ski_solve_batched, dense problems: 0 = each problem's own  */
+                          /* Step 4 launches on its stream; 1 = Step 4 of all problems  */
+                          /* in flight grouped, one launch per kernel of an iteration   */
+                          /* over (problem, block) work items (same results)            */
   int64_t row_offset;     /* A holds rows [row_offset, row_offset + n) of a larger      */
                           /* matrix: the sketch entry points draw the columns of S for */
                           /* those global rows, so the sketches of row blocks sum to   */

@@ -60,7 +60,7 @@ class ski_opts(ctypes.Structure):
                 ("rcond", ctypes.c_double), ("perturb", ctypes.c_double), ("it_max", ctypes.c_int64),
                 ("streams", ctypes.c_int32), ("premix_slab", ctypes.c_int32),
                 ("lsqr_pass", ctypes.c_int32), ("lsqr_ctas", ctypes.c_int32), ("graphs", ctypes.c_int32),
-                ("hash_kind", ctypes.c_int32), ("factorization", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("hash_kind", ctypes.c_int32), ("factorization", ctypes.c_int32), ("batch_lsqr", ctypes.c_int32),
                 ("row_offset", ctypes.c_int64)]
 
 

@@ -94,7 +94,8 @@ static ski_status check_matrix(const ski_matrix* A) {
 }
 
 static bool launch_opts_ok(const ski_opts* o) {
-  return o->lsqr_pass >= 0 && o->lsqr_pass <= 4 && o->lsqr_ctas >= 0 && (o->graphs == 0 || o->graphs == 1);
+  return o->lsqr_pass >= 0 && o->lsqr_pass <= 4 && o->lsqr_ctas >= 0 && (o->graphs == 0 || o->graphs == 1) &&
+         (o->batch_lsqr == 0 || o->batch_lsqr == 1);
 }
 
 static ski_status check_sketch_opts(const ski_matrix* A, const ski_opts* o) {
@@ -703,7 +704,8 @@ extern "C" size_t ski_solve_workspace_size(const ski_matrix* A, const ski_opts* 
 }
 
 static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opts* o, double* x, double* R_out,
-                             ski_info* info, void* ws, size_t ws_bytes, void* stream, const ShardHook* sh) {
+                             ski_info* info, void* ws, size_t ws_bytes, void* stream, const ShardHook* sh,
+                             LsqrGroupHook* gh = nullptr) {
   if (info) {
     memset(info, 0, sizeof(*info));
     info->status = SKI_EINVAL;
@@ -1004,7 +1006,47 @@ static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opt
       SKI_TRY(ski_trmv_upper_update_launch(dl, P.M, P.vp, P.part_vv, P.v, P.w, P.y, P.z, P.sc, 1, st));
       const int CHUNK = 8;
       int64_t polled = 0;
-      for (;;) {
+      const bool grouped = gh && !P.csr && !sh;
+      if (grouped) {  // Step 4 on the batch's grouped launches
+        LsqrGroupTask task{};
+        DfArgs& f = task.job.df;
+        f.A2 = P.A2;
+        f.n = P.n;
+        f.d = dl;
+        f.ld2 = ski_a2_ld(dl);
+        f.sA = P.sA;
+        f.z = P.z;
+        f.u = P.t;
+        f.coef_from_scalars = 1;
+        f.t = P.t;
+        f.part = P.part;
+        f.part_tt = P.part_tt;
+        f.nblk = P.nblk;
+        f.rows_per = ski_cdiv(P.n, (int64_t)P.nblk);
+        f.sc = P.sc;
+        task.job.d = dl;
+        task.job.q = P.q;
+        task.job.Mt = P.Mt;
+        task.job.M = P.M;
+        task.job.v = P.v;
+        task.job.vp = P.vp;
+        task.job.part_vv = P.part_vv;
+        task.job.w = P.w;
+        task.job.y = P.y;
+        task.job.z = P.z;
+        task.job.nvv = ski_vv_blocks(dl);
+        task.cls = ski_df_group_class(dl);
+        task.smem = (size_t)f.rows_per * sizeof(double);
+        task.st = st;
+        task.it_max = o->it_max;
+        task.chunk = CHUNK;
+        task.budgeted = budgeted;
+        task.budget = budget;
+        task.tau_r = o->tau_r;
+        SKI_TRY(gh->run(task));
+        hs = task.hs;
+      }
+      while (!grouped) {
         SKI_TRY(lsqr_graph.run(st, [&](cudaStream_t s) -> ski_status {
           for (int k = 0; k < CHUNK; ++k) SKI_TRY(lsqr_iteration(A, P, s));
           return SKI_OK;
@@ -1112,6 +1154,17 @@ extern "C" ski_status ski_solve(const ski_matrix* A, const double* b, const ski_
                                 ski_info* info, void* ws, size_t ws_bytes, void* stream) {
   return solve_impl(A, b, o, x, R_out, info, ws, ws_bytes, stream, nullptr);
 }
+
+ski_status ski_solve_grouped(const ski_matrix* A, const double* b, const ski_opts* o, double* x, double* R_out,
+                             ski_info* info, void* ws, size_t ws_bytes, void* stream, LsqrGroupHook* hook) {
+  return solve_impl(A, b, o, x, R_out, info, ws, ws_bytes, stream, nullptr, hook);
+}
+
+bool ski_weak_preconditioner(double test, long long iters, double tau_r, int64_t budget) {
+  return weak_preconditioner(test, iters, tau_r, budget);
+}
+
+int ski_lsqr_ctas(int64_t n, const ski_opts* o) { return lsqr_ctas(n, o); }
 
 extern "C" ski_status ski_solve_rowblock(const ski_matrix* A, const double* b, const ski_opts* o, double* x,
                                          double* R_out, ski_info* info, void* ws, size_t ws_bytes, void* stream,

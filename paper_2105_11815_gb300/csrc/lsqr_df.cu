@@ -23,6 +23,8 @@
 // flag_b for the next K1.
 #include <stdlib.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "lsqr_impl.cuh"
 
@@ -95,8 +97,9 @@ __global__ void k_split_a(int64_t n, int64_t d, const double* __restrict__ A, in
 }
 
 // K2: double-float fused pass.  Thread tid owns columns tid + k*512 (k < CPT).
+// bid: the CTA's row block (blockIdx.x, or a work item's block in the grouped form)
 template <int CPT, int RR>
-__global__ void __launch_bounds__(512) k_fused_df(DfArgs f) {
+__device__ __forceinline__ void fused_df_body(const DfArgs& f, int64_t bid) {
   constexpr int NT = 512, NW = NT / 32;
   __shared__ float2 red[RR][NW];
   __shared__ float2 tsh[RR];
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(512) k_fused_df(DfArgs f) {
     ah_acc[k] = 0.f;
     al_acc[k] = 0.f;
   }
-  const int64_t r0 = (int64_t)blockIdx.x * f.rows_per;
+  const int64_t r0 = (int64_t)bid * f.rows_per;
   const int64_t r1 = min(f.n, r0 + f.rows_per);
   // u for this CTA's rows, staged once (off the per-row critical path)
   extern __shared__ double s_u[];
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(512) k_fused_df(DfArgs f) {
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
     const int64_t c = tid + (int64_t)k * NT;
-    if (c < f.d) f.part[(int64_t)blockIdx.x * f.d + c] = ldexp((double)ah_acc[k] + (double)al_acc[k], f.sA + st);
+    if (c < f.d) f.part[(int64_t)bid * f.d + c] = ldexp((double)ah_acc[k] + (double)al_acc[k], f.sA + st);
   }
   // ||t||^2: lane 0 of warps < RR hold pieces
   __shared__ double tts[NW];
@@ -201,9 +204,11 @@ __global__ void __launch_bounds__(512) k_fused_df(DfArgs f) {
   if (tid == 0) {
     double s = 0.0;
     for (int q = 0; q < RR; ++q) s += tts[q];
-    f.part_tt[blockIdx.x] = s;
+    f.part_tt[bid] = s;
   }
 }
+template <int CPT, int RR>
+__global__ void __launch_bounds__(512) k_fused_df(DfArgs f) { fused_df_body<CPT, RR>(f, blockIdx.x); }
 
 // K2, TMA-staged: rows of A2 stream into a shared-memory ring by 1-D bulk
 // copies (cp.async.bulk, completion on an mbarrier), one producer thread
@@ -500,14 +505,14 @@ __global__ void __launch_bounds__(512, 1) k_fused_df_rows(DfArgs f) {
 // shard: the row-block form -- q and ||t||^2 (in q[d]) are this process's
 // partial sums, to be summed over the processes before k_finish_shard
 // derives the scalars; a finished iteration (flag_a) contributes zeros.
-__global__ void __launch_bounds__(256) k_reduce_par(int nblk, int64_t d, const double* __restrict__ part,
-                                                    const double* __restrict__ part_tt, double* __restrict__ q,
-                                                    LsqrScalars* __restrict__ sc, int shard) {
+__device__ __forceinline__ void reduce_par_body(int nblk, int64_t d, const double* __restrict__ part,
+                                                const double* __restrict__ part_tt, double* __restrict__ q,
+                                                LsqrScalars* __restrict__ sc, int shard, int64_t bid) {
   __shared__ double sh[8][33];
   const bool skip = sc && flag_set(&sc->flag_a);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (!skip) {
-    const int64_t c = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t c = (int64_t)bid * 32 + lane;
     double s = 0.0;
     if (part && c < d)
       for (int b = wid; b < nblk; b += 8) s += part[(int64_t)b * d + c];
@@ -520,11 +525,11 @@ __global__ void __launch_bounds__(256) k_reduce_par(int nblk, int64_t d, const d
       if (part && c < d) q[c] = t;
     }
   } else if (shard && part) {
-    const int64_t c = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t c = (int64_t)bid * 32 + lane;
     if (wid == 0 && c < d) q[c] = 0.0;
   }
   if (shard) {
-    if (blockIdx.x == 0 && wid == 1) {
+    if (bid == 0 && wid == 1) {
       double t = 0.0;
       if (!skip) {
         for (int b = lane; b < nblk; b += 32) t += part_tt[b];
@@ -534,7 +539,7 @@ __global__ void __launch_bounds__(256) k_reduce_par(int nblk, int64_t d, const d
     }
     return;
   }
-  if (blockIdx.x == 0 && wid == 1 && sc) {
+  if (bid == 0 && wid == 1 && sc) {
     double t = 0.0;
     if (!skip) {
       for (int b = lane; b < nblk; b += 32) t += part_tt[b];
@@ -555,17 +560,22 @@ __global__ void __launch_bounds__(256) k_reduce_par(int nblk, int64_t d, const d
     }
   }
 }
+__global__ void __launch_bounds__(256) k_reduce_par(int nblk, int64_t d, const double* __restrict__ part,
+                                                    const double* __restrict__ part_tt, double* __restrict__ q,
+                                                    LsqrScalars* __restrict__ sc, int shard) {
+  reduce_par_body(nblk, d, part, part_tt, q, sc, shard, blockIdx.x);
+}
 
 // K4: p = M^T q (Mt lower triangular, warp per row), v' = p/beta - beta v
 // (start: v' = p/beta), per-CTA partial ||v'||^2.
-__global__ void __launch_bounds__(256) k_trmv_lower_vp(int64_t d, const double* __restrict__ Mt,
-                                                       const double* __restrict__ q, const double* __restrict__ v,
-                                                       double* __restrict__ vp, double* __restrict__ part_vv,
-                                                       LsqrScalars* __restrict__ sc, int start) {
+__device__ __forceinline__ void trmv_lower_vp_body(int64_t d, const double* __restrict__ Mt,
+                                                   const double* __restrict__ q, const double* __restrict__ v,
+                                                   double* __restrict__ vp, double* __restrict__ part_vv,
+                                                   LsqrScalars* __restrict__ sc, int start, int64_t bid) {
   __shared__ double sv[8];
   if (!start && flag_set(&sc->flag_a)) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t row = (int64_t)blockIdx.x * 8 + wid;
+  const int64_t row = (int64_t)bid * 8 + wid;
   const double beta = sc->beta_new;
   double vv = 0.0;
   if (row < d) {
@@ -585,18 +595,24 @@ __global__ void __launch_bounds__(256) k_trmv_lower_vp(int64_t d, const double* 
     double s = 0.0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) s += sv[w];
-    part_vv[blockIdx.x] = s;
+    part_vv[bid] = s;
   }
+}
+__global__ void __launch_bounds__(256) k_trmv_lower_vp(int64_t d, const double* __restrict__ Mt,
+                                                       const double* __restrict__ q, const double* __restrict__ v,
+                                                       double* __restrict__ vp, double* __restrict__ part_vv,
+                                                       LsqrScalars* __restrict__ sc, int start) {
+  trmv_lower_vp_body(d, Mt, q, v, vp, part_vv, sc, start, blockIdx.x);
 }
 
 // K1: alpha = ||v'|| from the K4 partials, LSQR rotation, v/y/w updates for
 // this CTA's rows, z = M v for the next pass.  Warp per row.
-__global__ void __launch_bounds__(256) k_trmv_upper_update(int64_t d, const double* __restrict__ M,
-                                                           const double* __restrict__ vp, int nvv,
-                                                           const double* __restrict__ part_vv, double* __restrict__ v,
-                                                           double* __restrict__ w, double* __restrict__ y,
-                                                           double* __restrict__ z, LsqrScalars* __restrict__ sc,
-                                                           int start) {
+__device__ __forceinline__ void trmv_upper_update_body(int64_t d, const double* __restrict__ M,
+                                                       const double* __restrict__ vp, int nvv,
+                                                       const double* __restrict__ part_vv, double* __restrict__ v,
+                                                       double* __restrict__ w, double* __restrict__ y,
+                                                       double* __restrict__ z, LsqrScalars* __restrict__ sc,
+                                                       int start, int64_t bid) {
   __shared__ double s_par[4];  // 1/alpha, c1, c2, done
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (!start && flag_set(&sc->flag_b)) return;
@@ -612,7 +628,7 @@ __global__ void __launch_bounds__(256) k_trmv_upper_update(int64_t d, const doub
       int done = 0;
       if (start) {
         done = (alpha * beta == 0.0) ? 1 : 0;
-        if (blockIdx.x == 0) {
+        if (bid == 0) {
           sc->alpha = alpha;
           sc->beta = beta;
           sc->phibar = beta;
@@ -640,7 +656,7 @@ __global__ void __launch_bounds__(256) k_trmv_upper_update(int64_t d, const doub
         const long long iters = sc->r_iters + 1;
         const bool conv = test <= sc->tau_r || alpha == 0.0 || beta == 0.0;
         done = (conv || iters >= sc->it_max) ? 1 : 0;
-        if (blockIdx.x == 0) {
+        if (bid == 0) {
           sc->anorm2 = anorm2;
           sc->rhobar = -cs * alpha;
           sc->phibar = phibar;
@@ -662,7 +678,7 @@ __global__ void __launch_bounds__(256) k_trmv_upper_update(int64_t d, const doub
   __syncthreads();
   const double ia = s_par[0], c1 = s_par[1], c2 = s_par[2];
   const bool done = s_par[3] != 0.0;
-  const int64_t row = (int64_t)blockIdx.x * 8 + wid;
+  const int64_t row = (int64_t)bid * 8 + wid;
   if (row >= d) return;
   if (lane == 0) {
     const double vn = vp[row] * ia;
@@ -683,8 +699,107 @@ __global__ void __launch_bounds__(256) k_trmv_upper_update(int64_t d, const doub
   acc = ski_warp_sum(acc);
   if (lane == 0) z[row] = acc * ia;
 }
+__global__ void __launch_bounds__(256) k_trmv_upper_update(int64_t d, const double* __restrict__ M,
+                                                           const double* __restrict__ vp, int nvv,
+                                                           const double* __restrict__ part_vv, double* __restrict__ v,
+                                                           double* __restrict__ w, double* __restrict__ y,
+                                                           double* __restrict__ z, LsqrScalars* __restrict__ sc,
+                                                           int start) {
+  trmv_upper_update_body(d, M, vp, nvv, part_vv, v, w, y, z, sc, start, blockIdx.x);
+}
+
+// ---- grouped form: one launch per kernel for every problem in flight
+template <int CPT, int RR>
+__global__ void __launch_bounds__(512) k_group_df(const LsqrGroupJob* __restrict__ jobs,
+                                                  const LsqrGroupItem* __restrict__ items) {
+  const LsqrGroupItem it = items[blockIdx.x];
+  fused_df_body<CPT, RR>(jobs[it.job].df, it.blk);
+}
+__global__ void __launch_bounds__(256) k_group_reduce(const LsqrGroupJob* __restrict__ jobs,
+                                                      const LsqrGroupItem* __restrict__ items) {
+  const LsqrGroupItem it = items[blockIdx.x];
+  const LsqrGroupJob& J = jobs[it.job];
+  reduce_par_body(J.df.nblk, J.d, J.df.part, J.df.part_tt, J.q, J.df.sc, 0, it.blk);
+}
+// K4 then K1 need the whole of K4 (part_vv): two launches over the same items
+__global__ void __launch_bounds__(256) k_group_trmv_lower(const LsqrGroupJob* __restrict__ jobs,
+                                                          const LsqrGroupItem* __restrict__ items) {
+  const LsqrGroupItem it = items[blockIdx.x];
+  const LsqrGroupJob& J = jobs[it.job];
+  trmv_lower_vp_body(J.d, J.Mt, J.q, J.v, J.vp, J.part_vv, J.df.sc, 0, it.blk);
+}
+__global__ void __launch_bounds__(256) k_group_trmv_upper(const LsqrGroupJob* __restrict__ jobs,
+                                                          const LsqrGroupItem* __restrict__ items) {
+  const LsqrGroupItem it = items[blockIdx.x];
+  const LsqrGroupJob& J = jobs[it.job];
+  trmv_upper_update_body(J.d, J.M, J.vp, J.nvv, J.part_vv, J.v, J.w, J.y, J.z, J.df.sc, 0, it.blk);
+}
+__global__ void k_group_scalars(const LsqrGroupJob* __restrict__ jobs, int njobs, LsqrScalars* __restrict__ out) {
+  constexpr int W = sizeof(LsqrScalars) / sizeof(int);
+  static_assert(sizeof(LsqrScalars) % sizeof(int) == 0, "LsqrScalars is copied as words");
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)njobs * W;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / W), k = (int)(e % W);
+    ((int*)(out + j))[k] = ((const volatile int*)jobs[j].df.sc)[k];
+  }
+}
 
 }  // namespace
+
+// Classes of the register-blocked pass (the default table of
+// ski_fused_df_launch): columns per thread 1, 2, 4, 8, 16
+int ski_df_group_class(int64_t d) {
+  const int64_t cpt = ski_cdiv(d, 512);
+  return cpt <= 1 ? 0 : cpt <= 2 ? 1 : cpt <= 4 ? 2 : cpt <= 8 ? 3 : 4;
+}
+
+ski_status ski_group_df_launch(int cls, const LsqrGroupJob* jobs, const LsqrGroupItem* items, int nitems,
+                               size_t smem, cudaStream_t st) {
+  if (nitems <= 0) return SKI_OK;
+  if (smem > 200 * 1024) return SKI_EINVAL;
+#define SKI_GDF_CASE(K, C, R)                                                                      \
+  if (cls == K) {                                                                                  \
+    if (smem > 48 * 1024)                                                                          \
+      SKI_CUDA_TRY(cudaFuncSetAttribute(k_group_df<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                        ski_smem_cap((const void*)k_group_df<C, R>)));             \
+    k_group_df<C, R><<<(unsigned)nitems, 512, smem, st>>>(jobs, items);                            \
+    SKI_LAUNCH_CHECK();                                                                            \
+    return SKI_OK;                                                                                 \
+  }
+  SKI_GDF_CASE(0, 1, 8)
+  SKI_GDF_CASE(1, 2, 8)
+  SKI_GDF_CASE(2, 4, 4)
+  SKI_GDF_CASE(3, 8, 4)
+  SKI_GDF_CASE(4, 16, 1)
+#undef SKI_GDF_CASE
+  return SKI_EINVAL;
+}
+
+ski_status ski_group_reduce_launch(const LsqrGroupJob* jobs, const LsqrGroupItem* items, int nitems,
+                                   cudaStream_t st) {
+  if (nitems <= 0) return SKI_OK;
+  k_group_reduce<<<(unsigned)nitems, 256, 0, st>>>(jobs, items);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+ski_status ski_group_trmv_launch(const LsqrGroupJob* jobs, const LsqrGroupItem* items, int nitems,
+                                 cudaStream_t st) {
+  if (nitems <= 0) return SKI_OK;
+  k_group_trmv_lower<<<(unsigned)nitems, 256, 0, st>>>(jobs, items);
+  SKI_LAUNCH_CHECK();
+  k_group_trmv_upper<<<(unsigned)nitems, 256, 0, st>>>(jobs, items);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+ski_status ski_group_scalars_launch(const LsqrGroupJob* jobs, int njobs, LsqrScalars* out, cudaStream_t st) {
+  if (njobs <= 0) return SKI_OK;
+  k_group_scalars<<<(unsigned)std::min<int64_t>(64, ski_cdiv((int64_t)njobs * 64, 256)), 256, 0, st>>>(jobs, njobs,
+                                                                                                      out);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
 
 ski_status ski_split_a_launch(int64_t n, int64_t d, const double* A, int64_t lda, int sA, float2* A2, cudaStream_t st,
                               const int32_t* cmap) {

@@ -94,6 +94,66 @@ ski_status ski_trmv_upper_update_launch(int64_t d, const double* M, const double
                                         double* v, double* w, double* y, double* z, LsqrScalars* sc, int start,
                                         cudaStream_t st);
 
+// ---- grouped LSQR iterations (ski_solve_batched): the four kernels of one
+// iteration (K2 pass, K3 reduction, K4 and K1 triangular products) each run
+// once for every problem in flight, over a list of (problem, block) work
+// items; a finished problem's items return at once (its flags).
+struct LsqrGroupJob {
+  DfArgs df;  // K2 of this problem (ld2 and rows_per set)
+  int64_t d;  // unknowns
+  double* q;
+  const double* Mt;
+  const double* M;
+  double *v, *vp, *part_vv, *w, *y, *z;
+  int nvv;  // K4 blocks (ski_vv_blocks(d))
+};
+struct LsqrGroupItem {
+  int32_t job, blk;
+};
+// K2 template class of the register-blocked pass for d unknowns (0 .. 4)
+int ski_df_group_class(int64_t d);
+constexpr int kDfGroupClasses = 5;
+// items[0 .. nitems): K2 blocks of jobs of class cls; smem: largest rows_per * 8
+ski_status ski_group_df_launch(int cls, const LsqrGroupJob* jobs, const LsqrGroupItem* items, int nitems,
+                               size_t smem, cudaStream_t st);
+// items: (job, 32-column block) for K3, (job, 8-row block) for K4 and K1
+ski_status ski_group_reduce_launch(const LsqrGroupJob* jobs, const LsqrGroupItem* items, int nitems,
+                                   cudaStream_t st);
+ski_status ski_group_trmv_launch(const LsqrGroupJob* jobs, const LsqrGroupItem* items, int nitems,
+                                 cudaStream_t st);
+// out[j] = *jobs[j].df.sc
+ski_status ski_group_scalars_launch(const LsqrGroupJob* jobs, int njobs, LsqrScalars* out, cudaStream_t st);
+
+// A problem's Step 4 handed to a batch-wide executor (batch.cu): the
+// solve fills the task after the LSQR start kernels are queued on st and
+// blocks in run() until the executor has iterated the problem to its stop,
+// with the single-problem loop's rules: flag_a, polled > it_max + chunk, or
+// (budgeted) the weak-preconditioner rule.
+struct LsqrGroupTask {
+  LsqrGroupJob job;
+  int cls;      // ski_df_group_class(job.d)
+  size_t smem;  // job.df.rows_per * 8
+  cudaStream_t st;
+  int64_t it_max;
+  int chunk;
+  bool budgeted;
+  int64_t budget;
+  double tau_r;
+  LsqrScalars hs;  // out: the scalars when the loop stopped
+};
+class LsqrGroupHook {
+ public:
+  virtual ski_status run(LsqrGroupTask& task) = 0;
+
+ protected:
+  ~LsqrGroupHook() = default;
+};
+// ski_solve with Step 4 of a dense problem run by hook (nullptr: ski_solve)
+ski_status ski_solve_grouped(const ski_matrix* A, const double* b, const ski_opts* o, double* x, double* R_out,
+                             ski_info* info, void* ws, size_t ws_bytes, void* stream, LsqrGroupHook* hook);
+bool ski_weak_preconditioner(double test, long long iters, double tau_r, int64_t budget);
+int ski_lsqr_ctas(int64_t n, const ski_opts* o);
+
 int ski_fused_ctas(int64_t n);
 ski_status ski_fused_launch(const FusedArgs& f, cudaStream_t st);
 ski_status ski_trmv_launch(bool upper, int64_t d, const double* M, int64_t ldm, const double* x, const double* add,

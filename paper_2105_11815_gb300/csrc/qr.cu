@@ -24,6 +24,7 @@
 // Applying the reflectors to column d of [SA | Sb] yields Q^T Sb for Step 3.
 #include <cooperative_groups.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -1043,16 +1044,20 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
     const int64_t nct = ncols - (k0 + w);
     T* Ctr = bf.Ct + (k0 + w) * ldt + k0;  // trailing columns, rows k0..m-1
     // V^T V (split-K over rows, for T) and W = V^T C.  Look-ahead: the next
-    // panel's NB columns first, on the high-priority stream -- W, T^T W and
-    // their update -- and the rest (its own W, T^T W and update) on the
-    // low-priority stream, so that neither the bulk of W nor of the update
-    // lies between this panel and the next.  Below ~4M updated elements the
-    // split costs more than it overlaps.
+    // panel's NB columns are updated first, on the high-priority stream, and
+    // the rest on the low-priority stream, so that the bulk of the update does
+    // not lie between this panel and the next.  FP32 also moves the rest's
+    // share of W (and of T^T W) to the low-priority stream; in FP64, where
+    // the GEMMs saturate the FP64 pipe and only overlap, W stays whole on the
+    // high-priority stream.  Below ~4M updated elements the split costs more
+    // than it overlaps.
     const int sv = t_from_panel ? 0 : (int)std::min<int64_t>(152, ski_cdiv(mr, 64));
     if (!t_from_panel)
       SKI_TRY(ski_gemm_ex<T>(NB, NB, mr, T(1), Vtk, ldt, 1, Vtk, 1, ldt, T(0), bf.pv, NB, sv, (int64_t)NB * NB, st));
-    const int64_t na = (qs && nct > NB && mr * (nct - NB) >= (1ll << 22)) ? NB : nct;
-    if (pending_lo) {  // the previous panel's low-priority update covered the next panel's columns' inputs
+    constexpr bool split_w = std::is_same<T, float>::value;
+    const int64_t nu = (qs && nct > NB && mr * (nct - NB) >= (1ll << 22)) ? NB : nct;
+    const int64_t nw = split_w ? nu : nct;
+    if (pending_lo) {  // the previous panel's low-priority update wrote the columns W reads
       SKI_CUDA_TRY(cudaStreamWaitEvent(st, qs->e_lo, 0));
       pending_lo = false;
     }
@@ -1062,42 +1067,49 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
       return (int)std::min<int64_t>(sc, ski_cdiv(mr, 128));
     };
     int sca = 1;
-    if (na > 0) {
-      sca = splits_for(na);
+    if (nw > 0) {
+      sca = splits_for(nw);
       timer.mark(st);
-      SKI_TRY(gemm_w<T>(na, mr, Ctr, ldt, Vtk, bf.pc, q.ldz, sca, bf.err, st, split3));
+      SKI_TRY(gemm_w<T>(nw, mr, Ctr, ldt, Vtk, bf.pc, q.ldz, sca, bf.err, st, split3));
       timer.mark(st);
     }
-    k_reduce_z<T><<<ski_cdiv(w * (w + na), 256), 256, 0, st>>>(w, na, bf.pv, sv, bf.pc, sca, q.ldz, bf.Z);
+    k_reduce_z<T><<<ski_cdiv(w * (w + nw), 256), 256, 0, st>>>(w, nw, bf.pv, sv, bf.pc, sca, q.ldz, bf.Z);
     SKI_LAUNCH_CHECK();
     if (!t_from_panel) {
       k_tfactor<T><<<1, 32, 0, st>>>(w, bf.Z, NB + q.ldz, bf.tau, Tmk);
       SKI_LAUNCH_CHECK();
     }
-    if (na < nct) {
-      // the rest, on the low-priority stream once V, V^T and T of this panel exist
-      const int64_t nr = nct - na;
+    if (nw > 0) {
+      k_ttw<T><<<ski_cdiv(nw, 128), 128, 0, st>>>(w, nw, bf.Z, NB + q.ldz, Tmk, bf.Bpt);
+      SKI_LAUNCH_CHECK();
+    }
+    if (nu < nct) {
+      // the rest, on the low-priority stream once V, V^T and T (and in FP64
+      // T^T W) of this panel exist
+      const int64_t nr = nct - nu;
       SKI_CUDA_TRY(cudaEventRecord(qs->e_upd, st));
       SKI_CUDA_TRY(cudaStreamWaitEvent(st_lo, qs->e_upd, 0));
-      const int scb = splits_for(nr);
+      const T* Bq = bf.Bpt + nu * NB;
+      if (split_w) {
+        const int scb = splits_for(nr);
+        timer.mark(st_lo);
+        SKI_TRY(gemm_w<T>(nr, mr, Ctr + nu * ldt, ldt, Vtk, bf.pc2, q.ldz, scb, bf.err, st_lo, split3));
+        timer.mark(st_lo);
+        k_reduce_z<T><<<ski_cdiv(w * (w + nr), 256), 256, 0, st_lo>>>(w, nr, bf.pv, 0, bf.pc2, scb, q.ldz, bf.Z2);
+        SKI_LAUNCH_CHECK();
+        k_ttw<T><<<ski_cdiv(nr, 128), 128, 0, st_lo>>>(w, nr, bf.Z2, NB + q.ldz, Tmk, bf.Bpt2);
+        SKI_LAUNCH_CHECK();
+        Bq = bf.Bpt2;
+      }
       timer.mark(st_lo);
-      SKI_TRY(gemm_w<T>(nr, mr, Ctr + na * ldt, ldt, Vtk, bf.pc2, q.ldz, scb, bf.err, st_lo, split3));
-      timer.mark(st_lo);
-      k_reduce_z<T><<<ski_cdiv(w * (w + nr), 256), 256, 0, st_lo>>>(w, nr, bf.pv, 0, bf.pc2, scb, q.ldz, bf.Z2);
-      SKI_LAUNCH_CHECK();
-      k_ttw<T><<<ski_cdiv(nr, 128), 128, 0, st_lo>>>(w, nr, bf.Z2, NB + q.ldz, Tmk, bf.Bpt2);
-      SKI_LAUNCH_CHECK();
-      timer.mark(st_lo);
-      SKI_TRY(gemm_update<T>(nr, mr, bf.Bpt2, Vk, Ctr + na * ldt, ldt, bf.err, st_lo, split3));
+      SKI_TRY(gemm_update<T>(nr, mr, Bq, Vk, Ctr + nu * ldt, ldt, bf.err, st_lo, split3));
       timer.mark(st_lo);
       SKI_CUDA_TRY(cudaEventRecord(qs->e_lo, st_lo));
       pending_lo = true;
     }
-    if (na > 0) {
-      k_ttw<T><<<ski_cdiv(na, 128), 128, 0, st>>>(w, na, bf.Z, NB + q.ldz, Tmk, bf.Bpt);
-      SKI_LAUNCH_CHECK();
+    if (nu > 0) {
       timer.mark(st);
-      SKI_TRY(gemm_update<T>(na, mr, bf.Bpt, Vk, Ctr, ldt, bf.err, st, split3));
+      SKI_TRY(gemm_update<T>(nu, mr, bf.Bpt, Vk, Ctr, ldt, bf.err, st, split3));
       timer.mark(st);
     }
   }

@@ -116,7 +116,8 @@ def test_argument_errors_before_launch(lib):
     assert L.ski_solve_adjoint(ctypes.byref(wide), x, x, x, 8193, x, x, 8193, x, ctypes.byref(ow), None, x, 1 << 40,
                                None) == 1
     for field, v in (("premix_slab", -1), ("streams", -1), ("s", 0), ("qr_dtype", 2), ("it_max", -1),
-                     ("lsqr_pass", 5), ("lsqr_pass", -1), ("lsqr_ctas", -1), ("graphs", 2)):
+                     ("lsqr_pass", 5), ("lsqr_pass", -1), ("lsqr_ctas", -1), ("graphs", 2), ("batch_lsqr", 2),
+                     ("batch_lsqr", -1)):
         o2 = lib.ski_opts_default(m=20, s=1)
         setattr(o2, field, v)
         assert L.ski_solve(ctypes.byref(A), x, ctypes.byref(o2), x, None, ctypes.byref(info), x, 1 << 40, None) == 1, \
@@ -162,6 +163,10 @@ def test_batched_workspace_scales_with_streams_and_rejects_negative(lib):
     assert w1 > 0 and w1 % 256 == 0
     assert pkg.ski_solve_batched_workspace_size(mats, four) == 4 * w1
     assert pkg.ski_solve_batched_workspace_size(mats, auto) == 5 * w1   # min(nprob, 8)
+    # grouped Step 4 adds the executor's job and work-item lists
+    grouped = pkg.ski_solve_batched_workspace_size(mats, pkg.ski_opts_default(m=-2000, streams=4, batch_lsqr=1))
+    assert 4 * w1 < grouped < 5 * w1 and grouped % 256 == 0
+    assert pkg.ski_solve_batched_workspace_size(mats, pkg.ski_opts_default(m=-2000, batch_lsqr=2)) == 0
     a1 = pkg.ski_solve_adjoint_batched_workspace_size(mats, one)
     assert a1 > 0 and pkg.ski_solve_adjoint_batched_workspace_size(mats, four) == 4 * a1
     bad = pkg.ski_opts_default(m=-2000, streams=-1)
