@@ -173,7 +173,8 @@ def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
     """Algorithm 1 with an s-hashing (optionally HRHT) sketch and Householder QR.
     variant=True sketches with the s-hashing variant of Def. 7.
     premix: False, True (the Walsh-Hadamard premix H D of Def. 8, padded to
-    n_pad) or "dht" (the HR-DHT premix F D of Ski-LLS-dense, no padding).
+    n_pad) or "dht" (the HR-DHT premix F D of Ski-LLS-dense, of length n, or
+    n_pad when given).
 
     factorization: "qr" (plain QR: when R fails the rank rule it raises, or,
     with perturb > 0, every back-solve with R divides by r_ii + perturb -- the
@@ -187,7 +188,7 @@ def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
     """
     n, d = A.shape
     if premix == "dht":
-        SAb = _dht.hrdht_sketch(seed, s, m, np.asarray(A), b, variant=variant)
+        SAb = _dht.hrdht_sketch(seed, s, m, np.asarray(A), b, variant=variant, n_h=n_pad)
     elif premix:
         SAb = _wht.hrht_sketch(seed, s, m, np.asarray(A), b, n_pad, variant=variant)
     else:

@@ -96,3 +96,49 @@ def test_hrdht_sketch_equals_explicit_product():
     S = sketch.s_hashing_matrix(11, s, m, n) @ dht.dht_matrix(n) @ np.diag(hashing.premix_signs(11, n).astype(float))
     out = dht.hrdht_sketch(11, s, m, A, b)
     assert np.allclose(out, np.column_stack([S @ A, S @ b]), atol=1e-12)
+
+
+def test_dht_length_is_the_next_13_smooth_integer():
+    def smooth(N):
+        for p in (2, 3, 5, 7, 11, 13):
+            while N % p == 0:
+                N //= p
+        return N == 1
+    # every size of the paper's experiments is already smooth: no padding
+    for n in (4000, 4096, 50000, 200000, 1000000, 1, 2, 13):
+        assert dht.dht_length(n) == n
+    # worked cases: 17 -> 18 = 2 3^2; 1009 (prime) -> 1014 = 2 3 13^2 (1010 = 2 5 101,
+    # 1011 = 3 337, 1012 = 2^2 11 23 and 1013 are not smooth); 0 -> 1
+    assert dht.dht_length(17) == 18 and dht.dht_length(1009) == 1014 and dht.dht_length(0) == 1
+    for n in range(1, 600):
+        N = dht.dht_length(n)
+        assert N >= n and smooth(N) and not any(smooth(k) for k in range(n, N))
+
+
+def test_padded_premix_is_the_transform_of_the_zero_padded_rows():
+    n, N = 17, 18
+    g = np.random.default_rng(8)
+    A, b = g.standard_normal((n, 4)), g.standard_normal(n)
+    D = hashing.premix_signs(3, n).astype(float)
+    X = np.vstack([D[:, None] * A, np.zeros((N - n, 4))])
+    assert np.allclose(dht.premix(3, A, N), dht.dht_matrix(N) @ X, atol=1e-12)
+    # orthogonal on the padded space: norms are kept
+    assert np.isclose(np.linalg.norm(dht.premix(3, b, N)), np.linalg.norm(b), rtol=1e-13)
+    with pytest.raises(ValueError):
+        dht.premix(3, A, n - 1)
+
+
+def test_srdht_sketch_picks_sampled_rows_of_the_premixed_matrix():
+    # S_s has a single 1 per row (Eq. SR-DHT): row i of S_s F D [A | b] is row
+    # c_i of F D [A | b], c_i the i-th sampled row index
+    n, N, m = 17, 18, 9
+    g = np.random.default_rng(9)
+    A, b = g.standard_normal((n, 3)), g.standard_normal(n)
+    rows = hashing.sample_rows(4, m, N)
+    Ss = np.zeros((m, N))
+    Ss[np.arange(m), rows] = 1.0
+    F = dht.dht_matrix(N)
+    D = hashing.premix_signs(4, n).astype(float)
+    X = np.vstack([np.column_stack([D[:, None] * A, D * b]), np.zeros((N - n, 4))])
+    assert np.allclose(dht.srdht_sketch(4, m, A, b, n_h=N), Ss @ F @ X, atol=1e-12)
+    assert np.allclose(dht.srdht_sketch(4, m, A, n_h=N), (Ss @ F @ X)[:, :3], atol=1e-12)
