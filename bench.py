@@ -401,6 +401,34 @@ def usv_solves(pkg, torch, args, n=200000, d=4000, n_pad=262144):
     return out
 
 
+def dht_sketch_stages(pkg, Amat, bt, cfg, args, sb):
+    """The same sketch with the Hartley premix F D of Eq. HR-DHT (length n, no
+    padding at the paper's sizes) instead of H D: one untimed and one timed
+    ski_sketch_hash per precision, outside the timed region."""
+    import torch
+    n, d, m, s = cfg["n"], cfg["d"], cfg["m"], cfg["s"]
+    out = {}
+    for lab, sdt, tdt in (("fp64", pkg.SKI_F64, torch.float64), ("fp32", pkg.SKI_F32, torch.float32)):
+        o = pkg.ski_opts_default(m=m, s=s, seed=args.seed, premix=2, sketch_dtype=sdt)
+        ws = torch.empty(pkg.ski_sketch_workspace_size(Amat, 1, o), dtype=torch.uint8, device="cuda")
+        SA = torch.empty(m, d + 1, dtype=tdt, device="cuda")
+        pkg.ski_sketch_hash(Amat, bt, o, SA, d + 1, ws=ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream()
+        e0.record(st)
+        pkg.ski_sketch_hash(Amat, bt, o, SA, d + 1, ws=ws)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        bytes_ = sb if sdt == pkg.SKI_F64 else 8.0 * n * (d + 1) + 4.0 * m * (d + 1)
+        out["premix_dht_and_hash_%s" % lab] = {
+            "ms": ms, "n_h": n, "bound": "alu" if sdt == pkg.SKI_F64 else "hbm", "algorithmic_bytes": bytes_,
+            "achieved_gbs": bytes_ / (ms * 1e-3) / 1e9, "timed": False}
+        del ws, SA
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, name):
     import numpy as np
     import torch
@@ -513,6 +541,8 @@ def run_ours(args, name):
         "qr_fp32": {"ms": qrmx, "bound": "alu", "flops": qr_flops,
                     "achieved_tflops": qr_flops / (qrmx * 1e-3) / 1e12, "peak_tflops": FP32_PEAK_TFLOPS},
     }
+    if npad and not args.no_dht:
+        stages.update(dht_sketch_stages(pkg, Amat, bt, cfg, args, sb))
     lls = {
         "fp64": {"ms": statistics.mean(i.ms_total for i, _ in infos), "iters": infos[-1][0].iters,
                  "restarts": infos[-1][0].restarts, "status": infos[-1][0].status,
@@ -1118,6 +1148,7 @@ def main():
     ap.add_argument("--ref-cols", type=int, default=1024, help="one-thread oracle sample: columns of A")
     ap.add_argument("--ref-cores", type=int, default=0, help="host processes of the oracle (0 = every host core)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-dht", action="store_true", help="skip the untimed Hartley-premix sketch stages")
     ap.add_argument("--no-usv", action="store_true",
                     help="skip the untimed mixed-precision-workload solves of the default line")
     ap.add_argument("--streams", type=int, default=0, help="batched workload: problems in flight (0 = auto)")

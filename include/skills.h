@@ -54,8 +54,10 @@ typedef enum {
  * significant bits), where SKI_F32 takes three passes (about FP32 accuracy). */
 typedef enum { SKI_F64 = 0, SKI_F32 = 1, SKI_BF16 = 2, SKI_TF32 = 3 } ski_dtype;
 typedef enum { SKI_DENSE = 0, SKI_CSR = 1 } ski_kind;
-/* The sketching matrix: s-hashing (Def. 5) or the s-hashing variant (Def. 7). */
-typedef enum { SKI_S_HASHING = 0, SKI_S_HASHING_VARIANT = 1 } ski_hash_kind;
+/* The sketching matrix: s-hashing (Def. 5), the s-hashing variant (Def. 7), or
+ * the sampling matrix S_s of Eq. SR-DHT (one 1 per row, in a column drawn
+ * uniformly with replacement). */
+typedef enum { SKI_S_HASHING = 0, SKI_S_HASHING_VARIANT = 1, SKI_SAMPLING = 2 } ski_hash_kind;
 
 /* The data matrix A (n x d).  Values are FP64 in both layouts. */
 typedef struct {
@@ -73,9 +75,14 @@ typedef struct {
 typedef struct {
   uint64_t seed;          /* draws S (Def. 5) and D (Def. 8) through the counter hash  */
   int32_t s;              /* nonzeros per column of S, 1 <= s <= m                     */
-  int32_t premix;         /* 1: S = S_h H D (Def. 8), dense A only; 0: S = S_h         */
+  int32_t premix;         /* 1: S = S_h H D (Def. 8); 2: S = S_h F D, F the normalised */
+                          /* discrete Hartley transform (Eq. HR-DHT); dense A only;    */
+                          /* 0: S = S_h                                                */
   int64_t m;              /* sketch rows, d <= m < 2^31                                */
-  int64_t n_pad;          /* premix height, a power of two >= n; 0: next power of two */
+  int64_t n_pad;          /* premix height N >= n: premix 1 a power of two (0: the     */
+                          /* next); premix 2 an integer whose prime factors are all    */
+                          /* <= 13 ([D A; 0] zero-padded to N rows; 0: the smallest    */
+                          /* such N >= n, n itself when n is one)                      */
   int32_t sketch_dtype;   /* ski_dtype of the premix, the sketch and its output SA     */
   int32_t qr_dtype;       /* QR of SA: SKI_F64, SKI_F32 (tensor-core products in three  */
                           /* TF32 passes) or SKI_TF32 (one); R kept in FP64.  R^{-1} is */
@@ -102,7 +109,9 @@ typedef struct {
                           /* once per solve as a CUDA graph and replayed; 0: launched   */
   int32_t hash_kind;      /* ski_hash_kind of S_h: 0 = s-hashing (Def. 5: s distinct    */
                           /* rows per column), 1 = the s-hashing variant (Def. 7: s     */
-                          /* rows drawn with replacement, coinciding entries add)       */
+                          /* rows drawn with replacement, coinciding entries add),      */
+                          /* 2 = sampling S_s (Eq. SR-DHT: row i of SA is row c_i of    */
+                          /* the (premixed) [A | b]; s = 1, dense A, premix 0 or 2)     */
   int32_t factorization;  /* Step 2 when R fails the rank rule (Remark (i)):            */
                           /* 0 = SKI_ESINGULAR, or the perturbed back-solve when        */
                           /* perturb > 0; 1 = column-pivoted QR (SA V = Q R with        */
@@ -233,12 +242,17 @@ ski_status ski_premix_signs(uint64_t seed, int64_t n, int8_t* D, void* stream);
 
 /*
  * ski_premix -- Y = H D [A b ; 0] for the n_pad x n_pad normalised
- * Walsh-Hadamard matrix H_ij = n_pad^{-1/2} (-1)^{<(i-1)_2,(j-1)_2>} (Def. 8).
- * A dense FP64 n x d; b device FP64 [n] or NULL.  Y: device, n_pad rows of
+ * Walsh-Hadamard matrix H_ij = n_pad^{-1/2} (-1)^{<(i-1)_2,(j-1)_2>} (Def. 8),
+ * or, with o->premix = 2, Y = F D [A b ; 0] for the N x N normalised discrete
+ * Hartley matrix F_ij = N^{-1/2} cas(2 pi i j / N), cas = cos + sin
+ * (Section 6, Eq. HR-DHT; N = o->n_pad or the default length described at
+ * ski_opts.n_pad), computed by a mixed-radix FFT in the sketch precision.
+ * A dense FP64 n x d; b device FP64 [n] or NULL.  Y: device, n_pad (N) rows of
  * d (+1 when b != NULL) columns, row stride ld_y, element type o->sketch_dtype
- * (FP64 or FP32).  Asynchronous.  Uses o->seed and o->n_pad.
- * A NaN or Inf in a column of [A b] makes that column of Y NaN (FP64 also when
- * a bounded wait of the first pass gave up: then all of Y).
+ * (FP64 or FP32).  Asynchronous.  Uses o->seed, o->premix and o->n_pad.
+ * Walsh-Hadamard: a NaN or Inf in a column of [A b] makes that column of Y
+ * NaN (FP64 also when a bounded wait of the first pass gave up: then all of
+ * Y); Hartley: it spreads through the FFT of that column.
  */
 size_t ski_premix_workspace_size(const ski_matrix* A, int32_t with_b, const ski_opts* o);
 ski_status ski_premix(const ski_matrix* A, const double* b, const ski_opts* o,
@@ -246,7 +260,9 @@ ski_status ski_premix(const ski_matrix* A, const double* b, const ski_opts* o,
 
 /*
  * ski_sketch_hash -- Step 1 of Algorithm 1: [SA | Sb] with S the s-hashing
- * matrix (Def. 5), or S = S_h H D (Def. 8) when o->premix = 1.
+ * matrix (Def. 5), or S = S_h H D (Def. 8) when o->premix = 1, or
+ * S = S_h F D (Eq. HR-DHT) when o->premix = 2; with o->hash_kind = 2 the
+ * sampling S_s takes the place of S_h (Eq. SR-DHT).
  *   SA  device, m rows, row stride ld_sa, element type o->sketch_dtype;
  *       columns 0..d-1 receive S A and, when b != NULL, column d receives S b.
  *       ld_sa >= d + (b != NULL).

@@ -13,7 +13,7 @@ import ctypes
 import os
 
 __all__ = [
-    "SKI_F64", "SKI_F32", "SKI_BF16", "SKI_DENSE", "SKI_CSR", "SKI_S_HASHING", "SKI_S_HASHING_VARIANT", "SkiError",
+    "SKI_F64", "SKI_F32", "SKI_BF16", "SKI_DENSE", "SKI_CSR", "SKI_S_HASHING", "SKI_S_HASHING_VARIANT", "SKI_SAMPLING", "SkiError",
     "ski_opts", "ski_info", "ski_matrix", "lib", "lib_path",
     "ski_opts_default", "ski_status_string", "ski_version", "ski_last_cuda_error", "ski_launch_count",
     "ski_selftest_wait_timeout", "ski_mixed_lsqr_budget",
@@ -30,7 +30,7 @@ __all__ = [
 
 SKI_F64, SKI_F32, SKI_BF16, SKI_TF32 = 0, 1, 2, 3
 SKI_DENSE, SKI_CSR = 0, 1
-SKI_S_HASHING, SKI_S_HASHING_VARIANT = 0, 1
+SKI_S_HASHING, SKI_S_HASHING_VARIANT, SKI_SAMPLING = 0, 1, 2
 STATUS = ["SKI_OK", "SKI_EINVAL", "SKI_ENOMEM", "SKI_ECUDA", "SKI_ENONFINITE",
           "SKI_ESINGULAR", "SKI_ENOCONV", "SKI_ETIMEOUT"]
 

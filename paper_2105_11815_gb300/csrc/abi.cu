@@ -100,18 +100,25 @@ static bool launch_opts_ok(const ski_opts* o) {
 
 static ski_status check_sketch_opts(const ski_matrix* A, const ski_opts* o) {
   if (!o) return SKI_EINVAL;
-  if (o->hash_kind != 0 && o->hash_kind != 1) return SKI_EINVAL;
+  if (o->hash_kind < 0 || o->hash_kind > 2) return SKI_EINVAL;
   if (o->s < 1 || o->s > 64 || o->m < (o->hash_kind ? 1 : o->s) || o->m >= (1ll << 31)) return SKI_EINVAL;
+  // the sampling sketch S_s (Eq. SR-DHT): one 1 per row, dense A, no s, and
+  // with the Hartley premix or none
+  if (o->hash_kind == 2 && (o->s != 1 || A->kind != SKI_DENSE || o->premix == 1 || o->row_offset != 0))
+    return SKI_EINVAL;
   if (o->premix_slab < 0 || o->streams < 0) return SKI_EINVAL;
   if (!launch_opts_ok(o)) return SKI_EINVAL;
   if (!dtype_ok(o->sketch_dtype)) return SKI_EINVAL;
+  if (o->premix < 0 || o->premix > 2) return SKI_EINVAL;
   if (o->premix) {
     if (A->kind != SKI_DENSE) return SKI_EINVAL;
-    if (o->n_pad != 0 && (!pow2(o->n_pad) || o->n_pad < A->n)) return SKI_EINVAL;
-    if (o->row_offset != 0) return SKI_EINVAL;  // H mixes every row of A: no row block premixes alone
+    if (o->premix == 1 && o->n_pad != 0 && (!pow2(o->n_pad) || o->n_pad < A->n)) return SKI_EINVAL;
+    if (o->premix == 2 && o->n_pad != 0 && (!ski_dht_length_ok(o->n_pad) || o->n_pad < A->n)) return SKI_EINVAL;
+    if (o->row_offset != 0) return SKI_EINVAL;  // the premix mixes every row of A: no row block premixes alone
   }
   if (o->row_offset < 0 || o->row_offset + A->n >= (1ll << 62)) return SKI_EINVAL;
-  const int64_t rows = o->premix ? (o->n_pad ? o->n_pad : next_pow2(A->n)) : A->n;
+  const int64_t rows = o->premix == 2 ? (o->n_pad ? o->n_pad : ski_dht_length(A->n))
+                       : o->premix ? (o->n_pad ? o->n_pad : next_pow2(A->n)) : A->n;
   if (rows * (int64_t)o->s >= (1ll << 31) || rows >= (1ll << 31)) return SKI_EINVAL;
   return SKI_OK;
 }
@@ -125,7 +132,10 @@ static int lsqr_ctas(int64_t n, const ski_opts* o) {
   return (int)std::max<int64_t>(c, ski_cdiv(n, 16384));
 }
 
+// Rows of the premixed matrix: n_pad, else the next power of two (Def. 8)
+// or the DHT length (Eq. HR-DHT: n itself when its prime factors are <= 13).
 static int64_t eff_npad(const ski_matrix* A, const ski_opts* o) {
+  if (o->premix == 2) return o->n_pad ? o->n_pad : ski_dht_length(A->n);
   return o->premix ? (o->n_pad ? o->n_pad : next_pow2(A->n)) : 0;
 }
 
@@ -157,9 +167,16 @@ static size_t sketch_scratch_bytes(const ski_matrix* A, int32_t with_b, const sk
   const int64_t ncols = A->d + (with_b ? 1 : 0);
   const int64_t rows = o->premix ? eff_npad(A, o) : A->n;
   SkiArena ar{nullptr, 0, 0, true};
-  ar.take<char>(ski_bucket_ws_bytes(rows, o->s, o->m));
+  // (the sampling sketch needs no bucket lists: one aligned block keeps the
+  // size query nonzero, 0 being its error value)
+  ar.take<char>(o->hash_kind != 2 ? ski_bucket_ws_bytes(rows, o->s, o->m) : 1);
   int64_t ldy = 0;
-  if (o->premix) {
+  if (o->premix == 2) {
+    const int32_t pdt = o->sketch_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
+    ldy = ski_round_up(ncols, 4);
+    ar.take<char>(dtype_size(pdt) * rows * ldy);
+    ar.take<char>(ski_dht_ws_bytes(A->n, ncols, rows, pdt));
+  } else if (o->premix) {
     const int32_t pdt = o->sketch_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
     ldy = premix_slab_cols(rows, ncols, pdt, o->premix_slab);
     // the full-width FP64 premix hands its int64 planes to the gather: no Y
@@ -176,15 +193,40 @@ static ski_status sketch_run(const ski_matrix* A, const double* b, const ski_opt
   const int64_t ncols = A->d + (b ? 1 : 0);
   const int64_t rows = o->premix ? eff_npad(A, o) : A->n;
   SkiArena ar{scratch, scratch_bytes, 0, false};
-  const size_t bkb = ski_bucket_ws_bytes(rows, o->s, o->m);
-  char* bkws = ar.take<char>(bkb);
-  if (!ar.ok() || !bkws) return SKI_ENOMEM;
-  SkiArena bar{bkws, bkb, 0, false};
-  SkiBuckets bk;
-  SKI_TRY(ski_build_buckets(o->seed, o->s, o->hash_kind, o->m, rows, bar, st, &bk, o->row_offset));
+  const bool sample = o->hash_kind == 2;
+  SkiBuckets bk{};
+  if (sample) {
+    ar.take<char>(1);
+  } else {
+    const size_t bkb = ski_bucket_ws_bytes(rows, o->s, o->m);
+    char* bkws = ar.take<char>(bkb);
+    if (!ar.ok() || !bkws) return SKI_ENOMEM;
+    SkiArena bar{bkws, bkb, 0, false};
+    SKI_TRY(ski_build_buckets(o->seed, o->s, o->hash_kind, o->m, rows, bar, st, &bk, o->row_offset));
+  }
   if (e_bk) SKI_CUDA_TRY(cudaEventRecord(e_bk, st));
   const double inv_sqrt_s = 1.0 / sqrt((double)o->s);
+  if (o->premix == 2) {
+    // Hartley premix F D into Y, then the s-hashing gather or the sampling
+    const int32_t pdt = o->sketch_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
+    const int64_t ldy = ski_round_up(ncols, 4);
+    void* Y = ar.take<char>(dtype_size(pdt) * rows * ldy);
+    const size_t dwb = ski_dht_ws_bytes(A->n, ncols, rows, pdt);
+    char* dws = ar.take<char>(dwb);
+    if (!ar.ok() || !dws) return SKI_ENOMEM;
+    SkiArena dar{dws, dwb, 0, false};
+    SKI_TRY(ski_dht_premix(A->val, A->ld, A->n, A->d, b, o->seed, rows, pdt, Y, ldy, dar, st));
+    if (e_pm) SKI_CUDA_TRY(cudaEventRecord(e_pm, st));
+    if (sample) return ski_sample_rows(o->seed, o->m, rows, Y, pdt, ldy, ncols, nullptr, o->sketch_dtype, SA, ld_sa, st);
+    if (pdt == SKI_F64)
+      return ski_gather_dense((const double*)Y, ldy, rows, ncols, nullptr, bk, inv_sqrt_s, SKI_F64, SA, ld_sa, st);
+    return ski_gather_dense_f32in((const float*)Y, ldy, ncols, bk, inv_sqrt_s, o->sketch_dtype, SA, ld_sa, st);
+  }
   if (!o->premix) {
+    if (sample) {
+      if (e_pm) SKI_CUDA_TRY(cudaEventRecord(e_pm, st));
+      return ski_sample_rows(o->seed, o->m, A->n, A->val, SKI_F64, A->ld, A->d, b, o->sketch_dtype, SA, ld_sa, st);
+    }
     if (e_pm) SKI_CUDA_TRY(cudaEventRecord(e_pm, st));
     if (A->kind == SKI_DENSE)
       return ski_gather_dense(A->val, A->ld, A->n, A->d, b, bk, inv_sqrt_s, o->sketch_dtype, SA, ld_sa, st);
@@ -248,8 +290,13 @@ extern "C" ski_status ski_sketch_hash(const ski_matrix* A, const double* b, cons
 
 extern "C" size_t ski_premix_workspace_size(const ski_matrix* A, int32_t with_b, const ski_opts* o) {
   if (check_matrix(A) != SKI_OK || !o || A->kind != SKI_DENSE) return 0;
-  const int64_t rows = o->n_pad ? o->n_pad : next_pow2(A->n);
   const int32_t pdt = o->sketch_dtype == SKI_F64 ? SKI_F64 : SKI_F32;
+  if (o->premix == 2) {
+    const int64_t rows = eff_npad(A, o);
+    if (!ski_dht_length_ok(rows) || rows < A->n) return 0;
+    return ski_dht_ws_bytes(A->n, A->d + (with_b ? 1 : 0), rows, pdt);
+  }
+  const int64_t rows = o->n_pad ? o->n_pad : next_pow2(A->n);
   return ski_premix_ws_bytes(A->n, A->d + (with_b ? 1 : 0), rows, pdt);
 }
 
@@ -258,6 +305,16 @@ extern "C" ski_status ski_premix(const ski_matrix* A, const double* b, const ski
   SKI_TRY(check_matrix(A));
   if (!o || A->kind != SKI_DENSE || !Y) return SKI_EINVAL;
   if (o->sketch_dtype != SKI_F64 && o->sketch_dtype != SKI_F32) return SKI_EINVAL;
+  if (o->premix == 2) {  // the Hartley premix F D of Eq. HR-DHT
+    const int64_t rows = eff_npad(A, o);
+    const int64_t ncols = A->d + (b ? 1 : 0);
+    if (!ski_dht_length_ok(rows) || rows < A->n || ld_y < ncols) return SKI_EINVAL;
+    const size_t need = ski_dht_ws_bytes(A->n, ncols, rows, o->sketch_dtype);
+    if (ws_bytes < need || !ws) return SKI_ENOMEM;
+    SkiArena ar{(char*)ws, ws_bytes, 0, false};
+    return ski_dht_premix(A->val, A->ld, A->n, A->d, b, o->seed, rows, o->sketch_dtype, Y, ld_y, ar,
+                          ski_stream(stream));
+  }
   const int64_t rows = o->n_pad ? o->n_pad : next_pow2(A->n);
   if (!pow2(rows) || rows < A->n) return SKI_EINVAL;
   const int64_t ncols = A->d + (b ? 1 : 0);

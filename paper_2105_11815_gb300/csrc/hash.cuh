@@ -11,12 +11,15 @@
 //             with replacement) keeps t = 0 for every k
 //   sign    = -1 iff the top bit of key(SIGN, j, k, 0) is set
 //   D_j     = -1 iff the top bit of key(PREMIX, j, 0, 0) is set
+//   c_i     = high 64 bits of key(SAMPLE, i, 0, 0) * N: the column of the 1 in
+//             row i of the sampling matrix S_s (Eq. SR-DHT)
 #pragma once
 #include <stdint.h>
 
 #define SKI_TAG_BUCKET 0xB1ull
 #define SKI_TAG_SIGN 0x5Aull
 #define SKI_TAG_PREMIX 0xD3ull
+#define SKI_TAG_SAMPLE 0x5Eull  // row draws c_i of the sampling sketch S_s (Eq. SR-DHT)
 
 __host__ __device__ __forceinline__ uint64_t ski_sm64(uint64_t z) {
   z += 0x9E3779B97F4A7C15ull;

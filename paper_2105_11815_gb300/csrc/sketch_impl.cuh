@@ -136,3 +136,14 @@ ski_status ski_gather_launch(int64_t p, const int32_t* idx, const double* src, d
 // dst = 0 (length d), then dst[idx[k]] = src[k] for k < p
 ski_status ski_scatter_launch(int64_t d, int64_t p, const int32_t* idx, const double* src, double* dst,
                               cudaStream_t st);
+
+// dht.cu: the DHT premix F D of Eq. HR-DHT (length N, prime factors <= 13)
+// into Y (N x ldY, FP64 or FP32), and the sampling sketch S_s of Eq. SR-DHT
+bool ski_dht_length_ok(int64_t N);
+int64_t ski_dht_length(int64_t n);
+size_t ski_dht_ws_bytes(int64_t n, int64_t ncols, int64_t N, int32_t dtype);
+ski_status ski_dht_premix(const double* A, int64_t lda, int64_t n, int64_t d, const double* b, uint64_t seed,
+                          int64_t N, int32_t dtype, void* Y, int64_t ldY, SkiArena& ar, cudaStream_t st);
+// SA[i, :] = X[c_i, :] (and b[c_i] in column dx when b is given), i < m
+ski_status ski_sample_rows(uint64_t seed, int64_t m, int64_t nrows, const void* X, int32_t x_dtype, int64_t ldx,
+                           int64_t dx, const double* b, int32_t out_dtype, void* SA, int64_t ld_sa, cudaStream_t st);

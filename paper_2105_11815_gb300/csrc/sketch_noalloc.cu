@@ -40,7 +40,7 @@ ski_status scratch_for_current_device(void** out) {
 extern "C" ski_status ski_sketch_hash_noalloc(const ski_matrix* A, const double* b, const ski_opts* o, void* SA,
                                               int64_t ld_sa, void* stream) {
   if (!A || !o || !SA) return SKI_EINVAL;
-  if (o->premix) return SKI_EINVAL;
+  if (o->premix || o->hash_kind == 2) return SKI_EINVAL;
   // the s-hashing variant (hash_kind 1) draws with replacement: s may exceed m
   if (A->n < 1 || A->d < 1 || o->s < 1 || o->s > 64 || o->m < (o->hash_kind == 1 ? 1 : o->s)) return SKI_EINVAL;
   if (A->n * (int64_t)o->s > SKI_NOALLOC_MAX_PAIRS || o->m > SKI_NOALLOC_MAX_M) return SKI_EINVAL;

@@ -196,3 +196,23 @@ def test_noalloc_limits_fit_its_fixed_scratch(lib):
                 for wb in (0, 1):
                     need = pkg.lib().ski_sketch_workspace_size(ctypes.byref(M), wb, ctypes.byref(o))
                     assert 0 < need <= cap, (s, hk, M.kind, wb, need)
+
+
+def test_hartley_premix_and_sampling_options(lib):
+    L = lib.lib()
+    A = _fake_dense(lib, 1009, 6)
+    ws = lambda **kw: L.ski_sketch_workspace_size(ctypes.byref(A), 1, ctypes.byref(lib.ski_opts_default(m=40, **kw)))
+    pm = lambda **kw: L.ski_premix_workspace_size(ctypes.byref(A), 1, ctypes.byref(lib.ski_opts_default(**kw)))
+    # F D of Eq. HR-DHT: lengths whose prime factors are <= 13, at least n; 0 = 1014
+    assert pm(premix=2) == pm(premix=2, n_pad=1014) > 0
+    for bad in (1010, 1013, 1008, 2 * 1009):
+        assert pm(premix=2, n_pad=bad) == 0, bad
+    # FP64: twiddles (2 x 1014) and four complex planes of 1014 x 8 doubles, at least
+    assert pm(premix=2) >= 8 * (2 * 1014 + 4 * 1014 * 8)
+    assert ws(premix=2) > 0 and ws(premix=2, n_pad=1010) == 0 and ws(premix=3) == 0
+    # the sampling sketch S_s (Eq. SR-DHT): s = 1, with the Hartley premix or none
+    assert ws(hash_kind=2) > 0 and ws(hash_kind=2, premix=2) > 0
+    assert ws(hash_kind=2, s=2) == 0 and ws(hash_kind=2, premix=1) == 0 and ws(hash_kind=3) == 0
+    csr = lib.ski_matrix(kind=lib.SKI_CSR, n=100, d=10, ld=0, val=0x1000, rowptr=0x1000, colidx=0x1000, nnz=5)
+    o = lib.ski_opts_default(m=20, hash_kind=2)
+    assert L.ski_sketch_workspace_size(ctypes.byref(csr), 1, ctypes.byref(o)) == 0
