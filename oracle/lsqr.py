@@ -178,8 +178,9 @@ def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
 
     factorization: "qr" (plain QR: when R fails the rank rule it raises, or,
     with perturb > 0, every back-solve with R divides by r_ii + perturb -- the
-    perturbed back-solve of Ski-LLS-sparse), or the rank-revealing forms of
-    Step 2 for any rank:
+    perturbed back-solve of Ski-LLS-sparse), "chol" (R the Cholesky factor of
+    SA^T SA, ``qr.gram_cholesky``, and Q^T Sb = R^{-T} SA^T Sb; the same rank
+    rule and perturbation), or the rank-revealing forms of Step 2 for any rank:
     "qrcp" (column-pivoted QR) or "cod" (complete orthogonal, R12 = 0); see
     ``ski_lls_rank_revealing``.
 
@@ -193,10 +194,14 @@ def ski_lls(A, b, seed, s, m, premix=False, n_pad=None, tau_a=1e-8, tau_r=1e-12,
         SAb = _wht.hrht_sketch(seed, s, m, np.asarray(A), b, n_pad, variant=variant)
     else:
         SAb = _sketch.sketch_rows(seed, s, m, A, b, variant=variant)
-    if factorization != "qr":
+    if factorization not in ("qr", "chol"):
         return ski_lls_rank_revealing(A, b, SAb, factorization, tau_a, tau_r, it_max, rcond)
-    R, C = _qr.householder_qr(SAb, ncols=d)                       # Step 2
-    qtsb = C[:, 0]
+    if factorization == "chol":                                   # Step 2 from the Gram
+        R = _qr.gram_cholesky(SAb[:, :d])
+        qtsb = solve_triangular(R, SAb[:, :d].T @ SAb[:, d], trans="T")
+    else:
+        R, C = _qr.householder_qr(SAb, ncols=d)                   # Step 2
+        qtsb = C[:, 0]
     p = _qr.numerical_rank(R, rcond)
     pert = 0.0
     if p < d:

@@ -112,3 +112,25 @@ def numerical_rank(R, rcond):
     while p < dg.size and ok[p]:
         p += 1
     return p
+
+
+def gram_cholesky(SA):
+    """R (d x d upper, positive diagonal) with R^T R = SA^T SA: the Cholesky
+    factor of the sketch's Gram matrix, written out column by column
+    (r_jj = sqrt(g_jj - sum_{k<j} r_kj^2), r_ji = (g_ji - sum_{k<j} r_kj r_ki) / r_jj
+    for i > j).  In exact arithmetic it is the R of a QR factorization of SA
+    with a positive diagonal -- the factor Ski-LLS-sparse takes from SPQR on a
+    sparse SA (Section 6) -- formed from a Gram matrix that a sparse SA gives
+    cheaply.  Raises LinAlgError when a pivot is not positive (SA numerically
+    rank-deficient in the Gram's precision)."""
+    SA = np.asarray(SA, dtype=np.float64)
+    G = SA.T @ SA
+    d = G.shape[0]
+    R = np.zeros((d, d))
+    for j in range(d):
+        piv = G[j, j] - R[:j, j] @ R[:j, j]
+        if not piv > 0.0:
+            raise np.linalg.LinAlgError(f"Gram pivot {j} is not positive")
+        R[j, j] = np.sqrt(piv)
+        R[j, j + 1:] = (G[j, j + 1:] - R[:j, j] @ R[:j, j + 1:]) / R[j, j]
+    return R

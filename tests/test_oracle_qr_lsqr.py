@@ -486,3 +486,36 @@ def test_residual_metric_dd_agrees_when_nothing_cancels():
     A2 = np.array([[2.0, 0.0, 0.0], [1.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
     assert lsqr.residual_metric_dd(A2, np.array([3.0, 2.0, 1.0]), np.ones(3)) == pytest.approx(2 / np.sqrt(7),
                                                                                               rel=1e-15)
+
+
+def test_gram_cholesky_hand_worked_and_against_householder():
+    # SA = [[3, 1], [4, 2]]: G = [[25, 11], [11, 5]], r11 = 5, r12 = 11/5,
+    # r22 = sqrt(5 - 121/25) = 2/5
+    R = qr.gram_cholesky(np.array([[3.0, 1.0], [4.0, 2.0]]))
+    assert np.allclose(R, [[5.0, 2.2], [0.0, 0.4]], rtol=0, atol=1e-14)
+    g = np.random.default_rng(3)
+    SA = g.standard_normal((60, 12)) * np.logspace(0, 2, 12)
+    Rc = qr.gram_cholesky(SA)
+    assert np.allclose(np.triu(Rc), Rc) and np.all(np.diag(Rc) > 0)
+    assert np.allclose(Rc.T @ Rc, SA.T @ SA, rtol=1e-12, atol=1e-9)
+    Rh, _ = qr.householder_qr(SA)
+    Rh = np.sign(np.diag(Rh))[:, None] * Rh          # the unique R with a positive diagonal
+    assert np.allclose(Rc, Rh, rtol=1e-10, atol=1e-10)
+    with pytest.raises(np.linalg.LinAlgError):
+        qr.gram_cholesky(np.column_stack([SA[:, :3], SA[:, 0]]))   # a repeated column
+
+
+def test_ski_lls_with_the_gram_cholesky_factor():
+    import scipy.sparse as sp
+    g = np.random.default_rng(4)
+    n, d = 3000, 40
+    A = sp.random(n, d, density=0.05, random_state=5, format="csr") + sp.eye(n, d, format="csr")
+    b = g.standard_normal(n)
+    x, info = lsqr.ski_lls(A, b, seed=2, s=2, m=120, factorization="chol")
+    xq, iq = lsqr.ski_lls(A, b, seed=2, s=2, m=120)
+    xr = np.linalg.lstsq(A.toarray(), b, rcond=None)[0]
+    assert np.linalg.norm(x - xr) <= 1e-8 * np.linalg.norm(xr)
+    Rq = np.sign(np.diag(iq["R"]))[:, None] * iq["R"]
+    assert np.allclose(info["R"], Rq, rtol=1e-9, atol=1e-9)
+    assert np.allclose(info["qtsb"], np.sign(np.diag(iq["R"])) * iq["qtsb"], rtol=1e-9, atol=1e-9)
+    assert abs(info["iters"] - iq["iters"]) <= 1
