@@ -116,7 +116,12 @@ typedef struct {
                           /* 0 = SKI_ESINGULAR, or the perturbed back-solve when        */
                           /* perturb > 0; 1 = column-pivoted QR (SA V = Q R with        */
                           /* R = [R11 R12; 0 0], R11 p x p), Steps 3-5 on W = A V1      */
-                          /* R11^{-1}; dense A only (CSR keeps the behaviour of 0)      */
+                          /* R11^{-1}; dense A only (CSR keeps the behaviour of 0);     */
+                          /* 2 (CSR A, FP64 factor) = R from a sparse sketch (Section   */
+                          /* 6): SA kept in CSR, R the Cholesky factor of SA^T SA       */
+                          /* (R^T R = SA^T SA, positive diagonal), Q^T Sb =             */
+                          /* R^{-T} SA^T Sb, with the Householder QR of the dense SA    */
+                          /* when the Cholesky breaks down; then as 0                   */
   int32_t batch_lsqr;     /* ski_solve_batched, dense problems: 0 = each problem's own  */
                           /* Step 4 launches on its stream; 1 = Step 4 of all problems  */
                           /* in flight grouped, one launch per kernel of an iteration   */
@@ -155,7 +160,8 @@ typedef struct {
                                /* requested precision; it decides the fallback)        */
   int32_t pivoted;             /* 1 when Step 2 took the column-pivoted QR: rank is   */
                                /* then p of R11, and x is zero outside V1's columns    */
-  int32_t pad_;
+  int32_t gram;                /* 1 when R came from the Cholesky factor of the sparse */
+                               /* sketch's Gram matrix (factorization 2)              */
 } ski_info;
 
 /* Defaults of Ski-LLS-dense (Section 6): m = 0 (caller must set), s = 1,

@@ -73,7 +73,7 @@ class ski_info(ctypes.Structure):
                 ("ms_lsqr", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("ms_premix", ctypes.c_float), ("ms_gather", ctypes.c_float), ("ms_qr_gemm", ctypes.c_float),
                 ("qr_fallback", ctypes.c_int32), ("inv_dtype", ctypes.c_int32), ("rdiag_ratio", ctypes.c_double),
-                ("pivoted", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("pivoted", ctypes.c_int32), ("gram", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -487,13 +487,22 @@ bool weak_preconditioner(double test, long long iters, double tau_r, int64_t bud
 }
 
 // Bytes of the phase region for the sketch / QR / trinv precisions of o.
+// Step 2 from the Gram matrix of a sparse SA (factorization 2: CSR A, FP64)
+bool gram_path(const ski_matrix* A, const ski_opts* o) {
+  return o->factorization == 2 && A->kind == SKI_CSR && o->qr_dtype == SKI_F64 && o->sketch_dtype == SKI_F64;
+}
+size_t gram_stage_bytes(const ski_matrix* A, const ski_opts* o) {
+  return gram_path(A, o) ? ski_gram_ws_bytes(A->n, A->d, A->nnz, o->s, o->m) : 0;
+}
+
 size_t region_need(const ski_matrix* A, const ski_opts* o) {
   const int64_t d = A->d, m = o->m, ncols = d + 1, ld_sa = ski_round_up(ncols, 4);
   const int32_t qdt = qr_storage(o->qr_dtype);
   const size_t sa_bytes = ski_round_up((int64_t)(dtype_size(o->sketch_dtype) * m * ld_sa), 256);
   const bool copy_q = dtype_size(o->sketch_dtype) != dtype_size(qdt) || o->sketch_dtype == SKI_BF16;
   const size_t saq_bytes = copy_q ? ski_round_up((int64_t)(dtype_size(qdt) * m * ld_sa), 256) : 0;
-  const size_t stage = std::max(sketch_scratch_bytes(A, 1, o, nullptr), ski_qr_ws_bytes(m, ncols, qdt));
+  const size_t stage = std::max({sketch_scratch_bytes(A, 1, o, nullptr), ski_qr_ws_bytes(m, ncols, qdt),
+                                  gram_stage_bytes(A, o)});
   return std::max(sa_bytes + saq_bytes + stage, ski_trinv_ws_bytes(d, qdt));
 }
 
@@ -509,7 +518,8 @@ void carve_region(const ski_matrix* A, const ski_opts* o, SolvePlan* P) {
   P->SA = P->region;
   P->SAq = copy_q ? (void*)(P->region + sa_bytes) : P->SA;
   P->stage = P->region + sa_bytes + saq_bytes;
-  P->stage_bytes = std::max(sketch_scratch_bytes(A, 1, o, nullptr), ski_qr_ws_bytes(m, ncols, P->qr_dt));
+  P->stage_bytes = std::max({sketch_scratch_bytes(A, 1, o, nullptr), ski_qr_ws_bytes(m, ncols, P->qr_dt),
+                             gram_stage_bytes(A, o)});
   (void)d;
 }
 
@@ -776,6 +786,7 @@ static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opt
   if (o->qr_dtype != SKI_F64 && o->qr_dtype != SKI_F32 && o->qr_dtype != SKI_TF32) return SKI_EINVAL;
   if (A->kind == SKI_DENSE && A->d > SKI_DENSE_DMAX) return SKI_EINVAL;
   if (o->it_max < 0) return SKI_EINVAL;
+  if (o->factorization < 0 || o->factorization > 2) return SKI_EINVAL;
   SolvePlan P;
   const size_t need = plan_solve(A, o, nullptr, 0, &P);
   if (ws_bytes < need || !ws) {
@@ -811,6 +822,7 @@ static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opt
   const bool pivot_ok = o->factorization == 1 && !P.csr;
   bool need_pivot = false;
   bool perturbed = false;  // R + perturb I replaced R (the perturbed back-solve)
+  bool gram_used = false;  // Step 2 took the Cholesky factor of the sparse sketch's Gram matrix
   // Steps 1-2 and R^{-1} in the precisions of `of`
   auto factor = [&](const ski_opts* of) -> ski_status {
     carve_region(A, of, &P);
@@ -837,8 +849,20 @@ static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opt
     }
     double gm = 0.0;
     {
+      // factorization 2 (CSR A, FP64): R from the Cholesky factor of the
+      // sparse sketch's Gram matrix, else (or when that breaks down) the
+      // Householder QR of the dense [SA | Sb]
+      bool done = false;
+      gram_used = false;
+      if (gram_path(A, of) && !P.sh) {
+        SkiArena gar{P.stage, P.stage_bytes, 0, false};
+        SKI_TRY(ski_gram_chol_run(A, of->seed, of->s, of->hash_kind, P.m, (const double*)P.SA + d, P.ld_sa, P.R, d,
+                                  P.qtsb, &done, gar, st));
+        gram_used = done;
+      }
       SkiArena qar{P.stage, P.stage_bytes, 0, false};
-      SKI_TRY(ski_qr_run(P.m, d, 1, P.SAq, P.ld_sa, P.qr_prec, P.R, d, P.qtsb, qar, st, info ? &gm : nullptr));
+      if (!done)
+        SKI_TRY(ski_qr_run(P.m, d, 1, P.SAq, P.ld_sa, P.qr_prec, P.R, d, P.qtsb, qar, st, info ? &gm : nullptr));
     }
     qr_gemm_ms += gm;
     SKI_CUDA_TRY(cudaEventRecord(fe.e[2], st));
@@ -1202,6 +1226,7 @@ static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opt
     info->inv_dtype = inv_dt;
     info->ms_qr_gemm = (float)qr_gemm_ms;
     info->pivoted = P.pivoted ? 1 : 0;
+    info->gram = gram_used ? 1 : 0;
     info->status = result;
   }
   return result;

@@ -33,6 +33,9 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm(
   // triangular (B[k,j] = 0 for k > j).  Skip the k-range that is all zero.
   if (tri & 1) kbeg = max(kbeg, m0 - (m0 % BK));
   if (tri & 2) kend = min(kend, n0 + BN);
+  // tri bit 2: only C's upper triangle is wanted -- a tile wholly below the
+  // diagonal (every row index above every column index) is skipped
+  if ((tri & 4) && m0 >= n0 + BN) return;
   C += (int64_t)blockIdx.z * c_zstride;
   T acc[TM][TN];
 #pragma unroll

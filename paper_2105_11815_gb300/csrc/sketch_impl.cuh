@@ -147,3 +147,13 @@ ski_status ski_dht_premix(const double* A, int64_t lda, int64_t n, int64_t d, co
 // SA[i, :] = X[c_i, :] (and b[c_i] in column dx when b is given), i < m
 ski_status ski_sample_rows(uint64_t seed, int64_t m, int64_t nrows, const void* X, int32_t x_dtype, int64_t ldx,
                            int64_t dx, const double* b, int32_t out_dtype, void* SA, int64_t ld_sa, cudaStream_t st);
+
+// gram.cu: Step 2 of Ski-LLS-sparse from a sparse sketch -- SA in CSR, its Gram
+// matrix SA^T SA, R = its Cholesky factor (d x d, upper, ldr; lower triangle
+// zeroed) and qtsb = R^{-T} SA^T Sb (Sb: column of the dense sketch, stride
+// ldsb).  *ok = false (R and qtsb unusable) when a sketch row is too long for
+// the shared-memory merge or a Cholesky pivot is not positive; synchronises st.
+size_t ski_gram_ws_bytes(int64_t n, int64_t d, int64_t nnz, int32_t s, int64_t m);
+ski_status ski_gram_chol_run(const ski_matrix* A, uint64_t seed, int32_t s, int32_t replace, int64_t m,
+                             const double* Sb, int64_t ldsb, double* R, int64_t ldr, double* qtsb, bool* ok,
+                             SkiArena& ar, cudaStream_t st);

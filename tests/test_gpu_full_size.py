@@ -104,19 +104,20 @@ def test_kappa_1e10_with_b_ones_sits_at_the_fp64_floor():
         assert host <= 1e-10
 
 
-@pytest.mark.parametrize("mixed", [False, True])
-def test_sparse_solve_full_size(mixed):
+@pytest.mark.parametrize("mixed,factorization", [(False, 0), (True, 0), (False, 2)])
+def test_sparse_solve_full_size(mixed, factorization):
     # CSR 1e6 x 20000 with 8 nonzeros per row and 0.1% rows of 2000, s = 2,
     # m = 2d; the FP64 path (its 40000 x 20001 QR on the FP64 pipe takes about
-    # 25 s) and the mixed form
+    # 25 s), the mixed form, and R from the sparse sketch's Gram matrix
     torch, pkg = cuda()
     n, d = 1_000_000, 20000
     rp, ci, v, b = workloads.csr_heavy_rows(n, d, seed=20210525)
     M = pkg.csr_matrix(to_dev(torch, rp), to_dev(torch, ci), to_dev(torch, v), n, d)
     kw = dict(sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32) if mixed else {}
-    o = pkg.ski_opts_default(m=2 * d, s=2, seed=20210525, tol=1e-10, tau_r=1e-10, **kw)
+    o = pkg.ski_opts_default(m=2 * d, s=2, seed=20210525, tol=1e-10, tau_r=1e-10, factorization=factorization, **kw)
     x = torch.empty(d, dtype=torch.float64, device="cuda")
     info = pkg.ski_solve(M, to_dev(torch, b), o, x)
     assert info.status == 0 and info.metric <= 1e-10
+    assert info.gram == (1 if factorization == 2 else 0)
     A = sp.csr_matrix((v, ci, rp), shape=(n, d))
     assert olsqr.residual_metric_dd(A, b, x.cpu().numpy()) <= 1e-10

@@ -1,0 +1,85 @@
+"""Step 2 of Ski-LLS-sparse from a sparse sketch (Section 6;
+ski_opts.factorization = 2): SA kept in CSR, R the Cholesky factor of its Gram
+matrix SA^T SA, Q^T Sb = R^{-T} SA^T Sb, against the oracle's
+``qr.gram_cholesky`` and ``ski_lls(factorization="chol")``; and the fallback to
+the Householder QR of the dense sketch when the Cholesky breaks down or a
+sketch row is too long for the shared-memory merge."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import lsqr as olsqr, qr as oqr, sketch as osk
+from paper_2105_11815_gb300 import workloads
+from gpu_util import cuda, rel_fro, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _csr(torch, pkg, A):
+    A = A.tocsr()
+    A.sort_indices()
+    arrs = (to_dev(torch, A.indptr.astype(np.int64)), to_dev(torch, A.indices.astype(np.int32)),
+            to_dev(torch, A.data.astype(np.float64)))
+    return pkg.csr_matrix(arrs[0], arrs[1], arrs[2], A.shape[0], A.shape[1]), arrs
+
+
+def _solve(torch, pkg, A, b, **kw):
+    M, keep = _csr(torch, pkg, A)
+    d = A.shape[1]
+    o = pkg.ski_opts_default(tol=1e-10, tau_r=1e-12, **kw)
+    x = torch.empty(d, dtype=torch.float64, device="cuda")
+    R = torch.empty(d, d, dtype=torch.float64, device="cuda")
+    info = pkg.ski_solve(M, to_dev(torch, b), o, x, R_out=R)
+    return x.cpu().numpy(), R.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("n,d,s,m", [(20000, 150, 2, 300), (8000, 64, 1, 200), (30000, 300, 3, 700)])
+def test_gram_factor_matches_the_oracle(n, d, s, m):
+    torch, pkg = cuda()
+    rp, ci, v, b = workloads.csr_heavy_rows(n, d, seed=n + d, nnz_row=8, heavy_frac=1e-3, heavy_nnz=min(d, 100))
+    A = sp.csr_matrix((v, ci, rp), shape=(n, d))
+    x, R, info = _solve(torch, pkg, A, b, m=m, s=s, seed=5, factorization=2)
+    assert info.status == 0 and info.gram == 1
+    SAb = osk.sketch_rows(5, s, m, A, b)
+    Ro = oqr.gram_cholesky(SAb[:, :d])
+    assert rel_fro(R, Ro) <= 1e-11
+    assert np.allclose(np.tril(R, -1), 0.0)
+    xo, oinfo = olsqr.ski_lls(A, b, seed=5, s=s, m=m, factorization="chol")
+    assert rel_fro(x, xo) <= 1e-9
+    assert abs(info.iters - oinfo["iters"]) <= 1
+    assert olsqr.residual_metric(A, b, x) <= 1e-10
+    # the same solve through the Householder QR: R agrees up to row signs
+    _, Rq, iq = _solve(torch, pkg, A, b, m=m, s=s, seed=5)
+    assert iq.gram == 0
+    assert rel_fro(np.sign(np.diag(Rq))[:, None] * Rq, R) <= 1e-9
+
+
+def test_breakdown_falls_back_to_householder():
+    # a zero column: the Gram's pivot is 0, the Cholesky reports failure and
+    # the Householder QR of the dense sketch is taken (then the perturbed
+    # back-solve, since R fails the rank rule)
+    torch, pkg = cuda()
+    n, d = 6000, 40
+    rp, ci, v, b = workloads.csr_heavy_rows(n, d, seed=3, nnz_row=6, heavy_frac=0.0, heavy_nnz=0)
+    A = sp.csr_matrix((v, ci, rp), shape=(n, d)).tolil()
+    A[:, 7] = 0.0
+    A = A.tocsr()
+    A.eliminate_zeros()
+    b = A @ np.random.default_rng(2).standard_normal(d)     # consistent: x_s solves it
+    x, R, info = _solve(torch, pkg, A, b, m=120, s=2, seed=9, factorization=2, perturb=1e-8, tau_a=1e-6)
+    # rank: the leading diagonal entries that pass the rule stop at column 7
+    assert info.status == 0 and info.gram == 0 and info.rank == 7
+    assert np.linalg.norm(A @ x - b) <= 1e-6
+
+
+def test_long_sketch_rows_fall_back():
+    # 20000 rows of 50 nonzeros hashed into m = 100 rows: each sketch row
+    # gathers ~10000 entries before merging, more than the shared-memory merge
+    # takes, so the Householder QR of the dense sketch is used
+    torch, pkg = cuda()
+    n, d = 20000, 80
+    A = sp.random(n, d, density=50 / d, random_state=6, format="csr")
+    b = np.random.default_rng(6).standard_normal(n)
+    x, R, info = _solve(torch, pkg, A, b, m=100, s=1, seed=1, factorization=2)
+    assert info.status == 0 and info.gram == 0
+    assert olsqr.residual_metric(A, b, x) <= 1e-10
