@@ -86,11 +86,9 @@ SKETCH_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 43264 + 38400 + 429056 + 333056
                   1598208 + 1618771200 + 2050941696 + 2425076480 + 236391168 + 20480}
 GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2425076480 + 236391168}
 # DRAM bytes (read + write) per step of the FP64 QR trailing-update GEMMs
-# (k_gemm<double>), from ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum
-# -k regex:"k_gemm<double"; none while no capture covers the current step.
-# The last capture (27.58 GB read + 6.93 GB written) also counted the FP64
-# R^{-1} products, which the FP64 solve of this workload now forms in FP32.
-GEMM64_TRAFFIC = {}
+# (k_gemm<double>): the sum over the 472 launches of one step of ncu's
+# dram__bytes_read.sum (27379879168) and dram__bytes_write.sum (6929454592)
+GEMM64_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 27379879168 + 6929454592}
 
 
 class ClockSampler:
@@ -508,8 +506,7 @@ def run_ours(args, name):
     roofline = {"kernel": "k_gemm<double> (FP64 QR trailing update)", "bound": "alu",
                 "achieved": gemm_flops / (g64 * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": gemm_flops / (g64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": GEMM64_TRAFFIC.get(name),
-                "traffic_scope": "bytes per step, the k_gemm<double> QR-update launches; null until re-captured "
-                                 "(the last capture also counted FP64 R^-1 products no longer in the step)",
+                "traffic_scope": "bytes per step, summed over the k_gemm<double> QR-update launches of one step",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (DFMA loop measured 1.00)",
                 "flops_per_step": gemm_flops, "ms_per_step": g64}
     sketch_roofline = {"kernel": ("premix + hash stage (k_wht_p1_tma, k_wht_fx, k_sketch_qa_f64acc)"
