@@ -99,10 +99,12 @@ typedef struct {
                           /* (a multiple of 32, <= 128) kept in L2; 0 = auto            */
   /* Launch parameters of Steps 4-5 (the result is the same up to rounding; the
      Python autotuner times them per problem shape and caches the fastest):    */
-  int32_t lsqr_pass;      /* dense LSQR pass over A: 0 = auto (4 for 2048 < d <= 4096, */
-                          /* else 1), 1 = register-                                     */
+  int32_t lsqr_pass;      /* dense LSQR pass over A: 0 = auto (4 for d <= 2048, 5 for  */
+                          /* 2048 < d <= 4096, else 1), 1 = register-                   */
                           /* blocked rows, 2 = TMA-staged row ring, 3 = row per warp,   */
-                          /* 4 = register-blocked with twice the rows per row group     */
+                          /* 4 = register-blocked with twice the rows per row group,    */
+                          /* 5 = register-blocked with the next row group's loads       */
+                          /* issued before this group's reductions (d <= 4096)          */
   int32_t lsqr_ctas;      /* CTAs of that pass, i.e. row tiles of ceil(n / ctas) rows; */
                           /* 0 = auto (min(152, n / 16)); raised to n / 16384 at least  */
   int32_t graphs;         /* 1: each chunk of 8 LSQR (or CG) iterations is recorded    */

@@ -5,7 +5,8 @@ Steps 4-5 and the batched entry point run but not what they compute:
 
 - ``lsqr_pass``: which kernel runs the dense LSQR pass. 1 is register-blocked
   rows, 2 a TMA-staged row ring, 3 one row per warp, 4 register-blocked rows
-  with twice the rows between the two barriers of a row group.
+  with twice the rows between the two barriers of a row group, 5
+  register-blocked rows with the next row group's loads in flight.
 - ``lsqr_ctas``: its row tiles, i.e. the number of CTAs. 0 is the library
   default.
 - ``graphs``: replay each chunk of iterations as a CUDA graph (1) or launch
@@ -35,7 +36,7 @@ import numpy as np
 
 # Candidate values per field, the default first.
 SPACE_BATCHED = {
-    "lsqr_pass": (1, 2, 3, 4),
+    "lsqr_pass": (1, 2, 3, 4, 5),
     "lsqr_ctas": (0, 19, 38, 76, 304, 608),  # few CTAs: passes of different problems share the SMs
     "graphs": (0, 1),
     "streams": (8, 1, 2, 4, 16),

@@ -94,7 +94,7 @@ static ski_status check_matrix(const ski_matrix* A) {
 }
 
 static bool launch_opts_ok(const ski_opts* o) {
-  return o->lsqr_pass >= 0 && o->lsqr_pass <= 4 && o->lsqr_ctas >= 0 && (o->graphs == 0 || o->graphs == 1) &&
+  return o->lsqr_pass >= 0 && o->lsqr_pass <= 5 && o->lsqr_ctas >= 0 && (o->graphs == 0 || o->graphs == 1) &&
          (o->batch_lsqr == 0 || o->batch_lsqr == 1);
 }
 

@@ -97,8 +97,10 @@ __global__ void k_split_a(int64_t n, int64_t d, const double* __restrict__ A, in
 }
 
 // K2: double-float fused pass.  Thread tid owns columns tid + k*512 (k < CPT).
-// bid: the CTA's row block (blockIdx.x, or a work item's block in the grouped form)
-template <int CPT, int RR>
+// bid: the CTA's row block (blockIdx.x, or a work item's block in the grouped
+// form); PF: two row groups in registers, the next one's loads issued before
+// this one's reductions (LSQR pass variant 5)
+template <int CPT, int RR, bool PF = false>
 __device__ __forceinline__ void fused_df_body(const DfArgs& f, int64_t bid) {
   constexpr int NT = 512, NW = NT / 32;
   __shared__ float2 red[RR][NW];
@@ -142,8 +144,8 @@ __device__ __forceinline__ void fused_df_body(const DfArgs& f, int64_t bid) {
     for (int64_t j = r0 + tid; j < r1; j += NT) s_u[j - r0] = f.u[j];
   __syncthreads();
   double tt = 0.0;
-  for (int64_t j0 = r0; j0 < r1; j0 += RR) {
-    float2 a[RR][CPT];
+  // rows j0 .. j0 + RR - 1 of A2 into registers
+  auto load = [&](float2 (&a)[RR][CPT], int64_t j0) {
 #pragma unroll
     for (int r = 0; r < RR; ++r)
 #pragma unroll
@@ -151,6 +153,9 @@ __device__ __forceinline__ void fused_df_body(const DfArgs& f, int64_t bid) {
         const int64_t c = tid + (int64_t)k * NT;
         a[r][k] = (j0 + r < r1 && c < f.d) ? __ldcs(&f.A2[(j0 + r) * f.ld2 + c]) : make_float2(0.f, 0.f);
       }
+  };
+  // one row group: t_j for its rows, then their share of A^T t
+  auto process = [&](const float2 (&a)[RR][CPT], int64_t j0) {
 #pragma unroll
     for (int r = 0; r < RR; ++r) {
       float h = 0.f, l = 0.f;
@@ -190,6 +195,25 @@ __device__ __forceinline__ void fused_df_body(const DfArgs& f, int64_t bid) {
 #pragma unroll
       for (int k = 0; k < CPT; ++k) df_mac(ah_acc[k], al_acc[k], a[r][k].x, a[r][k].y, t.x, t.y);
     }
+  };
+  if constexpr (!PF) {
+    for (int64_t j0 = r0; j0 < r1; j0 += RR) {
+      float2 a[RR][CPT];
+      load(a, j0);
+      process(a, j0);
+    }
+  } else {
+    // two register buffers: the next group's loads are in flight while this
+    // group's reductions and barriers run
+    float2 a0[RR][CPT], a1[RR][CPT];
+    if (r0 < r1) load(a0, r0);
+    for (int64_t j0 = r0; j0 < r1; j0 += 2 * RR) {
+      if (j0 + RR < r1) load(a1, j0 + RR);
+      process(a0, j0);
+      if (j0 + RR >= r1) break;
+      if (j0 + 2 * RR < r1) load(a0, j0 + 2 * RR);
+      process(a1, j0 + RR);
+    }
   }
   // partial A^T t of this CTA: (A2 * 2^sA)^T (t2 * 2^st)
 #pragma unroll
@@ -209,6 +233,8 @@ __device__ __forceinline__ void fused_df_body(const DfArgs& f, int64_t bid) {
 }
 template <int CPT, int RR>
 __global__ void __launch_bounds__(512) k_fused_df(DfArgs f) { fused_df_body<CPT, RR>(f, blockIdx.x); }
+template <int CPT, int RR>
+__global__ void __launch_bounds__(512) k_fused_df_pf(DfArgs f) { fused_df_body<CPT, RR, true>(f, blockIdx.x); }
 
 // K2, TMA-staged: rows of A2 stream into a shared-memory ring by 1-D bulk
 // copies (cp.async.bulk, completion on an mbarrier), one producer thread
@@ -709,11 +735,11 @@ __global__ void __launch_bounds__(256) k_trmv_upper_update(int64_t d, const doub
 }
 
 // ---- grouped form: one launch per kernel for every problem in flight
-template <int CPT, int RR>
+template <int CPT, int RR, bool PF>
 __global__ void __launch_bounds__(512) k_group_df(const LsqrGroupJob* __restrict__ jobs,
                                                   const LsqrGroupItem* __restrict__ items) {
   const LsqrGroupItem it = items[blockIdx.x];
-  fused_df_body<CPT, RR>(jobs[it.job].df, it.blk);
+  fused_df_body<CPT, RR, PF>(jobs[it.job].df, it.blk);
 }
 __global__ void __launch_bounds__(256) k_group_reduce(const LsqrGroupJob* __restrict__ jobs,
                                                       const LsqrGroupItem* __restrict__ items) {
@@ -746,8 +772,9 @@ __global__ void k_group_scalars(const LsqrGroupJob* __restrict__ jobs, int njobs
 
 }  // namespace
 
-// Classes of the register-blocked pass (the default table of
-// ski_fused_df_launch): columns per thread 1, 2, 4, 8, 16
+// Classes of the register-blocked pass as ski_fused_df_launch picks it by
+// default (the same rows per group, so the same summation order): columns per
+// thread 1, 2, 4 with twice the rows, 8 with prefetch, 16
 int ski_df_group_class(int64_t d) {
   const int64_t cpt = ski_cdiv(d, 512);
   return cpt <= 1 ? 0 : cpt <= 2 ? 1 : cpt <= 4 ? 2 : cpt <= 8 ? 3 : 4;
@@ -757,20 +784,20 @@ ski_status ski_group_df_launch(int cls, const LsqrGroupJob* jobs, const LsqrGrou
                                size_t smem, cudaStream_t st) {
   if (nitems <= 0) return SKI_OK;
   if (smem > 200 * 1024) return SKI_EINVAL;
-#define SKI_GDF_CASE(K, C, R)                                                                      \
+#define SKI_GDF_CASE(K, C, R, P)                                                                   \
   if (cls == K) {                                                                                  \
     if (smem > 48 * 1024)                                                                          \
-      SKI_CUDA_TRY(cudaFuncSetAttribute(k_group_df<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                        ski_smem_cap((const void*)k_group_df<C, R>)));             \
-    k_group_df<C, R><<<(unsigned)nitems, 512, smem, st>>>(jobs, items);                            \
+      SKI_CUDA_TRY(cudaFuncSetAttribute(k_group_df<C, R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                        ski_smem_cap((const void*)k_group_df<C, R, P>)));          \
+    k_group_df<C, R, P><<<(unsigned)nitems, 512, smem, st>>>(jobs, items);                         \
     SKI_LAUNCH_CHECK();                                                                            \
     return SKI_OK;                                                                                 \
   }
-  SKI_GDF_CASE(0, 1, 8)
-  SKI_GDF_CASE(1, 2, 8)
-  SKI_GDF_CASE(2, 4, 4)
-  SKI_GDF_CASE(3, 8, 4)
-  SKI_GDF_CASE(4, 16, 1)
+  SKI_GDF_CASE(0, 1, 16, false)
+  SKI_GDF_CASE(1, 2, 16, false)
+  SKI_GDF_CASE(2, 4, 8, false)
+  SKI_GDF_CASE(3, 8, 2, true)
+  SKI_GDF_CASE(4, 16, 1, false)
 #undef SKI_GDF_CASE
   return SKI_EINVAL;
 }
@@ -880,9 +907,29 @@ ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
     SKI_LAUNCH_CHECK();                                                                          \
     return SKI_OK;                                                                               \
   }
-  // auto: twice the rows per row group where it was measured faster (d in
-  // (2048, 4096]: the LSQR stage of a 50000 x 4000 solve 36.1 -> 33.1 ms)
-  if (f.variant == 4 || (f.variant == 0 && cpt > 4 && cpt <= 8)) {  // twice the rows between the two barriers of a row group
+  // variant 5: prefetching form (two register buffers of RR rows); the auto
+  // choice for d in (2048, 4096], where it was measured fastest (LSQR stage of
+  // 50000 x 4000: 33.3 -> 32.1 ms; 200000 x 4000: 111.2 -> 108.1 ms)
+  if (f.variant == 5 || (f.variant == 0 && cpt > 4 && cpt <= 8)) {
+#define SKI_DFP_CASE(C, R)                                                                       \
+    if (cpt <= C) {                                                                              \
+      if (smem > 48 * 1024)                                                                      \
+        SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df_pf<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                          ski_smem_cap((const void*)k_fused_df_pf<C, R>)));      \
+      k_fused_df_pf<C, R><<<f.nblk, 512, smem, st>>>(f);                                         \
+      SKI_LAUNCH_CHECK();                                                                        \
+      return SKI_OK;                                                                             \
+    }
+    SKI_DFP_CASE(1, 8)
+    SKI_DFP_CASE(2, 4)
+    SKI_DFP_CASE(4, 2)
+    SKI_DFP_CASE(8, 2)
+#undef SKI_DFP_CASE
+  }
+  // auto: twice the rows per row group for d <= 2048, where it was measured
+  // faster (LSQR stage of 50000 x 2000: 26.0 -> 19.5 ms; 30000 x 1000: 10.1 ->
+  // 9.7 ms)
+  if (f.variant == 4 || (f.variant == 0 && cpt <= 4)) {  // twice the rows between the two barriers of a row group
     SKI_DF_CASE(1, 16)
     SKI_DF_CASE(2, 16)
     SKI_DF_CASE(4, 8)

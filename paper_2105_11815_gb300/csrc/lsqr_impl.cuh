@@ -67,7 +67,8 @@ struct DfArgs {
   int nblk;
   int64_t rows_per;
   LsqrScalars* sc;
-  int variant;  // 0, 1: register-blocked rows; 2: TMA-staged row ring; 3: row per warp
+  int variant;  // 0, 1: register-blocked rows; 2: TMA-staged row ring; 3: row per warp;
+                // 4: register-blocked, twice the rows; 5: register-blocked with prefetch
 };
 
 // A2 = the (hi, lo) split of A * 2^-sA; with cmap, column c of A2 is column

@@ -116,7 +116,7 @@ def test_argument_errors_before_launch(lib):
     assert L.ski_solve_adjoint(ctypes.byref(wide), x, x, x, 8193, x, x, 8193, x, ctypes.byref(ow), None, x, 1 << 40,
                                None) == 1
     for field, v in (("premix_slab", -1), ("streams", -1), ("s", 0), ("qr_dtype", 2), ("it_max", -1),
-                     ("lsqr_pass", 5), ("lsqr_pass", -1), ("lsqr_ctas", -1), ("graphs", 2), ("batch_lsqr", 2),
+                     ("lsqr_pass", 6), ("lsqr_pass", -1), ("lsqr_ctas", -1), ("graphs", 2), ("batch_lsqr", 2),
                      ("batch_lsqr", -1)):
         o2 = lib.ski_opts_default(m=20, s=1)
         setattr(o2, field, v)

@@ -37,7 +37,7 @@ def test_chunk_graphs_match_direct_launches():
     assert (i0.iters, a0.iters) == (i1.iters, a1.iters)
 
 
-@pytest.mark.parametrize("lsqr_pass,lsqr_ctas", [(1, 0), (2, 0), (3, 0), (1, 7), (2, 300), (3, 1)])
+@pytest.mark.parametrize("lsqr_pass,lsqr_ctas", [(1, 0), (2, 0), (3, 0), (1, 7), (2, 300), (3, 1), (4, 0), (5, 0), (5, 7), (5, 300)])
 def test_lsqr_pass_variants_agree(lsqr_pass, lsqr_ctas):
     torch, pkg = cuda()
     x0, db0, i0, _ = _solve_and_adjoint(torch, pkg)
