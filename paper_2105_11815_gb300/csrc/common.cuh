@@ -7,6 +7,9 @@
 #include <stdint.h>
 #include <stddef.h>
 #include <algorithm>
+#include <mutex>
+#include <set>
+#include <tuple>
 #include "../../include/skills.h"
 
 #define SKI_CUDA_TRY(expr)                                   \
@@ -38,6 +41,29 @@ static inline cudaStream_t ski_stream(void* s) { return reinterpret_cast<cudaStr
 // the device's opt-in maximum less the kernel's static shared memory.  A cap
 // only permits, so one constant per kernel keeps concurrent host threads from
 // lowering it under each other's in-flight launches (a per-launch cap races).
+// cudaFuncSetAttribute(fn, attr, value()) once per (device, kernel, attribute)
+// and call site: every caller passes the same value for a given kernel, so
+// later calls, from any host thread, skip the driver (whose calls serialise
+// the threads that launch the problems of a batch).
+template <class F>
+inline cudaError_t ski_attr_once(const void* fn, cudaFuncAttribute attr, F value) {
+  static std::mutex mu;
+  static std::set<std::tuple<int, const void*, int>> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
+  const auto key = std::make_tuple(dev, fn, (int)attr);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(key)) return cudaSuccess;
+  }
+  const cudaError_t e = cudaFuncSetAttribute(fn, attr, value());
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(mu);
+    done.insert(key);
+  }
+  return e;
+}
+
 static inline int ski_smem_cap(const void* fn) {
   int dev = 0, optin = 0;
   cudaFuncAttributes a;

@@ -368,8 +368,8 @@ ski_status launch(const float* A, int64_t lda, const float* B, int64_t ldb, int 
   if (!make_map(&ta, A, M, K, lda, BM) || !make_map(&tb, B, N, K, ldb, BN)) return SKI_ECUDA;
   const size_t smem = sizeof(TcSmem<BN, STAGES, SPLIT>) + 1024;
   static_assert(sizeof(TcSmem<BN, STAGES, SPLIT>) + 1024 <= 227 * 1024, "shared memory");
-  SKI_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+  SKI_CUDA_TRY(ski_attr_once((const void*)k_gemm_tc<BN, STAGES, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              [&] { return (int)smem; }));
   const int kchunk = (int)ski_round_up(ski_cdiv(K, splits), BK);
   dim3 grid((unsigned)ski_cdiv(M, BM), (unsigned)ski_cdiv(N, BN), (unsigned)splits);
   k_gemm_tc<BN, STAGES, SPLIT><<<grid, NTHR, smem, st>>>(ta, tb, M, N, K, kchunk, C, ldc, c_zstride, mode, err);

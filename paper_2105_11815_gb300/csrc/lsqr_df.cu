@@ -787,8 +787,8 @@ ski_status ski_group_df_launch(int cls, const LsqrGroupJob* jobs, const LsqrGrou
 #define SKI_GDF_CASE(K, C, R, P)                                                                   \
   if (cls == K) {                                                                                  \
     if (smem > 48 * 1024)                                                                          \
-      SKI_CUDA_TRY(cudaFuncSetAttribute(k_group_df<C, R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                        ski_smem_cap((const void*)k_group_df<C, R, P>)));          \
+      SKI_CUDA_TRY(ski_attr_once((const void*)k_group_df<C, R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                        [&] { return ski_smem_cap((const void*)k_group_df<C, R, P>); }));          \
     k_group_df<C, R, P><<<(unsigned)nitems, 512, smem, st>>>(jobs, items);                         \
     SKI_LAUNCH_CHECK();                                                                            \
     return SKI_OK;                                                                                 \
@@ -859,8 +859,8 @@ ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
     if (sm <= 200 * 1024 && f.variant == 3) {
 #define SKI_DFR_CASE(C)                                                                                  \
       if (cpt <= C) {                                                                                    \
-        SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df_rows<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                          ski_smem_cap((const void*)k_fused_df_rows<C>)));               \
+        SKI_CUDA_TRY(ski_attr_once((const void*)k_fused_df_rows<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                          [&] { return ski_smem_cap((const void*)k_fused_df_rows<C>); }));               \
         k_fused_df_rows<C><<<f.nblk, 512, sm, st>>>(f);                                                  \
         SKI_LAUNCH_CHECK();                                                                              \
         return SKI_OK;                                                                                   \
@@ -882,8 +882,8 @@ ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
       for (int ns = 3; ns >= 2; --ns) {                                                               \
         const size_t sm = (size_t)ns * R * rowb + ub;                                                 \
         if (sm <= budget) {                                                                           \
-          SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df_tma<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                            ski_smem_cap((const void*)k_fused_df_tma<C, R>)));        \
+          SKI_CUDA_TRY(ski_attr_once((const void*)k_fused_df_tma<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                            [&] { return ski_smem_cap((const void*)k_fused_df_tma<C, R>); }));        \
           k_fused_df_tma<C, R><<<f.nblk, 512, sm, st>>>(f, ns);                                       \
           SKI_LAUNCH_CHECK();                                                                         \
           return SKI_OK;                                                                              \
@@ -901,8 +901,8 @@ ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
 #define SKI_DF_CASE(C, R)                                                                        \
   if (cpt <= C) {                                                                                \
     if (smem > 48 * 1024)                                                                        \
-      SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                        ski_smem_cap((const void*)k_fused_df<C, R>)));           \
+      SKI_CUDA_TRY(ski_attr_once((const void*)k_fused_df<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                        [&] { return ski_smem_cap((const void*)k_fused_df<C, R>); }));           \
     k_fused_df<C, R><<<f.nblk, 512, smem, st>>>(f);                                              \
     SKI_LAUNCH_CHECK();                                                                          \
     return SKI_OK;                                                                               \
@@ -914,8 +914,8 @@ ski_status ski_fused_df_launch(const DfArgs& f0, cudaStream_t st) {
 #define SKI_DFP_CASE(C, R)                                                                       \
     if (cpt <= C) {                                                                              \
       if (smem > 48 * 1024)                                                                      \
-        SKI_CUDA_TRY(cudaFuncSetAttribute(k_fused_df_pf<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                          ski_smem_cap((const void*)k_fused_df_pf<C, R>)));      \
+        SKI_CUDA_TRY(ski_attr_once((const void*)k_fused_df_pf<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                          [&] { return ski_smem_cap((const void*)k_fused_df_pf<C, R>); }));      \
       k_fused_df_pf<C, R><<<f.nblk, 512, smem, st>>>(f);                                         \
       SKI_LAUNCH_CHECK();                                                                        \
       return SKI_OK;                                                                             \

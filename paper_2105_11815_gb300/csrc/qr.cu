@@ -848,6 +848,80 @@ QrStreams* qr_streams() {
   return q.ok ? &q : nullptr;
 }
 
+// cluster panels: 16 CTAs (non-portable size) when the device runs such a
+// cluster with the largest slab, else 8.  FP32, and FP64 panels of at most
+// kClusterRowsF64 rows whose slabs fit in shared memory (about 12400 rows with
+// 16 CTAs).  A tall FP64 panel does its rank-1 updates on the 1/64-rate FP64
+// pipe, which 64 SMs (grid-barrier kernel) finish sooner than 16.  But the
+// FP64 QR is bound by the trailing update that runs beside the panel, and a
+// 16-CTA cluster leaves it 136 SMs instead of 88: the FP64 QR of 8000 x 4001
+// took 245.5 ms with cluster panels against 250.3 ms with grid-barrier panels
+// above 4096 rows.  A short panel is bound by the per-column synchronisation,
+// which the cluster barrier does faster; and 16-CTA clusters run beside the
+// other streams' work, where a cooperative grid waits for 64 free SMs.
+constexpr int kPanelWarps = 32;  // 16 hid too little of each step's row-loop latency (36.5 -> 32.1 ms at 8000 x 4000)
+// FP32 panels: Cholesky QR twice and Householder reconstruction in the
+// cluster (two cluster reductions per panel instead of one barrier per
+// column), when its work matrices and slab fit in shared memory
+constexpr size_t kCholSmem = 200 * 1024;
+struct QrSetup {
+  bool coop = false, cluster_ok = false, chol_ok = false;
+  int CL = 0;
+};
+template <class T>
+const QrSetup& qr_setup() {
+  static std::mutex mu;
+  static QrSetup su[8];
+  static bool have[8] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 8) {
+    cudaGetLastError();
+    static const QrSetup none;
+    return none;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (have[dev]) return su[dev];
+  QrSetup& q = su[dev];
+  int can = 0;
+  q.coop = cudaDeviceGetAttribute(&can, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && can != 0;
+  constexpr int CNW = kPanelWarps;
+  const size_t big = (size_t)(200 * 1024 + 2 * PW * sizeof(T));
+  if (cudaFuncSetAttribute(k_panel_cluster<T, CNW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess &&
+      cudaFuncSetAttribute(k_panel_cluster<T, CNW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big) ==
+          cudaSuccess) {
+    for (int cand : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cand;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(cand);
+      cfg.blockDim = dim3(32 * CNW);
+      cfg.dynamicSmemBytes = big;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclus = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclus, k_panel_cluster<T, CNW>, &cfg) == cudaSuccess && nclus >= 1) {
+        q.CL = cand;
+        q.cluster_ok = true;
+        break;
+      }
+    }
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (q.cluster_ok &&
+        cudaFuncSetAttribute(k_panel_chol<CNW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+        cudaFuncSetAttribute(k_panel_chol<CNW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmem) ==
+            cudaSuccess)
+      q.chol_ok = true;
+  }
+  cudaGetLastError();
+  have[dev] = true;
+  return q;
+}
+
 template <class T>
 ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, double* R, int64_t ldr, double* qtsb,
                    SkiArena& ar, cudaStream_t caller, double* gemm_ms, bool split3) {
@@ -868,74 +942,20 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
   QrBufs<T> bf = qr_carve<T>(ar, m, ncols);
   if (!ar.ok() || !bf.err) return SKI_ENOMEM;
   const int64_t ldt = q.ldt;
-  // cooperative persistent panels when every panel CTA can be co-resident
-  bool coop = false;
-  {
-    int dev = 0, can = 0, sms = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&can, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-      coop = can != 0;
-    cudaGetLastError();
-  }
+  // launch setup of this device (cooperative panels, cluster size, the FP32
+  // Cholesky panel), queried once per process and device: the attribute and
+  // occupancy calls take the driver's process-wide lock, which the host threads
+  // of a batch would otherwise meet at every factorisation
+  const QrSetup& su = qr_setup<T>();
+  const bool coop = su.coop;
   const int64_t max_slab_rows = (200 * 1024) / ((NB + 1) * (int64_t)sizeof(T));
-  // cluster panels: 16 CTAs (non-portable size) when the device runs such a
-  // cluster with the largest slab, else 8
-  constexpr int CNW = 32;  // 32 warps: 16 hid too little of each step's row-loop latency (36.5 -> 32.1 ms at 8000 x 4000)
-  int CL = 0;
-  bool cluster_ok = false;
-  // FP32, and FP64 panels of at most kClusterRowsF64 rows whose slabs fit in
-  // shared memory (about 12400 rows with 16 CTAs).  A tall FP64 panel does its
-  // rank-1 updates on the 1/64-rate FP64 pipe, which 64 SMs (grid-barrier
-  // kernel) finish sooner than 16.  But the FP64 QR is bound by the trailing
-  // update that runs beside the panel, and a 16-CTA cluster leaves it 136
-  // SMs instead of 88: the FP64 QR of 8000 x 4001 took 245.5 ms with cluster
-  // panels against 250.3 ms with grid-barrier panels above 4096 rows.  A
-  // short panel is bound by the per-column synchronisation, which the cluster
-  // barrier does faster; and 16-CTA clusters run beside the other streams'
-  // work, where a cooperative grid waits for 64 free SMs.
-  if (sizeof(T) == 4 || m <= kClusterRowsF64) {
-    const size_t big = (size_t)(200 * 1024 + 2 * PW * sizeof(T));
-    if (cudaFuncSetAttribute(k_panel_cluster<T, CNW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-            cudaSuccess &&
-        cudaFuncSetAttribute(k_panel_cluster<T, CNW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big) ==
-            cudaSuccess) {
-      for (int cand : {16, 8}) {
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = cand;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(cand);
-        cfg.blockDim = dim3(32 * CNW);
-        cfg.dynamicSmemBytes = big;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nclus = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclus, k_panel_cluster<T, CNW>, &cfg) == cudaSuccess && nclus >= 1) {
-          CL = cand;
-          cluster_ok = true;
-          break;
-        }
-      }
-    }
-    cudaGetLastError();
-  }
-  // FP32 panels: Cholesky QR twice and Householder reconstruction in the
-  // cluster (two cluster reductions per panel instead of one barrier per
-  // column), when its work matrices and slab fit in shared memory
+  constexpr int CNW = kPanelWarps;
+  const int CL = su.CL;
+  // FP32, and FP64 panels of at most kClusterRowsF64 rows, take the cluster kernel
+  const bool cluster_ok = su.cluster_ok && (sizeof(T) == 4 || m <= kClusterRowsF64);
   constexpr size_t kCholMats = (size_t)(2 * PW + (10 + GRAM_WARPS) * NB * (NB + 1) + NB) * sizeof(float);
-  constexpr size_t kCholSmemMax = 200 * 1024;
-  bool chol_ok = false;
-  if constexpr (sizeof(T) == 4) {
-    if (cluster_ok &&
-        cudaFuncSetAttribute(k_panel_chol<CNW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-        cudaFuncSetAttribute(k_panel_chol<CNW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmemMax) ==
-            cudaSuccess)
-      chol_ok = true;
-    cudaGetLastError();
-  }
+  constexpr size_t kCholSmemMax = kCholSmem;
+  const bool chol_ok = sizeof(T) == 4 && cluster_ok && su.chol_ok;
   SKI_CUDA_TRY(cudaMemsetAsync(bf.err, 0, sizeof(int), st));
   SKI_CUDA_TRY(cudaMemsetAsync(bf.gb, 0, sizeof(GridBar), st));
   {
@@ -1009,8 +1029,6 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
         cfg.stream = st;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        SKI_CUDA_TRY(cudaFuncSetAttribute(k_panel_cluster<T, CNW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(200 * 1024 + 2 * PW * sizeof(T))));
         SKI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_cluster<T, CNW>, pc));
         SKI_LAUNCH_CHECK();
         done_panel = true;

@@ -59,3 +59,22 @@ def test_grouped_batch_with_csr_problems():
         assert ig[i].status == 0 and ig[i].iters == io[i].iters and np.array_equal(xg[i], xo[i]), i
     for i, A, b in host:
         assert olsqr.residual_metric_dd(A, b, xg[i]) <= 1e-10
+
+
+def test_grouped_batch_across_every_pass_class():
+    # d = 300, 800, 1500, 3000: the four register-blocked classes of the LSQR
+    # pass (columns per thread 1, 2, 4 with twice the rows, 8 with prefetch)
+    # in one group, against each problem's own launches
+    torch, pkg = cuda()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(17)
+    shapes = [(9000, 300), (10000, 800), (12000, 1500), (14000, 3000)]
+    As = [torch.randn(n, d, generator=g, device="cuda", dtype=torch.float64) for n, d in shapes]
+    bs = [torch.randn(n, generator=g, device="cuda", dtype=torch.float64) for n, _ in shapes]
+    mats = [pkg.dense_matrix(a) for a in As]
+    base = dict(m=-2000, s=1, seed=3, tol=1e-10, tau_r=1e-12, streams=4)
+    xg, ig = _solve(torch, pkg, mats, bs, shapes, pkg.ski_opts_default(batch_lsqr=1, **base))
+    xo, io = _solve(torch, pkg, mats, bs, shapes, pkg.ski_opts_default(batch_lsqr=0, **base))
+    for i in range(len(shapes)):
+        assert ig[i].status == 0 and ig[i].iters == io[i].iters and np.array_equal(xg[i], xo[i]), i
+        assert olsqr.residual_metric_dd(As[i].cpu().numpy(), bs[i].cpu().numpy(), xg[i]) <= 1e-10
