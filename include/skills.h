@@ -119,11 +119,13 @@ typedef struct {
                           /* perturb > 0; 1 = column-pivoted QR (SA V = Q R with        */
                           /* R = [R11 R12; 0 0], R11 p x p), Steps 3-5 on W = A V1      */
                           /* R11^{-1}; dense A only (CSR keeps the behaviour of 0);     */
-                          /* 2 (CSR A, FP64 factor) = R from a sparse sketch (Section   */
-                          /* 6): SA kept in CSR, R the Cholesky factor of SA^T SA       */
-                          /* (R^T R = SA^T SA, positive diagonal), Q^T Sb =             */
-                          /* R^{-T} SA^T Sb, with the Householder QR of the dense SA    */
-                          /* when the Cholesky breaks down; then as 0                   */
+                          /* 2 = R the Cholesky factor of SA^T SA (R^T R = SA^T SA,     */
+                          /* positive diagonal) and Q^T Sb = R^{-T} SA^T Sb: for CSR A  */
+                          /* (FP64 factor) from a sparse SA kept in CSR (Section 6),    */
+                          /* for dense A from the dense sketch in the QR precision;     */
+                          /* the Householder QR when the Cholesky breaks down or the    */
+                          /* factor's diagonal ratio passes 2^23 (FP64) / 2^9 (FP32);   */
+                          /* then as 0                                                  */
   int32_t batch_lsqr;     /* ski_solve_batched, dense problems: 0 = each problem's own  */
                           /* Step 4 launches on its stream; 1 = Step 4 of all problems  */
                           /* in flight grouped, one launch per kernel of an iteration   */

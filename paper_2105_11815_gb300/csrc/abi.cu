@@ -487,13 +487,23 @@ bool weak_preconditioner(double test, long long iters, double tau_r, int64_t bud
 }
 
 // Bytes of the phase region for the sketch / QR / trinv precisions of o.
-// Step 2 from the Gram matrix of a sparse SA (factorization 2: CSR A, FP64)
+// Step 2 from the Gram matrix SA^T SA (factorization 2): of a sparse SA for
+// CSR A (FP64), of the dense sketch for dense A (any QR precision)
 bool gram_path(const ski_matrix* A, const ski_opts* o) {
-  return o->factorization == 2 && A->kind == SKI_CSR && o->qr_dtype == SKI_F64 && o->sketch_dtype == SKI_F64;
+  if (o->factorization != 2) return false;
+  if (A->kind == SKI_CSR) return o->qr_dtype == SKI_F64 && o->sketch_dtype == SKI_F64;
+  return true;
 }
 size_t gram_stage_bytes(const ski_matrix* A, const ski_opts* o) {
-  return gram_path(A, o) ? ski_gram_ws_bytes(A->n, A->d, A->nnz, o->s, o->m) : 0;
+  if (!gram_path(A, o)) return 0;
+  if (A->kind == SKI_CSR) return ski_gram_ws_bytes(A->n, A->d, A->nnz, o->s, o->m);
+  return ski_gram_dense_ws_bytes(o->m, A->d, o->qr_dtype);
 }
+// Largest max|r_ii| / min|r_ii| of a factor from the Gram matrix kept as the
+// preconditioner: its relative error grows like kappa(SA)^2 u, so the limit
+// is about u^{-1/2} / 8 of the Gram's precision; past it Step 2 is redone by
+// the Householder QR in the same precision.
+double gram_ratio_limit(int32_t qr_prec) { return qr_prec == SKI_F64 ? 0x1p23 : 0x1p9; }
 
 size_t region_need(const ski_matrix* A, const ski_opts* o) {
   const int64_t d = A->d, m = o->m, ncols = d + 1, ld_sa = ski_round_up(ncols, 4);
@@ -856,8 +866,11 @@ static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opt
       gram_used = false;
       if (gram_path(A, of) && !P.sh) {
         SkiArena gar{P.stage, P.stage_bytes, 0, false};
-        SKI_TRY(ski_gram_chol_run(A, of->seed, of->s, of->hash_kind, P.m, (const double*)P.SA + d, P.ld_sa, P.R, d,
-                                  P.qtsb, &done, gar, st));
+        if (P.csr)
+          SKI_TRY(ski_gram_chol_run(A, of->seed, of->s, of->hash_kind, P.m, (const double*)P.SA + d, P.ld_sa, P.R,
+                                    d, P.qtsb, &done, gar, st));
+        else
+          SKI_TRY(ski_gram_dense_run(P.SAq, P.ld_sa, P.m, d, P.qr_prec, P.R, d, P.qtsb, &done, gar, st));
         gram_used = done;
       }
       SkiArena qar{P.stage, P.stage_bytes, 0, false};
@@ -868,6 +881,13 @@ static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opt
     SKI_CUDA_TRY(cudaEventRecord(fe.e[2], st));
     bool nonfinite = false;
     SKI_TRY(rank_from_diag(d, P.R, d, o->rcond, st, &rank, &nonfinite, &rdiag_ratio));
+    if (gram_used && (nonfinite || rank < d || !(rdiag_ratio <= gram_ratio_limit(P.qr_prec)))) {
+      // too ill-conditioned for the Gram matrix's precision: Householder QR
+      gram_used = false;
+      SkiArena qar{P.stage, P.stage_bytes, 0, false};
+      SKI_TRY(ski_qr_run(P.m, d, 1, P.SAq, P.ld_sa, P.qr_prec, P.R, d, P.qtsb, qar, st, info ? &gm : nullptr));
+      SKI_TRY(rank_from_diag(d, P.R, d, o->rcond, st, &rank, &nonfinite, &rdiag_ratio));
+    }
     int perr = 0;
     SKI_CUDA_TRY(cudaMemcpyAsync(&perr, P.perr, sizeof(int), cudaMemcpyDeviceToHost, st));
     SKI_CUDA_TRY(cudaStreamSynchronize(st));

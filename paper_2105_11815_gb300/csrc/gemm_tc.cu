@@ -117,6 +117,7 @@ __device__ __forceinline__ void tf32_split(float* hi_tile, float* lo_tile, int c
 }
 
 // mode 0: C[m * ldc + n] = D; mode 1: C[m * ldc + n] -= D; mode 2: C[n * ldc + m] = D.
+// mode | 4: only the tiles that meet the upper triangle (some m <= n).
 template <int BN, int STAGES, bool SPLIT>
 __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
                                                       const __grid_constant__ CUtensorMap tb, int M, int N, int K,
@@ -131,6 +132,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
   const int kend = min(K, kbeg + kchunk);
   const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
   C += (int64_t)blockIdx.z * c_zstride;
+  if ((mode & 4) && m0 >= n0 + BN) return;  // the whole tile is below the diagonal (CTA-uniform)
+  mode &= 3;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -398,7 +401,8 @@ ski_status dispatch(const float* A, int64_t lda, const float* B, int64_t ldb, in
 // D = A B^T (TF32 tensor cores, FP32 accumulate).  A: M x K, B: N x K, both
 // row-major (K contiguous) with row strides lda, ldb that are multiples of 4
 // and 16-byte aligned bases.  mode 0 stores C = D, 1 subtracts C -= D, 2
-// stores the transpose.  splits > 1 splits K, writing partials at
+// stores the transpose; mode | 4 computes only the tiles that meet the upper
+// triangle of C (for a symmetric product whose lower part is not used).  splits > 1 splits K, writing partials at
 // C + z * c_zstride (modes 0 and 2 only).
 ski_status ski_gemm_tf32(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
                          float* C, int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st,

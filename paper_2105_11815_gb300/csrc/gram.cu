@@ -25,9 +25,12 @@
 //  6. c = SA^T Sb by columns of SA, then Q^T Sb = R^{-T} c by blocked forward
 //     substitution (the diagonal block in one CTA, the rest as GEMV updates).
 // On failure the caller factors the dense sketch by Householder QR instead.
+// The same Cholesky serves a dense sketch (ski_gram_dense_run), whose Gram
+// matrix is a GEMM.
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "hash.cuh"
@@ -211,67 +214,137 @@ __global__ void __launch_bounds__(256) k_gram_rows(int64_t d, const int64_t* __r
   for (int64_t c = lo + threadIdx.x; c < hi; c += blockDim.x) G[i * ldg + c] = acc[c - c0];
 }
 
-// ---- 5. Cholesky: diagonal block (nb <= CB) in place, one CTA
-__global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ G, int64_t ldg, int nb,
+// ---- 5. Cholesky: diagonal block (nb <= CB) in place, 256 threads, in
+// bands of RB rows.  Per band: warp 0 factors the RB rows over the block's
+// columns with the band in registers (lane l: columns l and l + 32; pivot
+// r_jj = sqrt(g_jj) and its reciprocal, row j scaled, the band's later rows
+// updated, row entries broadcast by shuffles); then every
+// thread applies the band's rank-RB update to its column of the trailing
+// upper triangle, g_ic -= sum_q r_qi r_qc (threads over columns, rows strided
+// by 4).  The reciprocals 1 / r_jj go to dinv for the block-row solve.
+// *fail is set on a pivot that is not positive (1 is used for it).
+template <class T>
+__global__ void __launch_bounds__(256) k_chol_diag(T* __restrict__ G, int64_t ldg, int nb, T* __restrict__ dinv,
                                                    int* __restrict__ fail) {
-  __shared__ double a[CB][CB + 1];
-  __shared__ double s_inv;
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    const int r = e / nb, c = e % nb;
-    a[r][c] = c >= r ? G[r * ldg + c] : 0.0;
+  constexpr int RB = 8, RS = 256 / CB;  // band rows; row stride of the trailing update
+  __shared__ T a[CB][CB + 1];
+  const int tid = threadIdx.x, tx = tid & (CB - 1), ty = tid / CB;
+  {
+    constexpr int RPT = CB / RS;  // rows per thread
+    T v[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int r = ty + q * RS;
+      v[q] = (r < nb && tx < nb && tx >= r) ? G[r * ldg + tx] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) a[ty + q * RS][tx] = v[q];
   }
   __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    if (threadIdx.x == 0) {
-      double piv = a[j][j];
-      if (!(piv > 0.0)) {
-        atomicExch(fail, 1);
-        piv = 1.0;
+  for (int j0 = 0; j0 < nb; j0 += RB) {
+    const int je = min(nb, j0 + RB);
+    if (tid < 32) {
+      // the band in registers: rows j0 + q, columns tid and tid + 32
+      T v0[RB], v1[RB];
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        v0[q] = a[j0 + q][tid];
+        v1[q] = a[j0 + q][tid + 32];
       }
-      const double r = sqrt(piv);
-      a[j][j] = r;
-      s_inv = 1.0 / r;
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        const int j = j0 + q;
+        if (j < je) {
+          T piv = __shfl_sync(0xffffffffu, j < 32 ? v0[q] : v1[q], j & 31);
+          const bool bad = !(piv > T(0));
+          if (bad) piv = T(1);
+          const T r = sqrt(piv), ir = T(1) / r;
+          if (tid == 0) {
+            if (bad) atomicExch(fail, 1);
+            dinv[j] = ir;
+          }
+          v0[q] = tid == j ? r : (tid > j ? v0[q] * ir : v0[q]);
+          v1[q] = tid + 32 == j ? r : (tid + 32 > j ? v1[q] * ir : v1[q]);
+#pragma unroll
+          for (int p = q + 1; p < RB; ++p) {
+            const int i = j0 + p;
+            const T rji = __shfl_sync(0xffffffffu, i < 32 ? v0[q] : v1[q], i & 31);
+            if (tid >= i) v0[p] = fma(-rji, v0[q], v0[p]);
+            if (tid + 32 >= i) v1[p] = fma(-rji, v1[q], v1[p]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        a[j0 + q][tid] = v0[q];
+        a[j0 + q][tid + 32] = v1[q];
+      }
     }
     __syncthreads();
-    for (int c = j + 1 + threadIdx.x; c < nb; c += blockDim.x) a[j][c] *= s_inv;
-    __syncthreads();
-    const int w = nb - j - 1;  // trailing upper triangle (i, c), j < i <= c
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-      const int i = j + 1 + e / w, c = j + 1 + e % w;
-      if (c >= i) a[i][c] = fma(-a[j][i], a[j][c], a[i][c]);
+    if (tx >= je && tx < nb) {
+      T rc[RB];
+#pragma unroll
+      for (int q = 0; q < RB; ++q) rc[q] = j0 + q < je ? a[j0 + q][tx] : T(0);
+      for (int i = je + ty; i <= tx; i += RS) {
+        T s = a[i][tx];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) s = fma(-(j0 + q < je ? a[j0 + q][i] : T(0)), rc[q], s);
+        a[i][tx] = s;
+      }
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    const int r = e / nb, c = e % nb;
-    if (c >= r) G[r * ldg + c] = a[r][c];
-  }
+  for (int r = ty; r < nb; r += RS)
+    if (tx >= r && tx < nb) G[r * ldg + tx] = a[r][tx];
 }
 
-// R12 = R11^{-T} G12 in place: thread per column of the panel (rows k0..k0+nb)
-__global__ void __launch_bounds__(128) k_chol_panel(double* __restrict__ G, int64_t ldg, int nb, int64_t ncol) {
-  __shared__ double r11[CB][CB + 1];
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    const int r = e / nb, c = e % nb;
-    r11[r][c] = c >= r ? G[r * ldg + c] : 0.0;
+// block row R12 = R11^{-T} G12 in place, one thread per column of G12 (the
+// column in registers, R11 broadcast from shared memory): forward
+// substitution y_i = (g_i - sum_{k<i} r_ki y_k) / r_ii with the reciprocals
+// from the diagonal kernel.  For the tensor-core update the column also goes
+// to row c of Pt (rest x CB, zeros past nb).
+template <class T>
+__global__ void __launch_bounds__(32) k_trsm_row(T* __restrict__ Gk, int64_t ldg, int nb, int64_t rest,
+                                                 const T* __restrict__ dinv, T* __restrict__ Pt) {
+  __shared__ T r[CB][CB];
+  __shared__ T di[CB];
+  const int tid = threadIdx.x;
+#pragma unroll 1
+  for (int i0 = 0; i0 < CB; i0 += 16) {
+    T v[16][2];
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = i0 + u, k = tid + 32 * h;
+        v[u][h] = (i < nb && k > i && k < nb) ? Gk[i * ldg + k] : T(0);
+      }
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) r[i0 + u][tid + 32 * h] = v[u][h];
   }
+  for (int i = tid; i < CB; i += 32) di[i] = i < nb ? dinv[i] : T(0);
   __syncthreads();
-  const int64_t c = nb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // column of the block row
-  if (c >= nb + ncol) return;
-  double y[CB];
+  const int64_t c = blockIdx.x * 32ll + tid;
+  if (c >= rest) return;
+  T g[CB];
+#pragma unroll
+  for (int i = 0; i < CB; ++i) g[i] = i < nb ? Gk[i * ldg + nb + c] : T(0);
 #pragma unroll
   for (int i = 0; i < CB; ++i) {
-    if (i < nb) {
-      double t = G[i * ldg + c];
+    const T y = g[i] * di[i];
+    g[i] = y;
 #pragma unroll
-      for (int k = 0; k < CB; ++k)
-        if (k < i) t = fma(-r11[k][i], y[k], t);
-      y[i] = t / r11[i][i];
-    }
+    for (int k = i + 1; k < CB; ++k) g[k] = fma(-r[i][k], y, g[k]);
   }
 #pragma unroll
   for (int i = 0; i < CB; ++i)
-    if (i < nb) G[i * ldg + c] = y[i];
+    if (i < nb) Gk[i * ldg + nb + c] = g[i];
+  if (Pt) {
+#pragma unroll
+    for (int i = 0; i < CB; ++i) Pt[c * CB + i] = g[i];
+  }
 }
 
 __global__ void k_zero_lower(int64_t d, double* __restrict__ R, int64_t ldr) {
@@ -279,6 +352,76 @@ __global__ void k_zero_lower(int64_t d, double* __restrict__ R, int64_t ldr) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < d && c < r;
        c += (int64_t)gridDim.x * blockDim.x)
     R[r * ldr + c] = 0.0;
+}
+
+// R (FP64, upper, zeros below) from the upper triangle of an FP32 factor
+__global__ void k_upper_to_f64(int64_t d, const float* __restrict__ G, int64_t ldg, double* __restrict__ R,
+                               int64_t ldr) {
+  const int64_t r = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < d && c < d;
+       c += (int64_t)gridDim.x * blockDim.x)
+    R[r * ldr + c] = c >= r ? (double)G[r * ldg + c] : 0.0;
+}
+
+// SA^T Sb of a dense sketch [SA | Sb] (m x (d + 1), row stride lda), in
+// FP64 accumulation: part[z][i] sums rows [z rows_per, (z + 1) rows_per) of
+// SA[r][i] Sb[r] (threads over columns, rows in flight eight at a time), and
+// k_sum_parts adds the chunks in order
+template <class T>
+__global__ void __launch_bounds__(128) k_sat_sb_part(int64_t m, int64_t d, const T* __restrict__ A, int64_t lda,
+                                                     int64_t rows_per, double* __restrict__ part) {
+  const int64_t i = blockIdx.x * 128ll + threadIdx.x;
+  const int64_t r0 = blockIdx.y * rows_per, r1 = std::min<int64_t>(m, r0 + rows_per);
+  if (i >= d) return;
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t r = r0; r < r1; r += 8) {
+    double a[8], b[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const bool in = r + u < r1;
+      a[u] = in ? (double)A[(r + u) * lda + i] : 0.0;
+      b[u] = in ? (double)A[(r + u) * lda + d] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = fma(a[u], b[u], acc[u]);
+  }
+  part[blockIdx.y * d + i] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+}
+
+__global__ void k_sum_parts(int64_t d, int nz, const double* __restrict__ part, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= d) return;
+  double s = 0.0;
+  for (int z = 0; z < nz; ++z) s += part[z * d + i];
+  out[i] = s;
+}
+
+constexpr int64_t kSatRows = 256;  // rows of the sketch per partial sum
+
+template <class T>
+ski_status sat_sb_dense(const T* A, int64_t lda, int64_t m, int64_t d, double* part, double* out, cudaStream_t st) {
+  const int64_t nz = ski_cdiv(m, kSatRows);
+  k_sat_sb_part<T><<<dim3((unsigned)ski_cdiv(d, 128), (unsigned)nz), 128, 0, st>>>(m, d, A, lda, kSatRows, part);
+  SKI_LAUNCH_CHECK();
+  k_sum_parts<<<(unsigned)ski_cdiv(d, 256), 256, 0, st>>>(d, (int)nz, part, out);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
+// rows [0, ncols) of X^T: X m x ncols (row-major, ldx) -> Xt ncols x ldt
+__global__ void k_transpose_f32(int64_t m, int64_t ncols, const float* __restrict__ X, int64_t ldx,
+                                float* __restrict__ Xt, int64_t ldt) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + k, c = c0 + threadIdx.x;
+    tile[k][threadIdx.x] = (r < m && c < ncols) ? X[r * ldx + c] : 0.f;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c = c0 + k, r = r0 + threadIdx.x;
+    if (c < ncols && r < m) Xt[c * ldt + r] = tile[threadIdx.x][k];
+  }
 }
 
 // ---- 6. c = SA^T Sb (warp per column, rows ascending)
@@ -294,27 +437,117 @@ __global__ void k_sat_sb(int64_t d, const int64_t* __restrict__ colptr, const in
   if (lane == 0) c[col] = s;
 }
 
-// forward substitution R11^T y = c for one diagonal block (in place in c)
+// G (upper triangle, ld) := its Cholesky factor R (R^T R = G) in place:
+// blocked right-looking, blocks of CB.  Per block: the diagonal factor (one
+// CTA), the block row R12 = R11^{-T} G12 (one thread per column), and the
+// trailing G22 -= R12^T R12 -- in FP32 on the tensor cores (three TF32
+// passes) from the transposed block row Pt, in FP64 on the SIMT GEMM over the
+// tiles that meet the upper triangle.  Scratch: dinv (CB), and for FP32 Pt
+// (d x CB).  *fail is set on a pivot that is not positive or a tensor-core
+// wait that gave up.
+template <class T>
+ski_status chol_upper(T* G, int64_t ld, int64_t d, T* dinv, T* Pt, int* fail, cudaStream_t st) {
+  for (int64_t k0 = 0; k0 < d; k0 += CB) {
+    const int nb = (int)std::min<int64_t>(CB, d - k0);
+    T* Gk = G + k0 * ld + k0;
+    k_chol_diag<T><<<1, 256, 0, st>>>(Gk, ld, nb, dinv, fail);
+    SKI_LAUNCH_CHECK();
+    const int64_t rest = d - k0 - nb;
+    if (rest <= 0) continue;
+    T* pt = std::is_same<T, float>::value ? Pt : nullptr;
+    k_trsm_row<T><<<(unsigned)ski_cdiv(rest, 32), 32, 0, st>>>(Gk, ld, nb, rest, dinv, pt);
+    SKI_LAUNCH_CHECK();
+    T* G22 = Gk + nb * ld + nb;
+    if constexpr (std::is_same<T, float>::value) {
+      SKI_TRY(ski_gemm_tf32(Pt, CB, Pt, CB, rest, rest, CB, G22, ld, 1 | 4, 1, 0, fail, st, true));
+    } else {
+      const T* R12 = Gk + nb;
+      SKI_TRY(ski_gemm_ex<T>(rest, rest, nb, T(-1), R12, 1, ld, R12, ld, 1, T(1), G22, ld, 1, 0, st, 4));
+    }
+  }
+  return SKI_OK;
+}
+
+// forward substitution R11^T y = c for one diagonal block of nb <= 64 rows,
+// in place in c: the block is staged in shared memory by 256 threads (all
+// loads in flight at once), then one warp solves: the reciprocals of the
+// diagonal are taken up front (two per lane); lane l holds c_l and c_{l+32}.
+// Step i: the owner of c_i forms y_i = c_i / r_ii, a shuffle broadcasts it,
+// and each lane subtracts r_ij y_i from its later c_j.
 __global__ void __launch_bounds__(256) k_trsv_t_diag(const double* __restrict__ R, int64_t ldr, int nb,
                                                      double* __restrict__ c) {
-  __shared__ double y[256];
-  __shared__ double part[8][33];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int i = 0; i < nb; ++i) {
-    // y_i = (c_i - sum_{k<i} R[k][i] y_k) / R[i][i]
-    double t = 0.0;
-    for (int k = threadIdx.x; k < i; k += blockDim.x) t = fma(R[k * ldr + i], y[k], t);
-    t = ski_warp_sum(t);
-    if (lane == 0) part[wid][0] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < 8; ++w) s += part[w][0];
-      y[i] = (c[i] - s) / R[i * ldr + i];
+  __shared__ double r[64][65];
+  {
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    double v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int i = ty + 4 * q;
+      v[q] = (i < nb && tx < nb) ? R[(int64_t)i * ldr + tx] : 0.0;
     }
-    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) r[ty + 4 * q][tx] = v[q];
   }
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) c[i] = y[i];
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const double inv0 = lane < nb ? 1.0 / r[lane][lane] : 0.0;
+  const double inv1 = lane + 32 < nb ? 1.0 / r[lane + 32][lane + 32] : 0.0;
+  double c0 = lane < nb ? c[lane] : 0.0, c1 = lane + 32 < nb ? c[lane + 32] : 0.0;
+  for (int i = 0; i < nb; ++i) {
+    const bool lo = i < 32;
+    if (lane == (i & 31)) {
+      if (lo) c0 *= inv0;
+      else c1 *= inv1;
+    }
+    const double y = __shfl_sync(0xffffffffu, lo ? c0 : c1, i & 31);
+    if (lane > i && lane < nb) c0 = fma(-r[i][lane], y, c0);
+    if (lane + 32 > i && lane + 32 < nb) c1 = fma(-r[i][lane + 32], y, c1);
+  }
+  if (lane < nb) c[lane] = c0;
+  if (lane + 32 < nb) c[lane + 32] = c1;
+}
+
+// c_j -= sum_{i < nb} r_ij y_i for the rest columns j: a CTA takes 32
+// columns, its 8 warps 8 rows each (one load round trip), and the 8 partial
+// sums of a column are added in shared memory in a fixed order
+__global__ void __launch_bounds__(256) k_gemv_t_sub(const double* __restrict__ R, int64_t ldr, int nb, int64_t rest,
+                                                    const double* __restrict__ y, double* __restrict__ c) {
+  __shared__ double part[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t j = blockIdx.x * 32ll + lane;
+  double v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int i = w * 8 + u;
+    v[u] = (i < nb && j < rest) ? R[(int64_t)i * ldr + j] * y[i] : 0.0;
+  }
+  part[w][lane] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+  __syncthreads();
+  if (w == 0 && j < rest) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += part[q][lane];
+    c[j] -= s;
+  }
+}
+
+// R^T y = c in place (R upper, FP64): the diagonal blocks by one warp, the
+// rest as GEMV updates
+ski_status trsv_upper_t(const double* R, int64_t ldr, int64_t d, double* c, cudaStream_t st) {
+  constexpr int TB = 64;
+  for (int64_t k0 = 0; k0 < d; k0 += TB) {
+    const int nb = (int)std::min<int64_t>(TB, d - k0);
+    k_trsv_t_diag<<<1, 256, 0, st>>>(R + k0 * ldr + k0, ldr, nb, c + k0);
+    SKI_LAUNCH_CHECK();
+    const int64_t rest = d - k0 - nb;
+    if (rest > 0) {  // c[k0+nb:] -= R[k0:k0+nb, k0+nb:]^T y
+      k_gemv_t_sub<<<(unsigned)ski_cdiv(rest, 32), 256, 0, st>>>(R + k0 * ldr + k0 + nb, ldr, nb, rest, c + k0,
+                                                                 c + k0 + nb);
+      SKI_LAUNCH_CHECK();
+    }
+  }
+  return SKI_OK;
 }
 
 }  // namespace
@@ -337,6 +570,7 @@ size_t ski_gram_ws_bytes(int64_t n, int64_t d, int64_t nnz, int32_t s, int64_t m
   ar.take<char>(ski_csc_ws_bytes(m, d, cap));
   ar.take<double>(d);           // SA^T Sb
   ar.take<int>(1);              // failure flag
+  ar.take<double>(CB);          // Cholesky: 1 / r_jj of a block
   return ar.off;
 }
 
@@ -363,7 +597,8 @@ ski_status ski_gram_chol_run(const ski_matrix* A, uint64_t seed, int32_t s, int3
   char* cscws = ar.take<char>(cscb);
   double* cvec = ar.take<double>(d);
   int* fail = ar.take<int>(1);
-  if (!ar.ok() || !fail) return SKI_ENOMEM;
+  double* dinv = ar.take<double>(CB);
+  if (!ar.ok() || !dinv) return SKI_ENOMEM;
   SKI_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), st));
   // 1. bucket lists
   SkiArena bar{bkws, bkb, 0, false};
@@ -410,21 +645,7 @@ ski_status ski_gram_chol_run(const ski_matrix* A, uint64_t seed, int32_t s, int3
     SKI_LAUNCH_CHECK();
   }
   // 5. Cholesky in place
-  for (int64_t k0 = 0; k0 < d; k0 += CB) {
-    const int nb = (int)std::min<int64_t>(CB, d - k0);
-    double* Gk = R + k0 * ldr + k0;
-    k_chol_diag<<<1, 256, 0, st>>>(Gk, ldr, nb, fail);
-    SKI_LAUNCH_CHECK();
-    const int64_t rest = d - k0 - nb;
-    if (rest > 0) {
-      k_chol_panel<<<(unsigned)ski_cdiv(rest, 128), 128, 0, st>>>(Gk, ldr, nb, rest);
-      SKI_LAUNCH_CHECK();
-      // G22 -= R12^T R12 (tiles meeting the upper triangle only)
-      const double* R12 = Gk + nb;
-      SKI_TRY(ski_gemm_ex<double>(rest, rest, nb, -1.0, R12, 1, ldr, R12, ldr, 1, 1.0, Gk + nb * ldr + nb, ldr, 1,
-                                  0, st, 4));
-    }
-  }
+  SKI_TRY(chol_upper<double>(R, ldr, d, dinv, nullptr, fail, st));
   {
     dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
     k_zero_lower<<<grid, blk, 0, st>>>(d, R, ldr);
@@ -434,18 +655,89 @@ ski_status ski_gram_chol_run(const ski_matrix* A, uint64_t seed, int32_t s, int3
   if (qtsb) {
     k_sat_sb<<<(unsigned)ski_cdiv(d * 32, 256), 256, 0, st>>>(d, colptr, crow, cval, Sb, ldsb, cvec);
     SKI_LAUNCH_CHECK();
-    constexpr int TB = 256;
-    for (int64_t k0 = 0; k0 < d; k0 += TB) {
-      const int nb = (int)std::min<int64_t>(TB, d - k0);
-      k_trsv_t_diag<<<1, 256, 0, st>>>(R + k0 * ldr + k0, ldr, nb, cvec + k0);
-      SKI_LAUNCH_CHECK();
-      const int64_t rest = d - k0 - nb;
-      if (rest > 0)  // c[k0+nb:] -= R[k0:k0+nb, k0+nb:]^T y
-        SKI_TRY(ski_gemm<double>(rest, 1, nb, -1.0, R + k0 * ldr + k0 + nb, 1, ldr, cvec + k0, 1, 1, 1.0,
-                                 cvec + k0 + nb, 1, st));
-    }
+    SKI_TRY(trsv_upper_t(R, ldr, d, cvec, st));
     SKI_CUDA_TRY(cudaMemcpyAsync(qtsb, cvec, d * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
+  SKI_CUDA_TRY(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SKI_CUDA_TRY(cudaStreamSynchronize(st));
+  *ok = hfail == 0;
+  return SKI_OK;
+}
+
+// ---- dense sketch: R from the Cholesky factor of SA^T SA
+// FP64: G = SA^T SA on the FP64 SIMT GEMM (the tiles that meet the upper
+// triangle), then the FP64 blocked Cholesky.  FP32 / TF32: SA^T (the
+// GEMM's K-major operand) by a tile transpose, G on the tensor cores (three
+// TF32 passes for FP32, one for TF32), the Cholesky in FP32, R cast to FP64.
+// Work: m d^2 + d^3 / 3 multiply-adds against 2 m d^2 - 2 d^3 / 3 for the
+// Householder QR.  Q^T Sb = R^{-T} SA^T Sb in FP64 (SA^T Sb accumulated in
+// FP64 from the sketch's values).
+size_t ski_gram_dense_ws_bytes(int64_t m, int64_t d, int32_t prec) {
+  SkiArena ar{nullptr, 0, 0, true};
+  ar.take<double>(d);                        // SA^T Sb
+  ar.take<int>(1);                           // failure flag
+  ar.take<double>(ski_cdiv(m, kSatRows) * d);  // SA^T Sb partial sums
+  if (prec != SKI_F64) {
+    const int64_t ldt = ski_round_up(m, 32), ldg = ski_round_up(d, 4);
+    ar.take<float>(d * ldt);        // SA^T
+    ar.take<float>(d * ldg);        // G, then R
+    ar.take<float>(CB);             // Cholesky: 1 / r_jj of a block
+    ar.take<float>(ldg * CB);       // Cholesky: block row transposed
+  } else {
+    ar.take<double>(CB);
+  }
+  return ar.off;
+}
+
+ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t d, int32_t prec, double* R,
+                              int64_t ldr, double* qtsb, bool* ok, SkiArena& ar, cudaStream_t st) {
+  *ok = false;
+  if (d < 1 || m < d) return SKI_EINVAL;
+  double* cvec = ar.take<double>(d);
+  int* fail = ar.take<int>(1);
+  double* part = ar.take<double>(ski_cdiv(m, kSatRows) * d);
+  if (!ar.ok() || !part) return SKI_ENOMEM;
+  SKI_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), st));
+  if (prec == SKI_F64) {
+    const double* A = (const double*)SA;
+    // G = SA^T SA (upper tiles) into R, in place to its factor
+    double* dinv = ar.take<double>(CB);
+    if (!ar.ok() || !dinv) return SKI_ENOMEM;
+    SKI_TRY(ski_gemm_ex<double>(d, d, m, 1.0, A, 1, ld_sa, A, ld_sa, 1, 0.0, R, ldr, 1, 0, st, 4));
+    SKI_TRY(chol_upper<double>(R, ldr, d, dinv, nullptr, fail, st));
+    dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
+    k_zero_lower<<<grid, blk, 0, st>>>(d, R, ldr);
+    SKI_LAUNCH_CHECK();
+    // SA^T Sb (Sb = column d of the sketch)
+    SKI_TRY(sat_sb_dense<double>(A, ld_sa, m, d, part, cvec, st));
+  } else if (prec == SKI_F32 || prec == SKI_TF32) {
+    const float* A = (const float*)SA;
+    const int64_t ldt = ski_round_up(m, 32), ldg = ski_round_up(d, 4);
+    float* At = ar.take<float>(d * ldt);
+    float* G = ar.take<float>(d * ldg);
+    float* dinv = ar.take<float>(CB);
+    float* Pts = ar.take<float>(ldg * CB);
+    if (!ar.ok() || !Pts) return SKI_ENOMEM;
+    {
+      dim3 grid((unsigned)ski_cdiv(m, 32), (unsigned)ski_cdiv(d, 32));
+      k_transpose_f32<<<grid, dim3(32, 8), 0, st>>>(m, d, A, ld_sa, At, ldt);
+      SKI_LAUNCH_CHECK();
+    }
+    // G = SA^T SA on the tensor cores (D = At At^T, stored; upper tiles only)
+    SKI_TRY(ski_gemm_tf32(At, ldt, At, ldt, d, d, m, G, ldg, 0 | 4, 1, 0, fail, st, prec == SKI_F32));
+    SKI_TRY(chol_upper<float>(G, ldg, d, dinv, Pts, fail, st));
+    dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
+    k_upper_to_f64<<<grid, blk, 0, st>>>(d, G, ldg, R, ldr);
+    SKI_LAUNCH_CHECK();
+    SKI_TRY(sat_sb_dense<float>(A, ld_sa, m, d, part, cvec, st));
+  } else {
+    return SKI_EINVAL;
+  }
+  if (qtsb) {
+    SKI_TRY(trsv_upper_t(R, ldr, d, cvec, st));
+    SKI_CUDA_TRY(cudaMemcpyAsync(qtsb, cvec, d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  int hfail = 0;
   SKI_CUDA_TRY(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
   SKI_CUDA_TRY(cudaStreamSynchronize(st));
   *ok = hfail == 0;

@@ -639,6 +639,10 @@ __global__ void k_tfactor(int w, const T* __restrict__ Z, int64_t ldzz, const T*
   for (int c = 0; c < NB; ++c) Tm[lane * NB + c] = Ts[lane][c];
 }
 
+// One column per thread, one warp per CTA: in FP64 each column's 528 FMAs
+// run on the 2-per-clock FP64 pipe, so the columns are spread over as many SMs
+// as possible (a 545-column FP64 update: 43 us with 128 threads per CTA).
+constexpr int kTtwThreads = 32;
 // B'^T[c][i] = (T^T W)[i][c] for i < w, 0 for w <= i < NB; W = columns
 // [w, w + nct) of Z.  Row-major nct x NB: the K-major operand of the update.
 template <class T>
@@ -1098,7 +1102,7 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
       SKI_LAUNCH_CHECK();
     }
     if (nw > 0) {
-      k_ttw<T><<<ski_cdiv(nw, 128), 128, 0, st>>>(w, nw, bf.Z, NB + q.ldz, Tmk, bf.Bpt);
+      k_ttw<T><<<ski_cdiv(nw, kTtwThreads), kTtwThreads, 0, st>>>(w, nw, bf.Z, NB + q.ldz, Tmk, bf.Bpt);
       SKI_LAUNCH_CHECK();
     }
     if (nu < nct) {
@@ -1115,7 +1119,7 @@ ski_status qr_impl(int64_t m, int64_t d, int32_t with_rhs, T* B, int64_t ld, dou
         timer.mark(st_lo);
         k_reduce_z<T><<<ski_cdiv(w * (w + nr), 256), 256, 0, st_lo>>>(w, nr, bf.pv, 0, bf.pc2, scb, q.ldz, bf.Z2);
         SKI_LAUNCH_CHECK();
-        k_ttw<T><<<ski_cdiv(nr, 128), 128, 0, st_lo>>>(w, nr, bf.Z2, NB + q.ldz, Tmk, bf.Bpt2);
+        k_ttw<T><<<ski_cdiv(nr, kTtwThreads), kTtwThreads, 0, st_lo>>>(w, nr, bf.Z2, NB + q.ldz, Tmk, bf.Bpt2);
         SKI_LAUNCH_CHECK();
         Bq = bf.Bpt2;
       }

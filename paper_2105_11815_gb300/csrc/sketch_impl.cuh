@@ -157,3 +157,8 @@ size_t ski_gram_ws_bytes(int64_t n, int64_t d, int64_t nnz, int32_t s, int64_t m
 ski_status ski_gram_chol_run(const ski_matrix* A, uint64_t seed, int32_t s, int32_t replace, int64_t m,
                              const double* Sb, int64_t ldsb, double* R, int64_t ldr, double* qtsb, bool* ok,
                              SkiArena& ar, cudaStream_t st);
+// R from the Cholesky factor of SA^T SA of a dense sketch (SA: m x (d + 1)
+// row-major, FP64 for prec SKI_F64, else FP32; column d holds Sb); *ok as above
+size_t ski_gram_dense_ws_bytes(int64_t m, int64_t d, int32_t prec);
+ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t d, int32_t prec, double* R,
+                              int64_t ldr, double* qtsb, bool* ok, SkiArena& ar, cudaStream_t st);

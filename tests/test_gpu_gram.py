@@ -83,3 +83,66 @@ def test_long_sketch_rows_fall_back():
     x, R, info = _solve(torch, pkg, A, b, m=100, s=1, seed=1, factorization=2)
     assert info.status == 0 and info.gram == 0
     assert olsqr.residual_metric(A, b, x) <= 1e-10
+
+
+def _dense_solve(torch, pkg, A, b, check=True, **kw):
+    d = A.shape[1]
+    o = pkg.ski_opts_default(tol=1e-10, tau_r=1e-12, **kw)
+    x = torch.empty(d, dtype=torch.float64, device="cuda")
+    R = torch.empty(d, d, dtype=torch.float64, device="cuda")
+    info = pkg.ski_solve(pkg.dense_matrix(to_dev(torch, A)), to_dev(torch, b), o, x, R_out=R, check=check)
+    return x.cpu().numpy(), R.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("n,d,m,premix", [(6000, 150, 300, 0), (9000, 260, 520, 1), (4000, 33, 70, 0)])
+def test_dense_gram_factor_matches_the_oracle(n, d, m, premix):
+    torch, pkg = cuda()
+    A, b, _ = workloads.gaussian_lls(n, d, seed=n + d)
+    kw = dict(m=m, s=1, seed=6)
+    npad = 1 << (n - 1).bit_length()
+    if premix:
+        kw.update(premix=1, n_pad=npad)
+    x, R, info = _dense_solve(torch, pkg, A, b, factorization=2, **kw)
+    assert info.status == 0 and info.gram == 1
+    xo, oinfo = olsqr.ski_lls(A, b, seed=6, s=1, m=m, premix=bool(premix), n_pad=npad if premix else None,
+                              factorization="chol")
+    assert rel_fro(R, oinfo["R"]) <= 1e-11
+    assert rel_fro(x, xo) <= 1e-9
+    assert abs(info.iters - oinfo["iters"]) <= 1
+    assert olsqr.residual_metric(A, b, x) <= 1e-10
+
+
+@pytest.mark.parametrize("qr", ["f32", "tf32"])
+def test_dense_gram_factor_in_fp32(qr):
+    # the Gram matrix on the tensor cores and the Cholesky in FP32: R within
+    # the FP32 factor's accuracy of the oracle's, and the solve meets 1e-10
+    # after as many iterations as the FP64 factor's (TF32: a few more)
+    torch, pkg = cuda()
+    n, d, m = 20000, 400, 800
+    A, b, _ = workloads.gaussian_lls(n, d, seed=8)
+    qdt = pkg.SKI_F32 if qr == "f32" else pkg.SKI_TF32
+    x, R, info = _dense_solve(torch, pkg, A, b, m=m, s=1, seed=4, factorization=2, sketch_dtype=pkg.SKI_F32,
+                              qr_dtype=qdt)
+    assert info.status == 0 and info.gram == 1 and info.qr_fallback == 0
+    _, oinfo = olsqr.ski_lls(A, b, seed=4, s=1, m=m, factorization="chol")
+    assert rel_fro(R, oinfo["R"]) <= (1e-5 if qr == "f32" else 2e-2)
+    assert olsqr.residual_metric(A, b, x) <= 1e-10
+    if qr == "f32":
+        assert abs(info.iters - oinfo["iters"]) <= 2
+
+
+@pytest.mark.parametrize("kappa,mixed", [(1e6, True), (1e10, False)])
+def test_dense_gram_falls_back_when_ill_conditioned(kappa, mixed):
+    # kappa(SA)^2 u too large for the Gram matrix's precision: the factor's
+    # diagonal ratio passes the limit and Step 2 takes the Householder QR
+    torch, pkg = cuda()
+    n, d = 12000, 200
+    A, b = workloads.usv(n, d, kappa, seed=3)
+    prec = dict(sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32) if mixed else {}
+    x, R, info = _dense_solve(torch, pkg, A, b, check=False, m=2 * d, s=1, seed=2, factorization=2, **prec)
+    assert info.gram == 0
+    assert info.status in (0, pkg.STATUS.index("SKI_ENOCONV"))
+    # the Householder solve's accuracy.  At kappa = 1e10, |x| ~ 1e9: the
+    # FP64 rounding of x alone moves the metric by about 1e-10, so the
+    # double-double check allows a few times the acceptance level
+    assert olsqr.residual_metric_dd(A, b, x) <= (3e-10 if kappa < 1e8 else 1e-9)
