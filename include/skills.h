@@ -123,8 +123,8 @@ typedef struct {
                           /* positive diagonal) and Q^T Sb = R^{-T} SA^T Sb: for CSR A  */
                           /* (FP64 factor) from a sparse SA kept in CSR (Section 6),    */
                           /* for dense A from the dense sketch in the QR precision;     */
-                          /* the Householder QR when the Cholesky breaks down or the    */
-                          /* factor's diagonal ratio passes 2^23 (FP64) / 2^9 (FP32);   */
+                          /* the Householder QR when the Cholesky breaks down or       */
+                          /* max_j |SA_j| / r_jj passes 2^23 (FP64) / 2^9 (FP32);       */
                           /* then as 0                                                  */
   int32_t batch_lsqr;     /* ski_solve_batched, dense problems: 0 = each problem's own  */
                           /* Step 4 launches on its stream; 1 = Step 4 of all problems  */

@@ -499,10 +499,13 @@ size_t gram_stage_bytes(const ski_matrix* A, const ski_opts* o) {
   if (A->kind == SKI_CSR) return ski_gram_ws_bytes(A->n, A->d, A->nnz, o->s, o->m);
   return ski_gram_dense_ws_bytes(o->m, A->d, o->qr_dtype);
 }
-// Largest max|r_ii| / min|r_ii| of a factor from the Gram matrix kept as the
-// preconditioner: its relative error grows like kappa(SA)^2 u, so the limit
-// is about u^{-1/2} / 8 of the Gram's precision; past it Step 2 is redone by
-// the Householder QR in the same precision.
+// Largest max_j sqrt(g_jj) / r_jj (g_jj = |SA_j|^2; a lower bound on the
+// condition number of SA with unit columns) of a factor from the Gram matrix
+// kept as the preconditioner: its relative error grows like kappa^2 u, with
+// kappa that of the column-scaled SA (the Cholesky is invariant under
+// power-of-two column scales), so the limit is about u^{-1/2} / 8 of the
+// Gram's precision; past it Step 2 is redone by the Householder QR in the
+// same precision.
 double gram_ratio_limit(int32_t qr_prec) { return qr_prec == SKI_F64 ? 0x1p23 : 0x1p9; }
 
 size_t region_need(const ski_matrix* A, const ski_opts* o) {
@@ -832,7 +835,8 @@ static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opt
   const bool pivot_ok = o->factorization == 1 && !P.csr;
   bool need_pivot = false;
   bool perturbed = false;  // R + perturb I replaced R (the perturbed back-solve)
-  bool gram_used = false;  // Step 2 took the Cholesky factor of the sparse sketch's Gram matrix
+  bool gram_used = false;  // Step 2 took the Cholesky factor of the sketch's Gram matrix
+  double gram_eq = INFINITY;  // its column-scaled diagonal ratio
   // Steps 1-2 and R^{-1} in the precisions of `of`
   auto factor = [&](const ski_opts* of) -> ski_status {
     carve_region(A, of, &P);
@@ -868,9 +872,9 @@ static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opt
         SkiArena gar{P.stage, P.stage_bytes, 0, false};
         if (P.csr)
           SKI_TRY(ski_gram_chol_run(A, of->seed, of->s, of->hash_kind, P.m, (const double*)P.SA + d, P.ld_sa, P.R,
-                                    d, P.qtsb, &done, gar, st));
+                                    d, P.qtsb, &done, &gram_eq, gar, st));
         else
-          SKI_TRY(ski_gram_dense_run(P.SAq, P.ld_sa, P.m, d, P.qr_prec, P.R, d, P.qtsb, &done, gar, st));
+          SKI_TRY(ski_gram_dense_run(P.SAq, P.ld_sa, P.m, d, P.qr_prec, P.R, d, P.qtsb, &done, &gram_eq, gar, st));
         gram_used = done;
       }
       SkiArena qar{P.stage, P.stage_bytes, 0, false};
@@ -881,7 +885,7 @@ static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opt
     SKI_CUDA_TRY(cudaEventRecord(fe.e[2], st));
     bool nonfinite = false;
     SKI_TRY(rank_from_diag(d, P.R, d, o->rcond, st, &rank, &nonfinite, &rdiag_ratio));
-    if (gram_used && (nonfinite || rank < d || !(rdiag_ratio <= gram_ratio_limit(P.qr_prec)))) {
+    if (gram_used && (nonfinite || rank < d || !(gram_eq <= gram_ratio_limit(P.qr_prec)))) {
       // too ill-conditioned for the Gram matrix's precision: Householder QR
       gram_used = false;
       SkiArena qar{P.stage, P.stage_bytes, 0, false};

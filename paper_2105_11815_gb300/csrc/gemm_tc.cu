@@ -84,6 +84,10 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
 __host__ __device__ constexpr uint32_t tf32_idesc(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
+// Instruction descriptor of kind::f16: D = F32, A = B = F16, both K-major.
+__host__ __device__ constexpr uint32_t f16_idesc(int m, int n) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
 
 template <int BN, int STAGES, bool SPLIT>
 struct TcSmem {
@@ -116,13 +120,19 @@ __device__ __forceinline__ void tf32_split(float* hi_tile, float* lo_tile, int c
   }
 }
 
-// mode 0: C[m * ldc + n] = D; mode 1: C[m * ldc + n] -= D; mode 2: C[n * ldc + m] = D.
+// mode 0: C[m * ldc + n] = D; mode 1: C[m * ldc + n] -= D; mode 2: C[n * ldc + m] = D;
+// mode 3 (F16 only): C64[m * ldc + n] += scale64 * D (FP64).
 // mode | 4: only the tiles that meet the upper triangle (some m <= n).
-template <int BN, int STAGES, bool SPLIT>
+// F16: operands FP16 (a stage is 64 of them per row, the same 128 bytes),
+// multiplied by kind::f16 (K = 16 per instruction); else FP32 as TF32.
+template <int BN, int STAGES, bool SPLIT, bool F16 = false>
 __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
                                                       const __grid_constant__ CUtensorMap tb, int M, int N, int K,
                                                       int kchunk, float* __restrict__ C, int64_t ldc,
-                                                      int64_t c_zstride, int mode, int* err) {
+                                                      int64_t c_zstride, int mode, int* err,
+                                                      double* __restrict__ C64, double scale64) {
+  static_assert(!(F16 && SPLIT), "the split form is for FP32 operands");
+  constexpr int BKE = F16 ? 2 * BK : BK;  // K elements per stage
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem<BN, STAGES, SPLIT>& sm = *reinterpret_cast<TcSmem<BN, STAGES, SPLIT>*>(
       (void*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023));
@@ -130,7 +140,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
-  const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+  const int nk = kend > kbeg ? (kend - kbeg + BKE - 1) / BKE : 0;
   C += (int64_t)blockIdx.z * c_zstride;
   if ((mode & 4) && m0 >= n0 + BN) return;  // the whole tile is below the diagonal (CTA-uniform)
   mode &= 3;
@@ -163,7 +173,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
       const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
       if (!mbar_wait(smem_u32(&sm.empty[s]), ph ^ 1u, err)) break;
       mbar_expect_tx(smem_u32(&sm.full[s]), bytes);
-      const int kx = kbeg + kt * BK;
+      const int kx = kbeg + kt * BKE;
       tma_load_2d(smem_u32(sm.A[s]), &ta, kx, m0, smem_u32(&sm.full[s]));
       tma_load_2d(smem_u32(sm.B[s]), &tb, kx, n0, smem_u32(&sm.full[s]));
       ++issued;
@@ -179,7 +189,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    constexpr uint32_t idesc = tf32_idesc(BM, BN);
+    constexpr uint32_t idesc = F16 ? f16_idesc(BM, BN) : tf32_idesc(BM, BN);
     bool ok = true;
     for (int kt = 0; kt < nk && ok; ++kt) {
       const int s = kt % STAGES;
@@ -208,10 +218,16 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
               "l"(ad), "l"(bdl), "r"(idesc), "r"(1u));
           acc = 1u;
         }
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        if constexpr (F16)
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        else
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        smem_u32(&sm.empty[s]))
@@ -270,7 +286,19 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
         __syncwarp();
         const int col = n0 + c0 + lane;
         const bool cok = col < N;
-        if (mode == 1) {
+        if (F16 && mode == 3) {
+          double cv[32];
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) {
+            const int r = m0 + warp * 32 + rr;
+            cv[rr] = (r < M && cok) ? C64[(int64_t)r * ldc + col] : 0.0;
+          }
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) {
+            const int r = m0 + warp * 32 + rr;
+            if (r < M && cok) C64[(int64_t)r * ldc + col] = fma(scale64, (double)st[rr][lane], cv[rr]);
+          }
+        } else if (mode == 1) {
           // all 32 rows' loads in flight before the first use
           float cv[32];
 #pragma unroll
@@ -341,6 +369,21 @@ bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, i
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2-D FP16 tensor map over a row-major (rows x cols) matrix with row stride
+// ld elements; box = box_rows x 64 columns (128 bytes), 128-byte swizzle;
+// reads outside the matrix fill with zeros.
+bool make_map_f16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  EncodeTiled fn = encoder();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)(2 * BK), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 // 2-D FP64 tensor map over a row-major rows x cols matrix (row stride ld
@@ -375,7 +418,8 @@ ski_status launch(const float* A, int64_t lda, const float* B, int64_t ldb, int 
                               [&] { return (int)smem; }));
   const int kchunk = (int)ski_round_up(ski_cdiv(K, splits), BK);
   dim3 grid((unsigned)ski_cdiv(M, BM), (unsigned)ski_cdiv(N, BN), (unsigned)splits);
-  k_gemm_tc<BN, STAGES, SPLIT><<<grid, NTHR, smem, st>>>(ta, tb, M, N, K, kchunk, C, ldc, c_zstride, mode, err);
+  k_gemm_tc<BN, STAGES, SPLIT><<<grid, NTHR, smem, st>>>(ta, tb, M, N, K, kchunk, C, ldc, c_zstride, mode, err,
+                                                          nullptr, 0.0);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }
@@ -413,6 +457,33 @@ ski_status ski_gemm_tf32(const float* A, int64_t lda, const float* B, int64_t ld
   if (split3)
     return dispatch<true>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
   return dispatch<false>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
+}
+
+// C64 (+)= scale * A B^T with A (M x K) and B (N x K) FP16, row-major and
+// K-contiguous (row strides lda, ldb: multiples of 8; 16-byte aligned bases),
+// multiplied on the tensor cores (kind::f16) with FP32 accumulation, then
+// scaled and added to the FP64 C64 in the epilogue.  The FP32 accumulation is
+// exact when the operands are integers and every partial sum stays below
+// 2^24 in magnitude.  upper: only the tiles that meet the upper triangle.
+ski_status ski_gemm_f16_f64acc(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
+                               int64_t K, double* C64, int64_t ldc, double scale, bool upper, int* err,
+                               cudaStream_t st) {
+  if (M <= 0 || N <= 0) return SKI_OK;
+  if ((lda & 7) || (ldb & 7) || ((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return SKI_EINVAL;
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return SKI_EINVAL;
+  constexpr int BNF = 256, STF = 4;
+  CUtensorMap ta, tb;
+  if (!make_map_f16(&ta, A, M, K, lda, BM) || !make_map_f16(&tb, B, N, K, ldb, BNF)) return SKI_ECUDA;
+  const size_t smem = sizeof(TcSmem<BNF, STF, false>) + 1024;
+  static_assert(sizeof(TcSmem<BNF, STF, false>) + 1024 <= 227 * 1024, "shared memory");
+  SKI_CUDA_TRY(ski_attr_once((const void*)k_gemm_tc<BNF, STF, false, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, [&] { return (int)smem; }));
+  dim3 grid((unsigned)ski_cdiv(M, BM), (unsigned)ski_cdiv(N, BNF), 1);
+  k_gemm_tc<BNF, STF, false, true><<<grid, NTHR, smem, st>>>(ta, tb, (int)M, (int)N, (int)K,
+                                                              (int)ski_round_up(K, 2 * BK), nullptr, ldc, 0,
+                                                              3 | (upper ? 4 : 0), err, C64, scale);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
 }
 
 extern "C" ski_status ski_gemm_tc_f32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,

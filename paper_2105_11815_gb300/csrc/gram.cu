@@ -27,6 +27,7 @@
 // On failure the caller factors the dense sketch by Householder QR instead.
 // The same Cholesky serves a dense sketch (ski_gram_dense_run), whose Gram
 // matrix is a GEMM.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include <algorithm>
@@ -398,6 +399,156 @@ __global__ void k_sum_parts(int64_t d, int nz, const double* __restrict__ part, 
 
 constexpr int64_t kSatRows = 256;  // rows of the sketch per partial sum
 
+// ---- FP64 Gram matrix from exact slice products on the tensor cores.
+// Column j of SA is scaled by 2^-e_j (every |a_rj| < 2^e_j) and cut into
+// integer slices of beta bits: x = a 2^-e_j = sum_k 2^(-beta k) S_k + rho,
+// the S_k the balanced base-2^beta digits of round(2^(beta s) x), so
+// |S_1| <= 2^beta, |S_k| <= 2^(beta-1) after it and |rho| <= 2^(-beta s - 1).  A product of
+// slices summed over m rows stays below m 2^(2 beta) < 2^24, so the tensor
+// cores' FP32 accumulation of FP16 slice products is exact; G = 2^(e_i + e_j)
+// sum over k + l <= s + 1 of 2^(-beta (k + l)) S_k^T S_l, added in FP64 in
+// decreasing order of magnitude.  The dropped pairs are below 2^(-beta s) per
+// row of the normalised columns.
+int oz_beta(int64_t m) {
+  int lg = 0;
+  while ((1ll << lg) <= m) ++lg;  // m < 2^lg
+  return (24 - lg) / 2;
+}
+int oz_slices(int beta) { return (54 + beta - 1) / beta; }
+constexpr int kOzMinBeta = 4;  // below it (m >= 2^16) the FP64 SIMT GEMM forms G
+
+// e_j: an exponent with every |a_rj| (r < m) below 2^e_j; the caller fills e
+// with a very negative value first (a zero column keeps exponent 0).  A NaN
+// or infinite entry sets *fail (the Gram factor is then not used).
+__global__ void __launch_bounds__(128) k_col_exp(int64_t m, int64_t d, const double* __restrict__ A, int64_t lda,
+                                                 int64_t rows_per, int* __restrict__ e, int* __restrict__ fail) {
+  const int64_t j = blockIdx.x * 128ll + threadIdx.x;
+  const int64_t r0 = blockIdx.y * rows_per, r1 = std::min<int64_t>(m, r0 + rows_per);
+  if (j >= d) return;
+  double mx = 0.0;
+  bool bad = false;
+  for (int64_t r = r0; r < r1; ++r) {
+    const double a = fabs(A[r * lda + j]);
+    bad |= !(a <= 1.7976931348623157e308);
+    mx = fmax(mx, a);
+  }
+  if (bad) {
+    atomicExch(fail, 1);
+    return;
+  }
+  int ex = 0;
+  frexp(mx, &ex);
+  atomicMax(&e[j], ex);
+}
+
+// v = round(a 2^(bits - e)) as an integer, for |a| < 2^e (so |v| <= 2^bits),
+// from a's bit pattern: a = +-M 2^(E - 1075) with the 53-bit M.  Integer
+// operations only (the FP64 pipe is slow here).
+__device__ __forceinline__ long long oz_fixed(double a, int e, int bits) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const int E = (int)((u >> 52) & 0x7FF);
+  unsigned long long M = u & 0xFFFFFFFFFFFFFull;
+  if ((E == 0 && M == 0) || E == 0x7FF) return 0;  // zero; NaN / Inf are flagged by k_col_exp
+  int ex = E;
+  if (E != 0) M |= 1ull << 52;
+  else ex = 1;  // subnormal
+  const int sh = ex - 1075 - e + bits;
+  unsigned long long v;
+  if (sh >= 0) v = M << sh;  // |a| < 2^e keeps v below 2^bits
+  else if (sh > -64) v = (M + (1ull << (-sh - 1))) >> -sh;
+  else v = 0;
+  return (u >> 63) ? -(long long)v : (long long)v;
+}
+
+// slices of a 64-row x 32-column tile of SA, transposed: Sl[k][j][r] (FP16,
+// row stride lds, slice stride sstride).  Thread (tx, ty) takes column
+// j0 + tx, rows r0 + ty + 8 q: v = round(x 2^(beta ns)) in int64, cut into
+// balanced base-2^beta digits from the low end (each in [-2^(beta-1),
+// 2^(beta-1)), the leading one what remains, |S_1| <= 2^beta); the tile is
+// transposed through shared memory so that each slice row is written as
+// 128-byte segments.
+__global__ void __launch_bounds__(256) k_oz_slice(int64_t m, int64_t d, const double* __restrict__ A, int64_t lda,
+                                                  const int* __restrict__ e, int beta, int ns,
+                                                  __half* __restrict__ Sl, int64_t lds, int64_t sstride) {
+  extern __shared__ __align__(16) unsigned char oz_raw[];
+  __half* t = reinterpret_cast<__half*>(oz_raw);  // [ns][32][66]
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t j0 = (int64_t)blockIdx.y * 32, r0 = (int64_t)blockIdx.x * 64, j = j0 + tx;
+  const int ej = j < d ? e[j] : 0;
+  const long long mask = (1ll << beta) - 1, half_ = 1ll << (beta - 1);
+  double av[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t r = r0 + ty + 8 * q;
+    av[q] = (r < m && j < d) ? A[r * lda + j] : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int rl = ty + 8 * q;
+    long long v = oz_fixed(av[q], ej, beta * ns);
+    for (int k = ns - 1; k >= 1; --k) {
+      long long dg = v & mask;
+      if (dg >= half_) dg -= (1ll << beta);
+      v = (v - dg) >> beta;  // exact: v - dg is a multiple of 2^beta
+      t[(k * 32 + tx) * 66 + rl] = __int2half_rn((int)dg);
+    }
+    t[tx * 66 + rl] = __int2half_rn((int)v);  // |v| <= 2^beta: exact
+  }
+  __syncthreads();
+  // slice k, column jl: 64 halves = 32 words, one per lane
+  for (int w = ty; w < ns * 32; w += 8) {
+    const int k = w >> 5, jl = w & 31;
+    const int64_t jj = j0 + jl, r = r0 + 2 * tx;
+    if (jj >= d || r >= m) continue;
+    const __half* src = t + (k * 32 + jl) * 66 + 2 * tx;
+    __half* dst = Sl + k * sstride + jj * lds + r;
+    if (r + 1 < m) {
+      *reinterpret_cast<__half2*>(dst) = __halves2half2(src[0], src[1]);
+    } else {
+      dst[0] = src[0];
+    }
+  }
+}
+
+// G[i][j] *= 2^(e_i + e_j) on the upper triangle
+__global__ void k_oz_scale(int64_t d, double* __restrict__ G, int64_t ldg, const int* __restrict__ e) {
+  const int64_t i = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
+  if (i >= d) return;
+  const int ei = e[i];
+  for (int64_t j = i + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x)
+    G[i * ldg + j] = ldexp(G[i * ldg + j], ei + e[j]);
+}
+
+int64_t oz_lds(int64_t m) { return ski_round_up(m, 8); }
+
+// G (upper triangle, d x d, row stride ldg) = SA^T SA for the FP64 SA (m x d,
+// row stride lda); e: d ints, Sl: ns d lds halves of scratch
+ski_status oz_gram(const double* A, int64_t lda, int64_t m, int64_t d, double* G, int64_t ldg, int* e, __half* Sl,
+                   int* fail, cudaStream_t st) {
+  const int beta = oz_beta(m), ns = oz_slices(beta);
+  const int64_t lds = oz_lds(m), sstride = d * lds;
+  SKI_CUDA_TRY(cudaMemsetAsync(e, 0x80, d * sizeof(int), st));
+  const int64_t nz = ski_cdiv(m, kSatRows);
+  k_col_exp<<<dim3((unsigned)ski_cdiv(d, 128), (unsigned)nz), 128, 0, st>>>(m, d, A, lda, kSatRows, e, fail);
+  SKI_LAUNCH_CHECK();
+  // the attribute is set once, for the most slices (the fewest bits) taken
+  const size_t smem = (size_t)ns * 32 * 66 * sizeof(__half);
+  SKI_CUDA_TRY(ski_attr_once((const void*)k_oz_slice, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              [] { return (int)((size_t)oz_slices(kOzMinBeta) * 32 * 66 * sizeof(__half)); }));
+  k_oz_slice<<<dim3((unsigned)ski_cdiv(m, 64), (unsigned)ski_cdiv(d, 32)), 256, smem, st>>>(m, d, A, lda, e, beta, ns,
+                                                                                           Sl, lds, sstride);
+  SKI_LAUNCH_CHECK();
+  SKI_CUDA_TRY(cudaMemset2DAsync(G, ldg * sizeof(double), 0, d * sizeof(double), d, st));
+  for (int tt = 2; tt <= ns + 1; ++tt)
+    for (int k = std::max(1, tt - ns); k <= std::min(ns, tt - 1); ++k)
+      SKI_TRY(ski_gemm_f16_f64acc(Sl + (k - 1) * sstride, lds, Sl + (tt - k - 1) * sstride, lds, d, d, m, G, ldg,
+                                  ldexp(1.0, -beta * tt), true, fail, st));
+  dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
+  k_oz_scale<<<grid, blk, 0, st>>>(d, G, ldg, e);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
 template <class T>
 ski_status sat_sb_dense(const T* A, int64_t lda, int64_t m, int64_t d, double* part, double* out, cudaStream_t st) {
   const int64_t nz = ski_cdiv(m, kSatRows);
@@ -437,16 +588,50 @@ __global__ void k_sat_sb(int64_t d, const int64_t* __restrict__ colptr, const in
   if (lane == 0) c[col] = s;
 }
 
+// gdiag[j] = G[j][j] (the Gram matrix's diagonal, before the factorisation)
+template <class T>
+__global__ void k_save_diag(int64_t d, const T* __restrict__ G, int64_t ld, double* __restrict__ gdiag) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < d) gdiag[j] = (double)G[j * ld + j];
+}
+
+// *eq = max_j sqrt(g_jj) / r_jj: r_jj / |a_j| is the distance of column j of
+// SA from the span of the columns before it, relative to its length, so eq is
+// a lower bound on the condition number of SA with its columns scaled to unit
+// length (infinite for a pivot that is not positive or not finite).  One CTA.
+template <class T>
+__global__ void __launch_bounds__(256) k_eq_ratio(int64_t d, const T* __restrict__ R, int64_t ld,
+                                                  const double* __restrict__ gdiag, double* __restrict__ eq) {
+  __shared__ double red[256];
+  double mx = 0.0;
+  for (int64_t j = threadIdx.x; j < d; j += 256) {
+    const double r = (double)R[j * ld + j], g = gdiag[j];
+    const double q = (r > 0.0 && isfinite(r) && isfinite(g)) ? sqrt(fmax(g, 0.0)) / r : INFINITY;
+    mx = fmax(mx, q);
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *eq = red[0];
+}
+
 // G (upper triangle, ld) := its Cholesky factor R (R^T R = G) in place:
 // blocked right-looking, blocks of CB.  Per block: the diagonal factor (one
 // CTA), the block row R12 = R11^{-T} G12 (one thread per column), and the
 // trailing G22 -= R12^T R12 -- in FP32 on the tensor cores (three TF32
 // passes) from the transposed block row Pt, in FP64 on the SIMT GEMM over the
-// tiles that meet the upper triangle.  Scratch: dinv (CB), and for FP32 Pt
-// (d x CB).  *fail is set on a pivot that is not positive or a tensor-core
-// wait that gave up.
+// tiles that meet the upper triangle.  Scratch: dinv (CB), gdiag (d), and
+// for FP32 Pt (d x CB).  *fail is set on a pivot that is not positive or a
+// tensor-core wait that gave up; *eq receives the column-scaled diagonal
+// ratio of k_eq_ratio.
 template <class T>
-ski_status chol_upper(T* G, int64_t ld, int64_t d, T* dinv, T* Pt, int* fail, cudaStream_t st) {
+ski_status chol_upper(T* G, int64_t ld, int64_t d, T* dinv, T* Pt, double* gdiag, double* eq, int* fail,
+                      cudaStream_t st) {
+  k_save_diag<T><<<(unsigned)ski_cdiv(d, 256), 256, 0, st>>>(d, G, ld, gdiag);
+  SKI_LAUNCH_CHECK();
   for (int64_t k0 = 0; k0 < d; k0 += CB) {
     const int nb = (int)std::min<int64_t>(CB, d - k0);
     T* Gk = G + k0 * ld + k0;
@@ -465,6 +650,8 @@ ski_status chol_upper(T* G, int64_t ld, int64_t d, T* dinv, T* Pt, int* fail, cu
       SKI_TRY(ski_gemm_ex<T>(rest, rest, nb, T(-1), R12, 1, ld, R12, ld, 1, T(1), G22, ld, 1, 0, st, 4));
     }
   }
+  k_eq_ratio<T><<<1, 256, 0, st>>>(d, G, ld, gdiag, eq);
+  SKI_LAUNCH_CHECK();
   return SKI_OK;
 }
 
@@ -571,13 +758,15 @@ size_t ski_gram_ws_bytes(int64_t n, int64_t d, int64_t nnz, int32_t s, int64_t m
   ar.take<double>(d);           // SA^T Sb
   ar.take<int>(1);              // failure flag
   ar.take<double>(CB);          // Cholesky: 1 / r_jj of a block
+  ar.take<double>(d + 1);       // Cholesky: diagonal of G, ratio
   return ar.off;
 }
 
 ski_status ski_gram_chol_run(const ski_matrix* A, uint64_t seed, int32_t s, int32_t replace, int64_t m,
                              const double* Sb, int64_t ldsb, double* R, int64_t ldr, double* qtsb, bool* ok,
-                             SkiArena& ar, cudaStream_t st) {
+                             double* eq_ratio, SkiArena& ar, cudaStream_t st) {
   *ok = false;
+  *eq_ratio = INFINITY;
   const int64_t n = A->n, d = A->d, nnz = A->nnz, cap = (int64_t)s * nnz;
   if (A->kind != SKI_CSR || d < 1 || m < 1 || cap >= (1ll << 31)) return SKI_EINVAL;
   const size_t bkb = ski_bucket_ws_bytes(n, s, m);
@@ -598,7 +787,8 @@ ski_status ski_gram_chol_run(const ski_matrix* A, uint64_t seed, int32_t s, int3
   double* cvec = ar.take<double>(d);
   int* fail = ar.take<int>(1);
   double* dinv = ar.take<double>(CB);
-  if (!ar.ok() || !dinv) return SKI_ENOMEM;
+  double* gdiag = ar.take<double>(d + 1);
+  if (!ar.ok() || !gdiag) return SKI_ENOMEM;
   SKI_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), st));
   // 1. bucket lists
   SkiArena bar{bkws, bkb, 0, false};
@@ -645,7 +835,7 @@ ski_status ski_gram_chol_run(const ski_matrix* A, uint64_t seed, int32_t s, int3
     SKI_LAUNCH_CHECK();
   }
   // 5. Cholesky in place
-  SKI_TRY(chol_upper<double>(R, ldr, d, dinv, nullptr, fail, st));
+  SKI_TRY(chol_upper<double>(R, ldr, d, dinv, nullptr, gdiag, gdiag + d, fail, st));
   {
     dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
     k_zero_lower<<<grid, blk, 0, st>>>(d, R, ldr);
@@ -659,14 +849,16 @@ ski_status ski_gram_chol_run(const ski_matrix* A, uint64_t seed, int32_t s, int3
     SKI_CUDA_TRY(cudaMemcpyAsync(qtsb, cvec, d * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
   SKI_CUDA_TRY(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SKI_CUDA_TRY(cudaMemcpyAsync(eq_ratio, gdiag + d, sizeof(double), cudaMemcpyDeviceToHost, st));
   SKI_CUDA_TRY(cudaStreamSynchronize(st));
   *ok = hfail == 0;
   return SKI_OK;
 }
 
 // ---- dense sketch: R from the Cholesky factor of SA^T SA
-// FP64: G = SA^T SA on the FP64 SIMT GEMM (the tiles that meet the upper
-// triangle), then the FP64 blocked Cholesky.  FP32 / TF32: SA^T (the
+// FP64: G = SA^T SA from exact FP16 slice products on the tensor cores
+// (m < 2^16; above, on the FP64 SIMT GEMM), the tiles that meet the upper
+// triangle, then the FP64 blocked Cholesky.  FP32 / TF32: SA^T (the
 // GEMM's K-major operand) by a tile transpose, G on the tensor cores (three
 // TF32 passes for FP32, one for TF32), the Cholesky in FP32, R cast to FP64.
 // Work: m d^2 + d^3 / 3 multiply-adds against 2 m d^2 - 2 d^3 / 3 for the
@@ -677,6 +869,7 @@ size_t ski_gram_dense_ws_bytes(int64_t m, int64_t d, int32_t prec) {
   ar.take<double>(d);                        // SA^T Sb
   ar.take<int>(1);                           // failure flag
   ar.take<double>(ski_cdiv(m, kSatRows) * d);  // SA^T Sb partial sums
+  ar.take<double>(d + 1);                    // Cholesky: diagonal of G, ratio
   if (prec != SKI_F64) {
     const int64_t ldt = ski_round_up(m, 32), ldg = ski_round_up(d, 4);
     ar.take<float>(d * ldt);        // SA^T
@@ -685,26 +878,41 @@ size_t ski_gram_dense_ws_bytes(int64_t m, int64_t d, int32_t prec) {
     ar.take<float>(ldg * CB);       // Cholesky: block row transposed
   } else {
     ar.take<double>(CB);
+    if (oz_beta(m) >= kOzMinBeta) {
+      ar.take<int>(d);                                                    // column exponents
+      ar.take<__half>((int64_t)oz_slices(oz_beta(m)) * d * oz_lds(m));  // slices
+    }
   }
   return ar.off;
 }
 
 ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t d, int32_t prec, double* R,
-                              int64_t ldr, double* qtsb, bool* ok, SkiArena& ar, cudaStream_t st) {
+                              int64_t ldr, double* qtsb, bool* ok, double* eq_ratio, SkiArena& ar,
+                              cudaStream_t st) {
   *ok = false;
+  *eq_ratio = INFINITY;
   if (d < 1 || m < d) return SKI_EINVAL;
   double* cvec = ar.take<double>(d);
   int* fail = ar.take<int>(1);
   double* part = ar.take<double>(ski_cdiv(m, kSatRows) * d);
-  if (!ar.ok() || !part) return SKI_ENOMEM;
+  double* gdiag = ar.take<double>(d + 1);
+  if (!ar.ok() || !gdiag) return SKI_ENOMEM;
   SKI_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), st));
   if (prec == SKI_F64) {
     const double* A = (const double*)SA;
     // G = SA^T SA (upper tiles) into R, in place to its factor
     double* dinv = ar.take<double>(CB);
     if (!ar.ok() || !dinv) return SKI_ENOMEM;
-    SKI_TRY(ski_gemm_ex<double>(d, d, m, 1.0, A, 1, ld_sa, A, ld_sa, 1, 0.0, R, ldr, 1, 0, st, 4));
-    SKI_TRY(chol_upper<double>(R, ldr, d, dinv, nullptr, fail, st));
+    if (oz_beta(m) >= kOzMinBeta) {
+      // G from exact FP16 slice products on the tensor cores
+      int* e = ar.take<int>(d);
+      __half* Sl = ar.take<__half>((int64_t)oz_slices(oz_beta(m)) * d * oz_lds(m));
+      if (!ar.ok() || !Sl) return SKI_ENOMEM;
+      SKI_TRY(oz_gram(A, ld_sa, m, d, R, ldr, e, Sl, fail, st));
+    } else {
+      SKI_TRY(ski_gemm_ex<double>(d, d, m, 1.0, A, 1, ld_sa, A, ld_sa, 1, 0.0, R, ldr, 1, 0, st, 4));
+    }
+    SKI_TRY(chol_upper<double>(R, ldr, d, dinv, nullptr, gdiag, gdiag + d, fail, st));
     dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
     k_zero_lower<<<grid, blk, 0, st>>>(d, R, ldr);
     SKI_LAUNCH_CHECK();
@@ -725,7 +933,7 @@ ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t 
     }
     // G = SA^T SA on the tensor cores (D = At At^T, stored; upper tiles only)
     SKI_TRY(ski_gemm_tf32(At, ldt, At, ldt, d, d, m, G, ldg, 0 | 4, 1, 0, fail, st, prec == SKI_F32));
-    SKI_TRY(chol_upper<float>(G, ldg, d, dinv, Pts, fail, st));
+    SKI_TRY(chol_upper<float>(G, ldg, d, dinv, Pts, gdiag, gdiag + d, fail, st));
     dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
     k_upper_to_f64<<<grid, blk, 0, st>>>(d, G, ldg, R, ldr);
     SKI_LAUNCH_CHECK();
@@ -739,6 +947,7 @@ ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t 
   }
   int hfail = 0;
   SKI_CUDA_TRY(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SKI_CUDA_TRY(cudaMemcpyAsync(eq_ratio, gdiag + d, sizeof(double), cudaMemcpyDeviceToHost, st));
   SKI_CUDA_TRY(cudaStreamSynchronize(st));
   *ok = hfail == 0;
   return SKI_OK;

@@ -104,6 +104,12 @@ ski_status ski_gemm_tf32(const float* A, int64_t lda, const float* B, int64_t ld
                          float* C, int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st,
                          bool split3);
 
+// C64 (+)= scale * A B^T on the tensor cores from FP16 operands (gemm_tc.cu):
+// exact FP32 accumulation for integer operands with partial sums below 2^24
+ski_status ski_gemm_f16_f64acc(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
+                               int64_t K, double* C64, int64_t ldc, double scale, bool upper, int* err,
+                               cudaStream_t st);
+
 // ---- trinv.cu
 size_t ski_trinv_ws_bytes(int64_t d, int32_t dtype);
 ski_status ski_trinv_run(int64_t d, const double* R, int64_t ldr, double* M, double* Mt, int64_t ldm,
@@ -152,13 +158,15 @@ ski_status ski_sample_rows(uint64_t seed, int64_t m, int64_t nrows, const void* 
 // matrix SA^T SA, R = its Cholesky factor (d x d, upper, ldr; lower triangle
 // zeroed) and qtsb = R^{-T} SA^T Sb (Sb: column of the dense sketch, stride
 // ldsb).  *ok = false (R and qtsb unusable) when a sketch row is too long for
-// the shared-memory merge or a Cholesky pivot is not positive; synchronises st.
+// the shared-memory merge or a Cholesky pivot is not positive; *eq_ratio =
+// max_j sqrt(g_jj) / r_jj (infinite when not computed); synchronises st.
 size_t ski_gram_ws_bytes(int64_t n, int64_t d, int64_t nnz, int32_t s, int64_t m);
 ski_status ski_gram_chol_run(const ski_matrix* A, uint64_t seed, int32_t s, int32_t replace, int64_t m,
                              const double* Sb, int64_t ldsb, double* R, int64_t ldr, double* qtsb, bool* ok,
-                             SkiArena& ar, cudaStream_t st);
+                             double* eq_ratio, SkiArena& ar, cudaStream_t st);
 // R from the Cholesky factor of SA^T SA of a dense sketch (SA: m x (d + 1)
 // row-major, FP64 for prec SKI_F64, else FP32; column d holds Sb); *ok as above
 size_t ski_gram_dense_ws_bytes(int64_t m, int64_t d, int32_t prec);
 ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t d, int32_t prec, double* R,
-                              int64_t ldr, double* qtsb, bool* ok, SkiArena& ar, cudaStream_t st);
+                              int64_t ldr, double* qtsb, bool* ok, double* eq_ratio, SkiArena& ar,
+                              cudaStream_t st);

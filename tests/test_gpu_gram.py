@@ -146,3 +146,52 @@ def test_dense_gram_falls_back_when_ill_conditioned(kappa, mixed):
     # FP64 rounding of x alone moves the metric by about 1e-10, so the
     # double-double check allows a few times the acceptance level
     assert olsqr.residual_metric_dd(A, b, x) <= (3e-10 if kappa < 1e8 else 1e-9)
+
+
+@pytest.mark.parametrize("n,d,m", [(40000, 64, 20000), (3000, 130, 2999)])
+def test_dense_fp64_gram_from_slices_matches_the_oracle(n, d, m):
+    # the FP64 Gram matrix from exact FP16 slice products on the tensor cores:
+    # m = 20000 rows leave 4 bits per slice (14 slices), m = 2999 five (11)
+    torch, pkg = cuda()
+    A, b, _ = workloads.gaussian_lls(n, d, seed=n + d + m)
+    x, R, info = _dense_solve(torch, pkg, A, b, m=m, s=1, seed=8, factorization=2)
+    assert info.status == 0 and info.gram == 1
+    xo, oinfo = olsqr.ski_lls(A, b, seed=8, s=1, m=m, factorization="chol")
+    assert rel_fro(R, oinfo["R"]) <= 1e-12
+    assert rel_fro(x, xo) <= 1e-9
+    assert olsqr.residual_metric(A, b, x) <= 1e-10
+
+
+def test_dense_fp64_gram_column_scales():
+    # columns 2^-19 .. 2^19 apart (within the rank rule's 1e-12): each column
+    # of SA keeps its own exponent in the slices, and the fallback test looks
+    # at |SA_j| / r_jj, which such scales leave alone, so the Gram factor is
+    # kept although max r_jj / min r_jj is near 2^38; R = R0 D for the column
+    # scaling D, R0 the oracle's factor of the unscaled problem
+    torch, pkg = cuda()
+    n, d, m = 5000, 96, 400
+    A, b, _ = workloads.gaussian_lls(n, d, seed=31)
+    ex = np.round(np.linspace(-19, 19, d)).astype(int)
+    D = np.ldexp(1.0, ex)
+    x, R, info = _dense_solve(torch, pkg, A * D, b, m=m, s=1, seed=9, factorization=2)
+    assert info.status == 0 and info.gram == 1
+    _, oinfo = olsqr.ski_lls(A, b, seed=9, s=1, m=m, factorization="chol")
+    assert rel_fro(R / D, oinfo["R"]) <= 1e-12
+    assert olsqr.residual_metric(A * D, b, x) <= 1e-10
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_dense_gram_nonfinite_and_singular(mixed):
+    # a NaN in A, or two equal columns: the Gram path reports what the
+    # Householder path reports (SKI_ENONFINITE, SKI_ESINGULAR)
+    torch, pkg = cuda()
+    A, b, _ = workloads.gaussian_lls(500, 20, seed=1)
+    prec = dict(sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32) if mixed else {}
+    An = A.copy()
+    An[17, 5] = np.nan
+    _, _, info = _dense_solve(torch, pkg, An, b, check=False, m=40, s=1, seed=1, factorization=2, **prec)
+    assert info.status == pkg.STATUS.index("SKI_ENONFINITE")
+    Ad = A.copy()
+    Ad[:, 7] = Ad[:, 3]
+    _, _, info = _dense_solve(torch, pkg, Ad, b, check=False, m=40, s=1, seed=1, factorization=2, **prec)
+    assert info.status == pkg.STATUS.index("SKI_ESINGULAR")
