@@ -584,8 +584,40 @@ def run_ours(args, name):
         lls[lab] = {"ms": ig.ms_total, "iters": ig.iters, "restarts": ig.restarts, "status": ig.status,
                     "gram": ig.gram, "rdiag_ratio": ig.rdiag_ratio, "metric": max(r.metric for r in runs),
                     "ms_sketch": ig.ms_sketch, "ms_qr": ig.ms_qr, "ms_trinv": ig.ms_trinv, "ms_lsqr": ig.ms_lsqr,
-                    "timed": False}
+                    "ms_gram_product": ig.ms_qr_gemm, "timed": False}
         del wsg
+    # the Gram products on the tensor cores, against the measured dense bf16
+    # burst (FP16 and BF16 share the nominal rate; TF32 is half of it).
+    # Algorithmic flops of SA^T SA's upper triangle: m d (d + 1); the FP64
+    # form multiplies 66 pairs of FP16 slices (5-bit slices at m = 8000), the
+    # FP32 form three TF32 passes
+    bf16_peak = pj.get("bf16_tflops", 1900.0)
+    n_pairs = 0
+    lg = 0
+    while (1 << lg) <= m:
+        lg += 1
+    beta = (24 - lg) // 2
+    ns = (54 + beta - 1) // beta
+    for tt in range(2, ns + 2):
+        n_pairs += min(ns, tt - 1) - max(1, tt - ns) + 1
+    gflop = m * d * (d + 1)
+    gram_roofline = {}
+    if lls["fp64_gram"]["gram"] and lls["fp64_gram"]["ms_gram_product"] > 0:
+        t = lls["fp64_gram"]["ms_gram_product"] * 1e-3
+        gram_roofline["fp64_slices"] = {
+            "kernel": "k_gemm_tc<256, 4, 0, 1> (kind::f16 slice products, FP64 accumulation)", "bound": "tensor",
+            "pairs": n_pairs, "slice_bits": beta, "achieved": n_pairs * gflop / t / 1e12,
+            "peak": bf16_peak, "unit": "TFLOP/s", "frac": n_pairs * gflop / t / 1e12 / bf16_peak,
+            "fp64_equivalent_tflops": gflop / t / 1e12, "peak_source": "measured bf16 burst", "ms": t * 1e3}
+    if lls["mixed_gram"]["gram"] and lls["mixed_gram"]["ms_gram_product"] > 0:
+        t = lls["mixed_gram"]["ms_gram_product"] * 1e-3
+        passes = 3 if args.qr_mixed != "tf32" else 1
+        gram_roofline["fp32_3xtf32"] = {
+            "kernel": "k_gemm_tc<256, 2, 1> (3-pass TF32 Gram product)" if passes == 3 else
+                      "k_gemm_tc<256, 2, 0> (TF32 Gram product)", "bound": "tensor",
+            "achieved": passes * gflop / t / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
+            "frac": passes * gflop / t / 1e12 / tf32_peak,
+            "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 0.5", "ms": t * 1e3}
 
     # end to end through the public API with host buffers: pinned A, b -> device,
     # ski_sketch_hash, [SA | Sb] -> pinned host
@@ -650,7 +682,8 @@ def run_ours(args, name):
                        "l2": "inputs larger than L2 (A = %.2f GB)" % (8e-9 * n * d),
                        "parallelism": "replicas" if world > 1 else "single"},
             "hbm_frac": value / world / hbm, "roofline": roofline, "sketch_roofline": sketch_roofline,
-            "hash_roofline": hash_roofline, "tc_roofline": tc_roofline, "stages": stages, "lls": lls,
+            "hash_roofline": hash_roofline, "tc_roofline": tc_roofline, "gram_roofline": gram_roofline,
+            "stages": stages, "lls": lls,
             "e2e": e2e, "e2e_solve": e2e_solve, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line), flush=True)

@@ -151,6 +151,7 @@ typedef struct {
   float ms_sketch, ms_qr, ms_trinv, ms_lsqr, ms_total;  /* stage times, CUDA events */
   float ms_premix, ms_gather;  /* inside ms_sketch: the H D premix and the hash gather */
   float ms_qr_gemm;            /* inside ms_qr: the trailing-update GEMMs, summed     */
+                               /* (Step 2 from the Gram matrix: its product SA^T SA)  */
   int32_t qr_fallback;         /* mixed form: 0 kept the FP32/TF32 factor; 1 redid     */
                                /* Steps 1-2 in FP64 (ratio or rank), 2 after its LSQR  */
                                /* run exhausted, or was predicted to exceed, a budget  */

@@ -874,7 +874,8 @@ static ski_status solve_impl(const ski_matrix* A, const double* b, const ski_opt
           SKI_TRY(ski_gram_chol_run(A, of->seed, of->s, of->hash_kind, P.m, (const double*)P.SA + d, P.ld_sa, P.R,
                                     d, P.qtsb, &done, &gram_eq, gar, st));
         else
-          SKI_TRY(ski_gram_dense_run(P.SAq, P.ld_sa, P.m, d, P.qr_prec, P.R, d, P.qtsb, &done, &gram_eq, gar, st));
+          SKI_TRY(ski_gram_dense_run(P.SAq, P.ld_sa, P.m, d, P.qr_prec, P.R, d, P.qtsb, &done, &gram_eq, gar, st,
+                                     info ? &gm : nullptr));
         gram_used = done;
       }
       SkiArena qar{P.stage, P.stage_bytes, 0, false};

@@ -521,10 +521,31 @@ __global__ void k_oz_scale(int64_t d, double* __restrict__ G, int64_t ldg, const
 
 int64_t oz_lds(int64_t m) { return ski_round_up(m, 8); }
 
+// Optional CUDA-event timing of the Gram matrix product (one span on the
+// launching stream); ms() after the stream has been synchronised
+struct SpanTimer {
+  cudaEvent_t e[2] = {nullptr, nullptr};
+  bool on;
+  explicit SpanTimer(bool enable) : on(enable) {
+    if (on && (cudaEventCreate(&e[0]) != cudaSuccess || cudaEventCreate(&e[1]) != cudaSuccess)) on = false;
+  }
+  ~SpanTimer() {
+    for (auto x : e)
+      if (x) cudaEventDestroy(x);
+  }
+  void mark(int i, cudaStream_t st) {
+    if (on) cudaEventRecord(e[i], st);
+  }
+  double ms() {
+    float t = 0.f;
+    return on && cudaEventElapsedTime(&t, e[0], e[1]) == cudaSuccess ? t : 0.0;
+  }
+};
+
 // G (upper triangle, d x d, row stride ldg) = SA^T SA for the FP64 SA (m x d,
 // row stride lda); e: d ints, Sl: ns d lds halves of scratch
 ski_status oz_gram(const double* A, int64_t lda, int64_t m, int64_t d, double* G, int64_t ldg, int* e, __half* Sl,
-                   int* fail, cudaStream_t st) {
+                   int* fail, SpanTimer& tm, cudaStream_t st) {
   const int beta = oz_beta(m), ns = oz_slices(beta);
   const int64_t lds = oz_lds(m), sstride = d * lds;
   SKI_CUDA_TRY(cudaMemsetAsync(e, 0x80, d * sizeof(int), st));
@@ -539,10 +560,12 @@ ski_status oz_gram(const double* A, int64_t lda, int64_t m, int64_t d, double* G
                                                                                            Sl, lds, sstride);
   SKI_LAUNCH_CHECK();
   SKI_CUDA_TRY(cudaMemset2DAsync(G, ldg * sizeof(double), 0, d * sizeof(double), d, st));
+  tm.mark(0, st);
   for (int tt = 2; tt <= ns + 1; ++tt)
     for (int k = std::max(1, tt - ns); k <= std::min(ns, tt - 1); ++k)
       SKI_TRY(ski_gemm_f16_f64acc(Sl + (k - 1) * sstride, lds, Sl + (tt - k - 1) * sstride, lds, d, d, m, G, ldg,
                                   ldexp(1.0, -beta * tt), true, fail, st));
+  tm.mark(1, st);
   dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
   k_oz_scale<<<grid, blk, 0, st>>>(d, G, ldg, e);
   SKI_LAUNCH_CHECK();
@@ -887,10 +910,11 @@ size_t ski_gram_dense_ws_bytes(int64_t m, int64_t d, int32_t prec) {
 }
 
 ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t d, int32_t prec, double* R,
-                              int64_t ldr, double* qtsb, bool* ok, double* eq_ratio, SkiArena& ar,
-                              cudaStream_t st) {
+                              int64_t ldr, double* qtsb, bool* ok, double* eq_ratio, SkiArena& ar, cudaStream_t st,
+                              double* gemm_ms) {
   *ok = false;
   *eq_ratio = INFINITY;
+  SpanTimer tm(gemm_ms != nullptr);
   if (d < 1 || m < d) return SKI_EINVAL;
   double* cvec = ar.take<double>(d);
   int* fail = ar.take<int>(1);
@@ -908,9 +932,11 @@ ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t 
       int* e = ar.take<int>(d);
       __half* Sl = ar.take<__half>((int64_t)oz_slices(oz_beta(m)) * d * oz_lds(m));
       if (!ar.ok() || !Sl) return SKI_ENOMEM;
-      SKI_TRY(oz_gram(A, ld_sa, m, d, R, ldr, e, Sl, fail, st));
+      SKI_TRY(oz_gram(A, ld_sa, m, d, R, ldr, e, Sl, fail, tm, st));
     } else {
+      tm.mark(0, st);
       SKI_TRY(ski_gemm_ex<double>(d, d, m, 1.0, A, 1, ld_sa, A, ld_sa, 1, 0.0, R, ldr, 1, 0, st, 4));
+      tm.mark(1, st);
     }
     SKI_TRY(chol_upper<double>(R, ldr, d, dinv, nullptr, gdiag, gdiag + d, fail, st));
     dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
@@ -932,7 +958,9 @@ ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t 
       SKI_LAUNCH_CHECK();
     }
     // G = SA^T SA on the tensor cores (D = At At^T, stored; upper tiles only)
+    tm.mark(0, st);
     SKI_TRY(ski_gemm_tf32(At, ldt, At, ldt, d, d, m, G, ldg, 0 | 4, 1, 0, fail, st, prec == SKI_F32));
+    tm.mark(1, st);
     SKI_TRY(chol_upper<float>(G, ldg, d, dinv, Pts, gdiag, gdiag + d, fail, st));
     dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
     k_upper_to_f64<<<grid, blk, 0, st>>>(d, G, ldg, R, ldr);
@@ -949,6 +977,7 @@ ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t 
   SKI_CUDA_TRY(cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
   SKI_CUDA_TRY(cudaMemcpyAsync(eq_ratio, gdiag + d, sizeof(double), cudaMemcpyDeviceToHost, st));
   SKI_CUDA_TRY(cudaStreamSynchronize(st));
+  if (gemm_ms) *gemm_ms = tm.ms();
   *ok = hfail == 0;
   return SKI_OK;
 }

@@ -167,6 +167,7 @@ ski_status ski_gram_chol_run(const ski_matrix* A, uint64_t seed, int32_t s, int3
 // R from the Cholesky factor of SA^T SA of a dense sketch (SA: m x (d + 1)
 // row-major, FP64 for prec SKI_F64, else FP32; column d holds Sb); *ok as above
 size_t ski_gram_dense_ws_bytes(int64_t m, int64_t d, int32_t prec);
+// gemm_ms (optional): CUDA-event time of the Gram matrix product
 ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t d, int32_t prec, double* R,
-                              int64_t ldr, double* qtsb, bool* ok, double* eq_ratio, SkiArena& ar,
-                              cudaStream_t st);
+                              int64_t ldr, double* qtsb, bool* ok, double* eq_ratio, SkiArena& ar, cudaStream_t st,
+                              double* gemm_ms = nullptr);
