@@ -450,9 +450,9 @@ def run_ours(args, name):
     # ||A^T r|| / (||A||_F ||r||) <= 1e-10 is then checked (warm restart if not)
     common = dict(m=m, s=s, seed=args.seed, premix=1 if npad else 0, n_pad=npad, tol=1e-10, tau_r=1e-10,
                   premix_slab=args.premix_slab)
-    o64 = pkg.ski_opts_default(**common)
+    o64 = pkg.ski_opts_default(factorization=args.factorization, **common)
     qmx = pkg.SKI_TF32 if args.qr_mixed == "tf32" else pkg.SKI_F32
-    omx = pkg.ski_opts_default(sketch_dtype=pkg.SKI_F32, qr_dtype=qmx, **common)
+    omx = pkg.ski_opts_default(sketch_dtype=pkg.SKI_F32, qr_dtype=qmx, factorization=args.factorization, **common)
     x = torch.empty(d, dtype=torch.float64, device="cuda")
     ws = torch.empty(max(pkg.ski_solve_workspace_size(Amat, o64), pkg.ski_solve_workspace_size(Amat, omx)),
                      dtype=torch.uint8, device="cuda")
@@ -532,6 +532,27 @@ def run_ours(args, name):
                    "achieved": gemm_flops / (g32 * 1e-3) / 1e12, "unit": "TFLOP/s",
                    "peak": tf32_peak, "frac": gemm_flops / (g32 * 1e-3) / 1e12 / tf32_peak,
                    "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 0.5", "ms_per_step": g32}
+    if args.factorization == 2 and infos[-1][0].gram and infos[-1][1].gram:
+        # Step 2 from the Gram matrix in both timed solves: the products are
+        # the FP64 form's 66 FP16 slice pairs and the mixed form's 3 TF32
+        # passes, m d (d + 1) flops each (the upper triangle of SA^T SA)
+        lg = 0
+        while (1 << lg) <= m:
+            lg += 1
+        beta = (24 - lg) // 2
+        ns = (54 + beta - 1) // beta
+        pairs = sum(min(ns, tt - 1) - max(1, tt - ns) + 1 for tt in range(2, ns + 2))
+        gfl = float(m) * d * (d + 1)
+        bfp = pj.get("bf16_tflops", 1900.0)
+        roofline = {"kernel": "k_gemm_tc<256, 4, 0, 1> (FP64 Gram matrix from FP16 slice products)",
+                    "bound": "tensor", "achieved": pairs * gfl / (g64 * 1e-3) / 1e12, "peak": bfp,
+                    "unit": "TFLOP/s", "frac": pairs * gfl / (g64 * 1e-3) / 1e12 / bfp, "traffic": None,
+                    "peak_source": "measured bf16 burst", "pairs": pairs, "flops_per_step": pairs * gfl,
+                    "ms_per_step": g64}
+        tc_roofline = {"kernel": "k_gemm_tc<256, 2, 1> (3-pass TF32 Gram matrix, mixed path)", "bound": "tensor",
+                       "achieved": 3 * gfl / (g32 * 1e-3) / 1e12, "unit": "TFLOP/s", "peak": tf32_peak,
+                       "frac": 3 * gfl / (g32 * 1e-3) / 1e12 / tf32_peak,
+                       "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 0.5", "ms_per_step": g32}
     stages = {
         "premix_and_hash_fp64": {"ms": stage_ms, "bound": "hbm", "algorithmic_bytes": sb,
                                  "achieved_gbs": sb / (stage_ms * 1e-3) / 1e9 if stage_ms > 0 else None},
@@ -678,6 +699,7 @@ def run_ours(args, name):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": name, "n": n, "d": d, "n_pad": npad, "m": m, "s": s, "gamma": cfg["gamma"],
                        "mixed_qr": args.qr_mixed, "premix_slab": args.premix_slab,
+                       "factorization": args.factorization,
                        "A": cfg["kind"], "b": "ones" if cfg["kind"] != "lls" else "A x + 1e-3 N(0,1)",
                        "l2": "inputs larger than L2 (A = %.2f GB)" % (8e-9 * n * d),
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -1215,6 +1237,8 @@ def main():
     ap.add_argument("--sweep", type=int, nargs="*", default=[1], help="batched workload: also time these")
     ap.add_argument("--ref-problems", type=int, default=3, help="batched workload: oracle sample size")
     ap.add_argument("--premix-slab", type=int, default=0, help="premix column slab width (0 = full width)")
+    ap.add_argument("--factorization", type=int, default=0, choices=(0, 2),
+                    help="dense workloads: Step 2 of the timed solves (0 Householder QR, 2 from the Gram matrix)")
     ap.add_argument("--qr-mixed", default="f32", choices=["f32", "tf32"],
                     help="QR precision of the mixed solve: f32 (three TF32 passes) or tf32 (one)")
     ap.add_argument("--sketch-sweep", action="store_true",

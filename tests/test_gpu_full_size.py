@@ -20,18 +20,23 @@ from gpu_util import cuda, to_dev
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("mixed", [False, True])
-def test_dense_test_set_solve_full_size(mixed):
+@pytest.mark.parametrize("mixed,factorization", [(False, 0), (True, 0), (False, 2), (True, 2)])
+def test_dense_test_set_solve_full_size(mixed, factorization):
     # n = 50000, d = 4000, premix to 65536, s = 1, m = 2d (the benchmark's
-    # workload), FP64 and the mixed form (FP32 sketch, three-pass TF32 QR)
+    # workload), FP64 and the mixed form (FP32 sketch, three-pass TF32 QR),
+    # Step 2 by the Householder QR or from the Gram matrix (kept here: the
+    # i.i.d. Gaussian SA is well conditioned)
     torch, pkg = cuda()
     n, d = 50000, 4000
     At, bt = workloads.gaussian_torch(n, d, 20210525, "cuda")
     kw = dict(sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32) if mixed else {}
-    o = pkg.ski_opts_default(m=2 * d, s=1, seed=20210525, premix=1, n_pad=65536, tol=1e-10, tau_r=1e-10, **kw)
+    o = pkg.ski_opts_default(m=2 * d, s=1, seed=20210525, premix=1, n_pad=65536, tol=1e-10, tau_r=1e-10,
+                             factorization=factorization, **kw)
     x = torch.empty(d, dtype=torch.float64, device="cuda")
     info = pkg.ski_solve(pkg.dense_matrix(At), bt, o, x)
     assert info.status == 0 and info.metric <= 1e-10
+    assert info.gram == (1 if factorization == 2 else 0)
+    assert info.iters <= 60
     if mixed:
         assert info.qr_fallback == 0      # i.i.d. Gaussian: the FP32 factor preconditions
     assert olsqr.residual_metric_dd(At.cpu().numpy(), bt.cpu().numpy(), x.cpu().numpy()) <= 1e-10
@@ -52,10 +57,11 @@ def _usv(torch, kappa, rhs="ones"):
     return _USV[key]
 
 
-def _solve_usv(torch, pkg, At, bt, mixed, check=True):
+def _solve_usv(torch, pkg, At, bt, mixed, check=True, factorization=0):
     d = 4000
     kw = dict(sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32) if mixed else {}
-    o = pkg.ski_opts_default(m=2 * d, s=1, seed=20210525, premix=1, n_pad=262144, tol=1e-10, tau_r=1e-10, **kw)
+    o = pkg.ski_opts_default(m=2 * d, s=1, seed=20210525, premix=1, n_pad=262144, tol=1e-10, tau_r=1e-10,
+                             factorization=factorization, **kw)
     x = torch.empty(d, dtype=torch.float64, device="cuda")
     info = pkg.ski_solve(pkg.dense_matrix(At), bt, o, x, check=check)
     host = olsqr.residual_metric_dd(At.cpu().numpy(), bt.cpu().numpy(), x.cpu().numpy())
@@ -84,6 +90,22 @@ def test_mixed_precision_workload_full_size(kappa, rhs, mixed):
     # both sides evaluate r accurately: they differ only by the FP64 rounding
     # of A^T r (about sqrt(n) u relative to ||A|| ||r||, 5e-4 of the metric here)
     assert abs(host - info.metric) <= 0.01 * host
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_mixed_precision_workload_gram_full_size(mixed):
+    # Step 2 from the Gram matrix on the mixed-precision workload at kappa =
+    # 1e6: max |SA_j| / r_jj is near 1e6, past the FP32 Gram's 2^9 (the mixed
+    # form falls back to its Householder QR) and inside the FP64 Gram's 2^23
+    # (the FP64 form keeps the factor of its tensor-core Gram matrix)
+    torch, pkg = cuda()
+    At, bt = _usv(torch, 1e6, "ones")
+    info, host = _solve_usv(torch, pkg, At, bt, mixed, factorization=2)
+    assert info.status == 0 and info.metric <= 1e-10, (info.status, info.metric, info.iters, info.restarts)
+    assert info.gram == (0 if mixed else 1)
+    assert info.qr_fallback == 0
+    assert info.iters <= 62
+    assert host <= 1e-10
 
 
 def test_kappa_1e10_with_b_ones_sits_at_the_fp64_floor():
