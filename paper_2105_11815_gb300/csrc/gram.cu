@@ -542,10 +542,11 @@ struct SpanTimer {
   }
 };
 
-// G (upper triangle, d x d, row stride ldg) = SA^T SA for the FP64 SA (m x d,
-// row stride lda); e: d ints, Sl: ns d lds halves of scratch
-ski_status oz_gram(const double* A, int64_t lda, int64_t m, int64_t d, double* G, int64_t ldg, int* e, __half* Sl,
-                   int* fail, SpanTimer& tm, cudaStream_t st) {
+// P (upper triangle, d x d, row stride ldg) = the slice sum of A^T A for the
+// FP64 A (m x d, row stride lda) without the column scales: P[i][j] 2^(e_i +
+// e_j) = (A^T A)[i][j].  e: d ints, Sl: ns d lds halves of scratch.
+ski_status oz_products(const double* A, int64_t lda, int64_t m, int64_t d, double* G, int64_t ldg, int* e,
+                       __half* Sl, int* fail, SpanTimer& tm, cudaStream_t st) {
   const int beta = oz_beta(m), ns = oz_slices(beta);
   const int64_t lds = oz_lds(m), sstride = d * lds;
   SKI_CUDA_TRY(cudaMemsetAsync(e, 0x80, d * sizeof(int), st));
@@ -566,10 +567,28 @@ ski_status oz_gram(const double* A, int64_t lda, int64_t m, int64_t d, double* G
       SKI_TRY(ski_gemm_f16_f64acc(Sl + (k - 1) * sstride, lds, Sl + (tt - k - 1) * sstride, lds, d, d, m, G, ldg,
                                   ldexp(1.0, -beta * tt), true, fail, st));
   tm.mark(1, st);
+  return SKI_OK;
+}
+
+// G (upper triangle, d x d, row stride ldg) = SA^T SA for the FP64 SA (m x d,
+// row stride lda), from exact slice products
+ski_status oz_gram(const double* A, int64_t lda, int64_t m, int64_t d, double* G, int64_t ldg, int* e, __half* Sl,
+                   int* fail, SpanTimer& tm, cudaStream_t st) {
+  SKI_TRY(oz_products(A, lda, m, d, G, ldg, e, Sl, fail, tm, st));
   dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
   k_oz_scale<<<grid, blk, 0, st>>>(d, G, ldg, e);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
+}
+
+// C[i][j] -= P[i][j] 2^(e_i + e_j) on the upper triangle (n x n)
+__global__ void k_oz_sub(int64_t n, double* __restrict__ C, int64_t ldc, const double* __restrict__ P, int64_t ldp,
+                         const int* __restrict__ e) {
+  const int64_t i = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
+  if (i >= n) return;
+  const int ei = e[i];
+  for (int64_t j = i + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    C[i * ldc + j] -= ldexp(P[i * ldp + j], ei + e[j]);
 }
 
 template <class T>
@@ -678,6 +697,63 @@ ski_status chol_upper(T* G, int64_t ld, int64_t d, T* dinv, T* Pt, double* gdiag
   return SKI_OK;
 }
 
+// FP64 Cholesky in two levels: panels of kOzPanel columns; inside a panel the
+// blocks of CB as above, with the rank-CB update applied only to the panel's
+// later rows (over every column to their right); across panels one update
+// G22 -= R12^T R12 with K = the panel's rows, from exact FP16 slice products
+// of R12 on the tensor cores (P = the unscaled product, then G22 -= P scaled
+// by the column exponents).  Scratch (chol2_bytes): e (d ints), the slices
+// of one panel's R12, P (d x d).
+constexpr int64_t kOzPanel = 512;
+size_t chol2_bytes(int64_t d) {
+  SkiArena ar{nullptr, 0, 0, true};
+  ar.take<int>(d);
+  ar.take<__half>((int64_t)oz_slices(oz_beta(kOzPanel)) * d * oz_lds(kOzPanel));
+  ar.take<double>(d * d);
+  return ar.off;
+}
+bool chol2_applies(int64_t d) { return d > 2 * kOzPanel; }
+
+ski_status chol_upper2(double* G, int64_t ld, int64_t d, double* dinv, double* gdiag, double* eq, int* fail,
+                       SkiArena& ar, cudaStream_t st) {
+  int* e = ar.take<int>(d);
+  __half* Sl = ar.take<__half>((int64_t)oz_slices(oz_beta(kOzPanel)) * d * oz_lds(kOzPanel));
+  double* P = ar.take<double>(d * d);
+  if (!ar.ok() || !P) return SKI_ENOMEM;
+  SpanTimer none(false);
+  k_save_diag<double><<<(unsigned)ski_cdiv(d, 256), 256, 0, st>>>(d, G, ld, gdiag);
+  SKI_LAUNCH_CHECK();
+  for (int64_t K0 = 0; K0 < d; K0 += kOzPanel) {
+    const int64_t Ke = std::min(d, K0 + kOzPanel);
+    for (int64_t k0 = K0; k0 < Ke; k0 += CB) {
+      const int nb = (int)std::min<int64_t>(CB, Ke - k0);
+      double* Gk = G + k0 * ld + k0;
+      k_chol_diag<double><<<1, 256, 0, st>>>(Gk, ld, nb, dinv, fail);
+      SKI_LAUNCH_CHECK();
+      const int64_t rest = d - k0 - nb;
+      if (rest <= 0) continue;
+      k_trsm_row<double><<<(unsigned)ski_cdiv(rest, 32), 32, 0, st>>>(Gk, ld, nb, rest, dinv, nullptr);
+      SKI_LAUNCH_CHECK();
+      const int64_t rows = Ke - k0 - nb;  // the panel's later rows
+      if (rows > 0) {
+        const double* R12 = Gk + nb;
+        SKI_TRY(ski_gemm_ex<double>(rows, rest, nb, -1.0, R12, 1, ld, R12, ld, 1, 1.0, Gk + nb * ld + nb, ld, 1, 0,
+                                    st, 4));
+      }
+    }
+    const int64_t rest = d - Ke;
+    if (rest <= 0) continue;
+    // G22 -= R12^T R12: R12 = rows [K0, Ke), columns [Ke, d)
+    SKI_TRY(oz_products(G + K0 * ld + Ke, ld, Ke - K0, rest, P, rest, e, Sl, fail, none, st));
+    dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(rest, 32)), (unsigned)ski_cdiv(rest, 8));
+    k_oz_sub<<<grid, blk, 0, st>>>(rest, G + Ke * ld + Ke, ld, P, rest, e);
+    SKI_LAUNCH_CHECK();
+  }
+  k_eq_ratio<double><<<1, 256, 0, st>>>(d, G, ld, gdiag, eq);
+  SKI_LAUNCH_CHECK();
+  return SKI_OK;
+}
+
 // forward substitution R11^T y = c for one diagonal block of nb <= 64 rows,
 // in place in c: the block is staged in shared memory by 256 threads (all
 // loads in flight at once), then one warp solves: the reciprocals of the
@@ -782,6 +858,7 @@ size_t ski_gram_ws_bytes(int64_t n, int64_t d, int64_t nnz, int32_t s, int64_t m
   ar.take<int>(1);              // failure flag
   ar.take<double>(CB);          // Cholesky: 1 / r_jj of a block
   ar.take<double>(d + 1);       // Cholesky: diagonal of G, ratio
+  if (chol2_applies(d)) ar.take<char>(chol2_bytes(d));
   return ar.off;
 }
 
@@ -858,7 +935,14 @@ ski_status ski_gram_chol_run(const ski_matrix* A, uint64_t seed, int32_t s, int3
     SKI_LAUNCH_CHECK();
   }
   // 5. Cholesky in place
-  SKI_TRY(chol_upper<double>(R, ldr, d, dinv, nullptr, gdiag, gdiag + d, fail, st));
+  if (chol2_applies(d)) {
+    const size_t cb = chol2_bytes(d);
+    SkiArena car2{ar.take<char>(cb), cb, 0, false};
+    if (!ar.ok()) return SKI_ENOMEM;
+    SKI_TRY(chol_upper2(R, ldr, d, dinv, gdiag, gdiag + d, fail, car2, st));
+  } else {
+    SKI_TRY(chol_upper<double>(R, ldr, d, dinv, nullptr, gdiag, gdiag + d, fail, st));
+  }
   {
     dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
     k_zero_lower<<<grid, blk, 0, st>>>(d, R, ldr);
@@ -901,6 +985,7 @@ size_t ski_gram_dense_ws_bytes(int64_t m, int64_t d, int32_t prec) {
     ar.take<float>(ldg * CB);       // Cholesky: block row transposed
   } else {
     ar.take<double>(CB);
+    if (chol2_applies(d)) ar.take<char>(chol2_bytes(d));
     if (oz_beta(m) >= kOzMinBeta) {
       ar.take<int>(d);                                                    // column exponents
       ar.take<__half>((int64_t)oz_slices(oz_beta(m)) * d * oz_lds(m));  // slices
@@ -926,6 +1011,8 @@ ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t 
     const double* A = (const double*)SA;
     // G = SA^T SA (upper tiles) into R, in place to its factor
     double* dinv = ar.take<double>(CB);
+    const size_t c2b = chol2_applies(d) ? chol2_bytes(d) : 0;
+    char* c2 = c2b ? ar.take<char>(c2b) : nullptr;
     if (!ar.ok() || !dinv) return SKI_ENOMEM;
     if (oz_beta(m) >= kOzMinBeta) {
       // G from exact FP16 slice products on the tensor cores
@@ -938,7 +1025,12 @@ ski_status ski_gram_dense_run(const void* SA, int64_t ld_sa, int64_t m, int64_t 
       SKI_TRY(ski_gemm_ex<double>(d, d, m, 1.0, A, 1, ld_sa, A, ld_sa, 1, 0.0, R, ldr, 1, 0, st, 4));
       tm.mark(1, st);
     }
-    SKI_TRY(chol_upper<double>(R, ldr, d, dinv, nullptr, gdiag, gdiag + d, fail, st));
+    if (chol2_applies(d)) {
+      SkiArena car2{c2, c2b, 0, false};
+      SKI_TRY(chol_upper2(R, ldr, d, dinv, gdiag, gdiag + d, fail, car2, st));
+    } else {
+      SKI_TRY(chol_upper<double>(R, ldr, d, dinv, nullptr, gdiag, gdiag + d, fail, st));
+    }
     dim3 blk(32, 8), grid((unsigned)std::min<int64_t>(64, ski_cdiv(d, 32)), (unsigned)ski_cdiv(d, 8));
     k_zero_lower<<<grid, blk, 0, st>>>(d, R, ldr);
     SKI_LAUNCH_CHECK();

@@ -195,3 +195,26 @@ def test_dense_gram_nonfinite_and_singular(mixed):
     Ad[:, 7] = Ad[:, 3]
     _, _, info = _dense_solve(torch, pkg, Ad, b, check=False, m=40, s=1, seed=1, factorization=2, **prec)
     assert info.status == pkg.STATUS.index("SKI_ESINGULAR")
+
+
+@pytest.mark.parametrize("premix", [0, 1])
+def test_dense_fp64_gram_two_level_cholesky(premix):
+    # d > 1024: the FP64 Cholesky runs in panels of 512 columns, the update
+    # across panels from exact FP16 slice products of the panel's block row
+    # (7-bit slices, K = 512) on the tensor cores; R against the oracle's
+    # FP64 Gram factor
+    torch, pkg = cuda()
+    n, d, m = 9000, 1300, 2600
+    A, b, _ = workloads.gaussian_lls(n, d, seed=77)
+    kw = dict(m=m, s=1, seed=12)
+    npad = 16384
+    if premix:
+        kw.update(premix=1, n_pad=npad)
+    x, R, info = _dense_solve(torch, pkg, A, b, factorization=2, **kw)
+    assert info.status == 0 and info.gram == 1
+    xo, oinfo = olsqr.ski_lls(A, b, seed=12, s=1, m=m, premix=bool(premix), n_pad=npad if premix else None,
+                              factorization="chol")
+    assert rel_fro(R, oinfo["R"]) <= 1e-12
+    assert rel_fro(x, xo) <= 1e-9
+    assert abs(info.iters - oinfo["iters"]) <= 1
+    assert olsqr.residual_metric(A, b, x) <= 1e-10
