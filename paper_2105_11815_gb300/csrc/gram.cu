@@ -348,6 +348,58 @@ __global__ void __launch_bounds__(32) k_trsm_row(T* __restrict__ Gk, int64_t ldg
   }
 }
 
+// The same block-row solve with four lanes per column (FP64, where the
+// FP64 pipe sets the pace): lane t of a column's group holds rows t + 4q; at
+// step i the owner of row i forms y_i and a shuffle gives it to the group,
+// which updates its later rows.  A warp takes 8 columns, so the columns
+// spread over several CTAs per SM and nothing spills.
+__global__ void __launch_bounds__(32) k_trsm_row4(double* __restrict__ Gk, int64_t ldg, int nb, int64_t rest,
+                                                  const double* __restrict__ dinv) {
+  __shared__ double r[CB][CB];
+  __shared__ double di[CB];
+  const int lane = threadIdx.x, t = lane & 3;
+#pragma unroll 1
+  for (int i0 = 0; i0 < CB; i0 += 16) {
+    double v[16][2];
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = i0 + u, k = lane + 32 * h;
+        v[u][h] = (i < nb && k > i && k < nb) ? Gk[i * ldg + k] : 0.0;
+      }
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) r[i0 + u][lane + 32 * h] = v[u][h];
+  }
+  for (int i = lane; i < CB; i += 32) di[i] = i < nb ? dinv[i] : 0.0;
+  __syncthreads();
+  const int64_t c = blockIdx.x * 8ll + (lane >> 2);
+  const bool on = c < rest;
+  double g[CB / 4];
+#pragma unroll
+  for (int q = 0; q < CB / 4; ++q) {
+    const int k = t + 4 * q;
+    g[q] = (on && k < nb) ? Gk[k * ldg + nb + c] : 0.0;
+  }
+#pragma unroll
+  for (int i = 0; i < CB; ++i) {
+    const int qi = i >> 2, ti = i & 3;
+    if (t == ti) g[qi] *= di[i];
+    const double y = __shfl_sync(0xffffffffu, g[qi], (lane & ~3) | ti);
+#pragma unroll
+    for (int q = (i >> 2); q < CB / 4; ++q)
+      if (t + 4 * q > i) g[q] = fma(-r[i][t + 4 * q], y, g[q]);
+  }
+  if (!on) return;
+#pragma unroll
+  for (int q = 0; q < CB / 4; ++q) {
+    const int k = t + 4 * q;
+    if (k < nb) Gk[k * ldg + nb + c] = g[q];
+  }
+}
+
 __global__ void k_zero_lower(int64_t d, double* __restrict__ R, int64_t ldr) {
   const int64_t r = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < d && c < r;
@@ -681,8 +733,11 @@ ski_status chol_upper(T* G, int64_t ld, int64_t d, T* dinv, T* Pt, double* gdiag
     SKI_LAUNCH_CHECK();
     const int64_t rest = d - k0 - nb;
     if (rest <= 0) continue;
-    T* pt = std::is_same<T, float>::value ? Pt : nullptr;
-    k_trsm_row<T><<<(unsigned)ski_cdiv(rest, 32), 32, 0, st>>>(Gk, ld, nb, rest, dinv, pt);
+    if constexpr (std::is_same<T, float>::value) {
+      k_trsm_row<T><<<(unsigned)ski_cdiv(rest, 32), 32, 0, st>>>(Gk, ld, nb, rest, dinv, Pt);
+    } else {
+      k_trsm_row4<<<(unsigned)ski_cdiv(rest, 8), 32, 0, st>>>(Gk, ld, nb, rest, dinv);
+    }
     SKI_LAUNCH_CHECK();
     T* G22 = Gk + nb * ld + nb;
     if constexpr (std::is_same<T, float>::value) {
@@ -732,7 +787,7 @@ ski_status chol_upper2(double* G, int64_t ld, int64_t d, double* dinv, double* g
       SKI_LAUNCH_CHECK();
       const int64_t rest = d - k0 - nb;
       if (rest <= 0) continue;
-      k_trsm_row<double><<<(unsigned)ski_cdiv(rest, 32), 32, 0, st>>>(Gk, ld, nb, rest, dinv, nullptr);
+      k_trsm_row4<<<(unsigned)ski_cdiv(rest, 8), 32, 0, st>>>(Gk, ld, nb, rest, dinv);
       SKI_LAUNCH_CHECK();
       const int64_t rows = Ke - k0 - nb;  // the panel's later rows
       if (rows > 0) {
