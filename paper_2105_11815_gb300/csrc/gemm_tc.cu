@@ -64,6 +64,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
   return false;
 }
 
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -124,13 +132,15 @@ __device__ __forceinline__ void tf32_split(float* hi_tile, float* lo_tile, int c
 // mode 3 (F16 only): C64[m * ldc + n] += scale64 * D (FP64).
 // mode | 4: only the tiles that meet the upper triangle (some m <= n).
 // F16: operands FP16 (a stage is 64 of them per row, the same 128 bytes),
-// multiplied by kind::f16 (K = 16 per instruction); else FP32 as TF32.
+// multiplied by kind::f16 (K = 16 per instruction), read through 3-D tensor
+// maps over a stack of matrices: the accumulator sums A[pr.a[p]] B[pr.b[p]]^T
+// over the pr.n pairs p (K each); else FP32 as TF32.
 template <int BN, int STAGES, bool SPLIT, bool F16 = false>
 __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ta,
                                                       const __grid_constant__ CUtensorMap tb, int M, int N, int K,
                                                       int kchunk, float* __restrict__ C, int64_t ldc,
                                                       int64_t c_zstride, int mode, int* err,
-                                                      double* __restrict__ C64, double scale64) {
+                                                      double* __restrict__ C64, double scale64, TcPairs pr) {
   static_assert(!(F16 && SPLIT), "the split form is for FP32 operands");
   constexpr int BKE = F16 ? 2 * BK : BK;  // K elements per stage
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -140,7 +150,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
-  const int nk = kend > kbeg ? (kend - kbeg + BKE - 1) / BKE : 0;
+  const int nkp = kend > kbeg ? (kend - kbeg + BKE - 1) / BKE : 0;  // K steps of one pair
+  const int nk = F16 ? nkp * pr.n : nkp;
   C += (int64_t)blockIdx.z * c_zstride;
   if ((mode & 4) && m0 >= n0 + BN) return;  // the whole tile is below the diagonal (CTA-uniform)
   mode &= 3;
@@ -173,9 +184,15 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_tc(const __grid_constant__ CUt
       const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
       if (!mbar_wait(smem_u32(&sm.empty[s]), ph ^ 1u, err)) break;
       mbar_expect_tx(smem_u32(&sm.full[s]), bytes);
-      const int kx = kbeg + kt * BKE;
-      tma_load_2d(smem_u32(sm.A[s]), &ta, kx, m0, smem_u32(&sm.full[s]));
-      tma_load_2d(smem_u32(sm.B[s]), &tb, kx, n0, smem_u32(&sm.full[s]));
+      if constexpr (F16) {
+        const int p = kt / nkp, kx = kbeg + (kt - p * nkp) * BKE;
+        tma_load_3d(smem_u32(sm.A[s]), &ta, kx, m0, pr.a[p], smem_u32(&sm.full[s]));
+        tma_load_3d(smem_u32(sm.B[s]), &tb, kx, n0, pr.b[p], smem_u32(&sm.full[s]));
+      } else {
+        const int kx = kbeg + kt * BKE;
+        tma_load_2d(smem_u32(sm.A[s]), &ta, kx, m0, smem_u32(&sm.full[s]));
+        tma_load_2d(smem_u32(sm.B[s]), &tb, kx, n0, smem_u32(&sm.full[s]));
+      }
       ++issued;
     }
     if (issued < nk) {
@@ -369,17 +386,19 @@ bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, i
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// 2-D FP16 tensor map over a row-major (rows x cols) matrix with row stride
-// ld elements; box = box_rows x 64 columns (128 bytes), 128-byte swizzle;
-// reads outside the matrix fill with zeros.
-bool make_map_f16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+// 3-D FP16 tensor map over a stack of ns row-major (rows x cols) matrices,
+// row stride ld elements, matrix stride mstride elements; box = box_rows x 64
+// columns (128 bytes) of one matrix, 128-byte swizzle; reads outside fill
+// with zeros.
+bool make_map_f16_3d(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int64_t mstride,
+                     int ns, int box_rows) {
   EncodeTiled fn = encoder();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)(2 * BK), (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)base, dims, strides, box, estr,
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)ns};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(mstride * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)(2 * BK), (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, (void*)base, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -419,7 +438,7 @@ ski_status launch(const float* A, int64_t lda, const float* B, int64_t ldb, int 
   const int kchunk = (int)ski_round_up(ski_cdiv(K, splits), BK);
   dim3 grid((unsigned)ski_cdiv(M, BM), (unsigned)ski_cdiv(N, BN), (unsigned)splits);
   k_gemm_tc<BN, STAGES, SPLIT><<<grid, NTHR, smem, st>>>(ta, tb, M, N, K, kchunk, C, ldc, c_zstride, mode, err,
-                                                          nullptr, 0.0);
+                                                          nullptr, 0.0, TcPairs{});
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }
@@ -459,29 +478,35 @@ ski_status ski_gemm_tf32(const float* A, int64_t lda, const float* B, int64_t ld
   return dispatch<false>(A, lda, B, ldb, (int)M, (int)N, (int)K, C, ldc, mode, splits, c_zstride, err, st);
 }
 
-// C64 (+)= scale * A B^T with A (M x K) and B (N x K) FP16, row-major and
-// K-contiguous (row strides lda, ldb: multiples of 8; 16-byte aligned bases),
-// multiplied on the tensor cores (kind::f16) with FP32 accumulation, then
-// scaled and added to the FP64 C64 in the epilogue.  The FP32 accumulation is
-// exact when the operands are integers and every partial sum stays below
-// 2^24 in magnitude.  upper: only the tiles that meet the upper triangle.
-ski_status ski_gemm_f16_f64acc(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
-                               int64_t K, double* C64, int64_t ldc, double scale, bool upper, int* err,
-                               cudaStream_t st) {
-  if (M <= 0 || N <= 0) return SKI_OK;
-  if ((lda & 7) || (ldb & 7) || ((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return SKI_EINVAL;
-  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return SKI_EINVAL;
+// C64 += scale * sum over the pairs p of S[pr.a[p]] S[pr.b[p]]^T, S a stack
+// of ns FP16 matrices (rows x K each, row-major and K-contiguous; row stride
+// lds, a multiple of 8; matrix stride sstride; 16-byte aligned base),
+// multiplied on the tensor cores (kind::f16) with one FP32 accumulator for
+// all the pairs, then scaled and added to the FP64 C64 (rows x rows) in the
+// epilogue.  The accumulation is exact when the operands are integers and
+// every partial sum stays below 2^24 in magnitude.  upper: only the tiles
+// that meet the upper triangle.
+ski_status ski_gemm_f16_pairs_f64acc(const void* S, int64_t lds, int64_t sstride, int ns, int64_t rows, int64_t K,
+                                     const TcPairs& pr, double* C64, int64_t ldc, double scale, bool upper, int* err,
+                                     cudaStream_t st) {
+  if (rows <= 0 || pr.n <= 0) return SKI_OK;
+  if (pr.n > kTcMaxPairs || ns < 1) return SKI_EINVAL;
+  for (int p = 0; p < pr.n; ++p)
+    if (pr.a[p] < 0 || pr.a[p] >= ns || pr.b[p] < 0 || pr.b[p] >= ns) return SKI_EINVAL;
+  if ((lds & 7) || (sstride & 7) || ((uintptr_t)S & 15)) return SKI_EINVAL;
+  if (rows > INT32_MAX || K > INT32_MAX) return SKI_EINVAL;
   constexpr int BNF = 256, STF = 4;
   CUtensorMap ta, tb;
-  if (!make_map_f16(&ta, A, M, K, lda, BM) || !make_map_f16(&tb, B, N, K, ldb, BNF)) return SKI_ECUDA;
+  if (!make_map_f16_3d(&ta, S, rows, K, lds, sstride, ns, BM) || !make_map_f16_3d(&tb, S, rows, K, lds, sstride, ns, BNF))
+    return SKI_ECUDA;
   const size_t smem = sizeof(TcSmem<BNF, STF, false>) + 1024;
   static_assert(sizeof(TcSmem<BNF, STF, false>) + 1024 <= 227 * 1024, "shared memory");
   SKI_CUDA_TRY(ski_attr_once((const void*)k_gemm_tc<BNF, STF, false, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, [&] { return (int)smem; }));
-  dim3 grid((unsigned)ski_cdiv(M, BM), (unsigned)ski_cdiv(N, BNF), 1);
-  k_gemm_tc<BNF, STF, false, true><<<grid, NTHR, smem, st>>>(ta, tb, (int)M, (int)N, (int)K,
+  dim3 grid((unsigned)ski_cdiv(rows, BM), (unsigned)ski_cdiv(rows, BNF), 1);
+  k_gemm_tc<BNF, STF, false, true><<<grid, NTHR, smem, st>>>(ta, tb, (int)rows, (int)rows, (int)K,
                                                               (int)ski_round_up(K, 2 * BK), nullptr, ldc, 0,
-                                                              3 | (upper ? 4 : 0), err, C64, scale);
+                                                              3 | (upper ? 4 : 0), err, C64, scale, pr);
   SKI_LAUNCH_CHECK();
   return SKI_OK;
 }

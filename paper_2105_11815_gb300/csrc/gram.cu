@@ -459,8 +459,9 @@ constexpr int64_t kSatRows = 256;  // rows of the sketch per partial sum
 // slices summed over m rows stays below m 2^(2 beta) < 2^24, so the tensor
 // cores' FP32 accumulation of FP16 slice products is exact; G = 2^(e_i + e_j)
 // sum over k + l <= s + 1 of 2^(-beta (k + l)) S_k^T S_l, added in FP64 in
-// decreasing order of magnitude.  The dropped pairs are below 2^(-beta s) per
-// row of the normalised columns.
+// decreasing order of magnitude.  Pairs of one weight k + l share an FP32
+// accumulator while the bound on its sum stays below 2^24.  The dropped
+// pairs are below 2^(-beta s) per row of the normalised columns.
 int oz_beta(int64_t m) {
   int lg = 0;
   while ((1ll << lg) <= m) ++lg;  // m < 2^lg
@@ -614,10 +615,31 @@ ski_status oz_products(const double* A, int64_t lda, int64_t m, int64_t d, doubl
   SKI_LAUNCH_CHECK();
   SKI_CUDA_TRY(cudaMemset2DAsync(G, ldg * sizeof(double), 0, d * sizeof(double), d, st));
   tm.mark(0, st);
-  for (int tt = 2; tt <= ns + 1; ++tt)
-    for (int k = std::max(1, tt - ns); k <= std::min(ns, tt - 1); ++k)
-      SKI_TRY(ski_gemm_f16_f64acc(Sl + (k - 1) * sstride, lds, Sl + (tt - k - 1) * sstride, lds, d, d, m, G, ldg,
-                                  ldexp(1.0, -beta * tt), true, fail, st));
+  // the pairs of one weight t = k + l share an accumulator while the bound
+  // on its sum, m |S_k|max |S_l|max summed over them, stays below 2^24
+  // (|S_1| <= 2^beta, |S_k| <= 2^(beta-1) after it)
+  auto smax = [&](int k) { return k == 1 ? (double)(1 << beta) : (double)(1 << (beta - 1)); };
+  for (int tt = 2; tt <= ns + 1; ++tt) {
+    TcPairs pr{};
+    double bound = 0.0;
+    auto flush = [&]() -> ski_status {
+      if (pr.n == 0) return SKI_OK;
+      SKI_TRY(ski_gemm_f16_pairs_f64acc(Sl, lds, sstride, ns, d, m, pr, G, ldg, ldexp(1.0, -beta * tt), true, fail,
+                                        st));
+      pr.n = 0;
+      bound = 0.0;
+      return SKI_OK;
+    };
+    for (int k = std::max(1, tt - ns); k <= std::min(ns, tt - 1); ++k) {
+      const double b = (double)m * smax(k) * smax(tt - k);
+      if (pr.n == kTcMaxPairs || (pr.n > 0 && bound + b >= 16777216.0)) SKI_TRY(flush());
+      pr.a[pr.n] = (int8_t)(k - 1);
+      pr.b[pr.n] = (int8_t)(tt - k - 1);
+      ++pr.n;
+      bound += b;
+    }
+    SKI_TRY(flush());
+  }
   tm.mark(1, st);
   return SKI_OK;
 }

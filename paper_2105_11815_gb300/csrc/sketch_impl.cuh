@@ -104,11 +104,17 @@ ski_status ski_gemm_tf32(const float* A, int64_t lda, const float* B, int64_t ld
                          float* C, int64_t ldc, int mode, int splits, int64_t c_zstride, int* err, cudaStream_t st,
                          bool split3);
 
-// C64 (+)= scale * A B^T on the tensor cores from FP16 operands (gemm_tc.cu):
-// exact FP32 accumulation for integer operands with partial sums below 2^24
-ski_status ski_gemm_f16_f64acc(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int64_t N,
-                               int64_t K, double* C64, int64_t ldc, double scale, bool upper, int* err,
-                               cudaStream_t st);
+// C64 += scale * sum over pairs of S[a] S[b]^T on the tensor cores from a
+// stack S of FP16 matrices (gemm_tc.cu): one FP32 accumulator for the pairs,
+// exact for integer operands with partial sums below 2^24
+constexpr int kTcMaxPairs = 16;
+struct TcPairs {
+  int n;
+  int8_t a[kTcMaxPairs], b[kTcMaxPairs];
+};
+ski_status ski_gemm_f16_pairs_f64acc(const void* S, int64_t lds, int64_t sstride, int ns, int64_t rows, int64_t K,
+                                     const TcPairs& pr, double* C64, int64_t ldc, double scale, bool upper, int* err,
+                                     cudaStream_t st);
 
 // ---- trinv.cu
 size_t ski_trinv_ws_bytes(int64_t d, int32_t dtype);
