@@ -259,7 +259,9 @@ __global__ void __launch_bounds__(256) k_chol_diag(T* __restrict__ G, int64_t ld
           T piv = __shfl_sync(0xffffffffu, j < 32 ? v0[q] : v1[q], j & 31);
           const bool bad = !(piv > T(0));
           if (bad) piv = T(1);
-          const T r = sqrt(piv), ir = T(1) / r;
+          // one reciprocal square root and a product (within an ulp or two of
+          // sqrt and its reciprocal): the shortest chain on the pivot's path
+          const T ir = rsqrt(piv), r = piv * ir;
           if (tid == 0) {
             if (bad) atomicExch(fail, 1);
             dinv[j] = ir;
