@@ -96,6 +96,24 @@ struct SkiArena {
   bool ok() const { return dry || off <= cap; }
 };
 
+// One lane's share of a row dot product: sum over c = c0, c0 + 32, ... < c1
+// of m[c] x[c], with eight independent accumulators so that eight loads of
+// the row are in flight per lane (one chain left the pass latency-bound)
+__device__ __forceinline__ double row_dot8(const double* __restrict__ m, const double* __restrict__ x, int64_t c0,
+                                           int64_t c1) {
+  double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int64_t c = c0;
+  for (; c + 7 * 32 < c1; c += 8 * 32) {
+    double mv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) mv[u] = __ldcs(&m[c + 32 * u]);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = fma(mv[u], x[c + 32 * u], a[u]);
+  }
+  for (; c < c1; c += 32) a[0] = fma(__ldcs(&m[c]), x[c], a[0]);
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
 // ----------------------------------------------------------------- device
 __device__ __forceinline__ double ski_warp_sum(double v) {
 #pragma unroll

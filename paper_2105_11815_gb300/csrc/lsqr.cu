@@ -41,8 +41,7 @@ __global__ void __launch_bounds__(256) k_trmv(int64_t d, const double* __restric
   if (row >= d) return;
   const int64_t c0 = UPPER ? row : 0, c1 = UPPER ? d : row + 1;
   const double* mr = M + row * ldm;
-  double acc = 0.0;
-  for (int64_t c = c0 + lane; c < c1; c += 32) acc = fma(__ldcs(&mr[c]), x[c], acc);
+  double acc = row_dot8(mr, x, c0 + lane, c1);
   acc = ski_warp_sum(acc);
   if (lane == 0) y[row] = add ? add[row] + acc : acc;
 }

@@ -606,8 +606,7 @@ __device__ __forceinline__ void trmv_lower_vp_body(int64_t d, const double* __re
   double vv = 0.0;
   if (row < d) {
     const double* mr = Mt + row * d;
-    double acc = 0.0;
-    for (int64_t c = lane; c <= row; c += 32) acc = fma(__ldcs(&mr[c]), q[c], acc);
+    double acc = row_dot8(mr, q, lane, row + 1);
     acc = ski_warp_sum(acc);
     const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
     double x = acc * ib;
@@ -720,8 +719,7 @@ __device__ __forceinline__ void trmv_upper_update_body(int64_t d, const double* 
   }
   if (done) return;
   const double* mr = M + row * d;
-  double acc = 0.0;
-  for (int64_t c = row + lane; c < d; c += 32) acc = fma(__ldcs(&mr[c]), vp[c], acc);
+  double acc = row_dot8(mr, vp, row + lane, d);
   acc = ski_warp_sum(acc);
   if (lane == 0) z[row] = acc * ia;
 }
