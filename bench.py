@@ -88,6 +88,10 @@ GATHER_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 2425076480 + 236391168}
 # DRAM bytes (read + write) per step of the FP64 QR trailing-update GEMMs
 # (k_gemm<double>): the sum over the 472 launches of one step of ncu's
 # dram__bytes_read.sum (27379879168) and dram__bytes_write.sum (6929454592)
+# DRAM bytes per step of the grouped FP16 slice-product launches that form
+# SA^T SA in the FP64 solve (one ncu capture of the three DRAM/time metrics,
+# one pass, full size)
+GRAM64_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 10297787904 + 580307200}
 GEMM64_TRAFFIC = {"dense_50000x4000_hrht_s1_g2": 27379879168 + 6929454592}
 
 
@@ -546,9 +550,12 @@ def run_ours(args, name):
         bfp = pj.get("bf16_tflops", 1900.0)
         roofline = {"kernel": "k_gemm_tc<256, 4, 0, 1> (FP64 Gram matrix from FP16 slice products)",
                     "bound": "tensor", "achieved": pairs * gfl / (g64 * 1e-3) / 1e12, "peak": bfp,
-                    "unit": "TFLOP/s", "frac": pairs * gfl / (g64 * 1e-3) / 1e12 / bfp, "traffic": None,
+                    "unit": "TFLOP/s", "frac": pairs * gfl / (g64 * 1e-3) / 1e12 / bfp,
+                    "traffic": GRAM64_TRAFFIC.get(name),
+                    "traffic_scope": "bytes per step, summed over the grouped slice-product launches that form "
+                                     "SA^T SA",
                     "peak_source": "measured bf16 burst", "pairs": pairs, "flops_per_step": pairs * gfl,
-                    "ms_per_step": g64}
+                    "fp64_equivalent_tflops": gfl / (g64 * 1e-3) / 1e12, "ms_per_step": g64}
         tc_roofline = {"kernel": "k_gemm_tc<256, 2, 1> (3-pass TF32 Gram matrix, mixed path)", "bound": "tensor",
                        "achieved": 3 * gfl / (g32 * 1e-3) / 1e12, "unit": "TFLOP/s", "peak": tf32_peak,
                        "frac": 3 * gfl / (g32 * 1e-3) / 1e12 / tf32_peak,
@@ -562,6 +569,15 @@ def run_ours(args, name):
         "qr_fp32": {"ms": qrmx, "bound": "alu", "flops": qr_flops,
                     "achieved_tflops": qr_flops / (qrmx * 1e-3) / 1e12, "peak_tflops": FP32_PEAK_TFLOPS},
     }
+    if args.factorization == 2:
+        # Step 2 from the Gram matrix: G's upper triangle and the Cholesky,
+        # FP64-equivalent flops (the FP64 form runs G on the tensor cores)
+        s2 = float(m) * d * (d + 1) + d ** 3 / 3.0
+        del stages["qr_fp64"], stages["qr_fp32"]
+        stages["step2_fp64"] = {"ms": qr64, "method": "gram" if infos[-1][0].gram else "householder (fallback)",
+                                "flops": s2, "achieved_tflops": s2 / (qr64 * 1e-3) / 1e12}
+        stages["step2_fp32"] = {"ms": qrmx, "method": "gram" if infos[-1][1].gram else "householder (fallback)",
+                                "flops": s2, "achieved_tflops": s2 / (qrmx * 1e-3) / 1e12}
     if npad and not args.no_dht:
         stages.update(dht_sketch_stages(pkg, Amat, bt, cfg, args, sb))
     lls = {
@@ -570,14 +586,18 @@ def run_ours(args, name):
                  "rdiag_ratio": infos[-1][0].rdiag_ratio,
                  "metric": max(i.metric for i, _ in infos), "ms_sketch": sk_ms, "ms_qr": qr64,
                  "ms_trinv": statistics.mean(i.ms_trinv for i, _ in infos),
-                 "ms_lsqr": statistics.mean(i.ms_lsqr for i, _ in infos)},
+                 "ms_lsqr": statistics.mean(i.ms_lsqr for i, _ in infos),
+                 "factorization": args.factorization, "gram": infos[-1][0].gram,
+                 "ms_gram_product": statistics.mean(i.ms_qr_gemm for i, _ in infos) if infos[-1][0].gram else 0.0},
         "mixed_fp32": {"ms": statistics.mean(j.ms_total for _, j in infos), "iters": infos[-1][1].iters,
                        "restarts": infos[-1][1].restarts, "status": infos[-1][1].status,
                        "qr_fallback": infos[-1][1].qr_fallback, "rdiag_ratio": infos[-1][1].rdiag_ratio,
                        "metric": max(j.metric for _, j in infos),
                        "ms_sketch": statistics.mean(j.ms_sketch for _, j in infos), "ms_qr": qrmx,
                        "ms_trinv": statistics.mean(j.ms_trinv for _, j in infos),
-                       "ms_lsqr": statistics.mean(j.ms_lsqr for _, j in infos)},
+                       "ms_lsqr": statistics.mean(j.ms_lsqr for _, j in infos),
+                       "factorization": args.factorization, "gram": infos[-1][1].gram,
+                       "ms_gram_product": statistics.mean(j.ms_qr_gemm for _, j in infos) if infos[-1][1].gram else 0.0},
     }
 
     # the BF16 form (BF16 premix and sketch, 3-pass TF32 QR of the BF16 sketch,
@@ -592,13 +612,16 @@ def run_ours(args, name):
                          "qr_fallback": ib.qr_fallback, "rdiag_ratio": ib.rdiag_ratio, "metric": ib.metric,
                          "ms_sketch": ib.ms_sketch, "ms_qr": ib.ms_qr, "ms_trinv": ib.ms_trinv,
                          "ms_lsqr": ib.ms_lsqr, "timed": False}
-    # Step 2 from the Gram matrix (factorization = 2: R the Cholesky factor of
-    # SA^T SA, the Householder QR past the diagonal-ratio limit), FP64 and
-    # mixed (G on the tensor cores, Cholesky in FP32), outside the timed step:
-    # the best of three solves after one untimed
-    for lab, oo in (("fp64_gram", pkg.ski_opts_default(factorization=2, **common)),
-                    ("mixed_gram", pkg.ski_opts_default(factorization=2, sketch_dtype=pkg.SKI_F32, qr_dtype=qmx,
-                                                        **common))):
+    # Step 2 the other way, outside the timed step (the best of three solves
+    # after one untimed): with the Gram matrix in the timed step (the default,
+    # factorization = 2: R the Cholesky factor of SA^T SA, the Householder QR
+    # past the ratio limit), the Householder QR of SA (Algorithm 1 as printed,
+    # factorization = 0), and the other way round
+    other = 0 if args.factorization == 2 else 2
+    tag = "householder" if other == 0 else "gram"
+    for lab, oo in (("fp64_" + tag, pkg.ski_opts_default(factorization=other, **common)),
+                    ("mixed_" + tag, pkg.ski_opts_default(factorization=other, sketch_dtype=pkg.SKI_F32,
+                                                          qr_dtype=qmx, **common))):
         wsg = torch.empty(pkg.ski_solve_workspace_size(Amat, oo), dtype=torch.uint8, device="cuda")
         runs = [pkg.ski_solve(Amat, bt, oo, x, ws=wsg, check=False) for _ in range(4)][1:]
         ig = min(runs, key=lambda r: r.ms_total)
@@ -623,15 +646,17 @@ def run_ours(args, name):
         n_pairs += min(ns, tt - 1) - max(1, tt - ns) + 1
     gflop = m * d * (d + 1)
     gram_roofline = {}
-    if lls["fp64_gram"]["gram"] and lls["fp64_gram"]["ms_gram_product"] > 0:
-        t = lls["fp64_gram"]["ms_gram_product"] * 1e-3
+    g_fp64 = lls["fp64"] if args.factorization == 2 else lls["fp64_gram"]
+    g_mx = lls["mixed_fp32"] if args.factorization == 2 else lls["mixed_gram"]
+    if g_fp64["gram"] and g_fp64["ms_gram_product"] > 0:
+        t = g_fp64["ms_gram_product"] * 1e-3
         gram_roofline["fp64_slices"] = {
             "kernel": "k_gemm_tc<256, 4, 0, 1> (kind::f16 slice products, FP64 accumulation)", "bound": "tensor",
             "pairs": n_pairs, "slice_bits": beta, "achieved": n_pairs * gflop / t / 1e12,
             "peak": bf16_peak, "unit": "TFLOP/s", "frac": n_pairs * gflop / t / 1e12 / bf16_peak,
             "fp64_equivalent_tflops": gflop / t / 1e12, "peak_source": "measured bf16 burst", "ms": t * 1e3}
-    if lls["mixed_gram"]["gram"] and lls["mixed_gram"]["ms_gram_product"] > 0:
-        t = lls["mixed_gram"]["ms_gram_product"] * 1e-3
+    if g_mx["gram"] and g_mx["ms_gram_product"] > 0:
+        t = g_mx["ms_gram_product"] * 1e-3
         passes = 3 if args.qr_mixed != "tf32" else 1
         gram_roofline["fp32_3xtf32"] = {
             "kernel": "k_gemm_tc<256, 2, 1> (3-pass TF32 Gram product)" if passes == 3 else
@@ -1237,8 +1262,9 @@ def main():
     ap.add_argument("--sweep", type=int, nargs="*", default=[1], help="batched workload: also time these")
     ap.add_argument("--ref-problems", type=int, default=3, help="batched workload: oracle sample size")
     ap.add_argument("--premix-slab", type=int, default=0, help="premix column slab width (0 = full width)")
-    ap.add_argument("--factorization", type=int, default=0, choices=(0, 2),
-                    help="dense workloads: Step 2 of the timed solves (0 Householder QR, 2 from the Gram matrix)")
+    ap.add_argument("--factorization", type=int, default=2, choices=(0, 2),
+                    help="dense workloads: Step 2 of the timed solves (2 from the Gram matrix SA^T SA, with the "
+                         "Householder QR past its ratio limit; 0 the Householder QR); the other runs untimed")
     ap.add_argument("--qr-mixed", default="f32", choices=["f32", "tf32"],
                     help="QR precision of the mixed solve: f32 (three TF32 passes) or tf32 (one)")
     ap.add_argument("--sketch-sweep", action="store_true",
