@@ -1038,7 +1038,7 @@ def run_batched(args, name):
 
     def opts(streams, batch_lsqr=args.batch_lsqr):
         return pkg.ski_opts_default(m=-int(round(1000 * gamma)), s=1, seed=args.seed, tol=1e-10, tau_r=1e-10,
-                                    streams=streams, batch_lsqr=batch_lsqr, **prec)
+                                    streams=streams, batch_lsqr=batch_lsqr, factorization=args.factorization, **prec)
 
     wsz = {}
 
@@ -1165,6 +1165,7 @@ def run_batched(args, name):
             "config": {"workload": name, "problems": count, "gamma": gamma, "s": 1,
                        "sketch_qr": args.batch_precision,
                        "streams": o_main.streams or "auto", "batch_lsqr": o_main.batch_lsqr,
+                       "factorization": args.factorization,
                        "lsqr_pass": o_main.lsqr_pass,
                        "lsqr_ctas": o_main.lsqr_ctas, "graphs": o_main.graphs, "autotune": tuned, "A_bytes": 8 * nA,
                        "l2": "inputs larger than L2 (%.1f GB)" % (8e-9 * nA),

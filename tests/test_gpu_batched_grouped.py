@@ -78,3 +78,26 @@ def test_grouped_batch_across_every_pass_class():
     for i in range(len(shapes)):
         assert ig[i].status == 0 and ig[i].iters == io[i].iters and np.array_equal(xg[i], xo[i]), i
         assert olsqr.residual_metric_dd(As[i].cpu().numpy(), bs[i].cpu().numpy(), xg[i]) <= 1e-10
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_with_gram_step2_matches_single_solves(mixed):
+    # Step 2 from the Gram matrix in a batch (several problems in flight on
+    # their streams): each problem's x, R factor choice and iteration count
+    # equal its own ski_solve with the same options, bit for bit
+    torch, pkg = cuda()
+    shapes, As, bs = workloads.ragged_batch_torch(10, 4242, "cuda")
+    prec = dict(sketch_dtype=pkg.SKI_F32, qr_dtype=pkg.SKI_F32) if mixed else {}
+    mats = [pkg.dense_matrix(a) for a in As]
+    base = dict(s=1, tol=1e-10, tau_r=1e-12, factorization=2, **prec)
+    # in a batch, m = -2000 gives each problem m = 2 d, and problem i draws
+    # its sketch with seed + i; a single solve takes both itself
+    xb, ib = _solve(torch, pkg, mats, bs, shapes, pkg.ski_opts_default(m=-2000, seed=5, streams=4, **base))
+    for i, (n, d) in enumerate(shapes):
+        x = torch.empty(d, dtype=torch.float64, device="cuda")
+        info = pkg.ski_solve(mats[i], bs[i], pkg.ski_opts_default(m=2 * d, seed=5 + i, **base), x)
+        assert ib[i].status == 0 and info.status == 0, (i, ib[i].status, info.status)
+        assert ib[i].gram == info.gram == 1, (i, ib[i].gram, info.gram)
+        assert ib[i].iters == info.iters, (i, ib[i].iters, info.iters)
+        assert np.array_equal(xb[i], x.cpu().numpy()), i
+        assert olsqr.residual_metric_dd(As[i].cpu().numpy(), bs[i].cpu().numpy(), xb[i]) <= 1e-10
