@@ -144,6 +144,24 @@ def test_workspace_queries_are_consistent(lib):
     assert L.ski_sketch_workspace_size(ctypes.byref(A), 1, ctypes.byref(bad)) == 0
 
 
+def test_gram_step2_workspace_covers_its_scratch(lib):
+    # factorization = 2 for dense A: the FP64 slices of SA (11 FP16 slices of
+    # d x m at m = 8000) and, for d > 1024, the d x d FP64 panel product come
+    # out of the same workspace; the mixed form is sized for its FP64
+    # fallback too
+    L = lib.lib()
+    A = _fake_dense(lib, 50000, 4000)
+    sizes = {}
+    for f in (0, 2):
+        for mixed in (False, True):
+            prec = dict(sketch_dtype=lib.SKI_F32, qr_dtype=lib.SKI_F32) if mixed else {}
+            o = lib.ski_opts_default(m=8000, s=1, factorization=f, **prec)
+            sizes[f, mixed] = L.ski_solve_workspace_size(ctypes.byref(A), ctypes.byref(o))
+    assert sizes[2, False] > sizes[0, False] > 0
+    assert sizes[2, False] >= 11 * 4000 * 8000 * 2 + 4000 * 4000 * 8
+    assert sizes[2, True] >= sizes[2, False]
+
+
 def test_missing_library_fails_loudly(monkeypatch):
     import paper_2105_11815_gb300 as pkg
     monkeypatch.setattr(pkg, "_lib", None)
