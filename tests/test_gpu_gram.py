@@ -33,7 +33,10 @@ def _solve(torch, pkg, A, b, **kw):
     return x.cpu().numpy(), R.cpu().numpy(), info
 
 
-@pytest.mark.parametrize("n,d,s,m", [(20000, 150, 2, 300), (8000, 64, 1, 200), (30000, 300, 3, 700)])
+# d = 1300 > 1024: the FP64 Cholesky runs in 512-column panels, the update
+# across panels from exact FP16 slice products on the tensor cores
+@pytest.mark.parametrize("n,d,s,m", [(20000, 150, 2, 300), (8000, 64, 1, 200), (30000, 300, 3, 700),
+                                     (40000, 1300, 2, 2600)])
 def test_gram_factor_matches_the_oracle(n, d, s, m):
     torch, pkg = cuda()
     rp, ci, v, b = workloads.csr_heavy_rows(n, d, seed=n + d, nnz_row=8, heavy_frac=1e-3, heavy_nnz=min(d, 100))
