@@ -19,14 +19,17 @@
 //     sum_r nnz(row r)^2 / 2 (G of a dense SA would cost m d^2 / 2).
 //  5. Blocked right-looking Cholesky in place (blocks of 64 columns): the
 //     diagonal block in one CTA, R12 = R11^{-T} G12 by forward substitution
-//     down each column of the panel (one thread per column), and
+//     down each column of the panel (four lanes per column in FP64), and
 //     G22 -= R12^T R12 on the SIMT GEMM restricted to tiles that meet the
-//     upper triangle.  A pivot that is not positive reports failure.
+//     upper triangle.  For d > 1024 the FP64 factorisation runs in panels of
+//     512 columns, the update across panels from exact FP16 slice products
+//     on the tensor cores.  A pivot that is not positive reports failure.
 //  6. c = SA^T Sb by columns of SA, then Q^T Sb = R^{-T} c by blocked forward
 //     substitution (the diagonal block in one CTA, the rest as GEMV updates).
 // On failure the caller factors the dense sketch by Householder QR instead.
 // The same Cholesky serves a dense sketch (ski_gram_dense_run), whose Gram
-// matrix is a GEMM.
+// matrix is a product on the tensor cores: 3xTF32 for FP32, exact FP16 slice
+// products summed in FP64 for FP64.
 #include <cuda_fp16.h>
 #include <math.h>
 
